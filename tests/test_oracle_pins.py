@@ -1,0 +1,379 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle
+itself: finite differences, closed-form trajectories, invariants, a dense
+KKT solve, a textbook scalar Riccati fixed point and an independent rotation
+library.  CPU only."""
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import workload as W
+
+QUAD = W.QUAD
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------ MLP (Eq. 4)
+
+@pytest.mark.parametrize("widths", [[17, 32, 32, 3], [17, 64, 64, 64, 3], [17, 8, 3]])
+def test_mlp_jacobian_vs_central_fd(orc, widths):
+    layers = W.xavier_mlp(widths, 3)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        z = rng.normal(0, 1, 17)
+        f, J = orc.mlp_fwd_jac(layers, z)
+        assert np.allclose(f, orc.mlp_forward(layers, z), rtol=0, atol=1e-15)
+        Jfd = np.zeros_like(J)
+        for j in range(17):
+            h = 1e-6 * max(1.0, abs(z[j]))
+            zp, zm = z.copy(), z.copy()
+            zp[j] += h; zm[j] -= h
+            Jfd[:, j] = (orc.mlp_forward(layers, zp) - orc.mlp_forward(layers, zm)) / (2 * h)
+        assert _rel(J, Jfd) < 1e-8
+
+
+def test_mlp_forward_vs_reverse_mode(orc):
+    layers = W.xavier_mlp([17, 128, 128, 128, 3], 5)
+    z = np.random.default_rng(2).normal(0, 2, 17)
+    _, J = orc.mlp_fwd_jac(layers, z)
+    assert _rel(J, orc.mlp_rev_jac(layers, z)) < 1e-13
+
+
+def test_mlp_single_unit_closed_form(orc):
+    # f = w2 tanh(w1 . z + b1) + b2 ; J = w2 (1 - tanh^2) w1
+    rng = np.random.default_rng(3)
+    w1, b1, w2, b2 = rng.normal(size=(1, 17)), rng.normal(size=1), rng.normal(size=(3, 1)), rng.normal(size=3)
+    z = rng.normal(size=17)
+    s = float((w1 @ z)[0] + b1[0])
+    f, J = orc.mlp_fwd_jac([(w1, b1), (w2, b2)], z)
+    assert np.allclose(f, w2[:, 0] * np.tanh(s) + b2, rtol=1e-15, atol=1e-15)
+    assert np.allclose(J, np.outer(w2[:, 0], w1[0]) * (1 - np.tanh(s) ** 2), rtol=1e-14, atol=1e-16)
+
+
+def test_mlp_zero_output_network(orc):
+    # the runtime-analysis network of Sec. IV is forced to output zero
+    layers = [(W_ * 0, b * 0) for W_, b in W.xavier_mlp([17, 16, 16, 3], 0)]
+    f, J = orc.mlp_fwd_jac(layers, np.ones(17))
+    assert not f.any() and not J.any()
+
+
+# ---------------------------------------------------------- nominal model (Eq. 6)
+
+def test_qrot_matches_rotation_library(orc):
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        v = rng.normal(size=3)
+        ref = Rotation.from_quat([q[1], q[2], q[3], q[0]]).apply(v)
+        assert np.allclose(orc.qrot(q, v), ref, atol=1e-14)
+    # literal q v q^*: scales by |q|^2 for a non-unit quaternion
+    q = np.array([2.0, 0, 0, 0])
+    assert np.allclose(orc.qrot(q, [1.0, 2.0, 3.0]), [4.0, 8.0, 12.0])
+
+
+def test_rotor_torques_from_fig3_geometry(orc):
+    # torque of each single rotor = r_i x (0,0,T) with the X-layout positions,
+    # yaw reaction -c_tau T for CCW rotors (0, 2), +c_tau T for CW (1, 3)
+    d = QUAD["arm"] / np.sqrt(2)
+    pos = np.array([[d, -d, 0], [-d, -d, 0], [-d, d, 0], [d, d, 0]])
+    spin = np.array([-1, 1, -1, 1])
+    J = np.array([QUAD["Jx"], QUAD["Jy"], QUAD["Jz"]])
+    x = np.zeros(13); x[3] = 1.0
+    for i in range(4):
+        u = np.zeros(4); u[i] = 2.0
+        tau = np.cross(pos[i], [0, 0, 2.0]) + [0, 0, spin[i] * QUAD["c_tau"] * 2.0]
+        assert np.allclose(orc.quad_f(QUAD, x, u)[10:], tau / J, atol=1e-12)
+
+
+def test_hover_is_equilibrium(orc):
+    x = np.zeros(13); x[3] = 1.0
+    u = np.full(4, W.hover_thrust())
+    assert np.abs(orc.quad_f(QUAD, x, u)).max() < 1e-14
+
+
+def test_free_fall_rk4_exact(orc):
+    # T = 0, omega = 0: p(t) = p0 + v0 t + 1/2 g t^2, exact for RK4
+    x = np.zeros(13)
+    x[0:3] = [0.3, -0.2, 1.0]
+    q = np.array([0.9, 0.1, -0.3, 0.2]); x[3:7] = q / np.linalg.norm(q)
+    x[7:10] = [1.0, -2.0, 0.5]
+    dt = 0.05
+    phi, A, B = orc.rk4_lin(QUAD, x, np.zeros(4), dt)
+    p = x[0:3] + x[7:10] * dt + 0.5 * np.array([0, 0, -QUAD["g"]]) * dt ** 2
+    assert np.allclose(phi[0:3], p, atol=1e-14)
+    assert np.allclose(phi[7:10], x[7:10] + np.array([0, 0, -QUAD["g"]]) * dt, atol=1e-14)
+    # the p-v block of A is dt * I exactly
+    assert np.allclose(A[0:3, 7:10], dt * np.eye(3), atol=1e-15)
+
+
+def test_torque_free_principal_spin(orc):
+    # omega along a principal axis with no torque stays constant; the
+    # attitude is q(t) = (cos(wt/2), 0, 0, sin(wt/2))
+    wz, dt = 2.0, 0.01
+    x = np.zeros(13); x[3] = 1.0; x[12] = wz
+    for _ in range(50):
+        x = orc.rk4_true(QUAD, x, np.zeros(4), dt)
+    t = 50 * dt
+    assert abs(x[12] - wz) < 1e-15
+    assert np.allclose(x[3:7], [np.cos(wz * t / 2), 0, 0, np.sin(wz * t / 2)], atol=1e-11)
+
+
+def test_dfdz_vs_central_fd(orc):
+    rng = np.random.default_rng(6)
+    X, U = W.random_nodes(4, 1)
+    for x, u in zip(X, U):
+        D = orc.quad_dfdz(QUAD, x, u)
+        z = np.concatenate([x, u])
+        Dfd = np.zeros_like(D)
+        for j in range(17):
+            h = 1e-6 * max(1.0, abs(z[j]))
+            zp, zm = z.copy(), z.copy()
+            zp[j] += h; zm[j] -= h
+            Dfd[:, j] = (orc.quad_f(QUAD, zp[:13], zp[13:]) - orc.quad_f(QUAD, zm[:13], zm[13:])) / (2 * h)
+        assert _rel(D, Dfd) < 1e-8
+
+
+# ------------------------------------------------- RK4 sensitivities (Eq. 2)
+
+def test_rk4_sensitivities_vs_fd(orc):
+    layers = W.xavier_mlp([17, 32, 32, 3], 1)
+    X, U = W.random_nodes(3, 2)
+    for x, u in zip(X, U):
+        fbar, J = orc.mlp_fwd_jac(layers, np.concatenate([x, u]))
+        phi, A, B = orc.rk4_lin(QUAD, x, u, 0.05, fbar, J)
+        z = np.concatenate([x, u])
+        G = np.zeros((13, 17))
+        for j in range(17):
+            h = 1e-6 * max(1.0, abs(z[j]))
+            zp, zm = z.copy(), z.copy()
+            zp[j] += h; zm[j] -= h
+            # the local model stays anchored at (x, u) while the stage moves
+            def ph(zz):
+                xx, uu = zz[:13], zz[13:]
+                f2 = fbar + J @ (zz - z)
+                return orc.rk4_lin(QUAD, xx, uu, 0.05, f2, J)[0]
+            G[:, j] = (ph(zp) - ph(zm)) / (2 * h)
+        assert _rel(np.hstack([A, B]), G) < 1e-8
+
+
+def test_local_model_error_is_third_order(orc):
+    # |phi(f_F + f_D*) - phi(f_F + f_D)| = O(dt^3): halving dt divides it by ~8
+    # (asymptotic regime: the thrust-driven stage offsets must be small)
+    layers = W.xavier_mlp([17, 32, 32, 3], 2)
+    X, U = W.random_nodes(6, 3)
+    for x, u in zip(X, U):
+        fbar, J = orc.mlp_fwd_jac(layers, np.concatenate([x, u]))
+        err = []
+        for dt in (0.002, 0.001, 0.0005):
+            loc = orc.rk4_lin(QUAD, x, u, dt, fbar, J)[0]
+            tru = orc.rk4_true(QUAD, x, u, dt, kind=2, layers=layers)
+            err.append(np.linalg.norm(loc - tru))
+        r1, r2 = err[0] / err[1], err[1] / err[2]
+        assert 7.5 < r1 < 8.5 and 7.5 < r2 < 8.5, (err, r1, r2)
+
+
+def test_zero_network_local_model_exact(orc):
+    layers = [(W_ * 0, b * 0) for W_, b in W.xavier_mlp([17, 16, 3], 0)]
+    x, u = W.random_nodes(1, 4)
+    fbar, J = orc.mlp_fwd_jac(layers, np.concatenate([x[0], u[0]]))
+    loc = orc.rk4_lin(QUAD, x[0], u[0], 0.05, fbar, J)[0]
+    assert np.array_equal(loc, orc.rk4_true(QUAD, x[0], u[0], 0.05, kind=2, layers=layers))
+    assert np.array_equal(loc, orc.rk4_true(QUAD, x[0], u[0], 0.05, kind=0))
+
+
+# --------------------------------------------------------- quaternion norm
+
+def test_plant_renormalises_quaternion(orc):
+    X, U = W.random_nodes(5, 5)
+    for x, u in zip(X, U):
+        x = x.copy(); x[3:7] /= np.linalg.norm(x[3:7])
+        xn = orc.plant_step(QUAD, x, u, 0.05, kind=1)
+        assert abs(np.linalg.norm(xn[3:7]) - 1.0) <= 4e-16
+
+
+@pytest.mark.parametrize("wz", [1.0, 5.0, 20.0])
+def test_rk4_quaternion_norm_drift_closed_form(orc, wz):
+    # constant spin about a principal axis with zero torque: the exact flow
+    # keeps |q| = 1, one RK4 step is the 4th-order Taylor polynomial of the
+    # rotation, whose modulus is sqrt(1 - th^6/72 + th^8/576), th = |w| dt / 2
+    dt = 0.05
+    x = np.zeros(13); x[3:7] = [0.8, 0.0, 0.0, 0.6]; x[12] = wz
+    u = np.full(4, 1.0)
+    xn = orc.rk4_true(QUAD, x, u, dt)
+    th = wz * dt / 2
+    assert abs(np.linalg.norm(xn[3:7]) - np.sqrt(1 - th ** 6 / 72 + th ** 8 / 576)) < 1e-15
+
+
+def test_drag_matches_rotation_library(orc):
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        v = rng.normal(0, 5, 3)
+        x = np.zeros(13); x[3:7] = q; x[7:10] = v
+        R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        ref = -R @ np.diag([0.3, 0.3, 0.1]) @ R.T @ v - 0.01 * np.linalg.norm(v) * v
+        assert np.allclose(orc.drag(x), ref, atol=1e-13)
+
+
+# ---------------------------------------------------------------- Riccati/QP
+
+def _random_qp(rng, N, nx=13, nu=4):
+    A = np.eye(nx) + 0.1 * rng.normal(size=(N, nx, nx))
+    B = 0.1 * rng.normal(size=(N, nx, nu))
+    c = 0.01 * rng.normal(size=(N, nx))
+    x = rng.normal(size=(N + 1, nx)); u = rng.normal(size=(N, nu))
+    xr = rng.normal(size=(N + 1, nx)); ur = rng.normal(size=(N, nu))
+    Q = rng.uniform(0.1, 10, nx); R = rng.uniform(0.05, 1, nu); QN = rng.uniform(0.1, 10, nx)
+    x0m = x[0] + 0.1 * rng.normal(size=nx)
+    return A, B, c, x, u, xr, ur, Q, R, QN, x0m
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5])
+def test_riccati_matches_dense_kkt(orc, N):
+    rng = np.random.default_rng(10 + N)
+    qp = _random_qp(rng, N)
+    st, dx, du = orc.riccati(*qp)
+    st2, dx2, du2 = orc.kkt_dense(*qp)
+    assert st == 0 and st2 == 0
+    assert _rel(dx, dx2) < 1e-10 and _rel(du, du2) < 1e-10
+
+
+def test_riccati_kkt_residual(orc):
+    # stationarity of the Lagrangian and primal feasibility at the solution
+    rng = np.random.default_rng(20)
+    N = 8
+    A, B, c, x, u, xr, ur, Q, R, QN, x0m = _random_qp(rng, N)
+    st, dx, du = orc.riccati(A, B, c, x, u, xr, ur, Q, R, QN, x0m)
+    assert st == 0
+    assert np.allclose(dx[0], x0m - x[0], atol=1e-12)
+    for k in range(N):
+        assert np.abs(dx[k + 1] - (A[k] @ dx[k] + B[k] @ du[k] + c[k])).max() < 1e-10
+    # adjoint recursion: lam_N = QN(x_N + dx_N - xr_N); lam_k = Q(...) + A' lam_{k+1}
+    lam = QN * (x[N] + dx[N] - xr[N])
+    for k in range(N - 1, -1, -1):
+        gu = R * (u[k] + du[k] - ur[k]) + B[k].T @ lam
+        assert np.abs(gu).max() < 1e-10
+        lam = Q * (x[k] + dx[k] - xr[k]) + A[k].T @ lam
+
+
+def test_scalar_riccati_golden_ratio(orc):
+    vals = dict(l.split() for l in open(os.path.join(GOLD, "scalar_lqr.txt")) if l[0] != "#")
+    N = 60
+    one = np.ones((N, 1, 1))
+    z = np.zeros
+    st, dx, du, K, k = orc.riccati(one, one, z((N, 1)), z((N + 1, 1)), z((N, 1)), z((N + 1, 1)),
+                                   z((N, 1)), np.ones(1), np.ones(1), np.ones(1), np.ones(1),
+                                   nx=1, nu=1, return_gains=True)
+    assert st == 0
+    assert abs(K[0, 0, 0] - float(vals["K_inf"])) < 1e-12
+    # the scalar recursion P <- q + a^2 P - (abP)^2/(r + b^2 P) from P_N = 1
+    P = 1.0
+    for _ in range(N):
+        P = 1 + P - P * P / (1 + P)
+    assert abs(P - float(vals["P_inf"])) < 1e-12
+    # closed loop from x0 = 1 decays by (1 + K) per step
+    assert abs(dx[1, 0] - (1 + K[0, 0, 0])) < 1e-12
+
+
+def test_riccati_reports_not_pd(orc):
+    rng = np.random.default_rng(21)
+    qp = list(_random_qp(rng, 3))
+    qp[8] = -np.ones(4)  # R negative definite, Q_N small
+    qp[9] = np.full(13, 1e-6)
+    qp[1] = qp[1] * 0
+    st, _, _ = orc.riccati(*qp)
+    assert st == 4
+
+
+# ------------------------------------------------------------------ RTI step
+
+def test_rti_step_on_reference_is_stationary(orc):
+    # hover at the reference point with the nominal model: the QP step is zero,
+    # u0 = hover, and the shifted iterate is unchanged
+    N = np.array([5], np.int32); dt = np.array([0.05])
+    x = np.zeros((6, 13)); x[:, 3] = 1.0; x[:, 0:3] = [0.5, -0.5, 1.0]
+    u = np.full((5, 4), W.hover_thrust())
+    u0, xn, un, st = orc.rti_step(QUAD, [], N, dt, W.Q_DIAG, W.R_DIAG, W.Q_DIAG, x, u, x.copy(),
+                                  u.copy(), x[:1].copy())
+    assert st[0] == 0
+    assert np.allclose(u0, W.hover_thrust(), atol=1e-12)
+    assert np.allclose(xn, x, atol=1e-12) and np.allclose(un, u, atol=1e-12)
+
+
+def test_rti_step_composition(orc):
+    # one RTI step equals linearise -> Riccati -> update -> clamp -> shift
+    prob = W.make_problem("cfg1_single_fp64", seed=3)
+    N, dt = prob["N"], prob["dt"]
+    X, U = W.random_nodes(int(N.sum()) + 1, 9)
+    x, u = X, U[:-1]
+    xref, uref = W.node_refs(prob)
+    x0m = x[:1] + 0.05
+    fD, JD, A, B, c = orc.linearize(QUAD, prob["layers"], N, dt, x, u)
+    st, dx, du = orc.riccati(A, B, c, x, u, xref, uref, prob["Q"], prob["R"], prob["QN"], x0m[0])
+    u0, xn, un, st2 = orc.rti_step(QUAD, prob["layers"], N, dt, prob["Q"], prob["R"], prob["QN"],
+                                   x, u, xref, uref, x0m)
+    xs, us = x + dx, u + du
+    assert np.allclose(u0[0], np.clip(us[0], 0, QUAD["u_max"]), atol=1e-13)
+    assert np.allclose(xn[:-1], xs[1:], atol=1e-13) and np.allclose(xn[-1], xs[-1], atol=1e-13)
+    assert np.allclose(un[:-1], us[1:], atol=1e-13) and np.allclose(un[-1], us[-1], atol=1e-13)
+
+
+def test_closed_loop_tracks_reference(orc):
+    # cfg1: single instance, circle r = 2 m at 3 m/s, 100 steps; the plant is
+    # the nominal model plus the same network, so the controller's model is
+    # exact up to the local approximation: the position error settles
+    prob = W.make_problem("cfg1_single_fp64", seed=0)
+    steps = 100
+    xrt, urt = W.trajectory_refs(prob, steps)
+    x0 = xrt[:, 0].copy()
+    traj, uh = orc.closed_loop(QUAD, prob["layers"], 2, prob["layers"], prob["N"], prob["dt"],
+                               prob["Q"], prob["R"], prob["QN"], x0, xrt, urt, steps)
+    err = np.linalg.norm(traj[:, 0, 0:3] - xrt[0, 1:steps + 1, 0:3], axis=1)
+    assert np.all(np.isfinite(traj))
+    assert err[-40:].mean() < 0.3
+    assert np.all(uh >= 0) and np.all(uh <= QUAD["u_max"])
+
+
+# ------------------------------------------------------------------ training
+
+def test_mse_gradient_vs_fd(orc):
+    layers = W.xavier_mlp([17, 16, 16, 3], 4)
+    X, U = W.training_samples(8, 0)
+    Z = np.concatenate([X, U], 1)
+    Y = orc.drag_targets(X)
+    loss, G = orc.mse_grad(layers, Z, Y)
+    rng = np.random.default_rng(0)
+    for l in range(len(layers)):
+        for _ in range(4):
+            i, j = rng.integers(layers[l][0].shape[0]), rng.integers(layers[l][0].shape[1])
+            h = 1e-6
+            Lp = [(w.copy(), b.copy()) for w, b in layers]; Lm = [(w.copy(), b.copy()) for w, b in layers]
+            Lp[l][0][i, j] += h; Lm[l][0][i, j] -= h
+            fd = (orc.mse_grad(Lp, Z, Y)[0] - orc.mse_grad(Lm, Z, Y)[0]) / (2 * h)
+            assert abs(fd - G[l][0][i, j]) < 1e-6 * max(1.0, abs(fd))
+        i = rng.integers(layers[l][1].shape[0])
+        Lp = [(w.copy(), b.copy()) for w, b in layers]; Lm = [(w.copy(), b.copy()) for w, b in layers]
+        Lp[l][1][i] += 1e-6; Lm[l][1][i] -= 1e-6
+        fd = (orc.mse_grad(Lp, Z, Y)[0] - orc.mse_grad(Lm, Z, Y)[0]) / 2e-6
+        assert abs(fd - G[l][1][i]) < 1e-6 * max(1.0, abs(fd))
+    # loss is the mean of squared errors over samples and outputs
+    pred = np.stack([orc.mlp_forward(layers, z) for z in Z])
+    assert abs(loss - ((pred - Y) ** 2).mean()) < 1e-13
+
+
+def test_adam_first_step_closed_form(orc):
+    # from zero moments, the bias-corrected first step is lr * g / (|g| + eps)
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p = np.array([1.0, 2.0, 3.0, 4.0]); p0 = p.copy()
+    m = np.zeros(4); v = np.zeros(4)
+    orc.adam(p, g, m, v, 1, 1e-3)
+    assert np.allclose(p, p0 - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    # second step with the same gradient: m_hat = g, v_hat = g^2 again
+    orc.adam(p, g, m, v, 2, 1e-3)
+    assert np.allclose(p, p0 - 2e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-14)
