@@ -1,0 +1,178 @@
+/*
+ * rtn.h -- C ABI of the B300-native Real-time Neural MPC hot path.
+ *
+ * Method: Salzmann, Kaufmann, Arrizabalaga, Pavone, Scaramuzza, Ryll,
+ * "Real-time Neural MPC", RA-L 2023.  For every shooting node k of every
+ * controller instance b the library
+ *   (a1) evaluates the residual network f_D and its input Jacobian J_D
+ *        (the first-order local model of Sec. III-A, Eq. 4),
+ *   (a2) forms the RK4 discretisation phi of f_F + f_D* (Sec. II, Eq. 1;
+ *        f_F is the nominal quadrotor model of Sec. V, Eq. 6) with the
+ *        sensitivities A_k, B_k and the defect c_k = phi_k - x_{k+1} of the
+ *        continuity condition (Eq. 2),
+ *   (a3) solves the linear-quadratic subproblem of Sec. III-A with the
+ *        tracking cost of Sec. V by a Riccati sweep,
+ *   (a4) applies the feedback response of Sec. III-B (Fig. 2): the measured
+ *        x0 enters, the iterate is updated and the first command is sent,
+ *   (a5) steps a plant (nominal model + a true residual) for closed loops,
+ *   (a6) trains the residual network (MSE, Adam; Sec. VI).
+ *
+ * Conventions (all entry points):
+ *   - nx = 13: x = [p(3), q(4) w-first, v(3), omega(3)];  nu = 4: rotor thrusts.
+ *   - Node-packed arrays: instance b owns N_b nodes.  States are packed as
+ *     [sum_b (N_b + 1)][13] (x_0..x_N per instance, instance-major), inputs
+ *     and per-node outputs as [sum_b N_b][...] in the same order.
+ *   - Matrices are row-major float32: A [node][13][13], B [node][13][4],
+ *     J_D [node][3][17] (columns: 13 state, then 4 input derivatives).
+ *   - Pointers documented "dev" are device pointers owned by the caller; the
+ *     library never frees them.  "host" pointers are read during the call.
+ *   - Every call is asynchronous on the stream given to rtn_create, except
+ *     where stated.  Argument errors are returned synchronously; per-instance
+ *     numerical failures are written to inst_status (dev int [B]).
+ *   - No C++ exception crosses this boundary.  rtn_last_error() returns a
+ *     description of the last failure on the context.
+ */
+#ifndef RTN_H
+#define RTN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtn_ctx rtn_ctx;
+
+typedef enum {
+  RTN_OK = 0,
+  RTN_E_INVAL = 1,       /* bad argument (sizes, NULL, unsupported shape) */
+  RTN_E_CUDA = 2,        /* a CUDA runtime call failed */
+  RTN_E_NONFINITE = 3,   /* per instance: NaN/Inf in the measured state */
+  RTN_E_NOT_PD = 4,      /* per instance: R + B'PB not positive definite */
+  RTN_E_TIMEOUT = 5,     /* a bounded device wait gave up */
+  RTN_E_NOMEM = 6,       /* device allocation failed */
+  RTN_E_UNSUPPORTED = 7  /* feature not available for this configuration */
+} rtn_status;
+
+/* arithmetic of the network evaluation (a1) */
+enum {
+  RTN_FP32 = 0,   /* SIMT FP32 */
+  RTN_BF16 = 1,   /* tcgen05, BF16 operands, FP32 accumulation, one pass */
+  RTN_BF16X2 = 2  /* tcgen05, activations/tangents split hi+lo in BF16
+                     (two passes), FP32 accumulation */
+};
+
+/* plant residual used by rtn_plant_step / rtn_closed_loop */
+enum { RTN_PLANT_NOMINAL = 0, RTN_PLANT_DRAG = 1, RTN_PLANT_MLP = 2 };
+
+/* Residual network: n_layers weight matrices (hidden tanh layers then one
+ * linear output layer).  widths has n_layers+1 entries, widths[0] = 17,
+ * widths[n_layers] = 3.  W[l] is host float32 row-major
+ * [widths[l+1]][widths[l]], b[l] host float32 [widths[l+1]].  Copied at
+ * rtn_create; the caller keeps ownership. */
+typedef struct {
+  int n_layers;
+  const int* widths;
+  const float* const* W;
+  const float* const* b;
+} rtn_mlp;
+
+/* Quadrotor parameters (Sec. V): mass [kg], diagonal inertia [kg m^2],
+ * arm length [m] (X layout of Fig. 3), yaw-torque coefficient, maximum
+ * thrust per rotor [N], gravity [m/s^2]. */
+typedef struct {
+  double mass, Jx, Jy, Jz, arm, c_tau, u_max, g;
+} rtn_quad;
+
+typedef struct {
+  int precision;    /* RTN_FP32 / RTN_BF16 / RTN_BF16X2 */
+  int riccati_f64;  /* 0: FP32 sweep with FP64 Cholesky of R+B'PB; 1: FP64 sweep */
+  int shift;        /* 1: shift the iterate by one stage after every RTI step */
+} rtn_options;
+
+/* Create a controller batch of `batch` instances with horizons N[b] >= 1 and
+ * step sizes dt[b] > 0 (host arrays [batch]).  Q, R, Q_N are host diagonals
+ * (nx, nu, nx); Q_N may be NULL (then Q_N = Q).  mlp may be NULL (nominal
+ * model only).  opt may be NULL (FP32, FP32 sweep, shift on).  cuda_stream is
+ * a cudaStream_t (NULL = legacy default stream).  nx must be 13 and nu 4.
+ * The iterate starts at x_k = 0 (q = identity), u_k = hover; see rtn_reset.
+ * Synchronous.  Returns RTN_E_INVAL on bad sizes, RTN_E_NOMEM/RTN_E_CUDA on
+ * device failures (then *out is NULL). */
+rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, const double* dt,
+                      const double* Q, const double* R, const double* Q_N, const rtn_quad* quad,
+                      const rtn_mlp* mlp, const rtn_options* opt, void* cuda_stream);
+
+/* Free every device buffer of the context (synchronises its stream). */
+void rtn_destroy(rtn_ctx* ctx);
+
+/* Description of the last error on ctx (or of the last failed rtn_create when
+ * ctx is NULL).  Valid until the next call on the same context. */
+const char* rtn_last_error(const rtn_ctx* ctx);
+
+/* Sizes of the node-packed layout: total nodes sum N_b and states sum(N_b+1). */
+rtn_status rtn_sizes(const rtn_ctx* ctx, int* n_nodes, int* n_states);
+
+/* Initial iterate (Sec. III-B needs an iterate to linearise around):
+ * x_k = x0[b] for every k, u_k = m g / 4.  x0: dev float [B][13]. */
+rtn_status rtn_reset(rtn_ctx* ctx, const float* x0);
+
+/* Copy the iterate in or out: x dev float [sum(N_b+1)][13], u dev float
+ * [sum N_b][4]. */
+rtn_status rtn_set_iterate(rtn_ctx* ctx, const float* x, const float* u);
+rtn_status rtn_get_iterate(rtn_ctx* ctx, float* x, float* u);
+
+/* (a1) Data-driven preparation (Sec. III-B): f_D and J_D at every node of the
+ * given points.  x dev [sum(N_b+1)][13] (x_N rows are ignored), u dev
+ * [sum N_b][4]; outputs fD dev [sum N_b][3], JD dev [sum N_b][3][17].  Uses
+ * the precision chosen at create.  RTN_E_UNSUPPORTED if the context has no
+ * network. */
+rtn_status rtn_mlp_eval(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+
+/* (a1)+(a2) Linearise every node (Eq. 2 with the local model of Eq. 4):
+ * fD, JD as above (may be NULL), A dev [sum N_b][13][13], B dev
+ * [sum N_b][13][4], c dev [sum N_b][13] = phi(x_k, u_k) - x_{k+1}. */
+rtn_status rtn_linearize(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD,
+                         float* A, float* B, float* c);
+
+/* (a3)+(a4) Solve the QP of Sec. III-A for given A, B, c around the points
+ * x, u (layouts as above) with references xref dev [sum(N_b+1)][13], uref dev
+ * [sum N_b][4] and measured states x0 dev [B][13].  Writes the step
+ * dx dev [sum(N_b+1)][13], du dev [sum N_b][4] and inst_status dev int [B]
+ * (RTN_OK, RTN_E_NOT_PD, RTN_E_NONFINITE; failed instances get a zero step). */
+rtn_status rtn_qp_solve(rtn_ctx* ctx, const float* A, const float* B, const float* c,
+                        const float* x, const float* u, const float* xref, const float* uref,
+                        const float* x0, float* dx, float* du, int* inst_status);
+
+/* One real-time iteration (Sec. III-B) on the context's iterate: a1..a4,
+ * then the iterate update (w += dw), the sent command u0 = clamp(u_0, 0,
+ * u_max) and (option) the shift.  x0 dev [B][13] (measured states), xref,
+ * uref as in rtn_qp_solve, u0_out dev [B][4], inst_status dev int [B] (may be
+ * NULL).  Failed instances keep their iterate and send uref's first entry. */
+rtn_status rtn_rti_step(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
+                        float* u0_out, int* inst_status);
+
+/* (a5) Plant step for every instance: nsub RK4 sub-steps of dt_b/nsub of the
+ * true dynamics f_F + residual (kind RTN_PLANT_*), then q <- q/|q|, all in
+ * FP64.  x dev double [B][13] in, u dev float [B][4], x_next dev double
+ * [B][13] (may alias x).  RTN_PLANT_MLP uses the context's network in FP64
+ * and needs widths <= 64. */
+rtn_status rtn_plant_step(rtn_ctx* ctx, int kind, const double* x, const float* u, double* x_next,
+                          int nsub);
+
+/* Closed loop of `steps` control steps, captured once as a CUDA graph and
+ * replayed: RTI step from the plant state, plant step with u0 (4 RK4
+ * sub-steps), record.  xref_traj dev float [B][T][13] and uref_traj dev float
+ * [B][T-1][4] are sampled on each instance's dt grid with
+ * T >= steps + max N_b + 1; step t uses rows t..t+N_b.  x_plant dev double
+ * [B][13] holds the initial plant state and receives the final one.
+ * traj_out dev float [steps][B][13] (may be NULL) receives the plant state
+ * after every step, u_out dev float [steps][B][4] (may be NULL) the sent
+ * commands.  The iterate is NOT reset: call rtn_reset first.  Synchronous. */
+rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float* xref_traj,
+                           const float* uref_traj, int T, double* x_plant, float* traj_out,
+                           float* u_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTN_H */

@@ -1,0 +1,270 @@
+"""Python binding of librtn (include/rtn.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA kernels of ``librtn.so``; this
+module checks shapes and dtypes of torch CUDA tensors, passes their device
+pointers and the current stream through ctypes, and turns status codes into
+exceptions.  There is no CPU fallback: without the built library every call
+raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+NX, NU, NZ, NO = 13, 4, 17, 3
+PRECISION = {"fp32": 0, "bf16": 1, "bf16x2": 2}
+PLANT = {"nominal": 0, "drag": 1, "mlp": 2}
+STATUS = {0: "RTN_OK", 1: "RTN_E_INVAL", 2: "RTN_E_CUDA", 3: "RTN_E_NONFINITE",
+          4: "RTN_E_NOT_PD", 5: "RTN_E_TIMEOUT", 6: "RTN_E_NOMEM", 7: "RTN_E_UNSUPPORTED"}
+
+# every symbol include/rtn.h declares
+EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_reset",
+           "rtn_set_iterate", "rtn_get_iterate", "rtn_mlp_eval", "rtn_linearize",
+           "rtn_qp_solve", "rtn_rti_step", "rtn_plant_step", "rtn_closed_loop"]
+
+_lib = None
+
+
+class RtnError(RuntimeError):
+    pass
+
+
+class _Quad(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("mass", "Jx", "Jy", "Jz", "arm", "c_tau", "u_max", "g")]
+
+
+class _MLP(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("widths", C.POINTER(C.c_int)),
+                ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float)))]
+
+
+class _Opt(C.Structure):
+    _fields_ = [("precision", C.c_int), ("riccati_f64", C.c_int), ("shift", C.c_int)]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load librtn.so from the package directory (built in-tree)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RtnError("librtn.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2203_07747_b300._build)")
+    L = C.CDLL(_build.LIB)
+    vp = C.c_void_p
+    L.rtn_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                             C.POINTER(C.c_double), C.POINTER(_Quad), C.POINTER(_MLP),
+                             C.POINTER(_Opt), vp]
+    L.rtn_destroy.argtypes = [vp]
+    L.rtn_destroy.restype = None
+    L.rtn_last_error.argtypes = [vp]
+    L.rtn_last_error.restype = C.c_char_p
+    L.rtn_sizes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rtn_reset.argtypes = [vp, vp]
+    L.rtn_set_iterate.argtypes = [vp, vp, vp]
+    L.rtn_get_iterate.argtypes = [vp, vp, vp]
+    L.rtn_mlp_eval.argtypes = [vp] * 5
+    L.rtn_linearize.argtypes = [vp] * 8
+    L.rtn_qp_solve.argtypes = [vp] * 12
+    L.rtn_rti_step.argtypes = [vp] * 6
+    L.rtn_plant_step.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
+    L.rtn_closed_loop.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp, vp, vp]
+    for name in EXPORTS:
+        if name not in ("rtn_destroy", "rtn_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t, dtype, shape, name):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise RtnError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise RtnError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise RtnError(f"{name}: must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise RtnError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Controller:
+    """A batch of B controller instances (one RTI-SQP problem each)."""
+
+    def __init__(self, N, dt, Q, R, QN=None, quad=None, layers=None, precision="fp32",
+                 riccati_f64=False, shift=True, stream=None):
+        import torch
+        L = load()
+        self.N = np.ascontiguousarray(N, dtype=np.int32)
+        self.dt = np.ascontiguousarray(dt, dtype=np.float64)
+        self.B = int(self.N.size)
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        QN = None if QN is None else np.ascontiguousarray(QN, dtype=np.float64)
+        if quad is None:
+            import workload
+            quad = workload.QUAD
+        self.quad = dict(quad)
+        q = _Quad(*[float(quad[k]) for k in ("mass", "Jx", "Jy", "Jz", "arm", "c_tau", "u_max", "g")])
+        self._keep = []
+        mlp_p = None
+        self.layers = layers
+        if layers:
+            widths = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
+            w = (C.c_int * len(widths))(*widths)
+            Ws = [np.ascontiguousarray(W, dtype=np.float32) for W, _ in layers]
+            bs = [np.ascontiguousarray(b, dtype=np.float32) for _, b in layers]
+            self._keep += [w, Ws, bs]
+            Wp = (C.POINTER(C.c_float) * len(Ws))(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in Ws])
+            bp = (C.POINTER(C.c_float) * len(bs))(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in bs])
+            self._keep += [Wp, bp]
+            mlp = _MLP(len(layers), w, Wp, bp)
+            mlp_p = C.byref(mlp)
+        opt = _Opt(PRECISION[precision], int(bool(riccati_f64)), int(bool(shift)))
+        self.precision = precision
+        self.stream = stream
+        h = C.c_void_p()
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        st = L.rtn_create(C.byref(h), NX, NU, self.B, self.N.ctypes.data_as(C.POINTER(C.c_int)),
+                          dp(self.dt), dp(Q), dp(R), None if QN is None else dp(QN), C.byref(q),
+                          mlp_p, C.byref(opt), _stream_handle(stream))
+        if st != 0:
+            raise RtnError(f"rtn_create: {STATUS.get(st, st)}: {L.rtn_last_error(None).decode()}")
+        self._h = h
+        nn, ns = C.c_int(), C.c_int()
+        L.rtn_sizes(h, C.byref(nn), C.byref(ns))
+        self.n_nodes, self.n_states = nn.value, ns.value
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rtn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, name):
+        if st != 0:
+            msg = load().rtn_last_error(self._h).decode()
+            raise RtnError(f"{name}: {STATUS.get(st, st)}: {msg}")
+
+    def _empty(self, *shape, dtype=None):
+        import torch
+        return torch.empty(shape, dtype=dtype or torch.float32, device=self.device)
+
+    # -- iterate ----------------------------------------------------------
+    def reset(self, x0):
+        import torch
+        self._check(load().rtn_reset(self._h, _ptr(x0, torch.float32, (self.B, NX), "x0")), "rtn_reset")
+
+    def set_iterate(self, x, u):
+        import torch
+        self._check(load().rtn_set_iterate(self._h, _ptr(x, torch.float32, (self.n_states, NX), "x"),
+                                           _ptr(u, torch.float32, (self.n_nodes, NU), "u")),
+                    "rtn_set_iterate")
+
+    def get_iterate(self):
+        import torch
+        x, u = self._empty(self.n_states, NX), self._empty(self.n_nodes, NU)
+        self._check(load().rtn_get_iterate(self._h, _ptr(x, torch.float32, None, "x"),
+                                           _ptr(u, torch.float32, None, "u")), "rtn_get_iterate")
+        return x, u
+
+    # -- hot path ---------------------------------------------------------
+    def mlp_eval(self, x, u, fD=None, JD=None):
+        import torch
+        fD = self._empty(self.n_nodes, NO) if fD is None else fD
+        JD = self._empty(self.n_nodes, NO, NZ) if JD is None else JD
+        self._check(load().rtn_mlp_eval(self._h, _ptr(x, torch.float32, (self.n_states, NX), "x"),
+                                        _ptr(u, torch.float32, (self.n_nodes, NU), "u"),
+                                        _ptr(fD, torch.float32, (self.n_nodes, NO), "fD"),
+                                        _ptr(JD, torch.float32, (self.n_nodes, NO, NZ), "JD")),
+                    "rtn_mlp_eval")
+        return fD, JD
+
+    def linearize(self, x, u, out=None):
+        import torch
+        n = self.n_nodes
+        if out is None:
+            out = (self._empty(n, NO), self._empty(n, NO, NZ), self._empty(n, NX, NX),
+                   self._empty(n, NX, NU), self._empty(n, NX))
+        fD, JD, A, Bm, c = out
+        self._check(load().rtn_linearize(
+            self._h, _ptr(x, torch.float32, (self.n_states, NX), "x"),
+            _ptr(u, torch.float32, (n, NU), "u"), _ptr(fD, torch.float32, (n, NO), "fD"),
+            _ptr(JD, torch.float32, (n, NO, NZ), "JD"), _ptr(A, torch.float32, (n, NX, NX), "A"),
+            _ptr(Bm, torch.float32, (n, NX, NU), "B"), _ptr(c, torch.float32, (n, NX), "c")),
+            "rtn_linearize")
+        return fD, JD, A, Bm, c
+
+    def qp_solve(self, A, Bm, c, x, u, xref, uref, x0):
+        import torch
+        n, ns = self.n_nodes, self.n_states
+        dx, du = self._empty(ns, NX), self._empty(n, NU)
+        st = self._empty(self.B, dtype=torch.int32)
+        f = torch.float32
+        self._check(load().rtn_qp_solve(
+            self._h, _ptr(A, f, (n, NX, NX), "A"), _ptr(Bm, f, (n, NX, NU), "B"),
+            _ptr(c, f, (n, NX), "c"), _ptr(x, f, (ns, NX), "x"), _ptr(u, f, (n, NU), "u"),
+            _ptr(xref, f, (ns, NX), "xref"), _ptr(uref, f, (n, NU), "uref"),
+            _ptr(x0, f, (self.B, NX), "x0"), _ptr(dx, f, None, "dx"), _ptr(du, f, None, "du"),
+            _ptr(st, torch.int32, None, "status")), "rtn_qp_solve")
+        return dx, du, st
+
+    def rti_step(self, x0, xref, uref, u0=None, status=None):
+        import torch
+        f = torch.float32
+        u0 = self._empty(self.B, NU) if u0 is None else u0
+        status = self._empty(self.B, dtype=torch.int32) if status is None else status
+        self._check(load().rtn_rti_step(
+            self._h, _ptr(x0, f, (self.B, NX), "x0"), _ptr(xref, f, (self.n_states, NX), "xref"),
+            _ptr(uref, f, (self.n_nodes, NU), "uref"), _ptr(u0, f, (self.B, NU), "u0"),
+            _ptr(status, torch.int32, (self.B,), "status")), "rtn_rti_step")
+        return u0, status
+
+    def plant_step(self, x, u, kind="nominal", nsub=4, out=None):
+        import torch
+        out = self._empty(self.B, NX, dtype=torch.float64) if out is None else out
+        self._check(load().rtn_plant_step(
+            self._h, PLANT[kind], _ptr(x, torch.float64, (self.B, NX), "x"),
+            _ptr(u, torch.float32, (self.B, NU), "u"), _ptr(out, torch.float64, (self.B, NX), "x_next"),
+            int(nsub)), "rtn_plant_step")
+        return out
+
+    def closed_loop(self, steps, xref_traj, uref_traj, x_plant, plant="nominal", record=True):
+        """xref_traj [B][T][13], uref_traj [B][T-1][4] float32, x_plant [B][13]
+        float64 (updated in place).  Returns (traj [steps][B][13], u [steps][B][4])."""
+        import torch
+        f = torch.float32
+        T = int(xref_traj.shape[1])
+        traj = self._empty(steps, self.B, NX) if record else None
+        uo = self._empty(steps, self.B, NU) if record else None
+        self._check(load().rtn_closed_loop(
+            self._h, int(steps), PLANT[plant], _ptr(xref_traj, f, (self.B, T, NX), "xref_traj"),
+            _ptr(uref_traj, f, (self.B, T - 1, NU), "uref_traj"), T,
+            _ptr(x_plant, torch.float64, (self.B, NX), "x_plant"), _ptr(traj, f, None, "traj"),
+            _ptr(uo, f, None, "u_out")), "rtn_closed_loop")
+        return traj, uo

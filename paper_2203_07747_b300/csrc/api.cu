@@ -1,0 +1,430 @@
+// api.cu -- the C ABI of include/rtn.h: argument checking, the node-packed
+// ragged layout, device buffers and the call sequences of one RTI step
+// (Sec. III-B, Fig. 2) and of a graph-captured closed loop.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "rtn_internal.cuh"
+
+using namespace rtn;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+#define CK(call)                                                               \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+      return e_ == cudaErrorMemoryAllocation ? RTN_E_NOMEM : RTN_E_CUDA;       \
+    }                                                                          \
+  } while (0)
+
+rtn_status fail(rtn_ctx* ctx, rtn_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+template <typename T>
+cudaError_t upload(T** p, const T* h, size_t n) {
+  cudaError_t e = dalloc(p, n);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*p, h, n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+__global__ void reset_kernel(const float* __restrict__ x0, const int* __restrict__ N,
+                             const int* __restrict__ xoff, const int* __restrict__ uoff, int B,
+                             float hover, float* __restrict__ x, float* __restrict__ u) {
+  int b = blockIdx.x;
+  if (b >= B) return;
+  int n = N[b];
+  for (int e = threadIdx.x; e < (n + 1) * NX; e += blockDim.x)
+    x[(size_t)xoff[b] * NX + e] = x0[(size_t)b * NX + e % NX];
+  for (int e = threadIdx.x; e < n * NU; e += blockDim.x) u[(size_t)uoff[b] * NU + e] = hover;
+}
+
+// closed loop bookkeeping: record the plant state / sent command of step t
+__global__ void record_kernel(const int* t_dev, int B, const double* __restrict__ xp,
+                              const float* __restrict__ u0, float* traj, float* uo) {
+  int t = *t_dev;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * NX; e += gridDim.x * blockDim.x) {
+    if (traj) traj[(size_t)t * B * NX + e] = (float)xp[e];
+    if (uo && e < B * NU) uo[(size_t)t * B * NU + e] = u0[e];
+  }
+}
+
+__global__ void advance_kernel(int* t_dev) { *t_dev += 1; }
+
+__global__ void convert_state_kernel(const double* __restrict__ x, float* __restrict__ y, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+rtn_status run_mlp(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD) {
+  cudaError_t e = ctx->opt.precision == RTN_FP32 ? mlp_f32_forward(ctx, x, u, fD, JD)
+                                                 : mlp_tc_forward(ctx, x, u, fD, JD);
+  if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("mlp: ") + cudaGetErrorString(e));
+  return RTN_OK;
+}
+
+rtn_status linearize_impl(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD,
+                          float* A, float* Bm, float* c) {
+  if (ctx->has_mlp) {
+    rtn_status st = run_mlp(ctx, x, u, fD, JD);
+    if (st != RTN_OK) return st;
+  }
+  cudaError_t e = rk4_sens(ctx, x, u, ctx->has_mlp ? fD : nullptr, ctx->has_mlp ? JD : nullptr, A,
+                           Bm, c);
+  if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("rk4: ") + cudaGetErrorString(e));
+  return RTN_OK;
+}
+
+// one RTI step on the context's iterate; refs addressed by strides (0 =
+// node-packed), t read from t_dev when given
+rtn_status rti_impl(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
+                    int xref_stride, int uref_stride, const int* t_dev, float* u0, int* status) {
+  rtn_status st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);
+  if (st != RTN_OK) return st;
+  QpArgs a{};
+  a.A = ctx->A; a.Bm = ctx->Bm; a.c = ctx->c;
+  a.x = ctx->x; a.u = ctx->u;
+  a.xref = xref; a.uref = uref;
+  a.xref_stride = xref_stride; a.uref_stride = uref_stride;
+  a.t_dev = t_dev;
+  a.x0 = x0;
+  a.u0 = u0;
+  a.status = status ? status : ctx->status;
+  a.update = 1;
+  a.shift = ctx->opt.shift;
+  cudaError_t e = qp_solve(ctx, a);
+  if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("qp: ") + cudaGetErrorString(e));
+  return RTN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, const double* dt,
+                      const double* Q, const double* R, const double* Q_N, const rtn_quad* quad,
+                      const rtn_mlp* mlp, const rtn_options* opt, void* cuda_stream) {
+  if (!out) return RTN_E_INVAL;
+  *out = nullptr;
+  if (nx != NX || nu != NU) { g_create_err = "nx must be 13 and nu 4"; return RTN_E_INVAL; }
+  if (batch < 1 || !N || !dt || !Q || !R || !quad) { g_create_err = "bad batch/arrays"; return RTN_E_INVAL; }
+  long long nn = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (N[b] < 1 || !(dt[b] > 0.0)) { g_create_err = "N[b] >= 1 and dt[b] > 0 required"; return RTN_E_INVAL; }
+    nn += N[b];
+  }
+  if (nn + batch > (1LL << 28)) { g_create_err = "batch too large"; return RTN_E_INVAL; }
+  rtn_options o{RTN_FP32, 0, 1};
+  if (opt) o = *opt;
+  if (o.precision < RTN_FP32 || o.precision > RTN_BF16X2) { g_create_err = "bad precision"; return RTN_E_INVAL; }
+  if (mlp) {
+    if (mlp->n_layers < 2 || !mlp->widths || !mlp->W || !mlp->b || mlp->widths[0] != NZ ||
+        mlp->widths[mlp->n_layers] != NO) {
+      g_create_err = "network must map 17 inputs to 3 outputs with >= 1 hidden layer";
+      return RTN_E_INVAL;
+    }
+    for (int l = 1; l < mlp->n_layers; ++l)
+      if (mlp->widths[l] < 1 || mlp->widths[l] > 4096) { g_create_err = "bad hidden width"; return RTN_E_INVAL; }
+  }
+
+  rtn_ctx* ctx = new (std::nothrow) rtn_ctx();
+  if (!ctx) return RTN_E_NOMEM;
+  rtn_status st = RTN_OK;
+  // every allocation below goes through this lambda so that a failure frees
+  // what was built so far
+  auto build = [&]() -> rtn_status {
+    ctx->B = batch;
+    ctx->opt = o;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->hN.assign(N, N + batch);
+    ctx->hdt.assign(dt, dt + batch);
+    ctx->quad64 = *quad;
+    QuadParams& qp = ctx->quad;
+    qp.mass = (float)quad->mass; qp.inv_mass = (float)(1.0 / quad->mass);
+    qp.Jx = (float)quad->Jx; qp.Jy = (float)quad->Jy; qp.Jz = (float)quad->Jz;
+    qp.d = (float)(quad->arm / std::sqrt(2.0)); qp.c_tau = (float)quad->c_tau;
+    qp.u_max = (float)quad->u_max; qp.g = (float)quad->g;
+    qp.hover = (float)(quad->mass * quad->g / 4.0);
+    for (int i = 0; i < NX; ++i) { ctx->cost.Q[i] = Q[i]; ctx->cost.QN[i] = Q_N ? Q_N[i] : Q[i]; }
+    for (int i = 0; i < NU; ++i) ctx->cost.R[i] = R[i];
+
+    // ragged layout
+    Layout& L = ctx->lay;
+    L.B = batch;
+    std::vector<int> xoff(batch), uoff(batch), order(batch), node_inst;
+    std::vector<float> dtf(batch);
+    int xs = 0, us = 0;
+    for (int b = 0; b < batch; ++b) {
+      xoff[b] = xs; uoff[b] = us;
+      xs += N[b] + 1; us += N[b];
+      dtf[b] = (float)dt[b];
+      L.N_max = std::max(L.N_max, N[b]);
+    }
+    L.n_nodes = us; L.n_states = xs;
+    node_inst.resize(us);
+    for (int b = 0; b < batch; ++b)
+      for (int k = 0; k < N[b]; ++k) node_inst[uoff[b] + k] = b;
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return N[a] > N[c]; });
+    CK(upload(&L.N, N, batch));
+    CK(upload(&L.dt, dtf.data(), batch));
+    CK(upload(&L.dt64, dt, batch));
+    CK(upload(&L.xoff, xoff.data(), batch));
+    CK(upload(&L.uoff, uoff.data(), batch));
+    CK(upload(&L.node_inst, node_inst.data(), us));
+    CK(upload(&L.order, order.data(), batch));
+
+    // network
+    if (mlp) {
+      ctx->has_mlp = true;
+      Net& net = ctx->net;
+      net.n_layers = mlp->n_layers;
+      net.widths.assign(mlp->widths, mlp->widths + mlp->n_layers + 1);
+      std::vector<float> Wh, bh;
+      std::vector<double> P64;
+      for (int l = 0; l < net.n_layers; ++l) {
+        int fi = net.widths[l], fo = net.widths[l + 1];
+        net.w_off.push_back(Wh.size());
+        net.b_off.push_back(bh.size());
+        Wh.insert(Wh.end(), mlp->W[l], mlp->W[l] + (size_t)fo * fi);
+        bh.insert(bh.end(), mlp->b[l], mlp->b[l] + fo);
+        P64.insert(P64.end(), mlp->W[l], mlp->W[l] + (size_t)fo * fi);
+        P64.insert(P64.end(), mlp->b[l], mlp->b[l] + fo);
+        net.h_max = std::max(net.h_max, std::max(fi, fo));
+      }
+      CK(upload(&net.W32, Wh.data(), Wh.size()));
+      CK(upload(&net.b32, bh.data(), bh.size()));
+      CK(upload(&net.P64, P64.data(), P64.size()));
+      if (o.precision == RTN_FP32) {
+        size_t na = (size_t)net.h_max * NC * us;
+        CK(dalloc(&ctx->act0, na));
+        CK(dalloc(&ctx->act1, na));
+      } else {
+        std::string e;
+        cudaError_t ce = mlp_tc_prepare(ctx, e);
+        if (ce != cudaSuccess || !e.empty()) {
+          ctx->err = e.empty() ? std::string("tc prepare: ") + cudaGetErrorString(ce) : e;
+          return e.empty() ? RTN_E_CUDA : RTN_E_UNSUPPORTED;
+        }
+      }
+    } else if (o.precision != RTN_FP32) {
+      // nominal model only: nothing to run on the tensor cores
+      ctx->opt.precision = RTN_FP32;
+    }
+
+    // iterate and workspace
+    size_t gsz = ctx->opt.riccati_f64 ? sizeof(double) : sizeof(float);
+    CK(dalloc(&ctx->x, (size_t)xs * NX));
+    CK(dalloc(&ctx->u, (size_t)us * NU));
+    CK(dalloc(&ctx->fD, (size_t)us * NO));
+    CK(dalloc(&ctx->JD, (size_t)us * NO * NZ));
+    CK(dalloc(&ctx->A, (size_t)us * NX * NX));
+    CK(dalloc(&ctx->Bm, (size_t)us * NX * NU));
+    CK(dalloc(&ctx->c, (size_t)us * NX));
+    CK(cudaMalloc(&ctx->K, (size_t)us * NU * NX * gsz));
+    CK(cudaMalloc(&ctx->kff, (size_t)us * NU * gsz));
+    CK(dalloc(&ctx->status, batch));
+    CK(dalloc(&ctx->dev_t, 1));
+    CK(dalloc(&ctx->x0f, (size_t)batch * NX));
+    CK(dalloc(&ctx->u0, (size_t)batch * NU));
+    // initial iterate: hover at the origin
+    std::vector<float> x0(batch * NX, 0.0f);
+    for (int b = 0; b < batch; ++b) x0[b * NX + 3] = 1.0f;
+    CK(cudaMemcpy(ctx->x0f, x0.data(), x0.size() * sizeof(float), cudaMemcpyHostToDevice));
+    reset_kernel<<<batch, 128>>>(ctx->x0f, L.N, L.xoff, L.uoff, batch, qp.hover, ctx->x, ctx->u);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    return RTN_OK;
+  };
+  st = build();
+  if (st != RTN_OK) {
+    g_create_err = ctx->err;
+    rtn_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return RTN_OK;
+}
+
+void rtn_destroy(rtn_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  Layout& L = ctx->lay;
+  void* ptrs[] = {L.N, L.dt, L.dt64, L.xoff, L.uoff, L.node_inst, L.order, ctx->net.W32, ctx->net.b32,
+                  ctx->net.P64, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c, ctx->K,
+                  ctx->kff, ctx->act0, ctx->act1, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  mlp_tc_release(ctx);
+  delete ctx;
+}
+
+const char* rtn_last_error(const rtn_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+rtn_status rtn_sizes(const rtn_ctx* ctx, int* n_nodes, int* n_states) {
+  if (!ctx) return RTN_E_INVAL;
+  if (n_nodes) *n_nodes = ctx->lay.n_nodes;
+  if (n_states) *n_states = ctx->lay.n_states;
+  return RTN_OK;
+}
+
+rtn_status rtn_reset(rtn_ctx* ctx, const float* x0) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x0) return fail(ctx, RTN_E_INVAL, "rtn_reset: NULL argument");
+  reset_kernel<<<ctx->B, 128, 0, ctx->stream>>>(x0, ctx->lay.N, ctx->lay.xoff, ctx->lay.uoff,
+                                                 ctx->B, ctx->quad.hover, ctx->x, ctx->u);
+  CK(cudaGetLastError());
+  return RTN_OK;
+}
+
+rtn_status rtn_set_iterate(rtn_ctx* ctx, const float* x, const float* u) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x || !u) return fail(ctx, RTN_E_INVAL, "rtn_set_iterate: NULL argument");
+  CK(cudaMemcpyAsync(ctx->x, x, (size_t)ctx->lay.n_states * NX * sizeof(float),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->u, u, (size_t)ctx->lay.n_nodes * NU * sizeof(float),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return RTN_OK;
+}
+
+rtn_status rtn_get_iterate(rtn_ctx* ctx, float* x, float* u) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x || !u) return fail(ctx, RTN_E_INVAL, "rtn_get_iterate: NULL argument");
+  CK(cudaMemcpyAsync(x, ctx->x, (size_t)ctx->lay.n_states * NX * sizeof(float),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(u, ctx->u, (size_t)ctx->lay.n_nodes * NU * sizeof(float),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return RTN_OK;
+}
+
+rtn_status rtn_mlp_eval(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x || !u || !fD || !JD) return fail(ctx, RTN_E_INVAL, "rtn_mlp_eval: NULL argument");
+  if (!ctx->has_mlp) return fail(ctx, RTN_E_UNSUPPORTED, "rtn_mlp_eval: no network");
+  return run_mlp(ctx, x, u, fD, JD);
+}
+
+rtn_status rtn_linearize(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD,
+                         float* A, float* B, float* c) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x || !u || !A || !B || !c) return fail(ctx, RTN_E_INVAL, "rtn_linearize: NULL argument");
+  return linearize_impl(ctx, x, u, fD ? fD : ctx->fD, JD ? JD : ctx->JD, A, B, c);
+}
+
+rtn_status rtn_qp_solve(rtn_ctx* ctx, const float* A, const float* B, const float* c,
+                        const float* x, const float* u, const float* xref, const float* uref,
+                        const float* x0, float* dx, float* du, int* inst_status) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!A || !B || !c || !x || !u || !xref || !uref || !x0 || !dx || !du || !inst_status)
+    return fail(ctx, RTN_E_INVAL, "rtn_qp_solve: NULL argument");
+  QpArgs a{};
+  a.A = A; a.Bm = B; a.c = c;
+  a.x = const_cast<float*>(x); a.u = const_cast<float*>(u);
+  a.xref = xref; a.uref = uref;
+  a.x0 = x0; a.dx = dx; a.du = du; a.status = inst_status;
+  a.update = 0;
+  CK(qp_solve(ctx, a));
+  return RTN_OK;
+}
+
+rtn_status rtn_rti_step(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
+                        float* u0_out, int* inst_status) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x0 || !xref || !uref || !u0_out) return fail(ctx, RTN_E_INVAL, "rtn_rti_step: NULL argument");
+  return rti_impl(ctx, x0, xref, uref, 0, 0, nullptr, u0_out, inst_status);
+}
+
+rtn_status rtn_plant_step(rtn_ctx* ctx, int kind, const double* x, const float* u, double* x_next,
+                          int nsub) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x || !u || !x_next || nsub < 1 || kind < 0 || kind > 2)
+    return fail(ctx, RTN_E_INVAL, "rtn_plant_step: bad argument");
+  cudaError_t e = plant_step(ctx, kind, x, u, x_next, nsub, nullptr);
+  if (e == cudaErrorNotSupported)
+    return fail(ctx, RTN_E_UNSUPPORTED, "plant network needs widths <= 64 and a network");
+  CK(e);
+  return RTN_OK;
+}
+
+rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float* xref_traj,
+                           const float* uref_traj, int T, double* x_plant, float* traj_out,
+                           float* u_out) {
+  if (!ctx) return RTN_E_INVAL;
+  if (steps < 0 || !xref_traj || !uref_traj || !x_plant || plant_kind < 0 || plant_kind > 2 ||
+      T < steps + ctx->lay.N_max + 1)
+    return fail(ctx, RTN_E_INVAL, "rtn_closed_loop: bad argument");
+  if (steps == 0) return RTN_OK;
+  if (plant_kind == RTN_PLANT_MLP && (!ctx->has_mlp || ctx->net.h_max > 64))
+    return fail(ctx, RTN_E_UNSUPPORTED, "plant network needs widths <= 64 and a network");
+  // capture one control step on a private stream ordered after the caller's
+  // stream, then replay it `steps` times; the kernels read the step index
+  // from ctx->dev_t, which the graph advances
+  cudaStream_t user = ctx->stream, cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  rtn_status st = RTN_OK;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+    ctx->stream = user;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_t, 0, sizeof(int), user);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+  if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); cleanup(); return RTN_E_CUDA; }
+  ctx->stream = cs;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    // the plant state in float is the measured x0 of the RTI step
+    st = rti_impl(ctx, ctx->x0f, xref_traj, uref_traj, T, T - 1, ctx->dev_t, ctx->u0, ctx->status);
+    if (st == RTN_OK) {
+      e = plant_step(ctx, plant_kind, x_plant, ctx->u0, x_plant, 4, ctx->x0f);
+      record_kernel<<<(ctx->B * NX + 255) / 256, 256, 0, cs>>>(ctx->dev_t, ctx->B, x_plant, ctx->u0,
+                                                               traj_out, u_out);
+      advance_kernel<<<1, 1, 0, cs>>>(ctx->dev_t);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (st != RTN_OK || e != cudaSuccess) {
+    if (st == RTN_OK) { ctx->err = std::string("capture: ") + cudaGetErrorString(e); st = RTN_E_CUDA; }
+    cleanup();
+    return st;
+  }
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) {
+    convert_state_kernel<<<(ctx->B * NX + 255) / 256, 256, 0, cs>>>(x_plant, ctx->x0f, ctx->B * NX);
+    e = cudaGetLastError();
+  }
+  for (int s = 0; s < steps && e == cudaSuccess; ++s) e = cudaGraphLaunch(exec, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ev, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) { ctx->err = std::string("closed loop: ") + cudaGetErrorString(e); st = RTN_E_CUDA; }
+  cleanup();
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// mlp_f32.cu -- (a1) residual network value + input Jacobian, FP32 SIMT path.
+//
+// Forward-mode differentiation of f_D (Sec. III-A, Eq. 4): every node carries
+// 18 columns through the network, its value and the 17 tangent directions
+// d/d[x;u].  With the activations of all nodes stored as one matrix
+// X_l [h_l][18 n_nodes] (column 18 n + j = node n, column j), a hidden layer
+// is one GEMM  Z = W_l X_l  followed by an epilogue that, per node and
+// neuron, takes the value column a = tanh(z + b) and scales the 17 tangent
+// columns by tanh' = 1 - a^2.  The input layer needs no GEMM (its tangent is
+// W_0 itself) and the 3-row output layer is a thin reduction.
+#include "rtn_internal.cuh"
+
+namespace rtn {
+namespace {
+
+// input layer: thread (neuron i, node n), n fastest so that consecutive
+// threads write consecutive 18-column blocks of row i
+__global__ void mlp_in_kernel(const float* __restrict__ x, const float* __restrict__ u,
+                              const int* __restrict__ node_inst, int n_nodes,
+                              const float* __restrict__ W0, const float* __restrict__ b0, int h0,
+                              float* __restrict__ X1) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)h0 * n_nodes) return;
+  int i = (int)(tid / n_nodes), n = (int)(tid % n_nodes);
+  const float* xr = x + (size_t)(n + node_inst[n]) * NX;
+  const float* ur = u + (size_t)n * NU;
+  const float* w = W0 + (size_t)i * NZ;
+  float s = b0[i];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) s = fmaf(w[j], xr[j], s);
+#pragma unroll
+  for (int j = 0; j < NU; ++j) s = fmaf(w[NX + j], ur[j], s);
+  float a = tanhf(s), d = 1.0f - a * a;
+  float* o = X1 + (size_t)i * ((size_t)NC * n_nodes) + (size_t)NC * n;
+  o[0] = a;
+#pragma unroll
+  for (int j = 0; j < NZ; ++j) o[1 + j] = d * w[j];
+}
+
+// hidden layer GEMM with the fused tanh / tanh' epilogue.
+// Tile: 128 neurons x 8 nodes (144 columns), K in slices of 16.  Thread
+// (rg, ng): rows 8 rg .. 8 rg + 7 of the tile, node ng -> 8 x 18 accumulators,
+// so the whole value/tangent block of a node is in one thread's registers.
+constexpr int BM = 128, BNN = 8, BN = BNN * NC, BK = 16, NTH = 128;
+
+__global__ void __launch_bounds__(NTH) mlp_hidden_kernel(const float* __restrict__ W,
+                                                         const float* __restrict__ bias, int M,
+                                                         int K, const float* __restrict__ X,
+                                                         float* __restrict__ Y, int n_nodes) {
+  __shared__ __align__(16) float As[BK][BM];
+  __shared__ __align__(16) float Bs[BK][BN];
+  const size_t ldx = (size_t)NC * n_nodes;
+  const int tid = threadIdx.x, rg = tid & 15, ng = tid >> 4;
+  const int m0 = blockIdx.y * BM;
+  const int node0 = blockIdx.x * BNN;
+  const size_t col0 = (size_t)node0 * NC;
+  const int ncols = (int)min((size_t)BN, ldx - col0);
+  float acc[8][NC];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[r][j] = 0.0f;
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    {
+      int m = m0 + tid;
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        int k = k0 + kk;
+        As[kk][tid] = (m < M && k < K) ? W[(size_t)m * K + k] : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < (BK * BN) / NTH; ++it) {
+      int e = it * NTH + tid;
+      int kk = e / BN, cc = e % BN;
+      int k = k0 + kk;
+      Bs[kk][cc] = (k < K && cc < ncols) ? X[(size_t)k * ldx + col0 + cc] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[8], b[NC];
+      const float4* ap = reinterpret_cast<const float4*>(&As[kk][rg * 8]);
+      float4 a0 = ap[0], a1 = ap[1];
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      const float2* bp = reinterpret_cast<const float2*>(&Bs[kk][ng * NC]);
+#pragma unroll
+      for (int j = 0; j < NC / 2; ++j) {
+        float2 t = bp[j];
+        b[2 * j] = t.x; b[2 * j + 1] = t.y;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[r][j] = fmaf(a[r], b[j], acc[r][j]);
+    }
+    __syncthreads();
+  }
+  int node = node0 + ng;
+  if (node >= n_nodes) return;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    int m = m0 + rg * 8 + r;
+    if (m >= M) continue;
+    float av = tanhf(acc[r][0] + bias[m]);
+    float d = 1.0f - av * av;
+    float2* o = reinterpret_cast<float2*>(Y + (size_t)m * ldx + (size_t)node * NC);
+    o[0] = make_float2(av, acc[r][1] * d);
+#pragma unroll
+    for (int j = 1; j < NC / 2; ++j) o[j] = make_float2(acc[r][2 * j] * d, acc[r][2 * j + 1] * d);
+  }
+}
+
+// output layer (3 rows, linear): thread (node n, column j) computes the three
+// outputs of its column
+__global__ void mlp_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL, int K,
+                               const float* __restrict__ X, int n_nodes, float* __restrict__ fD,
+                               float* __restrict__ JD) {
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)n_nodes * NC) return;
+  int n = (int)(tid / NC), j = (int)(tid % NC);
+  const size_t ldx = (size_t)NC * n_nodes;
+  const float* xc = X + (size_t)n * NC + j;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int k = 0; k < K; ++k) {
+    float v = xc[(size_t)k * ldx];
+    s0 = fmaf(WL[k], v, s0);
+    s1 = fmaf(WL[K + k], v, s1);
+    s2 = fmaf(WL[2 * K + k], v, s2);
+  }
+  if (j == 0) {
+    fD[(size_t)n * NO + 0] = s0 + bL[0];
+    fD[(size_t)n * NO + 1] = s1 + bL[1];
+    fD[(size_t)n * NO + 2] = s2 + bL[2];
+  } else {
+    float* o = JD + (size_t)n * NO * NZ + (j - 1);
+    o[0] = s0; o[NZ] = s1; o[2 * NZ] = s2;
+  }
+}
+
+}  // namespace
+
+cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD) {
+  const Net& net = ctx->net;
+  const int nn = ctx->lay.n_nodes, L = net.n_layers;
+  cudaStream_t s = ctx->stream;
+  const float* W = net.W32;
+  const float* b = net.b32;
+  int h0 = net.widths[1];
+  {
+    long long tot = (long long)h0 * nn;
+    mlp_in_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, u, ctx->lay.node_inst, nn,
+                                                                W + net.w_off[0], b + net.b_off[0],
+                                                                h0, ctx->act0);
+  }
+  float* cur = ctx->act0;
+  float* nxt = ctx->act1;
+  for (int l = 1; l < L - 1; ++l) {
+    int K = net.widths[l], M = net.widths[l + 1];
+    dim3 grid((nn + BNN - 1) / BNN, (M + BM - 1) / BM);
+    mlp_hidden_kernel<<<grid, NTH, 0, s>>>(W + net.w_off[l], b + net.b_off[l], M, K, cur, nxt, nn);
+    float* t = cur; cur = nxt; nxt = t;
+  }
+  {
+    long long tot = (long long)nn * NC;
+    mlp_out_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        W + net.w_off[L - 1], b + net.b_off[L - 1], net.widths[L - 1], cur, nn, fD, JD);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rtn

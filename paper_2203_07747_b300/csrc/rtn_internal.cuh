@@ -1,0 +1,135 @@
+// rtn_internal.cuh -- context layout and kernel entry points shared by the
+// CUDA translation units of librtn.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rtn.h"
+
+namespace rtn {
+
+constexpr int NX = 13;
+constexpr int NU = 4;
+constexpr int NZ = 17;   // network input [x; u]
+constexpr int NO = 3;    // network output: world-frame acceleration residual
+constexpr int NC = 18;   // columns per node in forward mode: value + 17 tangents
+
+// Quadrotor constants in FP32 for the linearisation kernels (by value).
+struct QuadParams {
+  float mass, inv_mass, Jx, Jy, Jz, d, c_tau, u_max, g, hover;
+};
+
+// Diagonal tracking weights (Sec. V cost), kept in FP64 so that the FP64
+// sweep sees the caller's exact values.
+struct CostParams {
+  double Q[NX], R[NU], QN[NX];
+};
+
+// Node-packed ragged layout of one controller batch.
+struct Layout {
+  int B = 0, n_nodes = 0, n_states = 0, N_max = 0;
+  int* N = nullptr;          // [B]
+  float* dt = nullptr;       // [B]
+  double* dt64 = nullptr;    // [B] (plant integration)
+  int* xoff = nullptr;       // [B] first state row of instance b
+  int* uoff = nullptr;       // [B] first node row of instance b
+  int* node_inst = nullptr;  // [n_nodes] instance of every node
+  int* order = nullptr;      // [B] instances sorted by decreasing N_b
+};
+
+// Packed network for the tensor-core path -- see mlp_tc.cu.
+struct TcNet {
+  int h_pad = 0;                // hidden width padded to a multiple of 128
+  int n_mm = 0;                 // layers on the tensor cores (hidden->hidden + output)
+  __nv_bfloat16* W = nullptr;   // stacked BF16 rows, K padded to h_pad
+  float* bias = nullptr;        // [n_hidden][h_pad] then [4] output bias
+  float* W0 = nullptr;          // input layer FP32 [h_pad][17]
+  int rows_total = 0;
+  int cols = 0;                 // node columns per CTA
+  int stages = 0;               // weight pipeline depth
+  void* tmap = nullptr;         // device-side copy not needed: host CUtensorMap bytes
+  alignas(64) unsigned char tmap_bytes[128];
+};
+
+struct Net {
+  int n_layers = 0;                 // weight matrices
+  std::vector<int> widths;
+  float* W32 = nullptr;             // FP32 weights, all layers, row-major, packed
+  float* b32 = nullptr;             // FP32 biases, packed
+  std::vector<size_t> w_off, b_off; // offsets into W32 / b32
+  double* P64 = nullptr;            // FP64 copy for the plant (W then b per layer)
+  int h_max = 0;
+  TcNet tc;
+};
+
+}  // namespace rtn
+
+struct rtn_ctx {
+  int B = 0;
+  rtn::Layout lay;
+  std::vector<int> hN;
+  std::vector<double> hdt;
+  rtn::QuadParams quad{};
+  rtn_quad quad64{};
+  rtn::CostParams cost{};
+  rtn_options opt{};
+  bool has_mlp = false;
+  rtn::Net net;
+  cudaStream_t stream = nullptr;
+  // iterate (omega of Sec. II)
+  float* x = nullptr;  // [n_states][13]
+  float* u = nullptr;  // [n_nodes][4]
+  // workspace
+  float *fD = nullptr, *JD = nullptr, *A = nullptr, *Bm = nullptr, *c = nullptr;
+  void *K = nullptr, *kff = nullptr;      // Riccati gains (float or double) [n][4][13], [n][4]
+  float *act0 = nullptr, *act1 = nullptr; // FP32 network activations [h_max][18 n_nodes]
+  int* status = nullptr;                  // [B]
+  int* dev_t = nullptr;                   // closed-loop step counter
+  float* x0f = nullptr;                   // [B][13] float copy of the plant state
+  float* u0 = nullptr;                    // [B][4]
+  std::string err;
+};
+
+namespace rtn {
+
+// ---- launchers (each returns cudaGetLastError()) --------------------------
+
+// a1, FP32 SIMT path
+cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+// a1, tcgen05 path
+cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err);
+cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+void mlp_tc_release(rtn_ctx* ctx);
+
+// a2
+cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
+                     const float* JD, float* A, float* Bm, float* c);
+
+// a3 + a4.  Refs are read at rows base(b) + t + k where t is *t_dev (or 0) and
+// base(b) = b * stride when stride > 0, else the layout's own offset of
+// instance b (node-packed references).
+struct QpArgs {
+  const float *A, *Bm, *c;
+  float *x, *u;                 // linearisation points (updated when update != 0)
+  const float *xref, *uref;
+  int xref_stride, uref_stride;
+  const int* t_dev;
+  const float* x0;              // [B][13]
+  float *dx, *du;               // optional step outputs
+  float* u0;                    // optional sent command [B][4]
+  int* status;                  // [B]
+  int update;                   // apply step + (shift) to x, u
+  int shift;
+};
+cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a);
+
+// a5
+cudaError_t plant_step(rtn_ctx* ctx, int kind, const double* x, const float* u, double* xn,
+                       int nsub, float* x_f32);
+
+}  // namespace rtn
