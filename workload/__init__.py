@@ -214,3 +214,12 @@ def trajectory_refs(prob, steps):
     xr = reference_states(prob["ref"], t)
     ur = np.full((len(N), T - 1, NU), hover_thrust())
     return xr, ur
+
+
+def subset(prob, nb):
+    """The first nb instances of a problem (same seeds, same arrays)."""
+    out = dict(prob)
+    out["B"] = nb
+    out["N"], out["dt"], out["x0"] = prob["N"][:nb], prob["dt"][:nb], prob["x0"][:nb]
+    out["ref"] = {k: (v if isinstance(v, str) else v[:nb]) for k, v in prob["ref"].items()}
+    return out
