@@ -1,0 +1,338 @@
+"""Benchmark of the Real-time Neural MPC hot path on one B300.
+
+One step = one closed-loop control step of every controller instance: the
+RTI step (network value + Jacobian at every node, RK4 sensitivities, Riccati
+sweep, feedback update) followed by the plant step, replayed as a CUDA graph
+through rtn_closed_loop.  `value` is instance RTI steps per second
+(B x K / device time of K steps).  the design doc gives the workload recipe, the
+roofline accounting and the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload as W  # noqa: E402
+
+_BJ = os.path.join(ROOT, "BASELINE.json")
+METRIC = (json.load(open(_BJ))["metric"] if os.path.exists(_BJ)
+          else "SQP-RTI node-linearizations/s + RTI steps/s, BF16 vs FP32 @ <=1e-3 Jac err")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained", d["bf16_tflops"]), "measured"
+    return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+def fwd_flops_per_node(widths):
+    """Forward-mode algorithmic FLOPs per node.  Hidden->hidden and output
+    layers multiply 18 columns (value + 17 tangents); the input layer costs
+    its value dot products plus the tangent scaling (its tangent block is the
+    weight matrix itself)."""
+    f = 2 * 17 * widths[1] + 17 * widths[1]
+    for fi, fo in zip(widths[1:-1], widths[2:]):
+        f += 2 * 18 * fi * fo
+    return f
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self):
+        self.rows, self.p = [], None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+            self.p = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[0]) for r in self.rows) if v is not None]
+        mx = [v for v in (num(r[1]) for r in self.rows) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make(prob, precision, riccati_f64=False):
+    import paper_2203_07747_b300 as rtn
+    return rtn.Controller(prob["N"], prob["dt"], prob["Q"], prob["R"], QN=prob["QN"], quad=prob["quad"],
+                          layers=prob["layers"], precision=precision, riccati_f64=riccati_f64)
+
+
+def launches_per_step(ctl):
+    L = len(ctl.layers) if ctl.layers else 0
+    mlp = 0 if not L else (1 if ctl.precision != "fp32" else L)
+    return mlp + 1 + 1 + 3  # network, RK4, Riccati, plant + record + advance
+
+
+def time_closed_loop(ctl, prob, steps, warmup):
+    import torch
+    xrt, urt = W.trajectory_refs(prob, steps + warmup)
+    xrt_d = torch.as_tensor(xrt, dtype=torch.float32, device="cuda").contiguous()
+    urt_d = torch.as_tensor(urt, dtype=torch.float32, device="cuda").contiguous()
+    x0 = prob["x0"].copy()
+    ctl.reset(torch.as_tensor(x0, dtype=torch.float32, device="cuda"))
+    xp = torch.as_tensor(x0, dtype=torch.float64, device="cuda").contiguous()
+    ctl.closed_loop(warmup, xrt_d, urt_d, xp, plant="drag", record=False)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the timed steps continue on the reference window after the warm-up
+    xr2, ur2 = xrt_d[:, warmup:].contiguous(), urt_d[:, warmup:].contiguous()
+    with Clocks() as ck:
+        torch.cuda.synchronize()
+        e0.record(s)
+        traj, _ = ctl.closed_loop(steps, xr2, ur2, xp, plant="drag", record=True)
+        e1.record(s)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pos = traj[:, :, :3].double().cpu().numpy()
+    err = np.linalg.norm(pos - xrt[:, warmup + 1:warmup + steps + 1, :3].transpose(1, 0, 2), axis=2)
+    return ms / steps, ck.summary(), float(np.sqrt((err ** 2).mean()))
+
+
+def time_calls(fn, reps, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def e2e_rti(ctl, prob, steps):
+    """Through the public API with host buffers: per step copy x0, xref,
+    uref from pinned host memory, run rtn_rti_step, copy u0 back."""
+    import torch
+    xref, uref = W.node_refs(prob)
+    h_x0 = torch.as_tensor(prob["x0"], dtype=torch.float32).pin_memory()
+    h_xr = torch.as_tensor(xref, dtype=torch.float32).pin_memory()
+    h_ur = torch.as_tensor(uref, dtype=torch.float32).pin_memory()
+    h_u0 = torch.empty((ctl.B, 4), dtype=torch.float32).pin_memory()
+    d_x0, d_xr, d_ur = (torch.empty_like(h, device="cuda") for h in (h_x0, h_xr, h_ur))
+    d_u0 = torch.empty((ctl.B, 4), device="cuda")
+    d_st = torch.empty(ctl.B, dtype=torch.int32, device="cuda")
+
+    def one():
+        d_x0.copy_(h_x0, non_blocking=True)
+        d_xr.copy_(h_xr, non_blocking=True)
+        d_ur.copy_(h_ur, non_blocking=True)
+        ctl.rti_step(d_x0, d_xr, d_ur, d_u0, d_st)
+        h_u0.copy_(d_u0, non_blocking=True)
+
+    ms = time_calls(one, steps)
+    bi = sum(h.numel() * 4 for h in (h_x0, h_xr, h_ur))
+    return ms, bi, h_u0.numel() * 4
+
+
+def jac_error(ctl, prob, n_check=64):
+    """Largest relative Jacobian error per node against the FP64 oracle on a
+    seeded sample of nodes (the oracle evaluates the same weights)."""
+    import torch
+    import oracle
+    X, U = W.random_nodes(ctl.n_states, 11)
+    U = U[:ctl.n_nodes]
+    _, JD = ctl.mlp_eval(torch.as_tensor(X, dtype=torch.float32, device="cuda"),
+                         torch.as_tensor(U, dtype=torch.float32, device="cuda"))
+    JD = JD.double().cpu().numpy()
+    inst = np.repeat(np.arange(len(prob["N"])), prob["N"])
+    idx = np.random.default_rng(0).choice(ctl.n_nodes, n_check, replace=False)
+    Xf, Uf = X.astype(np.float32).astype(np.float64), U.astype(np.float32).astype(np.float64)
+    worst = 0.0
+    for n in idx:
+        _, J = oracle.mlp_fwd_jac(prob["layers"], np.concatenate([Xf[n + inst[n]], Uf[n]]))
+        worst = max(worst, np.linalg.norm(JD[n] - J) / np.linalg.norm(J))
+    return worst
+
+
+def cpu_baseline(prob, budget_s=15.0):
+    """The oracle's RTI step on a bounded sample of instances of the same
+    workload, timed on the host cores (the sample doubles until the budget
+    would be exceeded)."""
+    import oracle
+    oracle.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    nb, total, rate, done = 1, 0.0, None, 0
+    while nb <= prob["B"]:
+        sub = W.subset(prob, nb)
+        N, dt, x0 = sub["N"], sub["dt"], sub["x0"]
+        xref, uref = W.node_refs(sub)
+        x = np.concatenate([np.repeat(x0[b:b + 1], N[b] + 1, 0) for b in range(nb)])
+        u = np.full((int(N.sum()), 4), W.hover_thrust())
+        t0 = time.perf_counter()
+        oracle.rti_step(sub["quad"], sub["layers"], N, dt, sub["Q"], sub["R"], sub["QN"], x, u,
+                        xref, uref, x0)
+        el = time.perf_counter() - t0
+        total += el
+        rate, done = nb / el, nb
+        if total + 2.2 * el > budget_s:
+            break
+        nb *= 2
+    return {"value": rate, "unit": "RTI steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {prob['B']} instances, one RTI step (FP64 C, OpenMP over instances)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg3_bf16_precision")
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    hbm, bf16_burst, bf16_sus, peak_src = peaks()
+    prob = W.make_problem(args.config, seed=0, bf16=True)
+    widths = prob["widths"]
+    B, nn = prob["B"], int(prob["N"].sum())
+    cfg = {"workload": f"{args.config}: {B} instances, N={int(prob['N'].max())}, "
+                       f"MLP {'-'.join(map(str, widths))} tanh (BF16-representable weights), "
+                       "figure-8 references, step = RTI step + drag plant step",
+           "instances": B, "nodes": nn,
+           "l2": "inputs larger than L2 (A, B, c of all nodes exceed 126 MB)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(prob)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "RTI steps/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded workload generator)", "config": cfg, "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "RTI steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_2203_07747_b300 as rtn
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    rtn.load(build_if_missing=True)
+
+    precs = ["bf16x2", "fp32"] if args.precision == "auto" else [args.precision]
+    ctl, prec = None, None
+    for p in precs:
+        try:
+            ctl, prec = make(prob, p), p
+            break
+        except rtn.RtnError as e:
+            if "UNSUPPORTED" not in str(e):
+                raise
+    cfg["precision"] = prec
+    ms_step, clocks, rmse = time_closed_loop(ctl, prob, args.steps, args.warmup)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = B * world / (ms_step * 1e-3)
+
+    # node linearisations (a1 + a2) and the network kernel alone (a1)
+    x, u = ctl.get_iterate()
+    out = ctl.linearize(x, u)
+    ms_lin = time_calls(lambda: ctl.linearize(x, u, out), max(5, args.steps))
+    ms_mlp = time_calls(lambda: ctl.mlp_eval(x, u, out[0], out[1]), max(5, args.steps))
+    flops = fwd_flops_per_node(widths) * nn
+    if prec == "fp32":
+        roof = {"bound": "alu", "peak": 148 * 128 * 2 * 2.032e9 / 1e12,
+                "peak_kind": "nominal FP32 FFMA: 148 SM x 128 lanes x 2 x 2.032 GHz"}
+    else:
+        roof = {"bound": "tensor", "peak": bf16_burst, "peak_kind": f"bf16 burst ({peak_src})"}
+    roof.update({"achieved": flops / (ms_mlp * 1e-3) / 1e12, "unit": "TFLOP/s",
+                 "algorithmic_flops_per_launch": flops, "ms_per_launch": ms_mlp,
+                 "kernel": "network value + forward-mode Jacobian (a1)", "traffic": None})
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    ms_e2e, bi, bo = e2e_rti(ctl, prob, max(5, args.steps))
+    jerr = jac_error(ctl, prob)
+    line = {"metric": METRIC, "value": value, "unit": "RTI steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "fp32", "bf16": "bf16", "bf16x2": "bf16 (hi+lo split operands), fp32 accum"}[prec],
+            "data": "synthetic (seeded workload generator)", "config": cfg,
+            "node_linearizations_per_s": nn / (ms_lin * 1e-3),
+            "jac_rel_err_max": jerr, "tracking_rmse_m": rmse, "roofline": roof,
+            "e2e": {"value": B / (ms_e2e * 1e-3), "unit": "RTI steps/s", "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo, "path": "rtn_rti_step with pinned host buffers"},
+            "gpu_launches": launches_per_step(ctl) * args.steps, "clocks": clocks}
+    ctl.close()
+    if prec != "fp32" and not args.no_fp32:
+        c32 = make(prob, "fp32")
+        ms32, _, _ = time_closed_loop(c32, prob, max(3, args.steps // 4), 2)
+        x32, u32 = c32.get_iterate()
+        o32 = c32.linearize(x32, u32)
+        ml32 = time_calls(lambda: c32.linearize(x32, u32, o32), 5)
+        line["fp32_same_workload"] = {"value": B / (ms32 * 1e-3), "unit": "RTI steps/s",
+                                      "node_linearizations_per_s": nn / (ml32 * 1e-3),
+                                      "jac_rel_err_max": jac_error(c32, prob)}
+        c32.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(prob)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()
