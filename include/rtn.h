@@ -172,6 +172,37 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
                            const float* uref_traj, int T, double* x_plant, float* traj_out,
                            float* u_out);
 
+/* Size of the fixed activation array used by rtn_mlp_eval_f32_noalloc. */
+#define RTN_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* FP32 network value + forward-mode Jacobian without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (and so cannot create a context with rtn_create),
+ * e.g. a host that owns every device buffer itself, or a real-time loop in
+ * which allocating is forbidden because it can stall the device for an
+ * unbounded time.  It computes the same result as rtn_mlp_eval with
+ * precision RTN_FP32, keeping the activations in a fixed array of
+ * RTN_NOALLOC_SCRATCH_BYTES (16 MiB) that the library places on every GPU
+ * that loads it, for the life of the process.
+ *   n_layers, widths : host, as in rtn_mlp (widths[0] = 17, last = 3)
+ *   W, b             : dev float, all layers packed back to back, W[l]
+ *                      row-major [widths[l+1]][widths[l]], b[l] [widths[l+1]]
+ *   x, u             : dev float, one row per node: x [n_nodes][13],
+ *                      u [n_nodes][4]
+ *   fD, JD           : dev float outputs [n_nodes][3], [n_nodes][3][17]
+ *   cuda_stream      : cudaStream_t (NULL = legacy default stream)
+ *   err, err_len     : optional host buffer for a message on failure
+ * Requires 2 * max hidden width * 18 * n_nodes * 4 bytes <= 16 MiB, else
+ * RTN_E_INVAL with the needed size in err.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls whose kernels overlap on the GPU race on it.
+ * Asynchronous on cuda_stream. */
+rtn_status rtn_mlp_eval_f32_noalloc(int n_layers, const int* widths, const float* W,
+                                    const float* b, int n_nodes, const float* x, const float* u,
+                                    float* fD, float* JD, void* cuda_stream, char* err,
+                                    size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

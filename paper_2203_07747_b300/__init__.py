@@ -22,7 +22,8 @@ STATUS = {0: "RTN_OK", 1: "RTN_E_INVAL", 2: "RTN_E_CUDA", 3: "RTN_E_NONFINITE",
 # every symbol include/rtn.h declares
 EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_reset",
            "rtn_set_iterate", "rtn_get_iterate", "rtn_mlp_eval", "rtn_linearize",
-           "rtn_qp_solve", "rtn_rti_step", "rtn_plant_step", "rtn_closed_loop"]
+           "rtn_qp_solve", "rtn_rti_step", "rtn_plant_step", "rtn_closed_loop",
+           "rtn_mlp_eval_f32_noalloc"]
 
 _lib = None
 
@@ -79,6 +80,8 @@ def load(build_if_missing=False):
     L.rtn_rti_step.argtypes = [vp] * 6
     L.rtn_plant_step.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     L.rtn_closed_loop.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp, vp, vp]
+    L.rtn_mlp_eval_f32_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int)] + [vp] * 2 + [C.c_int] + \
+        [vp] * 5 + [C.c_char_p, C.c_size_t]
     for name in EXPORTS:
         if name not in ("rtn_destroy", "rtn_last_error"):
             getattr(L, name).restype = C.c_int

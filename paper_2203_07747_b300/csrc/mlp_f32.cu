@@ -172,3 +172,23 @@ cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float*
 }
 
 }  // namespace rtn
+
+namespace rtn {
+
+// Thin launchers of the hidden-layer and output-layer kernels above for
+// callers that manage their own activation buffers.
+cudaError_t mlp_f32_hidden_launch(const float* W, const float* bias, int M, int K, const float* X,
+                                  float* Y, int n_nodes, cudaStream_t s) {
+  dim3 grid((n_nodes + BNN - 1) / BNN, (M + BM - 1) / BM);
+  mlp_hidden_kernel<<<grid, NTH, 0, s>>>(W, bias, M, K, X, Y, n_nodes);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_f32_out_launch(const float* WL, const float* bL, int K, const float* X,
+                               int n_nodes, float* fD, float* JD, cudaStream_t s) {
+  long long tot = (long long)n_nodes * NC;
+  mlp_out_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(WL, bL, K, X, n_nodes, fD, JD);
+  return cudaGetLastError();
+}
+
+}  // namespace rtn

@@ -101,6 +101,10 @@ namespace rtn {
 
 // a1, FP32 SIMT path
 cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+cudaError_t mlp_f32_hidden_launch(const float* W, const float* bias, int M, int K, const float* X,
+                                  float* Y, int n_nodes, cudaStream_t s);
+cudaError_t mlp_f32_out_launch(const float* WL, const float* bL, int K, const float* X,
+                               int n_nodes, float* fD, float* JD, cudaStream_t s);
 // a1, tcgen05 path
 cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err);
 cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
