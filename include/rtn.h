@@ -172,6 +172,12 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
                            const float* uref_traj, int T, double* x_plant, float* traj_out,
                            float* u_out);
 
+/* Synchronous: the first device-side failure recorded since the last call
+ * (RTN_OK if none), then clears it.  Device-side failures are bounded waits of
+ * the tensor-core pipeline that gave up (RTN_E_TIMEOUT); the affected outputs
+ * are then undefined. */
+rtn_status rtn_device_error(rtn_ctx* ctx, int* code);
+
 /* Size of the fixed activation array used by rtn_mlp_eval_f32_noalloc. */
 #define RTN_NOALLOC_SCRATCH_BYTES (16u << 20)
 

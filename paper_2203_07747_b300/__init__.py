@@ -23,7 +23,7 @@ STATUS = {0: "RTN_OK", 1: "RTN_E_INVAL", 2: "RTN_E_CUDA", 3: "RTN_E_NONFINITE",
 EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_reset",
            "rtn_set_iterate", "rtn_get_iterate", "rtn_mlp_eval", "rtn_linearize",
            "rtn_qp_solve", "rtn_rti_step", "rtn_plant_step", "rtn_closed_loop",
-           "rtn_mlp_eval_f32_noalloc"]
+           "rtn_mlp_eval_f32_noalloc", "rtn_device_error"]
 
 _lib = None
 
@@ -80,6 +80,7 @@ def load(build_if_missing=False):
     L.rtn_rti_step.argtypes = [vp] * 6
     L.rtn_plant_step.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     L.rtn_closed_loop.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp, vp, vp]
+    L.rtn_device_error.argtypes = [vp, C.POINTER(C.c_int)]
     L.rtn_mlp_eval_f32_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int)] + [vp] * 2 + [C.c_int] + \
         [vp] * 5 + [C.c_char_p, C.c_size_t]
     for name in EXPORTS:
@@ -177,6 +178,12 @@ class Controller:
     def _empty(self, *shape, dtype=None):
         import torch
         return torch.empty(shape, dtype=dtype or torch.float32, device=self.device)
+
+    def device_error(self):
+        """Synchronise and return (and clear) the device-side status code."""
+        code = C.c_int(0)
+        self._check(load().rtn_device_error(self._h, C.byref(code)), "rtn_device_error")
+        return code.value
 
     # -- iterate ----------------------------------------------------------
     def reset(self, x0):

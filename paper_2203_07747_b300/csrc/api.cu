@@ -363,6 +363,14 @@ rtn_status rtn_plant_step(rtn_ctx* ctx, int kind, const double* x, const float* 
   return RTN_OK;
 }
 
+rtn_status rtn_device_error(rtn_ctx* ctx, int* code) {
+  if (!ctx || !code) return RTN_E_INVAL;
+  if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+  else CK(cudaDeviceSynchronize());
+  *code = mlp_tc_take_error(ctx);
+  return RTN_OK;
+}
+
 rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float* xref_traj,
                            const float* uref_traj, int T, double* x_plant, float* traj_out,
                            float* u_out) {

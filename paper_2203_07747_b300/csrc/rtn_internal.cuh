@@ -45,15 +45,17 @@ struct Layout {
 // Packed network for the tensor-core path -- see mlp_tc.cu.
 struct TcNet {
   int h_pad = 0;                // hidden width padded to a multiple of 128
-  int n_mm = 0;                 // layers on the tensor cores (hidden->hidden + output)
-  __nv_bfloat16* W = nullptr;   // stacked BF16 rows, K padded to h_pad
-  float* bias = nullptr;        // [n_hidden][h_pad] then [4] output bias
+  int n_mm = 0;                 // hidden -> hidden layers on the tensor cores
+  __nv_bfloat16* W = nullptr;   // stacked BF16 rows [n_mm*h_pad + 128][h_pad]
+  float* bias = nullptr;        // [n_mm*h_pad + 128]
   float* W0 = nullptr;          // input layer FP32 [h_pad][17]
+  float* b0 = nullptr;          // [h_pad]
+  int* err = nullptr;           // device status flag (RTN_E_TIMEOUT)
   int rows_total = 0;
-  int cols = 0;                 // node columns per CTA
-  int stages = 0;               // weight pipeline depth
-  void* tmap = nullptr;         // device-side copy not needed: host CUtensorMap bytes
-  alignas(64) unsigned char tmap_bytes[128];
+  int cols = 0, npc = 0, stages = 0, tmem_cols = 0;
+  size_t smem = 0;
+  const void* fn = nullptr;     // kernel variant
+  alignas(64) unsigned char tmap_bytes[128];  // CUtensorMap of W
 };
 
 struct Net {
@@ -109,6 +111,7 @@ cudaError_t mlp_f32_out_launch(const float* WL, const float* bL, int K, const fl
 cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err);
 cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
 void mlp_tc_release(rtn_ctx* ctx);
+int mlp_tc_take_error(rtn_ctx* ctx);
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,

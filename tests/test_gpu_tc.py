@@ -1,0 +1,91 @@
+"""GPU parity of the tcgen05 network kernel against the FP64 oracle.
+
+The weights are BF16-representable (rounded on the input side) so the oracle
+and the kernel evaluate the same network; the error measures the kernel's
+arithmetic.  Gate: the split-operand BF16 path (RTN_BF16X2) reaches a
+per-node relative Jacobian error <= 1e-3.  The single-pass BF16 path
+(activations and tangents rounded to BF16 at every layer) is checked against
+a looser bound of 2e-2 and its error is reported."""
+import numpy as np
+import pytest
+
+import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+QUAD = W.QUAD
+
+
+@pytest.fixture(scope="module")
+def rtn():
+    import paper_2203_07747_b300 as rtn
+    rtn.load(build_if_missing=True)
+    return rtn
+
+
+def _rel_rows(a, b, floor=1e-30):
+    a = a.reshape(a.shape[0], -1); b = b.reshape(b.shape[0], -1)
+    return (np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), floor))
+
+
+def _case(rtn, orc, widths, N, precision, seed=0, bias=True):
+    layers = W.xavier_mlp(widths, seed, bf16=True)
+    if bias:
+        layers = [(Wl, W.round_bf16(np.random.default_rng(10 + i).normal(0, 0.05, bl.shape)))
+                  for i, (Wl, bl) in enumerate(layers)]
+    N = np.asarray(N, np.int32)
+    dt = np.full(len(N), 0.05)
+    ctl = rtn.Controller(N, dt, W.Q_DIAG, W.R_DIAG, quad=QUAD, layers=layers, precision=precision)
+    X, U = W.random_nodes(ctl.n_states, seed + 1)
+    X = X.astype(np.float32).astype(np.float64)
+    U = U[:ctl.n_nodes].astype(np.float32).astype(np.float64)
+    fD, JD = ctl.mlp_eval(torch.as_tensor(X, dtype=torch.float32, device="cuda"),
+                          torch.as_tensor(U, dtype=torch.float32, device="cuda"))
+    assert ctl.device_error() == 0
+    fr, Jr, *_ = orc.linearize(QUAD, layers, N, dt, X, U)
+    ej = _rel_rows(JD.double().cpu().numpy(), Jr)
+    ef = np.abs(fD.double().cpu().numpy() - fr).max() / np.abs(fr).max()
+    return ej, ef
+
+
+@pytest.mark.parametrize("widths,N", [
+    ([17, 128, 128, 3], [3, 5]),                 # one CTA, partial
+    ([17, 128, 3], [1]),                          # no hidden->hidden layer
+    ([17, 256, 256, 256, 256, 3], [17, 50, 10, 33]),  # ragged, several CTAs
+    ([17, 512, 512, 512, 512, 512, 3], [20] * 9),     # cfg3 shape, tail CTA
+    ([17, 300, 200, 3], [7, 9]),                  # widths not multiples of 128
+])
+def test_tc_bf16x2_jacobian_within_1e3(rtn, orc, widths, N):
+    ej, ef = _case(rtn, orc, widths, N, "bf16x2")
+    assert ej.max() < 1e-3, ej.max()
+    assert ef < 1e-3, ef
+
+
+@pytest.mark.parametrize("widths,N", [([17, 128, 128, 3], [3, 5]),
+                                      ([17, 512, 512, 512, 3], [20, 20])])
+def test_tc_bf16_single_pass(rtn, orc, widths, N):
+    ej, ef = _case(rtn, orc, widths, N, "bf16")
+    assert ej.max() < 2e-2, ej.max()
+
+
+def test_tc_rti_step_matches_fp32_path(rtn, orc):
+    # the whole RTI step with the tensor-core network against the oracle
+    prob = W.make_problem("cfg2_fp32_batch", seed=2, B=5, bf16=True)
+    N, dt = prob["N"], prob["dt"].astype(np.float32).astype(np.float64)
+    X, U = W.random_nodes(int(N.sum()) + len(N), 3)
+    X = X.astype(np.float32).astype(np.float64)
+    U = U[:int(N.sum())].astype(np.float32).astype(np.float64)
+    xref, uref = W.node_refs(prob)
+    xref = xref.astype(np.float32).astype(np.float64)
+    uref = uref.astype(np.float32).astype(np.float64)
+    x0 = X[np.concatenate([[0], np.cumsum(N + 1)])[:-1]] + 0.02
+    x0 = x0.astype(np.float32).astype(np.float64)
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float32, device="cuda")
+    ctl = rtn.Controller(N, dt, prob["Q"], prob["R"], quad=QUAD, layers=prob["layers"],
+                         precision="bf16x2", riccati_f64=True)
+    ctl.set_iterate(dev(X), dev(U))
+    u0, st = ctl.rti_step(dev(x0), dev(xref), dev(uref))
+    u0r, _, _, _ = orc.rti_step(QUAD, prob["layers"], N, dt, prob["Q"], prob["R"], prob["QN"],
+                                X, U, xref, uref, x0)
+    assert (st.cpu().numpy() == 0).all() and ctl.device_error() == 0
+    assert np.abs(u0.cpu().numpy() - u0r).max() / np.abs(u0r).max() < 1e-3
