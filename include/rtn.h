@@ -172,6 +172,31 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
                            const float* uref_traj, int T, double* x_plant, float* traj_out,
                            float* u_out);
 
+/* Tile shapes of the tensor-core network kernel (the autotuner's search
+ * space).  rtn_tc_variants: number of compiled shapes.  rtn_tc_variant_info:
+ * nodes per CTA, split flag and pipeline depth of shape idx, *fits = 1 if it
+ * can run this context's network and precision.  rtn_tc_select: use shape idx
+ * (RTN_E_UNSUPPORTED if it does not fit).  rtn_autotune: time every fitting
+ * shape on the context's current iterate (synchronous; 1 warm-up + 3 timed
+ * calls each), keep the fastest, return its index and time per call [ms].
+ * Only for contexts created with RTN_BF16 / RTN_BF16X2. */
+rtn_status rtn_tc_variants(rtn_ctx* ctx, int* count);
+rtn_status rtn_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages,
+                               int* fits);
+rtn_status rtn_tc_select(rtn_ctx* ctx, int idx);
+rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms);
+
+/* Phase tracing of the tensor-core kernel (profiling aid).  enable != 0
+ * makes every later network evaluation record %globaltimer stamps [ns] of
+ * CTA 0 into a device buffer of RTN_TC_TRACE_LEN entries: entry
+ * ((i * (L + 1) + l) * 8 + f) for the i-th tile of CTA 0, layer l < L
+ * (L = tensor-core layers) with f = 0 MMA start, 1 MMA issued, 2 epilogue
+ * start, 3 epilogue done, and l = L for the input layer (f = 0 start,
+ * 1 done).  rtn_tc_trace_read copies n entries to host memory (synchronous). */
+#define RTN_TC_TRACE_LEN 65536
+rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable);
+rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n);
+
 /* Synchronous: the first device-side failure recorded since the last call
  * (RTN_OK if none), then clears it.  Device-side failures are bounded waits of
  * the tensor-core pipeline that gave up (RTN_E_TIMEOUT); the affected outputs

@@ -23,7 +23,9 @@ STATUS = {0: "RTN_OK", 1: "RTN_E_INVAL", 2: "RTN_E_CUDA", 3: "RTN_E_NONFINITE",
 EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_reset",
            "rtn_set_iterate", "rtn_get_iterate", "rtn_mlp_eval", "rtn_linearize",
            "rtn_qp_solve", "rtn_rti_step", "rtn_plant_step", "rtn_closed_loop",
-           "rtn_mlp_eval_f32_noalloc", "rtn_device_error"]
+           "rtn_mlp_eval_f32_noalloc", "rtn_device_error", "rtn_tc_variants",
+           "rtn_tc_variant_info", "rtn_tc_select", "rtn_autotune", "rtn_tc_trace",
+           "rtn_tc_trace_read"]
 
 _lib = None
 
@@ -81,6 +83,13 @@ def load(build_if_missing=False):
     L.rtn_plant_step.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     L.rtn_closed_loop.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp, vp, vp]
     L.rtn_device_error.argtypes = [vp, C.POINTER(C.c_int)]
+    ip = C.POINTER(C.c_int)
+    L.rtn_tc_variants.argtypes = [vp, ip]
+    L.rtn_tc_variant_info.argtypes = [vp, C.c_int, ip, ip, ip, ip]
+    L.rtn_tc_select.argtypes = [vp, C.c_int]
+    L.rtn_autotune.argtypes = [vp, ip, C.POINTER(C.c_float)]
+    L.rtn_tc_trace.argtypes = [vp, C.c_int]
+    L.rtn_tc_trace_read.argtypes = [vp, C.POINTER(C.c_ulonglong), C.c_int]
     L.rtn_mlp_eval_f32_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int)] + [vp] * 2 + [C.c_int] + \
         [vp] * 5 + [C.c_char_p, C.c_size_t]
     for name in EXPORTS:
@@ -184,6 +193,37 @@ class Controller:
         code = C.c_int(0)
         self._check(load().rtn_device_error(self._h, C.byref(code)), "rtn_device_error")
         return code.value
+
+    def tc_variants(self):
+        """[(index, nodes per CTA, split, stages)] of the tile shapes that fit."""
+        L = load()
+        n = C.c_int()
+        self._check(L.rtn_tc_variants(self._h, C.byref(n)), "rtn_tc_variants")
+        out = []
+        for i in range(n.value):
+            npc, sp, stg, fits = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+            self._check(L.rtn_tc_variant_info(self._h, i, C.byref(npc), C.byref(sp), C.byref(stg),
+                                              C.byref(fits)), "rtn_tc_variant_info")
+            if fits.value:
+                out.append((i, npc.value, bool(sp.value), stg.value))
+        return out
+
+    def tc_select(self, idx):
+        self._check(load().rtn_tc_select(self._h, int(idx)), "rtn_tc_select")
+
+    def autotune(self):
+        """Time every fitting tile shape, keep the fastest: (index, ms)."""
+        i, ms = C.c_int(), C.c_float()
+        self._check(load().rtn_autotune(self._h, C.byref(i), C.byref(ms)), "rtn_autotune")
+        return i.value, ms.value
+
+    def tc_trace(self, enable=True):
+        self._check(load().rtn_tc_trace(self._h, int(bool(enable))), "rtn_tc_trace")
+
+    def tc_trace_read(self, n=65536):
+        buf = (C.c_ulonglong * n)()
+        self._check(load().rtn_tc_trace_read(self._h, buf, n), "rtn_tc_trace_read")
+        return np.frombuffer(buf, dtype=np.uint64).copy()
 
     # -- iterate ----------------------------------------------------------
     def reset(self, x0):

@@ -363,6 +363,92 @@ rtn_status rtn_plant_step(rtn_ctx* ctx, int kind, const double* x, const float* 
   return RTN_OK;
 }
 
+rtn_status rtn_tc_variants(rtn_ctx* ctx, int* count) {
+  if (!ctx || !count) return RTN_E_INVAL;
+  *count = mlp_tc_variant_count();
+  return RTN_OK;
+}
+
+rtn_status rtn_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages,
+                               int* fits) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
+    return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
+  int r = mlp_tc_variant_info(ctx, idx, npc, split, stages);
+  if (r < 0) return fail(ctx, RTN_E_INVAL, "variant index out of range");
+  if (fits) *fits = (r == 0);
+  return RTN_OK;
+}
+
+rtn_status rtn_tc_select(rtn_ctx* ctx, int idx) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
+    return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
+  int r = mlp_tc_variant_info(ctx, idx, nullptr, nullptr, nullptr);
+  if (r < 0) return fail(ctx, RTN_E_INVAL, "variant index out of range");
+  if (r > 0) return fail(ctx, RTN_E_UNSUPPORTED, "variant does not fit this network");
+  CK(mlp_tc_select(ctx, idx));
+  return RTN_OK;
+}
+
+rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
+    return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = -1;
+  float bms = 1e30f;
+  const int n = mlp_tc_variant_count();
+  rtn_status st = RTN_OK;
+  for (int i = 0; i < n && st == RTN_OK; ++i) {
+    if (mlp_tc_variant_info(ctx, i, nullptr, nullptr, nullptr) != 0) continue;
+    cudaError_t e = mlp_tc_select(ctx, i);
+    if (e == cudaSuccess) e = mlp_tc_forward(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = mlp_tc_forward(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { ctx->err = std::string("autotune: ") + cudaGetErrorString(e); st = RTN_E_CUDA; break; }
+    if (mlp_tc_take_error(ctx)) { ctx->err = "autotune: device timeout"; st = RTN_E_TIMEOUT; break; }
+    ms /= 3.0f;
+    if (ms < bms) { bms = ms; best = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RTN_OK) return st;
+  if (best < 0) return fail(ctx, RTN_E_UNSUPPORTED, "no variant fits");
+  CK(mlp_tc_select(ctx, best));
+  if (best_idx) *best_idx = best;
+  if (best_ms) *best_ms = bms;
+  return RTN_OK;
+}
+
+rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable) {
+  if (!ctx) return RTN_E_INVAL;
+  TcNet& tc = ctx->net.tc;
+  if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
+    return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
+  if (enable && !tc.trace) {
+    CK(cudaMalloc(&tc.trace, RTN_TC_TRACE_LEN * sizeof(unsigned long long)));
+    CK(cudaMemset(tc.trace, 0, RTN_TC_TRACE_LEN * sizeof(unsigned long long)));
+  } else if (!enable && tc.trace) {
+    CK(cudaFree(tc.trace));
+    tc.trace = nullptr;
+  }
+  return RTN_OK;
+}
+
+rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n) {
+  if (!ctx || !host || n < 0 || n > RTN_TC_TRACE_LEN) return fail(ctx, RTN_E_INVAL, "rtn_tc_trace_read: bad argument");
+  if (!ctx->net.tc.trace) return fail(ctx, RTN_E_INVAL, "tracing is not enabled");
+  CK(cudaMemcpy(host, ctx->net.tc.trace, (size_t)n * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  return RTN_OK;
+}
+
 rtn_status rtn_device_error(rtn_ctx* ctx, int* code) {
   if (!ctx || !code) return RTN_E_INVAL;
   if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));

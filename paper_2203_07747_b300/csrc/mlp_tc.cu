@@ -65,6 +65,7 @@ struct TcArgs {
   float* fD;
   float* JD;
   int* err;
+  unsigned long long* trace;  // optional phase timestamps of CTA 0 (see rtn_tc_trace)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -108,6 +109,20 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     }
   }
   return true;
+}
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// trace slot of (tile index within this CTA, layer, field): CTA 0 only
+__device__ __forceinline__ void trace(const TcArgs& a, int it, int l, int n_layers, int f) {
+  if (a.trace && blockIdx.x == 0) {
+    const int idx = ((it * (n_layers + 1) + l) * 8 + f);
+    if (idx < (1 << 16)) a.trace[idx] = gtime();
+  }
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
@@ -169,24 +184,93 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// store element (column c, row k of the K-major X) given the per-thread row
-// pieces: base offset of k's 64-wide block + (k % 8) * 2 and chunk (k % 64) / 8
+// X (the B operand) is N-major without swizzle: core matrices of 8 k-rows x
+// 8 node columns (128 B, rows 16 B apart); node-column groups are 128 B apart
+// (stride byte offset) and k-groups C*16 B apart (leading byte offset).  A
+// thread that owns neuron k writes 8 consecutive columns as one 16-byte store.
+__device__ __forceinline__ uint64_t xdesc(uint32_t saddr, uint32_t lbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_col, float hi_col) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo_col, hi_col);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// residual of a packed pair: v - bf16(v), packed again
+__device__ __forceinline__ uint32_t pack_res(float v0, float v1, uint32_t hi) {
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+  return pack_bf16(v0 - h0, v1 - h1);
+}
+
+// 8 consecutive columns (one 16-byte chunk) of row k
 template <bool SPLIT>
-__device__ __forceinline__ void x_store(uint8_t* Xhi, uint8_t* Xlo, uint32_t krow, uint32_t kchunk,
-                                        int c, float v) {
-  uint32_t off = krow + (uint32_t)c * 128u + (((kchunk ^ (uint32_t)(c & 7))) << 4);
+__device__ __forceinline__ void x_store8(uint8_t* Xhi, uint8_t* Xlo, uint32_t off, const float* v) {
+  uint4 h;
+  h.x = pack_bf16(v[0], v[1]);
+  h.y = pack_bf16(v[2], v[3]);
+  h.z = pack_bf16(v[4], v[5]);
+  h.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4*>(Xhi + off) = h;
+  if (SPLIT) {
+    uint4 l;
+    l.x = pack_res(v[0], v[1], h.x);
+    l.y = pack_res(v[2], v[3], h.y);
+    l.z = pack_res(v[4], v[5], h.z);
+    l.w = pack_res(v[6], v[7], h.w);
+    *reinterpret_cast<uint4*>(Xlo + off) = l;
+  }
+}
+
+template <bool SPLIT>
+__device__ __forceinline__ void x_store1(uint8_t* Xhi, uint8_t* Xlo, uint32_t off, float v) {
   __nv_bfloat16 hi = __float2bfloat16_rn(v);
   *reinterpret_cast<__nv_bfloat16*>(Xhi + off) = hi;
   if (SPLIT) *reinterpret_cast<__nv_bfloat16*>(Xlo + off) = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// byte offset of (row k, column c) in X
+template <int C>
+__device__ __forceinline__ uint32_t xoff(int k, int c) {
+  return (uint32_t)(k >> 3) * (C * 16u) + (uint32_t)(c >> 3) * 128u + (uint32_t)(k & 7) * 16u +
+         (uint32_t)(c & 7) * 2u;
+}
+
+// one node's outputs for row k: value a, tangents d * t[0..16]
+template <int NPC, int C, bool SPLIT>
+__device__ __forceinline__ void write_node(uint8_t* Xhi, uint8_t* Xlo, int k, int n, float a, float d,
+                                           const float* t16, float t17) {
+  float v[8];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = d * t16[8 * h + j];
+    x_store8<SPLIT>(Xhi, Xlo, xoff<C>(k, 16 * n + 8 * h), v);
+  }
+  x_store1<SPLIT>(Xhi, Xlo, xoff<C>(k, 16 * NPC + n), a);
+  x_store1<SPLIT>(Xhi, Xlo, xoff<C>(k, 17 * NPC + n), d * t17);
+}
+
+// z (network input) of node `node` (0 beyond the batch): entry j < 17
+__device__ __forceinline__ float load_z(const TcArgs& a, int node, int j) {
+  if (node >= a.n_nodes) return 0.0f;
+  return j < NX ? a.x[(size_t)(node + a.node_inst[node]) * NX + j] : a.u[(size_t)node * NU + (j - NX)];
+}
+
+// Persistent: CTA b handles node tiles b, b + gridDim.x, ...  The producer and
+// MMA issuer run through the same sequence of (tile, layer, M tile, K block)
+// without stopping, so the weights of the next tile stream in while the
+// epilogue of the current one runs.
 template <int NPC, bool SPLIT, int STAGES>
 __global__ void __launch_bounds__(THREADS, 1)
     mlp_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   constexpr int C = Cols<NPC>::C, TAIL = Cols<NPC>::TAIL, HALF = (NPC + 1) / 2;
+  constexpr int NZV = NPC * NZ;
   extern __shared__ uint8_t smem_raw[];
   const int HP = a.HP, nkb = HP / 64, n_mt = HP / 128;
   const int n_layers = a.n_hidden_mm + 1;
+  const int n_tiles = (a.n_nodes + NPC - 1) / NPC;
   const uint32_t sraw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
   uint8_t* sm = smem_raw + pad;
@@ -204,9 +288,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t x_ready = bar_s + 8u * (2 * STAGES + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail_area + 8 * (2 * STAGES + 2));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* zbuf = reinterpret_cast<float*>(tail_area + 8 * (2 * STAGES + 2) + 16);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int node0 = blockIdx.x * NPC;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -231,53 +315,59 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- TMA producer: weight tiles of every layer, in order
+    // ---------------- TMA producer
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int l = 0; l < n_layers && ok; ++l) {
-        const int mts = (l < a.n_hidden_mm) ? n_mt : 1;
-        for (int m = 0; m < mts && ok; ++m)
-          for (int kb = 0; kb < nkb && ok; ++kb) {
-            if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
-            mbar_expect_tx(full_bar(s), WT_BYTES);
-            tma_load_2d(w_s + s * WT_BYTES, &tmap, kb * 64, l * HP + m * 128, full_bar(s));
-            if (++s == STAGES) { s = 0; ph ^= 1u; }
-          }
-      }
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
+        for (int l = 0; l < n_layers && ok; ++l) {
+          const int mts = (l < a.n_hidden_mm) ? n_mt : 1;
+          for (int m = 0; m < mts && ok; ++m)
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+              if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
+              mbar_expect_tx(full_bar(s), WT_BYTES);
+              tma_load_2d(w_s + s * WT_BYTES, &tmap, kb * 64, l * HP + m * 128, full_bar(s));
+              if (++s == STAGES) { s = 0; ph ^= 1u; }
+            }
+        }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(128, C);
+      constexpr uint32_t idesc = idesc_bf16(128, C) | (1u << 16);  // B is N-major
+      const uint32_t lbo = C * 16u;
       int s = 0;
-      uint32_t ph = 0;
+      uint32_t ph = 0, xr = 0;
       bool ok = true;
-      for (int l = 0; l < n_layers && ok; ++l) {
-        if (!(ok = mbar_wait(x_ready, (uint32_t)(l & 1), abort_flag, a.err))) break;
-        tc_fence_after();
-        const int mts = (l < a.n_hidden_mm) ? n_mt : 1;
-        for (int m = 0; m < mts && ok; ++m) {
-          const uint32_t d = tmem + (uint32_t)(m * C);
-          for (int kb = 0; kb < nkb && ok; ++kb) {
-            if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, a.err))) break;
-            tc_fence_after();
-            const uint32_t as = w_s + s * WT_BYTES;
-            const uint32_t bo = (uint32_t)kb * C * 128u;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it)
+        for (int l = 0; l < n_layers && ok; ++l, ++xr) {
+          if (!(ok = mbar_wait(x_ready, xr & 1u, abort_flag, a.err))) break;
+          trace(a, it, l, n_layers, 0);
+          tc_fence_after();
+          const int mts = (l < a.n_hidden_mm) ? n_mt : 1;
+          for (int m = 0; m < mts && ok; ++m) {
+            const uint32_t d = tmem + (uint32_t)(m * C);
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+              if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, a.err))) break;
+              tc_fence_after();
+              const uint32_t as = w_s + s * WT_BYTES;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t ad = sdesc(as + ks * 32);
-              mma_bf16(d, ad, sdesc(xhi_s + bo + ks * 32), idesc, (kb | ks) != 0);
-              if (SPLIT) mma_bf16(d, ad, sdesc(xlo_s + bo + ks * 32), idesc, 1u);
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t ad = sdesc(as + ks * 32);
+                const uint32_t bo = (uint32_t)(kb * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
+                mma_bf16(d, ad, xdesc(xhi_s + bo, lbo), idesc, (kb | ks) != 0);
+                if (SPLIT) mma_bf16(d, ad, xdesc(xlo_s + bo, lbo), idesc, 1u);
+              }
+              mma_commit(empty_bar(s));
+              if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
-            mma_commit(empty_bar(s));
-            if (++s == STAGES) { s = 0; ph ^= 1u; }
           }
+          if (ok) mma_commit(acc_full);
+          trace(a, it, l, n_layers, 1);
         }
-        if (ok) mma_commit(acc_full);
-      }
     }
   } else {
     // ---------------- epilogue warps
@@ -285,102 +375,103 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const int half = e >> 2;
     const int et = threadIdx.x - 64;  // 0..255
-
-    // input layer (FP32): X_1 rows k = neuron i, columns of every node
-    for (int i = et; i < HP; i += 256) {
-      float w[NZ];
+    // zero both X buffers once: pad columns are never written again
+    for (uint32_t o = (uint32_t)et * 16u; o < (SPLIT ? 2u : 1u) * xbytes; o += 256u * 16u)
+      *reinterpret_cast<uint4*>(sm + o) = make_uint4(0u, 0u, 0u, 0u);
+    float zpref = (et < NZV) ? load_z(a, blockIdx.x * NPC + et / NZ, et % NZ) : 0.0f;
+    uint32_t accp = 0;
+    bool ok = true;
+    const bool tr = (e == 0 && lane == 0);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+      const int node0 = tile * NPC;
+      if (tr) trace(a, it, n_layers, n_layers, 0);
+      if (et < NZV) zbuf[et] = zpref;
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      // input layer (FP32): rows k = neuron i
+      for (int i = et; i < HP; i += 256) {
+        float w[NZ];
 #pragma unroll
-      for (int j = 0; j < NZ; ++j) w[j] = a.W0[(size_t)i * NZ + j];
-      const float bi = a.b0[i];
-      const uint32_t krow = (uint32_t)(i >> 6) * C * 128u + (uint32_t)(i & 7) * 2u;
-      const uint32_t kchunk = (uint32_t)((i & 63) >> 3);
-      for (int n = 0; n < NPC; ++n) {
-        const int node = node0 + n;
-        if (node < a.n_nodes) {
-          const float* xr = a.x + (size_t)(node + a.node_inst[node]) * NX;
-          const float* ur = a.u + (size_t)node * NU;
-          float s = bi;
-#pragma unroll
-          for (int j = 0; j < NX; ++j) s = fmaf(w[j], xr[j], s);
-#pragma unroll
-          for (int j = 0; j < NU; ++j) s = fmaf(w[NX + j], ur[j], s);
-          const float av = tanhf(s), d = 1.0f - av * av;
-          x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 16 * NPC + n, av);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 16 * n + j, d * w[j]);
-          x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 17 * NPC + n, d * w[16]);
-        } else {
-          x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 16 * NPC + n, 0.0f);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 16 * n + j, 0.0f);
-          x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 17 * NPC + n, 0.0f);
-        }
-      }
-      for (int c = 18 * NPC; c < C; ++c) x_store<SPLIT>(Xhi, Xlo, krow, kchunk, c, 0.0f);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncwarp();
-    if (lane == 0) mbar_arrive(x_ready);
-
-    for (int l = 0; l < n_layers; ++l) {
-      int ok = 0;
-      if (lane == 0) ok = mbar_wait(acc_full, (uint32_t)(l & 1), abort_flag, a.err);
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      tc_fence_after();
-      const bool last = (l == a.n_hidden_mm);
-      if (!last) {
-        for (int m = 0; m < n_mt; ++m) {
-          const int i = 128 * m + 32 * q + lane;
-          const float bi = a.bias[(size_t)l * HP + i];
-          const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * C);
-          const uint32_t krow = (uint32_t)(i >> 6) * C * 128u + (uint32_t)(i & 7) * 2u;
-          const uint32_t kchunk = (uint32_t)((i & 63) >> 3);
-          float tl[TAIL];
-#pragma unroll
-          for (int c = 0; c < TAIL / 16; ++c) tmem_ld16(trow + 16 * NPC + 16 * c, tl + 16 * c);
-          tmem_wait_ld();
-#pragma unroll
-          for (int n = 0; n < NPC; ++n) {
-            if ((n < HALF) != (half == 0)) continue;
-            float t[16];
-            tmem_ld16(trow + 16 * n, t);
-            tmem_wait_ld();
-            const float av = tanhf(tl[n] + bi), d = 1.0f - av * av;
-            x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 16 * NPC + n, av);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 16 * n + j, d * t[j]);
-            x_store<SPLIT>(Xhi, Xlo, krow, kchunk, 17 * NPC + n, d * tl[NPC + n]);
-          }
-        }
-        tc_fence_before();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(x_ready);
-      } else if (q == 0) {
-        // output layer: TMEM lanes 0..2 hold the three outputs
-        const uint32_t trow = tmem;
-        float tl[TAIL];
-#pragma unroll
-        for (int c = 0; c < TAIL / 16; ++c) tmem_ld16(trow + 16 * NPC + 16 * c, tl + 16 * c);
-        tmem_wait_ld();
-        const float bo = lane < NO ? a.bias[(size_t)a.n_hidden_mm * HP + lane] : 0.0f;
+        for (int j = 0; j < NZ; ++j) w[j] = a.W0[(size_t)i * NZ + j];
+        const float bi = a.b0[i];
 #pragma unroll
         for (int n = 0; n < NPC; ++n) {
-          if ((n < HALF) != (half == 0)) continue;
-          float t[16];
-          tmem_ld16(trow + 16 * n, t);
-          tmem_wait_ld();
-          const int node = node0 + n;
-          if (lane < NO && node < a.n_nodes) {
-            a.fD[(size_t)node * NO + lane] = tl[n] + bo;
-            float* J = a.JD + (size_t)node * NO * NZ + lane * NZ;
+          float s = bi;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) J[j] = t[j];
-            J[16] = tl[NPC + n];
-          }
+          for (int j = 0; j < NZ; ++j) s = fmaf(w[j], zbuf[n * NZ + j], s);
+          const bool real = node0 + n < a.n_nodes;
+          const float av = real ? tanhf(s) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
+          write_node<NPC, C, SPLIT>(Xhi, Xlo, i, n, av, d, w, w[16]);
         }
-        tc_fence_before();
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(x_ready);
+      if (tr) trace(a, it, n_layers, n_layers, 1);
+
+      for (int l = 0; l < n_layers; ++l, ++accp) {
+        const bool last = (l == a.n_hidden_mm);
+        if (last && et < NZV) {
+          // prefetch the next tile's inputs while the output layer runs
+          const int nt = tile + gridDim.x;
+          zpref = nt < n_tiles ? load_z(a, nt * NPC + et / NZ, et % NZ) : 0.0f;
+        }
+        int w_ok = 0;
+        if (lane == 0) w_ok = mbar_wait(acc_full, accp & 1u, abort_flag, a.err);
+        w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+        if (!w_ok) { ok = false; break; }
+        if (tr) trace(a, it, l, n_layers, 2);
+        tc_fence_after();
+        if (!last) {
+          for (int m = 0; m < n_mt; ++m) {
+            const int i = 128 * m + 32 * q + lane;
+            const float bi = a.bias[(size_t)l * HP + i];
+            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * C);
+            float tl[TAIL];
+#pragma unroll
+            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16(trow + 16 * NPC + 16 * c, tl + 16 * c);
+            tmem_wait_ld();
+#pragma unroll
+            for (int n = 0; n < NPC; ++n) {
+              if ((n < HALF) != (half == 0)) continue;
+              float t[16];
+              tmem_ld16(trow + 16 * n, t);
+              tmem_wait_ld();
+              const float av = tanhf(tl[n] + bi), d = 1.0f - av * av;
+              write_node<NPC, C, SPLIT>(Xhi, Xlo, i, n, av, d, t, tl[NPC + n]);
+            }
+          }
+          tc_fence_before();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(x_ready);
+          if (tr) trace(a, it, l, n_layers, 3);
+        } else {
+          if (q == 0) {
+            // output layer: TMEM lanes 0..2 hold the three outputs
+            float tl[TAIL];
+#pragma unroll
+            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16(tmem + 16 * NPC + 16 * c, tl + 16 * c);
+            tmem_wait_ld();
+            const float bo = lane < NO ? a.bias[(size_t)a.n_hidden_mm * HP + lane] : 0.0f;
+#pragma unroll
+            for (int n = 0; n < NPC; ++n) {
+              if ((n < HALF) != (half == 0)) continue;
+              float t[16];
+              tmem_ld16(tmem + 16 * n, t);
+              tmem_wait_ld();
+              const int node = node0 + n;
+              if (lane < NO && node < a.n_nodes) {
+                a.fD[(size_t)node * NO + lane] = tl[n] + bo;
+                float* J = a.JD + (size_t)node * NO * NZ + lane * NZ;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) J[j] = t[j];
+                J[16] = tl[NPC + n];
+              }
+            }
+          }
+          tc_fence_before();
+        }
       }
     }
   }
@@ -403,7 +494,8 @@ struct Variant {
   const void* fn;
   int cols() const { return 16 * npc + ((2 * npc + 15) / 16) * 16; }
   size_t smem(int HP) const {
-    return 1024 + (split ? 2 : 1) * (size_t)cols() * HP * 2 + (size_t)stages * WT_BYTES + 8 * (2 * stages + 2) + 16;
+    return 1024 + (split ? 2 : 1) * (size_t)cols() * HP * 2 + (size_t)stages * WT_BYTES +
+           8 * (2 * stages + 2) + 16 + (size_t)npc * NZ * 4;
   }
 };
 
@@ -412,10 +504,31 @@ Variant variant() {
   return Variant{NPC, SPLIT, STAGES, (const void*)&mlp_tc_kernel<NPC, SPLIT, STAGES>};
 }
 
-Variant pick(int HP, bool split) {
-  if (HP <= 128) return split ? variant<14, true, 5>() : variant<14, false, 6>();
-  if (HP <= 256) return split ? variant<8, true, 4>() : variant<14, false, 5>();
-  return split ? variant<4, true, 3>() : variant<7, false, 5>();
+// every compiled tile shape; the autotuner times those that fit
+const std::vector<Variant>& all_variants() {
+  static const std::vector<Variant> v = {
+      variant<14, false, 6>(), variant<14, false, 5>(), variant<8, false, 8>(),
+      variant<7, false, 5>(),  variant<6, false, 6>(),  variant<4, false, 8>(),
+      variant<14, true, 5>(),  variant<8, true, 4>(),   variant<5, true, 6>(),
+      variant<4, true, 3>(),   variant<3, true, 6>()};
+  return v;
+}
+
+bool fits(const Variant& v, int HP) {
+  return v.smem(HP) <= 232448 && (HP / 128) * v.cols() <= 512;
+}
+
+// default before autotuning: the widest tile that still leaves >= 3 stages
+int default_variant(int HP, bool split) {
+  const auto& vs = all_variants();
+  int best = -1;
+  for (int i = 0; i < (int)vs.size(); ++i) {
+    if (vs[i].split != split || !fits(vs[i], HP) || vs[i].stages < 3) continue;
+    if (best < 0 || vs[i].cols() > vs[best].cols() ||
+        (vs[i].cols() == vs[best].cols() && vs[i].stages > vs[best].stages))
+      best = i;
+  }
+  return best;
 }
 
 uint16_t f2bf(float f) {
@@ -424,6 +537,21 @@ uint16_t f2bf(float f) {
   if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
   u += 0x7fffu + ((u >> 16) & 1u);
   return (uint16_t)(u >> 16);
+}
+
+cudaError_t select_variant(rtn_ctx* ctx, int idx) {
+  TcNet& tc = ctx->net.tc;
+  const Variant& v = all_variants()[idx];
+  tc.variant = idx;
+  tc.cols = v.cols();
+  tc.npc = v.npc;
+  tc.stages = v.stages;
+  tc.smem = v.smem(tc.h_pad);
+  tc.fn = v.fn;
+  int ncol = 32;
+  while (ncol < (tc.h_pad / 128) * v.cols()) ncol *= 2;
+  tc.tmem_cols = ncol;
+  return cudaFuncSetAttribute(tc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
 }
 
 }  // namespace
@@ -444,18 +572,15 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
   tc.n_mm = nh;
   tc.rows_total = nh * HP + 128;
   const bool split = ctx->opt.precision == RTN_BF16X2;
-  Variant v = pick(HP, split);
-  tc.cols = v.cols();
-  tc.npc = v.npc;
-  tc.stages = v.stages;
-  tc.smem = v.smem(HP);
-  tc.fn = v.fn;
-  int ncol = 32;
-  while (ncol < (HP / 128) * v.cols()) ncol *= 2;
-  tc.tmem_cols = ncol;
-  if (tc.smem > 232448 || ncol > 512) {
-    err = "tensor-core tile configuration does not fit";
+  const int vi = default_variant(HP, split);
+  if (vi < 0) {
+    err = "no tensor-core tile configuration fits";
     return cudaSuccess;
+  }
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&tc.n_sm, cudaDevAttrMultiProcessorCount, dev);
   }
 
   // host copies of the network (FP32 as given at create)
@@ -524,8 +649,7 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
     return cudaSuccess;
   }
-  e = cudaFuncSetAttribute(tc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
-  return e;
+  return select_variant(ctx, vi);
 }
 
 cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD) {
@@ -544,15 +668,32 @@ cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* 
   a.fD = fD;
   a.JD = JD;
   a.err = tc.err;
+  a.trace = tc.trace;
   const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(tc.tmap_bytes);
   void* args[] = {(void*)map, (void*)&a};
-  dim3 grid((a.n_nodes + tc.npc - 1) / tc.npc);
+  const int n_tiles = (a.n_nodes + tc.npc - 1) / tc.npc;
+  dim3 grid(std::min(n_tiles, std::max(1, tc.n_sm)));
   return cudaLaunchKernel(tc.fn, grid, dim3(THREADS), args, tc.smem, ctx->stream);
 }
 
+int mlp_tc_variant_count() { return (int)all_variants().size(); }
+
+// describe variant idx: returns 0 if it fits this network, writes its shape
+int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages) {
+  const auto& vs = all_variants();
+  if (idx < 0 || idx >= (int)vs.size()) return -1;
+  if (npc) *npc = vs[idx].npc;
+  if (split) *split = vs[idx].split;
+  if (stages) *stages = vs[idx].stages;
+  const bool want = ctx->opt.precision == RTN_BF16X2;
+  return (vs[idx].split == want && fits(vs[idx], ctx->net.tc.h_pad)) ? 0 : 1;
+}
+
+cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx) { return select_variant(ctx, idx); }
+
 void mlp_tc_release(rtn_ctx* ctx) {
   TcNet& tc = ctx->net.tc;
-  void* ptrs[] = {tc.W, tc.bias, tc.W0, tc.b0, tc.err};
+  void* ptrs[] = {tc.W, tc.bias, tc.W0, tc.b0, tc.err, tc.trace};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   tc = TcNet{};

@@ -51,8 +51,9 @@ struct TcNet {
   float* W0 = nullptr;          // input layer FP32 [h_pad][17]
   float* b0 = nullptr;          // [h_pad]
   int* err = nullptr;           // device status flag (RTN_E_TIMEOUT)
+  unsigned long long* trace = nullptr;  // optional phase timestamps (rtn_tc_trace)
   int rows_total = 0;
-  int cols = 0, npc = 0, stages = 0, tmem_cols = 0;
+  int cols = 0, npc = 0, stages = 0, tmem_cols = 0, variant = -1, n_sm = 148;
   size_t smem = 0;
   const void* fn = nullptr;     // kernel variant
   alignas(64) unsigned char tmap_bytes[128];  // CUtensorMap of W
@@ -112,6 +113,9 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err);
 cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
 void mlp_tc_release(rtn_ctx* ctx);
 int mlp_tc_take_error(rtn_ctx* ctx);
+int mlp_tc_variant_count();
+int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages);
+cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx);
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
