@@ -172,6 +172,32 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
                            const float* uref_traj, int T, double* x_plant, float* traj_out,
                            float* u_out);
 
+/* (a6) Ground-truth residual targets of the drag simulator for training:
+ * Y[s] = -R(q) diag(0.3, 0.3, 0.1) R(q)' v - 0.01 |v| v  (world-frame
+ * acceleration), X dev [n][13], Y dev [n][3], FP32. */
+rtn_status rtn_drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y);
+
+/* (a6) Mean-squared-error loss 1/(3n) sum |f_D(x, u) - y|^2 of the context's
+ * network on n samples (X dev [n][13], U dev [n][4], Y dev [n][3]) and its
+ * gradient, FP32: grad dev [n_weights + n_biases] packed as all W[l]
+ * (row-major, layer order) then all b[l]; loss dev float [1]. */
+rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,
+                        float* grad, float* loss);
+
+/* (a6) Train the context's network in place (Sec. VI: MSE, Adam with
+ * b1 = 0.9, b2 = 0.999, eps = 1e-8, bias correction): `epochs` passes over
+ * the n samples in consecutive minibatches of `batch` (the remainder of each
+ * pass is skipped), learning rate lr.  FP32 master weights, FP32 SIMT
+ * forward/backward, one fused Adam launch per parameter block.  Adam state
+ * persists across calls.  loss_out (host, may be NULL) receives the loss of
+ * every step [epochs * (n / batch)].  Afterwards the tensor-core and plant
+ * copies of the network are refreshed.  Synchronous. */
+rtn_status rtn_train(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,
+                     int epochs, int batch, float lr, float* loss_out);
+
+/* Current FP32 parameters to host memory, packed as in rtn_mse_grad. */
+rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
+
 /* Tile shapes of the tensor-core network kernel (the autotuner's search
  * space).  rtn_tc_variants: number of compiled shapes.  rtn_tc_variant_info:
  * nodes per CTA, split flag and pipeline depth of shape idx, *fits = 1 if it

@@ -25,7 +25,8 @@ EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_rese
            "rtn_qp_solve", "rtn_rti_step", "rtn_plant_step", "rtn_closed_loop",
            "rtn_mlp_eval_f32_noalloc", "rtn_device_error", "rtn_tc_variants",
            "rtn_tc_variant_info", "rtn_tc_select", "rtn_autotune", "rtn_tc_trace",
-           "rtn_tc_trace_read"]
+           "rtn_tc_trace_read", "rtn_drag_targets", "rtn_mse_grad", "rtn_train",
+           "rtn_get_params"]
 
 _lib = None
 
@@ -89,6 +90,10 @@ def load(build_if_missing=False):
     L.rtn_tc_select.argtypes = [vp, C.c_int]
     L.rtn_autotune.argtypes = [vp, ip, C.POINTER(C.c_float)]
     L.rtn_tc_trace.argtypes = [vp, C.c_int]
+    L.rtn_drag_targets.argtypes = [vp, vp, C.c_int, vp]
+    L.rtn_mse_grad.argtypes = [vp, vp, vp, vp, C.c_int, vp, vp]
+    L.rtn_train.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.POINTER(C.c_float)]
+    L.rtn_get_params.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.rtn_tc_trace_read.argtypes = [vp, C.POINTER(C.c_ulonglong), C.c_int]
     L.rtn_mlp_eval_f32_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int)] + [vp] * 2 + [C.c_int] + \
         [vp] * 5 + [C.c_char_p, C.c_size_t]
@@ -224,6 +229,60 @@ class Controller:
         buf = (C.c_ulonglong * n)()
         self._check(load().rtn_tc_trace_read(self._h, buf, n), "rtn_tc_trace_read")
         return np.frombuffer(buf, dtype=np.uint64).copy()
+
+    # -- learned part (a6) --------------------------------------------------
+    def n_params(self):
+        nw = sum(W.shape[0] * W.shape[1] for W, _ in self.layers)
+        nb = sum(b.shape[0] for _, b in self.layers)
+        return nw, nb
+
+    def drag_targets(self, X):
+        import torch
+        Y = self._empty(X.shape[0], NO)
+        self._check(load().rtn_drag_targets(self._h, _ptr(X, torch.float32, (X.shape[0], NX), "X"),
+                                            int(X.shape[0]), _ptr(Y, torch.float32, None, "Y")),
+                    "rtn_drag_targets")
+        return Y
+
+    def mse_grad(self, X, U, Y):
+        import torch
+        n = int(X.shape[0])
+        nw, nb = self.n_params()
+        g = self._empty(nw + nb)
+        loss = self._empty(1)
+        self._check(load().rtn_mse_grad(self._h, _ptr(X, torch.float32, (n, NX), "X"),
+                                        _ptr(U, torch.float32, (n, NU), "U"),
+                                        _ptr(Y, torch.float32, (n, NO), "Y"), n,
+                                        _ptr(g, torch.float32, None, "grad"),
+                                        _ptr(loss, torch.float32, None, "loss")), "rtn_mse_grad")
+        return float(loss.item()), g
+
+    def train(self, X, U, Y, epochs, batch, lr):
+        import torch
+        n = int(X.shape[0])
+        steps = epochs * (n // batch)
+        losses = (C.c_float * max(steps, 1))()
+        self._check(load().rtn_train(self._h, _ptr(X, torch.float32, (n, NX), "X"),
+                                     _ptr(U, torch.float32, (n, NU), "U"),
+                                     _ptr(Y, torch.float32, (n, NO), "Y"), n, int(epochs), int(batch),
+                                     float(lr), losses), "rtn_train")
+        return np.frombuffer(losses, dtype=np.float32)[:steps].copy()
+
+    def get_params(self):
+        """[(W, b), ...] float64 arrays of the current network."""
+        nw, nb = self.n_params()
+        W = (C.c_float * nw)()
+        b = (C.c_float * nb)()
+        self._check(load().rtn_get_params(self._h, W, b), "rtn_get_params")
+        W = np.frombuffer(W, dtype=np.float32).astype(np.float64)
+        b = np.frombuffer(b, dtype=np.float32).astype(np.float64)
+        out, ow, ob = [], 0, 0
+        for Wl, bl in self.layers:
+            fo, fi = Wl.shape
+            out.append((W[ow:ow + fo * fi].reshape(fo, fi), b[ob:ob + fo]))
+            ow += fo * fi
+            ob += fo
+        return out
 
     # -- iterate ----------------------------------------------------------
     def reset(self, x0):

@@ -271,6 +271,7 @@ void rtn_destroy(rtn_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   mlp_tc_release(ctx);
+  train_release(ctx);
   delete ctx;
 }
 

@@ -70,6 +70,17 @@ struct Net {
   TcNet tc;
 };
 
+// Training buffers (allocated on the first rtn_train / rtn_mse_grad call).
+struct TrainState {
+  int bs = 0;                          // minibatch size the buffers fit
+  std::vector<float*> act;             // A_0 .. A_L, [h_l][bs]
+  float *g0 = nullptr, *g1 = nullptr;  // backward signals [h_max][bs]
+  float* grad = nullptr;               // dW (packed like W32) then db (like b32)
+  float *m = nullptr, *v = nullptr;    // Adam moments, same packing
+  size_t nw = 0, nb = 0, b_base = 0;
+  long long t = 0;                     // Adam step counter
+};
+
 }  // namespace rtn
 
 struct rtn_ctx {
@@ -95,6 +106,7 @@ struct rtn_ctx {
   int* dev_t = nullptr;                   // closed-loop step counter
   float* x0f = nullptr;                   // [B][13] float copy of the plant state
   float* u0 = nullptr;                    // [B][4]
+  rtn::TrainState train;
   std::string err;
 };
 
@@ -138,6 +150,14 @@ struct QpArgs {
   int shift;
 };
 cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a);
+
+// a6
+cudaError_t drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y);
+cudaError_t train_step(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
+                       int start, float lr, float* loss);
+cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
+                       int start, float* loss);
+void train_release(rtn_ctx* ctx);
 
 // a5
 cudaError_t plant_step(rtn_ctx* ctx, int kind, const double* x, const float* u, double* xn,
