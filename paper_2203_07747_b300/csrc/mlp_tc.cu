@@ -134,11 +134,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row atoms 1024 B
-// apart (stride byte offset), fixed version bits 46..48 = 0b001
+// shared-memory matrix descriptor of a weight slab: K-major, 32B swizzle
+// (rows of 16 K values = 32 B, exactly one MMA's K), 8-row groups 256 B apart
+// (stride byte offset), fixed version bits 46..48 = 0b001
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
 }
 
 // instruction descriptor, kind::f16: D f32, A = B = bf16, both K-major
@@ -328,7 +329,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int kb = 0; kb < nkb && ok; ++kb) {
               if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
               mbar_expect_tx(full_bar(s), WT_BYTES);
-              tma_load_2d(w_s + s * WT_BYTES, &tmap, kb * 64, l * HP + m * 128, full_bar(s));
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks)
+                tma_load_2d(w_s + s * WT_BYTES + ks * 4096u, &tmap, kb * 64 + ks * 16, l * HP + m * 128,
+                            full_bar(s));
               if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
         }
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint32_t as = w_s + s * WT_BYTES;
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t ad = sdesc(as + ks * 32);
+                const uint64_t ad = sdesc(as + ks * 4096u);
                 const uint32_t bo = (uint32_t)(kb * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
                 mma_bf16(d, ad, xdesc(xhi_s + bo, lbo), idesc, (kb | ks) != 0);
                 if (SPLIT) mma_bf16(d, ad, xdesc(xlo_s + bo, lbo), idesc, 1u);
@@ -639,11 +643,11 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)tc.rows_total};
   cuuint64_t strides[1] = {(cuuint64_t)HP * 2};
-  cuuint32_t box[2] = {64, 128};
+  cuuint32_t box[2] = {16, 128};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(reinterpret_cast<CUtensorMap*>(tc.tmap_bytes), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                       tc.W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
