@@ -205,52 +205,80 @@ __device__ __forceinline__ uint32_t pack_res(float v0, float v1, uint32_t hi) {
   return pack_bf16(v0 - h0, v1 - h1);
 }
 
-// 8 consecutive columns (one 16-byte chunk) of row k
-template <bool SPLIT>
-__device__ __forceinline__ void x_store8(uint8_t* Xhi, uint8_t* Xlo, uint32_t off, const float* v) {
+// Operand modes: 0 = BF16 single pass; 1 = split, X_hi and X_lo in two
+// buffers, two MMAs per K step; 2 = split, X_lo stored as C extra columns
+// next to X_hi so that one MMA of N = 2C computes both products (the
+// epilogue adds the two halves of the accumulator).
+template <int MODE>
+__device__ __forceinline__ void x_store8(uint8_t* X, uint32_t hi_off, uint32_t lo_off, const float* v) {
   uint4 h;
   h.x = pack_bf16(v[0], v[1]);
   h.y = pack_bf16(v[2], v[3]);
   h.z = pack_bf16(v[4], v[5]);
   h.w = pack_bf16(v[6], v[7]);
-  *reinterpret_cast<uint4*>(Xhi + off) = h;
-  if (SPLIT) {
+  *reinterpret_cast<uint4*>(X + hi_off) = h;
+  if (MODE != 0) {
     uint4 l;
     l.x = pack_res(v[0], v[1], h.x);
     l.y = pack_res(v[2], v[3], h.y);
     l.z = pack_res(v[4], v[5], h.z);
     l.w = pack_res(v[6], v[7], h.w);
-    *reinterpret_cast<uint4*>(Xlo + off) = l;
+    *reinterpret_cast<uint4*>(X + lo_off) = l;
   }
 }
 
-template <bool SPLIT>
-__device__ __forceinline__ void x_store1(uint8_t* Xhi, uint8_t* Xlo, uint32_t off, float v) {
+template <int MODE>
+__device__ __forceinline__ void x_store1(uint8_t* X, uint32_t hi_off, uint32_t lo_off, float v) {
   __nv_bfloat16 hi = __float2bfloat16_rn(v);
-  *reinterpret_cast<__nv_bfloat16*>(Xhi + off) = hi;
-  if (SPLIT) *reinterpret_cast<__nv_bfloat16*>(Xlo + off) = __float2bfloat16_rn(v - __bfloat162float(hi));
+  *reinterpret_cast<__nv_bfloat16*>(X + hi_off) = hi;
+  if (MODE != 0) *reinterpret_cast<__nv_bfloat16*>(X + lo_off) = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// byte offset of (row k, column c) in X
-template <int C>
+// byte offset of (row k, column c) in an N-major X of CX columns
+template <int CX>
 __device__ __forceinline__ uint32_t xoff(int k, int c) {
-  return (uint32_t)(k >> 3) * (C * 16u) + (uint32_t)(c >> 3) * 128u + (uint32_t)(k & 7) * 16u +
+  return (uint32_t)(k >> 3) * (CX * 16u) + (uint32_t)(c >> 3) * 128u + (uint32_t)(k & 7) * 16u +
          (uint32_t)(c & 7) * 2u;
 }
 
+// X geometry per mode: columns of one buffer and where a column's lo part goes
+template <int C, int MODE>
+struct XGeo {
+  static constexpr int CX = MODE == 2 ? 2 * C : C;  // columns of the buffer
+  static __device__ __forceinline__ uint32_t hi(int k, int c) { return xoff<CX>(k, c); }
+  static __device__ __forceinline__ uint32_t lo(int k, int c, uint32_t xbytes) {
+    return MODE == 2 ? xoff<CX>(k, C + c) : xbytes + xoff<CX>(k, c);
+  }
+};
+
 // one node's outputs for row k: value a, tangents d * t[0..16]
-template <int NPC, int C, bool SPLIT>
-__device__ __forceinline__ void write_node(uint8_t* Xhi, uint8_t* Xlo, int k, int n, float a, float d,
+template <int NPC, int C, int MODE>
+__device__ __forceinline__ void write_node(uint8_t* X, uint32_t xbytes, int k, int n, float a, float d,
                                            const float* t16, float t17) {
+  using G = XGeo<C, MODE>;
   float v[8];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = d * t16[8 * h + j];
-    x_store8<SPLIT>(Xhi, Xlo, xoff<C>(k, 16 * n + 8 * h), v);
+    const int c = 16 * n + 8 * h;
+    x_store8<MODE>(X, G::hi(k, c), G::lo(k, c, xbytes), v);
   }
-  x_store1<SPLIT>(Xhi, Xlo, xoff<C>(k, 16 * NPC + n), a);
-  x_store1<SPLIT>(Xhi, Xlo, xoff<C>(k, 17 * NPC + n), d * t17);
+  x_store1<MODE>(X, G::hi(k, 16 * NPC + n), G::lo(k, 16 * NPC + n, xbytes), a);
+  x_store1<MODE>(X, G::hi(k, 17 * NPC + n), G::lo(k, 17 * NPC + n, xbytes), d * t17);
+}
+
+// accumulator columns of one node group: hi part + (mode 2) lo part C later
+template <int C, int MODE>
+__device__ __forceinline__ void tmem_ld16_sum(uint32_t taddr, float* v) {
+  tmem_ld16(taddr, v);
+  if (MODE == 2) {
+    float w[16];
+    tmem_ld16(taddr + C, w);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] += w[i];
+  }
 }
 
 // z (network input) of node `node` (0 beyond the batch): entry j < 17
@@ -263,10 +291,14 @@ __device__ __forceinline__ float load_z(const TcArgs& a, int node, int j) {
 // MMA issuer run through the same sequence of (tile, layer, M tile, K block)
 // without stopping, so the weights of the next tile stream in while the
 // epilogue of the current one runs.
-template <int NPC, bool SPLIT, int STAGES>
+template <int NPC, int MODE, int STAGES>
 __global__ void __launch_bounds__(THREADS, 1)
     mlp_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   constexpr int C = Cols<NPC>::C, TAIL = Cols<NPC>::TAIL, HALF = (NPC + 1) / 2;
+  constexpr bool SPLIT = MODE != 0;
+  constexpr int CX = XGeo<C, MODE>::CX;   // columns of one X buffer
+  constexpr int NMMA = MODE == 2 ? 2 * C : C;  // N of every MMA = TMEM columns per M tile
+  static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
   constexpr int NZV = NPC * NZ;
   extern __shared__ uint8_t smem_raw[];
   const int HP = a.HP, nkb = HP / 64, n_mt = HP / 128;
@@ -276,12 +308,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
   uint8_t* sm = smem_raw + pad;
   const uint32_t sbase = sraw + pad;
-  const uint32_t xbytes = (uint32_t)C * HP * 2u;
-  uint8_t* Xhi = sm;
-  uint8_t* Xlo = sm + xbytes;
+  const uint32_t xbytes = (uint32_t)CX * HP * 2u;  // one X buffer
+  const uint32_t xtotal = (MODE == 1 ? 2u : 1u) * xbytes;
+  uint8_t* X = sm;
   const uint32_t xhi_s = sbase, xlo_s = sbase + xbytes;
-  const uint32_t w_s = sbase + (SPLIT ? 2u : 1u) * xbytes;
-  uint8_t* tail_area = sm + (SPLIT ? 2u : 1u) * xbytes + STAGES * WT_BYTES;
+  const uint32_t w_s = sbase + xtotal;
+  uint8_t* tail_area = sm + xtotal + STAGES * WT_BYTES;
   const uint32_t bar_s = smem_u32(tail_area);  // full[S], empty[S], acc_full, x_ready
   auto full_bar = [&](int s) { return bar_s + 8u * s; };
   auto empty_bar = [&](int s) { return bar_s + 8u * (STAGES + s); };
@@ -340,8 +372,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(128, C) | (1u << 16);  // B is N-major
-      const uint32_t lbo = C * 16u;
+      constexpr uint32_t idesc = idesc_bf16(128, NMMA) | (1u << 16);  // B is N-major
+      const uint32_t lbo = CX * 16u;
       int s = 0;
       uint32_t ph = 0, xr = 0;
       bool ok = true;
@@ -353,7 +385,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           tc_fence_after();
           const int mts = (l < a.n_hidden_mm) ? n_mt : 1;
           for (int m = 0; m < mts && ok; ++m) {
-            const uint32_t d = tmem + (uint32_t)(m * C);
+            const uint32_t d = tmem + (uint32_t)(m * NMMA);
             for (int kb = 0; kb < nkb && ok; ++kb) {
               if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, a.err))) break;
               tc_fence_after();
@@ -363,7 +395,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint64_t ad = sdesc(as + ks * 4096u);
                 const uint32_t bo = (uint32_t)(kb * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
                 mma_bf16(d, ad, xdesc(xhi_s + bo, lbo), idesc, (kb | ks) != 0);
-                if (SPLIT) mma_bf16(d, ad, xdesc(xlo_s + bo, lbo), idesc, 1u);
+                if (MODE == 1) mma_bf16(d, ad, xdesc(xlo_s + bo, lbo), idesc, 1u);
               }
               mma_commit(empty_bar(s));
               if (++s == STAGES) { s = 0; ph ^= 1u; }
@@ -380,7 +412,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int half = e >> 2;
     const int et = threadIdx.x - 64;  // 0..255
     // zero both X buffers once: pad columns are never written again
-    for (uint32_t o = (uint32_t)et * 16u; o < (SPLIT ? 2u : 1u) * xbytes; o += 256u * 16u)
+    for (uint32_t o = (uint32_t)et * 16u; o < xtotal; o += 256u * 16u)
       *reinterpret_cast<uint4*>(sm + o) = make_uint4(0u, 0u, 0u, 0u);
     float zpref = (et < NZV) ? load_z(a, blockIdx.x * NPC + et / NZ, et % NZ) : 0.0f;
     uint32_t accp = 0;
@@ -405,7 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int j = 0; j < NZ; ++j) s = fmaf(w[j], zbuf[n * NZ + j], s);
           const bool real = node0 + n < a.n_nodes;
           const float av = real ? tanhf(s) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
-          write_node<NPC, C, SPLIT>(Xhi, Xlo, i, n, av, d, w, w[16]);
+          write_node<NPC, C, MODE>(X, xbytes, i, n, av, d, w, w[16]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -430,19 +462,19 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int m = 0; m < n_mt; ++m) {
             const int i = 128 * m + 32 * q + lane;
             const float bi = a.bias[(size_t)l * HP + i];
-            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * C);
+            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * NMMA);
             float tl[TAIL];
 #pragma unroll
-            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16(trow + 16 * NPC + 16 * c, tl + 16 * c);
+            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16_sum<C, MODE>(trow + 16 * NPC + 16 * c, tl + 16 * c);
             tmem_wait_ld();
 #pragma unroll
             for (int n = 0; n < NPC; ++n) {
               if ((n < HALF) != (half == 0)) continue;
               float t[16];
-              tmem_ld16(trow + 16 * n, t);
+              tmem_ld16_sum<C, MODE>(trow + 16 * n, t);
               tmem_wait_ld();
               const float av = tanhf(tl[n] + bi), d = 1.0f - av * av;
-              write_node<NPC, C, SPLIT>(Xhi, Xlo, i, n, av, d, t, tl[NPC + n]);
+              write_node<NPC, C, MODE>(X, xbytes, i, n, av, d, t, tl[NPC + n]);
             }
           }
           tc_fence_before();
@@ -455,14 +487,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             // output layer: TMEM lanes 0..2 hold the three outputs
             float tl[TAIL];
 #pragma unroll
-            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16(tmem + 16 * NPC + 16 * c, tl + 16 * c);
+            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16_sum<C, MODE>(tmem + 16 * NPC + 16 * c, tl + 16 * c);
             tmem_wait_ld();
             const float bo = lane < NO ? a.bias[(size_t)a.n_hidden_mm * HP + lane] : 0.0f;
 #pragma unroll
             for (int n = 0; n < NPC; ++n) {
               if ((n < HALF) != (half == 0)) continue;
               float t[16];
-              tmem_ld16(tmem + 16 * n, t);
+              tmem_ld16_sum<C, MODE>(tmem + 16 * n, t);
               tmem_wait_ld();
               const int node = node0 + n;
               if (lane < NO && node < a.n_nodes) {
@@ -493,33 +525,35 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 struct Variant {
   int npc;
-  bool split;
+  int mode;  // 0 single, 1 split (two MMAs), 2 split (hi|lo along N)
   int stages;
   const void* fn;
+  bool split() const { return mode != 0; }
   int cols() const { return 16 * npc + ((2 * npc + 15) / 16) * 16; }
+  int tmem_per_mtile() const { return mode == 2 ? 2 * cols() : cols(); }
   size_t smem(int HP) const {
-    return 1024 + (split ? 2 : 1) * (size_t)cols() * HP * 2 + (size_t)stages * WT_BYTES +
+    return 1024 + (mode != 0 ? 2 : 1) * (size_t)cols() * HP * 2 + (size_t)stages * WT_BYTES +
            8 * (2 * stages + 2) + 16 + (size_t)npc * NZ * 4;
   }
 };
 
-template <int NPC, bool SPLIT, int STAGES>
+template <int NPC, int MODE, int STAGES>
 Variant variant() {
-  return Variant{NPC, SPLIT, STAGES, (const void*)&mlp_tc_kernel<NPC, SPLIT, STAGES>};
+  return Variant{NPC, MODE, STAGES, (const void*)&mlp_tc_kernel<NPC, MODE, STAGES>};
 }
 
 // every compiled tile shape; the autotuner times those that fit
 const std::vector<Variant>& all_variants() {
   static const std::vector<Variant> v = {
-      variant<14, false, 6>(), variant<14, false, 5>(), variant<8, false, 8>(),
-      variant<7, false, 5>(),  variant<6, false, 6>(),  variant<4, false, 8>(),
-      variant<14, true, 5>(),  variant<8, true, 4>(),   variant<5, true, 6>(),
-      variant<4, true, 3>(),   variant<3, true, 6>()};
+      variant<14, 0, 6>(), variant<14, 0, 5>(), variant<8, 0, 8>(), variant<7, 0, 5>(),
+      variant<6, 0, 6>(),  variant<4, 0, 8>(),  variant<14, 1, 5>(), variant<8, 1, 4>(),
+      variant<5, 1, 6>(),  variant<4, 1, 3>(),  variant<3, 1, 6>(),  variant<7, 2, 5>(),
+      variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>()};
   return v;
 }
 
 bool fits(const Variant& v, int HP) {
-  return v.smem(HP) <= 232448 && (HP / 128) * v.cols() <= 512;
+  return v.smem(HP) <= 232448 && (HP / 128) * v.tmem_per_mtile() <= 512;
 }
 
 // default before autotuning: the widest tile that still leaves >= 3 stages
@@ -527,10 +561,10 @@ int default_variant(int HP, bool split) {
   const auto& vs = all_variants();
   int best = -1;
   for (int i = 0; i < (int)vs.size(); ++i) {
-    if (vs[i].split != split || !fits(vs[i], HP) || vs[i].stages < 3) continue;
-    if (best < 0 || vs[i].cols() > vs[best].cols() ||
-        (vs[i].cols() == vs[best].cols() && vs[i].stages > vs[best].stages))
-      best = i;
+    if (vs[i].split() != split || !fits(vs[i], HP) || vs[i].stages < 3) continue;
+    // widest MMA (fewest instructions per column), then the most columns
+    auto key = [&](const Variant& v) { return v.tmem_per_mtile() * 1000 + v.cols() * 10 + v.stages; };
+    if (best < 0 || key(vs[i]) > key(vs[best])) best = i;
   }
   return best;
 }
@@ -553,7 +587,7 @@ cudaError_t select_variant(rtn_ctx* ctx, int idx) {
   tc.smem = v.smem(tc.h_pad);
   tc.fn = v.fn;
   int ncol = 32;
-  while (ncol < (tc.h_pad / 128) * v.cols()) ncol *= 2;
+  while (ncol < (tc.h_pad / 128) * v.tmem_per_mtile()) ncol *= 2;
   tc.tmem_cols = ncol;
   return cudaFuncSetAttribute(tc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
 }
@@ -687,10 +721,10 @@ int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages
   const auto& vs = all_variants();
   if (idx < 0 || idx >= (int)vs.size()) return -1;
   if (npc) *npc = vs[idx].npc;
-  if (split) *split = vs[idx].split;
+  if (split) *split = vs[idx].mode;
   if (stages) *stages = vs[idx].stages;
   const bool want = ctx->opt.precision == RTN_BF16X2;
-  return (vs[idx].split == want && fits(vs[idx], ctx->net.tc.h_pad)) ? 0 : 1;
+  return (vs[idx].split() == want && fits(vs[idx], ctx->net.tc.h_pad)) ? 0 : 1;
 }
 
 cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx) { return select_variant(ctx, idx); }

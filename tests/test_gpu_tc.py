@@ -89,3 +89,32 @@ def test_tc_rti_step_matches_fp32_path(rtn, orc):
                                 X, U, xref, uref, x0)
     assert (st.cpu().numpy() == 0).all() and ctl.device_error() == 0
     assert np.abs(u0.cpu().numpy() - u0r).max() / np.abs(u0r).max() < 1e-3
+
+
+@pytest.mark.parametrize("widths", [[17, 256, 256, 256, 3], [17, 512, 512, 3], [17, 128, 128, 3]])
+@pytest.mark.parametrize("precision", ["bf16x2", "bf16"])
+def test_tc_every_tile_variant(rtn, orc, widths, precision):
+    # every tile shape the autotuner may pick gives the same result
+    layers = [(Wl, W.round_bf16(np.random.default_rng(20 + i).normal(0, 0.05, bl.shape)))
+              for i, (Wl, bl) in enumerate(W.xavier_mlp(widths, 5, bf16=True))]
+    N = np.array([20] * 40 + [7], np.int32)  # several tiles per CTA plus a ragged tail
+    ctl = rtn.Controller(N, np.full(len(N), 0.05), W.Q_DIAG, W.R_DIAG, quad=QUAD, layers=layers,
+                         precision=precision)
+    X, U = W.random_nodes(ctl.n_states, 8)
+    X = X.astype(np.float32).astype(np.float64)
+    U = U[:ctl.n_nodes].astype(np.float32).astype(np.float64)
+    inst = np.repeat(np.arange(len(N)), N)
+    idx = np.concatenate([np.random.default_rng(1).choice(ctl.n_nodes - 1, 40, replace=False), [ctl.n_nodes - 1]])
+    ref = [orc.mlp_fwd_jac(layers, np.concatenate([X[n + inst[n]], U[n]]))[1] for n in idx]
+    xd = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    ud = torch.as_tensor(U, dtype=torch.float32, device="cuda")
+    variants = ctl.tc_variants()
+    assert variants
+    tol = 1e-3 if precision == "bf16x2" else 2e-2
+    for vi, npc, mode, stages in variants:
+        ctl.tc_select(vi)
+        _, JD = ctl.mlp_eval(xd, ud)
+        assert ctl.device_error() == 0
+        J = JD.double().cpu().numpy()
+        err = max(np.linalg.norm(J[n] - r) / np.linalg.norm(r) for n, r in zip(idx, ref))
+        assert err < tol, (vi, npc, mode, stages, err)
