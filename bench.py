@@ -281,6 +281,12 @@ def main():
             if "UNSUPPORTED" not in str(e):
                 raise
     cfg["precision"] = prec
+    if prec != "fp32":
+        # pick the tensor-core tile shape for this network and batch
+        vi, vms = ctl.autotune()
+        shape = dict((v[0], v[1:]) for v in ctl.tc_variants())[vi]
+        cfg["tile"] = {"variant": vi, "nodes_per_cta": shape[0], "operand_mode": shape[1],
+                       "stages": shape[2], "autotune_ms": vms}
     ms_step, clocks, rmse = time_closed_loop(ctl, prob, args.steps, args.warmup)
     if world > 1:
         import torch.distributed as dist
@@ -320,6 +326,7 @@ def main():
     ctl.close()
     if prec != "fp32" and not args.no_fp32:
         c32 = make(prob, "fp32")
+
         ms32, _, _ = time_closed_loop(c32, prob, max(3, args.steps // 4), 2)
         x32, u32 = c32.get_iterate()
         o32 = c32.linearize(x32, u32)

@@ -287,22 +287,73 @@ __device__ __forceinline__ float load_z(const TcArgs& a, int node, int j) {
   return j < NX ? a.x[(size_t)(node + a.node_inst[node]) * NX + j] : a.u[(size_t)node * NU + (j - NX)];
 }
 
-// Persistent: CTA b handles node tiles b, b + gridDim.x, ...  The producer and
-// MMA issuer run through the same sequence of (tile, layer, M tile, K block)
-// without stopping, so the weights of the next tile stream in while the
-// epilogue of the current one runs.
+// packed results of one node for one row k (BF16 hi, and lo in split modes)
+struct NodeOut {
+  uint32_t th[8], tl[8];  // tangents 0..15 as bf16 pairs
+  uint32_t v, e;          // value and tangent 16: bf16 hi in bits 0..15, lo in 16..31
+};
+
+__device__ __forceinline__ uint32_t pack1(float x) {
+  __nv_bfloat16 hi = __float2bfloat16_rn(x);
+  __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+  return (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
+}
+
+template <int MODE>
+__device__ __forceinline__ void node_pack(float a, float d, const float* t16, float t17, NodeOut& o) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float v0 = d * t16[2 * j], v1 = d * t16[2 * j + 1];
+    o.th[j] = pack_bf16(v0, v1);
+    if (MODE != 0) o.tl[j] = pack_res(v0, v1, o.th[j]);
+  }
+  o.v = pack1(a);
+  o.e = pack1(d * t17);
+}
+
+template <int NPC, int C, int MODE>
+__device__ __forceinline__ void node_store(uint8_t* X, uint32_t xbytes, int k, int n, const NodeOut& o) {
+  using G = XGeo<C, MODE>;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = 16 * n + 8 * h;
+    *reinterpret_cast<uint4*>(X + G::hi(k, c)) = make_uint4(o.th[4 * h], o.th[4 * h + 1], o.th[4 * h + 2], o.th[4 * h + 3]);
+    if (MODE != 0)
+      *reinterpret_cast<uint4*>(X + G::lo(k, c, xbytes)) =
+          make_uint4(o.tl[4 * h], o.tl[4 * h + 1], o.tl[4 * h + 2], o.tl[4 * h + 3]);
+  }
+  *reinterpret_cast<uint16_t*>(X + G::hi(k, 16 * NPC + n)) = (uint16_t)(o.v & 0xffffu);
+  *reinterpret_cast<uint16_t*>(X + G::hi(k, 17 * NPC + n)) = (uint16_t)(o.e & 0xffffu);
+  if (MODE != 0) {
+    *reinterpret_cast<uint16_t*>(X + G::lo(k, 16 * NPC + n, xbytes)) = (uint16_t)(o.v >> 16);
+    *reinterpret_cast<uint16_t*>(X + G::lo(k, 17 * NPC + n, xbytes)) = (uint16_t)(o.e >> 16);
+  }
+}
+
+// Persistent: CTA b handles node tiles b, b + gridDim.x, ...  The activation
+// matrix X is tracked in blocks of 128 rows (one M tile of the producing
+// layer = two 64-wide K blocks of the consuming layer), so that
+//  * the epilogue of M tile m starts as soon as that tile's accumulator is
+//    final, and writes its rows once the current layer's last M tile has read
+//    the block it overwrites (xfree, committed inside the MMA stream);
+//  * the next layer's MMAs start on every block as soon as it is written
+//    (xready), while later blocks are still being produced;
+//  * the next tile's input layer is written block by block while the current
+//    tile's output layer still runs.
+// The producer and the MMA issuer run through the same sequence of
+// (tile, layer, M tile, K block) without stopping.
 template <int NPC, int MODE, int STAGES>
 __global__ void __launch_bounds__(THREADS, 1)
     mlp_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   constexpr int C = Cols<NPC>::C, TAIL = Cols<NPC>::TAIL, HALF = (NPC + 1) / 2;
-  constexpr bool SPLIT = MODE != 0;
-  constexpr int CX = XGeo<C, MODE>::CX;   // columns of one X buffer
+  constexpr int CX = XGeo<C, MODE>::CX;        // columns of one X buffer
   constexpr int NMMA = MODE == 2 ? 2 * C : C;  // N of every MMA = TMEM columns per M tile
   static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
   constexpr int NZV = NPC * NZ;
+  constexpr int MT = 4;  // at most 4 M tiles (hidden width <= 512)
   extern __shared__ uint8_t smem_raw[];
   const int HP = a.HP, nkb = HP / 64, n_mt = HP / 128;
-  const int n_layers = a.n_hidden_mm + 1;
+  const int nh = a.n_hidden_mm, n_layers = nh + 1;
   const int n_tiles = (a.n_nodes + NPC - 1) / NPC;
   const uint32_t sraw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
@@ -314,14 +365,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t xhi_s = sbase, xlo_s = sbase + xbytes;
   const uint32_t w_s = sbase + xtotal;
   uint8_t* tail_area = sm + xtotal + STAGES * WT_BYTES;
-  const uint32_t bar_s = smem_u32(tail_area);  // full[S], empty[S], acc_full, x_ready
+  const uint32_t bar_s = smem_u32(tail_area);
   auto full_bar = [&](int s) { return bar_s + 8u * s; };
   auto empty_bar = [&](int s) { return bar_s + 8u * (STAGES + s); };
-  const uint32_t acc_full = bar_s + 8u * (2 * STAGES);
-  const uint32_t x_ready = bar_s + 8u * (2 * STAGES + 1);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail_area + 8 * (2 * STAGES + 2));
+  auto acc_full = [&](int m) { return bar_s + 8u * (2 * STAGES + m); };
+  auto tmem_free = [&](int m) { return bar_s + 8u * (2 * STAGES + MT + m); };
+  auto xready = [&](int j) { return bar_s + 8u * (2 * STAGES + 2 * MT + j); };
+  auto xfree = [&](int j) { return bar_s + 8u * (2 * STAGES + 3 * MT + j); };
+  constexpr int NBAR = 2 * STAGES + 4 * MT;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail_area + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* zbuf = reinterpret_cast<float*>(tail_area + 8 * (2 * STAGES + 2) + 16);
+  float* zbuf = reinterpret_cast<float*>(tail_area + 8 * NBAR + 16);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -330,8 +384,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(x_ready, EPI_WARPS);
+    for (int m = 0; m < MT; ++m) {
+      mbar_init(acc_full(m), 1);
+      mbar_init(tmem_free(m), EPI_WARPS);
+      mbar_init(xready(m), EPI_WARPS);
+      mbar_init(xfree(m), 1);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -356,7 +414,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
         for (int l = 0; l < n_layers && ok; ++l) {
-          const int mts = (l < a.n_hidden_mm) ? n_mt : 1;
+          const int mts = (l < nh) ? n_mt : 1;
           for (int m = 0; m < mts && ok; ++m)
             for (int kb = 0; kb < nkb && ok; ++kb) {
               if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
@@ -375,18 +433,28 @@ __global__ void __launch_bounds__(THREADS, 1)
       constexpr uint32_t idesc = idesc_bf16(128, NMMA) | (1u << 16);  // B is N-major
       const uint32_t lbo = CX * 16u;
       int s = 0;
-      uint32_t ph = 0, xr = 0;
+      uint32_t ph = 0, used = 0, tf_par = 0, xr_par = 0;
       bool ok = true;
       int it = 0;
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it)
-        for (int l = 0; l < n_layers && ok; ++l, ++xr) {
-          if (!(ok = mbar_wait(x_ready, xr & 1u, abort_flag, a.err))) break;
+        for (int l = 0; l < n_layers && ok; ++l) {
           trace(a, it, l, n_layers, 0);
-          tc_fence_after();
-          const int mts = (l < a.n_hidden_mm) ? n_mt : 1;
+          const int mts = (l < nh) ? n_mt : 1;
           for (int m = 0; m < mts && ok; ++m) {
+            if (used & (1u << m)) {
+              if (!(ok = mbar_wait(tmem_free(m), (tf_par >> m) & 1u, abort_flag, a.err))) break;
+              tf_par ^= 1u << m;
+            }
+            used |= 1u << m;
+            tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(m * NMMA);
             for (int kb = 0; kb < nkb && ok; ++kb) {
+              const int j = kb >> 1;
+              if (m == 0 && (kb & 1) == 0) {
+                if (!(ok = mbar_wait(xready(j), (xr_par >> j) & 1u, abort_flag, a.err))) break;
+                xr_par ^= 1u << j;
+                tc_fence_after();
+              }
               if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, a.err))) break;
               tc_fence_after();
               const uint32_t as = w_s + s * WT_BYTES;
@@ -399,9 +467,11 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
               mma_commit(empty_bar(s));
               if (++s == STAGES) { s = 0; ph ^= 1u; }
+              // the last M tile of the layer has read block j: it may be rewritten
+              if (m == mts - 1 && (kb & 1)) mma_commit(xfree(j));
             }
+            if (ok) mma_commit(acc_full(m));
           }
-          if (ok) mma_commit(acc_full);
           trace(a, it, l, n_layers, 1);
         }
     }
@@ -411,104 +481,138 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const int half = e >> 2;
     const int et = threadIdx.x - 64;  // 0..255
-    // zero both X buffers once: pad columns are never written again
+    // zero the X buffers once: pad columns are never written again
     for (uint32_t o = (uint32_t)et * 16u; o < xtotal; o += 256u * 16u)
       *reinterpret_cast<uint4*>(sm + o) = make_uint4(0u, 0u, 0u, 0u);
     float zpref = (et < NZV) ? load_z(a, blockIdx.x * NPC + et / NZ, et % NZ) : 0.0f;
-    uint32_t accp = 0;
-    bool ok = true;
+    uint32_t acc_par = 0, xf_par = 0;
+    bool ok = true, first_input = true;
     const bool tr = (e == 0 && lane == 0);
-    int it = 0;
-    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+
+    // bounded wait by lane 0, result shared with the warp
+    auto wwait = [&](uint32_t bar, uint32_t par) -> bool {
+      int w_ok = 0;
+      if (lane == 0) w_ok = mbar_wait(bar, par, abort_flag, a.err);
+      return __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+    };
+
+    // input layer of tile `tile` (FP32), block by block; thread et handles
+    // neuron 128 j + (et % 128) for one half of the nodes
+    auto input_layer = [&](int tile, int it_) -> bool {
       const int node0 = tile * NPC;
-      if (tr) trace(a, it, n_layers, n_layers, 0);
       if (et < NZV) zbuf[et] = zpref;
       asm volatile("bar.sync 1, 256;" ::: "memory");
-      // input layer (FP32): rows k = neuron i
-      for (int i = et; i < HP; i += 256) {
+      if (tr) trace(a, it_, n_layers, n_layers, 0);
+      const int hh = et >> 7;
+      for (int j = 0; j < n_mt; ++j) {
+        if (!first_input) {
+          if (!wwait(xfree(j), (xf_par >> j) & 1u)) return false;
+          xf_par ^= 1u << j;
+        }
+        const int i = 128 * j + (et & 127);
         float w[NZ];
 #pragma unroll
-        for (int j = 0; j < NZ; ++j) w[j] = a.W0[(size_t)i * NZ + j];
+        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)i * NZ + jj];
         const float bi = a.b0[i];
 #pragma unroll
         for (int n = 0; n < NPC; ++n) {
+          if ((n < HALF) != (hh == 0)) continue;
           float s = bi;
 #pragma unroll
-          for (int j = 0; j < NZ; ++j) s = fmaf(w[j], zbuf[n * NZ + j], s);
+          for (int jj = 0; jj < NZ; ++jj) s = fmaf(w[jj], zbuf[n * NZ + jj], s);
           const bool real = node0 + n < a.n_nodes;
           const float av = real ? tanhf(s) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
-          write_node<NPC, C, MODE>(X, xbytes, i, n, av, d, w, w[16]);
+          NodeOut o;
+          node_pack<MODE>(av, d, w, w[16], o);
+          node_store<NPC, C, MODE>(X, xbytes, i, n, o);
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(xready(j));
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(x_ready);
-      if (tr) trace(a, it, n_layers, n_layers, 1);
+      first_input = false;
+      if (tr) trace(a, it_, n_layers, n_layers, 1);
+      return true;
+    };
 
-      for (int l = 0; l < n_layers; ++l, ++accp) {
-        const bool last = (l == a.n_hidden_mm);
-        if (last && et < NZV) {
-          // prefetch the next tile's inputs while the output layer runs
-          const int nt = tile + gridDim.x;
-          zpref = nt < n_tiles ? load_z(a, nt * NPC + et / NZ, et % NZ) : 0.0f;
-        }
-        int w_ok = 0;
-        if (lane == 0) w_ok = mbar_wait(acc_full, accp & 1u, abort_flag, a.err);
-        w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
-        if (!w_ok) { ok = false; break; }
-        if (tr) trace(a, it, l, n_layers, 2);
-        tc_fence_after();
-        if (!last) {
-          for (int m = 0; m < n_mt; ++m) {
-            const int i = 128 * m + 32 * q + lane;
-            const float bi = a.bias[(size_t)l * HP + i];
-            const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * NMMA);
-            float tl[TAIL];
+    int it = 0;
+    if (blockIdx.x < n_tiles) ok = input_layer(blockIdx.x, 0);
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+      const int node0 = tile * NPC;
+      // hidden layers
+      for (int l = 0; l < nh && ok; ++l) {
+        for (int m = 0; m < n_mt; ++m) {
+          if (!(ok = wwait(acc_full(m), (acc_par >> m) & 1u))) break;
+          acc_par ^= 1u << m;
+          if (tr && m == 0) trace(a, it, l, n_layers, 2);
+          tc_fence_after();
+          const int i = 128 * m + 32 * q + lane;
+          const float bi = a.bias[(size_t)l * HP + i];
+          const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * NMMA);
+          // block m of X may be overwritten once this layer's last M tile read it
+          if (!(ok = wwait(xfree(m), (xf_par >> m) & 1u))) break;
+          xf_par ^= 1u << m;
+          float tl[TAIL];
 #pragma unroll
-            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16_sum<C, MODE>(trow + 16 * NPC + 16 * c, tl + 16 * c);
+          for (int c = 0; c < TAIL / 16; ++c) tmem_ld16_sum<C, MODE>(trow + 16 * NPC + 16 * c, tl + 16 * c);
+          tmem_wait_ld();
+#pragma unroll
+          for (int n = 0; n < NPC; ++n) {
+            if ((n < HALF) != (half == 0)) continue;
+            float t[16];
+            tmem_ld16_sum<C, MODE>(trow + 16 * n, t);
             tmem_wait_ld();
-#pragma unroll
-            for (int n = 0; n < NPC; ++n) {
-              if ((n < HALF) != (half == 0)) continue;
-              float t[16];
-              tmem_ld16_sum<C, MODE>(trow + 16 * n, t);
-              tmem_wait_ld();
-              const float av = tanhf(tl[n] + bi), d = 1.0f - av * av;
-              write_node<NPC, C, MODE>(X, xbytes, i, n, av, d, t, tl[NPC + n]);
-            }
+            const float av = tanhf(tl[n] + bi), d = 1.0f - av * av;
+            NodeOut o;
+            node_pack<MODE>(av, d, t, tl[NPC + n], o);
+            node_store<NPC, C, MODE>(X, xbytes, i, n, o);
           }
           tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tmem_free(m));
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
-          if (lane == 0) mbar_arrive(x_ready);
-          if (tr) trace(a, it, l, n_layers, 3);
-        } else {
-          if (q == 0) {
-            // output layer: TMEM lanes 0..2 hold the three outputs
-            float tl[TAIL];
+          if (lane == 0) mbar_arrive(xready(m));
+        }
+        if (tr) trace(a, it, l, n_layers, 3);
+      }
+      if (!ok) break;
+      // next tile's input layer, overlapping this tile's output layer
+      const int nt = tile + gridDim.x;
+      if (nt < n_tiles) {
+        if (et < NZV) zpref = load_z(a, nt * NPC + et / NZ, et % NZ);
+        if (!(ok = input_layer(nt, it + 1))) break;
+      }
+      // output layer: TMEM lanes 0..2 of M tile 0 hold the three outputs
+      if (!(ok = wwait(acc_full(0), acc_par & 1u))) break;
+      acc_par ^= 1u;
+      if (tr) trace(a, it, nh, n_layers, 2);
+      tc_fence_after();
+      if (q == 0) {
+        float tl[TAIL];
 #pragma unroll
-            for (int c = 0; c < TAIL / 16; ++c) tmem_ld16_sum<C, MODE>(tmem + 16 * NPC + 16 * c, tl + 16 * c);
-            tmem_wait_ld();
-            const float bo = lane < NO ? a.bias[(size_t)a.n_hidden_mm * HP + lane] : 0.0f;
+        for (int c = 0; c < TAIL / 16; ++c) tmem_ld16_sum<C, MODE>(tmem + 16 * NPC + 16 * c, tl + 16 * c);
+        tmem_wait_ld();
+        const float bo = lane < NO ? a.bias[(size_t)nh * HP + lane] : 0.0f;
 #pragma unroll
-            for (int n = 0; n < NPC; ++n) {
-              if ((n < HALF) != (half == 0)) continue;
-              float t[16];
-              tmem_ld16_sum<C, MODE>(tmem + 16 * n, t);
-              tmem_wait_ld();
-              const int node = node0 + n;
-              if (lane < NO && node < a.n_nodes) {
-                a.fD[(size_t)node * NO + lane] = tl[n] + bo;
-                float* J = a.JD + (size_t)node * NO * NZ + lane * NZ;
+        for (int n = 0; n < NPC; ++n) {
+          if ((n < HALF) != (half == 0)) continue;
+          float t[16];
+          tmem_ld16_sum<C, MODE>(tmem + 16 * n, t);
+          tmem_wait_ld();
+          const int node = node0 + n;
+          if (lane < NO && node < a.n_nodes) {
+            a.fD[(size_t)node * NO + lane] = tl[n] + bo;
+            float* J = a.JD + (size_t)node * NO * NZ + lane * NZ;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) J[j] = t[j];
-                J[16] = tl[NPC + n];
-              }
-            }
+            for (int j = 0; j < 16; ++j) J[j] = t[j];
+            J[16] = tl[NPC + n];
           }
-          tc_fence_before();
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_free(0));
     }
   }
 
@@ -533,7 +637,7 @@ struct Variant {
   int tmem_per_mtile() const { return mode == 2 ? 2 * cols() : cols(); }
   size_t smem(int HP) const {
     return 1024 + (mode != 0 ? 2 : 1) * (size_t)cols() * HP * 2 + (size_t)stages * WT_BYTES +
-           8 * (2 * stages + 2) + 16 + (size_t)npc * NZ * 4;
+           8 * (2 * stages + 16) + 16 + (size_t)npc * NZ * 4;
   }
 };
 
@@ -546,7 +650,7 @@ Variant variant() {
 const std::vector<Variant>& all_variants() {
   static const std::vector<Variant> v = {
       variant<14, 0, 6>(), variant<14, 0, 5>(), variant<8, 0, 8>(), variant<7, 0, 5>(),
-      variant<6, 0, 6>(),  variant<4, 0, 8>(),  variant<14, 1, 5>(), variant<8, 1, 4>(),
+      variant<6, 0, 6>(),  variant<4, 0, 8>(),  variant<8, 1, 4>(),
       variant<5, 1, 6>(),  variant<4, 1, 3>(),  variant<3, 1, 6>(),  variant<7, 2, 5>(),
       variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>()};
   return v;
