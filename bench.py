@@ -114,11 +114,14 @@ def launches_per_step(ctl):
 
 
 def time_closed_loop(ctl, prob, steps, warmup):
+    """Closed loop on the drag plant; every instance starts on its reference
+    state (the random initial states of the workload recipe are used for the
+    single-RTI-step measurements)."""
     import torch
     xrt, urt = W.trajectory_refs(prob, steps + warmup)
     xrt_d = torch.as_tensor(xrt, dtype=torch.float32, device="cuda").contiguous()
     urt_d = torch.as_tensor(urt, dtype=torch.float32, device="cuda").contiguous()
-    x0 = prob["x0"].copy()
+    x0 = xrt[:, 0].copy()
     ctl.reset(torch.as_tensor(x0, dtype=torch.float32, device="cuda"))
     xp = torch.as_tensor(x0, dtype=torch.float64, device="cuda").contiguous()
     ctl.closed_loop(warmup, xrt_d, urt_d, xp, plant="drag", record=False)
@@ -226,6 +229,61 @@ def cpu_baseline(prob, budget_s=15.0):
             "sample": f"{done} of {prob['B']} instances, one RTI step (FP64 C, OpenMP over instances)"}
 
 
+def bench_ragged(steps=200):
+    """cfg4: 4096 instances with horizons N_b ~ U{10..50}, dt_b ~ U[0.02, 0.1],
+    17-256x4-3 network (split BF16), closed loop on the drag plant."""
+    import torch
+    prob = W.make_problem("cfg4_ragged_batch", seed=0, bf16=True)
+    ctl = make(prob, "bf16x2")
+    vi, _ = ctl.autotune()
+    ms, clocks, rmse = time_closed_loop(ctl, prob, steps, 3)
+    x, u = ctl.get_iterate()
+    out = ctl.linearize(x, u)
+    nn = int(prob["N"].sum())
+    ms_lin = time_calls(lambda: ctl.linearize(x, u, out), 10)
+    jerr = jac_error(ctl, prob)
+    ctl.close()
+    return {"workload": "cfg4_ragged_batch: 4096 instances, N_b in {10..50} (sum %d nodes), "
+                        "dt_b in [0.02, 0.1] s, MLP 17-256x4-3 split BF16, %d-step closed loop, "
+                        "drag plant, one CUDA graph per step" % (nn, steps),
+            "rti_steps_per_s": prob["B"] / (ms * 1e-3), "ms_per_step": ms,
+            "node_linearizations_per_s": nn / (ms_lin * 1e-3), "jac_rel_err_max": jerr,
+            "tracking_rmse_m": rmse, "tile_variant": vi}
+
+
+def bench_learned(epochs=2, steps=100):
+    """cfg5: 2^20 seeded samples -> drag residual targets, train 17-512x6-3
+    (Adam, lr 1e-3, batch 4096), then a 4096-instance closed loop on the drag
+    plant with the learned network vs the nominal model."""
+    import torch
+    prob = W.make_problem("cfg5_learned", seed=0, bf16=True)
+    n = prob["cfg"]["n_samples"]
+    X, U = W.training_samples(n, 0)
+    Xd = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    Ud = torch.as_tensor(U, dtype=torch.float32, device="cuda")
+    learn = make(prob, "bf16x2")
+    Yd = learn.drag_targets(Xd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = learn.train(Xd, Ud, Yd, epochs=epochs, batch=prob["cfg"]["batch"], lr=prob["cfg"]["lr"])
+    t_train = time.perf_counter() - t0
+    w = prob["widths"]
+    fwd = 2 * sum(a * b for a, b in zip(w[:-1], w[1:]))
+    flops = 3 * fwd * epochs * (n // prob["cfg"]["batch"]) * prob["cfg"]["batch"]
+    learn.autotune()
+    _, _, rmse_l = time_closed_loop(learn, prob, steps, 3)
+    nominal = make(dict(prob, layers=None), "fp32")
+    _, _, rmse_n = time_closed_loop(nominal, prob, steps, 3)
+    learn.close(); nominal.close()
+    return {"workload": "cfg5_learned: %d samples, MLP %s, Adam lr 1e-3 batch 4096, %d epochs, "
+                        "then %d-step closed loop of 4096 instances on the drag plant" % (
+                            n, "-".join(map(str, w)), epochs, steps),
+            "train_samples_per_s": epochs * (n // prob["cfg"]["batch"]) * prob["cfg"]["batch"] / t_train,
+            "train_tflops": flops / t_train / 1e12, "train_precision": "fp32 SIMT",
+            "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
+            "tracking_rmse_m": {"learned": rmse_l, "nominal": rmse_n}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -236,6 +294,7 @@ def main():
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the ragged and learned workloads")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -335,6 +394,9 @@ def main():
                                       "node_linearizations_per_s": nn / (ml32 * 1e-3),
                                       "jac_rel_err_max": jac_error(c32, prob)}
         c32.close()
+    if rank == 0 and world == 1 and not args.no_extra:
+        line["ragged_batch"] = bench_ragged()
+        line["learned_part"] = bench_learned()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob)
     if rank == 0:

@@ -32,6 +32,7 @@ struct Slot {
   T K[NU * NX], k[NU];
   T P2[NX * NX], p2[NX];
   T dx[NX], du[NU];
+  double L[NU * NU], Linv[NU];  // FP64 Cholesky factor (strict lower part) and 1/diag
   int notpd;
 };
 
@@ -134,8 +135,9 @@ __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
       }
     }
     __syncwarp();
-    // FP64 Cholesky of Huu and the 14 right-hand sides (13 of Hux, 1 of hu)
-    if (lane < NX + 1) {
+    // FP64 Cholesky of Huu by one lane (4 square roots, 4 reciprocals), then
+    // the 14 right-hand sides (13 of Hux, 1 of hu) on 14 lanes with products
+    if (lane == 0) {
       double L[NU][NU];
       bool pd = true;
 #pragma unroll
@@ -144,37 +146,45 @@ __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
 #pragma unroll
         for (int q = 0; q < j; ++q) s -= L[j][q] * L[j][q];
         pd &= (s > 0.0);
-        double d = sqrt(fmax(s, 1e-300));
+        const double d = sqrt(fmax(s, 1e-300)), inv = 1.0 / d;
         L[j][j] = d;
+        S.Linv[j] = inv;
 #pragma unroll
         for (int i = j + 1; i < NU; ++i) {
           double v = (double)S.Huu[i * NU + j];
 #pragma unroll
           for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
-          L[i][j] = v / d;
+          L[i][j] = v * inv;
         }
       }
+#pragma unroll
+      for (int i = 0; i < NU; ++i)
+#pragma unroll
+        for (int j = 0; j < NU; ++j) S.L[i * NU + j] = (j < i) ? L[i][j] : 0.0;
+      if (!pd) S.notpd = 1;
+    }
+    __syncwarp();
+    if (lane < NX + 1) {
       double y[NU];
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
         double v = (lane < NX) ? (double)S.Hux[i * NX + lane] : (double)S.hu[i];
 #pragma unroll
-        for (int q = 0; q < i; ++q) v -= L[i][q] * y[q];
-        y[i] = v / L[i][i];
+        for (int q = 0; q < i; ++q) v -= S.L[i * NU + q] * y[q];
+        y[i] = v * S.Linv[i];
       }
 #pragma unroll
       for (int i = NU - 1; i >= 0; --i) {
         double v = y[i];
 #pragma unroll
-        for (int q = i + 1; q < NU; ++q) v -= L[q][i] * y[q];
-        y[i] = v / L[i][i];
+        for (int q = i + 1; q < NU; ++q) v -= S.L[q * NU + i] * y[q];
+        y[i] = v * S.Linv[i];
       }
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
         if (lane < NX) S.K[i * NX + lane] = (T)(-y[i]);
         else S.k[i] = (T)(-y[i]);
       }
-      if (!pd) S.notpd = 1;
     }
     __syncwarp();
     // P2 = Q + A'PA + Hux'K,  p2 = q + A'g + Hux'k ; store the gains
