@@ -10,7 +10,9 @@ roofline accounting and the CPU baseline.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
+import hashlib
 import json
+import re
 import os
 import subprocess
 import sys
@@ -35,6 +37,23 @@ def peaks():
         d = json.load(open(p))
         return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained", d["bf16_tflops"]), "measured"
     return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+def profiled_traffic(tile):
+    """DRAM bytes per launch of the network kernel from the committed ncu
+    summary, if the kernel source and tile shape are still the captured ones."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "mlp_tc_kernel_cfg3_h512_bf16x2.md")).read()
+        src = open(os.path.join(ROOT, "paper_2203_07747_b300", "csrc", "mlp_tc.cu"), "rb").read()
+        md5 = re.search(r"mlp_tc.cu md5 at capture: (\w+)", text).group(1)
+        shape = re.search(r"mlp_tc_kernel<(\d+), (\d+), (\d+)>", text).groups()
+        if md5 != hashlib.md5(src).hexdigest() or tile is None:
+            return None
+        if (tile["nodes_per_cta"], int(tile["operand_mode"]), tile["stages"]) != tuple(map(int, shape)):
+            return None
+        return int(re.search(r"dram_bytes_per_launch: (\d+)", text).group(1))
+    except (OSError, AttributeError):
+        return None
 
 
 def fwd_flops_per_node(widths):
@@ -367,7 +386,8 @@ def main():
         roof = {"bound": "tensor", "peak": bf16_burst, "peak_kind": f"bf16 burst ({peak_src})"}
     roof.update({"achieved": flops / (ms_mlp * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "algorithmic_flops_per_launch": flops, "ms_per_launch": ms_mlp,
-                 "kernel": "network value + forward-mode Jacobian (a1)", "traffic": None})
+                 "kernel": "network value + forward-mode Jacobian (a1)",
+                 "traffic": profiled_traffic(cfg.get("tile")) if args.config == "cfg3_bf16_precision" else None})
     roof["frac"] = roof["achieved"] / roof["peak"]
 
     ms_e2e, bi, bo = e2e_rti(ctl, prob, max(5, args.steps))

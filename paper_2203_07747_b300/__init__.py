@@ -200,7 +200,7 @@ class Controller:
         return code.value
 
     def tc_variants(self):
-        """[(index, nodes per CTA, split, stages)] of the tile shapes that fit."""
+        """[(index, nodes per CTA, operand mode 0|1|2, stages)] of the tile shapes that fit."""
         L = load()
         n = C.c_int()
         self._check(L.rtn_tc_variants(self._h, C.byref(n)), "rtn_tc_variants")
@@ -210,7 +210,7 @@ class Controller:
             self._check(L.rtn_tc_variant_info(self._h, i, C.byref(npc), C.byref(sp), C.byref(stg),
                                               C.byref(fits)), "rtn_tc_variant_info")
             if fits.value:
-                out.append((i, npc.value, bool(sp.value), stg.value))
+                out.append((i, npc.value, sp.value, stg.value))
         return out
 
     def tc_select(self, idx):
