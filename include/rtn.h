@@ -200,8 +200,10 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
 
 /* Tile shapes of the tensor-core network kernel (the autotuner's search
  * space).  rtn_tc_variants: number of compiled shapes.  rtn_tc_variant_info:
- * nodes per CTA, split flag and pipeline depth of shape idx, *fits = 1 if it
- * can run this context's network and precision.  rtn_tc_select: use shape idx
+ * nodes per CTA (per CTA pair in mode 3), operand mode in *split (0 single
+ * BF16; 1, 2 split hi + lo on one CTA; 3 split on a CTA pair, M = 256) and
+ * pipeline depth of shape idx, *fits = 1 if it can run this context's
+ * network and precision.  rtn_tc_select: use shape idx
  * (RTN_E_UNSUPPORTED if it does not fit).  rtn_autotune: time every fitting
  * shape on the context's current iterate (synchronous; 1 warm-up + 3 timed
  * calls each), keep the fastest, return its index and time per call [ms].
@@ -218,7 +220,15 @@ rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms);
  * ((i * (L + 1) + l) * 8 + f) for the i-th tile of CTA 0, layer l < L
  * (L = tensor-core layers) with f = 0 MMA start, 1 MMA issued, 2 epilogue
  * start, 3 epilogue done, and l = L for the input layer (f = 0 start,
- * 1 done).  rtn_tc_trace_read copies n entries to host memory (synchronous). */
+ * 1 done).  Fields 4..7 of layer l < L hold SM clock cycles spent waiting
+ * during that layer: the MMA issuer on activation blocks (4), on weight tiles
+ * (5) and on the release of an accumulator (6); the first epilogue warp on
+ * accumulators and free activation blocks (7).  On the CTA-pair shapes
+ * (mode 3) fields 2..7 of l = L hold cycle sums over tile i: epilogue work
+ * (2), waiting for all epilogue warps before a block is published (3),
+ * pushing blocks to the peer CTA (4), and the MMA issuer's waits on
+ * activation blocks produced by rank 1 (6) and by rank 0 (7).
+ * rtn_tc_trace_read copies n entries to host memory (synchronous). */
 #define RTN_TC_TRACE_LEN 65536
 rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable);
 rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n);

@@ -200,7 +200,8 @@ class Controller:
         return code.value
 
     def tc_variants(self):
-        """[(index, nodes per CTA, operand mode 0|1|2, stages)] of the tile shapes that fit."""
+        """[(index, nodes per CTA (per CTA pair in mode 3), operand mode 0|1|2|3, stages)]
+        of the tile shapes that fit."""
         L = load()
         n = C.c_int()
         self._check(L.rtn_tc_variants(self._h, C.byref(n)), "rtn_tc_variants")

@@ -46,11 +46,11 @@ struct Layout {
 struct TcNet {
   int h_pad = 0;                // hidden width padded to a multiple of 128
   int n_mm = 0;                 // hidden -> hidden layers on the tensor cores
-  __nv_bfloat16* W = nullptr;   // stacked BF16 rows [n_mm*h_pad + 128][h_pad]
+  __nv_bfloat16* W = nullptr;   // stacked BF16 rows [n_mm*h_pad + 256][h_pad]
   float* bias = nullptr;        // [n_mm*h_pad + 128]
   float* W0 = nullptr;          // input layer FP32 [h_pad][17]
   float* b0 = nullptr;          // [h_pad]
-  int* err = nullptr;           // device status flag (RTN_E_TIMEOUT)
+  int* err = nullptr;           // device status flag (RTN_E_TIMEOUT, RTN_E_UNSUPPORTED)
   unsigned long long* trace = nullptr;  // optional phase timestamps (rtn_tc_trace)
   int rows_total = 0;
   int cols = 0, npc = 0, stages = 0, tmem_cols = 0, variant = -1, n_sm = 148;
@@ -128,6 +128,8 @@ int mlp_tc_take_error(rtn_ctx* ctx);
 int mlp_tc_variant_count();
 int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages);
 cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx);
+// kernel of the CTA-pair variant (npc nodes per pair, stages weight stages), or null
+const void* mlp_tc2_fn(int npc, int stages);
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
