@@ -39,21 +39,38 @@ def peaks():
     return 6400.0, 1800.0, 1400.0, "fallback"
 
 
+KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc2.cu", "tc_common.cuh")
+PROFILES = ("mlp_tc2_kernel_cfg3_h512_bf16x2.md", "mlp_tc_kernel_cfg3_h512_bf16x2.md")
+
+
+def kernel_md5():
+    """md5 over the tensor-core network kernel sources (the profiles record it)."""
+    h = hashlib.md5()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_07747_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def profiled_traffic(tile):
-    """DRAM bytes per launch of the network kernel from the committed ncu
-    summary, if the kernel source and tile shape are still the captured ones."""
-    try:
-        text = open(os.path.join(ROOT, "profiles", "mlp_tc_kernel_cfg3_h512_bf16x2.md")).read()
-        src = open(os.path.join(ROOT, "paper_2203_07747_b300", "csrc", "mlp_tc.cu"), "rb").read()
-        md5 = re.search(r"mlp_tc.cu md5 at capture: (\w+)", text).group(1)
-        shape = re.search(r"mlp_tc_kernel<(\d+), (\d+), (\d+)>", text).groups()
-        if md5 != hashlib.md5(src).hexdigest() or tile is None:
-            return None
-        if (tile["nodes_per_cta"], int(tile["operand_mode"]), tile["stages"]) != tuple(map(int, shape)):
-            return None
-        return int(re.search(r"dram_bytes_per_launch: (\d+)", text).group(1))
-    except (OSError, AttributeError):
+    """DRAM bytes per launch of the network kernel from a committed ncu
+    summary, if the kernel sources and the tile shape are the captured ones."""
+    if tile is None:
         return None
+    try:
+        md5 = kernel_md5()
+        for name in PROFILES:
+            text = open(os.path.join(ROOT, "profiles", name)).read()
+            m = re.search(r"kernel sources md5 at capture: (\w+)", text)
+            shape = re.search(r"tile shape: npc=(\d+) mode=(\d+) stages=(\d+)", text)
+            if not m or not shape or m.group(1) != md5:
+                continue
+            if (tile["nodes_per_cta"], int(tile["operand_mode"]), tile["stages"]) != tuple(map(int, shape.groups())):
+                continue
+            return int(re.search(r"dram_bytes_per_launch: (\d+)", text).group(1))
+    except (OSError, AttributeError):
+        pass
+    return None
 
 
 def fwd_flops_per_node(widths):

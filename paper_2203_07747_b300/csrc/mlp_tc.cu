@@ -5,11 +5,14 @@
 // network (its value and the 17 tangent directions d/d[x; u]).  A CTA owns
 // NPC nodes; their columns stay on chip for the whole network:
 //   * the layer input X (K = hidden width, N = node columns) lives in shared
-//     memory as the K-major, 128B-swizzled B operand of tcgen05.mma, in BF16
-//     (RTN_BF16) or as a BF16 hi + lo pair (RTN_BF16X2: X = hi + lo, two MMAs
-//     per K step into the same FP32 accumulator, ~16 significant bits);
+//     memory as the N-major, unswizzled B operand of tcgen05.mma, in BF16
+//     (RTN_BF16) or as a BF16 hi + lo pair (RTN_BF16X2: X = hi + lo, ~16
+//     significant bits), either in two buffers with two MMAs per K step
+//     (mode 1) or side by side along N in one MMA of twice the width whose
+//     two accumulator halves the epilogue adds (mode 2); mlp_tc2.cu runs the
+//     split on CTA pairs when one SM cannot hold it;
 //   * the weights W_l (M = output neurons, K-major) stream from L2 by TMA in
-//     128 x 64 tiles through an mbarrier pipeline;
+//     128 x 64 tiles (128B swizzle) through an mbarrier pipeline;
 //   * the accumulators of all output neurons (M tiles of 128 lanes x N
 //     columns, FP32) sit in tensor memory;
 //   * the epilogue warps read their lanes back (tcgen05.ld), apply
@@ -130,8 +133,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
               mbar_expect_tx(full_bar(s), WT_BYTES);
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks)
-                tma_load_2d(w_s + s * WT_BYTES + ks * 4096u, &tmap, kb * 64 + ks * 16, l * HP + m * 128,
+              for (int bx = 0; bx < W_BOXES; ++bx)
+                tma_load_2d(w_s + s * WT_BYTES + bx * 4096u, &tmap, kb * 64 + bx * W_BOX_K, l * HP + m * 128,
                             full_bar(s));
               if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint32_t as = w_s + s * WT_BYTES;
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t ad = sdesc(as + ks * 4096u);
+                const uint64_t ad = wdesc(as, ks);
                 const uint32_t bo = (uint32_t)(kb * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
                 mma_bf16(d, ad, xdesc(xhi_s + bo, lbo), idesc, (kb | ks) != 0);
                 if (MODE == 1) mma_bf16(d, ad, xdesc(xlo_s + bo, lbo), idesc, 1u);
@@ -363,6 +366,7 @@ struct Variant {
   const void* fn;
   bool split() const { return mode != 0; }
   bool pair() const { return mode == 3; }
+  int threads() const { return pair() ? THREADS + 32 : THREADS; }
   int cols() const { return 16 * npc + ((2 * npc + 15) / 16) * 16; }
   // tensor-memory columns of one accumulator tile (128 rows; 256 rows on a pair)
   int tmem_per_mtile() const { return mode >= 2 ? 2 * cols() : cols(); }
@@ -375,7 +379,7 @@ struct Variant {
   size_t smem(int HP) const {
     if (pair())
       return 1024 + (size_t)cols() * HP * 2 + (size_t)cols() * 256 + (size_t)stages * WT_BYTES +
-             8 * (2 * stages + 20) + 16 + (size_t)npc * NZ * 4;
+             8 * (2 * stages + 24) + 16 + (size_t)npc * NZ * 4;
     return 1024 + (mode != 0 ? 2 : 1) * (size_t)cols() * HP * 2 + (size_t)stages * WT_BYTES +
            8 * (2 * stages + 18) + 16 + (size_t)npc * NZ * 4;
   }
@@ -531,11 +535,11 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)tc.rows_total};
   cuuint64_t strides[1] = {(cuuint64_t)HP * 2};
-  cuuint32_t box[2] = {16, 128};
+  cuuint32_t box[2] = {(cuuint32_t)W_BOX_K, 128};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(reinterpret_cast<CUtensorMap*>(tc.tmap_bytes), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                       tc.W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                      CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
@@ -564,10 +568,10 @@ cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* 
   const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(tc.tmap_bytes);
   void* args[] = {(void*)map, (void*)&a};
   const int n_tiles = (a.n_nodes + tc.npc - 1) / tc.npc;
-  const bool pair = all_variants()[tc.variant].pair();
-  dim3 grid = pair ? dim3(2 * std::min(n_tiles, std::max(1, tc.n_sm / 2)))
-                   : dim3(std::min(n_tiles, std::max(1, tc.n_sm)));
-  return cudaLaunchKernel(tc.fn, grid, dim3(THREADS), args, tc.smem, ctx->stream);
+  const Variant& v = all_variants()[tc.variant];
+  dim3 grid = v.pair() ? dim3(2 * std::min(n_tiles, std::max(1, tc.n_sm / 2)))
+                       : dim3(std::min(n_tiles, std::max(1, tc.n_sm)));
+  return cudaLaunchKernel(tc.fn, grid, dim3(v.threads()), args, tc.smem, ctx->stream);
 }
 
 int mlp_tc_variant_count() { return (int)all_variants().size(); }

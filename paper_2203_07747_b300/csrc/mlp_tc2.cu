@@ -19,16 +19,30 @@
 // block (hi on rank 0, lo on rank 1) straight into its X and the peer's half
 // into a local staging buffer, and one thread pushes the staged 128-row block
 // to the peer with a single bulk copy that completes on a barrier by byte
-// count.  The epilogue warps therefore never wait on remote stores:
+// count.  The epilogue warps therefore never wait on remote stores.  A copy
+// has read its staging block once its destination barrier completed: the
+// thread that sees that completion frees the producer's staging block
+// (s_free):
 //   * block j odd (rank 1): the copy lands in rank 0's X and completes on
 //     rank 0's xready[j]; the same arrival (release, cluster scope) publishes
-//     rank 1's own half;
+//     rank 1's own half; rank 0's exchange warp sees xready[j] complete and
+//     frees rank 1's staging block;
 //   * block j even (rank 0): the copy lands in rank 1's X and completes on
-//     rank 1's lo_in[j]; rank 1's relay thread forwards it to xready[j].
+//     rank 1's lo_in[j]; rank 1's exchange warp forwards it to xready[j]
+//     and frees rank 0's staging block.
+// The exchange warps (warp 10 of each CTA) wait on nothing the MMA issuer
+// or the epilogue must do first, so a staging block is freed however far the
+// MMA issuer has got (it may itself wait on the epilogue that needs it).
+// The input layer (FP32, 17 inputs) needs no exchange: both CTAs compute
+// every row and keep their own half of the columns; all 16 epilogue warps
+// arrive on rank 0's xin[j].  The notice that the MMAs have read block j
+// (xfree) reaches both CTAs, and every wait on it names its completion by
+// the layer count (one completion per layer).
 // Every wait is bounded (RTN_E_TIMEOUT in the device flag).  After the pair
 // allocates tensor memory it checks that both CTAs received the same address;
 // if not it records RTN_E_UNSUPPORTED and does no work.
 #include <algorithm>
+#include <type_traits>
 
 #include "tc_common.cuh"
 
@@ -68,6 +82,14 @@ __device__ __forceinline__ void arrive_expect_tx_cluster(uint32_t cluster_addr, 
                : "memory");
 }
 
+// the same without ordering earlier stores (announces bytes only)
+__device__ __forceinline__ void arrive_expect_tx_cluster_relaxed(uint32_t cluster_addr, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.relaxed.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(
+                   cluster_addr),
+               "r"(bytes)
+               : "memory");
+}
+
 // shared::cta -> peer shared memory, complete_tx on a barrier of the peer
 __device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst_cl, uint32_t src, uint32_t bytes,
                                                   uint32_t bar_cl) {
@@ -78,11 +100,6 @@ __device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst_cl, uint32_t src,
       : "memory");
 }
 
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t mbar_try_cl(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -143,30 +160,54 @@ __device__ __forceinline__ void cluster_sync() {
                    : "memory");
 }
 
-// one node's row-k results: this CTA's half (hi on rank 0, lo on rank 1) into
-// X, the peer's half into the staging block S (row k % 128)
+// the peer's half of nodes N0..N1-1 for one row, held in registers until
+// the staging block is free (hi halves on rank 1, lo halves on rank 0)
+template <int NPC, int C, int N0, int N1>
+struct PeerHalf {
+  static constexpr int END = N1;
+  uint4 t[N1 - N0][2];
+  uint32_t ve[N1 - N0];  // value (bits 0..15) and 17th tangent (16..31)
+  __device__ __forceinline__ void put(int n, const NodeOut& o, bool lo_local) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      t[n - N0][h] = lo_local ? make_uint4(o.th[4 * h], o.th[4 * h + 1], o.th[4 * h + 2], o.th[4 * h + 3])
+                              : make_uint4(o.tl[4 * h], o.tl[4 * h + 1], o.tl[4 * h + 2], o.tl[4 * h + 3]);
+    ve[n - N0] = lo_local ? ((o.v & 0xffffu) | (o.e << 16)) : ((o.v >> 16) | (o.e & 0xffff0000u));
+  }
+  // row k of the 128-row block into the staging block S
+  __device__ __forceinline__ void flush(uint8_t* S, int k) const {
+    const int ks = k & 127;
+#pragma unroll
+    for (int n = N0; n < N1; ++n) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) *reinterpret_cast<uint4*>(S + xoff<C>(ks, 16 * n + 8 * h)) = t[n - N0][h];
+      *reinterpret_cast<uint16_t*>(S + xoff<C>(ks, 16 * NPC + n)) = (uint16_t)(ve[n - N0] & 0xffffu);
+      *reinterpret_cast<uint16_t*>(S + xoff<C>(ks, 17 * NPC + n)) = (uint16_t)(ve[n - N0] >> 16);
+    }
+  }
+};
+
+// one node's row-k results, this CTA's half only
 template <int NPC, int C>
-__device__ __forceinline__ void node_store_split(uint8_t* X, uint8_t* S, bool lo_local, int k, int n,
-                                                 const NodeOut& o) {
-  const int ks = k & 127;
+__device__ __forceinline__ void node_store_own(uint8_t* X, bool lo_local, int k, int n, const NodeOut& o) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int c = 16 * n + 8 * h;
     const uint4 hv = make_uint4(o.th[4 * h], o.th[4 * h + 1], o.th[4 * h + 2], o.th[4 * h + 3]);
     const uint4 lv = make_uint4(o.tl[4 * h], o.tl[4 * h + 1], o.tl[4 * h + 2], o.tl[4 * h + 3]);
     *reinterpret_cast<uint4*>(X + xoff<C>(k, c)) = lo_local ? lv : hv;
-    *reinterpret_cast<uint4*>(S + xoff<C>(ks, c)) = lo_local ? hv : lv;
   }
-  const uint16_t vh = (uint16_t)(o.v & 0xffffu), vl = (uint16_t)(o.v >> 16);
-  const uint16_t eh = (uint16_t)(o.e & 0xffffu), el = (uint16_t)(o.e >> 16);
-  *reinterpret_cast<uint16_t*>(X + xoff<C>(k, 16 * NPC + n)) = lo_local ? vl : vh;
-  *reinterpret_cast<uint16_t*>(X + xoff<C>(k, 17 * NPC + n)) = lo_local ? el : eh;
-  *reinterpret_cast<uint16_t*>(S + xoff<C>(ks, 16 * NPC + n)) = lo_local ? vh : vl;
-  *reinterpret_cast<uint16_t*>(S + xoff<C>(ks, 17 * NPC + n)) = lo_local ? eh : el;
+  *reinterpret_cast<uint16_t*>(X + xoff<C>(k, 16 * NPC + n)) =
+      lo_local ? (uint16_t)(o.v >> 16) : (uint16_t)(o.v & 0xffffu);
+  *reinterpret_cast<uint16_t*>(X + xoff<C>(k, 17 * NPC + n)) =
+      lo_local ? (uint16_t)(o.e >> 16) : (uint16_t)(o.e & 0xffffu);
 }
 
+// warps 0..9 as in mlp_tc.cu, warp 10: activation exchange
+constexpr int THREADS2 = THREADS + 32;
+
 template <int NPC, int STAGES>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     mlp_tc2_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   constexpr int C = Cols<NPC>::C, TAIL = Cols<NPC>::TAIL, HALF = (NPC + 1) / 2;
   constexpr int NMMA = 2 * C;  // hi columns (rank 0) then lo columns (rank 1)
@@ -200,9 +241,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
   auto xready = [&](int j) { return bar_s + 8u * (2 * STAGES + 2 * MT + j); };
   auto xfree = [&](int j) { return bar_s + 8u * (2 * STAGES + 2 * MT + NB + j); };
   auto lo_in = [&](int j) { return bar_s + 8u * (2 * STAGES + 2 * MT + 2 * NB + j); };
-  const uint32_t s_full = bar_s + 8u * (2 * STAGES + 2 * MT + 3 * NB);
+  auto xin = [&](int j) { return bar_s + 8u * (2 * STAGES + 2 * MT + 3 * NB + j); };
+  const uint32_t s_full = bar_s + 8u * (2 * STAGES + 2 * MT + 4 * NB);
   const uint32_t s_free = s_full + 8u, z_full = s_full + 16u, z_free = s_full + 24u;
-  constexpr int NBAR = 2 * STAGES + 2 * MT + 3 * NB + 4;
+  constexpr int NBAR = 2 * STAGES + 2 * MT + 4 * NB + 4;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail_area + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* zbuf = reinterpret_cast<float*>(tail_area + 8 * NBAR + 16);
@@ -224,6 +266,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       mbar_init(xready(j), (j & 1) ? 1 : 2);
       mbar_init(xfree(j), 1);
       mbar_init(lo_in(j), 1);
+      mbar_init(xin(j), 2 * EPI_WARPS);
     }
     mbar_init(s_full, EPI_WARPS);
     mbar_init(s_free, 1);
@@ -233,7 +276,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero this CTA's X (padding columns stay 0) and S before the peer may copy into X
-  for (uint32_t o = threadIdx.x * 16u; o < xbytes + SBYTES; o += THREADS * 16u)
+  for (uint32_t o = threadIdx.x * 16u; o < xbytes + SBYTES; o += THREADS2 * 16u)
     *reinterpret_cast<uint4*>(sm + o) = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -277,12 +320,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
           for (int m = 0; m < mts && ok; ++m)
             for (int kb = 0; kb < nkb && ok; ++kb) {
               if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
-              if (rank == 0) mbar_expect_tx(full_bar(s), 2 * WT_BYTES);
+              // the output layer's rows 128..255 (rank 1's half) are padding
+              // whose products land in accumulator rows nobody reads: not loaded
+              const bool load = l < nh || rank == 0;
+              if (rank == 0) mbar_expect_tx(full_bar(s), (l < nh ? 2 : 1) * WT_BYTES);
               const int kk = kb ^ 2;  // K order of the MMAs (blocks 1, 0, 3, 2)
+              if (load) {
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks)
-                tma_load_2d_pair(w_s + s * WT_BYTES + ks * 4096u, &tmap, kk * 64 + ks * 16,
-                                 l * HP + m * 256 + (int)rank * 128, full0 + 8u * s);
+                for (int bx = 0; bx < W_BOXES; ++bx)
+                  tma_load_2d_pair(w_s + s * WT_BYTES + bx * 4096u, &tmap, kk * 64 + bx * W_BOX_K,
+                                   l * HP + m * 256 + (int)rank * 128, full0 + 8u * s);
+              }
               if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
         }
@@ -293,24 +341,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       }
     }
   } else if (run && warp == 1) {
-    if (lane == 0 && rank == 1) {
-      // ---------------- relay: rank 0's lo halves have landed here -> rank 0's xready
-      const uint32_t xr0 = mapa(xready(0), 0);
-      uint32_t par = 0;
-      bool ok = true;
-      for (int tile = pair; tile < n_tiles && ok; tile += n_pairs)
-        for (int l = 0; l <= nh && ok; ++l)  // the input layer, then each hidden layer's output
-          for (int j = 0; j < nblk && ok; j += 2) {
-            if (!(ok = mbar_wait_cl(lo_in(j), (par >> j) & 1u, abort_flag, a.err))) break;
-            par ^= 1u << j;
-            arrive_cluster(xr0 + 8u * j);
-          }
-    } else if (lane == 0 && rank == 0) {
+    if (lane == 0 && rank == 0) {
       // ---------------- MMA issuer of the pair
       constexpr uint32_t idesc = idesc_bf16(256, NMMA) | (1u << 16);  // B is N-major
       const uint32_t lbo = C * 16u;
       int s = 0;
-      uint32_t ph = 0, used = 0, tf_par = 0, xr_par = 0;
+      uint32_t ph = 0, used = 0, tf_par = 0, xr_par = 0, xi_par = 0;
       bool ok = true;
       int it = 0;
       WaitClock wc(a.trace != nullptr && blockIdx.x == 0);
@@ -342,11 +378,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
               if (m == 0 && (kb & 1) == 0) {
                 long long w0 = w_x;
                 wc.start();
-                ok = mbar_wait_cl(xready(j), (xr_par >> j) & 1u, abort_flag, a.err);
+                if (l == 0) {  // the input layer's blocks
+                  ok = mbar_wait_cl(xin(j), (xi_par >> j) & 1u, abort_flag, a.err);
+                  xi_par ^= 1u << j;
+                } else {
+                  ok = mbar_wait_cl(xready(j), (xr_par >> j) & 1u, abort_flag, a.err);
+                  xr_par ^= 1u << j;
+                }
                 wc.stop(w_x);
                 ((j & 1) ? w_odd : w_even) += w_x - w0;
                 if (!ok) break;
-                xr_par ^= 1u << j;
                 tc_fence_after();
               }
               wc.start();
@@ -358,12 +399,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t bo = (uint32_t)(kk * 4 + ks) * 2u * lbo;
-                mma2_bf16(d, sdesc(as + ks * 4096u), xdesc(x_s + bo, lbo), idesc, (kb | ks) != 0);
+                mma2_bf16(d, wdesc(as, ks), xdesc(x_s + bo, lbo), idesc, (kb | ks) != 0);
               }
               commit2(empty_bar(s), 3);
               if (++s == STAGES) { s = 0; ph ^= 1u; }
               // the layer's last M tile has read block j: its producer may rewrite it
-              if (m == mts - 1 && (kb & 1)) commit2(xfree(j), (uint16_t)(1u << (j & 1)));
+              if (m == mts - 1 && (kb & 1)) commit2(xfree(j), 3);
             }
             if (ok) commit2(acc_full(slot), 3);
           }
@@ -378,7 +419,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
           }
         }
     }
-  } else if (run) {
+  } else if (run && warp == THREADS / 32) {
+    if (lane == 0) {
+      // ---------------- exchange warp: hidden-layer outputs, blocks in the
+      // order their producers publish them
+      const uint32_t xr0 = mapa(xready(0), 0);
+      const uint32_t sfree_peer = mapa(s_free, rank ^ 1u);
+      uint32_t par = 0;
+      bool ok = true;
+      for (int tile = pair; tile < n_tiles && ok; tile += n_pairs)
+        for (int l = 0; l < nh && ok; ++l)
+          for (int m = 0; m < n_mt2 && ok; ++m) {
+            if (rank == 1) {
+              // rank 0's lo half of block 2m has landed here
+              const int j = 2 * m;
+              if (!(ok = mbar_wait_cl(lo_in(j), (par >> j) & 1u, abort_flag, a.err))) break;
+              par ^= 1u << j;
+              arrive_cluster(xr0 + 8u * j);
+            } else {
+              // rank 1's hi half of block 2m + 1 has landed here
+              const int j = 2 * m + 1;
+              if (!(ok = mbar_wait_cl(xready(j), (par >> j) & 1u, abort_flag, a.err))) break;
+              par ^= 1u << j;
+            }
+            arrive_cluster(sfree_peer);  // the copy has read the peer's staging block
+          }
+    }
+  } else if (run && warp >= 2) {
     // ---------------- epilogue warps (both CTAs)
     const int e = warp - 2;
     const int q = warp & 3;
@@ -386,11 +453,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     const int et = threadIdx.x - 64;
     const bool elected = (e == 0 && lane == 0);  // publishes each block
     float zpref = (et < NZV) ? load_z(a, pair * NPC + et / NZ, et % NZ) : 0.0f;
-    uint32_t acc_par = 0, xf_par = 0, sf_ph = 0, ss_par = 0, zf_par = 0, zr_ph = 0;
-    bool ok = true, first_input = true;
+    uint32_t acc_par = 0, sf_ph = 0, ss_par = 0, zf_par = 0, zr_ph = 0;
+    bool ok = true;
     const bool tr = (rank == 0 && e == 0 && lane == 0);
     const uint32_t tf0 = mapa(tmem_free(0), 0);
-    const uint32_t xr0 = mapa(xready(0), 0), lo1 = mapa(lo_in(0), 1);
+    const uint32_t xr0 = mapa(xready(0), 0), lo1 = mapa(lo_in(0), 1), xi0 = mapa(xin(0), 0);
+    // xfree[j] completes once per MMA layer: completion c (from 1) of this
+    // pair's tile it, layer l is c = n_layers it + l + 1; wait parity (c-1)&1
+    auto xfree_par = [&](int it_, int l) -> uint32_t { return (uint32_t)(n_layers * it_ + l) & 1u; };
     long long epi_wait = 0, t_work = 0, t_sfull = 0, t_copy = 0;
     WaitClock ewc(tr && a.trace != nullptr && blockIdx.x == 0);
 
@@ -402,13 +472,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       return __shfl_sync(0xffffffffu, w_ok, 0) != 0;
     };
 
-    // before block j is written: the MMAs have read its old contents (xfree)
-    // and the previous staging block has been copied out (s_free)
-    auto block_begin = [&](int j, bool wait_xfree) -> bool {
-      if (wait_xfree) {
-        if (!wwait(xfree(j), (xf_par >> j) & 1u)) return false;
-        xf_par ^= 1u << j;
-      }
+    // before the staging block is rewritten: the previous copy has landed
+    auto wait_staging = [&]() -> bool {
       if (!wwait(s_free, sf_ph ^ 1u)) return false;
       sf_ph ^= 1u;
       return true;
@@ -428,36 +493,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         ss_par ^= 1u;
         ewc.start();
         if (p_ok) {
-          if (rank == 0) mbar_arrive(xready(j));
           const uint32_t bar = (rank == 0 ? lo1 : xr0) + 8u * j;
-          arrive_expect_tx_cluster(bar, SBYTES);
 #pragma unroll
-          for (int c = 0; c < 4; ++c)  // four copies in flight
+          for (int c = 0; c < 4; ++c)  // four copies in flight, issued first
             bulk_copy_to_peer(x_rem + (uint32_t)j * SBYTES + c * (SBYTES / 4), s_s + c * (SBYTES / 4),
                               SBYTES / 4, bar);
-          bulk_commit();
-          bulk_wait_read();
-          mbar_arrive(s_free);
+          if (rank == 0) {
+            mbar_arrive(xready(j));                             // own hi half
+            arrive_expect_tx_cluster_relaxed(bar, SBYTES);      // the copy's bytes
+          } else {
+            arrive_expect_tx_cluster(bar, SBYTES);  // the copy's bytes + own lo half
+          }
         }
         ewc.stop(t_copy);
       }
       return __shfl_sync(0xffffffffu, p_ok, 0) != 0;
     };
 
-    // input layer: this CTA writes the blocks j with j % 2 == rank
+    // input layer (FP32): this CTA computes every row and keeps its own
+    // half of the columns; blocks in the order the MMAs read them (1, 0, 3, 2)
     auto input_layer = [&](int tile, int it_) -> bool {
       const int node0 = tile * NPC;
-      // this thread's input-layer rows of both blocks, loaded before the waits
-      float w2[2][NZ], b2[2];
-#pragma unroll
-      for (int jb = 0; jb < 2; ++jb) {
-        const int i = 128 * ((int)rank + 2 * jb) + (et & 127);
-        if (i < HP) {
-#pragma unroll
-          for (int jj = 0; jj < NZ; ++jj) w2[jb][jj] = a.W0[(size_t)i * NZ + jj];
-          b2[jb] = a.b0[i];
-        }
-      }
       if (!wwait(z_free, zr_ph ^ 1u)) return false;  // every warp done with the last z
       zr_ph ^= 1u;
       if (et < NZV) zbuf[et] = zpref;
@@ -467,14 +523,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       zf_par ^= 1u;
       if (tr) trace(a, it_, n_layers, n_layers, 0);
       const int hh = et >> 7;
-#pragma unroll
-      for (int jb = 0; jb < 2; ++jb) {
-        const int j = (int)rank + 2 * jb;
-        if (j >= nblk) break;
-        if (!block_begin(j, !first_input)) return false;
+      for (int jb = 0; jb < nblk; ++jb) {
+        const int j = jb ^ 1;
         const int i = 128 * j + (et & 127);
-        const float* w = w2[jb];
-        const float bi = b2[jb];
+        float w[NZ];
+#pragma unroll
+        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)i * NZ + jj];
+        const float bi = a.b0[i];
+        // the previous tile's output layer has read block j
+        if (it_ > 0 && !wwait(xfree(j), (uint32_t)(n_layers * it_ - 1) & 1u)) return false;
 #pragma unroll
         for (int n = 0; n < NPC; ++n) {
           if ((n < HALF) != (hh == 0)) continue;
@@ -485,13 +542,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
           const float av = real ? tanhf(sacc) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
           NodeOut o;
           node_pack<1>(av, d, w, w[16], o);
-          node_store_split<NPC, C>(X, S, lo_local, i, n, o);
+          node_store_own<NPC, C>(X, lo_local, i, n, o);
         }
-        if (!block_end(j)) return false;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (rank == 0)
+            mbar_arrive(xin(j));
+          else
+            arrive_cluster(xi0 + 8u * j);
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(z_free);
-      first_input = false;
       if (tr) trace(a, it_, n_layers, n_layers, 1);
       return true;
     };
@@ -507,21 +570,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
           if (tr && m == 0) trace(a, it, l, n_layers, 2);
           tc_fence_after();
           const int j = 2 * m + (int)rank;  // the block this CTA's rows produce
-          if (!(ok = block_begin(j, true))) break;
+          // the MMAs of layer l have read block j's old contents
+          if (!(ok = wwait(xfree(j), xfree_par(it, l)))) break;
           ewc.start();
           const int i = 128 * j + 32 * q + lane;
           const float bi = a.bias[(size_t)l * HP + i];
           const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * NMMA);
-          auto store = [&](int n, const NodeOut& o) { node_store_split<NPC, C>(X, S, lo_local, i, n, o); };
-          if (half == 0)
-            epilogue_nodes<NPC, C, 2, 0, HALF>(trow, bi, store);
-          else
-            epilogue_nodes<NPC, C, 2, HALF, NPC>(trow, bi, store);
-          // the accumulator tile is free once its loads completed
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) arrive_cluster_relaxed(tf0 + 8u * m);
+          // own half into X now, the peer's half once the staging block is free
+          auto run_nodes = [&](auto& peer, auto n0) -> bool {
+            auto store = [&](int n, const NodeOut& o) {
+              node_store_own<NPC, C>(X, lo_local, i, n, o);
+              peer.put(n, o, lo_local);
+            };
+            epilogue_nodes<NPC, C, 2, decltype(n0)::value, std::remove_reference_t<decltype(peer)>::END>(
+                trow, bi, store);
+            // the accumulator tile is free once its loads completed
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) arrive_cluster_relaxed(tf0 + 8u * m);
+            if (!wait_staging()) return false;
+            peer.flush(S, i);
+            return true;
+          };
+          if (half == 0) {
+            PeerHalf<NPC, C, 0, HALF> peer;
+            ok = run_nodes(peer, std::integral_constant<int, 0>());
+          } else {
+            PeerHalf<NPC, C, HALF, NPC> peer;
+            ok = run_nodes(peer, std::integral_constant<int, HALF>());
+          }
           ewc.stop(t_work);
+          if (!ok) break;
           if (!(ok = block_end(j))) break;
         }
         if (tr) {
@@ -574,10 +653,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
       __syncwarp();
       if (lane == 0) arrive_cluster_relaxed(tf0 + 8u);
     }
-    // tail: the last output layer's release of this CTA's blocks
-    if (ok && pair < n_tiles)
-      for (int j = (int)rank; j < nblk && ok; j += 2) ok = wwait(xfree(j), (xf_par >> j) & 1u);
-    if (elected) bulk_wait_all();
+    // tail: the last output layer's release of every block (its commit
+    // reaches both CTAs)
+    if (ok && it > 0)
+      for (int j = 0; j < nblk && ok; ++j) ok = wwait(xfree(j), (uint32_t)(n_layers * it - 1) & 1u);
   }
 
   __syncthreads();

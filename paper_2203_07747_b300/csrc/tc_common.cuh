@@ -127,12 +127,24 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// shared-memory matrix descriptor of a weight slab: K-major, 32B swizzle
-// (rows of 16 K values = 32 B, exactly one MMA's K), 8-row groups 256 B apart
-// (stride byte offset), fixed version bits 46..48 = 0b001
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+// Weight stages (128 rows x 64 K, BF16) in shared memory: K-major, one
+// 128B-swizzled TMA box per stage (rows of 64 K = 128 B, 8-row groups 1 KB
+// apart, stage base 1 KB aligned).
+constexpr int W_BOXES = 1;    // TMA boxes per stage
+constexpr int W_BOX_K = 64;   // K extent of a box
+
+// shared-memory matrix descriptor, K-major: start address, leading byte
+// offset 16 (unused when swizzled), stride byte offset between 8-row groups,
+// fixed version bits 46..48 = 0b001, swizzle mode in bits 61..63 (2 = 128B)
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t sbo, uint32_t mode) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)mode << 61);
+}
+
+// A operand of MMA K step ks (16 K) of the stage at `stage`: the K step
+// moves the start address by 32 B inside the 128 B swizzle atom
+__device__ __forceinline__ uint64_t wdesc(uint32_t stage, int ks) {
+  return kmajor_desc(stage + ks * 32u, 1024, 2);
 }
 
 // instruction descriptor, kind::f16: D f32, A = B = bf16, both K-major
