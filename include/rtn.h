@@ -86,7 +86,7 @@ typedef struct {
 
 typedef struct {
   int precision;    /* RTN_FP32 / RTN_BF16 / RTN_BF16X2 */
-  int riccati_f64;  /* 0: FP32 sweep with FP64 Cholesky of R+B'PB; 1: FP64 sweep */
+  int riccati_f64;  /* 0: FP32 sweep (Cholesky of R+B'PB in FP32); 1: FP64 sweep */
   int shift;        /* 1: shift the iterate by one stage after every RTI step */
 } rtn_options;
 

@@ -8,33 +8,78 @@
 //
 // Backward Riccati sweep (sequential over k, parallel over instances):
 //   Huu = R + B'PB, Hux = B'PA, hu = r + B'(p + Pc)
-//   [K | k] = -Huu^{-1} [Hux | hu]            (Cholesky of Huu in FP64)
+//   [K | k] = -Huu^{-1} [Hux | hu]            (Cholesky of Huu)
 //   P <- Q + A'PA + Hux'K (symmetrised),  p <- q + A'(p + Pc) + Hux'k
 // Forward: du_k = K dx_k + k,  dx_{k+1} = A dx_k + B du_k + c.
 // The feedback response then updates the iterate (w += dw), sends
 // u_0 = clamp(u_0 + du_0, 0, u_max) and shifts the iterate by one stage.
 //
-// One warp per instance; the 13x13 / 13x4 / 4x4 blocks live in the warp's
-// shared-memory slot and the lanes share each matrix product element-wise.
-// Instances are visited longest-horizon first so that the ragged tail of a
-// batch with uneven N_b finishes together.
+// One warp per instance, instances visited longest-horizon first so that
+// the ragged tail of a batch with uneven N_b finishes together.  In the
+// backward sweep lane i < 13 keeps row i of P and p_i in registers; the
+// stage matrices and the intermediate products live in the warp's
+// shared-memory slot with rows padded to 16 elements, so that every row a
+// lane needs whole is read with 16-byte broadcast loads.  The Cholesky of
+// Huu (4x4) is computed by one lane and the 14 triangular solves of [K | k]
+// on 14 lanes, all in the sweep precision: Huu is formed in that precision,
+// so a wider factorisation would not change the error's order, and one FP64
+// factorisation per node costs more than the rest of the FP32 sweep on this
+// part's FP64 pipe.  The FP64 sweep (rtn_options.riccati_f64) is the wide path.
 #include "rtn_internal.cuh"
 
 namespace rtn {
 namespace {
 
 template <typename T>
-struct Slot {
-  T A[NX * NX], Bm[NX * NU], c[NX];
-  T P[NX * NX], p[NX];
-  T PA[NX * NX], PB[NX * NU], g[NX];
-  T Huu[NU * NU], Hux[NU * NX], hu[NU];
-  T K[NU * NX], k[NU];
-  T P2[NX * NX], p2[NX];
-  T dx[NX], du[NU];
-  double L[NU * NU], Linv[NU];  // FP64 Cholesky factor (strict lower part) and 1/diag
+struct __align__(16) Slot {
+  T A[NX][16];    // A_k
+  T PA[NX][16];   // P A
+  T P2[NX][16];   // next P before symmetrisation
+  T Hux[NU][16];  // B'PA
+  T K[NU][16];    // feedback gains
+  T Bm[NX][NU], PB[NX][NU];
+  T c[16], g[16];  // c_k, p + P c
+  T Huu[NU * NU], hu[NU], k[NU];
+  T Lt[NU * NU], Linvt[NU];  // Cholesky factor of Huu (strict lower part) and 1/diag
+  T dx[16], du[NU];
   int notpd;
 };
+
+// 16 consecutive elements of a padded shared-memory row into registers
+template <typename T>
+__device__ __forceinline__ void row16(const T* src, T (&v)[16]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = s4[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double2 t = s2[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void row4(const T* src, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(src);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    const double2 a = s2[0], b = s2[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
 
 struct KArgs {
   QpArgs a;
@@ -71,87 +116,111 @@ __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
   float x0m = lane < NX ? a.x0[(size_t)b * NX + lane] : 0.0f;
   const bool finite = __all_sync(0xffffffffu, isfinite(x0m));
 
-  for (int e = lane; e < NX * NX; e += 32) {
-    int i = e / NX, j = e % NX;
-    S.P[e] = (i == j) ? (T)C.QN[i] : (T)0;
-  }
-  if (lane < NX)
-    S.p[lane] = (T)C.QN[lane] * ((T)x[(size_t)N * NX + lane] - (T)xr[(size_t)N * NX + lane]);
+  // P, p of the cost-to-go: row `lane` in registers (lanes 0..12)
+  T Prow[NX], p_i = 0;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) Prow[j] = (lane < NX && j == lane) ? (T)C.QN[lane] : (T)0;
+  if (lane < NX) p_i = (T)C.QN[lane] * ((T)x[(size_t)N * NX + lane] - (T)xr[(size_t)N * NX + lane]);
   if (lane == 0) S.notpd = 0;
   __syncwarp();
 
+  // stage data of node k (A 169, B 52, c 13 floats) as 8 registers per lane,
+  // loaded one node ahead so that the global-memory latency overlaps the
+  // previous node's arithmetic
+  constexpr int NSTAGE = NX * NX + NX * NU + NX;
+  float pf[8];
+  auto prefetch = [&](int k) {
+    const size_t node = (size_t)uo + k;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = lane + 32 * q;
+      float v = 0.0f;
+      if (e < NX * NX) v = a.A[node * NX * NX + e];
+      else if (e < NX * NX + NX * NU) v = a.Bm[node * NX * NU + (e - NX * NX)];
+      else if (e < NSTAGE) v = a.c[node * NX + (e - NX * NX - NX * NU)];
+      pf[q] = v;
+    }
+  };
+  if (finite && N > 0) prefetch(N - 1);
+
   for (int k = N - 1; k >= 0 && finite; --k) {
     const size_t node = (size_t)uo + k;
-    const float* Ak = a.A + node * NX * NX;
-    const float* Bk = a.Bm + node * NX * NU;
-    const float* ck = a.c + node * NX;
-    for (int e = lane; e < NX * NX; e += 32) S.A[e] = (T)Ak[e];
-    for (int e = lane; e < NX * NU; e += 32) S.Bm[e] = (T)Bk[e];
-    if (lane < NX) S.c[lane] = (T)ck[lane];
-    __syncwarp();
-    // PA = P A, PB = P B, g = p + P c
-    for (int e = lane; e < NX * NX + NX * NU + NX; e += 32) {
-      if (e < NX * NX) {
-        int i = e / NX, j = e % NX;
-        T s = 0;
 #pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.P[i * NX + l] * S.A[l * NX + j];
-        S.PA[e] = s;
-      } else if (e < NX * NX + NX * NU) {
-        int f = e - NX * NX, i = f / NU, j = f % NU;
-        T s = 0;
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.P[i * NX + l] * S.Bm[l * NU + j];
-        S.PB[f] = s;
-      } else {
-        int i = e - NX * NX - NX * NU;
-        T s = S.p[i];
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.P[i * NX + l] * S.c[l];
-        S.g[i] = s;
-      }
+    for (int q = 0; q < 8; ++q) {
+      const int e = lane + 32 * q;
+      if (e < NX * NX) S.A[e / NX][e % NX] = (T)pf[q];
+      else if (e < NX * NX + NX * NU) S.Bm[(e - NX * NX) / NU][(e - NX * NX) % NU] = (T)pf[q];
+      else if (e < NSTAGE) S.c[e - NX * NX - NX * NU] = (T)pf[q];
     }
     __syncwarp();
-    // Huu = R + B'PB, Hux = B'PA, hu = r + B'g
-    for (int e = lane; e < NU * NU + NU * NX + NU; e += 32) {
-      if (e < NU * NU) {
-        int i = e / NU, j = e % NU;
-        T s = (i == j) ? (T)C.R[i] : (T)0;
+    if (k > 0) prefetch(k - 1);
+    // PA = P A, PB = P B, g = p + P c: lane i forms row i
+    if (lane < NX) {
+      T pa[16], pb[NU], gi = p_i;
 #pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.Bm[l * NU + i] * S.PB[l * NU + j];
+      for (int j = 0; j < 16; ++j) pa[j] = 0;
+#pragma unroll
+      for (int m = 0; m < NU; ++m) pb[m] = 0;
+#pragma unroll
+      for (int l = 0; l < NX; ++l) {
+        T ar[16], br[4];
+        row16(&S.A[l][0], ar);
+        row4(&S.Bm[l][0], br);
+        const T pl = Prow[l];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) pa[j] += pl * ar[j];
+#pragma unroll
+        for (int m = 0; m < NU; ++m) pb[m] += pl * br[m];
+        gi += pl * S.c[l];
+      }
+#pragma unroll
+      for (int j = 0; j < NX; ++j) S.PA[lane][j] = pa[j];
+#pragma unroll
+      for (int m = 0; m < NU; ++m) S.PB[lane][m] = pb[m];
+      S.g[lane] = gi;
+    }
+    __syncwarp();
+    // Hux = B'PA (52), Huu = R + B'PB (16), hu = r + B'g (4) over the warp
+    for (int o = lane; o < NU * NX + NU * NU + NU; o += 32) {
+      T s = 0;
+      if (o < NU * NX) {
+        const int m = o / NX, j = o % NX;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.PA[l][j];
+        S.Hux[m][j] = s;
+      } else if (o < NU * NX + NU * NU) {
+        const int e = o - NU * NX, m = e / NU, n = e % NU;
+        s = (m == n) ? (T)C.R[m] : (T)0;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.PB[l][n];
         S.Huu[e] = s;
-      } else if (e < NU * NU + NU * NX) {
-        int f = e - NU * NU, i = f / NX, j = f % NX;
-        T s = 0;
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.Bm[l * NU + i] * S.PA[l * NX + j];
-        S.Hux[f] = s;
       } else {
-        int i = e - NU * NU - NU * NX;
-        T s = (T)C.R[i] * ((T)u[(size_t)k * NU + i] - (T)ur[(size_t)k * NU + i]);
+        const int m = o - NU * NX - NU * NU;
+        s = (T)C.R[m] * ((T)u[(size_t)k * NU + m] - (T)ur[(size_t)k * NU + m]);
 #pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.Bm[l * NU + i] * S.g[l];
-        S.hu[i] = s;
+        for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.g[l];
+        S.hu[m] = s;
       }
     }
     __syncwarp();
-    // FP64 Cholesky of Huu by one lane (4 square roots, 4 reciprocals), then
-    // the 14 right-hand sides (13 of Hux, 1 of hu) on 14 lanes with products
+    // Cholesky of Huu by one lane (one reciprocal square root per pivot)
     if (lane == 0) {
-      double L[NU][NU];
+      T L[NU][NU];
       bool pd = true;
 #pragma unroll
       for (int j = 0; j < NU; ++j) {
-        double s = (double)S.Huu[j * NU + j];
+        T s = S.Huu[j * NU + j];
 #pragma unroll
         for (int q = 0; q < j; ++q) s -= L[j][q] * L[j][q];
-        pd &= (s > 0.0);
-        const double d = sqrt(fmax(s, 1e-300)), inv = 1.0 / d;
-        L[j][j] = d;
-        S.Linv[j] = inv;
+        pd &= (s > (T)0);
+        T inv;
+        if constexpr (sizeof(T) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
+        else inv = rsqrt(fmax(s, 1e-300));
+        L[j][j] = s * inv;
+        S.Linvt[j] = (T)inv;
 #pragma unroll
         for (int i = j + 1; i < NU; ++i) {
-          double v = (double)S.Huu[i * NU + j];
+          T v = S.Huu[i * NU + j];
 #pragma unroll
           for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
           L[i][j] = v * inv;
@@ -160,65 +229,70 @@ __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
 #pragma unroll
       for (int i = 0; i < NU; ++i)
 #pragma unroll
-        for (int j = 0; j < NU; ++j) S.L[i * NU + j] = (j < i) ? L[i][j] : 0.0;
+        for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (T)0;
       if (!pd) S.notpd = 1;
     }
     __syncwarp();
+    // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `lane` (13 = hu)
     if (lane < NX + 1) {
-      double y[NU];
+      T y[NU];
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
-        double v = (lane < NX) ? (double)S.Hux[i * NX + lane] : (double)S.hu[i];
+        T v = (lane < NX) ? S.Hux[i][lane] : S.hu[i];
 #pragma unroll
-        for (int q = 0; q < i; ++q) v -= S.L[i * NU + q] * y[q];
-        y[i] = v * S.Linv[i];
+        for (int q = 0; q < i; ++q) v -= S.Lt[i * NU + q] * y[q];
+        y[i] = v * S.Linvt[i];
       }
 #pragma unroll
       for (int i = NU - 1; i >= 0; --i) {
-        double v = y[i];
+        T v = y[i];
 #pragma unroll
-        for (int q = i + 1; q < NU; ++q) v -= S.L[q * NU + i] * y[q];
-        y[i] = v * S.Linv[i];
+        for (int q = i + 1; q < NU; ++q) v -= S.Lt[q * NU + i] * y[q];
+        y[i] = v * S.Linvt[i];
       }
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
-        if (lane < NX) S.K[i * NX + lane] = (T)(-y[i]);
-        else S.k[i] = (T)(-y[i]);
+        if (lane < NX) S.K[i][lane] = -y[i];
+        else S.k[i] = -y[i];
       }
     }
     __syncwarp();
-    // P2 = Q + A'PA + Hux'K,  p2 = q + A'g + Hux'k ; store the gains
-    for (int e = lane; e < NX * NX + NX; e += 32) {
-      if (e < NX * NX) {
-        int i = e / NX, j = e % NX;
-        T s = (i == j) ? (T)C.Q[i] : (T)0;
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.A[l * NX + i] * S.PA[l * NX + j];
-#pragma unroll
-        for (int l = 0; l < NU; ++l) s += S.Hux[l * NX + i] * S.K[l * NX + j];
-        S.P2[e] = s;
-      } else {
-        int i = e - NX * NX;
-        T s = (T)C.Q[i] * ((T)x[(size_t)k * NX + i] - (T)xr[(size_t)k * NX + i]);
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.A[l * NX + i] * S.g[l];
-#pragma unroll
-        for (int l = 0; l < NU; ++l) s += S.Hux[l * NX + i] * S.k[l];
-        S.p2[i] = s;
-      }
-    }
     for (int e = lane; e < NU * NX + NU; e += 32) {
-      if (e < NU * NX) Kg[node * NU * NX + e] = S.K[e];
+      if (e < NU * NX) Kg[node * NU * NX + e] = S.K[e / NX][e % NX];
       else kg[node * NU + (e - NU * NX)] = S.k[e - NU * NX];
     }
-    __syncwarp();
-    for (int e = lane; e < NX * NX + NX; e += 32) {
-      if (e < NX * NX) {
-        int i = e / NX, j = e % NX;
-        S.P[e] = (T)0.5 * (S.P2[i * NX + j] + S.P2[j * NX + i]);
-      } else {
-        S.p[e - NX * NX] = S.p2[e - NX * NX];
+    // P2 = Q + A'PA + Hux'K (row i on lane i), p2 = q + A'g + Hux'k
+    T P2row[16], p2 = 0;
+    if (lane < NX) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) P2row[j] = (j == lane) ? (T)C.Q[lane] : (T)0;
+      p2 = (T)C.Q[lane] * ((T)x[(size_t)k * NX + lane] - (T)xr[(size_t)k * NX + lane]);
+#pragma unroll
+      for (int l = 0; l < NX; ++l) {
+        T pr[16];
+        row16(&S.PA[l][0], pr);
+        const T al = S.A[l][lane];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) P2row[j] += al * pr[j];
+        p2 += al * S.g[l];
       }
+#pragma unroll
+      for (int m = 0; m < NU; ++m) {
+        T kr[16];
+        row16(&S.K[m][0], kr);
+        const T hm = S.Hux[m][lane];
+#pragma unroll
+        for (int j = 0; j < NX; ++j) P2row[j] += hm * kr[j];
+        p2 += hm * S.k[m];
+      }
+#pragma unroll
+      for (int j = 0; j < NX; ++j) S.P2[lane][j] = P2row[j];
+    }
+    __syncwarp();
+    if (lane < NX) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) Prow[j] = (T)0.5 * (P2row[j] + S.P2[j][lane]);
+      p_i = p2;
     }
     __syncwarp();
   }
@@ -244,24 +318,50 @@ __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
   __syncwarp();
   if (a.dx && lane < NX) a.dx[(size_t)xo * NX + lane] = (float)S.dx[lane];
   if (a.update && !a.shift && lane < NX) xw[lane] = (float)((T)x[lane] + S.dx[lane]);
+  // per node: lane m < 4 needs its row of K and k; lane i < 13 its rows of
+  // A and B and c_i; loaded one node ahead
+  float fa[NX], fb[NU], fc = 0.0f;
+  T fk[NX], fkk = 0;
+  auto fetch = [&](int k) {
+    const size_t node = (size_t)uo + k;
+    if (lane < NX) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) fa[j] = a.A[node * NX * NX + lane * NX + j];
+#pragma unroll
+      for (int j = 0; j < NU; ++j) fb[j] = a.Bm[node * NX * NU + lane * NU + j];
+      fc = a.c[node * NX + lane];
+    }
+    if (lane < NU) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) fk[j] = Kg[node * NU * NX + lane * NX + j];
+      fkk = kg[node * NU + lane];
+    }
+  };
+  fetch(0);
   for (int k = 0; k < N; ++k) {
     const size_t node = (size_t)uo + k;
-    if (lane < NU) {
-      T s = kg[node * NU + lane];
+    float ca[NX], cb[NU];
+    T ck[NX], ckk = fkk;
+    const float cc = fc;
 #pragma unroll
-      for (int j = 0; j < NX; ++j) s += Kg[node * NU * NX + lane * NX + j] * S.dx[j];
+    for (int j = 0; j < NX; ++j) { ca[j] = fa[j]; ck[j] = fk[j]; }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) cb[j] = fb[j];
+    if (k + 1 < N) fetch(k + 1);
+    if (lane < NU) {
+      T s = ckk;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) s += ck[j] * S.dx[j];
       S.du[lane] = s;
     }
     __syncwarp();
     T dxn = 0;
     if (lane < NX) {
-      const float* Ak = a.A + node * NX * NX + lane * NX;
-      const float* Bk = a.Bm + node * NX * NU + lane * NU;
-      T s = (T)a.c[node * NX + lane];
+      T s = (T)cc;
 #pragma unroll
-      for (int j = 0; j < NX; ++j) s += (T)Ak[j] * S.dx[j];
+      for (int j = 0; j < NX; ++j) s += (T)ca[j] * S.dx[j];
 #pragma unroll
-      for (int j = 0; j < NU; ++j) s += (T)Bk[j] * S.du[j];
+      for (int j = 0; j < NU; ++j) s += (T)cb[j] * S.du[j];
       dxn = s;
     }
     if (lane < NU) {

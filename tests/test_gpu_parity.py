@@ -6,7 +6,7 @@ Tolerances (per node, relative Frobenius norm against the oracle):
   FP64 steps: plant integration + quaternion renormalisation 1e-9; the FP64
   Riccati sweep writes FP32 outputs, so it must equal the oracle's result
   rounded to FP32 (relative 2^-23 per element).
-The FP32 Riccati sweep (FP64 Cholesky) is held to the same 1e-5 relative
+The FP32 Riccati sweep is held to the same 1e-5 relative
 bar on the QP step (measured about 3e-6 at N <= 22)."""
 import numpy as np
 import pytest

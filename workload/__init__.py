@@ -189,7 +189,7 @@ def make_problem(name, seed=0, B=None, bf16=False):
     refp = circle_params(Bn, seed) if cfg["ref"] == "circle" else figure8_params(Bn, seed)
     return dict(name=name, B=Bn, N=N, dt=dt, layers=layers, widths=cfg["widths"], x0=x0,
                 ref=refp, Q=Q_DIAG.copy(), R=R_DIAG.copy(), QN=Q_DIAG.copy(), quad=dict(QUAD),
-                cfg=cfg)
+                cfg=cfg, seed=seed, bf16=bf16)
 
 
 def node_refs(prob, t0=0.0):
