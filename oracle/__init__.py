@@ -191,6 +191,18 @@ def riccati(A, B, c, x, u, xr, ur, Q, R, QN, x0m, nx=NX, nu=NU, return_gains=Fal
     return st, dx, du
 
 
+def box_qp(A, B, c, x, u, xr, ur, Q, R, QN, x0m, lb, ub, max_iter=20, nx=NX, nu=NU):
+    """The QP with lb <= du <= ub (primal-dual active set on the Riccati
+    structure).  Returns (status, dx, du, iterations)."""
+    N = A.shape[0]
+    args = [_d(a) for a in (A, B, c, x, u, xr, ur, Q, R, QN, x0m, lb, ub)]
+    dx = np.zeros((N + 1, nx)); du = np.zeros((N, nu))
+    it = C.c_int(0)
+    st = lib().orc_box_qp(nx, nu, N, *[a[1] for a in args], int(max_iter), _p(dx), _p(du),
+                          C.byref(it))
+    return st, dx, du, it.value
+
+
 def kkt_dense(A, B, c, x, u, xr, ur, Q, R, QN, x0m, nx=NX, nu=NU):
     N = A.shape[0]
     args = [_d(a) for a in (A, B, c, x, u, xr, ur, Q, R, QN, x0m)]
@@ -229,7 +241,26 @@ def rti_step(quad, layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=True):
     return u0, x, u, st
 
 
-def closed_loop(quad, layers, plant_kind, plant_layers, N, dt, Q, R, QN, x0, xrt, urt, steps):
+def rti_step_box(quad, layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=True, max_iter=20):
+    """RTI step with the thrust bounds in the QP.  Returns (u0, x_new, u_new,
+    status [B], iterations [B])."""
+    m = _MLP(layers or [])
+    N, pN = _i(N); dt, pdt = _d(dt)
+    x = np.array(x, dtype=np.float64, copy=True); u = np.array(u, dtype=np.float64, copy=True)
+    args = [_d(a) for a in (Q, R, QN)]
+    xref, pxr = _d(xref); uref, pur = _d(uref); x0m, px0 = _d(x0m)
+    Bn = len(N)
+    u0 = np.zeros((Bn, NU)); st = np.zeros(Bn, np.int32); its = np.zeros(Bn, np.int32)
+    q = _quad(quad)
+    ip = C.POINTER(C.c_int)
+    lib().orc_rti_step_box(C.byref(q), m.nl, m.pw, m.pp, Bn, pN, pdt, args[0][1], args[1][1],
+                           args[2][1], _p(x), _p(u), pxr, pur, px0, int(shift), int(max_iter),
+                           _p(u0), st.ctypes.data_as(ip), its.ctypes.data_as(ip))
+    return u0, x, u, st, its
+
+
+def closed_loop(quad, layers, plant_kind, plant_layers, N, dt, Q, R, QN, x0, xrt, urt, steps,
+                box=False, max_iter=20):
     """Returns traj [steps][B][13] and u0 history [steps][B][4]."""
     m = _MLP(layers or [])
     pm = _MLP(plant_layers or [])
@@ -238,8 +269,13 @@ def closed_loop(quad, layers, plant_kind, plant_layers, N, dt, Q, R, QN, x0, xrt
     Bn, T = xrt.shape[0], xrt.shape[1]
     traj = np.zeros((steps, Bn, NX)); uh = np.zeros((steps, Bn, NU))
     q = _quad(quad)
-    lib().orc_closed_loop(C.byref(q), m.nl, m.pw, m.pp, plant_kind, pm.nl, pm.pw, pm.pp, Bn, pN,
-                          pdt, *[a[1] for a in args], T, steps, _p(traj), _p(uh))
+    if box:
+        lib().orc_closed_loop_box(C.byref(q), m.nl, m.pw, m.pp, plant_kind, pm.nl, pm.pw, pm.pp, Bn,
+                                  pN, pdt, *[a[1] for a in args], T, steps, int(max_iter),
+                                  _p(traj), _p(uh))
+    else:
+        lib().orc_closed_loop(C.byref(q), m.nl, m.pw, m.pp, plant_kind, pm.nl, pm.pw, pm.pp, Bn, pN,
+                              pdt, *[a[1] for a in args], T, steps, _p(traj), _p(uh))
     return traj, uh
 
 

@@ -17,7 +17,9 @@
  *     local model of Eq. 4, with the sensitivities A_k, B_k of the continuity
  *     condition (Eq. 2) obtained by propagating d(stage)/d[x;u].
  *   - The QP of Sec. III-A with the quadratic tracking cost of Sec. V, solved
- *     by the textbook Riccati recursion, plus a dense KKT solve used as a pin.
+ *     by the textbook Riccati recursion, plus a dense KKT solve used as a pin;
+ *     with the thrust bounds of Sec. V, by a primal-dual active-set method
+ *     whose subproblems are masked Riccati recursions.
  *   - One RTI step (Sec. III-B): linearise, solve, update the iterate, shift.
  *   - Plant step, closed loop, drag residual, and MLP training (MSE + Adam,
  *     Sec. VI).
@@ -410,10 +412,17 @@ static void chol_solve(int n, const double* L, int ncol, double* Bm) {
  * Generic sizes nx, nu so that a scalar special case can be checked.
  * Q, R, QN are diagonal (vectors).  Returns 0 on success, 4 if not PD.
  */
-int orc_riccati(int nx, int nu, int N, const double* A, const double* Bm, const double* c,
-                const double* x, const double* u, const double* xr, const double* ur,
-                const double* Q, const double* R, const double* QN, const double* x0m,
-                double* dx, double* du, double* Kout, double* kout) {
+/* Core of the recursion.  With fixed != NULL, input i of node k is held at
+ * du_k[i] = aval[k*nu+i] wherever fixed[k*nu+i] != 0 and the others are
+ * optimised (an equality-constrained LQ subproblem of the box-constrained QP
+ * below): at each node the free inputs solve Huu_ff du_f = -(hu_f + Huu_fA a)
+ * - Hux_f dx, the fixed rows of K are zero and of k the held values, and the
+ * cost-to-go update uses the full Hux.  gam (optional) receives diag(Huu). */
+static int riccati_core(int nx, int nu, int N, const double* A, const double* Bm, const double* c,
+                        const double* x, const double* u, const double* xr, const double* ur,
+                        const double* Q, const double* R, const double* QN, const double* x0m,
+                        const int* fixed, const double* aval, double* dx, double* du,
+                        double* Kout, double* kout, double* gam) {
   int ok = 1;
   double* P = (double*)calloc(nx * nx, sizeof(double));
   double* p = (double*)calloc(nx, sizeof(double));
@@ -467,12 +476,29 @@ int orc_riccati(int nx, int nu, int N, const double* A, const double* Bm, const 
       for (int l = 0; l < nx; ++l) s += Bk[l * nu + i] * g[l];
       hu[i] = s;
     }
-    if (!chol(nu, Huu, Lc)) { ok = 0; break; }
-    /* [K | k] = -Huu^{-1} [Hux | hu] */
+    if (gam)
+      for (int i = 0; i < nu; ++i) gam[(size_t)k * nu + i] = Huu[i * nu + i];
+    /* [K | k] = -Huu^{-1} [Hux | hu]  (fixed inputs: identity rows/columns,
+     * zero rows of Hux, right-hand side -a; coupling moved to the free rows) */
     for (int i = 0; i < nu; ++i) {
-      for (int j = 0; j < nx; ++j) rhs[i * (nx + 1) + j] = Hux[i * nx + j];
-      rhs[i * (nx + 1) + nx] = hu[i];
+      const int fi = fixed && fixed[(size_t)k * nu + i];
+      for (int j = 0; j < nx; ++j) rhs[i * (nx + 1) + j] = fi ? 0.0 : Hux[i * nx + j];
+      double h = hu[i];
+      if (fi) {
+        h = -aval[(size_t)k * nu + i];
+      } else if (fixed) {
+        for (int m = 0; m < nu; ++m)
+          if (fixed[(size_t)k * nu + m]) h += Huu[i * nu + m] * aval[(size_t)k * nu + m];
+      }
+      rhs[i * (nx + 1) + nx] = h;
     }
+    if (fixed) {
+      for (int i = 0; i < nu; ++i)
+        for (int m = 0; m < nu; ++m)
+          if (fixed[(size_t)k * nu + i] || fixed[(size_t)k * nu + m])
+            Huu[i * nu + m] = (i == m) ? 1.0 : 0.0;
+    }
+    if (!chol(nu, Huu, Lc)) { ok = 0; break; }
     chol_solve(nu, Lc, nx + 1, rhs);
     double* Kk = K + (size_t)k * nu * nx;
     double* kk = kf + (size_t)k * nu;
@@ -526,6 +552,120 @@ int orc_riccati(int nx, int nu, int N, const double* A, const double* Bm, const 
   free(P); free(p); free(K); free(kf); free(PA); free(PB); free(Huu); free(Hux); free(Lc);
   free(g); free(hu); free(P2); free(p2); free(rhs);
   return ok ? 0 : 4;
+}
+
+int orc_riccati(int nx, int nu, int N, const double* A, const double* Bm, const double* c,
+                const double* x, const double* u, const double* xr, const double* ur,
+                const double* Q, const double* R, const double* QN, const double* x0m,
+                double* dx, double* du, double* Kout, double* kout) {
+  return riccati_core(nx, nu, N, A, Bm, c, x, u, xr, ur, Q, R, QN, x0m, NULL, NULL, dx, du, Kout,
+                      kout, NULL);
+}
+
+/* Gradient of the QP's cost with respect to every du_k along a trajectory
+ * (dx, du) that satisfies the dynamics, by the adjoint recursion:
+ *   lam_N = QN (x_N + dx_N - xr_N),
+ *   G_k = R (u_k + du_k - ur_k) + B_k' lam_{k+1},
+ *   lam_k = Q (x_k + dx_k - xr_k) + A_k' lam_{k+1}. */
+static void qp_gradient(int nx, int nu, int N, const double* A, const double* Bm, const double* x,
+                        const double* u, const double* xr, const double* ur, const double* Q,
+                        const double* R, const double* QN, const double* dx, const double* du,
+                        double* G) {
+  double* lam = (double*)malloc(sizeof(double) * nx);
+  double* l2 = (double*)malloc(sizeof(double) * nx);
+  for (int i = 0; i < nx; ++i)
+    lam[i] = QN[i] * (x[(size_t)N * nx + i] + dx[(size_t)N * nx + i] - xr[(size_t)N * nx + i]);
+  for (int k = N - 1; k >= 0; --k) {
+    const double* Ak = A + (size_t)k * nx * nx;
+    const double* Bk = Bm + (size_t)k * nx * nu;
+    for (int i = 0; i < nu; ++i) {
+      double s = R[i] * (u[(size_t)k * nu + i] + du[(size_t)k * nu + i] - ur[(size_t)k * nu + i]);
+      for (int l = 0; l < nx; ++l) s += Bk[l * nu + i] * lam[l];
+      G[(size_t)k * nu + i] = s;
+    }
+    for (int i = 0; i < nx; ++i) {
+      double s = Q[i] * (x[(size_t)k * nx + i] + dx[(size_t)k * nx + i] - xr[(size_t)k * nx + i]);
+      for (int l = 0; l < nx; ++l) s += Ak[l * nx + i] * lam[l];
+      l2[i] = s;
+    }
+    memcpy(lam, l2, sizeof(double) * nx);
+  }
+  free(lam); free(l2);
+}
+
+/*
+ * The same QP with box constraints on the inputs, lb_k <= du_k <= ub_k (the
+ * thrust bounds 0 <= u_k + du_k <= u_max of Sec. V), by a primal-dual active
+ * set method on the Riccati structure:
+ *   1. solve without bounds; if feasible, that is the solution;
+ *   2. otherwise, with G the gradient of the cost at the current solution and
+ *      gamma = diag(Huu) per node, the new active sets are
+ *        lower = {du - G/gamma < lb},  upper = {du - G/gamma > ub};
+ *      hold those inputs at their bounds and solve the equality-constrained
+ *      subproblem (riccati_core with a mask); repeat until the sets repeat,
+ *      which is then a KKT point: free inputs inside the box with zero
+ *      gradient, held inputs with multipliers of the right sign.
+ * At most max_iter subproblems are solved.  Returns 0 on convergence, 4 if a
+ * Huu is not positive definite, 8 if the sets did not settle within max_iter
+ * (then du is the last solution clamped to the box and dx its roll-out).
+ * *iters receives the number of subproblems solved.
+ */
+int orc_box_qp(int nx, int nu, int N, const double* A, const double* Bm, const double* c,
+               const double* x, const double* u, const double* xr, const double* ur,
+               const double* Q, const double* R, const double* QN, const double* x0m,
+               const double* lb, const double* ub, int max_iter, double* dx, double* du,
+               int* iters) {
+  const size_t n = (size_t)N * nu;
+  int* fixed = (int*)calloc(n, sizeof(int));
+  int* nfix = (int*)calloc(n, sizeof(int));
+  double* aval = (double*)calloc(n, sizeof(double));
+  double* gam = (double*)malloc(sizeof(double) * n);
+  double* G = (double*)malloc(sizeof(double) * n);
+  int st = riccati_core(nx, nu, N, A, Bm, c, x, u, xr, ur, Q, R, QN, x0m, NULL, NULL, dx, du, NULL,
+                        NULL, gam);
+  int it = 1, done = 0;
+  if (st == 0) {
+    done = 1;
+    for (size_t i = 0; i < n; ++i)
+      if (du[i] < lb[i] || du[i] > ub[i]) done = 0;
+  }
+  while (st == 0 && !done) {
+    qp_gradient(nx, nu, N, A, Bm, x, u, xr, ur, Q, R, QN, dx, du, G);
+    int changed = 0;
+    for (size_t i = 0; i < n; ++i) {
+      const double v = du[i] - G[i] / gam[i];
+      nfix[i] = v < lb[i] ? -1 : (v > ub[i] ? 1 : 0);
+      if (nfix[i] != fixed[i]) changed = 1;
+    }
+    if (!changed && it > 1) { done = 1; break; }
+    if (it >= max_iter) {
+      /* not settled: the last solution clamped to the box, rolled out */
+      for (size_t i = 0; i < n; ++i) du[i] = du[i] < lb[i] ? lb[i] : (du[i] > ub[i] ? ub[i] : du[i]);
+      for (int i = 0; i < nx; ++i) dx[i] = x0m[i] - x[i];
+      for (int k = 0; k < N; ++k) {
+        const double* Ak = A + (size_t)k * nx * nx;
+        const double* Bk = Bm + (size_t)k * nx * nu;
+        for (int i = 0; i < nx; ++i) {
+          double s = c[(size_t)k * nx + i];
+          for (int j = 0; j < nx; ++j) s += Ak[i * nx + j] * dx[(size_t)k * nx + j];
+          for (int j = 0; j < nu; ++j) s += Bk[i * nu + j] * du[(size_t)k * nu + j];
+          dx[(size_t)(k + 1) * nx + i] = s;
+        }
+      }
+      st = 8;
+      break;
+    }
+    for (size_t i = 0; i < n; ++i) {
+      fixed[i] = nfix[i];
+      aval[i] = nfix[i] < 0 ? lb[i] : (nfix[i] > 0 ? ub[i] : 0.0);
+    }
+    st = riccati_core(nx, nu, N, A, Bm, c, x, u, xr, ur, Q, R, QN, x0m, fixed, aval, dx, du, NULL,
+                      NULL, gam);
+    ++it;
+  }
+  if (iters) *iters = it;
+  free(fixed); free(nfix); free(aval); free(gam); free(G);
+  return st;
 }
 
 /* dense KKT solve of the same QP (LU with partial pivoting), used only as an
@@ -647,11 +787,15 @@ void orc_linearize(const orc_quad* Qd, int nl, const int* w, const double* P, in
  * the iterate, solve the QP with the measured x0, update the iterate
  * (w += dw), send u_0 clamped to [0, u_max], then optionally shift the
  * iterate by one stage (last entries repeated).  x, u are updated in place.
- * status[b] = 0 ok, 4 not positive definite (iterate untouched, u0 = uref). */
-void orc_rti_step(const orc_quad* Qd, int nl, const int* w, const double* P, int B, const int* N,
-                  const double* dt, const double* Q, const double* R, const double* QN, double* x,
-                  double* u, const double* xref, const double* uref, const double* x0m,
-                  int shift, double* u0, int* status) {
+ * status[b] = 0 ok, 4 not positive definite (iterate untouched, u0 = uref).
+ * With box != 0 the QP carries the thrust bounds 0 <= u_k + du_k <= u_max
+ * (orc_box_qp, at most max_iter subproblems; status 8 if the active sets did
+ * not settle, the clamped step is applied); iters[b] receives the number of
+ * subproblems solved. */
+static void rti_core(const orc_quad* Qd, int nl, const int* w, const double* P, int B, const int* N,
+                     const double* dt, const double* Q, const double* R, const double* QN, double* x,
+                     double* u, const double* xref, const double* uref, const double* x0m,
+                     int shift, double* u0, int* status, int box, int max_iter, int* iters) {
   size_t* xo = (size_t*)malloc(sizeof(size_t) * B);
   size_t* uo = (size_t*)malloc(sizeof(size_t) * B);
   offsets(B, N, xo, uo);
@@ -667,11 +811,23 @@ void orc_rti_step(const orc_quad* Qd, int nl, const int* w, const double* P, int
     double* ub = u + uo[b] * NU;
     double* dx = (double*)malloc(sizeof(double) * (Nb + 1) * NX);
     double* du = (double*)malloc(sizeof(double) * Nb * NU);
-    int st = orc_riccati(NX, NU, Nb, A + uo[b] * NX * NX, Bm + uo[b] * NX * NU, c + uo[b] * NX,
-                         xb, ub, xref + xo[b] * NX, uref + uo[b] * NU, Q, R, QN, x0m + b * NX,
-                         dx, du, NULL, NULL);
+    int st, it = 1;
+    if (box) {
+      double* lb = (double*)malloc(sizeof(double) * Nb * NU);
+      double* hb = (double*)malloc(sizeof(double) * Nb * NU);
+      for (int i = 0; i < Nb * NU; ++i) { lb[i] = -ub[i]; hb[i] = Qd->u_max - ub[i]; }
+      st = orc_box_qp(NX, NU, Nb, A + uo[b] * NX * NX, Bm + uo[b] * NX * NU, c + uo[b] * NX, xb, ub,
+                      xref + xo[b] * NX, uref + uo[b] * NU, Q, R, QN, x0m + b * NX, lb, hb,
+                      max_iter, dx, du, &it);
+      free(lb); free(hb);
+    } else {
+      st = orc_riccati(NX, NU, Nb, A + uo[b] * NX * NX, Bm + uo[b] * NX * NU, c + uo[b] * NX, xb,
+                       ub, xref + xo[b] * NX, uref + uo[b] * NU, Q, R, QN, x0m + b * NX, dx, du,
+                       NULL, NULL);
+    }
     status[b] = st;
-    if (st == 0) {
+    if (iters) iters[b] = it;
+    if (st == 0 || st == 8) {
       for (int i = 0; i < (Nb + 1) * NX; ++i) xb[i] += dx[i];
       for (int i = 0; i < Nb * NU; ++i) ub[i] += du[i];
       for (int i = 0; i < NU; ++i) {
@@ -690,17 +846,34 @@ void orc_rti_step(const orc_quad* Qd, int nl, const int* w, const double* P, int
   free(A); free(Bm); free(c); free(xo); free(uo);
 }
 
+void orc_rti_step(const orc_quad* Qd, int nl, const int* w, const double* P, int B, const int* N,
+                  const double* dt, const double* Q, const double* R, const double* QN, double* x,
+                  double* u, const double* xref, const double* uref, const double* x0m,
+                  int shift, double* u0, int* status) {
+  rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift, u0, status, 0, 0, NULL);
+}
+
+void orc_rti_step_box(const orc_quad* Qd, int nl, const int* w, const double* P, int B,
+                      const int* N, const double* dt, const double* Q, const double* R,
+                      const double* QN, double* x, double* u, const double* xref,
+                      const double* uref, const double* x0m, int shift, int max_iter, double* u0,
+                      int* status, int* iters) {
+  rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift, u0, status, 1, max_iter,
+           iters);
+}
+
 /* Closed loop: each control step runs one RTI step from the plant's state,
  * applies u_0 to the plant for dt (nsub RK4 sub-steps of the true dynamics,
  * then quaternion renormalisation).  References are sampled on each
  * instance's own dt grid: xrt [B][T][13], urt [B][T-1][4] with
  * T >= steps + max N + 1.  The iterate starts at x_k = x0, u_k = hover.
  * traj[steps][B][13] receives the plant state after every step. */
-void orc_closed_loop(const orc_quad* Qd, int nl, const int* w, const double* P, int plant_kind,
-                     int pnl, const int* pw, const double* PP, int B, const int* N,
-                     const double* dt, const double* Q, const double* R, const double* QN,
-                     const double* x0, const double* xrt, const double* urt, int T, int steps,
-                     double* traj, double* u0_hist) {
+static void closed_loop_core(const orc_quad* Qd, int nl, const int* w, const double* P,
+                             int plant_kind, int pnl, const int* pw, const double* PP, int B,
+                             const int* N, const double* dt, const double* Q, const double* R,
+                             const double* QN, const double* x0, const double* xrt,
+                             const double* urt, int T, int steps, double* traj, double* u0_hist,
+                             int box, int max_iter) {
   size_t* xo = (size_t*)malloc(sizeof(size_t) * B);
   size_t* uo = (size_t*)malloc(sizeof(size_t) * B);
   offsets(B, N, xo, uo);
@@ -726,7 +899,7 @@ void orc_closed_loop(const orc_quad* Qd, int nl, const int* w, const double* P, 
       for (int k = 0; k < N[b]; ++k)
         memcpy(ur + (uo[b] + k) * NU, urt + ((size_t)b * (T - 1) + t + k) * NU, sizeof(double) * NU);
     }
-    orc_rti_step(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xr, ur, xp, 1, u0, st);
+    rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xr, ur, xp, 1, u0, st, box, max_iter, NULL);
 #pragma omp parallel for
     for (int b = 0; b < B; ++b) {
       double xn[NX];
@@ -737,6 +910,25 @@ void orc_closed_loop(const orc_quad* Qd, int nl, const int* w, const double* P, 
     if (u0_hist) memcpy(u0_hist + (size_t)t * B * NU, u0, sizeof(double) * B * NU);
   }
   free(xo); free(uo); free(x); free(u); free(xr); free(ur); free(xp); free(u0); free(st);
+}
+
+void orc_closed_loop(const orc_quad* Qd, int nl, const int* w, const double* P, int plant_kind,
+                     int pnl, const int* pw, const double* PP, int B, const int* N,
+                     const double* dt, const double* Q, const double* R, const double* QN,
+                     const double* x0, const double* xrt, const double* urt, int T, int steps,
+                     double* traj, double* u0_hist) {
+  closed_loop_core(Qd, nl, w, P, plant_kind, pnl, pw, PP, B, N, dt, Q, R, QN, x0, xrt, urt, T,
+                   steps, traj, u0_hist, 0, 0);
+}
+
+void orc_closed_loop_box(const orc_quad* Qd, int nl, const int* w, const double* P,
+                         int plant_kind, int pnl, const int* pw, const double* PP, int B,
+                         const int* N, const double* dt, const double* Q, const double* R,
+                         const double* QN, const double* x0, const double* xrt,
+                         const double* urt, int T, int steps, int max_iter, double* traj,
+                         double* u0_hist) {
+  closed_loop_core(Qd, nl, w, P, plant_kind, pnl, pw, PP, B, N, dt, Q, R, QN, x0, xrt, urt, T,
+                   steps, traj, u0_hist, 1, max_iter);
 }
 
 /* ------------------------------------------------------------ training --- */

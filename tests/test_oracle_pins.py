@@ -377,3 +377,124 @@ def test_adam_first_step_closed_form(orc):
     # second step with the same gradient: m_hat = g, v_hat = g^2 again
     orc.adam(p, g, m, v, 2, 1e-3)
     assert np.allclose(p, p0 - 2e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- box QP ---
+# The thrust bounds 0 <= u_k + du_k <= u_max of Sec. V inside the QP.  Pins:
+# the exact solution of the same bound-constrained problem by an independent
+# solver (bounded-variable least squares on the condensed problem, built
+# here from the dynamics), its KKT conditions, and the unconstrained Riccati
+# solution when no bound is active.
+
+def _linearised_qp(orc, seed, N=10, scale=1.0):
+    """QP data of the nominal quadrotor linearised along a perturbed hover
+    trajectory, with references far enough away that bounds become active."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((N + 1, 13)); x[:, 3] = 1.0
+    x[:, 7:10] += rng.normal(0, 2 * scale, 3)
+    u = np.clip(np.full((N, 4), W.hover_thrust()) + rng.uniform(-1.5, 1.5, (N, 4)) * scale,
+                0, W.QUAD["u_max"])
+    _, _, A, B, c = orc.linearize(W.QUAD, [], np.array([N]), np.array([0.05]), x, u)
+    xr = np.zeros((N + 1, 13)); xr[:, 3] = 1.0
+    xr[:, :3] += rng.normal(0, 3 * scale, 3)
+    ur = np.full((N, 4), W.hover_thrust())
+    x0m = x[0] + rng.normal(0, 0.5 * scale, 13)
+    lb, ub = -u, W.QUAD["u_max"] - u
+    return A, B, c, x, u, xr, ur, x0m, lb, ub
+
+
+def _condensed(A, B, c, x, u, xr, ur, x0m, Q, R, QN):
+    """Eliminate the dynamics: dx_k = Phi_k dx_0 + Gam_k du + e_k, so the cost
+    is 1/2 du'H du + g'du + const."""
+    N, nx, nu = A.shape[0], A.shape[1], B.shape[2]
+    Phi, Gam, e = [np.eye(nx)], [np.zeros((nx, N * nu))], [np.zeros(nx)]
+    for k in range(N):
+        Phi.append(A[k] @ Phi[-1])
+        Gk = A[k] @ Gam[-1]
+        Gk[:, k * nu:(k + 1) * nu] += B[k]
+        Gam.append(Gk)
+        e.append(A[k] @ e[-1] + c[k])
+    dx0 = x0m - x[0]
+    H = np.diag(np.tile(R, N)).astype(float)
+    g = np.concatenate([R * (u[k] - ur[k]) for k in range(N)])
+    for k in range(N + 1):
+        W_ = np.diag(QN if k == N else Q)
+        off = x[k] + Phi[k] @ dx0 + e[k] - xr[k]
+        H += Gam[k].T @ W_ @ Gam[k]
+        g += Gam[k].T @ W_ @ off
+    return H, g
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_box_qp_matches_bounded_least_squares(orc, seed):
+    from scipy.optimize import lsq_linear
+    A, B, c, x, u, xr, ur, x0m, lb, ub = _linearised_qp(orc, seed)
+    Q, R = W.Q_DIAG, W.R_DIAG
+    st, dx, du, its = orc.box_qp(A, B, c, x, u, xr, ur, Q, R, Q, x0m, lb, ub, max_iter=40)
+    assert st == 0
+    H, g = _condensed(A, B, c, x, u, xr, ur, x0m, Q, R, Q)
+    L = np.linalg.cholesky(H)
+    # min 1/2 v'Hv + g'v  ==  min 1/2 |L'v + L^-1 g|^2 under the same bounds
+    ref = lsq_linear(L.T, -np.linalg.solve(L, g), bounds=(lb.ravel(), ub.ravel()), method="bvls",
+                     tol=1e-14).x
+    assert np.abs(du.ravel() - ref).max() < 1e-8 * max(1.0, np.abs(ref).max())
+    at_bound = (np.abs(ref - lb.ravel()) < 1e-9) | (np.abs(ref - ub.ravel()) < 1e-9)
+    # KKT with the condensed gradient: zero on free inputs, sign at the bounds
+    G = H @ du.ravel() + g
+    free = ~at_bound
+    assert np.abs(G[free]).max() < 1e-6 * np.abs(g).max()
+    assert (G[np.abs(ref - lb.ravel()) < 1e-9] > -1e-6 * np.abs(g).max()).all()
+    assert (G[np.abs(ref - ub.ravel()) < 1e-9] < 1e-6 * np.abs(g).max()).all()
+    # dx is the roll-out of du
+    for k in range(A.shape[0]):
+        assert np.allclose(dx[k + 1], A[k] @ dx[k] + B[k] @ du[k] + c[k], atol=1e-9)
+
+
+def test_box_qp_inactive_bounds_is_riccati(orc):
+    A, B, c, x, u, xr, ur, x0m, lb, ub = _linearised_qp(orc, 11, scale=0.3)
+    Q, R = W.Q_DIAG, W.R_DIAG
+    st0, dx0, du0 = orc.riccati(A, B, c, x, u, xr, ur, Q, R, Q, x0m)
+    big = np.full_like(lb, 1e9)
+    st, dx, du, its = orc.box_qp(A, B, c, x, u, xr, ur, Q, R, Q, x0m, -big, big)
+    assert st == st0 == 0 and its == 1
+    assert np.array_equal(du, du0) and np.array_equal(dx, dx0)
+
+
+def test_box_qp_iteration_cap(orc):
+    A, B, c, x, u, xr, ur, x0m, lb, ub = _linearised_qp(orc, 0)
+    Q, R = W.Q_DIAG, W.R_DIAG
+    st, dx, du, its = orc.box_qp(A, B, c, x, u, xr, ur, Q, R, Q, x0m, lb, ub, max_iter=1)
+    assert st == 8 and its == 1
+    assert (du >= lb).all() and (du <= ub).all()
+    for k in range(A.shape[0]):
+        assert np.allclose(dx[k + 1], A[k] @ dx[k] + B[k] @ du[k] + c[k], atol=1e-9)
+
+
+def test_rti_step_box_keeps_thrust_in_bounds(orc):
+    prob = W.make_problem("cfg2_fp32_batch", seed=3, B=6)
+    N, dt = prob["N"], prob["dt"]
+    X, U = W.random_nodes(int(N.sum()) + len(N), 21)
+    U = U[:int(N.sum())]
+    xref, uref = W.node_refs(prob)
+    x0 = X[np.concatenate([[0], np.cumsum(N + 1)])[:-1]] + 0.5
+    u0, xn, un, st, its = orc.rti_step_box(W.QUAD, [], N, dt, prob["Q"], prob["R"], prob["QN"], X, U,
+                                           xref, uref, x0, shift=False, max_iter=40)
+    assert (st == 0).all()
+    assert (un >= -1e-12).all() and (un <= W.QUAD["u_max"] + 1e-12).all()
+    assert np.allclose(u0, un[np.concatenate([[0], np.cumsum(N)])[:-1]])
+    # without bounds the same step leaves the box somewhere (the bounds matter)
+    _, _, un_free, _ = orc.rti_step(W.QUAD, [], N, dt, prob["Q"], prob["R"], prob["QN"], X, U, xref,
+                                    uref, x0, shift=False)
+    assert ((un_free < 0) | (un_free > W.QUAD["u_max"])).any()
+
+
+def test_box_qp_pins_exercise_the_bounds(orc):
+    # the seeds above are cases where bounds are active at the solution
+    active = 0
+    for seed in range(6):
+        A, B, c, x, u, xr, ur, x0m, lb, ub = _linearised_qp(orc, seed)
+        _, _, du, its = orc.box_qp(A, B, c, x, u, xr, ur, W.Q_DIAG, W.R_DIAG, W.Q_DIAG, x0m, lb, ub,
+                                   max_iter=40)
+        if ((np.abs(du - lb) < 1e-12) | (np.abs(du - ub) < 1e-12)).sum() >= 2 and its > 1:
+            active += 1
+    assert active >= 4, active
