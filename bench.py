@@ -137,10 +137,11 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make(prob, precision, riccati_f64=False):
+def make(prob, precision, riccati_f64=False, box_qp=False):
     import paper_2203_07747_b300 as rtn
     return rtn.Controller(prob["N"], prob["dt"], prob["Q"], prob["R"], QN=prob["QN"], quad=prob["quad"],
-                          layers=prob["layers"], precision=precision, riccati_f64=riccati_f64)
+                          layers=prob["layers"], precision=precision, riccati_f64=riccati_f64,
+                          box_qp=box_qp)
 
 
 def launches_per_step(ctl):
@@ -315,6 +316,47 @@ def bench_ragged(steps=200):
             "error_table": etab, "tracking_rmse_m": rmse, "tile_variant": vi}
 
 
+def bench_box(prob, precision, tile, steps=20):
+    """The thrust bounds inside the QP (primal-dual active set on the Riccati
+    structure): the headline closed loop with the box QP, and the QP alone on
+    a displaced start (every instance 2 m from its reference, iterate at
+    hover there), where thrusts saturate, against the unconstrained QP."""
+    import torch
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    ctl = make(prob, precision, box_qp=True)
+    if tile is not None:
+        ctl.tc_select(tile["variant"])
+    ms, _, rmse = time_closed_loop(ctl, prob, steps, 3)
+    its_loop = ctl.box_iterations()
+    xrt, _ = W.trajectory_refs(prob, 1)
+    x0 = xrt[:, 0].copy()
+    x0[:, 0] += 2.0
+    ctl.reset(dev(x0))
+    x, u = ctl.get_iterate()
+    A, Bm, c = ctl.linearize(x, u)[2:]
+    xref, uref = W.node_refs(prob)
+    args = (A, Bm, c, x, u, dev(xref), dev(uref), dev(x0))
+    ms_box = time_calls(lambda: ctl.qp_solve(*args), 5)
+    _, _, st = ctl.qp_solve(*args)
+    its = ctl.box_iterations()
+    st = st.cpu().numpy()
+    ctl.close()
+    cu = make(prob, "fp32")
+    ms_free = time_calls(lambda: cu.qp_solve(*args), 5)
+    _, du_free, _ = cu.qp_solve(*args)
+    uf = (u + du_free).cpu().numpy()
+    cu.close()
+    return {"rti_steps_per_s": prob["B"] / (ms * 1e-3), "ms_per_step": ms, "tracking_rmse_m": rmse,
+            "closed_loop_subproblems_last_step": {"mean": float(its_loop.mean()), "max": int(its_loop.max())},
+            "displaced_start": {
+                "workload": "every instance 2 m from its reference, iterate at hover there, one QP",
+                "ms_box_qp": ms_box, "ms_unconstrained_qp": ms_free,
+                "unconstrained_step_nodes_outside_bounds_frac": float(((uf < 0) | (uf > prob["quad"]["u_max"])).any(axis=1).mean()) if uf.ndim == 2 else None,
+                "subproblems": {"mean": float(its.mean()), "p99": float(np.percentile(its, 99)),
+                                "max": int(its.max()), "frac_more_than_one": float((its > 1).mean())},
+                "not_converged": int((st == 8).sum())}}
+
+
 def bench_learned(epochs=2, steps=100):
     """cfg5: 2^20 seeded samples -> drag residual targets, train 17-512x6-3
     (Adam, lr 1e-3, batch 4096), then a 4096-instance closed loop on the drag
@@ -460,6 +502,7 @@ def main():
                                       "node_linearizations_per_s": nn / (ml32 * 1e-3)}
         c32.close()
     if rank == 0 and world == 1 and not args.no_extra:
+        line["box_qp"] = bench_box(prob, prec, cfg.get("tile"))
         line["ragged_batch"] = bench_ragged()
         line["learned_part"] = bench_learned()
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -51,7 +51,10 @@ typedef enum {
   RTN_E_NOT_PD = 4,      /* per instance: R + B'PB not positive definite */
   RTN_E_TIMEOUT = 5,     /* a bounded device wait gave up */
   RTN_E_NOMEM = 6,       /* device allocation failed */
-  RTN_E_UNSUPPORTED = 7  /* feature not available for this configuration */
+  RTN_E_UNSUPPORTED = 7, /* feature not available for this configuration */
+  RTN_E_NOT_CONVERGED = 8 /* per instance: the box-constrained QP's active sets
+                             did not settle within box_max_iter subproblems;
+                             the step applied is the last one clamped to the box */
 } rtn_status;
 
 /* arithmetic of the network evaluation (a1) */
@@ -88,6 +91,11 @@ typedef struct {
   int precision;    /* RTN_FP32 / RTN_BF16 / RTN_BF16X2 */
   int riccati_f64;  /* 0: FP32 sweep (Cholesky of R+B'PB in FP32); 1: FP64 sweep */
   int shift;        /* 1: shift the iterate by one stage after every RTI step */
+  int box_qp;       /* 1: the QP carries the thrust bounds 0 <= u_k + du_k <= u_max
+                       (Sec. V) and is solved by a primal-dual active-set method
+                       whose subproblems are masked Riccati sweeps; 0: no bounds
+                       in the QP, only the sent u_0 is clamped */
+  int box_max_iter; /* subproblems per QP at most (0: 20) */
 } rtn_options;
 
 /* Create a controller batch of `batch` instances with horizons N[b] >= 1 and
@@ -138,7 +146,8 @@ rtn_status rtn_linearize(rtn_ctx* ctx, const float* x, const float* u, float* fD
  * x, u (layouts as above) with references xref dev [sum(N_b+1)][13], uref dev
  * [sum N_b][4] and measured states x0 dev [B][13].  Writes the step
  * dx dev [sum(N_b+1)][13], du dev [sum N_b][4] and inst_status dev int [B]
- * (RTN_OK, RTN_E_NOT_PD, RTN_E_NONFINITE; failed instances get a zero step). */
+ * (RTN_OK, RTN_E_NOT_PD, RTN_E_NONFINITE; failed instances get a zero step;
+ * with box_qp also RTN_E_NOT_CONVERGED, see rtn_options). */
 rtn_status rtn_qp_solve(rtn_ctx* ctx, const float* A, const float* B, const float* c,
                         const float* x, const float* u, const float* xref, const float* uref,
                         const float* x0, float* dx, float* du, int* inst_status);
@@ -150,6 +159,11 @@ rtn_status rtn_qp_solve(rtn_ctx* ctx, const float* A, const float* B, const floa
  * NULL).  Failed instances keep their iterate and send uref's first entry. */
 rtn_status rtn_rti_step(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
                         float* u0_out, int* inst_status);
+
+/* Subproblems (masked Riccati sweeps) each instance's last box-constrained QP
+ * needed: host int [B] (1 = the unconstrained solution was feasible).
+ * Synchronous.  RTN_E_UNSUPPORTED unless the context was created with box_qp. */
+rtn_status rtn_box_iterations(rtn_ctx* ctx, int* iters);
 
 /* (a5) Plant step for every instance: nsub RK4 sub-steps of dt_b/nsub of the
  * true dynamics f_F + residual (kind RTN_PLANT_*), then q <- q/|q|, all in

@@ -17,7 +17,8 @@ NX, NU, NZ, NO = 13, 4, 17, 3
 PRECISION = {"fp32": 0, "bf16": 1, "bf16x2": 2}
 PLANT = {"nominal": 0, "drag": 1, "mlp": 2}
 STATUS = {0: "RTN_OK", 1: "RTN_E_INVAL", 2: "RTN_E_CUDA", 3: "RTN_E_NONFINITE",
-          4: "RTN_E_NOT_PD", 5: "RTN_E_TIMEOUT", 6: "RTN_E_NOMEM", 7: "RTN_E_UNSUPPORTED"}
+          4: "RTN_E_NOT_PD", 5: "RTN_E_TIMEOUT", 6: "RTN_E_NOMEM", 7: "RTN_E_UNSUPPORTED",
+          8: "RTN_E_NOT_CONVERGED"}
 
 # every symbol include/rtn.h declares
 EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_reset",
@@ -26,7 +27,7 @@ EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_rese
            "rtn_mlp_eval_f32_noalloc", "rtn_device_error", "rtn_tc_variants",
            "rtn_tc_variant_info", "rtn_tc_select", "rtn_autotune", "rtn_tc_trace",
            "rtn_tc_trace_read", "rtn_drag_targets", "rtn_mse_grad", "rtn_train",
-           "rtn_get_params"]
+           "rtn_get_params", "rtn_box_iterations"]
 
 _lib = None
 
@@ -45,7 +46,8 @@ class _MLP(C.Structure):
 
 
 class _Opt(C.Structure):
-    _fields_ = [("precision", C.c_int), ("riccati_f64", C.c_int), ("shift", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("riccati_f64", C.c_int), ("shift", C.c_int),
+                ("box_qp", C.c_int), ("box_max_iter", C.c_int)]
 
 
 def lib_path():
@@ -95,6 +97,7 @@ def load(build_if_missing=False):
     L.rtn_train.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.POINTER(C.c_float)]
     L.rtn_get_params.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.rtn_tc_trace_read.argtypes = [vp, C.POINTER(C.c_ulonglong), C.c_int]
+    L.rtn_box_iterations.argtypes = [vp, ip]
     L.rtn_mlp_eval_f32_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int)] + [vp] * 2 + [C.c_int] + \
         [vp] * 5 + [C.c_char_p, C.c_size_t]
     for name in EXPORTS:
@@ -129,7 +132,7 @@ class Controller:
     """A batch of B controller instances (one RTI-SQP problem each)."""
 
     def __init__(self, N, dt, Q, R, QN=None, quad=None, layers=None, precision="fp32",
-                 riccati_f64=False, shift=True, stream=None):
+                 riccati_f64=False, shift=True, stream=None, box_qp=False, box_max_iter=20):
         import torch
         L = load()
         self.N = np.ascontiguousarray(N, dtype=np.int32)
@@ -157,7 +160,9 @@ class Controller:
             self._keep += [Wp, bp]
             mlp = _MLP(len(layers), w, Wp, bp)
             mlp_p = C.byref(mlp)
-        opt = _Opt(PRECISION[precision], int(bool(riccati_f64)), int(bool(shift)))
+        opt = _Opt(PRECISION[precision], int(bool(riccati_f64)), int(bool(shift)), int(bool(box_qp)),
+                   int(box_max_iter))
+        self.box_qp = bool(box_qp)
         self.precision = precision
         self.stream = stream
         h = C.c_void_p()
@@ -192,6 +197,13 @@ class Controller:
     def _empty(self, *shape, dtype=None):
         import torch
         return torch.empty(shape, dtype=dtype or torch.float32, device=self.device)
+
+    def box_iterations(self):
+        """Subproblems each instance's last box-constrained QP needed (host array)."""
+        out = np.zeros(self.B, np.int32)
+        self._check(load().rtn_box_iterations(self._h, out.ctypes.data_as(C.POINTER(C.c_int))),
+                    "rtn_box_iterations")
+        return out
 
     def device_error(self):
         """Synchronise and return (and clear) the device-side status code."""

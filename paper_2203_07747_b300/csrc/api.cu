@@ -128,9 +128,12 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     nn += N[b];
   }
   if (nn + batch > (1LL << 28)) { g_create_err = "batch too large"; return RTN_E_INVAL; }
-  rtn_options o{RTN_FP32, 0, 1};
+  rtn_options o{RTN_FP32, 0, 1, 0, 0};
   if (opt) o = *opt;
   if (o.precision < RTN_FP32 || o.precision > RTN_BF16X2) { g_create_err = "bad precision"; return RTN_E_INVAL; }
+  if (o.box_max_iter < 0) { g_create_err = "box_max_iter must be >= 0"; return RTN_E_INVAL; }
+  if (o.box_max_iter == 0) o.box_max_iter = 20;
+  o.box_qp = o.box_qp ? 1 : 0;
   if (mlp) {
     if (mlp->n_layers < 2 || !mlp->widths || !mlp->W || !mlp->b || mlp->widths[0] != NZ ||
         mlp->widths[mlp->n_layers] != NO) {
@@ -241,6 +244,14 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     CK(dalloc(&ctx->dev_t, 1));
     CK(dalloc(&ctx->x0f, (size_t)batch * NX));
     CK(dalloc(&ctx->u0, (size_t)batch * NU));
+    if (o.box_qp) {
+      CK(dalloc(&ctx->box_dx, (size_t)xs * NX));
+      CK(dalloc(&ctx->box_du, (size_t)us * NU));
+      CK(dalloc(&ctx->box_gam, (size_t)us * NU));
+      CK(cudaMalloc(&ctx->box_act, (size_t)us * NU));
+      CK(dalloc(&ctx->box_iters, batch));
+      CK(cudaMemset(ctx->box_iters, 0, sizeof(int) * batch));
+    }
     // initial iterate: hover at the origin
     std::vector<float> x0(batch * NX, 0.0f);
     for (int b = 0; b < batch; ++b) x0[b * NX + 3] = 1.0f;
@@ -267,12 +278,23 @@ void rtn_destroy(rtn_ctx* ctx) {
   Layout& L = ctx->lay;
   void* ptrs[] = {L.N, L.dt, L.dt64, L.xoff, L.uoff, L.node_inst, L.order, ctx->net.W32, ctx->net.b32,
                   ctx->net.P64, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c, ctx->K,
-                  ctx->kff, ctx->act0, ctx->act1, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0};
+                  ctx->kff, ctx->act0, ctx->act1, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0,
+                  ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   mlp_tc_release(ctx);
   train_release(ctx);
   delete ctx;
+}
+
+rtn_status rtn_box_iterations(rtn_ctx* ctx, int* iters) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!iters) { ctx->err = "rtn_box_iterations: NULL output"; return RTN_E_INVAL; }
+  if (!ctx->opt.box_qp) { ctx->err = "rtn_box_iterations: context has no box-constrained QP"; return RTN_E_UNSUPPORTED; }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(iters, ctx->box_iters, sizeof(int) * ctx->B, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); return RTN_E_CUDA; }
+  return RTN_OK;
 }
 
 const char* rtn_last_error(const rtn_ctx* ctx) {

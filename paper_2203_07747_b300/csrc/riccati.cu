@@ -89,9 +89,14 @@ struct KArgs {
   const int *N, *xoff, *uoff, *order;
   void* Kg;  // [n_nodes][4][13] of T
   void* kg;  // [n_nodes][4] of T
+  // box-constrained QP (see rtn_ctx)
+  int box, box_max_iter;
+  float *box_dx, *box_du, *box_gam;
+  signed char* box_act;
+  int* box_iters;
 };
 
-template <typename T, int WPB>
+template <typename T, int WPB, bool BOX>
 __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
   __shared__ Slot<T> slots[WPB];
   const QpArgs& a = ka.a;
@@ -116,190 +121,418 @@ __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
   float x0m = lane < NX ? a.x0[(size_t)b * NX + lane] : 0.0f;
   const bool finite = __all_sync(0xffffffffu, isfinite(x0m));
 
-  // P, p of the cost-to-go: row `lane` in registers (lanes 0..12)
+  // ---------------- backward Riccati sweep (box mode: inputs flagged in
+  // box_act are held at their bounds); gains to Kg, kg; S.notpd on failure
   T Prow[NX], p_i = 0;
+  auto sweep = [&]() {
 #pragma unroll
-  for (int j = 0; j < NX; ++j) Prow[j] = (lane < NX && j == lane) ? (T)C.QN[lane] : (T)0;
-  if (lane < NX) p_i = (T)C.QN[lane] * ((T)x[(size_t)N * NX + lane] - (T)xr[(size_t)N * NX + lane]);
-  if (lane == 0) S.notpd = 0;
-  __syncwarp();
-
-  // stage data of node k (A 169, B 52, c 13 floats) as 8 registers per lane,
-  // loaded one node ahead so that the global-memory latency overlaps the
-  // previous node's arithmetic
-  constexpr int NSTAGE = NX * NX + NX * NU + NX;
-  float pf[8];
-  auto prefetch = [&](int k) {
-    const size_t node = (size_t)uo + k;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = lane + 32 * q;
-      float v = 0.0f;
-      if (e < NX * NX) v = a.A[node * NX * NX + e];
-      else if (e < NX * NX + NX * NU) v = a.Bm[node * NX * NU + (e - NX * NX)];
-      else if (e < NSTAGE) v = a.c[node * NX + (e - NX * NX - NX * NU)];
-      pf[q] = v;
-    }
-  };
-  if (finite && N > 0) prefetch(N - 1);
-
-  for (int k = N - 1; k >= 0 && finite; --k) {
-    const size_t node = (size_t)uo + k;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = lane + 32 * q;
-      if (e < NX * NX) S.A[e / NX][e % NX] = (T)pf[q];
-      else if (e < NX * NX + NX * NU) S.Bm[(e - NX * NX) / NU][(e - NX * NX) % NU] = (T)pf[q];
-      else if (e < NSTAGE) S.c[e - NX * NX - NX * NU] = (T)pf[q];
-    }
+    for (int j = 0; j < NX; ++j) Prow[j] = (lane < NX && j == lane) ? (T)C.QN[lane] : (T)0;
+    if (lane < NX) p_i = (T)C.QN[lane] * ((T)x[(size_t)N * NX + lane] - (T)xr[(size_t)N * NX + lane]);
+    if (lane == 0) S.notpd = 0;
     __syncwarp();
-    if (k > 0) prefetch(k - 1);
-    // PA = P A, PB = P B, g = p + P c: lane i forms row i
-    if (lane < NX) {
-      T pa[16], pb[NU], gi = p_i;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) pa[j] = 0;
-#pragma unroll
-      for (int m = 0; m < NU; ++m) pb[m] = 0;
-#pragma unroll
-      for (int l = 0; l < NX; ++l) {
-        T ar[16], br[4];
-        row16(&S.A[l][0], ar);
-        row4(&S.Bm[l][0], br);
-        const T pl = Prow[l];
-#pragma unroll
-        for (int j = 0; j < NX; ++j) pa[j] += pl * ar[j];
-#pragma unroll
-        for (int m = 0; m < NU; ++m) pb[m] += pl * br[m];
-        gi += pl * S.c[l];
+    // stage data of node k (A 169, B 52, c 13 floats) as 8 registers per lane,
+    // loaded one node ahead so that the global-memory latency overlaps the
+    // previous node's arithmetic
+    constexpr int NSTAGE = NX * NX + NX * NU + NX;
+    float pf[8];
+    auto prefetch = [&](int k) {
+      const size_t node = (size_t)uo + k;
+  #pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = lane + 32 * q;
+        float v = 0.0f;
+        if (e < NX * NX) v = a.A[node * NX * NX + e];
+        else if (e < NX * NX + NX * NU) v = a.Bm[node * NX * NU + (e - NX * NX)];
+        else if (e < NSTAGE) v = a.c[node * NX + (e - NX * NX - NX * NU)];
+        pf[q] = v;
       }
-#pragma unroll
-      for (int j = 0; j < NX; ++j) S.PA[lane][j] = pa[j];
-#pragma unroll
-      for (int m = 0; m < NU; ++m) S.PB[lane][m] = pb[m];
-      S.g[lane] = gi;
-    }
-    __syncwarp();
-    // Hux = B'PA (52), Huu = R + B'PB (16), hu = r + B'g (4) over the warp
-    for (int o = lane; o < NU * NX + NU * NU + NU; o += 32) {
-      T s = 0;
-      if (o < NU * NX) {
-        const int m = o / NX, j = o % NX;
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.PA[l][j];
-        S.Hux[m][j] = s;
-      } else if (o < NU * NX + NU * NU) {
-        const int e = o - NU * NX, m = e / NU, n = e % NU;
-        s = (m == n) ? (T)C.R[m] : (T)0;
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.PB[l][n];
-        S.Huu[e] = s;
-      } else {
-        const int m = o - NU * NX - NU * NU;
-        s = (T)C.R[m] * ((T)u[(size_t)k * NU + m] - (T)ur[(size_t)k * NU + m]);
-#pragma unroll
-        for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.g[l];
-        S.hu[m] = s;
+    };
+    if (finite && N > 0) prefetch(N - 1);
+
+    for (int k = N - 1; k >= 0 && finite; --k) {
+      const size_t node = (size_t)uo + k;
+  #pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = lane + 32 * q;
+        if (e < NX * NX) S.A[e / NX][e % NX] = (T)pf[q];
+        else if (e < NX * NX + NX * NU) S.Bm[(e - NX * NX) / NU][(e - NX * NX) % NU] = (T)pf[q];
+        else if (e < NSTAGE) S.c[e - NX * NX - NX * NU] = (T)pf[q];
       }
-    }
-    __syncwarp();
-    // Cholesky of Huu by one lane (one reciprocal square root per pivot)
-    if (lane == 0) {
-      T L[NU][NU];
-      bool pd = true;
-#pragma unroll
-      for (int j = 0; j < NU; ++j) {
-        T s = S.Huu[j * NU + j];
-#pragma unroll
-        for (int q = 0; q < j; ++q) s -= L[j][q] * L[j][q];
-        pd &= (s > (T)0);
-        T inv;
-        if constexpr (sizeof(T) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
-        else inv = rsqrt(fmax(s, 1e-300));
-        L[j][j] = s * inv;
-        S.Linvt[j] = (T)inv;
-#pragma unroll
-        for (int i = j + 1; i < NU; ++i) {
-          T v = S.Huu[i * NU + j];
-#pragma unroll
-          for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
-          L[i][j] = v * inv;
+      __syncwarp();
+      if (k > 0) prefetch(k - 1);
+      // box mode: inputs held at a bound in this subproblem (fx) and their values
+      int fx[NU];
+      T av[NU];
+      {
+        const uint32_t w4 = BOX ? *reinterpret_cast<const uint32_t*>(ka.box_act + node * NU) : 0u;
+  #pragma unroll
+        for (int m = 0; m < NU; ++m) {
+          const int v = (int)(signed char)((w4 >> (8 * m)) & 0xffu);
+          const T um = (T)u[(size_t)k * NU + m];
+          fx[m] = v != 0;
+          av[m] = v < 0 ? -um : (v > 0 ? (T)ka.u_max - um : (T)0);
         }
       }
-#pragma unroll
-      for (int i = 0; i < NU; ++i)
-#pragma unroll
-        for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (T)0;
-      if (!pd) S.notpd = 1;
-    }
-    __syncwarp();
-    // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `lane` (13 = hu)
-    if (lane < NX + 1) {
-      T y[NU];
-#pragma unroll
-      for (int i = 0; i < NU; ++i) {
-        T v = (lane < NX) ? S.Hux[i][lane] : S.hu[i];
-#pragma unroll
-        for (int q = 0; q < i; ++q) v -= S.Lt[i * NU + q] * y[q];
-        y[i] = v * S.Linvt[i];
+      // PA = P A, PB = P B, g = p + P c: lane i forms row i
+      if (lane < NX) {
+        T pa[16], pb[NU], gi = p_i;
+  #pragma unroll
+        for (int j = 0; j < 16; ++j) pa[j] = 0;
+  #pragma unroll
+        for (int m = 0; m < NU; ++m) pb[m] = 0;
+  #pragma unroll
+        for (int l = 0; l < NX; ++l) {
+          T ar[16], br[4];
+          row16(&S.A[l][0], ar);
+          row4(&S.Bm[l][0], br);
+          const T pl = Prow[l];
+  #pragma unroll
+          for (int j = 0; j < NX; ++j) pa[j] += pl * ar[j];
+  #pragma unroll
+          for (int m = 0; m < NU; ++m) pb[m] += pl * br[m];
+          gi += pl * S.c[l];
+        }
+  #pragma unroll
+        for (int j = 0; j < NX; ++j) S.PA[lane][j] = pa[j];
+  #pragma unroll
+        for (int m = 0; m < NU; ++m) S.PB[lane][m] = pb[m];
+        S.g[lane] = gi;
       }
-#pragma unroll
-      for (int i = NU - 1; i >= 0; --i) {
-        T v = y[i];
-#pragma unroll
-        for (int q = i + 1; q < NU; ++q) v -= S.Lt[q * NU + i] * y[q];
-        y[i] = v * S.Linvt[i];
+      __syncwarp();
+      // Hux = B'PA (52), Huu = R + B'PB (16), hu = r + B'g (4) over the warp
+      for (int o = lane; o < NU * NX + NU * NU + NU; o += 32) {
+        T s = 0;
+        if (o < NU * NX) {
+          const int m = o / NX, j = o % NX;
+  #pragma unroll
+          for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.PA[l][j];
+          S.Hux[m][j] = s;
+        } else if (o < NU * NX + NU * NU) {
+          const int e = o - NU * NX, m = e / NU, n = e % NU;
+          s = (m == n) ? (T)C.R[m] : (T)0;
+  #pragma unroll
+          for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.PB[l][n];
+          S.Huu[e] = s;
+        } else {
+          const int m = o - NU * NX - NU * NU;
+          s = (T)C.R[m] * ((T)u[(size_t)k * NU + m] - (T)ur[(size_t)k * NU + m]);
+  #pragma unroll
+          for (int l = 0; l < NX; ++l) s += S.Bm[l][m] * S.g[l];
+          S.hu[m] = s;
+        }
       }
-#pragma unroll
-      for (int i = 0; i < NU; ++i) {
-        if (lane < NX) S.K[i][lane] = -y[i];
-        else S.k[i] = -y[i];
+      __syncwarp();
+      if (BOX && lane < NU) ka.box_gam[node * NU + lane] = (float)S.Huu[lane * NU + lane];
+      // held inputs: identity rows/columns of Huu, zero rows of Hux, right-hand
+      // side -a; their coupling moves to the free rows' right-hand side
+      auto Hm = [&](int i, int j) -> T {
+        return (fx[i] || fx[j]) ? (i == j ? (T)1 : (T)0) : S.Huu[i * NU + j];
+      };
+      // Cholesky of Huu by one lane (one reciprocal square root per pivot)
+      if (lane == 0) {
+        T L[NU][NU];
+        bool pd = true;
+  #pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          T s = Hm(j, j);
+  #pragma unroll
+          for (int q = 0; q < j; ++q) s -= L[j][q] * L[j][q];
+          pd &= (s > (T)0);
+          T inv;
+          if constexpr (sizeof(T) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
+          else inv = rsqrt(fmax(s, 1e-300));
+          L[j][j] = s * inv;
+          S.Linvt[j] = (T)inv;
+  #pragma unroll
+          for (int i = j + 1; i < NU; ++i) {
+            T v = Hm(i, j);
+  #pragma unroll
+            for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
+            L[i][j] = v * inv;
+          }
+        }
+  #pragma unroll
+        for (int i = 0; i < NU; ++i)
+  #pragma unroll
+          for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (T)0;
+        if (!pd) S.notpd = 1;
       }
-    }
-    __syncwarp();
-    for (int e = lane; e < NU * NX + NU; e += 32) {
-      if (e < NU * NX) Kg[node * NU * NX + e] = S.K[e / NX][e % NX];
-      else kg[node * NU + (e - NU * NX)] = S.k[e - NU * NX];
-    }
-    // P2 = Q + A'PA + Hux'K (row i on lane i), p2 = q + A'g + Hux'k
-    T P2row[16], p2 = 0;
-    if (lane < NX) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) P2row[j] = (j == lane) ? (T)C.Q[lane] : (T)0;
-      p2 = (T)C.Q[lane] * ((T)x[(size_t)k * NX + lane] - (T)xr[(size_t)k * NX + lane]);
-#pragma unroll
-      for (int l = 0; l < NX; ++l) {
-        T pr[16];
-        row16(&S.PA[l][0], pr);
-        const T al = S.A[l][lane];
-#pragma unroll
-        for (int j = 0; j < NX; ++j) P2row[j] += al * pr[j];
-        p2 += al * S.g[l];
+      __syncwarp();
+      // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `lane` (13 = hu)
+      if (lane < NX + 1) {
+        T y[NU];
+  #pragma unroll
+        for (int i = 0; i < NU; ++i) {
+          T v;
+          if (fx[i]) {
+            v = (lane < NX) ? (T)0 : -av[i];
+          } else {
+            v = (lane < NX) ? S.Hux[i][lane] : S.hu[i];
+            if (lane == NX) {
+  #pragma unroll
+              for (int n = 0; n < NU; ++n)
+                if (fx[n]) v += S.Huu[i * NU + n] * av[n];
+            }
+          }
+  #pragma unroll
+          for (int q = 0; q < i; ++q) v -= S.Lt[i * NU + q] * y[q];
+          y[i] = v * S.Linvt[i];
+        }
+  #pragma unroll
+        for (int i = NU - 1; i >= 0; --i) {
+          T v = y[i];
+  #pragma unroll
+          for (int q = i + 1; q < NU; ++q) v -= S.Lt[q * NU + i] * y[q];
+          y[i] = v * S.Linvt[i];
+        }
+  #pragma unroll
+        for (int i = 0; i < NU; ++i) {
+          if (lane < NX) S.K[i][lane] = -y[i];
+          else S.k[i] = -y[i];
+        }
       }
-#pragma unroll
-      for (int m = 0; m < NU; ++m) {
-        T kr[16];
-        row16(&S.K[m][0], kr);
-        const T hm = S.Hux[m][lane];
-#pragma unroll
-        for (int j = 0; j < NX; ++j) P2row[j] += hm * kr[j];
-        p2 += hm * S.k[m];
+      __syncwarp();
+      for (int e = lane; e < NU * NX + NU; e += 32) {
+        if (e < NU * NX) Kg[node * NU * NX + e] = S.K[e / NX][e % NX];
+        else kg[node * NU + (e - NU * NX)] = S.k[e - NU * NX];
       }
-#pragma unroll
-      for (int j = 0; j < NX; ++j) S.P2[lane][j] = P2row[j];
+      // P2 = Q + A'PA + Hux'K (row i on lane i), p2 = q + A'g + Hux'k
+      T P2row[16], p2 = 0;
+      if (lane < NX) {
+  #pragma unroll
+        for (int j = 0; j < 16; ++j) P2row[j] = (j == lane) ? (T)C.Q[lane] : (T)0;
+        p2 = (T)C.Q[lane] * ((T)x[(size_t)k * NX + lane] - (T)xr[(size_t)k * NX + lane]);
+  #pragma unroll
+        for (int l = 0; l < NX; ++l) {
+          T pr[16];
+          row16(&S.PA[l][0], pr);
+          const T al = S.A[l][lane];
+  #pragma unroll
+          for (int j = 0; j < NX; ++j) P2row[j] += al * pr[j];
+          p2 += al * S.g[l];
+        }
+  #pragma unroll
+        for (int m = 0; m < NU; ++m) {
+          T kr[16];
+          row16(&S.K[m][0], kr);
+          const T hm = S.Hux[m][lane];
+  #pragma unroll
+          for (int j = 0; j < NX; ++j) P2row[j] += hm * kr[j];
+          p2 += hm * S.k[m];
+        }
+  #pragma unroll
+        for (int j = 0; j < NX; ++j) S.P2[lane][j] = P2row[j];
+      }
+      __syncwarp();
+      if (lane < NX) {
+  #pragma unroll
+        for (int j = 0; j < NX; ++j) Prow[j] = (T)0.5 * (P2row[j] + S.P2[j][lane]);
+        p_i = p2;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    if (lane < NX) {
-#pragma unroll
-      for (int j = 0; j < NX; ++j) Prow[j] = (T)0.5 * (P2row[j] + S.P2[j][lane]);
-      p_i = p2;
-    }
-    __syncwarp();
-  }
+  };
 
-  const int st = !finite ? RTN_E_NONFINITE : (S.notpd ? RTN_E_NOT_PD : RTN_OK);
+  // ---------------- forward roll-out from dx_0 = x0 - x_0.
+  //   mode 0: du = K dx + k; step to a.dx/a.du, iterate update, u0 (no bounds)
+  //   mode 1: du = K dx + k; step to the box scratch only
+  //   mode 2: du from the box scratch (clamped to the bounds if `clamp`);
+  //           step to a.dx/a.du, iterate update, u0
+  // Lane i only ever touches component i of a row, so the in-place update
+  // needs no cross-lane ordering: row k+1 of the old iterate is read before
+  // row k+1 is rewritten.
+  float* xw = a.x + (size_t)xo * NX;
+  float* uw = a.u + (size_t)uo * NU;
+  float* bdx = ka.box_dx ? ka.box_dx + (size_t)xo * NX : nullptr;
+  float* bdu = ka.box_du ? ka.box_du + (size_t)uo * NU : nullptr;
+  auto forward = [&](int mode, bool clamp) {
+    const bool final_out = mode != 1;
+    if (lane < NX) S.dx[lane] = (T)x0m - (T)x[lane];
+    __syncwarp();
+    if (lane < NX) {
+      if (final_out && a.dx) a.dx[(size_t)xo * NX + lane] = (float)S.dx[lane];
+      if (mode == 1) bdx[lane] = (float)S.dx[lane];
+      if (final_out && a.update && !a.shift) xw[lane] = (float)((T)x[lane] + S.dx[lane]);
+    }
+    // per node: lane m < 4 needs its row of K and k (or its stored du); lane
+    // i < 13 its rows of A and B and c_i; loaded one node ahead
+    float fa[NX], fb[NU], fc = 0.0f;
+    T fk[NX], fkk = 0;
+    auto fetch = [&](int k) {
+      const size_t node = (size_t)uo + k;
+      if (lane < NX) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) fa[j] = a.A[node * NX * NX + lane * NX + j];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) fb[j] = a.Bm[node * NX * NU + lane * NU + j];
+        fc = a.c[node * NX + lane];
+      }
+      if (lane < NU) {
+        if (mode == 2) {
+          fkk = (T)bdu[(size_t)k * NU + lane];
+        } else {
+#pragma unroll
+          for (int j = 0; j < NX; ++j) fk[j] = Kg[node * NU * NX + lane * NX + j];
+          fkk = kg[node * NU + lane];
+        }
+      }
+    };
+    fetch(0);
+    for (int k = 0; k < N; ++k) {
+      const size_t node = (size_t)uo + k;
+      float ca[NX], cb[NU];
+      T ck[NX], ckk = fkk;
+      const float cc = fc;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) { ca[j] = fa[j]; ck[j] = fk[j]; }
+#pragma unroll
+      for (int j = 0; j < NU; ++j) cb[j] = fb[j];
+      if (k + 1 < N) fetch(k + 1);
+      if (lane < NU) {
+        T s = ckk;
+        if (mode == 2) {
+          if (clamp) {
+            const T um = (T)u[(size_t)k * NU + lane];
+            s = fmin(fmax(s, -um), (T)ka.u_max - um);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NX; ++j) s += ck[j] * S.dx[j];
+        }
+        S.du[lane] = s;
+      }
+      __syncwarp();
+      T dxn = 0;
+      if (lane < NX) {
+        T s = (T)cc;
+#pragma unroll
+        for (int j = 0; j < NX; ++j) s += (T)ca[j] * S.dx[j];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) s += (T)cb[j] * S.du[j];
+        dxn = s;
+      }
+      if (mode == 1) {
+        if (lane < NU) bdu[(size_t)k * NU + lane] = (float)S.du[lane];
+        if (lane < NX) bdx[(size_t)(k + 1) * NX + lane] = (float)dxn;
+      } else {
+        if (lane < NU) {
+          T unew = (T)u[(size_t)k * NU + lane] + S.du[lane];
+          if (a.du) a.du[node * NU + lane] = (float)S.du[lane];
+          if (k == 0 && a.u0) {
+            float v = (float)unew;
+            a.u0[(size_t)b * NU + lane] = fminf(fmaxf(v, 0.0f), ka.u_max);
+          }
+          if (a.update) {
+            if (a.shift) {
+              if (k >= 1) uw[(size_t)(k - 1) * NU + lane] = (float)unew;
+              if (k == N - 1) uw[(size_t)k * NU + lane] = (float)unew;
+            } else {
+              uw[(size_t)k * NU + lane] = (float)unew;
+            }
+          }
+        }
+        if (lane < NX) {
+          if (a.dx) a.dx[(size_t)(xo + k + 1) * NX + lane] = (float)dxn;
+          if (a.update) {
+            T xnew = (T)x[(size_t)(k + 1) * NX + lane] + dxn;
+            if (a.shift) {
+              xw[(size_t)k * NX + lane] = (float)xnew;
+              if (k == N - 1) xw[(size_t)(k + 1) * NX + lane] = (float)xnew;
+            } else {
+              xw[(size_t)(k + 1) * NX + lane] = (float)xnew;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane < NX) S.dx[lane] = dxn;
+      __syncwarp();
+    }
+  };
+
+  // ---------------- box mode: the cost's gradient at the current step by the
+  // adjoint recursion, then the new active sets from du - G / diag(Huu)
+  // (written to box_act); returns whether any set changed
+  auto update_sets = [&]() -> bool {
+    T lam = 0;
+    if (lane < NX)
+      lam = (T)C.QN[lane] * ((T)x[(size_t)N * NX + lane] + (T)bdx[(size_t)N * NX + lane] -
+                             (T)xr[(size_t)N * NX + lane]);
+    bool changed = false;
+    for (int k = N - 1; k >= 0; --k) {
+      const size_t node = (size_t)uo + k;
+      for (int e = lane; e < NX * NX; e += 32) S.A[e / NX][e % NX] = (T)a.A[node * NX * NX + e];
+      for (int e = lane; e < NX * NU; e += 32) S.Bm[e / NU][e % NU] = (T)a.Bm[node * NX * NU + e];
+      if (lane < NX) S.g[lane] = lam;
+      __syncwarp();
+      if (lane < NU) {
+        const T um = (T)u[(size_t)k * NU + lane];
+        const T dum = (T)bdu[(size_t)k * NU + lane];
+        T G = (T)C.R[lane] * (um + dum - (T)ur[(size_t)k * NU + lane]);
+#pragma unroll
+        for (int l = 0; l < NX; ++l) G += S.Bm[l][lane] * S.g[l];
+        const T v = dum - G / (T)ka.box_gam[node * NU + lane];
+        const signed char nw = v < -um ? -1 : (v > (T)ka.u_max - um ? 1 : 0);
+        if (nw != ka.box_act[node * NU + lane]) {
+          changed = true;
+          ka.box_act[node * NU + lane] = nw;
+        }
+      }
+      T ln = 0;
+      if (lane < NX) {
+        ln = (T)C.Q[lane] * ((T)x[(size_t)k * NX + lane] + (T)bdx[(size_t)k * NX + lane] -
+                             (T)xr[(size_t)k * NX + lane]);
+#pragma unroll
+        for (int l = 0; l < NX; ++l) ln += S.A[l][lane] * S.g[l];
+      }
+      __syncwarp();
+      lam = ln;
+    }
+    return __any_sync(0xffffffffu, changed);
+  };
+
+  // every du of the scratch step within 0 <= u + du <= u_max
+  auto feasible = [&]() -> bool {
+    bool ok = true;
+    for (int e = lane; e < N * NU; e += 32) {
+      const float um = u[e], d = bdu[e];
+      ok &= (d >= -um) && (d <= ka.u_max - um);
+    }
+    return __all_sync(0xffffffffu, ok);
+  };
+
+  int st = finite ? RTN_OK : RTN_E_NONFINITE;
+  if (st == RTN_OK && !BOX) {
+    sweep();
+    if (S.notpd) st = RTN_E_NOT_PD;
+  } else if (BOX && st == RTN_OK) {
+    // primal-dual active set: solve without bounds; while the step leaves
+    // the box, update the sets and solve with the active inputs held at
+    // their bounds, until the sets repeat (at most box_max_iter solves)
+    for (int e = lane; e < N * NU; e += 32) ka.box_act[(size_t)uo * NU + e] = 0;
+    __syncwarp();
+    sweep();
+    int its = 1;
+    if (S.notpd) {
+      st = RTN_E_NOT_PD;
+    } else {
+      forward(1, false);
+      if (!feasible()) {
+        for (;;) {
+          const bool changed = update_sets();
+          if (!changed && its > 1) break;
+          if (its >= ka.box_max_iter) { st = RTN_E_NOT_CONVERGED; break; }
+          sweep();
+          ++its;
+          if (S.notpd) { st = RTN_E_NOT_PD; break; }
+          forward(1, false);
+        }
+      }
+    }
+    if (lane == 0) ka.box_iters[b] = its;
+  }
   if (lane == 0 && a.status) a.status[b] = st;
-  if (st != RTN_OK) {
+  if (st != RTN_OK && st != RTN_E_NOT_CONVERGED) {
     // failed instance: zero step, iterate untouched, send the reference input
     if (a.dx)
       for (int e = lane; e < (N + 1) * NX; e += 32) a.dx[(size_t)xo * NX + e] = 0.0f;
@@ -308,99 +541,15 @@ __global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
     if (a.u0 && lane < NU) a.u0[(size_t)b * NU + lane] = ur[lane];
     return;
   }
-
-  // forward roll-out and feedback response.  Lane i only ever touches
-  // component i of a row, so the in-place update needs no cross-lane ordering:
-  // row k+1 of the old iterate is read before row k+1 is rewritten.
-  float* xw = a.x + (size_t)xo * NX;
-  float* uw = a.u + (size_t)uo * NU;
-  if (lane < NX) S.dx[lane] = (T)x0m - (T)x[lane];
-  __syncwarp();
-  if (a.dx && lane < NX) a.dx[(size_t)xo * NX + lane] = (float)S.dx[lane];
-  if (a.update && !a.shift && lane < NX) xw[lane] = (float)((T)x[lane] + S.dx[lane]);
-  // per node: lane m < 4 needs its row of K and k; lane i < 13 its rows of
-  // A and B and c_i; loaded one node ahead
-  float fa[NX], fb[NU], fc = 0.0f;
-  T fk[NX], fkk = 0;
-  auto fetch = [&](int k) {
-    const size_t node = (size_t)uo + k;
-    if (lane < NX) {
-#pragma unroll
-      for (int j = 0; j < NX; ++j) fa[j] = a.A[node * NX * NX + lane * NX + j];
-#pragma unroll
-      for (int j = 0; j < NU; ++j) fb[j] = a.Bm[node * NX * NU + lane * NU + j];
-      fc = a.c[node * NX + lane];
-    }
-    if (lane < NU) {
-#pragma unroll
-      for (int j = 0; j < NX; ++j) fk[j] = Kg[node * NU * NX + lane * NX + j];
-      fkk = kg[node * NU + lane];
-    }
-  };
-  fetch(0);
-  for (int k = 0; k < N; ++k) {
-    const size_t node = (size_t)uo + k;
-    float ca[NX], cb[NU];
-    T ck[NX], ckk = fkk;
-    const float cc = fc;
-#pragma unroll
-    for (int j = 0; j < NX; ++j) { ca[j] = fa[j]; ck[j] = fk[j]; }
-#pragma unroll
-    for (int j = 0; j < NU; ++j) cb[j] = fb[j];
-    if (k + 1 < N) fetch(k + 1);
-    if (lane < NU) {
-      T s = ckk;
-#pragma unroll
-      for (int j = 0; j < NX; ++j) s += ck[j] * S.dx[j];
-      S.du[lane] = s;
-    }
-    __syncwarp();
-    T dxn = 0;
-    if (lane < NX) {
-      T s = (T)cc;
-#pragma unroll
-      for (int j = 0; j < NX; ++j) s += (T)ca[j] * S.dx[j];
-#pragma unroll
-      for (int j = 0; j < NU; ++j) s += (T)cb[j] * S.du[j];
-      dxn = s;
-    }
-    if (lane < NU) {
-      T unew = (T)u[(size_t)k * NU + lane] + S.du[lane];
-      if (a.du) a.du[node * NU + lane] = (float)S.du[lane];
-      if (k == 0 && a.u0) {
-        float v = (float)unew;
-        a.u0[(size_t)b * NU + lane] = fminf(fmaxf(v, 0.0f), ka.u_max);
-      }
-      if (a.update) {
-        if (a.shift) {
-          if (k >= 1) uw[(size_t)(k - 1) * NU + lane] = (float)unew;
-          if (k == N - 1) uw[(size_t)k * NU + lane] = (float)unew;
-        } else {
-          uw[(size_t)k * NU + lane] = (float)unew;
-        }
-      }
-    }
-    if (lane < NX) {
-      if (a.dx) a.dx[(size_t)(xo + k + 1) * NX + lane] = (float)dxn;
-      if (a.update) {
-        T xnew = (T)x[(size_t)(k + 1) * NX + lane] + dxn;
-        if (a.shift) {
-          xw[(size_t)k * NX + lane] = (float)xnew;
-          if (k == N - 1) xw[(size_t)(k + 1) * NX + lane] = (float)xnew;
-        } else {
-          xw[(size_t)(k + 1) * NX + lane] = (float)xnew;
-        }
-      }
-    }
-    __syncwarp();
-    if (lane < NX) S.dx[lane] = dxn;
-    __syncwarp();
-  }
+  if constexpr (!BOX) forward(0, false);
+  else forward(2, st == RTN_E_NOT_CONVERGED);
 }
 
 template <typename T, int WPB>
 cudaError_t launch(const KArgs& ka, cudaStream_t s) {
-  qp_kernel<T, WPB><<<(ka.B + WPB - 1) / WPB, WPB * 32, 0, s>>>(ka);
+  const int grid = (ka.B + WPB - 1) / WPB;
+  if (ka.box) qp_kernel<T, WPB, true><<<grid, WPB * 32, 0, s>>>(ka);
+  else qp_kernel<T, WPB, false><<<grid, WPB * 32, 0, s>>>(ka);
   return cudaGetLastError();
 }
 
@@ -418,6 +567,13 @@ cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a) {
   ka.order = ctx->lay.order;
   ka.Kg = ctx->K;
   ka.kg = ctx->kff;
+  ka.box = ctx->opt.box_qp;
+  ka.box_max_iter = ctx->opt.box_max_iter;
+  ka.box_dx = ctx->box_dx;
+  ka.box_du = ctx->box_du;
+  ka.box_gam = ctx->box_gam;
+  ka.box_act = ctx->box_act;
+  ka.box_iters = ctx->box_iters;
   if (ctx->opt.riccati_f64) return launch<double, 2>(ka, ctx->stream);
   return launch<float, 4>(ka, ctx->stream);
 }

@@ -106,6 +106,13 @@ struct rtn_ctx {
   int* dev_t = nullptr;                   // closed-loop step counter
   float* x0f = nullptr;                   // [B][13] float copy of the plant state
   float* u0 = nullptr;                    // [B][4]
+  // box-constrained QP (rtn_options.box_qp): per-node scratch of the
+  // active-set iterations
+  float* box_dx = nullptr;                // [n_states][13] current step
+  float* box_du = nullptr;                // [n_nodes][4]
+  float* box_gam = nullptr;               // [n_nodes][4] diag(Huu)
+  signed char* box_act = nullptr;         // [n_nodes][4] -1 lower, +1 upper, 0 free
+  int* box_iters = nullptr;               // [B] subproblems of the last QP
   rtn::TrainState train;
   std::string err;
 };
