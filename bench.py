@@ -39,8 +39,9 @@ def peaks():
     return 6400.0, 1800.0, 1400.0, "fallback"
 
 
-KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc2.cu", "tc_common.cuh")
-PROFILES = ("mlp_tc2_kernel_cfg3_h512_bf16x2.md", "mlp_tc_kernel_cfg3_h512_bf16x2.md")
+KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc2.cu", "mlp_rev.cu", "tc_common.cuh")
+PROFILES = ("mlp_rev_kernel_cfg3_h512_bf16x2.md", "mlp_tc2_kernel_cfg3_h512_bf16x2.md",
+            "mlp_tc_kernel_cfg3_h512_bf16x2.md")
 
 
 def kernel_md5():
@@ -82,6 +83,16 @@ def fwd_flops_per_node(widths):
     for fi, fo in zip(widths[1:-1], widths[2:]):
         f += 2 * 18 * fi * fo
     return f
+
+
+def rev_flops_per_node(widths):
+    """Reverse-mode algorithmic FLOPs per node: the value pass (input layer,
+    hidden->hidden layers, output layer) plus three adjoint rows carried back
+    through every hidden->hidden layer and the input layer (J_D = W_0' D_1).
+    The elementwise scalings by d_l = 1 - a_l^2 are not counted."""
+    h1, hl = widths[1], widths[-2]
+    mm = sum(fi * fo for fi, fo in zip(widths[1:-1], widths[2:-1]))
+    return 2 * 17 * h1 + 2 * 3 * hl + 4 * 2 * mm + 3 * 2 * 17 * h1
 
 
 class Clocks:
@@ -465,7 +476,8 @@ def main():
     out = ctl.linearize(x, u)
     ms_lin = time_calls(lambda: ctl.linearize(x, u, out), max(5, args.steps))
     ms_mlp = time_calls(lambda: ctl.mlp_eval(x, u, out[0], out[1]), max(5, args.steps))
-    flops = fwd_flops_per_node(widths) * nn
+    rev = cfg.get("tile", {}).get("operand_mode") == 4
+    flops = (rev_flops_per_node(widths) if rev else fwd_flops_per_node(widths)) * nn
     if prec == "fp32":
         roof = {"bound": "alu", "peak": 148 * 128 * 2 * 2.032e9 / 1e12,
                 "peak_kind": "nominal FP32 FFMA: 148 SM x 128 lanes x 2 x 2.032 GHz"}
@@ -473,7 +485,9 @@ def main():
         roof = {"bound": "tensor", "peak": bf16_burst, "peak_kind": f"bf16 burst ({peak_src})"}
     roof.update({"achieved": flops / (ms_mlp * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "algorithmic_flops_per_launch": flops, "ms_per_launch": ms_mlp,
-                 "kernel": "network value + forward-mode Jacobian (a1)",
+                 "kernel": ("network value + reverse-mode Jacobian (a1, three adjoint rows)" if rev
+                            else "network value + forward-mode Jacobian (a1)"),
+                 "forward_mode_equivalent_tflops": fwd_flops_per_node(widths) * nn / (ms_mlp * 1e-3) / 1e12,
                  "traffic": profiled_traffic(cfg.get("tile")) if args.config == "cfg3_bf16_precision" else None})
     roof["frac"] = roof["achieved"] / roof["peak"]
 

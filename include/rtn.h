@@ -215,7 +215,8 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
 /* Tile shapes of the tensor-core network kernel (the autotuner's search
  * space).  rtn_tc_variants: number of compiled shapes.  rtn_tc_variant_info:
  * nodes per CTA (per CTA pair in mode 3), operand mode in *split (0 single
- * BF16; 1, 2 split hi + lo on one CTA; 3 split on a CTA pair, M = 256) and
+ * BF16; 1, 2 split hi + lo on one CTA; 3 split on a CTA pair, M = 256;
+ * 4 split, reverse mode: values forward, three output adjoints backward) and
  * pipeline depth of shape idx, *fits = 1 if it can run this context's
  * network and precision.  rtn_tc_select: use shape idx
  * (RTN_E_UNSUPPORTED if it does not fit).  rtn_autotune: time every fitting
@@ -241,7 +242,12 @@ rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms);
  * (mode 3) fields 2..7 of l = L hold cycle sums over tile i: epilogue work
  * (2), waiting for all epilogue warps before a block is published (3),
  * pushing blocks to the peer CTA (4), and the MMA issuer's waits on
- * activation blocks produced by rank 1 (6) and by rank 0 (7).
+ * activation blocks produced by rank 1 (6) and by rank 0 (7).  On the
+ * reverse-mode shapes (mode 4) the layer index runs over the G = 2 L' + 2
+ * GEMMs of a tile (L' hidden->hidden layers: L' forward, the output layer,
+ * L' backward, J_D = W_0' D_1), entry ((i * (G + 1) + g) * 8 + f) with the
+ * same fields, and row g = G holds the SIMT phases: f = 0/1 the last
+ * layer's adjoints, f = 2/3 the input layer of tile i.
  * rtn_tc_trace_read copies n entries to host memory (synchronous). */
 #define RTN_TC_TRACE_LEN 65536
 rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable);

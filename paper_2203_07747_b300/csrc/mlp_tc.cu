@@ -361,15 +361,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 struct Variant {
   int npc;
-  int mode;  // 0 single, 1 split (two MMAs), 2 split (hi|lo along N), 3 split on a CTA pair
+  int mode;  // 0 single, 1 split (two MMAs), 2 split (hi|lo along N), 3 split on a CTA pair,
+             // 4 split, reverse mode (value forward, three adjoints backward)
   int stages;
   const void* fn;
   bool split() const { return mode != 0; }
   bool pair() const { return mode == 3; }
+  bool rev() const { return mode == 4; }
   int threads() const { return pair() ? THREADS + 32 : THREADS; }
-  int cols() const { return 16 * npc + ((2 * npc + 15) / 16) * 16; }
+  int cols() const { return rev() ? 128 : 16 * npc + ((2 * npc + 15) / 16) * 16; }
   // tensor-memory columns of one accumulator tile (128 rows; 256 rows on a pair)
-  int tmem_per_mtile() const { return mode >= 2 ? 2 * cols() : cols(); }
+  int tmem_per_mtile() const { return rev() ? 128 : (mode >= 2 ? 2 * cols() : cols()); }
   int rows_per_mtile() const { return pair() ? 256 : 128; }
   // accumulator columns: one slot per M tile (a pair always has two slots:
   // its output layer accumulates in the second)
@@ -377,6 +379,9 @@ struct Variant {
     return (pair() ? std::max(2, HP / 256) : HP / 128) * tmem_per_mtile();
   }
   size_t smem(int HP) const {
+    if (rev())
+      return 1024 + (size_t)128 * HP * 2 + (size_t)stages * WT_BYTES + 8 * (2 * stages + 20) + 16 +
+             (size_t)npc * NZ * 4;
     if (pair())
       return 1024 + (size_t)cols() * HP * 2 + (size_t)cols() * 256 + (size_t)stages * WT_BYTES +
              8 * (2 * stages + 24) + 16 + (size_t)npc * NZ * 4;
@@ -395,6 +400,11 @@ Variant pair_variant() {
   return Variant{NPC, 3, STAGES, mlp_tc2_fn(NPC, STAGES)};
 }
 
+template <int NPC, int STAGES>
+Variant rev_variant() {
+  return Variant{NPC, 4, STAGES, mlp_rev_fn(NPC, STAGES)};
+}
+
 // every compiled tile shape; the autotuner times those that fit
 const std::vector<Variant>& all_variants() {
   static const std::vector<Variant> v = {
@@ -402,7 +412,8 @@ const std::vector<Variant>& all_variants() {
       variant<6, 0, 6>(),  variant<4, 0, 8>(),  variant<8, 1, 4>(),
       variant<5, 1, 6>(),  variant<4, 1, 3>(),  variant<3, 1, 6>(),  variant<7, 2, 5>(),
       variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>(),  pair_variant<7, 4>(),
-      pair_variant<6, 5>(), pair_variant<7, 8>(), pair_variant<4, 6>()};
+      pair_variant<6, 5>(), pair_variant<7, 8>(), pair_variant<4, 6>(), rev_variant<21, 6>(),
+      rev_variant<21, 4>(), rev_variant<16, 6>()};
   return v;
 }
 
@@ -411,16 +422,18 @@ bool fits(const Variant& v, int HP) {
   return v.smem(HP) <= 232448 && v.tmem_columns(HP) <= 512;
 }
 
-// default before autotuning: the widest tile that still leaves >= 3 stages
+// default before autotuning: with split operands the reverse-mode tile (the
+// fewest MMAs per node); otherwise the widest tile that still leaves >= 3 stages
 int default_variant(int HP, bool split) {
   const auto& vs = all_variants();
   int best = -1;
   for (int i = 0; i < (int)vs.size(); ++i) {
     if (vs[i].split() != split || !fits(vs[i], HP) || vs[i].stages < 3) continue;
-    // widest MMA (fewest instructions per column), then one CTA before a
-    // pair, then the most columns
+    // reverse mode first, then the widest MMA (fewest instructions per
+    // column), then one CTA before a pair, then the most columns
     auto key = [&](const Variant& v) {
-      return v.tmem_per_mtile() * 10000 + (v.pair() ? 0 : 5000) + v.cols() * 10 + v.stages;
+      return (v.rev() ? 100000000 : 0) + v.tmem_per_mtile() * 10000 + (v.pair() ? 0 : 5000) +
+             v.cols() * 10 + v.npc;
     };
     if (best < 0 || key(vs[i]) > key(vs[best])) best = i;
   }
@@ -512,8 +525,46 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
       }
     }
   }
+  // reverse mode (mlp_rev.cu): the same rows, then the transposes of the
+  // hidden layers, then W_0' as BF16 hi and lo rows; the output layer in FP32
+  const size_t tb = (size_t)nh * HP + 128, rows_r = tb + (size_t)nh * HP + 256;
+  std::vector<uint16_t> WRh(rows_r * HP, 0);
+  std::copy(Wp.begin(), Wp.begin() + tb * HP, WRh.begin());
+  std::vector<float> WL((size_t)NO * HP, 0.0f);
+  for (int l = 1; l < L; ++l) {
+    const int fi = net.widths[l], fo = net.widths[l + 1];
+    const float* Wl = hW.data() + net.w_off[l];
+    if (l < L - 1) {
+      const size_t row0 = tb + (size_t)(l - 1) * HP;
+      for (int i = 0; i < fi; ++i)
+        for (int k = 0; k < fo; ++k) WRh[(row0 + i) * HP + k] = f2bf(Wl[(size_t)k * fi + i]);
+    } else {
+      for (int i = 0; i < NO; ++i)
+        for (int k = 0; k < fi; ++k) WL[(size_t)i * HP + k] = Wl[(size_t)i * fi + k];
+    }
+  }
+  {
+    const int fo = net.widths[1];
+    const float* W0l = hW.data() + net.w_off[0];
+    for (int j = 0; j < NZ; ++j)
+      for (int k = 0; k < fo; ++k) {
+        const float w = W0l[(size_t)k * NZ + j];
+        const uint16_t h = f2bf(w);
+        const uint32_t hb = (uint32_t)h << 16;
+        float hf;
+        memcpy(&hf, &hb, 4);
+        WRh[(tb + (size_t)nh * HP + j) * HP + k] = h;
+        WRh[(tb + (size_t)nh * HP + 128 + j) * HP + k] = f2bf(w - hf);
+      }
+  }
   cudaError_t e = cudaMalloc(&tc.W, Wp.size() * 2);
   if (e == cudaSuccess) e = cudaMemcpy(tc.W, Wp.data(), Wp.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&tc.WR, WRh.size() * 2);
+  if (e == cudaSuccess) e = cudaMemcpy(tc.WR, WRh.data(), WRh.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&tc.WL32, WL.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(tc.WL32, WL.data(), WL.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&tc.dscr, (size_t)std::max(1, tc.n_sm) * (nh + 1) * HP * REV_NPC_MAX * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&tc.bias, bias.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(tc.bias, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&tc.W0, W0.size() * 4);
@@ -545,6 +596,14 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
     return cudaSuccess;
   }
+  cuuint64_t dimsR[2] = {(cuuint64_t)HP, (cuuint64_t)rows_r};
+  r = encode(reinterpret_cast<CUtensorMap*>(tc.tmapR_bytes), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, tc.WR,
+             dimsR, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return cudaSuccess;
+  }
   return select_variant(ctx, vi);
 }
 
@@ -569,6 +628,7 @@ cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* 
   void* args[] = {(void*)map, (void*)&a};
   const int n_tiles = (a.n_nodes + tc.npc - 1) / tc.npc;
   const Variant& v = all_variants()[tc.variant];
+  if (v.rev()) return mlp_rev_launch(ctx, x, u, fD, JD);
   dim3 grid = v.pair() ? dim3(2 * std::min(n_tiles, std::max(1, tc.n_sm / 2)))
                        : dim3(std::min(n_tiles, std::max(1, tc.n_sm)));
   return cudaLaunchKernel(tc.fn, grid, dim3(v.threads()), args, tc.smem, ctx->stream);
@@ -591,7 +651,7 @@ cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx) { return select_variant(ctx, id
 
 void mlp_tc_release(rtn_ctx* ctx) {
   TcNet& tc = ctx->net.tc;
-  void* ptrs[] = {tc.W, tc.bias, tc.W0, tc.b0, tc.err, tc.trace};
+  void* ptrs[] = {tc.W, tc.bias, tc.W0, tc.b0, tc.err, tc.trace, tc.WR, tc.WL32, tc.dscr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   tc = TcNet{};

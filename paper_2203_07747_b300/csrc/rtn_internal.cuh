@@ -57,6 +57,11 @@ struct TcNet {
   size_t smem = 0;
   const void* fn = nullptr;     // kernel variant
   alignas(64) unsigned char tmap_bytes[128];  // CUtensorMap of W
+  // reverse mode (mlp_rev.cu): W_1..W_L, W_1'..W_{L-1}', W_0' hi, lo stacked
+  __nv_bfloat16* WR = nullptr;
+  float* WL32 = nullptr;                // output layer FP32 [3][h_pad]
+  float* dscr = nullptr;                // per-CTA d_l scratch
+  alignas(64) unsigned char tmapR_bytes[128];  // CUtensorMap of WR
 };
 
 struct Net {
@@ -137,6 +142,10 @@ int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages
 cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx);
 // kernel of the CTA-pair variant (npc nodes per pair, stages weight stages), or null
 const void* mlp_tc2_fn(int npc, int stages);
+// kernel of the reverse-mode variant, or null
+const void* mlp_rev_fn(int npc, int stages);
+// arguments of the reverse-mode kernel (mlp_rev.cu)
+cudaError_t mlp_rev_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,

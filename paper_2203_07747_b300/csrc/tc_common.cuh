@@ -15,6 +15,7 @@ constexpr int THREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr uint32_t WT_BYTES = 128 * 64 * 2;  // one 128 x 64 BF16 weight tile
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int REV_NPC_MAX = 21;  // nodes per tile of the reverse-mode shapes (scratch size)
 
 template <int NPC>
 struct Cols {
