@@ -39,7 +39,7 @@ struct RevArgs {
   const float* u;
   const int* node_inst;
   int n_nodes;
-  const float* W0;    // [HP][17] FP32 input layer
+  const float* W0;    // [17][HP] FP32 input layer (transposed)
   const float* b0;    // [HP]
   const float* bias;  // hidden biases [n_hidden_mm * HP] then output [>= 3]
   const float* WL;    // [3][HP] FP32 output layer
@@ -48,7 +48,7 @@ struct RevArgs {
   uint32_t tmem_cols;
   float* fD;
   float* JD;
-  float* dscr;  // [gridDim.x][n_hidden_mm + 1][HP][NPC] FP32: d_l of the tile
+  float* dscr;  // [gridDim.x][n_hidden_mm + 1][NPC][HP] FP32: d_l of the tile
   int* err;
   unsigned long long* trace;
 };
@@ -153,9 +153,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- TMA producer: the weight tiles of every GEMM in order
-    if (lane == 0) {
+    // ---------------- TMA producer (whole warp, one elected lane issues):
+    // the weight tiles of every GEMM in order
+    if (lane == 0)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    {
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -165,21 +167,24 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int nks = L.two ? 2 * nkb : nkb;
           for (int m = 0; m < L.mts && ok; ++m)
             for (int kb = 0; kb < nks && ok; ++kb) {
-              if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
-              mbar_expect_tx(full_bar(s), WT_BYTES);
-              const int row = L.row0 + m * 128 + (kb >= nkb ? 128 : 0);
-              const int kk = kb % nkb;
+              if (!(ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
+              if (elect_one()) {
+                mbar_expect_tx(full_bar(s), WT_BYTES);
+                const int row = L.row0 + m * 128 + (kb >= nkb ? 128 : 0);
+                const int kk = kb % nkb;
 #pragma unroll
-              for (int bx = 0; bx < W_BOXES; ++bx)
-                tma_load_2d(w_s + s * WT_BYTES + bx * 4096u, &tmap, kk * 64 + bx * W_BOX_K, row,
-                            full_bar(s));
+                for (int bx = 0; bx < W_BOXES; ++bx)
+                  tma_load_2d(w_s + s * WT_BYTES + bx * 4096u, &tmap, kk * 64 + bx * W_BOX_K, row,
+                              full_bar(s));
+              }
+              __syncwarp();
               if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
         }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
+    // ---------------- MMA issuer (whole warp, one elected lane issues)
+    {
       constexpr uint32_t id_f = idesc_bf16(128, 2 * REV_CF) | (1u << 16);  // B is N-major
       constexpr uint32_t id_b = idesc_bf16(128, 2 * REV_CB) | (1u << 16);
       const uint32_t lbo = REV_CX * 16u;
@@ -194,12 +199,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int nks = L.two ? 2 * nkb : nkb;
           const uint32_t idesc = L.bwd ? id_b : id_f;
           long long w_x = 0, w_w = 0, w_t = 0;
-          if (tr) rev_trace(a, it, g, n_gemm, 0, gtime());
+          if (tr && lane == 0) rev_trace(a, it, g, n_gemm, 0, gtime());
           for (int m = 0; m < L.mts && ok; ++m) {
             const int slot = rev_slot(L, m, n_mt);
             if (used & (1u << slot)) {
               wc.start();
-              if (!(ok = mbar_wait(tmem_free(slot), (tf_par >> slot) & 1u, abort_flag, a.err))) break;
+              if (!(ok = mbar_wait_warp(tmem_free(slot), (tf_par >> slot) & 1u, abort_flag, a.err))) break;
               wc.stop(w_t);
               tf_par ^= 1u << slot;
             }
@@ -210,29 +215,29 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int kk = kb % nkb, j = kk >> 1;
               if (m == 0 && kb < nkb && (kk & 1) == 0) {
                 wc.start();
-                if (!(ok = mbar_wait(xready(j), (xr_par >> j) & 1u, abort_flag, a.err))) break;
+                if (!(ok = mbar_wait_warp(xready(j), (xr_par >> j) & 1u, abort_flag, a.err))) break;
                 wc.stop(w_x);
                 xr_par ^= 1u << j;
                 tc_fence_after();
               }
               wc.start();
-              if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, a.err))) break;
+              if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err))) break;
               wc.stop(w_w);
               tc_fence_after();
               const uint32_t as = w_s + s * WT_BYTES;
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t bo = (uint32_t)(kk * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
-                mma_bf16(d, wdesc(as, ks), xdesc(x_s + bo, lbo), idesc, (kb | ks) != 0);
+                mma_bf16_elect(d, wdesc(as, ks), xdesc(x_s + bo, lbo), idesc, (kb | ks) != 0);
               }
-              mma_commit(empty_bar(s));
+              mma_commit_elect(empty_bar(s));
               if (++s == STAGES) { s = 0; ph ^= 1u; }
               // the GEMM's last read of block j: it may be rewritten
-              if (m == L.mts - 1 && kb >= nks - nkb && (kk & 1)) mma_commit(xfree(j));
+              if (m == L.mts - 1 && kb >= nks - nkb && (kk & 1)) mma_commit_elect(xfree(j));
             }
-            if (ok) mma_commit(acc_full(slot));
+            if (ok) mma_commit_elect(acc_full(slot));
           }
-          if (tr) {
+          if (tr && lane == 0) {
             rev_trace(a, it, g, n_gemm, 1, gtime());
             rev_trace(a, it, g, n_gemm, 4, w_x);
             rev_trace(a, it, g, n_gemm, 5, w_w);
@@ -287,7 +292,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       ew = 0;
     };
-    auto dptr = [&](int layer, int r) -> float* { return dscr + ((size_t)layer * HP + r) * NPC; };
+    // d_l of row r: node n at dptr(l, r)[n * HP] (a warp's rows are contiguous)
+    auto dptr = [&](int layer, int r) -> float* { return dscr + (size_t)layer * NPC * HP + r; };
     // 16 consecutive columns (two core-matrix groups) of row r as hi | lo
     auto put16 = [&](int r, int c_hi, int c_lo, const float* v) {
 #pragma unroll
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int r = 128 * m + 32 * q + lane;
         float w[NZ];
 #pragma unroll
-        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)r * NZ + jj];
+        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)jj * HP + r];
         const float bi = a.b0[r];
         float v[16];
         float* dr = dptr(0, r);
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int k = 0; k < NZ; ++k) s = fmaf(w[k], zbuf[n * NZ + k], s);
             const bool real = node0 + n < a.n_nodes;
             const float av = real ? tanhf(s) : 0.0f;
-            dr[n] = real ? 1.0f - av * av : 0.0f;
+            dr[(size_t)n * HP] = real ? 1.0f - av * av : 0.0f;
             v[jj] = av;
           }
         }
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (n < NPC) {
               const bool real = node0 + n < a.n_nodes;
               av = real ? tanhf(v[jj] + bi) : 0.0f;
-              dr[n] = real ? 1.0f - av * av : 0.0f;
+              dr[(size_t)n * HP] = real ? 1.0f - av * av : 0.0f;
             }
             v[jj] = av;
           }
@@ -450,7 +456,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int jj = 0; jj < 16; ++jj) {
             const int cc = 16 * c + jj;
             const int i = cc % 3;
-            v[jj] = cc < 3 * NPC ? dr[cc / 3] * (i == 0 ? wl0 : (i == 1 ? wl1 : wl2)) : 0.0f;
+            v[jj] = cc < 3 * NPC ? dr[(size_t)(cc / 3) * HP] * (i == 0 ? wl0 : (i == 1 ? wl1 : wl2)) : 0.0f;
           }
           put16(r, 16 * c, REV_CB + 16 * c, v);
         }
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
               const int cc = 16 * c + jj;
-              v[jj] = cc < 3 * NPC ? dr[cc / 3] * v[jj] : 0.0f;
+              v[jj] = cc < 3 * NPC ? dr[(size_t)(cc / 3) * HP] * v[jj] : 0.0f;
             }
             put16(r, 16 * c, REV_CB + 16 * c, v);
           }

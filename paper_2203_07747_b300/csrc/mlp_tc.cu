@@ -119,9 +119,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- TMA producer
-    if (lane == 0) {
+    // ---------------- TMA producer (whole warp, one elected lane issues)
+    if (lane == 0)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    {
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -130,19 +131,22 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int mts = (l < nh) ? n_mt : 1;
           for (int m = 0; m < mts && ok; ++m)
             for (int kb = 0; kb < nkb && ok; ++kb) {
-              if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
-              mbar_expect_tx(full_bar(s), WT_BYTES);
+              if (!(ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
+              if (elect_one()) {
+                mbar_expect_tx(full_bar(s), WT_BYTES);
 #pragma unroll
-              for (int bx = 0; bx < W_BOXES; ++bx)
-                tma_load_2d(w_s + s * WT_BYTES + bx * 4096u, &tmap, kb * 64 + bx * W_BOX_K, l * HP + m * 128,
-                            full_bar(s));
+                for (int bx = 0; bx < W_BOXES; ++bx)
+                  tma_load_2d(w_s + s * WT_BYTES + bx * 4096u, &tmap, kb * 64 + bx * W_BOX_K,
+                              l * HP + m * 128, full_bar(s));
+              }
+              __syncwarp();
               if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
         }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
+    // ---------------- MMA issuer (whole warp, one elected lane issues)
+    {
       constexpr uint32_t idesc = idesc_bf16(128, NMMA) | (1u << 16);  // B is N-major
       const uint32_t lbo = CX * 16u;
       int s = 0;
@@ -150,15 +154,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       int it = 0;
       WaitClock wc(a.trace != nullptr && blockIdx.x == 0);
+      const bool tl = lane == 0;
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it)
         for (int l = 0; l < n_layers && ok; ++l) {
-          trace(a, it, l, n_layers, 0);
+          if (tl) trace(a, it, l, n_layers, 0);
           long long w_x = 0, w_w = 0, w_t = 0;
           const int mts = (l < nh) ? n_mt : 1;
           for (int m = 0; m < mts && ok; ++m) {
             if (used & (1u << m)) {
               wc.start();
-              ok = mbar_wait(tmem_free(m), (tf_par >> m) & 1u, abort_flag, a.err);
+              ok = mbar_wait_warp(tmem_free(m), (tf_par >> m) & 1u, abort_flag, a.err);
               wc.stop(w_t);
               if (!ok) break;
               tf_par ^= 1u << m;
@@ -170,14 +175,14 @@ __global__ void __launch_bounds__(THREADS, 1)
               const int j = kb >> 1;
               if (m == 0 && (kb & 1) == 0) {
                 wc.start();
-                ok = mbar_wait(xready(j), (xr_par >> j) & 1u, abort_flag, a.err);
+                ok = mbar_wait_warp(xready(j), (xr_par >> j) & 1u, abort_flag, a.err);
                 wc.stop(w_x);
                 if (!ok) break;
                 xr_par ^= 1u << j;
                 tc_fence_after();
               }
               wc.start();
-              ok = mbar_wait(full_bar(s), ph, abort_flag, a.err);
+              ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err);
               wc.stop(w_w);
               if (!ok) break;
               tc_fence_after();
@@ -186,20 +191,22 @@ __global__ void __launch_bounds__(THREADS, 1)
               for (int ks = 0; ks < 4; ++ks) {
                 const uint64_t ad = wdesc(as, ks);
                 const uint32_t bo = (uint32_t)(kb * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
-                mma_bf16(d, ad, xdesc(xhi_s + bo, lbo), idesc, (kb | ks) != 0);
-                if (MODE == 1) mma_bf16(d, ad, xdesc(xlo_s + bo, lbo), idesc, 1u);
+                mma_bf16_elect(d, ad, xdesc(xhi_s + bo, lbo), idesc, (kb | ks) != 0);
+                if (MODE == 1) mma_bf16_elect(d, ad, xdesc(xlo_s + bo, lbo), idesc, 1u);
               }
-              mma_commit(empty_bar(s));
+              mma_commit_elect(empty_bar(s));
               if (++s == STAGES) { s = 0; ph ^= 1u; }
               // the last M tile of the layer has read block j: it may be rewritten
-              if (m == mts - 1 && (kb & 1)) mma_commit(xfree(j));
+              if (m == mts - 1 && (kb & 1)) mma_commit_elect(xfree(j));
             }
-            if (ok) mma_commit(acc_full(m));
+            if (ok) mma_commit_elect(acc_full(m));
           }
-          trace(a, it, l, n_layers, 1);
-          trace_put(a, it, l, n_layers, 4, w_x);
-          trace_put(a, it, l, n_layers, 5, w_w);
-          trace_put(a, it, l, n_layers, 6, w_t);
+          if (tl) {
+            trace(a, it, l, n_layers, 1);
+            trace_put(a, it, l, n_layers, 4, w_x);
+            trace_put(a, it, l, n_layers, 5, w_w);
+            trace_put(a, it, l, n_layers, 6, w_t);
+          }
         }
     }
   } else {
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int i = 128 * j + (et & 127);
         float w[NZ];
 #pragma unroll
-        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)i * NZ + jj];
+        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)jj * HP + i];
         const float bi = a.b0[i];
 #pragma unroll
         for (int n = 0; n < NPC; ++n) {
@@ -514,7 +521,7 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
     const float* bl = hb.data() + net.b_off[l];
     if (l == 0) {
       for (int i = 0; i < fo; ++i) {
-        for (int j = 0; j < NZ; ++j) W0[(size_t)i * NZ + j] = Wl[(size_t)i * fi + j];
+        for (int j = 0; j < NZ; ++j) W0[(size_t)j * HP + i] = Wl[(size_t)i * fi + j];
         b0[i] = bl[i];
       }
     } else {

@@ -127,6 +127,13 @@ __device__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_
   return true;
 }
 
+// the same by every lane of a warp, warp-uniform result
+__device__ __forceinline__ bool mbar_wait_cl_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                  int* err) {
+  const bool ok = mbar_try_cl(bar, parity) || mbar_wait_cl(bar, parity, abort_flag, err);
+  return __all_sync(0xffffffffu, ok);
+}
+
 // weight half of this CTA, completing on the stage barrier of rank 0
 __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                                  uint32_t bar_cl) {
@@ -137,19 +144,22 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
       : "memory");
 }
 
+// issued by one elected lane of a converged warp
 __device__ __forceinline__ void mma2_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                           uint32_t accum) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
 }
 
-// arrive on the barrier at this offset in the CTAs of `mask` (bit r = rank r)
+// arrive on the barrier at this offset in the CTAs of `mask` (bit r = rank r);
+// one elected lane of a converged warp
 __device__ __forceinline__ void commit2(uint32_t bar, uint16_t mask) {
   asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+      "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}" ::"r"(
           bar),
       "h"(mask)
       : "memory");
@@ -307,9 +317,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
   const bool run = (*abort_flag == 0);
 
   if (run && warp == 0) {
-    // ---------------- TMA producer (both CTAs): this CTA's 128 rows of each 256-row tile
-    if (lane == 0) {
+    // ---------------- TMA producer (both CTAs; whole warp, one elected lane
+    // issues): this CTA's 128 rows of each 256-row tile
+    if (lane == 0)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    {
       const uint32_t full0 = mapa(full_bar(0), 0);  // stage barriers of rank 0
       int s = 0;
       uint32_t ph = 0;
@@ -319,30 +331,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
           const int mts = (l < nh) ? n_mt2 : 1;
           for (int m = 0; m < mts && ok; ++m)
             for (int kb = 0; kb < nkb && ok; ++kb) {
-              if (!(ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
-              // the output layer's rows 128..255 (rank 1's half) are padding
-              // whose products land in accumulator rows nobody reads: not loaded
-              const bool load = l < nh || rank == 0;
-              if (rank == 0) mbar_expect_tx(full_bar(s), (l < nh ? 2 : 1) * WT_BYTES);
-              const int kk = kb ^ 2;  // K order of the MMAs (blocks 1, 0, 3, 2)
-              if (load) {
+              if (!(ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
+              if (elect_one()) {
+                // the output layer's rows 128..255 (rank 1's half) are padding
+                // whose products land in accumulator rows nobody reads: not loaded
+                const bool load = l < nh || rank == 0;
+                if (rank == 0) mbar_expect_tx(full_bar(s), (l < nh ? 2 : 1) * WT_BYTES);
+                const int kk = kb ^ 2;  // K order of the MMAs (blocks 1, 0, 3, 2)
+                if (load) {
 #pragma unroll
-                for (int bx = 0; bx < W_BOXES; ++bx)
-                  tma_load_2d_pair(w_s + s * WT_BYTES + bx * 4096u, &tmap, kk * 64 + bx * W_BOX_K,
-                                   l * HP + m * 256 + (int)rank * 128, full0 + 8u * s);
+                  for (int bx = 0; bx < W_BOXES; ++bx)
+                    tma_load_2d_pair(w_s + s * WT_BYTES + bx * 4096u, &tmap, kk * 64 + bx * W_BOX_K,
+                                     l * HP + m * 256 + (int)rank * 128, full0 + 8u * s);
+                }
               }
+              __syncwarp();
               if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
         }
       // tail: every stage released, so no commit from the peer lands after exit
       for (int i = 0; i < STAGES && ok; ++i) {
-        ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, a.err);
+        ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err);
         if (++s == STAGES) { s = 0; ph ^= 1u; }
       }
     }
   } else if (run && warp == 1) {
-    if (lane == 0 && rank == 0) {
-      // ---------------- MMA issuer of the pair
+    if (rank == 0) {
+      // ---------------- MMA issuer of the pair (whole warp, one elected lane issues)
       constexpr uint32_t idesc = idesc_bf16(256, NMMA) | (1u << 16);  // B is N-major
       const uint32_t lbo = C * 16u;
       int s = 0;
@@ -351,9 +366,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
       int it = 0;
       WaitClock wc(a.trace != nullptr && blockIdx.x == 0);
       long long w_odd = 0, w_even = 0;
+      const bool tl = lane == 0;
       for (int tile = pair; tile < n_tiles && ok; tile += n_pairs, ++it)
         for (int l = 0; l < n_layers && ok; ++l) {
-          trace(a, it, l, n_layers, 0);
+          if (tl) trace(a, it, l, n_layers, 0);
           long long w_x = 0, w_w = 0, w_t = 0;
           const int mts = (l < nh) ? n_mt2 : 1;
           for (int m = 0; m < mts && ok; ++m) {
@@ -362,7 +378,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             const int slot = (l < nh) ? m : 1;
             if (used & (1u << slot)) {
               wc.start();
-              ok = mbar_wait_cl(tmem_free(slot), (tf_par >> slot) & 1u, abort_flag, a.err);
+              ok = mbar_wait_cl_warp(tmem_free(slot), (tf_par >> slot) & 1u, abort_flag, a.err);
               wc.stop(w_t);
               if (!ok) break;
               tf_par ^= 1u << slot;
@@ -379,10 +395,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 long long w0 = w_x;
                 wc.start();
                 if (l == 0) {  // the input layer's blocks
-                  ok = mbar_wait_cl(xin(j), (xi_par >> j) & 1u, abort_flag, a.err);
+                  ok = mbar_wait_cl_warp(xin(j), (xi_par >> j) & 1u, abort_flag, a.err);
                   xi_par ^= 1u << j;
                 } else {
-                  ok = mbar_wait_cl(xready(j), (xr_par >> j) & 1u, abort_flag, a.err);
+                  ok = mbar_wait_cl_warp(xready(j), (xr_par >> j) & 1u, abort_flag, a.err);
                   xr_par ^= 1u << j;
                 }
                 wc.stop(w_x);
@@ -391,7 +407,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 tc_fence_after();
               }
               wc.start();
-              ok = mbar_wait(full_bar(s), ph, abort_flag, a.err);
+              ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err);
               wc.stop(w_w);
               if (!ok) break;
               tc_fence_after();
@@ -408,13 +424,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             }
             if (ok) commit2(acc_full(slot), 3);
           }
-          trace(a, it, l, n_layers, 1);
-          trace_put(a, it, l, n_layers, 4, w_x);
-          trace_put(a, it, l, n_layers, 5, w_w);
-          trace_put(a, it, l, n_layers, 6, w_t);
+          if (tl) {
+            trace(a, it, l, n_layers, 1);
+            trace_put(a, it, l, n_layers, 4, w_x);
+            trace_put(a, it, l, n_layers, 5, w_w);
+            trace_put(a, it, l, n_layers, 6, w_t);
+          }
           if (l == n_layers - 1) {
-            trace_put(a, it, n_layers, n_layers, 6, w_odd);
-            trace_put(a, it, n_layers, n_layers, 7, w_even);
+            if (tl) {
+              trace_put(a, it, n_layers, n_layers, 6, w_odd);
+              trace_put(a, it, n_layers, n_layers, 7, w_even);
+            }
             w_odd = w_even = 0;
           }
         }
@@ -528,7 +548,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
         const int i = 128 * j + (et & 127);
         float w[NZ];
 #pragma unroll
-        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)i * NZ + jj];
+        for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)jj * HP + i];
         const float bi = a.b0[i];
         // the previous tile's output layer has read block j
         if (it_ > 0 && !wwait(xfree(j), (uint32_t)(n_layers * it_ - 1) & 1u)) return false;

@@ -28,7 +28,7 @@ struct TcArgs {
   const float* u;
   const int* node_inst;
   int n_nodes;
-  const float* W0;    // [HP][17] FP32 input layer
+  const float* W0;    // [17][HP] FP32 input layer (transposed)
   const float* b0;    // [HP]
   const float* bias;  // [n_hidden_mm * HP + 128]
   int HP;
@@ -81,6 +81,16 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     }
   }
   return true;
+}
+
+// bounded wait by every lane of a warp, warp-uniform result.  The issuing
+// roles (TMA producer, MMA issuer) run as whole warps and issue from one
+// elected lane: their loop values stay warp-uniform, and a phase that has
+// already completed costs one try_wait and a vote.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                               int* err) {
+  const bool ok = mbar_try(bar, parity) || mbar_wait(bar, parity, abort_flag, err);
+  return __all_sync(0xffffffffu, ok);
 }
 
 __device__ __forceinline__ unsigned long long gtime() {
@@ -160,6 +170,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
+}
+
+// the same, issued by one elected lane of a converged warp
+__device__ __forceinline__ void mma_bf16_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_elect(uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
+      : "memory");
+}
+
+// one elected lane of a converged warp: true on exactly one lane
+__device__ __forceinline__ bool elect_one() {
+  uint32_t e;
+  asm volatile("{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(e));
+  return e != 0;
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
