@@ -476,7 +476,7 @@ def main():
     out = ctl.linearize(x, u)
     ms_lin = time_calls(lambda: ctl.linearize(x, u, out), max(5, args.steps))
     ms_mlp = time_calls(lambda: ctl.mlp_eval(x, u, out[0], out[1]), max(5, args.steps))
-    rev = cfg.get("tile", {}).get("operand_mode") == 4
+    rev = cfg.get("tile", {}).get("operand_mode") in (4, 5)  # reverse mode (one CTA / CTA pairs)
     flops = (rev_flops_per_node(widths) if rev else fwd_flops_per_node(widths)) * nn
     if prec == "fp32":
         roof = {"bound": "alu", "peak": 148 * 128 * 2 * 2.032e9 / 1e12,

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     : a.u[(size_t)node * NU + (j - NX)];
     };
     // the tile's inputs z (NPC x 17 values, up to two per epilogue thread)
-    static_assert(NZV <= 512, "z staging");
+    static_assert(NZV <= 512 && NPC <= 32, "z staging");
     float zpref[2];
     auto prefetch_z = [&](int tile) {
 #pragma unroll
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       zr_ph ^= 1u;
 #pragma unroll
       for (int h = 0; h < 2; ++h)
-        if (et + 256 * h < NZV) zbuf[et + 256 * h] = zpref[h];
+        if (et + 256 * h < NZV) zbuf[((et + 256 * h) / NZ) * ZS + (et + 256 * h) % NZ] = zpref[h];
       __syncwarp();
       if (lane == 0) mbar_arrive(z_full);
       if (!wwait(z_full, zf_par)) return false;
@@ -358,22 +358,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)jj * HP + r];
         const float bi = a.b0[r];
+        // nodes 16 half + t in batched phases
         float v[16];
-        float* dr = dptr(0, r);
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int n = 16 * half + jj;
-          v[jj] = 0.0f;
-          if (n < NPC) {
-            float s = bi;
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) s = fmaf(w[k], zbuf[n * NZ + k], s);
-            const bool real = node0 + n < a.n_nodes;
-            const float av = real ? tanhf(s) : 0.0f;
-            dr[(size_t)n * HP] = real ? 1.0f - av * av : 0.0f;
-            v[jj] = av;
-          }
-        }
+        for (int g8 = 0; g8 < 2; ++g8) dot17_x8(w, zbuf, 16 * half + 8 * g8, NPC, bi, v + 8 * g8);
+        tanh_batch<16>(v);
+        act_finish<16>(v, dptr(0, r) + (size_t)16 * half * HP, HP, min(NPC, a.n_nodes - node0) - 16 * half,
+                       NPC - 16 * half);
         put16(r, 16 * half, REV_CF + 16 * half, v);
         publish(m);
       }
@@ -391,26 +382,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int g = 0; g < nh && ok; ++g) {
         mark(it, g, 2);
         for (int m = 0; m < n_mt; ++m) {
+          const int r = 128 * m + 32 * q + lane;
+          const float bi = a.bias[(size_t)g * HP + r];  // before the waits
           if (!(ok = take_acc(m))) break;
           if (!(ok = take_block(m))) break;
-          const int r = 128 * m + 32 * q + lane;
-          const float bi = a.bias[(size_t)g * HP + r];
           const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * REV_CX);
           float v[16];
           acc16(trow + 16 * half, REV_CF, v);
           release_tmem(m);
-          float* dr = dptr(g + 1, r);
+          // nodes 16 half + t in batched phases
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int n = 16 * half + jj;
-            float av = 0.0f;
-            if (n < NPC) {
-              const bool real = node0 + n < a.n_nodes;
-              av = real ? tanhf(v[jj] + bi) : 0.0f;
-              dr[(size_t)n * HP] = real ? 1.0f - av * av : 0.0f;
-            }
-            v[jj] = av;
-          }
+          for (int t = 0; t < 16; ++t) v[t] += bi;
+          tanh_batch<16>(v);
+          act_finish<16>(v, dptr(g + 1, r) + (size_t)16 * half * HP, HP,
+                         min(NPC, a.n_nodes - node0) - 16 * half, NPC - 16 * half);
           put16(r, 16 * half, REV_CF + 16 * half, v);
           publish(m);
         }
@@ -512,17 +497,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         mark(it, n_gemm - 1, 2);
         if (!(ok = take_acc(slot))) break;
         if (q == 0) {
+          // column cc = 3 n + i is row (node0 + n) * 3 + i of J_D: entry
+          // (3 node0 + cc) * 17 + lane; columns of real nodes end at `lim`
+          const int lim = 3 * min(NPC, a.n_nodes - node0) - 32 * half;
+          float* jrow = a.JD + ((size_t)node0 * NO + 32 * half) * NZ + lane;
 #pragma unroll
           for (int c2 = 0; c2 < 2; ++c2) {
-            const int c = 2 * half + c2;
             float v[16];
-            acc16(tmem + (uint32_t)(slot * REV_CX) + 16 * c, REV_CB, v);
+            acc16(tmem + (uint32_t)(slot * REV_CX) + 16 * (2 * half + c2), REV_CB, v);
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int cc = 16 * c + jj, n = cc / 3, i = cc % 3, node = node0 + n;
-              if (cc < 3 * NPC && lane < NZ && node < a.n_nodes)
-                a.JD[((size_t)node * NO + i) * NZ + lane] = v[jj];
-            }
+            for (int jj = 0; jj < 16; ++jj)
+              if (16 * c2 + jj < lim && lane < NZ) jrow[(16 * c2 + jj) * NZ] = v[jj];
           }
         }
         release_tmem(slot);

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int jj = 0; jj < NZ; ++jj) s = fmaf(w[jj], zbuf[n * NZ + jj], s);
           const bool real = node0 + n < a.n_nodes;
-          const float av = real ? tanhf(s) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
+          const float av = real ? tanh_tc(s) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
           NodeOut o;
           node_pack<MODE>(av, d, w, w[16], o);
           node_store<NPC, C, MODE>(X, xbytes, i, n, o);
@@ -369,16 +369,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 struct Variant {
   int npc;
   int mode;  // 0 single, 1 split (two MMAs), 2 split (hi|lo along N), 3 split on a CTA pair,
-             // 4 split, reverse mode (value forward, three adjoints backward)
+             // 4 split, reverse mode (value forward, three adjoints backward),
+             // 5 split, reverse mode on a CTA pair
   int stages;
   const void* fn;
   bool split() const { return mode != 0; }
-  bool pair() const { return mode == 3; }
-  bool rev() const { return mode == 4; }
+  bool pair() const { return mode == 3 || mode == 5; }
+  bool rev() const { return mode == 4 || mode == 5; }
   int threads() const { return pair() ? THREADS + 32 : THREADS; }
   int cols() const { return rev() ? 128 : 16 * npc + ((2 * npc + 15) / 16) * 16; }
   // tensor-memory columns of one accumulator tile (128 rows; 256 rows on a pair)
-  int tmem_per_mtile() const { return rev() ? 128 : (mode >= 2 ? 2 * cols() : cols()); }
+  int tmem_per_mtile() const { return mode == 5 ? 256 : rev() ? 128 : (mode >= 2 ? 2 * cols() : cols()); }
   int rows_per_mtile() const { return pair() ? 256 : 128; }
   // accumulator columns: one slot per M tile (a pair always has two slots:
   // its output layer accumulates in the second)
@@ -386,9 +387,10 @@ struct Variant {
     return (pair() ? std::max(2, HP / 256) : HP / 128) * tmem_per_mtile();
   }
   size_t smem(int HP) const {
+    if (mode == 5) return mlp_rev2_smem(HP, stages);
     if (rev())
       return 1024 + (size_t)128 * HP * 2 + (size_t)stages * WT_BYTES + 8 * (2 * stages + 20) + 16 +
-             (size_t)npc * NZ * 4;
+             (size_t)npc * ZS * 4;
     if (pair())
       return 1024 + (size_t)cols() * HP * 2 + (size_t)cols() * 256 + (size_t)stages * WT_BYTES +
              8 * (2 * stages + 24) + 16 + (size_t)npc * NZ * 4;
@@ -412,6 +414,11 @@ Variant rev_variant() {
   return Variant{NPC, 4, STAGES, mlp_rev_fn(NPC, STAGES)};
 }
 
+template <int STAGES>
+Variant rev2_variant() {
+  return Variant{42, 5, STAGES, mlp_rev2_fn(42, STAGES)};
+}
+
 // every compiled tile shape; the autotuner times those that fit
 const std::vector<Variant>& all_variants() {
   static const std::vector<Variant> v = {
@@ -420,7 +427,7 @@ const std::vector<Variant>& all_variants() {
       variant<5, 1, 6>(),  variant<4, 1, 3>(),  variant<3, 1, 6>(),  variant<7, 2, 5>(),
       variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>(),  pair_variant<7, 4>(),
       pair_variant<6, 5>(), pair_variant<7, 8>(), pair_variant<4, 6>(), rev_variant<21, 6>(),
-      rev_variant<21, 4>(), rev_variant<16, 6>()};
+      rev_variant<21, 4>(), rev_variant<16, 6>(), rev2_variant<3>(), rev2_variant<6>()};
   return v;
 }
 
@@ -430,7 +437,9 @@ bool fits(const Variant& v, int HP) {
 }
 
 // default before autotuning: with split operands the reverse-mode tile (the
-// fewest MMAs per node); otherwise the widest tile that still leaves >= 3 stages
+// fewest MMAs per node; on CTA pairs from hidden width 512, where a single
+// CTA's MMAs are bound by shared-memory bytes); otherwise the widest tile that
+// still leaves >= 3 stages
 int default_variant(int HP, bool split) {
   const auto& vs = all_variants();
   int best = -1;
@@ -439,8 +448,8 @@ int default_variant(int HP, bool split) {
     // reverse mode first, then the widest MMA (fewest instructions per
     // column), then one CTA before a pair, then the most columns
     auto key = [&](const Variant& v) {
-      return (v.rev() ? 100000000 : 0) + v.tmem_per_mtile() * 10000 + (v.pair() ? 0 : 5000) +
-             v.cols() * 10 + v.npc;
+      const int rank = v.mode == 5 ? (HP >= 512 ? 3 : 1) : v.mode == 4 ? 2 : 0;
+      return rank * 100000000 + v.tmem_per_mtile() * 10000 + (v.pair() ? 0 : 5000) + v.cols() * 10 + v.npc;
     };
     if (best < 0 || key(vs[i]) > key(vs[best])) best = i;
   }
@@ -635,6 +644,7 @@ cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* 
   void* args[] = {(void*)map, (void*)&a};
   const int n_tiles = (a.n_nodes + tc.npc - 1) / tc.npc;
   const Variant& v = all_variants()[tc.variant];
+  if (v.mode == 5) return mlp_rev2_launch(ctx, x, u, fD, JD);
   if (v.rev()) return mlp_rev_launch(ctx, x, u, fD, JD);
   dim3 grid = v.pair() ? dim3(2 * std::min(n_tiles, std::max(1, tc.n_sm / 2)))
                        : dim3(std::min(n_tiles, std::max(1, tc.n_sm)));

@@ -44,131 +44,10 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "tc_common.cuh"
+#include "tc_pair.cuh"
 
 namespace rtn {
 namespace {
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// shared::cluster address of `addr` (a shared::cta address) in CTA `rank`
-__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
-
-__device__ __forceinline__ void arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
-}
-
-// arrival without ordering of earlier stores (tensor-memory release: the
-// loads have completed at tcgen05.wait::ld)
-__device__ __forceinline__ void arrive_cluster_relaxed(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
-}
-
-// arrival that also announces `bytes` of a bulk copy completing on the barrier
-__device__ __forceinline__ void arrive_expect_tx_cluster(uint32_t cluster_addr, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(
-                   cluster_addr),
-               "r"(bytes)
-               : "memory");
-}
-
-// the same without ordering earlier stores (announces bytes only)
-__device__ __forceinline__ void arrive_expect_tx_cluster_relaxed(uint32_t cluster_addr, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.relaxed.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(
-                   cluster_addr),
-               "r"(bytes)
-               : "memory");
-}
-
-// shared::cta -> peer shared memory, complete_tx on a barrier of the peer
-__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst_cl, uint32_t src, uint32_t bytes,
-                                                  uint32_t bar_cl) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst_cl),
-      "r"(src), "r"(bytes), "r"(bar_cl)
-      : "memory");
-}
-
-
-__device__ __forceinline__ uint32_t mbar_try_cl(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok;
-}
-
-// bounded wait with cluster-scope acquire
-__device__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
-  long long t0 = clock64();
-  while (!mbar_try_cl(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
-      *abort_flag = 1;
-      atomicExch(err, (int)RTN_E_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-
-// the same by every lane of a warp, warp-uniform result
-__device__ __forceinline__ bool mbar_wait_cl_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                                  int* err) {
-  const bool ok = mbar_try_cl(bar, parity) || mbar_wait_cl(bar, parity, abort_flag, err);
-  return __all_sync(0xffffffffu, ok);
-}
-
-// weight half of this CTA, completing on the stage barrier of rank 0
-__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                                 uint32_t bar_cl) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar_cl)
-      : "memory");
-}
-
-// issued by one elected lane of a converged warp
-__device__ __forceinline__ void mma2_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
-      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-// arrive on the barrier at this offset in the CTAs of `mask` (bit r = rank r);
-// one elected lane of a converged warp
-__device__ __forceinline__ void commit2(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
-      "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}" ::"r"(
-          bar),
-      "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
 
 // the peer's half of nodes N0..N1-1 for one row, held in registers until
 // the staging block is free (hi halves on rank 1, lo halves on rank 0)
@@ -559,7 +438,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
 #pragma unroll
           for (int jj = 0; jj < NZ; ++jj) sacc = fmaf(w[jj], zbuf[n * NZ + jj], sacc);
           const bool real = node0 + n < a.n_nodes;
-          const float av = real ? tanhf(sacc) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
+          const float av = real ? tanh_tc(sacc) : 0.0f, d = real ? 1.0f - av * av : 0.0f;
           NodeOut o;
           node_pack<1>(av, d, w, w[16], o);
           node_store_own<NPC, C>(X, lo_local, i, n, o);

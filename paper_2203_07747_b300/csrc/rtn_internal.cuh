@@ -146,6 +146,10 @@ const void* mlp_tc2_fn(int npc, int stages);
 const void* mlp_rev_fn(int npc, int stages);
 // arguments of the reverse-mode kernel (mlp_rev.cu)
 cudaError_t mlp_rev_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+// the reverse-mode kernel on CTA pairs (mlp_rev2.cu)
+const void* mlp_rev2_fn(int npc, int stages);
+size_t mlp_rev2_smem(int HP, int stages);
+cudaError_t mlp_rev2_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,

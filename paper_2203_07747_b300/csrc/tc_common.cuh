@@ -69,10 +69,27 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
   return ok;
 }
 
+// try_wait that may suspend the thread for up to `ns` nanoseconds; the
+// thread resumes when the phase completes
+__device__ __forceinline__ uint32_t mbar_try_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok;
+}
+
+constexpr uint32_t WAIT_SLEEP_NS = 2000;  // longest suspension per try
+
 // bounded wait by one thread; false on timeout or when another role aborted
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
-  long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_sleep(bar, parity, WAIT_SLEEP_NS)) {
     if (*abort_flag) return false;
     if (clock64() - t0 > WAIT_CYCLES) {
       *abort_flag = 1;
@@ -233,6 +250,81 @@ __device__ __forceinline__ void tmem_wait_ld() {
 __device__ __forceinline__ uint64_t xdesc(uint32_t saddr, uint32_t lbo) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
          ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// staged node inputs z: rows of ZS floats (17 used), 16-byte aligned, so
+// that a dot product reads them four at a time
+constexpr int ZS = 20;
+
+// b + w . z for one node's staged row (k = 0..16 in order)
+__device__ __forceinline__ float dot17(const float* w, const float* zrow, float b) {
+  const float4* z4 = reinterpret_cast<const float4*>(zrow);
+  float s = b;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float4 v = z4[c];
+    s = fmaf(w[4 * c], v.x, s);
+    s = fmaf(w[4 * c + 1], v.y, s);
+    s = fmaf(w[4 * c + 2], v.z, s);
+    s = fmaf(w[4 * c + 3], v.w, s);
+  }
+  return fmaf(w[16], zrow[16], s);
+}
+
+// tanh x = 1 - 2 / (exp(2x) + 1) with the fast exponential and division
+// intrinsics: absolute error ~1e-7 (saturates to +-1), far below the 2^-17
+// relative error of the split BF16 operands the result feeds
+__device__ __forceinline__ float tanh_tc(float x) {
+  return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f);
+}
+
+// tanh_tc of N values in phases (all exponentials, then all reciprocals), so
+// that the N dependency chains overlap
+template <int N>
+__device__ __forceinline__ void tanh_batch(float (&v)[N]) {
+#pragma unroll
+  for (int t = 0; t < N; ++t) v[t] = __expf(2.0f * v[t]);
+#pragma unroll
+  for (int t = 0; t < N; ++t) v[t] = 1.0f - __fdividef(2.0f, v[t] + 1.0f);
+}
+
+// activations of N nodes of one row: nodes t >= n_real (past the last node)
+// become 0; d = 1 - a^2 of nodes t < n_store to d_row[t * stride] (if given)
+template <int N>
+__device__ __forceinline__ void act_finish(float (&a)[N], float* d_row, int stride, int n_real, int n_store) {
+#pragma unroll
+  for (int t = 0; t < N; ++t) a[t] = t < n_real ? a[t] : 0.0f;
+  if (d_row) {
+#pragma unroll
+    for (int t = 0; t < N; ++t)
+      if (t < n_store) d_row[(size_t)t * stride] = t < n_real ? 1.0f - a[t] * a[t] : 0.0f;
+  }
+}
+
+// b + w . z for the 8 nodes n0 .. n0 + 7 of the staged rows zbuf (ZS floats
+// apart, rows 0 .. n_rows - 1 exist; a node past them reads the last row and
+// its sum is not used), the 8 sums side by side
+__device__ __forceinline__ void dot17_x8(const float* w, const float* zbuf, int n0, int n_rows, float b,
+                                         float* out) {
+  const float* zr[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) zr[t] = zbuf + min(n0 + t, n_rows - 1) * ZS;
+  float s[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) s[t] = b;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const float4 v = reinterpret_cast<const float4*>(zr[t])[c];
+      s[t] = fmaf(w[4 * c], v.x, s[t]);
+      s[t] = fmaf(w[4 * c + 1], v.y, s[t]);
+      s[t] = fmaf(w[4 * c + 2], v.z, s[t]);
+      s[t] = fmaf(w[4 * c + 3], v.w, s[t]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) out[t] = fmaf(w[16], zr[t][16], s[t]);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo_col, float hi_col) {
@@ -438,7 +530,7 @@ __device__ __forceinline__ void epilogue_nodes(uint32_t trow, float bias, Store&
     if (n + 1 < N1) nxt.issue(trow + 16 * (n + 1));
     float t[16];
     cur.sum(t);
-    const float av = tanhf(tl[n] + bias), d = 1.0f - av * av;
+    const float av = tanh_tc(tl[n] + bias), d = 1.0f - av * av;
     NodeOut o;
     node_pack<MODE == 0 ? 0 : 1>(av, d, t, tl[NPC + n], o);
     store(n, o);
