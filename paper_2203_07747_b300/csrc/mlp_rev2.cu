@@ -30,7 +30,11 @@
 // holds); the producer writes its own half into its X, stages the peer's half
 // and pushes it with a bulk copy that completes on a barrier of the peer; the
 // exchange warps relay the completion and free the staging block.  The input
-// layer (FP32, 17 inputs) needs no exchange: both CTAs compute every row.
+// layer (FP32 dot products over the 17 inputs) is exchanged the same way:
+// each CTA computes the rows of its own blocks for every node.  The
+// last-layer adjoints (one product per value) are not exchanged: each CTA
+// computes its own half for every row, after a cluster-scope barrier has made
+// the peer's d_L visible; all 16 epilogue warps publish on rank 0's xin[j].
 // The notice that the MMAs have read block j (xfree) reaches both CTAs once
 // per GEMM; every wait on it names its completion by the GEMM count.
 // Every wait is bounded (RTN_E_TIMEOUT in the device flag).
@@ -137,7 +141,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
   auto xin = [&](int j) { return bar_s + 8u * (2 * STAGES + 2 * MT + 3 * NB + j); };
   const uint32_t s_full = bar_s + 8u * (2 * STAGES + 2 * MT + 4 * NB);
   const uint32_t s_free = s_full + 8u, z_full = s_full + 16u, z_free = s_full + 24u;
-  const uint32_t fwd_done = s_full + 32u, bwd_done = s_full + 40u;
+  const uint32_t d_ready = s_full + 32u, bwd_done = s_full + 40u;
   constexpr int NBAR = 2 * STAGES + 2 * MT + 4 * NB + 6;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail_area + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -167,8 +171,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
     mbar_init(s_free, 1);
     mbar_init(z_full, EPI_WARPS);
     mbar_init(z_free, EPI_WARPS);
-    mbar_init(fwd_done, EPI_WARPS);
     mbar_init(bwd_done, EPI_WARPS);
+    mbar_init(d_ready, 2 * EPI_WARPS);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -277,7 +281,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
               const int kk = (kb % nkb) ^ 2, j = kk >> 1;
               if (m == 0 && kb < nkb && (kb & 1) == 0) {
                 wc.start();
-                if (g == 0) {  // the input layer's blocks
+                if (g == nh + 1) {  // the last-layer adjoints (both CTAs publish on xin)
                   ok = mbar_wait_cl_warp(xin(j), (xi_par >> j) & 1u, abort_flag, a.err);
                   xi_par ^= 1u << j;
                 } else {
@@ -317,8 +321,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
   } else if (run && warp == THREADS / 32) {
     if (lane == 0) {
       // ---------------- exchange warp: the exchanged blocks of every tile
-      // (nh forward layers, the last-layer adjoints, nh backward layers), in
-      // the order their producers publish them
+      // (the input layer, nh forward layers, nh backward layers), in the
+      // order their producers publish them
       const uint32_t xr0 = mapa(xready(0), 0);
       const uint32_t sfree_peer = mapa(s_free, rank ^ 1u);
       uint32_t par = 0;
@@ -364,10 +368,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
       }
     };
     if (pair < n_tiles) prefetch_z(pair);
-    uint32_t acc_par = 0, sf_ph = 0, ss_par = 0, zf_par = 0, zr_ph = 0, fd_par = 0, bd_par = 0;
+    uint32_t acc_par = 0, sf_ph = 0, ss_par = 0, zf_par = 0, zr_ph = 0, dr_par = 0, bd_par = 0;
     bool ok = true;
     const uint32_t tf0 = mapa(tmem_free(0), 0);
     const uint32_t xr0 = mapa(xready(0), 0), lo1 = mapa(lo_in(0), 1), xi0 = mapa(xin(0), 0);
+    const uint32_t dr0 = mapa(d_ready, 0), dr1 = mapa(d_ready, 1);
     // xfree[j] completes once per GEMM: completion c (from 1) of the pair's
     // tile it, GEMM g is c = n_gemm it + g + 1; wait parity (c - 1) & 1
     auto xfree_par = [&](int it_, int g) -> uint32_t { return (uint32_t)(n_gemm * it_ + g) & 1u; };
@@ -439,16 +444,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
       return tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(slot * 256);
     };
 
-    // input layer (FP32): this CTA computes every row and keeps its own half
-    // of the value columns (forward layout); d_1 of the rows it owns to the
-    // scratch.  Blocks in the order the MMAs read them (1, 0, 3, 2).
+    // input layer (FP32): a_1 = tanh(W_0 z + b_0) for the rows of this CTA's
+    // blocks (j = 2 m + rank) and the nodes of this warp half; d_1 to the
+    // scratch, own half into X (forward layout), the peer's half staged
     auto input_layer = [&](int tile, int it_) -> bool {
-      const int node0 = tile * NPC;
+      const int node0 = tile * NPC, nb = 24 * half;
       mark(it_, n_gemm, 2);
-      // W_0 row and bias of the first block (1, then 0, 3, 2), before the waits
+      // W_0 row and bias of M tile 0, before the waits
       float w[NZ], bi;
       {
-        const int i = 128 * 1 + (et & 127);
+        const int i = 128 * (int)rank + 32 * q + lane;
 #pragma unroll
         for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)jj * HP + i];
         bi = a.b0[i];
@@ -471,42 +476,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
         for (int jj = 0; jj < nblk; ++jj)
           if (!wwait(xfree(jj), (uint32_t)(n_gemm * it_ - 1) & 1u)) return false;
       }
-      const int hh = et >> 7, nb = 24 * hh;  // nodes nb .. nb + 23 (< NPC)
-      for (int jb = 0; jb < nblk; ++jb) {
-        const int j = jb ^ 1;
-        const int i = 128 * j + (et & 127);
-        const bool own_rows = (j & 1) == (int)rank;
+      for (int m = 0; m < n_mt2; ++m) {
+        const int j = 2 * m + (int)rank;
+        const int i = 128 * j + 32 * q + lane;
         float av[24];
 #pragma unroll
         for (int g8 = 0; g8 < 3; ++g8) dot17_x8(w, zbuf, nb + 8 * g8, NPC, bi, av + 8 * g8);
+        if (m + 1 < n_mt2) {  // the next M tile's W_0 row and bias
+#pragma unroll
+          for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)jj * HP + i + 256];
+          bi = a.b0[i + 256];
+        }
         tanh_batch<24>(av);
-        act_finish<24>(av, own_rows ? dptr(0, i) + (size_t)nb * HP : nullptr, HP, min(NPC, a.n_nodes - node0) - nb,
-                       NPC - nb);
-        uint32_t o[12];
+        act_finish<24>(av, dptr(0, i) + (size_t)nb * HP, HP, min(NPC, a.n_nodes - node0) - nb, NPC - nb);
+        uint32_t own[12], peer[12];
 #pragma unroll
         for (int p = 0; p < 12; ++p) {
           uint32_t hv, lv;
           split2(av[2 * p], av[2 * p + 1], hv, lv);
-          o[p] = lo_local ? lv : hv;
+          own[p] = lo_local ? lv : hv;
+          peer[p] = lo_local ? hv : lv;
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           *reinterpret_cast<uint4*>(X + xoff_n(R2_CF, i, nb + 8 * c)) =
-              make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
-        if (jb + 1 < nblk) {  // the next block's W_0 row and bias
-          const int i2 = 128 * ((jb + 1) ^ 1) + (et & 127);
+              make_uint4(own[4 * c], own[4 * c + 1], own[4 * c + 2], own[4 * c + 3]);
+        if (!wait_staging()) return false;
 #pragma unroll
-          for (int jj = 0; jj < NZ; ++jj) w[jj] = a.W0[(size_t)jj * HP + i2];
-          bi = a.b0[i2];
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) {
-          if (rank == 0)
-            mbar_arrive(xin(j));
-          else
-            arrive_cluster(xi0 + 8u * j);
-        }
+        for (int c = 0; c < 3; ++c)
+          *reinterpret_cast<uint4*>(S + xoff_n(R2_CF, i & 127, nb + 8 * c)) =
+              make_uint4(peer[4 * c], peer[4 * c + 1], peer[4 * c + 2], peer[4 * c + 3]);
+        if (!block_end(j, 128u * R2_CF * 2u)) return false;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(z_free);
@@ -644,51 +644,80 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
       for (int k = 0; k < 22; ++k) dd[k] = n0 + k < NPC ? dr[(size_t)(n0 + k) * HP] : 0.0f;
     };
 
-    // adjoints of the last hidden layer: D_L = d_L (.) W_L' (no accumulator)
+    // adjoints of the last hidden layer, D_L = d_L (.) W_L' (no accumulator,
+    // no exchange): this CTA writes its own half (hi or lo) of the 64 columns
+    // of this warp half for every row; blocks in the MMAs' order (1, 0, 3, 2)
     auto dl_init = [&](int it_) -> bool {
       mark(it_, n_gemm, 0);
-      const int i0 = 128 * (int)rank + 32 * q + lane;  // row of M tile 0; + 256 m
-      float wl[2][3];
+      const int cb = 64 * half;
+      // W_L columns of this thread's rows in every block (MMA order 1, 0, 3, 2)
+      float wl[NB][3];
 #pragma unroll
-      for (int m = 0; m < 2; ++m)
+      for (int jb = 0; jb < NB; ++jb)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) wl[m][k] = m < n_mt2 ? a.WL[(size_t)k * HP + i0 + 256 * m] : 0.0f;
-      // every warp has written its d of this tile
+        for (int k = 0; k < 3; ++k)
+          wl[jb][k] = jb < nblk ? a.WL[(size_t)k * HP + 128 * (jb ^ 1) + 32 * q + lane] : 0.0f;
+      // every epilogue warp of both CTAs has written its d_L of this tile
+      stamp(it_, nh, 0, 0);
       __syncwarp();
-      if (lane == 0) mbar_arrive(fwd_done);
-      if (!wwait(fwd_done, fd_par)) return false;
-      fd_par ^= 1u;
-      float dd0[22];
-      load_d(nh, i0, dd0);  // M tile 0's d, before the waits below
-      // the output layer's MMAs have read every block (the layouts switch)
-      for (int jj = 0; jj < nblk; ++jj)
-        if (!wwait(xfree(jj), xfree_par(it_, nh))) return false;
-      for (int m = 0; m < n_mt2; ++m) {
-        const int j = 2 * m + (int)rank;
+      if (lane == 0) {
+        arrive_cluster(dr0);
+        arrive_cluster(dr1);
+      }
+      {
+        int w_ok = 0;
+        if (lane == 0) w_ok = mbar_wait_cl(d_ready, dr_par, abort_flag, a.err);
+        if (!__shfl_sync(0xffffffffu, w_ok, 0)) return false;
+        __syncwarp();
+        dr_par ^= 1u;
+      }
+      stamp(it_, nh, 0, 1);
+      float dn[22];  // d of the next block, loaded one block ahead
+      load_d(nh, 128 * 1 + 32 * q + lane, dn);
+      for (int jb = 0; jb < nblk; ++jb) {
+        const int j = jb ^ 1;
         const int i = 128 * j + 32 * q + lane;
         float dd[22];
-        if (m == 0) {
 #pragma unroll
-          for (int k = 0; k < 22; ++k) dd[k] = dd0[k];
-        } else {
-          load_d(nh, i, dd);
+        for (int k = 0; k < 22; ++k) dd[k] = dn[k];
+        if (jb + 1 < nblk) load_d(nh, 128 * ((jb + 1) ^ 1) + 32 * q + lane, dn);
+        float wlj[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) wlj[k] = jb == 0 ? wl[0][k] : jb == 1 ? wl[1][k] : jb == 2 ? wl[2][k] : wl[3][k];
+        // the output layer's MMAs have read every block (the layouts switch)
+        if (jb == 0) {
+          for (int jj = 0; jj < nblk; ++jj)
+            if (!wwait(xfree(jj), xfree_par(it_, nh))) return false;
+          stamp(it_, nh, 0, 2);
         }
-        uint32_t peer[32];
 #pragma unroll
-        for (int c2 = 0; c2 < 4; ++c2) {
-          float v[16];
+        for (int c2 = 0; c2 < 8; ++c2) {
+          uint32_t own[4];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int c = 16 * c2 + k;
-            const float w0 = m ? wl[1][c % 3] : wl[0][c % 3];
-            const float w1 = m ? wl[1][(c + 1) % 3] : wl[0][(c + 1) % 3];
-            const float p0 = dd[c / 3] * w0;                             // half 0
-            const float p1 = c < 62 ? dd[(c + 1) / 3] * w1 : 0.0f;  // half 1
-            v[k] = half ? p1 : p0;
+          for (int p = 0; p < 4; ++p) {
+            float v2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int c = 8 * c2 + 2 * p + h;  // column within the half
+              const float p0 = dd[c / 3] * wlj[c % 3];                             // half 0
+              const float p1 = c < 62 ? dd[(c + 1) / 3] * wlj[(c + 1) % 3] : 0.0f;  // half 1
+              v2[h] = half ? p1 : p0;
+            }
+            uint32_t hv, lv;
+            split2(v2[0], v2[1], hv, lv);
+            own[p] = lo_local ? lv : hv;
           }
-          bwd_chunk(i, c2, v, peer);
+          *reinterpret_cast<uint4*>(X + xoff_n(R2_CB, i, cb + 8 * c2)) = make_uint4(own[0], own[1], own[2], own[3]);
         }
-        if (!bwd_flush(j, i, peer)) return false;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (rank == 0)
+            mbar_arrive(xin(j));
+          else
+            arrive_cluster(xi0 + 8u * j);
+        }
+        stamp(it_, nh, 0, 3 + jb);
       }
       mark(it_, n_gemm, 1);
       ew = 0;
@@ -702,12 +731,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
       for (int m = 0; m < n_mt2; ++m) {
         const int j = 2 * m + (int)rank;
         const int i = 128 * j + 32 * q + lane;
+        stamp(it_, g, m, 0);
         float dd[22];
         load_d(l - 1, i, dd);  // issued before the waits
         if (!wwait(acc_full(m), (acc_par >> m) & 1u)) return false;
         acc_par ^= 1u << m;
         tc_fence_after();
+        stamp(it_, g, m, 1);
         if (!wwait(xfree(j), xfree_par(it_, g))) return false;
+        stamp(it_, g, m, 2);
         const uint32_t tr_ = trow_of(m) + (uint32_t)(64 * half);
         uint32_t peer[32];
 #pragma unroll
@@ -727,7 +759,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) arrive_cluster_relaxed(tf0 + 8u * m);
+        stamp(it_, g, m, 3);
         if (!bwd_flush(j, i, peer)) return false;
+        stamp(it_, g, m, 7);
       }
       mark_end(it_, g);
       return true;
@@ -768,8 +802,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
     for (int tile = pair; tile < n_tiles && ok; tile += n_pairs, ++it) {
       const int node0 = tile * NPC;
       for (int g = 0; g < nh && ok; ++g) ok = fwd_layer(it, g, node0);
-      if (ok) ok = out_layer(it, node0);
+      // the last-layer adjoints while the output layer's MMAs run; f_D after
+      // them (the first backward GEMM's second M tile reuses that slot)
       if (ok) ok = dl_init(it);
+      if (ok) ok = out_layer(it, node0);
       if (ok && nh == 0) {
         __syncwarp();
         if (lane == 0) mbar_arrive(bwd_done);

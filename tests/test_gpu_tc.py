@@ -155,3 +155,39 @@ def test_cfg3_error_table_against_oracle(rtn, orc):
     _, rJm, _, _, _ = orc.linearize(QUAD, master, N, dt, X, U)
     em = _rel_rows(JDm.double().cpu().numpy(), rJm, 1e-12)
     assert np.isfinite(em).all() and em.max() < 5e-2, em.max()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("widths", [[17, 512, 512, 512, 3], [17, 512, 3], [17, 256, 256, 3]])
+def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
+    # reverse-mode shapes (one CTA: 21 nodes per tile; CTA pairs: 42) with
+    # several tiles per CTA or pair and a ragged tail: f_D and J_D of sampled
+    # nodes against the oracle, every node finite
+    layers = [(Wl, W.round_bf16(np.random.default_rng(40 + i).normal(0, 0.05, bl.shape)))
+              for i, (Wl, bl) in enumerate(W.xavier_mlp(widths, 7, bf16=True))]
+    N = np.array([20] * 400 + [13], np.int32)  # 8013 nodes
+    ctl = rtn.Controller(N, np.full(len(N), 0.05), W.Q_DIAG, W.R_DIAG, quad=QUAD, layers=layers,
+                         precision="bf16x2")
+    X, U = W.random_nodes(ctl.n_states, 9)
+    X = X.astype(np.float32).astype(np.float64)
+    U = U[:ctl.n_nodes].astype(np.float32).astype(np.float64)
+    inst = np.repeat(np.arange(len(N)), N)
+    idx = np.concatenate([np.random.default_rng(2).choice(ctl.n_nodes - 1, 40, replace=False),
+                          np.arange(ctl.n_nodes - 45, ctl.n_nodes)])
+    ref = [orc.mlp_fwd_jac(layers, np.concatenate([X[n + inst[n]], U[n]])) for n in idx]
+    xd = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    ud = torch.as_tensor(U, dtype=torch.float32, device="cuda")
+    seen = set()
+    for vi, npc, mode, stages in ctl.tc_variants():
+        if mode not in (4, 5):
+            continue
+        seen.add(mode)
+        ctl.tc_select(vi)
+        fD, JD = ctl.mlp_eval(xd, ud)
+        assert ctl.device_error() == 0
+        F, J = fD.double().cpu().numpy(), JD.double().cpu().numpy()
+        assert np.isfinite(F).all() and np.isfinite(J).all()
+        ej = max(np.linalg.norm(J[n] - r[1]) / np.linalg.norm(r[1]) for n, r in zip(idx, ref))
+        ef = max(np.abs(F[n] - r[0]).max() / max(np.abs(r[0]).max(), 1e-3) for n, r in zip(idx, ref))
+        assert ej < 1e-3 and ef < 1e-3, (vi, npc, mode, stages, ej, ef)
+    assert 4 in seen and (5 in seen or widths[1] < 256)
