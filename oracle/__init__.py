@@ -259,6 +259,47 @@ def rti_step_box(quad, layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=Tru
     return u0, x, u, st, its
 
 
+def di_rk4_lin(x, u, dt, fbar=None, J=None):
+    """Double integrator (Sec. IV): RK4 of f_F + f_D* with sensitivities.
+    Returns (phi [2], A [2][2], B [2])."""
+    x, px = _d(x)
+    phi = np.zeros(2); A = np.zeros((2, 2)); B = np.zeros(2)
+    if fbar is None:
+        pf = pJ = None
+    else:
+        fb, pf = _d(np.atleast_1d(fbar)); Jd, pJ = _d(J)
+    lib().orc_di_rk4_lin(px, C.c_double(float(u)), pf, pJ, C.c_double(float(dt)), _p(phi), _p(A), _p(B))
+    return phi, A, B
+
+
+def di_linearize(layers, N, dt, x, u):
+    """Double integrator, every node: fD [n], JD [n][3], A [n][2][2], B [n][2], c [n][2]."""
+    m = _MLP(layers or [])
+    N, pN = _i(N); dt, pdt = _d(dt)
+    x, px = _d(x); u, pu = _d(u)
+    n = int(N.sum())
+    fD = np.zeros(n); JD = np.zeros((n, 3))
+    A = np.zeros((n, 2, 2)); B = np.zeros((n, 2)); c = np.zeros((n, 2))
+    lib().orc_di_linearize(m.nl, m.pw, m.pp, len(N), pN, pdt, px, pu, _p(fD), _p(JD), _p(A), _p(B),
+                           _p(c))
+    return fD, JD, A, B, c
+
+
+def di_rti_step(layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=True):
+    """Double integrator RTI step.  x [n_states][2], u [n_nodes], xref, uref
+    likewise, x0m [B][2].  Returns (u0 [B], x_new, u_new, status [B])."""
+    m = _MLP(layers or [])
+    N, pN = _i(N); dt, pdt = _d(dt)
+    x = np.array(x, dtype=np.float64, copy=True); u = np.array(u, dtype=np.float64, copy=True)
+    args = [_d(a) for a in (Q, R, QN)]
+    xref, pxr = _d(xref); uref, pur = _d(uref); x0m, px0 = _d(x0m)
+    Bn = len(N)
+    u0 = np.zeros(Bn); st = np.zeros(Bn, np.int32)
+    lib().orc_di_rti_step(m.nl, m.pw, m.pp, Bn, pN, pdt, args[0][1], args[1][1], args[2][1], _p(x),
+                          _p(u), pxr, pur, px0, int(shift), _p(u0), st.ctypes.data_as(C.POINTER(C.c_int)))
+    return u0, x, u, st
+
+
 def closed_loop(quad, layers, plant_kind, plant_layers, N, dt, Q, R, QN, x0, xrt, urt, steps,
                 box=False, max_iter=20):
     """Returns traj [steps][B][13] and u0 history [steps][B][4]."""

@@ -931,6 +931,118 @@ void orc_closed_loop_box(const orc_quad* Qd, int nl, const int* w, const double*
                    steps, traj, u0_hist, 1, max_iter);
 }
 
+/* ---------------------------------------------------- double integrator --- */
+/* Runtime-analysis model (Sec. IV, Eq. 5): x = (p, v), u the commanded
+ * acceleration, f_F = (v, u).  The residual network maps z = (p, v, u) to one
+ * output added to dv/dt; f_D* is its first-order local model around the
+ * node (Eq. 4).  RK4 (u held) with the sensitivity S = d(stage)/d[x; u]
+ * (2 x 3) through the four stages; fbar/J may be NULL (nominal model). */
+void orc_di_rk4_lin(const double* x, double u, const double* fbar, const double* J, double dt,
+                    double* phi, double* A, double* B) {
+  double k[4][2], dk[4][6], xs[2], S[6];
+  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+  /* D = d f / d[p, v, u]: f_F contributes (v, u), f_D* its Jacobian row */
+  double D[6] = {0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
+  if (fbar)
+    for (int j = 0; j < 3; ++j) D[3 + j] += J[j];
+  for (int s = 0; s < 4; ++s) {
+    for (int i = 0; i < 2; ++i) xs[i] = x[i] + (s ? cst[s] * dt * k[s - 1][i] : 0.0);
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j)
+        S[i * 3 + j] = ((i == j) ? 1.0 : 0.0) + (s ? cst[s] * dt * dk[s - 1][i * 3 + j] : 0.0);
+    k[s][0] = xs[1];
+    k[s][1] = u;
+    if (fbar) k[s][1] += fbar[0] + J[0] * (xs[0] - x[0]) + J[1] * (xs[1] - x[1]);
+    /* d k_s / d[x; u] = D_x S + D_u [0 0 1] */
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double sum = (j == 2) ? D[i * 3 + 2] : 0.0;
+        for (int l = 0; l < 2; ++l) sum += D[i * 3 + l] * S[l * 3 + j];
+        dk[s][i * 3 + j] = sum;
+      }
+  }
+  for (int i = 0; i < 2; ++i) {
+    phi[i] = x[i] + dt / 6.0 * (k[0][i] + 2.0 * k[1][i] + 2.0 * k[2][i] + k[3][i]);
+    for (int j = 0; j < 3; ++j) {
+      double v = ((i == j) ? 1.0 : 0.0) +
+                 dt / 6.0 * (dk[0][i * 3 + j] + 2.0 * dk[1][i * 3 + j] + 2.0 * dk[2][i * 3 + j] +
+                             dk[3][i * 3 + j]);
+      if (j < 2) A[i * 2 + j] = v;
+      else B[i] = v;
+    }
+  }
+}
+
+/* Linearise every node of the double integrator (nl = 0: no network):
+ * fD [n_nodes], JD [n_nodes][3], A [n_nodes][2][2], Bm [n_nodes][2], c =
+ * phi_k - x_{k+1} [n_nodes][2].  Layout as orc_linearize with nx = 2, nu = 1. */
+void orc_di_linearize(int nl, const int* w, const double* P, int B, const int* N, const double* dt,
+                      const double* x, const double* u, double* fD, double* JD, double* A,
+                      double* Bm, double* c) {
+  size_t xs = 0, us = 0;
+  for (int b = 0; b < B; ++b) {
+    for (int k = 0; k < N[b]; ++k) {
+      const double* xk = x + (xs + k) * 2;
+      const double uk = u[us + k];
+      double f = 0.0, J[3] = {0.0, 0.0, 0.0}, phi[2];
+      if (nl > 0) {
+        const double z[3] = {xk[0], xk[1], uk};
+        orc_mlp_fwd_jac(nl, w, P, z, &f, J);
+      }
+      orc_di_rk4_lin(xk, uk, nl > 0 ? &f : NULL, J, dt[b], phi, A + (us + k) * 4, Bm + (us + k) * 2);
+      for (int i = 0; i < 2; ++i) c[(us + k) * 2 + i] = phi[i] - xk[2 + i];
+      if (fD) fD[us + k] = f;
+      if (JD)
+        for (int j = 0; j < 3; ++j) JD[(us + k) * 3 + j] = J[j];
+    }
+    xs += N[b] + 1;
+    us += N[b];
+  }
+}
+
+/* One RTI step of the double integrator for every instance: linearise
+ * around the iterate, solve the QP (orc_riccati, nx = 2, nu = 1) with the
+ * measured x0, update the iterate (w += dw), send u_0 (this model has no
+ * input bounds), then optionally shift.  status[b] = 0 ok, 4 not positive
+ * definite (iterate untouched, u0 = uref). */
+void orc_di_rti_step(int nl, const int* w, const double* P, int B, const int* N, const double* dt,
+                     const double* Q, const double* R, const double* QN, double* x, double* u,
+                     const double* xref, const double* uref, const double* x0m, int shift,
+                     double* u0, int* status) {
+  size_t nn = 0;
+  for (int b = 0; b < B; ++b) nn += N[b];
+  double* A = (double*)malloc(sizeof(double) * nn * 4);
+  double* Bm = (double*)malloc(sizeof(double) * nn * 2);
+  double* c = (double*)malloc(sizeof(double) * nn * 2);
+  orc_di_linearize(nl, w, P, B, N, dt, x, u, NULL, NULL, A, Bm, c);
+  size_t xs = 0, us = 0;
+  for (int b = 0; b < B; ++b) {
+    const int Nb = N[b];
+    double* xb = x + xs * 2;
+    double* ub = u + us;
+    double* dx = (double*)malloc(sizeof(double) * (Nb + 1) * 2);
+    double* du = (double*)malloc(sizeof(double) * Nb);
+    int st = orc_riccati(2, 1, Nb, A + us * 4, Bm + us * 2, c + us * 2, xb, ub, xref + xs * 2,
+                         uref + us, Q, R, QN, x0m + b * 2, dx, du, NULL, NULL);
+    status[b] = st;
+    if (st == 0) {
+      for (int i = 0; i < (Nb + 1) * 2; ++i) xb[i] += dx[i];
+      for (int i = 0; i < Nb; ++i) ub[i] += du[i];
+      u0[b] = ub[0];
+      if (shift) {
+        for (int k = 0; k < Nb; ++k) memcpy(xb + k * 2, xb + (k + 1) * 2, sizeof(double) * 2);
+        for (int k = 0; k + 1 < Nb; ++k) ub[k] = ub[k + 1];
+      }
+    } else {
+      u0[b] = uref[us];
+    }
+    free(dx); free(du);
+    xs += Nb + 1;
+    us += Nb;
+  }
+  free(A); free(Bm); free(c);
+}
+
 /* ------------------------------------------------------------ training --- */
 
 /* Mean-squared-error loss over a batch, L = 1/(n * nout) sum |MLP(z) - y|^2,

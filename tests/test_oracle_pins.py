@@ -498,3 +498,129 @@ def test_box_qp_pins_exercise_the_bounds(orc):
         if ((np.abs(du - lb) < 1e-12) | (np.abs(du - ub) < 1e-12)).sum() >= 2 and its > 1:
             active += 1
     assert active >= 4, active
+
+
+# ------------------------------------ double integrator (Sec. IV runtime model)
+
+def _di_net(widths, seed, zero_out=False):
+    layers = W.xavier_mlp(widths, seed)
+    if zero_out:  # Sec. IV: weights set so that the network outputs zero
+        Wl, bl = layers[-1]
+        layers[-1] = (np.zeros_like(Wl), np.zeros_like(bl))
+    return layers
+
+
+def test_di_rk4_nominal_is_exact(orc):
+    # the double integrator's trajectory is quadratic in t: RK4 reproduces it
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        x, u, dt = rng.normal(0, 2, 2), rng.normal(0, 3), rng.uniform(0.01, 0.3)
+        phi, A, B = orc.di_rk4_lin(x, u, dt)
+        assert np.allclose(phi, [x[0] + x[1] * dt + u * dt * dt / 2, x[1] + u * dt], rtol=0, atol=1e-14)
+        assert np.allclose(A, [[1, dt], [0, 1]], rtol=0, atol=1e-15)
+        assert np.allclose(B, [dt * dt / 2, dt], rtol=0, atol=1e-15)
+
+
+def test_di_rk4_constant_residual_closed_form(orc):
+    # f_D* = constant c (zero Jacobian): the residual adds to the acceleration
+    x, u, dt, c = np.array([0.3, -1.2]), 0.7, 0.05, -2.5
+    phi, A, B = orc.di_rk4_lin(x, u, dt, fbar=c, J=np.zeros(3))
+    assert np.allclose(phi, [x[0] + x[1] * dt + (u + c) * dt * dt / 2, x[1] + (u + c) * dt], rtol=0, atol=1e-14)
+
+
+def test_di_rk4_sensitivities_vs_fd_and_order(orc):
+    # A, B against central differences of the RK4 map (the local model held
+    # fixed), and phi against the exact flow of the affine ODE (matrix
+    # exponential): the error falls as dt^5
+    from scipy.linalg import expm
+    rng = np.random.default_rng(5)
+    x, u = rng.normal(0, 1, 2), 0.4
+    fbar, J = 0.3, np.array([-1.5, -0.7, 0.2])
+    dt = 0.1
+    phi, A, B = orc.di_rk4_lin(x, u, dt, fbar=fbar, J=J)
+    h = 1e-6
+    for j in range(3):
+        xp, xm, up, um = x.copy(), x.copy(), u, u
+        if j < 2:
+            xp[j] += h; xm[j] -= h
+        else:
+            up += h; um -= h
+        # the local model's expansion point stays at (x, u)
+        def step(xx, uu):
+            ff = fbar + J[0] * (xx[0] - x[0]) + J[1] * (xx[1] - x[1]) + J[2] * (uu - u)
+            return orc.di_rk4_lin(xx, uu, dt, fbar=ff, J=J)[0]
+        col = (step(xp, up) - step(xm, um)) / (2 * h)
+        ref = A[:, j] if j < 2 else B
+        assert np.allclose(col, ref, rtol=0, atol=1e-8)
+    # exact flow of d/dt [p, v, 1] = M [p, v, 1]
+    M = np.array([[0.0, 1.0, 0.0],
+                  [J[0], J[1], u + fbar - J[0] * x[0] - J[1] * x[1]],
+                  [0.0, 0.0, 0.0]])
+    errs = []
+    for d in (0.2, 0.1, 0.05):
+        ex = (expm(M * d) @ np.array([x[0], x[1], 1.0]))[:2]
+        errs.append(np.abs(orc.di_rk4_lin(x, u, d, fbar=fbar, J=J)[0] - ex).max())
+    assert 24 < errs[0] / errs[1] < 40 and 24 < errs[1] / errs[2] < 40
+
+
+def test_di_zero_output_network_is_nominal(orc):
+    # Sec. IV: a network forced to output zero changes nothing
+    layers = _di_net([3, 32, 32, 1], 6, zero_out=True)
+    N = np.array([10, 7], np.int32); dt = np.array([0.05, 0.08])
+    rng = np.random.default_rng(7)
+    x = rng.normal(0, 1, (int(N.sum()) + len(N), 2)); u = rng.normal(0, 1, int(N.sum()))
+    fD, JD, A, B, c = orc.di_linearize(layers, N, dt, x, u)
+    assert np.all(fD == 0) and np.all(JD == 0)
+    _, _, A0, B0, c0 = orc.di_linearize(None, N, dt, x, u)
+    assert np.array_equal(A, A0) and np.array_equal(B, B0) and np.array_equal(c, c0)
+
+
+def test_di_network_jacobian_vs_fd(orc):
+    layers = _di_net([3, 16, 16, 1], 8)
+    z = np.array([0.4, -0.9, 1.3])
+    f, J = orc.mlp_fwd_jac(layers, z)
+    for j in range(3):
+        zp, zm = z.copy(), z.copy()
+        zp[j] += 1e-6; zm[j] -= 1e-6
+        assert abs((orc.mlp_forward(layers, zp) - orc.mlp_forward(layers, zm))[0] / 2e-6 - J[0, j]) < 1e-8
+
+
+def test_di_rti_step_is_the_kkt_solution(orc):
+    # the RTI update equals a dense KKT solve of the same linearised QP
+    layers = _di_net([3, 16, 16, 1], 9)
+    N = np.array([10, 6], np.int32); dt = np.array([0.05, 0.1])
+    rng = np.random.default_rng(10)
+    ns, nn = int(N.sum()) + len(N), int(N.sum())
+    x = rng.normal(0, 1, (ns, 2)); u = rng.normal(0, 1, nn)
+    xref = rng.normal(0, 1, (ns, 2)); uref = rng.normal(0, 0.5, nn)
+    x0m = rng.normal(0, 1, (len(N), 2))
+    Q, R, QN = np.array([10.0, 1.0]), np.array([0.1]), np.array([20.0, 2.0])
+    u0, xn, un, st = orc.di_rti_step(layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=False)
+    assert np.all(st == 0)
+    _, _, A, B, c = orc.di_linearize(layers, N, dt, x, u)
+    xs = us = 0
+    for b, Nb in enumerate(N):
+        s2, dx, du = orc.kkt_dense(A[us:us + Nb], B[us:us + Nb].reshape(Nb, 2, 1), c[us:us + Nb],
+                                   x[xs:xs + Nb + 1], u[us:us + Nb].reshape(Nb, 1), xref[xs:xs + Nb + 1],
+                                   uref[us:us + Nb].reshape(Nb, 1), Q, R, QN, x0m[b], nx=2, nu=1)
+        assert s2 == 0
+        assert np.allclose(xn[xs:xs + Nb + 1], x[xs:xs + Nb + 1] + dx, rtol=0, atol=1e-10)
+        assert np.allclose(un[us:us + Nb], u[us:us + Nb] + du[:, 0], rtol=0, atol=1e-10)
+        assert abs(u0[b] - un[us]) < 1e-15
+        xs += Nb + 1; us += Nb
+
+
+def test_di_long_horizon_gain_is_the_lqr_gain(orc):
+    # far from the end of a long horizon the Riccati gain is the
+    # infinite-horizon LQR gain of the discrete double integrator
+    from scipy.linalg import solve_discrete_are
+    dt, Nh = 0.1, 300
+    Ad = np.array([[1, dt], [0, 1]]); Bd = np.array([[dt * dt / 2], [dt]])
+    Q, R = np.array([4.0, 0.5]), np.array([0.2])
+    P = solve_discrete_are(Ad, Bd, np.diag(Q), np.diag(R))
+    K_lqr = -np.linalg.solve(np.diag(R) + Bd.T @ P @ Bd, Bd.T @ P @ Ad)
+    A = np.repeat(Ad[None], Nh, 0); B = np.repeat(Bd[None], Nh, 0); c = np.zeros((Nh, 2))
+    x = np.zeros((Nh + 1, 2)); u = np.zeros((Nh, 1))
+    st, dx, du, K, k = orc.riccati(A, B, c, x, u, x, u, Q, R, Q, np.array([1.0, 0.0]), nx=2, nu=1,
+                                   return_gains=True)
+    assert st == 0 and np.allclose(K[0], K_lqr, rtol=1e-9, atol=1e-12)
