@@ -390,3 +390,105 @@ class Controller:
             _ptr(x_plant, torch.float64, (self.B, NX), "x_plant"), _ptr(traj, f, None, "traj"),
             _ptr(uo, f, None, "u_out")), "rtn_closed_loop")
         return traj, uo
+
+
+class DIController:
+    """A batch of B controllers of the runtime-analysis model (Sec. IV): the
+    double integrator x = (p, v), u = acceleration, with an optional residual
+    network (p, v, u) -> 1 output added to dv/dt.  Same C ABI as Controller
+    (rtn_create with nx = 2, nu = 1); FP32 network, FP64 QP, no input bounds."""
+
+    def __init__(self, N, dt, Q, R, QN=None, layers=None, shift=True, stream=None):
+        import torch
+        L = load()
+        self.N = np.ascontiguousarray(N, dtype=np.int32)
+        self.dt = np.ascontiguousarray(dt, dtype=np.float64)
+        self.B = int(self.N.size)
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        QN = None if QN is None else np.ascontiguousarray(QN, dtype=np.float64)
+        self._keep = []
+        mlp_p = None
+        self.layers = layers
+        if layers:
+            widths = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
+            w = (C.c_int * len(widths))(*widths)
+            Ws = [np.ascontiguousarray(W, dtype=np.float32) for W, _ in layers]
+            bs = [np.ascontiguousarray(b, dtype=np.float32) for _, b in layers]
+            Wp = (C.POINTER(C.c_float) * len(Ws))(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in Ws])
+            bp = (C.POINTER(C.c_float) * len(bs))(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in bs])
+            self._keep += [w, Ws, bs, Wp, bp]
+            mlp = _MLP(len(layers), w, Wp, bp)
+            self._keep.append(mlp)
+            mlp_p = C.byref(mlp)
+        opt = _Opt(PRECISION["fp32"], 0, int(bool(shift)), 0, 0)
+        self.stream = stream
+        h = C.c_void_p()
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        st = L.rtn_create(C.byref(h), 2, 1, self.B, self.N.ctypes.data_as(C.POINTER(C.c_int)), dp(self.dt),
+                          dp(Q), dp(R), None if QN is None else dp(QN), None, mlp_p, C.byref(opt),
+                          _stream_handle(stream))
+        if st != 0:
+            raise RtnError(f"rtn_create: {STATUS.get(st, st)}: {L.rtn_last_error(None).decode()}")
+        self._h = h
+        nn, ns = C.c_int(), C.c_int()
+        L.rtn_sizes(h, C.byref(nn), C.byref(ns))
+        self.n_nodes, self.n_states = nn.value, ns.value
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    close = Controller.close
+    __del__ = Controller.__del__
+    _check = Controller._check
+    _empty = Controller._empty
+
+    def reset(self, x0):
+        import torch
+        self._check(load().rtn_reset(self._h, _ptr(x0, torch.float32, (self.B, 2), "x0")), "rtn_reset")
+
+    def set_iterate(self, x, u):
+        import torch
+        self._check(load().rtn_set_iterate(self._h, _ptr(x, torch.float32, (self.n_states, 2), "x"),
+                                           _ptr(u, torch.float32, (self.n_nodes,), "u")), "rtn_set_iterate")
+
+    def get_iterate(self):
+        x, u = self._empty(self.n_states, 2), self._empty(self.n_nodes)
+        import torch
+        self._check(load().rtn_get_iterate(self._h, _ptr(x, torch.float32, None, "x"),
+                                           _ptr(u, torch.float32, None, "u")), "rtn_get_iterate")
+        return x, u
+
+    def mlp_eval(self, x, u, fD=None, JD=None):
+        """Network value [n_nodes] and Jacobian [n_nodes][3] at every node."""
+        import torch
+        n = self.n_nodes
+        fD = self._empty(n) if fD is None else fD
+        JD = self._empty(n, 3) if JD is None else JD
+        self._check(load().rtn_mlp_eval(self._h, _ptr(x, torch.float32, (self.n_states, 2), "x"),
+                                        _ptr(u, torch.float32, (n,), "u"), _ptr(fD, torch.float32, (n,), "fD"),
+                                        _ptr(JD, torch.float32, (n, 3), "JD")), "rtn_mlp_eval")
+        return fD, JD
+
+    def linearize(self, x, u):
+        """(fD [n], JD [n][3], A [n][2][2], B [n][2], c [n][2]) at every node."""
+        import torch
+        n = self.n_nodes
+        fD, JD = self._empty(n), self._empty(n, 3)
+        A, Bm, c = self._empty(n, 2, 2), self._empty(n, 2), self._empty(n, 2)
+        f = torch.float32
+        self._check(load().rtn_linearize(
+            self._h, _ptr(x, f, (self.n_states, 2), "x"), _ptr(u, f, (n,), "u"), _ptr(fD, f, (n,), "fD"),
+            _ptr(JD, f, (n, 3), "JD"), _ptr(A, f, (n, 2, 2), "A"), _ptr(Bm, f, (n, 2), "B"),
+            _ptr(c, f, (n, 2), "c")), "rtn_linearize")
+        return fD, JD, A, Bm, c
+
+    def rti_step(self, x0, xref, uref, u0=None, status=None):
+        """One RTI step of every instance: returns (u0 [B], status [B])."""
+        import torch
+        f = torch.float32
+        u0 = self._empty(self.B) if u0 is None else u0
+        status = self._empty(self.B, dtype=torch.int32) if status is None else status
+        self._check(load().rtn_rti_step(
+            self._h, _ptr(x0, f, (self.B, 2), "x0"), _ptr(xref, f, (self.n_states, 2), "xref"),
+            _ptr(uref, f, (self.n_nodes,), "uref"), _ptr(u0, f, (self.B,), "u0"),
+            _ptr(status, torch.int32, (self.B,), "status")), "rtn_rti_step")
+        return u0, status

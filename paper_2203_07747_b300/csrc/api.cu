@@ -111,6 +111,97 @@ rtn_status rti_impl(rtn_ctx* ctx, const float* x0, const float* xref, const floa
   return RTN_OK;
 }
 
+// ragged node-packed layout of the batch (both models)
+rtn_status make_layout(rtn_ctx* ctx, int batch, const int* N, const double* dt) {
+  Layout& L = ctx->lay;
+  L.B = batch;
+  std::vector<int> xoff(batch), uoff(batch), order(batch), node_inst;
+  std::vector<float> dtf(batch);
+  int xs = 0, us = 0;
+  for (int b = 0; b < batch; ++b) {
+    xoff[b] = xs; uoff[b] = us;
+    xs += N[b] + 1; us += N[b];
+    dtf[b] = (float)dt[b];
+    L.N_max = std::max(L.N_max, N[b]);
+  }
+  L.n_nodes = us; L.n_states = xs;
+  node_inst.resize(us);
+  for (int b = 0; b < batch; ++b)
+    for (int k = 0; k < N[b]; ++k) node_inst[uoff[b] + k] = b;
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return N[a] > N[c]; });
+  CK(upload(&L.N, N, batch));
+  CK(upload(&L.dt, dtf.data(), batch));
+  CK(upload(&L.dt64, dt, batch));
+  CK(upload(&L.xoff, xoff.data(), batch));
+  CK(upload(&L.uoff, uoff.data(), batch));
+  CK(upload(&L.node_inst, node_inst.data(), us));
+  CK(upload(&L.order, order.data(), batch));
+  return RTN_OK;
+}
+
+// double-integrator context (nx = 2, nu = 1): the runtime-analysis model of
+// Sec. IV; network z = (p, v, u) -> 1 output, FP32 only, no input bounds
+rtn_status create_di(rtn_ctx* ctx, int batch, const int* N, const double* dt, const double* Q,
+                     const double* R, const double* Q_N, const rtn_mlp* mlp, const rtn_options& o,
+                     void* cuda_stream) {
+  ctx->B = batch;
+  ctx->nx = 2;
+  ctx->nu = 1;
+  ctx->opt = o;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->hN.assign(N, N + batch);
+  ctx->hdt.assign(dt, dt + batch);
+  ctx->di = new (std::nothrow) DiState();
+  if (!ctx->di) return fail(ctx, RTN_E_NOMEM, "out of host memory");
+  DiState& D = *ctx->di;
+  for (int i = 0; i < 2; ++i) {
+    D.Q[i] = Q[i];
+    D.QN[i] = Q_N ? Q_N[i] : Q[i];
+  }
+  D.R = R[0];
+  rtn_status st = make_layout(ctx, batch, N, dt);
+  if (st != RTN_OK) return st;
+  const int us = ctx->lay.n_nodes, xs = ctx->lay.n_states;
+  if (mlp) {
+    ctx->has_mlp = true;
+    D.n_layers = mlp->n_layers;
+    D.widths.assign(mlp->widths, mlp->widths + mlp->n_layers + 1);
+    std::vector<float> Wh, bh;
+    for (int l = 0; l < D.n_layers; ++l) {
+      const int fi = D.widths[l], fo = D.widths[l + 1];
+      D.w_off.push_back(Wh.size());
+      D.b_off.push_back(bh.size());
+      Wh.insert(Wh.end(), mlp->W[l], mlp->W[l] + (size_t)fo * fi);
+      bh.insert(bh.end(), mlp->b[l], mlp->b[l] + fo);
+      D.h_max = std::max(D.h_max, std::max(fi, fo));
+    }
+    CK(upload(&D.W, Wh.data(), Wh.size()));
+    CK(upload(&D.b, bh.data(), bh.size()));
+    const size_t na = (size_t)4 * D.h_max * us;
+    CK(dalloc(&D.act0, na));
+    CK(dalloc(&D.act1, na));
+  }
+  CK(dalloc(&ctx->x, (size_t)xs * 2));
+  CK(dalloc(&ctx->u, (size_t)us));
+  CK(dalloc(&ctx->fD, (size_t)us));
+  CK(dalloc(&ctx->JD, (size_t)us * 3));
+  CK(dalloc(&D.K, (size_t)us * 2));
+  CK(dalloc(&D.kff, (size_t)us));
+  CK(dalloc(&ctx->status, batch));
+  CK(dalloc(&ctx->x0f, (size_t)batch * 2));
+  CK(dalloc(&ctx->u0, (size_t)batch));
+  CK(cudaMemset(ctx->x0f, 0, sizeof(float) * batch * 2));
+  CK(di_reset(ctx, ctx->x0f));
+  CK(cudaDeviceSynchronize());
+  return RTN_OK;
+}
+
+// entry points that the double-integrator model does not provide
+rtn_status di_unsupported(rtn_ctx* ctx, const char* what) {
+  return fail(ctx, RTN_E_UNSUPPORTED, std::string(what) + ": not available for the double-integrator model");
+}
+
 }  // namespace
 
 extern "C" {
@@ -120,8 +211,12 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
                       const rtn_mlp* mlp, const rtn_options* opt, void* cuda_stream) {
   if (!out) return RTN_E_INVAL;
   *out = nullptr;
-  if (nx != NX || nu != NU) { g_create_err = "nx must be 13 and nu 4"; return RTN_E_INVAL; }
-  if (batch < 1 || !N || !dt || !Q || !R || !quad) { g_create_err = "bad batch/arrays"; return RTN_E_INVAL; }
+  const bool di = nx == 2 && nu == 1;
+  if (!di && (nx != NX || nu != NU)) {
+    g_create_err = "nx, nu must be 13, 4 (quadrotor) or 2, 1 (double integrator)";
+    return RTN_E_INVAL;
+  }
+  if (batch < 1 || !N || !dt || !Q || !R || (!di && !quad)) { g_create_err = "bad batch/arrays"; return RTN_E_INVAL; }
   long long nn = 0;
   for (int b = 0; b < batch; ++b) {
     if (N[b] < 1 || !(dt[b] > 0.0)) { g_create_err = "N[b] >= 1 and dt[b] > 0 required"; return RTN_E_INVAL; }
@@ -134,6 +229,31 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
   if (o.box_max_iter < 0) { g_create_err = "box_max_iter must be >= 0"; return RTN_E_INVAL; }
   if (o.box_max_iter == 0) o.box_max_iter = 20;
   o.box_qp = o.box_qp ? 1 : 0;
+  if (di) {
+    if (o.precision != RTN_FP32 || o.box_qp || o.riccati_f64) {
+      g_create_err = "the double-integrator model runs the FP32 network path and an FP64 QP only";
+      return RTN_E_UNSUPPORTED;
+    }
+    if (mlp) {
+      if (mlp->n_layers < 2 || !mlp->widths || !mlp->W || !mlp->b || mlp->widths[0] != 3 ||
+          mlp->widths[mlp->n_layers] != 1) {
+        g_create_err = "double-integrator network must map 3 inputs (p, v, u) to 1 output with >= 1 hidden layer";
+        return RTN_E_INVAL;
+      }
+      for (int l = 1; l < mlp->n_layers; ++l)
+        if (mlp->widths[l] < 1 || mlp->widths[l] > 65536) { g_create_err = "bad hidden width"; return RTN_E_INVAL; }
+    }
+    rtn_ctx* ctx = new (std::nothrow) rtn_ctx();
+    if (!ctx) return RTN_E_NOMEM;
+    rtn_status st = create_di(ctx, batch, N, dt, Q, R, Q_N, mlp, o, cuda_stream);
+    if (st != RTN_OK) {
+      g_create_err = ctx->err;
+      rtn_destroy(ctx);
+      return st;
+    }
+    *out = ctx;
+    return RTN_OK;
+  }
   if (mlp) {
     if (mlp->n_layers < 2 || !mlp->widths || !mlp->W || !mlp->b || mlp->widths[0] != NZ ||
         mlp->widths[mlp->n_layers] != NO) {
@@ -167,29 +287,9 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
 
     // ragged layout
     Layout& L = ctx->lay;
-    L.B = batch;
-    std::vector<int> xoff(batch), uoff(batch), order(batch), node_inst;
-    std::vector<float> dtf(batch);
-    int xs = 0, us = 0;
-    for (int b = 0; b < batch; ++b) {
-      xoff[b] = xs; uoff[b] = us;
-      xs += N[b] + 1; us += N[b];
-      dtf[b] = (float)dt[b];
-      L.N_max = std::max(L.N_max, N[b]);
-    }
-    L.n_nodes = us; L.n_states = xs;
-    node_inst.resize(us);
-    for (int b = 0; b < batch; ++b)
-      for (int k = 0; k < N[b]; ++k) node_inst[uoff[b] + k] = b;
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return N[a] > N[c]; });
-    CK(upload(&L.N, N, batch));
-    CK(upload(&L.dt, dtf.data(), batch));
-    CK(upload(&L.dt64, dt, batch));
-    CK(upload(&L.xoff, xoff.data(), batch));
-    CK(upload(&L.uoff, uoff.data(), batch));
-    CK(upload(&L.node_inst, node_inst.data(), us));
-    CK(upload(&L.order, order.data(), batch));
+    rtn_status lst = make_layout(ctx, batch, N, dt);
+    if (lst != RTN_OK) return lst;
+    const int xs = L.n_states, us = L.n_nodes;
 
     // network
     if (mlp) {
@@ -282,6 +382,12 @@ void rtn_destroy(rtn_ctx* ctx) {
                   ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (ctx->di) {
+    void* dp[] = {ctx->di->W, ctx->di->b, ctx->di->act0, ctx->di->act1, ctx->di->K, ctx->di->kff};
+    for (void* p : dp)
+      if (p) cudaFree(p);
+    delete ctx->di;
+  }
   mlp_tc_release(ctx);
   train_release(ctx);
   delete ctx;
@@ -311,6 +417,10 @@ rtn_status rtn_sizes(const rtn_ctx* ctx, int* n_nodes, int* n_states) {
 rtn_status rtn_reset(rtn_ctx* ctx, const float* x0) {
   if (!ctx) return RTN_E_INVAL;
   if (!x0) return fail(ctx, RTN_E_INVAL, "rtn_reset: NULL argument");
+  if (ctx->di) {
+    CK(di_reset(ctx, x0));
+    return RTN_OK;
+  }
   reset_kernel<<<ctx->B, 128, 0, ctx->stream>>>(x0, ctx->lay.N, ctx->lay.xoff, ctx->lay.uoff,
                                                  ctx->B, ctx->quad.hover, ctx->x, ctx->u);
   CK(cudaGetLastError());
@@ -320,9 +430,9 @@ rtn_status rtn_reset(rtn_ctx* ctx, const float* x0) {
 rtn_status rtn_set_iterate(rtn_ctx* ctx, const float* x, const float* u) {
   if (!ctx) return RTN_E_INVAL;
   if (!x || !u) return fail(ctx, RTN_E_INVAL, "rtn_set_iterate: NULL argument");
-  CK(cudaMemcpyAsync(ctx->x, x, (size_t)ctx->lay.n_states * NX * sizeof(float),
+  CK(cudaMemcpyAsync(ctx->x, x, (size_t)ctx->lay.n_states * ctx->nx * sizeof(float),
                      cudaMemcpyDeviceToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->u, u, (size_t)ctx->lay.n_nodes * NU * sizeof(float),
+  CK(cudaMemcpyAsync(ctx->u, u, (size_t)ctx->lay.n_nodes * ctx->nu * sizeof(float),
                      cudaMemcpyDeviceToDevice, ctx->stream));
   return RTN_OK;
 }
@@ -330,9 +440,9 @@ rtn_status rtn_set_iterate(rtn_ctx* ctx, const float* x, const float* u) {
 rtn_status rtn_get_iterate(rtn_ctx* ctx, float* x, float* u) {
   if (!ctx) return RTN_E_INVAL;
   if (!x || !u) return fail(ctx, RTN_E_INVAL, "rtn_get_iterate: NULL argument");
-  CK(cudaMemcpyAsync(x, ctx->x, (size_t)ctx->lay.n_states * NX * sizeof(float),
+  CK(cudaMemcpyAsync(x, ctx->x, (size_t)ctx->lay.n_states * ctx->nx * sizeof(float),
                      cudaMemcpyDeviceToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(u, ctx->u, (size_t)ctx->lay.n_nodes * NU * sizeof(float),
+  CK(cudaMemcpyAsync(u, ctx->u, (size_t)ctx->lay.n_nodes * ctx->nu * sizeof(float),
                      cudaMemcpyDeviceToDevice, ctx->stream));
   return RTN_OK;
 }
@@ -341,6 +451,10 @@ rtn_status rtn_mlp_eval(rtn_ctx* ctx, const float* x, const float* u, float* fD,
   if (!ctx) return RTN_E_INVAL;
   if (!x || !u || !fD || !JD) return fail(ctx, RTN_E_INVAL, "rtn_mlp_eval: NULL argument");
   if (!ctx->has_mlp) return fail(ctx, RTN_E_UNSUPPORTED, "rtn_mlp_eval: no network");
+  if (ctx->di) {
+    CK(di_mlp(ctx, x, u, fD, JD));
+    return RTN_OK;
+  }
   return run_mlp(ctx, x, u, fD, JD);
 }
 
@@ -348,6 +462,13 @@ rtn_status rtn_linearize(rtn_ctx* ctx, const float* x, const float* u, float* fD
                          float* A, float* B, float* c) {
   if (!ctx) return RTN_E_INVAL;
   if (!x || !u || !A || !B || !c) return fail(ctx, RTN_E_INVAL, "rtn_linearize: NULL argument");
+  if (ctx->di) {
+    float* f = fD ? fD : ctx->fD;
+    float* J = JD ? JD : ctx->JD;
+    if (ctx->has_mlp) CK(di_mlp(ctx, x, u, f, J));
+    CK(di_linearize(ctx, x, u, ctx->has_mlp ? f : nullptr, J, A, B, c));
+    return RTN_OK;
+  }
   return linearize_impl(ctx, x, u, fD ? fD : ctx->fD, JD ? JD : ctx->JD, A, B, c);
 }
 
@@ -357,6 +478,7 @@ rtn_status rtn_qp_solve(rtn_ctx* ctx, const float* A, const float* B, const floa
   if (!ctx) return RTN_E_INVAL;
   if (!A || !B || !c || !x || !u || !xref || !uref || !x0 || !dx || !du || !inst_status)
     return fail(ctx, RTN_E_INVAL, "rtn_qp_solve: NULL argument");
+  if (ctx->di) return di_unsupported(ctx, "rtn_qp_solve");
   QpArgs a{};
   a.A = A; a.Bm = B; a.c = c;
   a.x = const_cast<float*>(x); a.u = const_cast<float*>(u);
@@ -371,12 +493,17 @@ rtn_status rtn_rti_step(rtn_ctx* ctx, const float* x0, const float* xref, const 
                         float* u0_out, int* inst_status) {
   if (!ctx) return RTN_E_INVAL;
   if (!x0 || !xref || !uref || !u0_out) return fail(ctx, RTN_E_INVAL, "rtn_rti_step: NULL argument");
+  if (ctx->di) {
+    CK(di_rti(ctx, x0, xref, uref, u0_out, inst_status));
+    return RTN_OK;
+  }
   return rti_impl(ctx, x0, xref, uref, 0, 0, nullptr, u0_out, inst_status);
 }
 
 rtn_status rtn_plant_step(rtn_ctx* ctx, int kind, const double* x, const float* u, double* x_next,
                           int nsub) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_plant_step");
   if (!x || !u || !x_next || nsub < 1 || kind < 0 || kind > 2)
     return fail(ctx, RTN_E_INVAL, "rtn_plant_step: bad argument");
   cudaError_t e = plant_step(ctx, kind, x, u, x_next, nsub, nullptr);
@@ -388,6 +515,7 @@ rtn_status rtn_plant_step(rtn_ctx* ctx, int kind, const double* x, const float* 
 
 rtn_status rtn_tc_variants(rtn_ctx* ctx, int* count) {
   if (!ctx || !count) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_tc_variants");
   *count = mlp_tc_variant_count();
   return RTN_OK;
 }
@@ -395,6 +523,7 @@ rtn_status rtn_tc_variants(rtn_ctx* ctx, int* count) {
 rtn_status rtn_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages,
                                int* fits) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_tc_variant_info");
   if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
     return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
   int r = mlp_tc_variant_info(ctx, idx, npc, split, stages);
@@ -405,6 +534,7 @@ rtn_status rtn_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int*
 
 rtn_status rtn_tc_select(rtn_ctx* ctx, int idx) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_tc_select");
   if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
     return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
   int r = mlp_tc_variant_info(ctx, idx, nullptr, nullptr, nullptr);
@@ -416,6 +546,7 @@ rtn_status rtn_tc_select(rtn_ctx* ctx, int idx) {
 
 rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_autotune");
   if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
     return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -452,6 +583,7 @@ rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms) {
 
 rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_tc_trace");
   TcNet& tc = ctx->net.tc;
   if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
     return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
@@ -467,6 +599,7 @@ rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable) {
 
 rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n) {
   if (!ctx || !host || n < 0 || n > RTN_TC_TRACE_LEN) return fail(ctx, RTN_E_INVAL, "rtn_tc_trace_read: bad argument");
+  if (ctx->di) return di_unsupported(ctx, "rtn_tc_trace_read");
   if (!ctx->net.tc.trace) return fail(ctx, RTN_E_INVAL, "tracing is not enabled");
   CK(cudaMemcpy(host, ctx->net.tc.trace, (size_t)n * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
   return RTN_OK;
@@ -484,6 +617,7 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
                            const float* uref_traj, int T, double* x_plant, float* traj_out,
                            float* u_out) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_closed_loop");
   if (steps < 0 || !xref_traj || !uref_traj || !x_plant || plant_kind < 0 || plant_kind > 2 ||
       T < steps + ctx->lay.N_max + 1)
     return fail(ctx, RTN_E_INVAL, "rtn_closed_loop: bad argument");

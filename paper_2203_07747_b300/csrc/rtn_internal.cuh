@@ -88,8 +88,30 @@ struct TrainState {
 
 }  // namespace rtn
 
+namespace rtn {
+// Double-integrator contexts (nx = 2, nu = 1): the runtime-analysis model of
+// Sec. IV, kernels in di.cu.  The residual network maps z = (p, v, u) to one
+// output added to dv/dt; it is evaluated in FP32 with forward mode (value + 3
+// tangents per node); the QP of each instance runs in FP64.
+struct DiState {
+  int n_layers = 0;                 // 0: nominal model only
+  std::vector<int> widths;          // widths[0] = 3, widths[n_layers] = 1
+  std::vector<size_t> w_off, b_off;
+  int h_max = 0;
+  float* W = nullptr;               // every layer, row-major [out][in]
+  float* b = nullptr;
+  float* act0 = nullptr;            // [n_nodes][4][h_max] activations and tangents
+  float* act1 = nullptr;
+  double Q[2] = {0, 0}, QN[2] = {0, 0}, R = 0;
+  double* K = nullptr;              // [n_nodes][2] feedback gains of the last QP
+  double* kff = nullptr;            // [n_nodes]
+};
+}  // namespace rtn
+
 struct rtn_ctx {
   int B = 0;
+  int nx = rtn::NX, nu = rtn::NU;   // 13, 4 (quadrotor) or 2, 1 (double integrator)
+  rtn::DiState* di = nullptr;       // set for double-integrator contexts
   rtn::Layout lay;
   std::vector<int> hN;
   std::vector<double> hdt;
@@ -125,6 +147,15 @@ struct rtn_ctx {
 namespace rtn {
 
 // ---- launchers (each returns cudaGetLastError()) --------------------------
+
+// f3, double integrator (di.cu): network value + Jacobian of every node,
+// linearisation (A [n][2][2], B [n][2], c [n][2]) and the RTI step
+cudaError_t di_mlp(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+cudaError_t di_linearize(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
+                         const float* JD, float* A, float* Bm, float* c);
+cudaError_t di_rti(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref, float* u0,
+                   int* status);
+cudaError_t di_reset(rtn_ctx* ctx, const float* x0);
 
 // a1, FP32 SIMT path
 cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);

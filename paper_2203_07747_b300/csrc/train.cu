@@ -322,6 +322,10 @@ extern "C" {
 
 rtn_status rtn_drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) {
+    ctx->err = "rtn_drag_targets: not available for the double-integrator model";
+    return RTN_E_UNSUPPORTED;
+  }
   if (!X || !Y || n < 1) return tfail(ctx, RTN_E_INVAL, "rtn_drag_targets: bad argument");
   TCK(drag_targets(ctx, X, n, Y));
   return RTN_OK;
@@ -330,6 +334,10 @@ rtn_status rtn_drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y) {
 rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,
                         float* grad, float* loss) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) {
+    ctx->err = "rtn_mse_grad: not available for the double-integrator model";
+    return RTN_E_UNSUPPORTED;
+  }
   if (!ctx->has_mlp) return tfail(ctx, RTN_E_UNSUPPORTED, "rtn_mse_grad: no network");
   if (!X || !U || !Y || n < 1 || !grad || !loss) return tfail(ctx, RTN_E_INVAL, "rtn_mse_grad: bad argument");
   rtn_status st = ensure_train(ctx, n);
@@ -350,6 +358,10 @@ rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const floa
 rtn_status rtn_train(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,
                      int epochs, int batch, float lr, float* loss_out) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) {
+    ctx->err = "rtn_train: not available for the double-integrator model";
+    return RTN_E_UNSUPPORTED;
+  }
   if (!ctx->has_mlp) return tfail(ctx, RTN_E_UNSUPPORTED, "rtn_train: no network");
   if (!X || !U || !Y || n < 1 || epochs < 0 || batch < 1 || batch > n || !(lr > 0.0f))
     return tfail(ctx, RTN_E_INVAL, "rtn_train: bad argument");
@@ -377,6 +389,10 @@ rtn_status rtn_train(rtn_ctx* ctx, const float* X, const float* U, const float* 
 
 rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b) {
   if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) {
+    ctx->err = "rtn_get_params: not available for the double-integrator model";
+    return RTN_E_UNSUPPORTED;
+  }
   if (!ctx->has_mlp || !W || !b) return tfail(ctx, RTN_E_INVAL, "rtn_get_params: bad argument");
   size_t nw = 0, nb = 0;
   for (int l = 0; l < ctx->net.n_layers; ++l) {
