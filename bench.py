@@ -401,6 +401,102 @@ def bench_learned(epochs=2, steps=100):
             "tracking_rmse_m": {"learned": rmse_l, "nominal": rmse_n}}
 
 
+# Table II (Sec. IV): hidden layers x width of the zero-output network, and
+# the paper's RTN control frequency on the RTX 3000 laptop GPU (context only)
+TABLE2 = [(0, 0, 4262), (2, 16, 781), (2, 128, 770), (5, 16, 586), (5, 128, 598), (12, 32, 363),
+          (12, 512, 363), (20, 512, 232), (50, 512, 117)]
+SWEEP2 = [(16, None), (128, None), (1024, None), (4096, 500.9), (8192, 169.7)]
+
+
+def di_layers(n_hidden, width, seed=0):
+    """Zero-output residual network of the runtime analysis: (p, v, u) ->
+    n_hidden tanh layers of `width` -> 1, last layer zero (Sec. IV)."""
+    if n_hidden == 0:
+        return None
+    layers = W.xavier_mlp([3] + [width] * n_hidden + [1], seed)
+    Wl, bl = layers[-1]
+    layers[-1] = (np.zeros_like(Wl), np.zeros_like(bl))
+    return layers
+
+
+def bench_runtime_analysis(steps=200):
+    """f3: control frequency of one double-integrator controller (N = 10)
+    with the zero-output networks of Table II and the 2-layer width sweep:
+    device-side (one RTI step captured in a CUDA graph, replayed) and through
+    the Python API; plus instance RTI steps/s of large batches."""
+    import torch
+    import paper_2203_07747_b300 as rtn
+    Qd, Rd = np.array([10.0, 1.0]), np.array([0.1])
+
+    def one(n_hidden, width, B=1, graph=True):
+        s = torch.cuda.Stream()
+        ctl = rtn.DIController(np.full(B, 10), np.full(B, 0.05), Qd, Rd, layers=di_layers(n_hidden, width),
+                               stream=s)
+        x0 = torch.zeros(B, 2, device="cuda")
+        xref = torch.zeros(ctl.n_states, 2, device="cuda")
+        xref[:, 0] = 1.0
+        uref = torch.zeros(ctl.n_nodes, device="cuda")
+        u0 = torch.empty(B, device="cuda")
+        st = torch.empty(B, dtype=torch.int32, device="cuda")
+        res = {}
+        with torch.cuda.stream(s):
+            for _ in range(10):
+                ctl.rti_step(x0, xref, uref, u0, st)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            n_api = steps if B == 1 else max(5, steps // 20)
+            e0.record(s)
+            for _ in range(n_api):
+                ctl.rti_step(x0, xref, uref, u0, st)
+            e1.record(s)
+            torch.cuda.synchronize()
+            res["ms_api"] = e0.elapsed_time(e1) / n_api
+            if graph:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    ctl.rti_step(x0, xref, uref, u0, st)
+                for _ in range(10):
+                    g.replay()
+                torch.cuda.synchronize()
+                e0.record(s)
+                for _ in range(steps):
+                    g.replay()
+                e1.record(s)
+                torch.cuda.synchronize()
+                res["ms_graph"] = e0.elapsed_time(e1) / steps
+        assert int((st != 0).sum()) == 0
+        ctl.close()
+        return res
+
+    def params(n_hidden, width):
+        if n_hidden == 0:
+            return 0
+        w = [3] + [width] * n_hidden + [1]
+        return int(sum(a * b + b for a, b in zip(w[:-1], w[1:])))
+
+    out = {"metric": "control frequency of one controller [Hz]: RTI step of the double integrator "
+                     "with a zero-output network, N = 10 (Sec. IV, Table II)",
+           "note": "hz = device-side (one RTI step in a CUDA graph, replayed); hz_api = through the "
+                   "Python binding; paper_rtx3000_hz = the paper's RTN on an RTX 3000 (context)",
+           "table2": [], "width_sweep_2_layers": [], "batch": []}
+    for n_hidden, width, paper in TABLE2:
+        r = one(n_hidden, width)
+        out["table2"].append({"hidden_layers": n_hidden, "width": width, "params": params(n_hidden, width),
+                              "hz": 1e3 / r["ms_graph"], "hz_api": 1e3 / r["ms_api"],
+                              "paper_rtx3000_hz": paper})
+    for width, paper in SWEEP2:
+        r = one(2, width)
+        out["width_sweep_2_layers"].append({"width": width, "params": params(2, width),
+                                            "hz": 1e3 / r["ms_graph"], "hz_api": 1e3 / r["ms_api"],
+                                            "paper_rtx3000_hz": paper})
+    for n_hidden, width in [(2, 128), (5, 128), (12, 512)]:
+        B = 8192
+        r = one(n_hidden, width, B=B, graph=False)
+        out["batch"].append({"instances": B, "hidden_layers": n_hidden, "width": width,
+                             "rti_steps_per_s": B / (r["ms_api"] * 1e-3), "ms_per_step": r["ms_api"]})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,6 +615,7 @@ def main():
         line["box_qp"] = bench_box(prob, prec, cfg.get("tile"))
         line["ragged_batch"] = bench_ragged()
         line["learned_part"] = bench_learned()
+        line["runtime_analysis"] = bench_runtime_analysis()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob)
     if rank == 0:

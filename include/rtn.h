@@ -102,10 +102,23 @@ typedef struct {
  * step sizes dt[b] > 0 (host arrays [batch]).  Q, R, Q_N are host diagonals
  * (nx, nu, nx); Q_N may be NULL (then Q_N = Q).  mlp may be NULL (nominal
  * model only).  opt may be NULL (FP32, FP32 sweep, shift on).  cuda_stream is
- * a cudaStream_t (NULL = legacy default stream).  nx must be 13 and nu 4.
- * The iterate starts at x_k = 0 (q = identity), u_k = hover; see rtn_reset.
- * Synchronous.  Returns RTN_E_INVAL on bad sizes, RTN_E_NOMEM/RTN_E_CUDA on
- * device failures (then *out is NULL). */
+ * a cudaStream_t (NULL = legacy default stream).
+ * Two models:
+ *   nx = 13, nu = 4: the quadrotor of Sec. V (quad required); network 17 -> 3;
+ *   nx = 2, nu = 1: the double integrator of the runtime analysis (Sec. IV,
+ *     Eq. 5): x = (p, v), u = commanded acceleration, f_F = (v, u); the
+ *     network maps z = (p, v, u) to 1 output added to dv/dt (any hidden
+ *     widths up to 65536); quad is ignored (may be NULL); opt must select
+ *     RTN_FP32 without box_qp or riccati_f64 (RTN_E_UNSUPPORTED otherwise);
+ *     the QP runs in FP32 and has no input bounds (u0 is sent unclamped).
+ *     Every entry point below then uses nx = 2, nu = 1 in its layouts (fD
+ *     [sum N_b][1], JD [sum N_b][1][3]); rtn_qp_solve, rtn_plant_step,
+ *     rtn_closed_loop, the tile autotuner, tracing and the training calls
+ *     return RTN_E_UNSUPPORTED.
+ * The iterate starts at x_k = 0 (quadrotor: q = identity, u_k = hover;
+ * double integrator: u_k = 0); see rtn_reset.  Synchronous.  Returns
+ * RTN_E_INVAL on bad sizes, RTN_E_NOMEM/RTN_E_CUDA on device failures (then
+ * *out is NULL). */
 rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, const double* dt,
                       const double* Q, const double* R, const double* Q_N, const rtn_quad* quad,
                       const rtn_mlp* mlp, const rtn_options* opt, void* cuda_stream);
@@ -121,7 +134,8 @@ const char* rtn_last_error(const rtn_ctx* ctx);
 rtn_status rtn_sizes(const rtn_ctx* ctx, int* n_nodes, int* n_states);
 
 /* Initial iterate (Sec. III-B needs an iterate to linearise around):
- * x_k = x0[b] for every k, u_k = m g / 4.  x0: dev float [B][13]. */
+ * x_k = x0[b] for every k, u_k = m g / 4 (double integrator: 0).  x0: dev
+ * float [B][nx]. */
 rtn_status rtn_reset(rtn_ctx* ctx, const float* x0);
 
 /* Copy the iterate in or out: x dev float [sum(N_b+1)][13], u dev float

@@ -396,7 +396,7 @@ class DIController:
     """A batch of B controllers of the runtime-analysis model (Sec. IV): the
     double integrator x = (p, v), u = acceleration, with an optional residual
     network (p, v, u) -> 1 output added to dv/dt.  Same C ABI as Controller
-    (rtn_create with nx = 2, nu = 1); FP32 network, FP64 QP, no input bounds."""
+    (rtn_create with nx = 2, nu = 1); FP32 network and QP, no input bounds."""
 
     def __init__(self, N, dt, Q, R, QN=None, layers=None, shift=True, stream=None):
         import torch

@@ -141,7 +141,7 @@ rtn_status make_layout(rtn_ctx* ctx, int batch, const int* N, const double* dt) 
 }
 
 // double-integrator context (nx = 2, nu = 1): the runtime-analysis model of
-// Sec. IV; network z = (p, v, u) -> 1 output, FP32 only, no input bounds
+// Sec. IV; network z = (p, v, u) -> 1 output, FP32, no input bounds
 rtn_status create_di(rtn_ctx* ctx, int batch, const int* N, const double* dt, const double* Q,
                      const double* R, const double* Q_N, const rtn_mlp* mlp, const rtn_options& o,
                      void* cuda_stream) {
@@ -186,8 +186,8 @@ rtn_status create_di(rtn_ctx* ctx, int batch, const int* N, const double* dt, co
   CK(dalloc(&ctx->u, (size_t)us));
   CK(dalloc(&ctx->fD, (size_t)us));
   CK(dalloc(&ctx->JD, (size_t)us * 3));
-  CK(dalloc(&D.K, (size_t)us * 2));
-  CK(dalloc(&D.kff, (size_t)us));
+  CK(dalloc(&D.lin, (size_t)us * 8));
+  CK(dalloc(&D.K, (size_t)us * 3));
   CK(dalloc(&ctx->status, batch));
   CK(dalloc(&ctx->x0f, (size_t)batch * 2));
   CK(dalloc(&ctx->u0, (size_t)batch));
@@ -231,7 +231,7 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
   o.box_qp = o.box_qp ? 1 : 0;
   if (di) {
     if (o.precision != RTN_FP32 || o.box_qp || o.riccati_f64) {
-      g_create_err = "the double-integrator model runs the FP32 network path and an FP64 QP only";
+      g_create_err = "the double-integrator model runs in FP32 (network and QP), without bounds";
       return RTN_E_UNSUPPORTED;
     }
     if (mlp) {
@@ -383,7 +383,7 @@ void rtn_destroy(rtn_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->di) {
-    void* dp[] = {ctx->di->W, ctx->di->b, ctx->di->act0, ctx->di->act1, ctx->di->K, ctx->di->kff};
+    void* dp[] = {ctx->di->W, ctx->di->b, ctx->di->act0, ctx->di->act1, ctx->di->lin, ctx->di->K};
     for (void* p : dp)
       if (p) cudaFree(p);
     delete ctx->di;

@@ -8,7 +8,7 @@
 //     forward mode (value + 3 tangents = 4 columns per node) -- di_in_kernel
 //     (first layer), di_hidden_kernel (hidden -> hidden, any width),
 //     di_out_kernel (last layer);
-//   * one thread per instance (di_step_kernel, FP64): RK4 of f_F + f_D* with
+//   * one thread per instance (di_step_kernel, FP32): RK4 of f_F + f_D* with
 //     the sensitivities A = dphi/dx, B = dphi/du at every node, the Riccati
 //     recursion of the QP (nx = 2, nu = 1), the forward roll-out from the
 //     measured x0, the iterate update, u_0, and the shift.
@@ -47,33 +47,17 @@ __global__ void di_in_kernel(const float* __restrict__ W0, const float* __restri
   }
 }
 
-// hidden layer: Y = W X for the 4 columns of 8 nodes and 8 consecutive units
-// per 256-thread block (warp w computes unit o0 + w; lanes split K), then
-// value a = tanh(y + b), tangents y * (1 - a^2).  X: [n_nodes][4][hi],
-// Y: [n_nodes][4][ho].
-__global__ void __launch_bounds__(256) di_hidden_kernel(const float* __restrict__ W,
-                                                        const float* __restrict__ bias, int hi, int ho,
-                                                        const float* __restrict__ X,
-                                                        float* __restrict__ Y, int n_nodes) {
-  __shared__ float out_s[32][9];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int o0 = blockIdx.x * 8, o = o0 + warp;
-  const int n0 = blockIdx.y * 8;
-  const int ncol = min(8, n_nodes - n0) * DI_NC;  // columns of real nodes
-  float acc[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0.0f;
-  if (o < ho) {
-    const float* wr = W + (size_t)o * hi;
-    const float* xb = X + (size_t)n0 * DI_NC * hi;
-    for (int k = lane; k < hi; k += 32) {
-      const float wv = __ldg(wr + k);
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < ncol) acc[c] = fmaf(wv, __ldg(xb + (size_t)c * hi + k), acc[c]);
-    }
-  }
-  // butterfly reduce-scatter: lane l ends with the sum of column l
+// hidden layer: Y = W X for the 4 columns of 8 nodes and 16 consecutive units
+// per 256-thread block (warp w computes units o0 + 2w, o0 + 2w + 1; lanes
+// split K), then value a = tanh(y + b), tangents y * (1 - a^2).  The block
+// stages its 32 columns of X in shared memory 128 K at a time (independent
+// coalesced loads), so every K step of a warp is register/shared-memory
+// arithmetic.  X: [n_nodes][4][hi], Y: [n_nodes][4][ho].
+constexpr int DI_KC = 128;  // K per staged chunk
+constexpr int DI_RO = 2;    // output units per warp
+
+__device__ __forceinline__ void reduce_scatter32(float (&acc)[32], int lane) {
+  // butterfly reduce-scatter: lane l ends with the sum of column l in acc[0]
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
     const bool up = (lane & s) != 0;
@@ -84,45 +68,94 @@ __global__ void __launch_bounds__(256) di_hidden_kernel(const float* __restrict_
       acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
   }
-  // column lane = 4 (node - n0) + component
-  const int comp = lane & 3;
-  float a = 0.0f, d = 0.0f;
-  if (comp == 0) {
-    a = tanhf(acc[0] + (o < ho ? bias[o] : 0.0f));
-    d = 1.0f - a * a;
-  }
-  d = __shfl_sync(0xffffffffu, d, lane & ~3);
-  out_s[lane][warp] = comp == 0 ? a : acc[0] * d;
-  __syncthreads();
-  // 8 consecutive units of each column: one 32-byte run per column
-  const int col = threadIdx.x >> 3, oo = threadIdx.x & 7;
-  if (col < ncol && o0 + oo < ho) Y[((size_t)n0 * DI_NC + col) * ho + o0 + oo] = out_s[col][oo];
 }
 
-// last layer (one output, linear): f = W_L a + b_L, J_j = W_L t_j; one warp
-// per node
+__global__ void __launch_bounds__(256) di_hidden_kernel(const float* __restrict__ W,
+                                                        const float* __restrict__ bias, int hi, int ho,
+                                                        const float* __restrict__ X,
+                                                        float* __restrict__ Y, int n_nodes) {
+  __shared__ float xs[32][DI_KC];
+  __shared__ float out_s[32][8 * DI_RO + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = blockIdx.x * 8 * DI_RO;
+  const int n0 = blockIdx.y * 8;
+  const int ncol = min(8, n_nodes - n0) * DI_NC;  // columns of real nodes
+  const float* xb = X + (size_t)n0 * DI_NC * hi;
+  float acc[DI_RO][32];
+#pragma unroll
+  for (int r = 0; r < DI_RO; ++r)
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[r][c] = 0.0f;
+  for (int k0 = 0; k0 < hi; k0 += DI_KC) {
+    const int kc = min(DI_KC, hi - k0);
+    __syncthreads();  // the previous chunk has been used
+#pragma unroll
+    for (int i = 0; i < 32 * DI_KC / 256; ++i) {
+      const int e = threadIdx.x + 256 * i, c = e / DI_KC, kk = e % DI_KC;
+      xs[c][kk] = (c < ncol && kk < kc) ? __ldg(xb + (size_t)c * hi + k0 + kk) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < DI_RO; ++r) {
+      const int o = o0 + DI_RO * warp + r;
+      if (o >= ho) continue;
+      float w[DI_KC / 32];
+#pragma unroll
+      for (int j = 0; j < DI_KC / 32; ++j)
+        w[j] = lane + 32 * j < kc ? __ldg(W + (size_t)o * hi + k0 + lane + 32 * j) : 0.0f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        float sacc = acc[r][c];
+#pragma unroll
+        for (int j = 0; j < DI_KC / 32; ++j) sacc = fmaf(w[j], xs[c][lane + 32 * j], sacc);
+        acc[r][c] = sacc;
+      }
+    }
+  }
+  // column lane = 4 (node - n0) + component
+  const int comp = lane & 3;
+#pragma unroll
+  for (int r = 0; r < DI_RO; ++r) {
+    const int o = o0 + DI_RO * warp + r;
+    reduce_scatter32(acc[r], lane);
+    float a = 0.0f, d = 0.0f;
+    if (comp == 0) {
+      a = tanhf(acc[r][0] + (o < ho ? bias[o] : 0.0f));
+      d = 1.0f - a * a;
+    }
+    d = __shfl_sync(0xffffffffu, d, lane & ~3);
+    out_s[lane][DI_RO * warp + r] = comp == 0 ? a : acc[r][0] * d;
+  }
+  __syncthreads();
+  // 16 consecutive units of each column: one 64-byte run per column
+  for (int e = threadIdx.x; e < 32 * 8 * DI_RO; e += 256) {
+    const int col = e / (8 * DI_RO), oo = e % (8 * DI_RO);
+    if (col < ncol && o0 + oo < ho) Y[((size_t)n0 * DI_NC + col) * ho + o0 + oo] = out_s[col][oo];
+  }
+}
+
+// last layer (one output, linear): f = W_L a + b_L, J_j = W_L t_j; 4 warps
+// per node, warp c the dot product of column c (loads unrolled 4 deep)
 __global__ void di_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL, int h,
                               const float* __restrict__ X, int n_nodes, float* __restrict__ fD,
                               float* __restrict__ JD) {
-  const int lane = threadIdx.x & 31;
-  const int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, c = (threadIdx.x >> 5) & 3;
+  const int node = blockIdx.x * (blockDim.x >> 7) + (threadIdx.x >> 7);
   if (node >= n_nodes) return;
-  const float* xb = X + (size_t)node * DI_NC * h;
-  float acc[DI_NC] = {0.0f, 0.0f, 0.0f, 0.0f};
-  for (int k = lane; k < h; k += 32) {
-    const float wv = __ldg(WL + k);
+  const float* xc = X + ((size_t)node * DI_NC + c) * h;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  int k = lane;
+  for (; k + 96 < h; k += 128) {
 #pragma unroll
-    for (int c = 0; c < DI_NC; ++c) acc[c] = fmaf(wv, __ldg(xb + (size_t)c * h + k), acc[c]);
+    for (int j = 0; j < 4; ++j) acc[j] = fmaf(__ldg(WL + k + 32 * j), __ldg(xc + k + 32 * j), acc[j]);
   }
+  for (; k < h; k += 32) acc[0] = fmaf(__ldg(WL + k), __ldg(xc + k), acc[0]);
+  float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1)
-#pragma unroll
-    for (int c = 0; c < DI_NC; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], s);
+  for (int sh = 16; sh >= 1; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
   if (lane == 0) {
-    fD[node] = acc[0] + bL[0];
-    JD[(size_t)node * 3] = acc[1];
-    JD[(size_t)node * 3 + 1] = acc[2];
-    JD[(size_t)node * 3 + 2] = acc[3];
+    if (c == 0) fD[node] = s + bL[0];
+    else JD[(size_t)node * 3 + c - 1] = s;
   }
 }
 
@@ -143,11 +176,11 @@ cudaError_t di_mlp(rtn_ctx* ctx, const float* x, const float* u, float* fD, floa
   float* nxt = D.act1;
   for (int l = 1; l + 1 < L; ++l) {
     const int hi = D.widths[l], ho = D.widths[l + 1];
-    dim3 grid((ho + 7) / 8, (n + 7) / 8);
+    dim3 grid((ho + 8 * DI_RO - 1) / (8 * DI_RO), (n + 7) / 8);
     di_hidden_kernel<<<grid, 256, 0, s>>>(D.W + D.w_off[l], D.b + D.b_off[l], hi, ho, cur, nxt, n);
     std::swap(cur, nxt);
   }
-  di_out_kernel<<<(n + 7) / 8, 256, 0, s>>>(D.W + D.w_off[L - 1], D.b + D.b_off[L - 1], D.widths[L - 1],
+  di_out_kernel<<<(n + 1) / 2, 256, 0, s>>>(D.W + D.w_off[L - 1], D.b + D.b_off[L - 1], D.widths[L - 1],
                                             cur, n, fD, JD);
   return cudaGetLastError();
 }
@@ -157,32 +190,34 @@ namespace {
 // RK4 (u held) of f_F + f_D* with f_D* = fb + J (z - z_k) around the node,
 // and the sensitivity S = d(stage)/d[x; u] (2 x 3) through the stages:
 // phi = x + dt/6 (k1 + 2 k2 + 2 k3 + k4), A = dphi/dx, B = dphi/du.
-__device__ void di_rk4(const double* x, double u, double fb, const double* J, double dt, double* phi,
-                       double* A, double* B) {
+template <typename T>
+__device__ void di_rk4(const T* x, T u, T fb, const T* J, T dt, T* phi, T* A, T* B) {
   // D = d f / d[p, v, u] (constant: f_F is linear, f_D* affine)
-  const double D[6] = {0.0, 1.0, 0.0, J[0], J[1], 1.0 + J[2]};
-  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
-  const double wt[4] = {1.0, 2.0, 2.0, 1.0};
-  double k[2] = {0.0, 0.0}, dk[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  double ksum[2] = {0.0, 0.0}, dksum[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const T D[6] = {T(0), T(1), T(0), J[0], J[1], T(1) + J[2]};
+  const T cst[4] = {T(0), T(0.5), T(0.5), T(1)};
+  const T wt[4] = {T(1), T(2), T(2), T(1)};
+  T k[2] = {T(0), T(0)}, dk[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  T ksum[2] = {T(0), T(0)}, dksum[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
   for (int s = 0; s < 4; ++s) {
-    double xs[2], S[6];
+    T xs[2], S[6];
     for (int i = 0; i < 2; ++i) xs[i] = x[i] + cst[s] * dt * k[i];
     for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 3; ++j) S[i * 3 + j] = ((i == j) ? 1.0 : 0.0) + cst[s] * dt * dk[i * 3 + j];
+      for (int j = 0; j < 3; ++j) S[i * 3 + j] = ((i == j) ? T(1) : T(0)) + cst[s] * dt * dk[i * 3 + j];
     k[0] = xs[1];
     k[1] = u + fb + J[0] * (xs[0] - x[0]) + J[1] * (xs[1] - x[1]);
     for (int i = 0; i < 2; ++i)
       for (int j = 0; j < 3; ++j)
-        dk[i * 3 + j] = ((j == 2) ? D[i * 3 + 2] : 0.0) + D[i * 3] * S[j] + D[i * 3 + 1] * S[3 + j];
+        dk[i * 3 + j] = ((j == 2) ? D[i * 3 + 2] : T(0)) + D[i * 3] * S[j] + D[i * 3 + 1] * S[3 + j];
     for (int i = 0; i < 2; ++i) ksum[i] += wt[s] * k[i];
     for (int i = 0; i < 6; ++i) dksum[i] += wt[s] * dk[i];
   }
+  const T h6 = dt / T(6);
   for (int i = 0; i < 2; ++i) {
-    phi[i] = x[i] + dt / 6.0 * ksum[i];
-    A[i * 2] = (i == 0 ? 1.0 : 0.0) + dt / 6.0 * dksum[i * 3];
-    A[i * 2 + 1] = (i == 1 ? 1.0 : 0.0) + dt / 6.0 * dksum[i * 3 + 1];
-    B[i] = dt / 6.0 * dksum[i * 3 + 2];
+    phi[i] = x[i] + h6 * ksum[i];
+    A[i * 2] = (i == 0 ? T(1) : T(0)) + h6 * dksum[i * 3];
+    A[i * 2 + 1] = (i == 1 ? T(1) : T(0)) + h6 * dksum[i * 3 + 1];
+    B[i] = h6 * dksum[i * 3 + 2];
   }
 }
 
@@ -209,7 +244,7 @@ __global__ void di_lin_kernel(DiLay L, const float* __restrict__ x, const float*
     for (int j = 0; j < 3; ++j) J[j] = JD[(size_t)node * 3 + j];
   }
   double phi[2], Ak[4], Bk[2];
-  di_rk4(xk, u[node], fb, J, L.dt[b], phi, Ak, Bk);
+  di_rk4<double>(xk, (double)u[node], fb, J, (double)L.dt[b], phi, Ak, Bk);
   for (int i = 0; i < 4; ++i) A[(size_t)node * 4 + i] = (float)Ak[i];
   for (int i = 0; i < 2; ++i) {
     Bm[(size_t)node * 2 + i] = (float)Bk[i];
@@ -226,22 +261,23 @@ struct DiStepArgs {
   const float* xref;
   const float* uref;
   const float* x0;   // [B][2] measured states
-  double Q[2], QN[2], R;
-  double* K;         // [n_nodes][2] workspace
-  double* kff;       // [n_nodes]
+  float Q[2], QN[2], R;
+  float* lin;        // [n_nodes][8] workspace: A (4), B (2), c (2)
+  float* K;          // [n_nodes][3] workspace: K (2), k (1)
   float* u0;         // [B]
   int* status;       // [B]
   int shift;
 };
 
-// one RTI step of instance b (one thread): linearise (RK4 + sensitivities),
-// Riccati recursion, roll-out from the measured x0, update, u_0, shift
+// one RTI step of instance b (one thread, FP32): linearise each node (RK4 +
+// sensitivities) on the way back through the Riccati recursion, roll out
+// from the measured x0 with the stored linearisation, update, u_0, shift
 __global__ void di_step_kernel(DiStepArgs a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.L.B) return;
   const int Nb = a.L.N[b], xo = a.L.xoff[b], uo = a.L.uoff[b];
-  const double dt = a.L.dt[b];
-  const double x0m[2] = {a.x0[(size_t)b * 2], a.x0[(size_t)b * 2 + 1]};
+  const float dt = a.L.dt[b];
+  const float x0m[2] = {a.x0[(size_t)b * 2], a.x0[(size_t)b * 2 + 1]};
   if (!isfinite(x0m[0]) || !isfinite(x0m[1])) {
     a.status[b] = RTN_E_NONFINITE;
     a.u0[b] = a.uref[uo];
@@ -249,78 +285,74 @@ __global__ void di_step_kernel(DiStepArgs a) {
   }
   float* xb = a.x + (size_t)xo * 2;
   float* ub = a.u + uo;
-  // backward recursion, linearising each node on the way:
+  // backward recursion:
   //   P <- Q + A'PA + Hux'K,  p <- q + A'(p + Pc) + Hux'k,
   //   K = -Hux / Huu, k = -hu / Huu  (Huu = R + B'PB scalar)
-  double P[4] = {a.QN[0], 0.0, 0.0, a.QN[1]};
-  double p[2] = {a.QN[0] * (xb[(size_t)Nb * 2] - a.xref[(size_t)(xo + Nb) * 2]),
-                 a.QN[1] * (xb[(size_t)Nb * 2 + 1] - a.xref[(size_t)(xo + Nb) * 2 + 1])};
+  float P[4] = {a.QN[0], 0.0f, 0.0f, a.QN[1]};
+  float p[2] = {a.QN[0] * (xb[(size_t)Nb * 2] - a.xref[(size_t)(xo + Nb) * 2]),
+                a.QN[1] * (xb[(size_t)Nb * 2 + 1] - a.xref[(size_t)(xo + Nb) * 2 + 1])};
   for (int k = Nb - 1; k >= 0; --k) {
     const int nd = uo + k;
-    const double xk[2] = {xb[(size_t)k * 2], xb[(size_t)k * 2 + 1]};
-    double J[3] = {0.0, 0.0, 0.0}, fb = 0.0;
+    const float xk[2] = {xb[(size_t)k * 2], xb[(size_t)k * 2 + 1]};
+    float J[3] = {0.0f, 0.0f, 0.0f}, fb = 0.0f;
     if (a.fD) {
       fb = a.fD[nd];
       for (int j = 0; j < 3; ++j) J[j] = a.JD[(size_t)nd * 3 + j];
     }
-    double phi[2], A[4], Bv[2];
-    di_rk4(xk, ub[k], fb, J, dt, phi, A, Bv);
-    const double c[2] = {phi[0] - xb[(size_t)(k + 1) * 2], phi[1] - xb[(size_t)(k + 1) * 2 + 1]};
-    double PA[4], PB[2], g[2];
+    float phi[2], A[4], Bv[2];
+    di_rk4<float>(xk, ub[k], fb, J, dt, phi, A, Bv);
+    const float c[2] = {phi[0] - xb[(size_t)(k + 1) * 2], phi[1] - xb[(size_t)(k + 1) * 2 + 1]};
+    float* ln = a.lin + (size_t)nd * 8;
+    for (int i = 0; i < 4; ++i) ln[i] = A[i];
+    ln[4] = Bv[0]; ln[5] = Bv[1]; ln[6] = c[0]; ln[7] = c[1];
+    float PA[4], PB[2], g[2];
     for (int i = 0; i < 2; ++i) {
       PA[i * 2] = P[i * 2] * A[0] + P[i * 2 + 1] * A[2];
       PA[i * 2 + 1] = P[i * 2] * A[1] + P[i * 2 + 1] * A[3];
       PB[i] = P[i * 2] * Bv[0] + P[i * 2 + 1] * Bv[1];
       g[i] = p[i] + P[i * 2] * c[0] + P[i * 2 + 1] * c[1];
     }
-    const double Huu = a.R + Bv[0] * PB[0] + Bv[1] * PB[1];
-    const double Hux[2] = {Bv[0] * PA[0] + Bv[1] * PA[2], Bv[0] * PA[1] + Bv[1] * PA[3]};
-    const double hu = a.R * (ub[k] - a.uref[nd]) + Bv[0] * g[0] + Bv[1] * g[1];
-    if (!(Huu > 0.0)) {
+    const float Huu = a.R + Bv[0] * PB[0] + Bv[1] * PB[1];
+    const float Hux[2] = {Bv[0] * PA[0] + Bv[1] * PA[2], Bv[0] * PA[1] + Bv[1] * PA[3]};
+    const float hu = a.R * (ub[k] - a.uref[nd]) + Bv[0] * g[0] + Bv[1] * g[1];
+    if (!(Huu > 0.0f)) {
       a.status[b] = RTN_E_NOT_PD;
       a.u0[b] = a.uref[uo];
       return;
     }
-    const double Kk[2] = {-Hux[0] / Huu, -Hux[1] / Huu}, kk = -hu / Huu;
-    a.K[(size_t)nd * 2] = Kk[0];
-    a.K[(size_t)nd * 2 + 1] = Kk[1];
-    a.kff[nd] = kk;
-    double P2[4], p2[2];
+    const float inv = 1.0f / Huu;
+    const float Kk[2] = {-Hux[0] * inv, -Hux[1] * inv}, kk = -hu * inv;
+    a.K[(size_t)nd * 3] = Kk[0];
+    a.K[(size_t)nd * 3 + 1] = Kk[1];
+    a.K[(size_t)nd * 3 + 2] = kk;
+    float P2[4], p2[2];
     for (int i = 0; i < 2; ++i) {
       for (int j = 0; j < 2; ++j)
-        P2[i * 2 + j] = (i == j ? a.Q[i] : 0.0) + A[i] * PA[j] + A[2 + i] * PA[2 + j] + Hux[i] * Kk[j];
+        P2[i * 2 + j] = (i == j ? a.Q[i] : 0.0f) + A[i] * PA[j] + A[2 + i] * PA[2 + j] + Hux[i] * Kk[j];
       p2[i] = a.Q[i] * (xk[i] - a.xref[(size_t)(xo + k) * 2 + i]) + A[i] * g[0] + A[2 + i] * g[1] + Hux[i] * kk;
     }
     P[0] = P2[0];
-    P[1] = P[2] = 0.5 * (P2[1] + P2[2]);
+    P[1] = P[2] = 0.5f * (P2[1] + P2[2]);
     P[3] = P2[3];
     p[0] = p2[0];
     p[1] = p2[1];
   }
-  // forward roll-out (A, B, c of the same linearisation) and update
-  double dx[2] = {x0m[0] - xb[0], x0m[1] - xb[1]};
+  // forward roll-out with the stored A, B, c, and the update
+  float dx[2] = {x0m[0] - xb[0], x0m[1] - xb[1]};
   for (int k = 0; k < Nb; ++k) {
     const int nd = uo + k;
-    const double du = a.kff[nd] + a.K[(size_t)nd * 2] * dx[0] + a.K[(size_t)nd * 2 + 1] * dx[1];
-    const double xk[2] = {xb[(size_t)k * 2], xb[(size_t)k * 2 + 1]};
-    double J[3] = {0.0, 0.0, 0.0}, fb = 0.0;
-    if (a.fD) {
-      fb = a.fD[nd];
-      for (int j = 0; j < 3; ++j) J[j] = a.JD[(size_t)nd * 3 + j];
-    }
-    double phi[2], A[4], Bv[2];
-    di_rk4(xk, ub[k], fb, J, dt, phi, A, Bv);
-    const double c[2] = {phi[0] - xb[(size_t)(k + 1) * 2], phi[1] - xb[(size_t)(k + 1) * 2 + 1]};
-    xb[(size_t)k * 2] = (float)(xk[0] + dx[0]);
-    xb[(size_t)k * 2 + 1] = (float)(xk[1] + dx[1]);
-    ub[k] = (float)(ub[k] + du);
-    const double nx0 = A[0] * dx[0] + A[1] * dx[1] + Bv[0] * du + c[0];
-    const double nx1 = A[2] * dx[0] + A[3] * dx[1] + Bv[1] * du + c[1];
+    const float* ln = a.lin + (size_t)nd * 8;
+    const float du = a.K[(size_t)nd * 3 + 2] + a.K[(size_t)nd * 3] * dx[0] + a.K[(size_t)nd * 3 + 1] * dx[1];
+    xb[(size_t)k * 2] += dx[0];
+    xb[(size_t)k * 2 + 1] += dx[1];
+    ub[k] += du;
+    const float nx0 = ln[0] * dx[0] + ln[1] * dx[1] + ln[4] * du + ln[6];
+    const float nx1 = ln[2] * dx[0] + ln[3] * dx[1] + ln[5] * du + ln[7];
     dx[0] = nx0;
     dx[1] = nx1;
   }
-  xb[(size_t)Nb * 2] = (float)(xb[(size_t)Nb * 2] + dx[0]);
-  xb[(size_t)Nb * 2 + 1] = (float)(xb[(size_t)Nb * 2 + 1] + dx[1]);
+  xb[(size_t)Nb * 2] += dx[0];
+  xb[(size_t)Nb * 2 + 1] += dx[1];
   a.u0[b] = ub[0];
   a.status[b] = RTN_OK;
   if (a.shift) {
@@ -370,11 +402,11 @@ cudaError_t di_rti(rtn_ctx* ctx, const float* x0, const float* xref, const float
   a.xref = xref;
   a.uref = uref;
   a.x0 = x0;
-  a.Q[0] = D.Q[0]; a.Q[1] = D.Q[1];
-  a.QN[0] = D.QN[0]; a.QN[1] = D.QN[1];
-  a.R = D.R;
+  a.Q[0] = (float)D.Q[0]; a.Q[1] = (float)D.Q[1];
+  a.QN[0] = (float)D.QN[0]; a.QN[1] = (float)D.QN[1];
+  a.R = (float)D.R;
+  a.lin = D.lin;
   a.K = D.K;
-  a.kff = D.kff;
   a.u0 = u0;
   a.status = status ? status : ctx->status;
   a.shift = ctx->opt.shift;

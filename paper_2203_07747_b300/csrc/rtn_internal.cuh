@@ -92,7 +92,7 @@ namespace rtn {
 // Double-integrator contexts (nx = 2, nu = 1): the runtime-analysis model of
 // Sec. IV, kernels in di.cu.  The residual network maps z = (p, v, u) to one
 // output added to dv/dt; it is evaluated in FP32 with forward mode (value + 3
-// tangents per node); the QP of each instance runs in FP64.
+// tangents per node); the QP of each instance runs in FP32 on one thread.
 struct DiState {
   int n_layers = 0;                 // 0: nominal model only
   std::vector<int> widths;          // widths[0] = 3, widths[n_layers] = 1
@@ -103,8 +103,8 @@ struct DiState {
   float* act0 = nullptr;            // [n_nodes][4][h_max] activations and tangents
   float* act1 = nullptr;
   double Q[2] = {0, 0}, QN[2] = {0, 0}, R = 0;
-  double* K = nullptr;              // [n_nodes][2] feedback gains of the last QP
-  double* kff = nullptr;            // [n_nodes]
+  float* lin = nullptr;             // [n_nodes][8] A, B, c of the last linearisation
+  float* K = nullptr;               // [n_nodes][3] feedback gains and offsets of the last QP
 };
 }  // namespace rtn
 
