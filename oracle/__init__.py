@@ -105,6 +105,17 @@ def mlp_fwd_jac(layers, z):
     return f, J
 
 
+def mlp_fwd_hess(layers, z):
+    """Value f [nout], Jacobian J [nout][nin] and Hessian H [nout][nin][nin]
+    (forward-over-forward; the H_D of Eq. 4)."""
+    m = _MLP(layers)
+    z, pz = _d(z)
+    nin, nout = m.w[0], m.w[-1]
+    f = np.zeros(nout); J = np.zeros((nout, nin)); H = np.zeros((nout, nin, nin))
+    lib().orc_mlp_fwd_hess(m.nl, m.pw, m.pp, pz, _p(f), _p(J), _p(H))
+    return f, J, H
+
+
 def mlp_rev_jac(layers, z):
     m = _MLP(layers)
     z, pz = _d(z)
@@ -136,15 +147,20 @@ def qrot(q, v):
     return out
 
 
-def rk4_lin(quad, x, u, dt, fbar=None, J=None):
+def rk4_lin(quad, x, u, dt, fbar=None, J=None, H=None):
+    """RK4 of f_F + f_D* with sensitivities; H (3 x 17 x 17) selects the
+    second-order local model."""
     x, px = _d(x); u, pu = _d(u)
     phi = np.zeros(NX); A = np.zeros((NX, NX)); B = np.zeros((NX, NU))
     q = _quad(quad)
+    ph = None
     if fbar is None:
         pf = pj = None
     else:
         fbar, pf = _d(fbar); J, pj = _d(J)
-    lib().orc_rk4_lin(C.byref(q), px, pu, pf, pj, C.c_double(dt), _p(phi), _p(A), _p(B))
+        if H is not None:
+            H, ph = _d(H)
+    lib().orc_rk4_lin_h(C.byref(q), px, pu, pf, pj, ph, C.c_double(dt), _p(phi), _p(A), _p(B))
     return phi, A, B
 
 
@@ -238,6 +254,35 @@ def rti_step(quad, layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=True):
     lib().orc_rti_step(C.byref(q), m.nl, m.pw, m.pp, Bn, pN, pdt, args[0][1], args[1][1], args[2][1],
                        _p(x), _p(u), pxr, pur, px0, int(shift), _p(u0),
                        st.ctypes.data_as(C.POINTER(C.c_int)))
+    return u0, x, u, st
+
+
+def linearize2(quad, layers, N, dt, x, u):
+    """Second-order local model: fD [n][3], JD [n][3][17], HD [n][3][17][17], A, B, c."""
+    m = _MLP(layers or [])
+    N, pN = _i(N); dt, pdt = _d(dt)
+    x, px = _d(x); u, pu = _d(u)
+    n = int(N.sum())
+    fD = np.zeros((n, 3)); JD = np.zeros((n, 3, NZ)); HD = np.zeros((n, 3, NZ, NZ))
+    A = np.zeros((n, NX, NX)); B = np.zeros((n, NX, NU)); c = np.zeros((n, NX))
+    q = _quad(quad)
+    lib().orc_linearize2(C.byref(q), m.nl, m.pw, m.pp, len(N), pN, pdt, px, pu, _p(fD), _p(JD), _p(HD),
+                         _p(A), _p(B), _p(c))
+    return fD, JD, HD, A, B, c
+
+
+def rti_step2(quad, layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=True):
+    """RTI step with the second-order local model.  Returns (u0, x_new, u_new, status)."""
+    m = _MLP(layers or [])
+    N, pN = _i(N); dt, pdt = _d(dt)
+    x = np.array(x, dtype=np.float64, copy=True); u = np.array(u, dtype=np.float64, copy=True)
+    args = [_d(a) for a in (Q, R, QN)]
+    xref, pxr = _d(xref); uref, pur = _d(uref); x0m, px0 = _d(x0m)
+    Bn = len(N)
+    u0 = np.zeros((Bn, NU)); st = np.zeros(Bn, np.int32)
+    q = _quad(quad)
+    lib().orc_rti_step2(C.byref(q), m.nl, m.pw, m.pp, Bn, pN, pdt, args[0][1], args[1][1], args[2][1],
+                        _p(x), _p(u), pxr, pur, px0, int(shift), _p(u0), st.ctypes.data_as(C.POINTER(C.c_int)))
     return u0, x, u, st
 
 

@@ -126,6 +126,73 @@ void orc_mlp_fwd_jac(int nl, const int* w, const double* P, const double* z, dou
   free(a); free(T); free(a2); free(T2);
 }
 
+/* second order (the H_D of Eq. 4): forward-over-forward, carrying per unit
+ * the value a, the tangents t_j = da/dz_j and the second derivatives
+ * s_jm = d^2 a / dz_j dz_m through every layer.  With the pre-activation
+ * y = W a + b (tangents W t, second derivatives W s) and a = tanh(y):
+ *   t_j = tanh'(y) (W t)_j,
+ *   s_jm = tanh'(y) (W s)_jm + tanh''(y) (W t)_j (W t)_m,
+ * tanh' = 1 - a^2, tanh'' = -2 a (1 - a^2); the last layer is linear.
+ * f [nout], J [nout][nin], H [nout][nin][nin]. */
+void orc_mlp_fwd_hess(int nl, const int* w, const double* P, const double* z, double* f, double* J,
+                      double* H) {
+  int hm = mlp_max_width(nl, w), nin = w[0], n2 = nin * nin;
+  double* a = (double*)malloc(sizeof(double) * hm);
+  double* T = (double*)malloc(sizeof(double) * hm * nin);
+  double* S = (double*)malloc(sizeof(double) * hm * n2);
+  double* a2 = (double*)malloc(sizeof(double) * hm);
+  double* T2 = (double*)malloc(sizeof(double) * hm * nin);
+  double* S2 = (double*)malloc(sizeof(double) * hm * n2);
+  for (int i = 0; i < nin; ++i) {
+    a[i] = z[i];
+    for (int j = 0; j < nin; ++j) T[i * nin + j] = (i == j) ? 1.0 : 0.0;
+    for (int j = 0; j < n2; ++j) S[i * n2 + j] = 0.0;
+  }
+  const double* p = P;
+  for (int l = 0; l < nl; ++l) {
+    int fi = w[l], fo = w[l + 1];
+    const double* W = p;
+    const double* b = p + (size_t)fo * fi;
+    for (int i = 0; i < fo; ++i) {
+      double y = b[i];
+      for (int k = 0; k < fi; ++k) y += W[(size_t)i * fi + k] * a[k];
+      for (int j = 0; j < nin; ++j) {
+        double t = 0.0;
+        for (int k = 0; k < fi; ++k) t += W[(size_t)i * fi + k] * T[k * nin + j];
+        T2[i * nin + j] = t;
+      }
+      for (int j = 0; j < n2; ++j) {
+        double v = 0.0;
+        for (int k = 0; k < fi; ++k) v += W[(size_t)i * fi + k] * S[(size_t)k * n2 + j];
+        S2[(size_t)i * n2 + j] = v;
+      }
+      if (l < nl - 1) {
+        double th = tanh(y), d1 = 1.0 - th * th, d2 = -2.0 * th * d1;
+        a2[i] = th;
+        for (int j = 0; j < nin; ++j)
+          for (int m = 0; m < nin; ++m)
+            S2[(size_t)i * n2 + j * nin + m] =
+                d1 * S2[(size_t)i * n2 + j * nin + m] + d2 * T2[i * nin + j] * T2[i * nin + m];
+        for (int j = 0; j < nin; ++j) T2[i * nin + j] *= d1;
+      } else {
+        a2[i] = y;
+      }
+    }
+    for (int i = 0; i < fo; ++i) {
+      a[i] = a2[i];
+      for (int j = 0; j < nin; ++j) T[i * nin + j] = T2[i * nin + j];
+      for (int j = 0; j < n2; ++j) S[(size_t)i * n2 + j] = S2[(size_t)i * n2 + j];
+    }
+    p += (size_t)fo * fi + fo;
+  }
+  for (int i = 0; i < w[nl]; ++i) {
+    f[i] = a[i];
+    for (int j = 0; j < nin; ++j) J[i * nin + j] = T[i * nin + j];
+    for (int j = 0; j < n2; ++j) H[(size_t)i * n2 + j] = S[(size_t)i * n2 + j];
+  }
+  free(a); free(T); free(S); free(a2); free(T2); free(S2);
+}
+
 /* reverse-mode cross-check: forward pass storing activations, then one
  * adjoint sweep per output row */
 void orc_mlp_rev_jac(int nl, const int* w, const double* P, const double* z, double* J) {
@@ -256,10 +323,12 @@ void orc_quad_dfdz(const orc_quad* Qd, const double* x, const double* u, double*
 #undef DD
 }
 
-/* f_F + f_D* where f_D* is the first-order local model of Eq. 4 around
- * (xk, uk): fbar + J [x - xk; u - uk], added to dv/dt */
+/* f_F + f_D* where f_D* is the local model of Eq. 4 around (xk, uk),
+ * fbar + J dz (+ 1/2 dz' H_r dz with H != NULL, the second-order model),
+ * dz = [x - xk; u - uk], added to dv/dt */
 static void f_local(const orc_quad* Qd, const double* x, const double* u, const double* xk,
-                    const double* uk, const double* fbar, const double* J, double* xd) {
+                    const double* uk, const double* fbar, const double* J, const double* H,
+                    double* xd) {
   orc_quad_f(Qd, x, u, xd);
   if (!fbar) return;
   double dz[NZ];
@@ -268,6 +337,9 @@ static void f_local(const orc_quad* Qd, const double* x, const double* u, const 
   for (int r = 0; r < 3; ++r) {
     double s = fbar[r];
     for (int j = 0; j < NZ; ++j) s += J[r * NZ + j] * dz[j];
+    if (H)
+      for (int j = 0; j < NZ; ++j)
+        for (int m = 0; m < NZ; ++m) s += 0.5 * dz[j] * H[(r * NZ + j) * NZ + m] * dz[m];
     xd[7 + r] += s;
   }
 }
@@ -276,8 +348,8 @@ static void f_local(const orc_quad* Qd, const double* x, const double* u, const 
  * (13 x 17) propagated through the four stages:
  *   phi = x + dt/6 (k1 + 2 k2 + 2 k3 + k4),  A = dphi/dx,  B = dphi/du.
  * fbar/J may be NULL (nominal model only). */
-void orc_rk4_lin(const orc_quad* Qd, const double* x, const double* u, const double* fbar,
-                 const double* J, double dt, double* phi, double* A, double* B) {
+void orc_rk4_lin_h(const orc_quad* Qd, const double* x, const double* u, const double* fbar,
+                   const double* J, const double* H, double dt, double* phi, double* A, double* B) {
   double k[4][NX], dk[4][NX * NZ], xs[NX], S[NX * NZ], D[NX * NZ];
   double cst[4] = {0.0, 0.5, 0.5, 1.0};
   for (int s = 0; s < 4; ++s) {
@@ -285,11 +357,17 @@ void orc_rk4_lin(const orc_quad* Qd, const double* x, const double* u, const dou
     for (int i = 0; i < NX; ++i)
       for (int j = 0; j < NZ; ++j)
         S[i * NZ + j] = ((i == j) ? 1.0 : 0.0) + (s ? cst[s] * dt * dk[s - 1][i * NZ + j] : 0.0);
-    f_local(Qd, xs, u, x, u, fbar, J, k[s]);
+    f_local(Qd, xs, u, x, u, fbar, J, H, k[s]);
     orc_quad_dfdz(Qd, xs, u, D);
+    /* the local model's gradient at the stage point: J_r (+ H_r dz) */
     if (fbar)
       for (int r = 0; r < 3; ++r)
-        for (int j = 0; j < NZ; ++j) D[(7 + r) * NZ + j] += J[r * NZ + j];
+        for (int j = 0; j < NZ; ++j) {
+          double g = J[r * NZ + j];
+          if (H)
+            for (int m = 0; m < NX; ++m) g += H[(r * NZ + j) * NZ + m] * (xs[m] - x[m]);
+          D[(7 + r) * NZ + j] += g;
+        }
     /* d k_s / d[x;u] = Dx * S + Du * [0 I] */
     for (int i = 0; i < NX; ++i)
       for (int j = 0; j < NZ; ++j) {
@@ -308,6 +386,11 @@ void orc_rk4_lin(const orc_quad* Qd, const double* x, const double* u, const dou
       else B[i * NU + (j - NX)] = v;
     }
   }
+}
+
+void orc_rk4_lin(const orc_quad* Qd, const double* x, const double* u, const double* fbar,
+                 const double* J, double dt, double* phi, double* A, double* B) {
+  orc_rk4_lin_h(Qd, x, u, fbar, J, NULL, dt, phi, A, B);
 }
 
 /* drag residual used as the ground-truth aerodynamics:
@@ -756,14 +839,18 @@ static void offsets(int B, const int* N, size_t* xo, size_t* uo) {
 /* Linearise every shooting node (data-driven preparation + QP preparation,
  * Sec. III-B): fD[node][3], JD[node][3][17], A[node][13][13], B[node][13][4],
  * c[node][13] = phi_k - x_{k+1}.  nl = 0 means nominal model only. */
-void orc_linearize(const orc_quad* Qd, int nl, const int* w, const double* P, int B,
-                   const int* N, const double* dt, const double* x, const double* u, double* fD,
-                   double* JD, double* A, double* Bm, double* c) {
+/* second != 0: the second-order local model (H_D from orc_mlp_fwd_hess,
+ * written to HD [n][3][17][17] when HD != NULL) */
+static void linearize_core(const orc_quad* Qd, int nl, const int* w, const double* P, int B,
+                           const int* N, const double* dt, const double* x, const double* u,
+                           double* fD, double* JD, double* HD, double* A, double* Bm, double* c,
+                           int second) {
   size_t* xo = (size_t*)malloc(sizeof(size_t) * B);
   size_t* uo = (size_t*)malloc(sizeof(size_t) * B);
   offsets(B, N, xo, uo);
 #pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < B; ++b) {
+    double* H = (double*)malloc(sizeof(double) * 3 * NZ * NZ);
     for (int k = 0; k < N[b]; ++k) {
       size_t n = uo[b] + k;
       const double* xk = x + (xo[b] + k) * NX;
@@ -771,16 +858,32 @@ void orc_linearize(const orc_quad* Qd, int nl, const int* w, const double* P, in
       double z[NZ], f[3], J[3 * NZ], phi[NX];
       for (int i = 0; i < NX; ++i) z[i] = xk[i];
       for (int i = 0; i < NU; ++i) z[NX + i] = uk[i];
-      if (nl > 0) orc_mlp_fwd_jac(nl, w, P, z, f, J);
+      if (nl > 0 && second) orc_mlp_fwd_hess(nl, w, P, z, f, J, H);
+      else if (nl > 0) orc_mlp_fwd_jac(nl, w, P, z, f, J);
       else { memset(f, 0, sizeof(f)); memset(J, 0, sizeof(J)); }
-      orc_rk4_lin(Qd, xk, uk, nl > 0 ? f : NULL, nl > 0 ? J : NULL, dt[b], phi, A + n * NX * NX,
-                  Bm + n * NX * NU);
+      orc_rk4_lin_h(Qd, xk, uk, nl > 0 ? f : NULL, nl > 0 ? J : NULL, (nl > 0 && second) ? H : NULL,
+                    dt[b], phi, A + n * NX * NX, Bm + n * NX * NU);
       for (int i = 0; i < NX; ++i) c[n * NX + i] = phi[i] - xk[NX + i];
       if (fD) memcpy(fD + n * 3, f, sizeof(f));
       if (JD) memcpy(JD + n * 3 * NZ, J, sizeof(J));
+      if (HD && second) memcpy(HD + n * 3 * NZ * NZ, H, sizeof(double) * 3 * NZ * NZ);
     }
+    free(H);
   }
   free(xo); free(uo);
+}
+
+void orc_linearize(const orc_quad* Qd, int nl, const int* w, const double* P, int B,
+                   const int* N, const double* dt, const double* x, const double* u, double* fD,
+                   double* JD, double* A, double* Bm, double* c) {
+  linearize_core(Qd, nl, w, P, B, N, dt, x, u, fD, JD, NULL, A, Bm, c, 0);
+}
+
+/* the same with the second-order local model of Eq. 4 (HD may be NULL) */
+void orc_linearize2(const orc_quad* Qd, int nl, const int* w, const double* P, int B,
+                    const int* N, const double* dt, const double* x, const double* u, double* fD,
+                    double* JD, double* HD, double* A, double* Bm, double* c) {
+  linearize_core(Qd, nl, w, P, B, N, dt, x, u, fD, JD, HD, A, Bm, c, 1);
 }
 
 /* One real-time iteration for every instance (Sec. III-B): linearise around
@@ -795,7 +898,8 @@ void orc_linearize(const orc_quad* Qd, int nl, const int* w, const double* P, in
 static void rti_core(const orc_quad* Qd, int nl, const int* w, const double* P, int B, const int* N,
                      const double* dt, const double* Q, const double* R, const double* QN, double* x,
                      double* u, const double* xref, const double* uref, const double* x0m,
-                     int shift, double* u0, int* status, int box, int max_iter, int* iters) {
+                     int shift, double* u0, int* status, int box, int max_iter, int* iters,
+                     int second) {
   size_t* xo = (size_t*)malloc(sizeof(size_t) * B);
   size_t* uo = (size_t*)malloc(sizeof(size_t) * B);
   offsets(B, N, xo, uo);
@@ -803,7 +907,7 @@ static void rti_core(const orc_quad* Qd, int nl, const int* w, const double* P, 
   double* A = (double*)malloc(sizeof(double) * nn * NX * NX);
   double* Bm = (double*)malloc(sizeof(double) * nn * NX * NU);
   double* c = (double*)malloc(sizeof(double) * nn * NX);
-  orc_linearize(Qd, nl, w, P, B, N, dt, x, u, NULL, NULL, A, Bm, c);
+  linearize_core(Qd, nl, w, P, B, N, dt, x, u, NULL, NULL, NULL, A, Bm, c, second);
 #pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < B; ++b) {
     int Nb = N[b];
@@ -850,7 +954,15 @@ void orc_rti_step(const orc_quad* Qd, int nl, const int* w, const double* P, int
                   const double* dt, const double* Q, const double* R, const double* QN, double* x,
                   double* u, const double* xref, const double* uref, const double* x0m,
                   int shift, double* u0, int* status) {
-  rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift, u0, status, 0, 0, NULL);
+  rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift, u0, status, 0, 0, NULL, 0);
+}
+
+/* RTI step with the second-order local model of Eq. 4 */
+void orc_rti_step2(const orc_quad* Qd, int nl, const int* w, const double* P, int B, const int* N,
+                   const double* dt, const double* Q, const double* R, const double* QN, double* x,
+                   double* u, const double* xref, const double* uref, const double* x0m,
+                   int shift, double* u0, int* status) {
+  rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift, u0, status, 0, 0, NULL, 1);
 }
 
 void orc_rti_step_box(const orc_quad* Qd, int nl, const int* w, const double* P, int B,
@@ -859,7 +971,7 @@ void orc_rti_step_box(const orc_quad* Qd, int nl, const int* w, const double* P,
                       const double* uref, const double* x0m, int shift, int max_iter, double* u0,
                       int* status, int* iters) {
   rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift, u0, status, 1, max_iter,
-           iters);
+           iters, 0);
 }
 
 /* Closed loop: each control step runs one RTI step from the plant's state,
@@ -899,7 +1011,7 @@ static void closed_loop_core(const orc_quad* Qd, int nl, const int* w, const dou
       for (int k = 0; k < N[b]; ++k)
         memcpy(ur + (uo[b] + k) * NU, urt + ((size_t)b * (T - 1) + t + k) * NU, sizeof(double) * NU);
     }
-    rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xr, ur, xp, 1, u0, st, box, max_iter, NULL);
+    rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xr, ur, xp, 1, u0, st, box, max_iter, NULL, 0);
 #pragma omp parallel for
     for (int b = 0; b < B; ++b) {
       double xn[NX];

@@ -624,3 +624,100 @@ def test_di_long_horizon_gain_is_the_lqr_gain(orc):
     st, dx, du, K, k = orc.riccati(A, B, c, x, u, x, u, Q, R, Q, np.array([1.0, 0.0]), nx=2, nu=1,
                                    return_gains=True)
     assert st == 0 and np.allclose(K[0], K_lqr, rtol=1e-9, atol=1e-12)
+
+
+# --------------------------------------- second-order local model (Eq. 4, H_D)
+
+@pytest.mark.parametrize("widths", [[17, 16, 16, 3], [17, 24, 3]])
+def test_mlp_hessian_vs_fd_of_jacobian(orc, widths):
+    layers = W.xavier_mlp(widths, 11)
+    z = np.random.default_rng(12).normal(0, 0.8, 17)
+    f, J, H = orc.mlp_fwd_hess(layers, z)
+    f1, J1 = orc.mlp_fwd_jac(layers, z)
+    assert np.array_equal(f, f1) or np.allclose(f, f1, rtol=0, atol=1e-15)
+    assert np.allclose(J, J1, rtol=0, atol=1e-15)
+    assert np.allclose(H, np.transpose(H, (0, 2, 1)), rtol=0, atol=1e-14)
+    Hfd = np.zeros_like(H)
+    for j in range(17):
+        zp, zm = z.copy(), z.copy()
+        zp[j] += 1e-5; zm[j] -= 1e-5
+        Hfd[:, :, j] = (orc.mlp_fwd_jac(layers, zp)[1] - orc.mlp_fwd_jac(layers, zm)[1]) / 2e-5
+    assert _rel(H, Hfd) < 1e-7
+
+
+def test_rk4_second_order_sensitivities_vs_fd(orc):
+    # A, B of the second-order local model against central differences of
+    # the RK4 map (expansion point held fixed)
+    layers = W.xavier_mlp([17, 16, 16, 3], 13)
+    rng = np.random.default_rng(14)
+    x = W.random_nodes(1, 15)[0][0].astype(np.float64)
+    u = np.full(4, 1.9)
+    z0 = np.concatenate([x, u])
+    f, J, H = orc.mlp_fwd_hess(layers, z0)
+    H = H * 50.0  # a strong curvature so that the term matters
+    dt = 0.05
+    phi, A, B = orc.rk4_lin(QUAD, x, u, dt, f, J, H)
+    def step(xx, uu):
+        dz = np.concatenate([xx - x, uu - u])
+        ff = f + J @ dz + 0.5 * np.einsum('j,rjm,m->r', dz, H, dz)
+        JJ = J + H @ dz
+        return orc.rk4_lin(QUAD, xx, uu, dt, ff, JJ, H)[0]
+    h = 1e-6
+    for j in range(17):
+        xp, xm, up, um = x.copy(), x.copy(), u.copy(), u.copy()
+        if j < 13:
+            xp[j] += h; xm[j] -= h
+        else:
+            up[j - 13] += h; um[j - 13] -= h
+        col = (step(xp, up) - step(xm, um)) / (2 * h)
+        ref = A[:, j] if j < 13 else B[:, j - 13]
+        assert np.allclose(col, ref, rtol=0, atol=1e-7), j
+    phi1 = orc.rk4_lin(QUAD, x, u, dt, f, J)[0]
+    assert np.abs(phi - phi1).max() > 1e-9  # the second-order term changes the step
+
+
+def test_local_model_error_orders(orc):
+    # Sec. III: replacing the network by its local model costs O(dz^2) per
+    # evaluation for the first-order model and O(dz^3) for the second-order
+    # one; over one RK4 step (dz = O(dt)) the step errors fall as dt^3 and
+    # dt^4 when dt halves
+    layers = W.xavier_mlp([17, 16, 16, 3], 16)
+    x = W.random_nodes(1, 17)[0][0].astype(np.float64)
+    x[7:10] = [3.0, -2.0, 1.5]  # velocity so that the stage points move
+    u = np.array([2.3, 1.5, 2.0, 1.7])
+    f, J, H = orc.mlp_fwd_hess(layers, np.concatenate([x, u]))
+    e1, e2 = [], []
+    for dt in (0.08, 0.04, 0.02):
+        true = orc.rk4_true(QUAD, x, u, dt, kind=2, layers=layers)
+        e1.append(np.abs(orc.rk4_lin(QUAD, x, u, dt, f, J)[0] - true).max())
+        e2.append(np.abs(orc.rk4_lin(QUAD, x, u, dt, f, J, H)[0] - true).max())
+    r1 = [e1[0] / e1[1], e1[1] / e1[2]]
+    r2 = [e2[0] / e2[1], e2[1] / e2[2]]
+    assert all(6 < r < 10 for r in r1), r1
+    assert all(12 < r < 20 for r in r2), r2
+    assert e2[-1] < e1[-1]
+
+
+def test_rti_step2_is_the_kkt_solution(orc):
+    layers = W.xavier_mlp([17, 16, 16, 3], 18)
+    N = np.array([6, 4], np.int32); dt = np.array([0.05, 0.04])
+    ns, nn = int(N.sum()) + len(N), int(N.sum())
+    X, U = W.random_nodes(ns, 19)
+    x = X.astype(np.float64); u = U[:nn].astype(np.float64)
+    rng = np.random.default_rng(20)
+    xref = x + rng.normal(0, 0.1, x.shape); uref = u + rng.normal(0, 0.1, u.shape)
+    x0m = x[[0, N[0] + 1]] + rng.normal(0, 0.05, (2, 13))
+    Q = np.full(13, 2.0); R = np.full(4, 0.5)
+    u0, xn, un, st = orc.rti_step2(QUAD, layers, N, dt, Q, R, Q, x, u, xref, uref, x0m, shift=False)
+    assert np.all(st == 0)
+    _, _, _, A, B, c = orc.linearize2(QUAD, layers, N, dt, x, u)
+    _, _, A1, B1, c1 = orc.linearize(QUAD, layers, N, dt, x, u)
+    assert np.abs(A - A1).max() > 1e-12  # second order differs from first order
+    xs = us = 0
+    for b, Nb in enumerate(N):
+        s2, dx, du = orc.kkt_dense(A[us:us + Nb], B[us:us + Nb], c[us:us + Nb], x[xs:xs + Nb + 1],
+                                   u[us:us + Nb], xref[xs:xs + Nb + 1], uref[us:us + Nb], Q, R, Q, x0m[b])
+        assert s2 == 0
+        assert np.allclose(xn[xs:xs + Nb + 1], x[xs:xs + Nb + 1] + dx, rtol=0, atol=1e-9)
+        assert np.allclose(un[us:us + Nb], u[us:us + Nb] + du, rtol=0, atol=1e-9)
+        xs += Nb + 1; us += Nb
