@@ -96,6 +96,13 @@ typedef struct {
                        whose subproblems are masked Riccati sweeps; 0: no bounds
                        in the QP, only the sent u_0 is clamped */
   int box_max_iter; /* subproblems per QP at most (0: 20) */
+  int second_order; /* 1: linearise with the second-order local model of Eq. 4,
+                       f_D* = f_D + J_D dz + 1/2 dz' H_D dz per output, H_D the
+                       network Hessian at the node (forward-over-forward, FP32);
+                       needs RTN_FP32, the quadrotor model and a network.  The
+                       RK4 stages see the quadratic term along the state
+                       deviation (u is held over the interval). 0: Eq. 4 to
+                       first order (J_D only) */
 } rtn_options;
 
 /* Create a controller batch of `batch` instances with horizons N[b] >= 1 and
@@ -149,6 +156,12 @@ rtn_status rtn_get_iterate(rtn_ctx* ctx, float* x, float* u);
  * the precision chosen at create.  RTN_E_UNSUPPORTED if the context has no
  * network. */
 rtn_status rtn_mlp_eval(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+
+/* (f4) Second-order data-driven preparation (Eq. 4 to second order): f_D,
+ * J_D as rtn_mlp_eval and the Hessian HD dev [sum N_b][3][17][17] (both
+ * triangles, HD[n][r][i][j] = d^2 f_D,r / dz_i dz_j) at every node, in FP32.
+ * RTN_E_UNSUPPORTED unless the context was created with second_order. */
+rtn_status rtn_mlp_hess(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD);
 
 /* (a1)+(a2) Linearise every node (Eq. 2 with the local model of Eq. 4):
  * fD, JD as above (may be NULL), A dev [sum N_b][13][13], B dev

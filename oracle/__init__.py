@@ -346,8 +346,9 @@ def di_rti_step(layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=True):
 
 
 def closed_loop(quad, layers, plant_kind, plant_layers, N, dt, Q, R, QN, x0, xrt, urt, steps,
-                box=False, max_iter=20):
-    """Returns traj [steps][B][13] and u0 history [steps][B][4]."""
+                box=False, max_iter=20, second=False):
+    """Returns traj [steps][B][13] and u0 history [steps][B][4]; second: the
+    second-order local model of Eq. 4 in every RTI step (no bounds)."""
     m = _MLP(layers or [])
     pm = _MLP(plant_layers or [])
     N, pN = _i(N); dt, pdt = _d(dt)
@@ -359,6 +360,9 @@ def closed_loop(quad, layers, plant_kind, plant_layers, N, dt, Q, R, QN, x0, xrt
         lib().orc_closed_loop_box(C.byref(q), m.nl, m.pw, m.pp, plant_kind, pm.nl, pm.pw, pm.pp, Bn,
                                   pN, pdt, *[a[1] for a in args], T, steps, int(max_iter),
                                   _p(traj), _p(uh))
+    elif second:
+        lib().orc_closed_loop2(C.byref(q), m.nl, m.pw, m.pp, plant_kind, pm.nl, pm.pw, pm.pp, Bn, pN,
+                               pdt, *[a[1] for a in args], T, steps, _p(traj), _p(uh))
     else:
         lib().orc_closed_loop(C.byref(q), m.nl, m.pw, m.pp, plant_kind, pm.nl, pm.pw, pm.pp, Bn, pN,
                               pdt, *[a[1] for a in args], T, steps, _p(traj), _p(uh))

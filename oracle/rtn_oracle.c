@@ -985,7 +985,7 @@ static void closed_loop_core(const orc_quad* Qd, int nl, const int* w, const dou
                              const int* N, const double* dt, const double* Q, const double* R,
                              const double* QN, const double* x0, const double* xrt,
                              const double* urt, int T, int steps, double* traj, double* u0_hist,
-                             int box, int max_iter) {
+                             int box, int max_iter, int second) {
   size_t* xo = (size_t*)malloc(sizeof(size_t) * B);
   size_t* uo = (size_t*)malloc(sizeof(size_t) * B);
   offsets(B, N, xo, uo);
@@ -1011,7 +1011,7 @@ static void closed_loop_core(const orc_quad* Qd, int nl, const int* w, const dou
       for (int k = 0; k < N[b]; ++k)
         memcpy(ur + (uo[b] + k) * NU, urt + ((size_t)b * (T - 1) + t + k) * NU, sizeof(double) * NU);
     }
-    rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xr, ur, xp, 1, u0, st, box, max_iter, NULL, 0);
+    rti_core(Qd, nl, w, P, B, N, dt, Q, R, QN, x, u, xr, ur, xp, 1, u0, st, box, max_iter, NULL, second);
 #pragma omp parallel for
     for (int b = 0; b < B; ++b) {
       double xn[NX];
@@ -1030,7 +1030,18 @@ void orc_closed_loop(const orc_quad* Qd, int nl, const int* w, const double* P, 
                      const double* x0, const double* xrt, const double* urt, int T, int steps,
                      double* traj, double* u0_hist) {
   closed_loop_core(Qd, nl, w, P, plant_kind, pnl, pw, PP, B, N, dt, Q, R, QN, x0, xrt, urt, T,
-                   steps, traj, u0_hist, 0, 0);
+                   steps, traj, u0_hist, 0, 0, 0);
+}
+
+/* The closed loop with the second-order local model of Eq. 4 in every RTI
+ * step. */
+void orc_closed_loop2(const orc_quad* Qd, int nl, const int* w, const double* P, int plant_kind,
+                      int pnl, const int* pw, const double* PP, int B, const int* N,
+                      const double* dt, const double* Q, const double* R, const double* QN,
+                      const double* x0, const double* xrt, const double* urt, int T, int steps,
+                      double* traj, double* u0_hist) {
+  closed_loop_core(Qd, nl, w, P, plant_kind, pnl, pw, PP, B, N, dt, Q, R, QN, x0, xrt, urt, T,
+                   steps, traj, u0_hist, 0, 0, 1);
 }
 
 void orc_closed_loop_box(const orc_quad* Qd, int nl, const int* w, const double* P,
@@ -1040,7 +1051,7 @@ void orc_closed_loop_box(const orc_quad* Qd, int nl, const int* w, const double*
                          const double* urt, int T, int steps, int max_iter, double* traj,
                          double* u0_hist) {
   closed_loop_core(Qd, nl, w, P, plant_kind, pnl, pw, PP, B, N, dt, Q, R, QN, x0, xrt, urt, T,
-                   steps, traj, u0_hist, 1, max_iter);
+                   steps, traj, u0_hist, 1, max_iter, 0);
 }
 
 /* ---------------------------------------------------- double integrator --- */

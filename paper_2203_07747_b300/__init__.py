@@ -27,7 +27,7 @@ EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_rese
            "rtn_mlp_eval_f32_noalloc", "rtn_device_error", "rtn_tc_variants",
            "rtn_tc_variant_info", "rtn_tc_select", "rtn_autotune", "rtn_tc_trace",
            "rtn_tc_trace_read", "rtn_drag_targets", "rtn_mse_grad", "rtn_train",
-           "rtn_get_params", "rtn_box_iterations"]
+           "rtn_get_params", "rtn_box_iterations", "rtn_mlp_hess"]
 
 _lib = None
 
@@ -47,7 +47,7 @@ class _MLP(C.Structure):
 
 class _Opt(C.Structure):
     _fields_ = [("precision", C.c_int), ("riccati_f64", C.c_int), ("shift", C.c_int),
-                ("box_qp", C.c_int), ("box_max_iter", C.c_int)]
+                ("box_qp", C.c_int), ("box_max_iter", C.c_int), ("second_order", C.c_int)]
 
 
 def lib_path():
@@ -80,6 +80,7 @@ def load(build_if_missing=False):
     L.rtn_set_iterate.argtypes = [vp, vp, vp]
     L.rtn_get_iterate.argtypes = [vp, vp, vp]
     L.rtn_mlp_eval.argtypes = [vp] * 5
+    L.rtn_mlp_hess.argtypes = [vp] * 6
     L.rtn_linearize.argtypes = [vp] * 8
     L.rtn_qp_solve.argtypes = [vp] * 12
     L.rtn_rti_step.argtypes = [vp] * 6
@@ -132,7 +133,8 @@ class Controller:
     """A batch of B controller instances (one RTI-SQP problem each)."""
 
     def __init__(self, N, dt, Q, R, QN=None, quad=None, layers=None, precision="fp32",
-                 riccati_f64=False, shift=True, stream=None, box_qp=False, box_max_iter=20):
+                 riccati_f64=False, shift=True, stream=None, box_qp=False, box_max_iter=20,
+                 second_order=False):
         import torch
         L = load()
         self.N = np.ascontiguousarray(N, dtype=np.int32)
@@ -161,8 +163,9 @@ class Controller:
             mlp = _MLP(len(layers), w, Wp, bp)
             mlp_p = C.byref(mlp)
         opt = _Opt(PRECISION[precision], int(bool(riccati_f64)), int(bool(shift)), int(bool(box_qp)),
-                   int(box_max_iter))
+                   int(box_max_iter), int(bool(second_order)))
         self.box_qp = bool(box_qp)
+        self.second_order = bool(second_order)
         self.precision = precision
         self.stream = stream
         h = C.c_void_p()
@@ -327,6 +330,19 @@ class Controller:
                     "rtn_mlp_eval")
         return fD, JD
 
+    def mlp_hess(self, x, u):
+        """f_D, J_D and the network Hessian H_D [n][3][17][17] (second_order
+        contexts only)."""
+        import torch
+        n = self.n_nodes
+        fD, JD, HD = self._empty(n, NO), self._empty(n, NO, NZ), self._empty(n, NO, NZ, NZ)
+        self._check(load().rtn_mlp_hess(self._h, _ptr(x, torch.float32, (self.n_states, NX), "x"),
+                                        _ptr(u, torch.float32, (n, NU), "u"),
+                                        _ptr(fD, torch.float32, (n, NO), "fD"),
+                                        _ptr(JD, torch.float32, (n, NO, NZ), "JD"),
+                                        _ptr(HD, torch.float32, (n, NO, NZ, NZ), "HD")), "rtn_mlp_hess")
+        return fD, JD, HD
+
     def linearize(self, x, u, out=None):
         import torch
         n = self.n_nodes
@@ -421,7 +437,7 @@ class DIController:
             mlp = _MLP(len(layers), w, Wp, bp)
             self._keep.append(mlp)
             mlp_p = C.byref(mlp)
-        opt = _Opt(PRECISION["fp32"], 0, int(bool(shift)), 0, 0)
+        opt = _Opt(PRECISION["fp32"], 0, int(bool(shift)), 0, 0, 0)
         self.stream = stream
         h = C.c_void_p()
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))

@@ -79,12 +79,15 @@ rtn_status run_mlp(rtn_ctx* ctx, const float* x, const float* u, float* fD, floa
 
 rtn_status linearize_impl(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD,
                           float* A, float* Bm, float* c) {
-  if (ctx->has_mlp) {
+  if (ctx->opt.second_order) {
+    cudaError_t e = mlp_hess_forward(ctx, x, u, fD, JD, ctx->HD);
+    if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("mlp_hess: ") + cudaGetErrorString(e));
+  } else if (ctx->has_mlp) {
     rtn_status st = run_mlp(ctx, x, u, fD, JD);
     if (st != RTN_OK) return st;
   }
-  cudaError_t e = rk4_sens(ctx, x, u, ctx->has_mlp ? fD : nullptr, ctx->has_mlp ? JD : nullptr, A,
-                           Bm, c);
+  cudaError_t e = rk4_sens(ctx, x, u, ctx->has_mlp ? fD : nullptr, ctx->has_mlp ? JD : nullptr,
+                           ctx->opt.second_order ? ctx->HD : nullptr, A, Bm, c);
   if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("rk4: ") + cudaGetErrorString(e));
   return RTN_OK;
 }
@@ -223,12 +226,17 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     nn += N[b];
   }
   if (nn + batch > (1LL << 28)) { g_create_err = "batch too large"; return RTN_E_INVAL; }
-  rtn_options o{RTN_FP32, 0, 1, 0, 0};
+  rtn_options o{RTN_FP32, 0, 1, 0, 0, 0};
   if (opt) o = *opt;
   if (o.precision < RTN_FP32 || o.precision > RTN_BF16X2) { g_create_err = "bad precision"; return RTN_E_INVAL; }
   if (o.box_max_iter < 0) { g_create_err = "box_max_iter must be >= 0"; return RTN_E_INVAL; }
   if (o.box_max_iter == 0) o.box_max_iter = 20;
   o.box_qp = o.box_qp ? 1 : 0;
+  o.second_order = o.second_order ? 1 : 0;
+  if (o.second_order && (di || !mlp || o.precision != RTN_FP32)) {
+    g_create_err = "second_order needs the quadrotor model, a network and RTN_FP32";
+    return RTN_E_UNSUPPORTED;
+  }
   if (di) {
     if (o.precision != RTN_FP32 || o.box_qp || o.riccati_f64) {
       g_create_err = "the double-integrator model runs in FP32 (network and QP), without bounds";
@@ -316,6 +324,12 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
         size_t na = (size_t)net.h_max * NC * us;
         CK(dalloc(&ctx->act0, na));
         CK(dalloc(&ctx->act1, na));
+        if (o.second_order) {
+          CK(mlp_hess_prepare());
+          CK(dalloc(&ctx->HD, (size_t)us * NO * NZ * NZ));
+          CK(dalloc(&ctx->h2_x, mlp_hess_act_floats(ctx)));
+          CK(dalloc(&ctx->h2_z, mlp_hess_act_floats(ctx)));
+        }
       } else {
         std::string e;
         cudaError_t ce = mlp_tc_prepare(ctx, e);
@@ -379,7 +393,8 @@ void rtn_destroy(rtn_ctx* ctx) {
   void* ptrs[] = {L.N, L.dt, L.dt64, L.xoff, L.uoff, L.node_inst, L.order, ctx->net.W32, ctx->net.b32,
                   ctx->net.P64, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c, ctx->K,
                   ctx->kff, ctx->act0, ctx->act1, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0,
-                  ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters};
+                  ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters, ctx->HD,
+                  ctx->h2_x, ctx->h2_z};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->di) {
@@ -456,6 +471,14 @@ rtn_status rtn_mlp_eval(rtn_ctx* ctx, const float* x, const float* u, float* fD,
     return RTN_OK;
   }
   return run_mlp(ctx, x, u, fD, JD);
+}
+
+rtn_status rtn_mlp_hess(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x || !u || !fD || !JD || !HD) return fail(ctx, RTN_E_INVAL, "rtn_mlp_hess: NULL argument");
+  if (!ctx->opt.second_order) return fail(ctx, RTN_E_UNSUPPORTED, "rtn_mlp_hess: context has no second-order model");
+  CK(mlp_hess_forward(ctx, x, u, fD, JD, HD));
+  return RTN_OK;
 }
 
 rtn_status rtn_linearize(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD,

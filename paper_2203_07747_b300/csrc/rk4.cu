@@ -2,9 +2,10 @@
 //
 // For node k the continuity condition of Eq. 2 needs phi_k = RK4(x_k, u_k),
 // A_k = dphi/dx and B_k = dphi/du (Sec. III-A), where the dynamics are the
-// nominal quadrotor model of Eq. 6 plus the first-order local model of the
-// residual (Eq. 4), f_D*(x, u) = fbar + J_D [x - x_k; u - u_k], added to dv/dt.
-// u is held over the interval.
+// nominal quadrotor model of Eq. 6 plus the local model of the residual
+// (Eq. 4), f_D*(x, u) = fbar + J_D dz (+ 1/2 dz' H_r dz for the second-order
+// model), dz = [x - x_k; u - u_k], added to dv/dt.  u is held over the
+// interval, so dz has no input part at the stage points.
 //
 // One thread per (node, column j of [A | B]): the thread integrates the node
 // and carries one sensitivity direction d(stage)/d z_j through the four
@@ -87,7 +88,8 @@ __device__ __forceinline__ void jvp_nominal(const QuadParams& P, const float* x,
 
 __global__ void __launch_bounds__(256) rk4_sens_kernel(
     QuadParams P, const float* __restrict__ x, const float* __restrict__ u,
-    const float* __restrict__ fD, const float* __restrict__ JD, const int* __restrict__ node_inst,
+    const float* __restrict__ fD, const float* __restrict__ JD, const float* __restrict__ HD,
+    const int* __restrict__ node_inst,
     const float* __restrict__ dt_inst, int n_nodes, float* __restrict__ A, float* __restrict__ Bm,
     float* __restrict__ c) {
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -152,6 +154,24 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
         }
 #pragma unroll
         for (int i = 0; i < NU; ++i) dv = fmaf(J[r][NX + i], du[i], dv);
+        if (HD && s > 0) {
+          // g = H_r dz (dz = xs - x0 on the state part): value + 1/2 dz'g,
+          // directional derivative + g . [S; du]
+          const float* Hr = HD + ((size_t)n * NO + r) * NZ * NZ;
+          float q = 0.0f;
+          for (int i = 0; i < NZ; ++i) {
+            float g = 0.0f;
+#pragma unroll
+            for (int m = 0; m < NX; ++m) g = fmaf(__ldg(Hr + i * NZ + m), xs[m] - x0[m], g);
+            if (i < NX) {
+              q = fmaf(0.5f * (xs[i] - x0[i]), g, q);
+              dv = fmaf(g, Ss[i], dv);
+            } else {
+              dv = fmaf(g, du[i - NX], dv);
+            }
+          }
+          v += q;
+        }
         k[7 + r] += v;
         dk[7 + r] += dv;
       }
@@ -182,11 +202,11 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
 }  // namespace
 
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
-                     const float* JD, float* A, float* Bm, float* c) {
+                     const float* JD, const float* HD, float* A, float* Bm, float* c) {
   const int nn = ctx->lay.n_nodes;
   long long tot = (long long)nn * NZ;
   rk4_sens_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(
-      ctx->quad, x, u, fD, JD, ctx->lay.node_inst, ctx->lay.dt, nn, A, Bm, c);
+      ctx->quad, x, u, fD, JD, fD ? HD : nullptr, ctx->lay.node_inst, ctx->lay.dt, nn, A, Bm, c);
   return cudaGetLastError();
 }
 

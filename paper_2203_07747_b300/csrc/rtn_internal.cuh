@@ -129,6 +129,11 @@ struct rtn_ctx {
   float *fD = nullptr, *JD = nullptr, *A = nullptr, *Bm = nullptr, *c = nullptr;
   void *K = nullptr, *kff = nullptr;      // Riccati gains (float or double) [n][4][13], [n][4]
   float *act0 = nullptr, *act1 = nullptr; // FP32 network activations [h_max][18 n_nodes]
+  // second-order local model (rtn_options.second_order): network Hessians
+  // [n_nodes][3][17][17] and the activations of forward-over-forward
+  // differentiation [h_max][171 n_nodes] (mlp_hess.cu)
+  float* HD = nullptr;
+  float *h2_x = nullptr, *h2_z = nullptr;
   int* status = nullptr;                  // [B]
   int* dev_t = nullptr;                   // closed-loop step counter
   float* x0f = nullptr;                   // [B][13] float copy of the plant state
@@ -147,6 +152,11 @@ struct rtn_ctx {
 namespace rtn {
 
 // ---- launchers (each returns cudaGetLastError()) --------------------------
+
+// second-order local model (mlp_hess.cu): f_D, J_D, H_D of every node
+cudaError_t mlp_hess_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD);
+size_t mlp_hess_act_floats(const rtn_ctx* ctx);
+cudaError_t mlp_hess_prepare();
 
 // f3, double integrator (di.cu): network value + Jacobian of every node,
 // linearisation (A [n][2][2], B [n][2], c [n][2]) and the RTI step
@@ -184,7 +194,7 @@ cudaError_t mlp_rev2_launch(rtn_ctx* ctx, const float* x, const float* u, float*
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
-                     const float* JD, float* A, float* Bm, float* c);
+                     const float* JD, const float* HD, float* A, float* Bm, float* c);
 
 // a3 + a4.  Refs are read at rows base(b) + t + k where t is *t_dev (or 0) and
 // base(b) = b * stride when stride > 0, else the layout's own offset of
