@@ -82,6 +82,16 @@ def unpack_mlp(widths, flat):
     return out
 
 
+def _n_out(layers):
+    """Outputs of a quadrotor residual network: 3 (linear acceleration) or 6
+    (the full residual of Eq. 7)."""
+    if not layers:
+        return 3
+    no = layers[-1][0].shape[0]
+    assert no in (3, 6), no
+    return no
+
+
 class _MLP:
     def __init__(self, layers):
         self.nl, w, p = pack_mlp(layers)
@@ -148,19 +158,23 @@ def qrot(q, v):
 
 
 def rk4_lin(quad, x, u, dt, fbar=None, J=None, H=None):
-    """RK4 of f_F + f_D* with sensitivities; H (3 x 17 x 17) selects the
-    second-order local model."""
+    """RK4 of f_F + f_D* with sensitivities; fbar has 3 entries (linear
+    acceleration residual) or 6 (the full residual of Eq. 7, rows 3-5 angular);
+    H (no x 17 x 17) selects the second-order local model."""
     x, px = _d(x); u, pu = _d(u)
     phi = np.zeros(NX); A = np.zeros((NX, NX)); B = np.zeros((NX, NU))
     q = _quad(quad)
     ph = None
+    no = 3
     if fbar is None:
         pf = pj = None
     else:
         fbar, pf = _d(fbar); J, pj = _d(J)
+        no = fbar.size
+        assert no in (3, 6) and J.size == no * NZ
         if H is not None:
             H, ph = _d(H)
-    lib().orc_rk4_lin_h(C.byref(q), px, pu, pf, pj, ph, C.c_double(dt), _p(phi), _p(A), _p(B))
+    lib().orc_rk4_lin_n(C.byref(q), px, pu, no, pf, pj, ph, C.c_double(dt), _p(phi), _p(A), _p(B))
     return phi, A, B
 
 
@@ -228,12 +242,14 @@ def kkt_dense(A, B, c, x, u, xr, ur, Q, R, QN, x0m, nx=NX, nu=NU):
 
 
 def linearize(quad, layers, N, dt, x, u):
-    """All nodes: returns fD [n][3], JD [n][3][17], A, B, c."""
+    """All nodes: returns fD [n][no], JD [n][no][17], A, B, c (no = the
+    network's outputs, 3 or 6)."""
     m = _MLP(layers or [])
     N, pN = _i(N); dt, pdt = _d(dt)
     x, px = _d(x); u, pu = _d(u)
     n = int(N.sum())
-    fD = np.zeros((n, 3)); JD = np.zeros((n, 3, NZ))
+    no = _n_out(layers)
+    fD = np.zeros((n, no)); JD = np.zeros((n, no, NZ))
     A = np.zeros((n, NX, NX)); B = np.zeros((n, NX, NU)); c = np.zeros((n, NX))
     q = _quad(quad)
     lib().orc_linearize(C.byref(q), m.nl, m.pw, m.pp, len(N), pN, pdt, px, pu, _p(fD), _p(JD),
@@ -258,12 +274,13 @@ def rti_step(quad, layers, N, dt, Q, R, QN, x, u, xref, uref, x0m, shift=True):
 
 
 def linearize2(quad, layers, N, dt, x, u):
-    """Second-order local model: fD [n][3], JD [n][3][17], HD [n][3][17][17], A, B, c."""
+    """Second-order local model: fD [n][no], JD [n][no][17], HD [n][no][17][17], A, B, c."""
     m = _MLP(layers or [])
     N, pN = _i(N); dt, pdt = _d(dt)
     x, px = _d(x); u, pu = _d(u)
     n = int(N.sum())
-    fD = np.zeros((n, 3)); JD = np.zeros((n, 3, NZ)); HD = np.zeros((n, 3, NZ, NZ))
+    no = _n_out(layers)
+    fD = np.zeros((n, no)); JD = np.zeros((n, no, NZ)); HD = np.zeros((n, no, NZ, NZ))
     A = np.zeros((n, NX, NX)); B = np.zeros((n, NX, NU)); c = np.zeros((n, NX))
     q = _quad(quad)
     lib().orc_linearize2(C.byref(q), m.nl, m.pw, m.pp, len(N), pN, pdt, px, pu, _p(fD), _p(JD), _p(HD),

@@ -325,16 +325,20 @@ void orc_quad_dfdz(const orc_quad* Qd, const double* x, const double* u, double*
 
 /* f_F + f_D* where f_D* is the local model of Eq. 4 around (xk, uk),
  * fbar + J dz (+ 1/2 dz' H_r dz with H != NULL, the second-order model),
- * dz = [x - xk; u - uk], added to dv/dt */
+ * dz = [x - xk; u - uk].  With no = 3 outputs the residual is a linear
+ * acceleration added to dv/dt; with no = 6 it is the full residual of Eq. 7,
+ * [0; 0; f_theta; f_psi]: rows 0-2 added to dv/dt, rows 3-5 (angular
+ * acceleration) to dw/dt.  In the state order [p, q, v, w] row r lands on
+ * component 7 + r in both cases. */
 static void f_local(const orc_quad* Qd, const double* x, const double* u, const double* xk,
-                    const double* uk, const double* fbar, const double* J, const double* H,
+                    const double* uk, int no, const double* fbar, const double* J, const double* H,
                     double* xd) {
   orc_quad_f(Qd, x, u, xd);
   if (!fbar) return;
   double dz[NZ];
   for (int i = 0; i < NX; ++i) dz[i] = x[i] - xk[i];
   for (int i = 0; i < NU; ++i) dz[NX + i] = u[i] - uk[i];
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < no; ++r) {
     double s = fbar[r];
     for (int j = 0; j < NZ; ++j) s += J[r * NZ + j] * dz[j];
     if (H)
@@ -348,7 +352,7 @@ static void f_local(const orc_quad* Qd, const double* x, const double* u, const 
  * (13 x 17) propagated through the four stages:
  *   phi = x + dt/6 (k1 + 2 k2 + 2 k3 + k4),  A = dphi/dx,  B = dphi/du.
  * fbar/J may be NULL (nominal model only). */
-void orc_rk4_lin_h(const orc_quad* Qd, const double* x, const double* u, const double* fbar,
+void orc_rk4_lin_n(const orc_quad* Qd, const double* x, const double* u, int no, const double* fbar,
                    const double* J, const double* H, double dt, double* phi, double* A, double* B) {
   double k[4][NX], dk[4][NX * NZ], xs[NX], S[NX * NZ], D[NX * NZ];
   double cst[4] = {0.0, 0.5, 0.5, 1.0};
@@ -357,11 +361,11 @@ void orc_rk4_lin_h(const orc_quad* Qd, const double* x, const double* u, const d
     for (int i = 0; i < NX; ++i)
       for (int j = 0; j < NZ; ++j)
         S[i * NZ + j] = ((i == j) ? 1.0 : 0.0) + (s ? cst[s] * dt * dk[s - 1][i * NZ + j] : 0.0);
-    f_local(Qd, xs, u, x, u, fbar, J, H, k[s]);
+    f_local(Qd, xs, u, x, u, no, fbar, J, H, k[s]);
     orc_quad_dfdz(Qd, xs, u, D);
     /* the local model's gradient at the stage point: J_r (+ H_r dz) */
     if (fbar)
-      for (int r = 0; r < 3; ++r)
+      for (int r = 0; r < no; ++r)
         for (int j = 0; j < NZ; ++j) {
           double g = J[r * NZ + j];
           if (H)
@@ -388,9 +392,15 @@ void orc_rk4_lin_h(const orc_quad* Qd, const double* x, const double* u, const d
   }
 }
 
+/* the 3-output residual (linear acceleration only) */
+void orc_rk4_lin_h(const orc_quad* Qd, const double* x, const double* u, const double* fbar,
+                   const double* J, const double* H, double dt, double* phi, double* A, double* B) {
+  orc_rk4_lin_n(Qd, x, u, 3, fbar, J, H, dt, phi, A, B);
+}
+
 void orc_rk4_lin(const orc_quad* Qd, const double* x, const double* u, const double* fbar,
                  const double* J, double dt, double* phi, double* A, double* B) {
-  orc_rk4_lin_h(Qd, x, u, fbar, J, NULL, dt, phi, A, B);
+  orc_rk4_lin_n(Qd, x, u, 3, fbar, J, NULL, dt, phi, A, B);
 }
 
 /* drag residual used as the ground-truth aerodynamics:
@@ -406,11 +416,14 @@ void orc_drag(const double* x, double* a) {
   for (int i = 0; i < 3; ++i) a[i] = -a[i] - 0.01 * nv * v[i];
 }
 
-/* true dynamics of the plant: f_F + residual; kind 0 none, 1 drag, 2 MLP */
+/* true dynamics of the plant: f_F + residual; kind 0 none, 1 drag, 2 MLP
+ * (3 outputs added to dv/dt, or 6: the full residual of Eq. 7, rows 3-5
+ * added to dw/dt) */
 static void f_true(const orc_quad* Qd, int kind, int nl, const int* w, const double* P,
                    const double* x, const double* u, double* xd) {
   orc_quad_f(Qd, x, u, xd);
-  double r[3] = {0, 0, 0};
+  double r[6] = {0, 0, 0, 0, 0, 0};
+  const int no = (kind == 2 && nl > 0) ? w[nl] : 3;
   if (kind == 1) orc_drag(x, r);
   if (kind == 2) {
     double z[NZ];
@@ -418,7 +431,7 @@ static void f_true(const orc_quad* Qd, int kind, int nl, const int* w, const dou
     for (int i = 0; i < NU; ++i) z[NX + i] = u[i];
     orc_mlp_forward(nl, w, P, z, r);
   }
-  for (int i = 0; i < 3; ++i) xd[7 + i] += r[i];
+  for (int i = 0; i < no; ++i) xd[7 + i] += r[i];
 }
 
 /* plain RK4 step of the true dynamics (no renormalisation) */
@@ -837,7 +850,8 @@ static void offsets(int B, const int* N, size_t* xo, size_t* uo) {
 }
 
 /* Linearise every shooting node (data-driven preparation + QP preparation,
- * Sec. III-B): fD[node][3], JD[node][3][17], A[node][13][13], B[node][13][4],
+ * Sec. III-B): fD[node][no], JD[node][no][17] (no = 3 or 6 network outputs),
+ * A[node][13][13], B[node][13][4],
  * c[node][13] = phi_k - x_{k+1}.  nl = 0 means nominal model only. */
 /* second != 0: the second-order local model (H_D from orc_mlp_fwd_hess,
  * written to HD [n][3][17][17] when HD != NULL) */
@@ -850,23 +864,24 @@ static void linearize_core(const orc_quad* Qd, int nl, const int* w, const doubl
   offsets(B, N, xo, uo);
 #pragma omp parallel for schedule(dynamic)
   for (int b = 0; b < B; ++b) {
-    double* H = (double*)malloc(sizeof(double) * 3 * NZ * NZ);
+    const int no = nl > 0 ? w[nl] : 3;
+    double* H = (double*)malloc(sizeof(double) * 6 * NZ * NZ);
     for (int k = 0; k < N[b]; ++k) {
       size_t n = uo[b] + k;
       const double* xk = x + (xo[b] + k) * NX;
       const double* uk = u + n * NU;
-      double z[NZ], f[3], J[3 * NZ], phi[NX];
+      double z[NZ], f[6], J[6 * NZ], phi[NX];
       for (int i = 0; i < NX; ++i) z[i] = xk[i];
       for (int i = 0; i < NU; ++i) z[NX + i] = uk[i];
       if (nl > 0 && second) orc_mlp_fwd_hess(nl, w, P, z, f, J, H);
       else if (nl > 0) orc_mlp_fwd_jac(nl, w, P, z, f, J);
       else { memset(f, 0, sizeof(f)); memset(J, 0, sizeof(J)); }
-      orc_rk4_lin_h(Qd, xk, uk, nl > 0 ? f : NULL, nl > 0 ? J : NULL, (nl > 0 && second) ? H : NULL,
+      orc_rk4_lin_n(Qd, xk, uk, no, nl > 0 ? f : NULL, nl > 0 ? J : NULL, (nl > 0 && second) ? H : NULL,
                     dt[b], phi, A + n * NX * NX, Bm + n * NX * NU);
       for (int i = 0; i < NX; ++i) c[n * NX + i] = phi[i] - xk[NX + i];
-      if (fD) memcpy(fD + n * 3, f, sizeof(f));
-      if (JD) memcpy(JD + n * 3 * NZ, J, sizeof(J));
-      if (HD && second) memcpy(HD + n * 3 * NZ * NZ, H, sizeof(double) * 3 * NZ * NZ);
+      if (fD) memcpy(fD + n * no, f, sizeof(double) * no);
+      if (JD) memcpy(JD + n * no * NZ, J, sizeof(double) * no * NZ);
+      if (HD && second) memcpy(HD + n * no * NZ * NZ, H, sizeof(double) * no * NZ * NZ);
     }
     free(H);
   }

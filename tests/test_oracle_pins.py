@@ -721,3 +721,112 @@ def test_rti_step2_is_the_kkt_solution(orc):
         assert np.allclose(xn[xs:xs + Nb + 1], x[xs:xs + Nb + 1] + dx, rtol=0, atol=1e-9)
         assert np.allclose(un[us:us + Nb], u[us:us + Nb] + du, rtol=0, atol=1e-9)
         xs += Nb + 1; us += Nb
+
+
+# ------------------------------ full residual of Eq. 7: [0; 0; f_theta; f_psi]
+
+def stack_residual(theta, psi):
+    """One 6-output network equal to the two networks of Eq. 7 side by side:
+    the first layer stacks their rows, deeper layers are block-diagonal."""
+    out = []
+    for l, ((Wt, bt), (Wp, bp)) in enumerate(zip(theta, psi)):
+        if l == 0:
+            Wl = np.vstack([Wt, Wp])
+        else:
+            Wl = np.zeros((Wt.shape[0] + Wp.shape[0], Wt.shape[1] + Wp.shape[1]))
+            Wl[:Wt.shape[0], :Wt.shape[1]] = Wt
+            Wl[Wt.shape[0]:, Wt.shape[1]:] = Wp
+        out.append((Wl, np.concatenate([bt, bp])))
+    return out
+
+
+def test_full_residual_constant_closed_form(orc):
+    # zero weights, output bias [b; a e_i]: with zero thrust the nominal model
+    # has no torque and no thrust, so v(t) = (b - g e_z) t, p(t) = v t / 2 and,
+    # the angular residual acting on one principal axis (w x J w = 0),
+    # w(t) = a e_i t -- all integrated exactly by RK4; q turns about e_i by
+    # a t^2 / 2 (RK4 error O(dt^5))
+    b, a, dt = np.array([0.3, -0.2, 0.5]), 1.7, 0.05
+    x = np.zeros(13); x[3] = 1.0
+    u = np.zeros(4)
+    acc = b - np.array([0.0, 0.0, QUAD["g"]])
+    for axis in range(3):
+        ang = np.zeros(3); ang[axis] = a
+        layers = [(np.zeros((8, 17)), np.zeros(8)), (np.zeros((6, 8)), np.concatenate([b, ang]))]
+        fbar, J = orc.mlp_fwd_jac(layers, np.concatenate([x, u]))
+        lin = orc.linearize(QUAD, layers, np.array([1], np.int32), np.array([dt]), np.vstack([x, x]), u[None])
+        for phi in (orc.rk4_lin(QUAD, x, u, dt, fbar, J)[0],
+                    orc.rk4_true(QUAD, x, u, dt, kind=2, layers=layers), lin[4][0] + x):
+            assert np.allclose(phi[0:3], acc * dt * dt / 2, rtol=0, atol=1e-15)
+            assert np.allclose(phi[7:10], acc * dt, rtol=0, atol=1e-15)
+            assert np.allclose(phi[10:13], ang * dt, rtol=0, atol=1e-15)
+            th = a * dt * dt / 2
+            qe = np.zeros(4); qe[0] = np.cos(th / 2); qe[1 + axis] = np.sin(th / 2)
+            assert np.allclose(phi[3:7], qe, rtol=0, atol=1e-9)
+
+
+def test_full_residual_stacked_networks(orc):
+    # the 6-output network of stacked theta / psi networks has the two
+    # networks' values, Jacobians and Hessians as its rows
+    theta = W.xavier_mlp([17, 12, 10, 3], 21)
+    psi = W.xavier_mlp([17, 9, 14, 3], 22)
+    full = stack_residual(theta, psi)
+    z = np.random.default_rng(23).normal(0, 0.7, 17)
+    f, J, H = orc.mlp_fwd_hess(full, z)
+    ft, Jt, Ht = orc.mlp_fwd_hess(theta, z)
+    fp, Jp, Hp = orc.mlp_fwd_hess(psi, z)
+    assert np.allclose(f, np.concatenate([ft, fp]), rtol=1e-15, atol=1e-16)
+    assert np.allclose(J, np.vstack([Jt, Jp]), rtol=1e-15, atol=1e-16)
+    assert np.allclose(H, np.concatenate([Ht, Hp]), rtol=1e-14, atol=1e-16)
+
+
+def test_full_residual_sensitivities_vs_fd(orc):
+    layers = W.xavier_mlp([17, 24, 16, 6], 24)
+    X, U = W.random_nodes(3, 25)
+    for x, u in zip(X, U):
+        z = np.concatenate([x, u])
+        fbar, J, H = orc.mlp_fwd_hess(layers, z)
+        for second in (False, True):
+            Hs = H * 20.0 if second else None
+            phi, A, B = orc.rk4_lin(QUAD, x, u, 0.05, fbar, J, Hs)
+            def ph(zz):
+                dz = zz - z
+                ff, JJ = fbar + J @ dz, J
+                if second:
+                    ff = ff + 0.5 * np.einsum('j,rjm,m->r', dz, Hs, dz)
+                    JJ = J + Hs @ dz
+                return orc.rk4_lin(QUAD, zz[:13], zz[13:], 0.05, ff, JJ, Hs)[0]
+            G = np.zeros((13, 17))
+            for j in range(17):
+                h = 1e-6 * max(1.0, abs(z[j]))
+                zp, zm = z.copy(), z.copy()
+                zp[j] += h; zm[j] -= h
+                G[:, j] = (ph(zp) - ph(zm)) / (2 * h)
+            assert _rel(np.hstack([A, B]), G) < 1e-7
+
+
+def test_full_residual_error_orders(orc):
+    # as for the 3-output residual: the local models' step errors against the
+    # true dynamics with the same 6-output network fall as dt^3 / dt^4; the
+    # angular rows are exercised (the psi block alone changes w)
+    layers = W.xavier_mlp([17, 16, 16, 6], 26)
+    x = W.random_nodes(1, 27)[0][0].astype(np.float64)
+    x[7:10] = [3.0, -2.0, 1.5]
+    u = np.array([2.3, 1.5, 2.0, 1.7])
+    f, J, H = orc.mlp_fwd_hess(layers, np.concatenate([x, u]))
+    e1, e2 = [], []
+    for dt in (0.08, 0.04, 0.02):
+        true = orc.rk4_true(QUAD, x, u, dt, kind=2, layers=layers)
+        e1.append(np.abs(orc.rk4_lin(QUAD, x, u, dt, f, J)[0] - true).max())
+        e2.append(np.abs(orc.rk4_lin(QUAD, x, u, dt, f, J, H)[0] - true).max())
+    r1 = [e1[0] / e1[1], e1[1] / e1[2]]
+    r2 = [e2[0] / e2[1], e2[1] / e2[2]]
+    assert all(6 < r < 10 for r in r1), r1
+    assert all(12 < r < 20 for r in r2), r2
+    # the psi rows move w: dropping them (3-output truncation) is a
+    # first-order error, far above the local model's
+    f3, J3 = f[:3], J[:3]
+    dt = 0.02
+    trunc = orc.rk4_lin(QUAD, x, u, dt, f3, J3)[0]
+    full = orc.rk4_lin(QUAD, x, u, dt, f, J)[0]
+    assert np.abs(trunc[10:13] - full[10:13]).max() > 100 * e1[-1]
