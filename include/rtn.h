@@ -23,7 +23,8 @@
  *     [sum_b (N_b + 1)][13] (x_0..x_N per instance, instance-major), inputs
  *     and per-node outputs as [sum_b N_b][...] in the same order.
  *   - Matrices are row-major float32: A [node][13][13], B [node][13][4],
- *     J_D [node][3][17] (columns: 13 state, then 4 input derivatives).
+ *     J_D [node][no][17] (columns: 13 state, then 4 input derivatives; no =
+ *     the network's outputs, 3 or 6, see rtn_mlp).
  *   - Pointers documented "dev" are device pointers owned by the caller; the
  *     library never frees them.  "host" pointers are read during the call.
  *   - Every call is asynchronous on the stream given to rtn_create, except
@@ -70,9 +71,16 @@ enum { RTN_PLANT_NOMINAL = 0, RTN_PLANT_DRAG = 1, RTN_PLANT_MLP = 2 };
 
 /* Residual network: n_layers weight matrices (hidden tanh layers then one
  * linear output layer).  widths has n_layers+1 entries, widths[0] = 17,
- * widths[n_layers] = 3.  W[l] is host float32 row-major
- * [widths[l+1]][widths[l]], b[l] host float32 [widths[l+1]].  Copied at
- * rtn_create; the caller keeps ownership. */
+ * widths[n_layers] = no, the outputs:
+ *   no = 3: a world-frame linear acceleration residual added to dv/dt;
+ *   no = 6: the full residual of Eq. 7, [0; 0; f_theta; f_psi]: rows 0-2
+ *     the linear acceleration (added to dv/dt), rows 3-5 the body angular
+ *     acceleration (added to domega/dt).  Two separate networks theta, psi
+ *     are one 6-output network whose first layer stacks their rows and whose
+ *     deeper layers are block-diagonal.  The 6-output residual runs on the
+ *     FP32 path (RTN_FP32; first or second order).
+ * W[l] is host float32 row-major [widths[l+1]][widths[l]], b[l] host float32
+ * [widths[l+1]].  Copied at rtn_create; the caller keeps ownership. */
 typedef struct {
   int n_layers;
   const int* widths;
@@ -111,7 +119,9 @@ typedef struct {
  * model only).  opt may be NULL (FP32, FP32 sweep, shift on).  cuda_stream is
  * a cudaStream_t (NULL = legacy default stream).
  * Two models:
- *   nx = 13, nu = 4: the quadrotor of Sec. V (quad required); network 17 -> 3;
+ *   nx = 13, nu = 4: the quadrotor of Sec. V (quad required); network 17 -> 3
+ *     (or 17 -> 6, the full residual, with RTN_FP32; RTN_E_UNSUPPORTED with
+ *     the tensor-core precisions);
  *   nx = 2, nu = 1: the double integrator of the runtime analysis (Sec. IV,
  *     Eq. 5): x = (p, v), u = commanded acceleration, f_F = (v, u); the
  *     network maps z = (p, v, u) to 1 output added to dv/dt (any hidden
@@ -152,13 +162,13 @@ rtn_status rtn_get_iterate(rtn_ctx* ctx, float* x, float* u);
 
 /* (a1) Data-driven preparation (Sec. III-B): f_D and J_D at every node of the
  * given points.  x dev [sum(N_b+1)][13] (x_N rows are ignored), u dev
- * [sum N_b][4]; outputs fD dev [sum N_b][3], JD dev [sum N_b][3][17].  Uses
+ * [sum N_b][4]; outputs fD dev [sum N_b][no], JD dev [sum N_b][no][17].  Uses
  * the precision chosen at create.  RTN_E_UNSUPPORTED if the context has no
  * network. */
 rtn_status rtn_mlp_eval(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
 
 /* (f4) Second-order data-driven preparation (Eq. 4 to second order): f_D,
- * J_D as rtn_mlp_eval and the Hessian HD dev [sum N_b][3][17][17] (both
+ * J_D as rtn_mlp_eval and the Hessian HD dev [sum N_b][no][17][17] (both
  * triangles, HD[n][r][i][j] = d^2 f_D,r / dz_i dz_j) at every node, in FP32.
  * RTN_E_UNSUPPORTED unless the context was created with second_order. */
 rtn_status rtn_mlp_hess(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD);
@@ -218,8 +228,8 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
  * acceleration), X dev [n][13], Y dev [n][3], FP32. */
 rtn_status rtn_drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y);
 
-/* (a6) Mean-squared-error loss 1/(3n) sum |f_D(x, u) - y|^2 of the context's
- * network on n samples (X dev [n][13], U dev [n][4], Y dev [n][3]) and its
+/* (a6) Mean-squared-error loss 1/(no n) sum |f_D(x, u) - y|^2 of the context's
+ * network on n samples (X dev [n][13], U dev [n][4], Y dev [n][no]) and its
  * gradient, FP32: grad dev [n_weights + n_biases] packed as all W[l]
  * (row-major, layer order) then all b[l]; loss dev float [1]. */
 rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,

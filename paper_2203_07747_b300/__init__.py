@@ -166,6 +166,9 @@ class Controller:
                    int(box_max_iter), int(bool(second_order)))
         self.box_qp = bool(box_qp)
         self.second_order = bool(second_order)
+        # network outputs: 3 (linear acceleration) or 6 (the full residual of
+        # Eq. 7: linear, then angular acceleration)
+        self.n_out = int(layers[-1][0].shape[0]) if layers else NO
         self.precision = precision
         self.stream = stream
         h = C.c_void_p()
@@ -268,7 +271,7 @@ class Controller:
         loss = self._empty(1)
         self._check(load().rtn_mse_grad(self._h, _ptr(X, torch.float32, (n, NX), "X"),
                                         _ptr(U, torch.float32, (n, NU), "U"),
-                                        _ptr(Y, torch.float32, (n, NO), "Y"), n,
+                                        _ptr(Y, torch.float32, (n, self.n_out), "Y"), n,
                                         _ptr(g, torch.float32, None, "grad"),
                                         _ptr(loss, torch.float32, None, "loss")), "rtn_mse_grad")
         return float(loss.item()), g
@@ -280,7 +283,7 @@ class Controller:
         losses = (C.c_float * max(steps, 1))()
         self._check(load().rtn_train(self._h, _ptr(X, torch.float32, (n, NX), "X"),
                                      _ptr(U, torch.float32, (n, NU), "U"),
-                                     _ptr(Y, torch.float32, (n, NO), "Y"), n, int(epochs), int(batch),
+                                     _ptr(Y, torch.float32, (n, self.n_out), "Y"), n, int(epochs), int(batch),
                                      float(lr), losses), "rtn_train")
         return np.frombuffer(losses, dtype=np.float32)[:steps].copy()
 
@@ -321,12 +324,12 @@ class Controller:
     # -- hot path ---------------------------------------------------------
     def mlp_eval(self, x, u, fD=None, JD=None):
         import torch
-        fD = self._empty(self.n_nodes, NO) if fD is None else fD
-        JD = self._empty(self.n_nodes, NO, NZ) if JD is None else JD
+        fD = self._empty(self.n_nodes, self.n_out) if fD is None else fD
+        JD = self._empty(self.n_nodes, self.n_out, NZ) if JD is None else JD
         self._check(load().rtn_mlp_eval(self._h, _ptr(x, torch.float32, (self.n_states, NX), "x"),
                                         _ptr(u, torch.float32, (self.n_nodes, NU), "u"),
-                                        _ptr(fD, torch.float32, (self.n_nodes, NO), "fD"),
-                                        _ptr(JD, torch.float32, (self.n_nodes, NO, NZ), "JD")),
+                                        _ptr(fD, torch.float32, (self.n_nodes, self.n_out), "fD"),
+                                        _ptr(JD, torch.float32, (self.n_nodes, self.n_out, NZ), "JD")),
                     "rtn_mlp_eval")
         return fD, JD
 
@@ -335,25 +338,25 @@ class Controller:
         contexts only)."""
         import torch
         n = self.n_nodes
-        fD, JD, HD = self._empty(n, NO), self._empty(n, NO, NZ), self._empty(n, NO, NZ, NZ)
+        fD, JD, HD = self._empty(n, self.n_out), self._empty(n, self.n_out, NZ), self._empty(n, self.n_out, NZ, NZ)
         self._check(load().rtn_mlp_hess(self._h, _ptr(x, torch.float32, (self.n_states, NX), "x"),
                                         _ptr(u, torch.float32, (n, NU), "u"),
-                                        _ptr(fD, torch.float32, (n, NO), "fD"),
-                                        _ptr(JD, torch.float32, (n, NO, NZ), "JD"),
-                                        _ptr(HD, torch.float32, (n, NO, NZ, NZ), "HD")), "rtn_mlp_hess")
+                                        _ptr(fD, torch.float32, (n, self.n_out), "fD"),
+                                        _ptr(JD, torch.float32, (n, self.n_out, NZ), "JD"),
+                                        _ptr(HD, torch.float32, (n, self.n_out, NZ, NZ), "HD")), "rtn_mlp_hess")
         return fD, JD, HD
 
     def linearize(self, x, u, out=None):
         import torch
         n = self.n_nodes
         if out is None:
-            out = (self._empty(n, NO), self._empty(n, NO, NZ), self._empty(n, NX, NX),
+            out = (self._empty(n, self.n_out), self._empty(n, self.n_out, NZ), self._empty(n, NX, NX),
                    self._empty(n, NX, NU), self._empty(n, NX))
         fD, JD, A, Bm, c = out
         self._check(load().rtn_linearize(
             self._h, _ptr(x, torch.float32, (self.n_states, NX), "x"),
-            _ptr(u, torch.float32, (n, NU), "u"), _ptr(fD, torch.float32, (n, NO), "fD"),
-            _ptr(JD, torch.float32, (n, NO, NZ), "JD"), _ptr(A, torch.float32, (n, NX, NX), "A"),
+            _ptr(u, torch.float32, (n, NU), "u"), _ptr(fD, torch.float32, (n, self.n_out), "fD"),
+            _ptr(JD, torch.float32, (n, self.n_out, NZ), "JD"), _ptr(A, torch.float32, (n, NX, NX), "A"),
             _ptr(Bm, torch.float32, (n, NX, NU), "B"), _ptr(c, torch.float32, (n, NX), "c")),
             "rtn_linearize")
         return fD, JD, A, Bm, c

@@ -264,9 +264,13 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
   }
   if (mlp) {
     if (mlp->n_layers < 2 || !mlp->widths || !mlp->W || !mlp->b || mlp->widths[0] != NZ ||
-        mlp->widths[mlp->n_layers] != NO) {
-      g_create_err = "network must map 17 inputs to 3 outputs with >= 1 hidden layer";
+        (mlp->widths[mlp->n_layers] != NO && mlp->widths[mlp->n_layers] != NO_FULL)) {
+      g_create_err = "network must map 17 inputs to 3 outputs (or 6: full residual) with >= 1 hidden layer";
       return RTN_E_INVAL;
+    }
+    if (mlp->widths[mlp->n_layers] == NO_FULL && o.precision != RTN_FP32) {
+      g_create_err = "the 6-output full residual runs on the FP32 path (the tensor-core kernels take 3 outputs)";
+      return RTN_E_UNSUPPORTED;
     }
     for (int l = 1; l < mlp->n_layers; ++l)
       if (mlp->widths[l] < 1 || mlp->widths[l] > 4096) { g_create_err = "bad hidden width"; return RTN_E_INVAL; }
@@ -302,6 +306,7 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     // network
     if (mlp) {
       ctx->has_mlp = true;
+      ctx->n_out = mlp->widths[mlp->n_layers];
       Net& net = ctx->net;
       net.n_layers = mlp->n_layers;
       net.widths.assign(mlp->widths, mlp->widths + mlp->n_layers + 1);
@@ -326,7 +331,7 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
         CK(dalloc(&ctx->act1, na));
         if (o.second_order) {
           CK(mlp_hess_prepare());
-          CK(dalloc(&ctx->HD, (size_t)us * NO * NZ * NZ));
+          CK(dalloc(&ctx->HD, (size_t)us * ctx->n_out * NZ * NZ));
           CK(dalloc(&ctx->h2_x, mlp_hess_act_floats(ctx)));
           CK(dalloc(&ctx->h2_z, mlp_hess_act_floats(ctx)));
         }
@@ -347,8 +352,8 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     size_t gsz = ctx->opt.riccati_f64 ? sizeof(double) : sizeof(float);
     CK(dalloc(&ctx->x, (size_t)xs * NX));
     CK(dalloc(&ctx->u, (size_t)us * NU));
-    CK(dalloc(&ctx->fD, (size_t)us * NO));
-    CK(dalloc(&ctx->JD, (size_t)us * NO * NZ));
+    CK(dalloc(&ctx->fD, (size_t)us * ctx->n_out));
+    CK(dalloc(&ctx->JD, (size_t)us * ctx->n_out * NZ));
     CK(dalloc(&ctx->A, (size_t)us * NX * NX));
     CK(dalloc(&ctx->Bm, (size_t)us * NX * NU));
     CK(dalloc(&ctx->c, (size_t)us * NX));

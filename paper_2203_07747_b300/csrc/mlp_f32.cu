@@ -113,8 +113,9 @@ __global__ void __launch_bounds__(NTH) mlp_hidden_kernel(const float* __restrict
   }
 }
 
-// output layer (3 rows, linear): thread (node n, column j) computes the three
-// outputs of its column
+// output layer (NOUT rows, linear: 3, or 6 for the full residual):
+// thread (node n, column j) computes the outputs of its column
+template <int NOUT>
 __global__ void mlp_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL, int K,
                                const float* __restrict__ X, int n_nodes, float* __restrict__ fD,
                                float* __restrict__ JD) {
@@ -123,20 +124,21 @@ __global__ void mlp_out_kernel(const float* __restrict__ WL, const float* __rest
   int n = (int)(tid / NC), j = (int)(tid % NC);
   const size_t ldx = (size_t)NC * n_nodes;
   const float* xc = X + (size_t)n * NC + j;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  float s[NOUT];
+#pragma unroll
+  for (int r = 0; r < NOUT; ++r) s[r] = 0.f;
   for (int k = 0; k < K; ++k) {
     float v = xc[(size_t)k * ldx];
-    s0 = fmaf(WL[k], v, s0);
-    s1 = fmaf(WL[K + k], v, s1);
-    s2 = fmaf(WL[2 * K + k], v, s2);
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r) s[r] = fmaf(WL[r * K + k], v, s[r]);
   }
   if (j == 0) {
-    fD[(size_t)n * NO + 0] = s0 + bL[0];
-    fD[(size_t)n * NO + 1] = s1 + bL[1];
-    fD[(size_t)n * NO + 2] = s2 + bL[2];
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r) fD[(size_t)n * NOUT + r] = s[r] + bL[r];
   } else {
-    float* o = JD + (size_t)n * NO * NZ + (j - 1);
-    o[0] = s0; o[NZ] = s1; o[2 * NZ] = s2;
+    float* o = JD + (size_t)n * NOUT * NZ + (j - 1);
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r) o[r * NZ] = s[r];
   }
 }
 
@@ -165,8 +167,9 @@ cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float*
   }
   {
     long long tot = (long long)nn * NC;
-    mlp_out_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-        W + net.w_off[L - 1], b + net.b_off[L - 1], net.widths[L - 1], cur, nn, fD, JD);
+    auto kern = net.widths[L] == NO_FULL ? mlp_out_kernel<NO_FULL> : mlp_out_kernel<NO>;
+    kern<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(W + net.w_off[L - 1], b + net.b_off[L - 1],
+                                                       net.widths[L - 1], cur, nn, fD, JD);
   }
   return cudaGetLastError();
 }
@@ -187,7 +190,7 @@ cudaError_t mlp_f32_hidden_launch(const float* W, const float* bias, int M, int 
 cudaError_t mlp_f32_out_launch(const float* WL, const float* bL, int K, const float* X,
                                int n_nodes, float* fD, float* JD, cudaStream_t s) {
   long long tot = (long long)n_nodes * NC;
-  mlp_out_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(WL, bL, K, X, n_nodes, fD, JD);
+  mlp_out_kernel<NO><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(WL, bL, K, X, n_nodes, fD, JD);
   return cudaGetLastError();
 }
 

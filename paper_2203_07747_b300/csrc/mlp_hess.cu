@@ -128,8 +128,10 @@ __global__ void h2_act_kernel(const float* __restrict__ Z, const float* __restri
   }
 }
 
-// output layer (linear, 3 rows): one thread per (node n, column c); writes
-// f_D [n][3], J_D [n][3][17] and H_D [n][3][17][17] (both triangles)
+// output layer (linear, NOUT = 3 or 6 rows): one thread per (node n, column
+// c); writes f_D [n][NOUT], J_D [n][NOUT][17] and H_D [n][NOUT][17][17]
+// (both triangles)
+template <int NOUT>
 __global__ void h2_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL, int h, int n_nodes,
                               const float* __restrict__ X, float* __restrict__ fD, float* __restrict__ JD,
                               float* __restrict__ HD) {
@@ -137,21 +139,23 @@ __global__ void h2_out_kernel(const float* __restrict__ WL, const float* __restr
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cols;
        e += (long long)gridDim.x * blockDim.x) {
     const int n = (int)(e / C2), c = (int)(e % C2);
-    float acc[NO] = {0.0f, 0.0f, 0.0f};
+    float acc[NOUT];
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r) acc[r] = 0.0f;
     for (int k = 0; k < h; ++k) {
       const float xv = __ldg(X + (size_t)k * cols + e);
 #pragma unroll
-      for (int r = 0; r < NO; ++r) acc[r] = fmaf(__ldg(WL + (size_t)r * h + k), xv, acc[r]);
+      for (int r = 0; r < NOUT; ++r) acc[r] = fmaf(__ldg(WL + (size_t)r * h + k), xv, acc[r]);
     }
 #pragma unroll
-    for (int r = 0; r < NO; ++r) {
+    for (int r = 0; r < NOUT; ++r) {
       if (c == 0) {
-        fD[(size_t)n * NO + r] = acc[r] + bL[r];
+        fD[(size_t)n * NOUT + r] = acc[r] + bL[r];
       } else if (c <= NZ) {
-        JD[((size_t)n * NO + r) * NZ + (c - 1)] = acc[r];
+        JD[((size_t)n * NOUT + r) * NZ + (c - 1)] = acc[r];
       } else {
         const int p = c - 1 - NZ, j = k_pj[p], m = k_pm[p];
-        float* Hr = HD + ((size_t)n * NO + r) * NZ * NZ;
+        float* Hr = HD + ((size_t)n * NOUT + r) * NZ * NZ;
         Hr[j * NZ + m] = acc[r];
         Hr[m * NZ + j] = acc[r];
       }
@@ -200,8 +204,9 @@ cudaError_t mlp_hess_forward(rtn_ctx* ctx, const float* x, const float* u, float
     h2_act_kernel<<<grid_for((long long)ho * cols), 256, 0, s>>>(ctx->h2_z, net.b32 + net.b_off[l], ho, n,
                                                                   ctx->h2_x);
   }
-  h2_out_kernel<<<grid_for(cols), 256, 0, s>>>(net.W32 + net.w_off[L - 1], net.b32 + net.b_off[L - 1],
-                                                net.widths[L - 1], n, ctx->h2_x, fD, JD, HD);
+  auto out = net.widths[L] == NO_FULL ? h2_out_kernel<NO_FULL> : h2_out_kernel<NO>;
+  out<<<grid_for(cols), 256, 0, s>>>(net.W32 + net.w_off[L - 1], net.b32 + net.b_off[L - 1], net.widths[L - 1], n,
+                                     ctx->h2_x, fD, JD, HD);
   return cudaGetLastError();
 }
 

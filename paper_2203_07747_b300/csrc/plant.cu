@@ -5,7 +5,9 @@
 // quaternion.  f_F is the nominal model of Sec. V (Eq. 6); f_res is one of
 //   - none,
 //   - body drag  -R diag(0.3, 0.3, 0.1) R' v - 0.01 |v| v  (world frame),
-//   - the full residual network evaluated exactly (no local model).
+//   - the residual network evaluated exactly (no local model): 3 outputs
+//     added to dv/dt, or 6 (the full residual of Eq. 7, rows 3-5 added to
+//     dw/dt; in the state order [p, q, v, w] row r lands on component 7 + r).
 // One thread per instance; the network variant reads an FP64 weight copy.
 #include "rtn_internal.cuh"
 
@@ -80,7 +82,7 @@ __device__ void dyn_true(const rtn_quad& P, int kind, const PlantNet& net, const
       for (int i = 0; i < fo; ++i) a0[i] = a1[i];
       p += fo * fi + fo;
     }
-    for (int i = 0; i < 3; ++i) xd[7 + i] += a0[i];
+    for (int i = 0; i < net.widths[net.n_layers]; ++i) xd[7 + i] += a0[i];
   }
 }
 

@@ -4,7 +4,8 @@
 // A_k = dphi/dx and B_k = dphi/du (Sec. III-A), where the dynamics are the
 // nominal quadrotor model of Eq. 6 plus the local model of the residual
 // (Eq. 4), f_D*(x, u) = fbar + J_D dz (+ 1/2 dz' H_r dz for the second-order
-// model), dz = [x - x_k; u - u_k], added to dv/dt.  u is held over the
+// model), dz = [x - x_k; u - u_k]; NOUT = 3 outputs are added to dv/dt, 6
+// (the full residual of Eq. 7) to dv/dt and dw/dt -- row r to component 7 + r.  u is held over the
 // interval, so dz has no input part at the stage points.
 //
 // One thread per (node, column j of [A | B]): the thread integrates the node
@@ -86,6 +87,7 @@ __device__ __forceinline__ void jvp_nominal(const QuadParams& P, const float* x,
   o[12] = (dtz - (P.Jy - P.Jx) * (dwx * wy + wx * dwy)) / P.Jz;
 }
 
+template <int NOUT>
 __global__ void __launch_bounds__(256) rk4_sens_kernel(
     QuadParams P, const float* __restrict__ x, const float* __restrict__ u,
     const float* __restrict__ fD, const float* __restrict__ JD, const float* __restrict__ HD,
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
   const int b = node_inst[n];
   const float h = dt_inst[b];
   const float* xk = x + (size_t)(n + b) * NX;
-  float x0[NX], uk[NU], fb[NO], J[NO][NZ];
+  float x0[NX], uk[NU], fb[NOUT], J[NOUT][NZ];
 #pragma unroll
   for (int i = 0; i < NX; ++i) x0[i] = xk[i];
 #pragma unroll
@@ -107,12 +109,12 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
   if (res) {
     bool fin = true;
 #pragma unroll
-    for (int r = 0; r < NO; ++r) {
-      fb[r] = fD[(size_t)n * NO + r];
+    for (int r = 0; r < NOUT; ++r) {
+      fb[r] = fD[(size_t)n * NOUT + r];
       fin &= isfinite(fb[r]);
 #pragma unroll
       for (int i = 0; i < NZ; ++i) {
-        J[r][i] = JD[(size_t)n * NO * NZ + r * NZ + i];
+        J[r][i] = JD[(size_t)n * NOUT * NZ + r * NZ + i];
         fin &= isfinite(J[r][i]);
       }
     }
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
     jvp_nominal(P, xs, uk, Ss, du, dk);
     if (res) {
 #pragma unroll
-      for (int r = 0; r < NO; ++r) {
+      for (int r = 0; r < NOUT; ++r) {
         float v = fb[r], dv = 0.0f;
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
         if (HD && s > 0) {
           // g = H_r dz (dz = xs - x0 on the state part): value + 1/2 dz'g,
           // directional derivative + g . [S; du]
-          const float* Hr = HD + ((size_t)n * NO + r) * NZ * NZ;
+          const float* Hr = HD + ((size_t)n * NOUT + r) * NZ * NZ;
           float q = 0.0f;
           for (int i = 0; i < NZ; ++i) {
             float g = 0.0f;
@@ -205,8 +207,9 @@ cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* 
                      const float* JD, const float* HD, float* A, float* Bm, float* c) {
   const int nn = ctx->lay.n_nodes;
   long long tot = (long long)nn * NZ;
-  rk4_sens_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(
-      ctx->quad, x, u, fD, JD, fD ? HD : nullptr, ctx->lay.node_inst, ctx->lay.dt, nn, A, Bm, c);
+  auto kern = ctx->n_out == NO_FULL ? rk4_sens_kernel<NO_FULL> : rk4_sens_kernel<NO>;
+  kern<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(ctx->quad, x, u, fD, JD, fD ? HD : nullptr,
+                                                                ctx->lay.node_inst, ctx->lay.dt, nn, A, Bm, c);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ constexpr int NX = 13;
 constexpr int NU = 4;
 constexpr int NZ = 17;   // network input [x; u]
 constexpr int NO = 3;    // network output: world-frame acceleration residual
+constexpr int NO_FULL = 6;  // the full residual of Eq. 7: + body angular acceleration
 constexpr int NC = 18;   // columns per node in forward mode: value + 17 tangents
 
 // Quadrotor constants in FP32 for the linearisation kernels (by value).
@@ -120,6 +121,7 @@ struct rtn_ctx {
   rtn::CostParams cost{};
   rtn_options opt{};
   bool has_mlp = false;
+  int n_out = rtn::NO;              // network outputs: 3, or 6 (full residual, rows 3-5 -> dw/dt)
   rtn::Net net;
   cudaStream_t stream = nullptr;
   // iterate (omega of Sec. II)

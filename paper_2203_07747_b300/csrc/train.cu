@@ -97,16 +97,17 @@ __global__ void bias_act_kernel(float* __restrict__ Z, const float* __restrict__
   Z[i] = linear ? v : tanhf(v);
 }
 
-// G = 2 (Yhat - Y) / (3 bs), loss partial sums (one atomicAdd per block)
+// G = 2 (Yhat - Y) / (no bs), loss partial sums (one atomicAdd per block);
+// no = the network's outputs (3, or 6 for the full residual)
 __global__ void loss_grad_kernel(const float* __restrict__ Yh, const float* __restrict__ Y, int start,
-                                 int bs, float* __restrict__ G, float* __restrict__ loss) {
+                                 int bs, int no, float* __restrict__ G, float* __restrict__ loss) {
   __shared__ float red[256];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float e2 = 0.0f;
-  if (i < NO * bs) {
+  if (i < no * bs) {
     int r = i / bs, s = i % bs;
-    float e = Yh[i] - Y[((size_t)start + s) * NO + r];
-    G[i] = 2.0f * e / (3.0f * bs);
+    float e = Yh[i] - Y[((size_t)start + s) * no + r];
+    G[i] = 2.0f * e / ((float)no * bs);
     e2 = e * e;
   }
   red[threadIdx.x] = e2;
@@ -115,7 +116,7 @@ __global__ void loss_grad_kernel(const float* __restrict__ Yh, const float* __re
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(loss, red[0] / (3.0f * bs));
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] / ((float)no * bs));
 }
 
 // db[r] = sum over the batch of G[r][:]  (one block per row)
@@ -196,7 +197,8 @@ cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float
     bias_act_kernel<<<blocks((size_t)fo * bs), 256, 0, s>>>(ts.act[l + 1], net.b32 + net.b_off[l], fo,
                                                             bs, l == L - 1);
   }
-  loss_grad_kernel<<<blocks((size_t)NO * bs), 256, 0, s>>>(ts.act[L], Y, start, bs, ts.g0, loss);
+  const int no = net.widths[L];
+  loss_grad_kernel<<<blocks((size_t)no * bs), 256, 0, s>>>(ts.act[L], Y, start, bs, no, ts.g0, loss);
   // backward
   float* G = ts.g0;
   float* Gn = ts.g1;
