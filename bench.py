@@ -497,6 +497,79 @@ def bench_runtime_analysis(steps=200):
     return out
 
 
+def hess_flops_per_node(widths):
+    """Second-order (forward-over-forward) algorithmic FLOPs per node: 171
+    columns per node (value, 17 tangents, 153 second derivatives) through
+    every hidden->hidden and the output layer; the input layer costs its value
+    dot products, the tangent scaling and the rank-one second-derivative
+    products d2 w_j w_m.  Elementwise activation work is not counted."""
+    f = 2 * 17 * widths[1] + 17 * widths[1] + 2 * 153 * widths[1]
+    for fi, fo in zip(widths[1:-1], widths[2:]):
+        f += 2 * 171 * fi * fo
+    return f
+
+
+def bench_second_order(config, B=1024, reps=3):
+    """f4: the second-order local model (network Hessian H_D, Eq. 4) and the
+    6-output full residual (Eq. 7) on the FP32 path, B instances of the
+    workload's horizon and network (the 171 second-order columns per node
+    need h x 171 x 4 B per node and layer buffer, so B is below the
+    headline's).  Node linearisations/s and RTI steps/s, against the
+    first-order model on the same workload."""
+    import torch
+    import paper_2203_07747_b300 as rtn
+    prob = W.make_problem(config, seed=0, B=B)
+    widths = prob["widths"]
+    nn = int(prob["N"].sum())
+    xref, uref = W.node_refs(prob)
+    xref_d = torch.as_tensor(xref, dtype=torch.float32, device="cuda")
+    uref_d = torch.as_tensor(uref, dtype=torch.float32, device="cuda")
+    X, U = W.random_nodes(nn + B, 1)
+    x_d = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    u_d = torch.as_tensor(U[:nn], dtype=torch.float32, device="cuda")
+    xo = np.concatenate([[0], np.cumsum(prob["N"] + 1)])[:-1]
+    x0_d = torch.as_tensor(X[xo], dtype=torch.float32, device="cuda")
+
+    def run(layers, second):
+        ctl = rtn.Controller(prob["N"], prob["dt"], prob["Q"], prob["R"], QN=prob["QN"], quad=prob["quad"],
+                             layers=layers, precision="fp32", second_order=second)
+        out = ctl.linearize(x_d, u_d)
+        r = {"ms_linearize": time_calls(lambda: ctl.linearize(x_d, u_d, out), reps, warm=1)}
+        if second:
+            r["ms_network"] = time_calls(lambda: ctl.mlp_hess(x_d, u_d), reps, warm=1)
+        else:
+            r["ms_network"] = time_calls(lambda: ctl.mlp_eval(x_d, u_d, out[0], out[1]), reps, warm=1)
+        u0 = torch.empty(B, 4, device="cuda")
+        st = torch.empty(B, dtype=torch.int32, device="cuda")
+
+        def step():
+            ctl.set_iterate(x_d, u_d)
+            ctl.rti_step(x0_d, xref_d, uref_d, u0, st)
+        r["ms_rti"] = time_calls(step, reps, warm=1)
+        r["failed_instances"] = int((st != 0).sum())
+        ctl.close()
+        return r
+
+    full = W.xavier_mlp(widths[:-1] + [6], 5)
+    out = {"workload": f"{config} network and horizon, {B} instances ({nn} nodes), FP32 path",
+           "peak_kind": "nominal FP32 FFMA: 148 SM x 128 lanes x 2 x 2.032 GHz", "runs": []}
+    peak = 148 * 128 * 2 * 2.032e9 / 1e12
+    for name, layers, second in (("first order, 3 outputs", prob["layers"], False),
+                                 ("second order, 3 outputs", prob["layers"], True),
+                                 ("first order, full residual (6 outputs)", full, False),
+                                 ("second order, full residual (6 outputs)", full, True)):
+        r = run(layers, second)
+        w = [wl.shape[1] for wl, _ in layers] + [layers[-1][0].shape[0]]
+        fl = (hess_flops_per_node(w) if second else fwd_flops_per_node(w)) * nn
+        out["runs"].append({"model": name, "widths": "-".join(map(str, w)),
+                            "node_linearizations_per_s": nn / (r["ms_linearize"] * 1e-3),
+                            "rti_steps_per_s": B / (r["ms_rti"] * 1e-3),
+                            "network_ms": r["ms_network"], "network_tflops": fl / (r["ms_network"] * 1e-3) / 1e12,
+                            "network_frac_of_fp32_peak": fl / (r["ms_network"] * 1e-3) / 1e12 / peak,
+                            "failed_instances": r["failed_instances"]})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -616,6 +689,7 @@ def main():
         line["ragged_batch"] = bench_ragged()
         line["learned_part"] = bench_learned()
         line["runtime_analysis"] = bench_runtime_analysis()
+        line["second_order_and_full_residual"] = bench_second_order(args.config)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob)
     if rank == 0:
