@@ -330,10 +330,13 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
         CK(dalloc(&ctx->act0, na));
         CK(dalloc(&ctx->act1, na));
         if (o.second_order) {
-          CK(mlp_hess_prepare());
           CK(dalloc(&ctx->HD, (size_t)us * ctx->n_out * NZ * NZ));
-          CK(dalloc(&ctx->h2_x, mlp_hess_act_floats(ctx)));
-          CK(dalloc(&ctx->h2_z, mlp_hess_act_floats(ctx)));
+          std::string e;
+          cudaError_t ce = mlp_hess_prepare(ctx, e);
+          if (ce != cudaSuccess || !e.empty()) {
+            ctx->err = e.empty() ? std::string("second-order prepare: ") + cudaGetErrorString(ce) : e;
+            return ce == cudaErrorMemoryAllocation ? RTN_E_NOMEM : (e.empty() ? RTN_E_CUDA : RTN_E_UNSUPPORTED);
+          }
         }
       } else {
         std::string e;
@@ -398,8 +401,7 @@ void rtn_destroy(rtn_ctx* ctx) {
   void* ptrs[] = {L.N, L.dt, L.dt64, L.xoff, L.uoff, L.node_inst, L.order, ctx->net.W32, ctx->net.b32,
                   ctx->net.P64, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c, ctx->K,
                   ctx->kff, ctx->act0, ctx->act1, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0,
-                  ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters, ctx->HD,
-                  ctx->h2_x, ctx->h2_z};
+                  ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters, ctx->HD};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->di) {
@@ -408,6 +410,7 @@ void rtn_destroy(rtn_ctx* ctx) {
       if (p) cudaFree(p);
     delete ctx->di;
   }
+  mlp_hess_release(ctx);
   mlp_tc_release(ctx);
   train_release(ctx);
   delete ctx;

@@ -1,152 +1,156 @@
 // mlp_hess.cu -- the second-order local model of Eq. 4: f_D, J_D and the
-// Hessian H_D of the residual network at every node (FP32 SIMT).
+// Hessian H_D of the residual network at every node.
 //
 // Forward-over-forward differentiation: every node carries 171 columns
 // through the network -- the value, the 17 tangents t_j = da/dz_j and the 153
-// second derivatives s_jm = d^2 a / dz_j dz_m (j <= m).  With the layout of
-// the FP32 path (X_l [h_l][171 n_nodes], node-major column blocks), a hidden
-// layer is a plain GEMM Z = W_l X_l (h2_gemm_kernel) followed by an
-// elementwise kernel (h2_act_kernel) that forms, per neuron and node,
+// second derivatives s_jm = d^2 a / dz_j dz_m (j <= m) -- padded to 176.  A
+// hidden neuron with pre-activation columns (z_0, z_j, z_jm) produces
 //   a = tanh(z_0 + b),  t_j = tanh'(.) z_j,
 //   s_jm = tanh'(.) z_jm + tanh''(.) z_j z_m,
-// with tanh' = 1 - a^2, tanh'' = -2 a (1 - a^2).  The input layer needs no
-// GEMM (its tangents are W_0's columns, its second derivatives zero before
-// the activation) and the 3-row output layer is a reduction per column.
+// with tanh' = 1 - a^2, tanh'' = -2 a (1 - a^2).
+//
+// Layout: activations are stored transposed, X' [node * 176 + column][hs], as
+// TF32 hi + lo pairs (v = hi + lo to about 2^-22), so that a hidden->hidden
+// layer Z = W X is one tensor-core GEMM per (128-neuron tile, node): M = 128
+// neurons, N = 176 columns of one node, K = the layer's input width, both
+// operands K-major, three kind::tf32 MMAs per K step (hi hi + hi lo + lo hi,
+// FP32 accumulation in TMEM).  A TMEM lane then holds every column of one
+// neuron and node, so the activation rule above is thread-local and runs in
+// the GEMM's epilogue, which writes the next layer's X' directly
+// (h2_tc_kernel).  The input layer (no GEMM: its tangents are W_0's columns
+// and its second derivatives the rank-one d2 w_j w_m) and the 3- or 6-row
+// output layer run on the SIMT cores (h2_in_kernel, h2_out_kernel).
 #include <algorithm>
+#include <cstring>
+#include <new>
+#include <utility>
 
-#include "rtn_internal.cuh"
+#include "tc_common.cuh"
 
 namespace rtn {
 namespace {
 
 constexpr int C2 = 1 + NZ + NZ * (NZ + 1) / 2;  // 171 columns per node
+constexpr int CP = 176;                         // padded: the MMA's N
+constexpr int H2_KB = 32;                       // K per stage: one 128 B swizzle row of FP32
+constexpr int H2_STAGES = 2;
+constexpr uint32_t H2_A_BYTES = 128u * H2_KB * 4u;  // weight tile, 16 KB
+constexpr uint32_t H2_B_BYTES = CP * H2_KB * 4u;    // node tile, 22 KB
+constexpr uint32_t H2_STAGE = 2u * H2_A_BYTES + 2u * H2_B_BYTES;
+constexpr int H2_THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr uint32_t H2_TMEM_COLS = 512;  // two accumulators of 176 columns, 256 apart
+constexpr size_t H2_SMEM = H2_STAGES * H2_STAGE + 1024 + 256;
+constexpr int H2_NBAR = 2 * H2_STAGES + 5;
 
-// column 18 + p of a node holds the pair (j, m), j <= m, in row-major upper
-// triangle order
+static_assert(H2_A_BYTES % 1024 == 0 && H2_B_BYTES % 1024 == 0, "swizzled tiles must stay 1 KB aligned");
+
+// pair (j, m), j <= m, of second-derivative column 18 + p (row-major upper
+// triangle)
+__host__ __device__ constexpr int pair_j(int p) {
+  int j = 0;
+  while (p >= NZ - j) { p -= NZ - j; ++j; }
+  return j;
+}
+__host__ __device__ constexpr int pair_m(int p) {
+  int j = 0;
+  while (p >= NZ - j) { p -= NZ - j; ++j; }
+  return j + p;
+}
+
 __constant__ unsigned char k_pj[NZ * (NZ + 1) / 2];
 __constant__ unsigned char k_pm[NZ * (NZ + 1) / 2];
 
-// input layer: one thread per (neuron i, node n, column c)
-__global__ void h2_in_kernel(const float* __restrict__ x, const float* __restrict__ u,
-                             const int* __restrict__ node_inst, int n_nodes, const float* __restrict__ W0,
-                             const float* __restrict__ b0, int h0, float* __restrict__ X1) {
-  const long long cols = (long long)C2 * n_nodes;
-  const long long total = (long long)h0 * cols;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols);
-    const long long rem = e % cols;
-    const int n = (int)(rem / C2), c = (int)(rem % C2);
+struct H2Maps {
+  CUtensorMap wh, wl, xh, xl;
+};
+
+// round to TF32 (10 explicit mantissa bits), nearest, ties away from zero
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split_store(float* __restrict__ hi, float* __restrict__ lo, size_t idx, float v) {
+  const float h = tf32_rna(v);
+  hi[idx] = h;
+  lo[idx] = tf32_rna(v - h);
+}
+
+// instruction descriptor, kind::tf32: D f32, A = B = tf32, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+// ---------------------------------------------------------------- input layer
+// thread (neuron i, node n): pre-activation s = b_i + w_i . z_n, then every
+// column of the node: a, d1 w_ij, d2 w_ij w_im, zero padding
+__global__ void __launch_bounds__(256) h2_in_kernel(const float* __restrict__ x, const float* __restrict__ u,
+                                                    const int* __restrict__ node_inst, int n_nodes,
+                                                    const float* __restrict__ W0, const float* __restrict__ b0,
+                                                    int h1, int hs, float* __restrict__ xh, float* __restrict__ xl) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const bool act = i < h1;
+  const float* w = W0 + (size_t)(act ? i : 0) * NZ;
+  for (int n = blockIdx.y * 8 + threadIdx.y; n < n_nodes; n += gridDim.y * 8) {
     const float* xr = x + (size_t)(n + node_inst[n]) * NX;
     const float* ur = u + (size_t)n * NU;
-    const float* w = W0 + (size_t)i * NZ;
-    float s = b0[i];
+    float s = b0[act ? i : 0];
 #pragma unroll
-    for (int j = 0; j < NX; ++j) s = fmaf(w[j], xr[j], s);
+    for (int j = 0; j < NX; ++j) s = fmaf(__ldg(w + j), xr[j], s);
 #pragma unroll
-    for (int j = 0; j < NU; ++j) s = fmaf(w[NX + j], ur[j], s);
+    for (int j = 0; j < NU; ++j) s = fmaf(__ldg(w + NX + j), ur[j], s);
     const float a = tanhf(s), d1 = 1.0f - a * a, d2 = -2.0f * a * d1;
-    float v;
-    if (c == 0) v = a;
-    else if (c <= NZ) v = d1 * w[c - 1];
-    else v = d2 * w[k_pj[c - 1 - NZ]] * w[k_pm[c - 1 - NZ]];
-    X1[(size_t)i * cols + rem] = v;
-  }
-}
-
-// C [M][N] = A [M][K] B [K][N], row-major FP32; 64 x 64 tiles, 16 K per step,
-// 256 threads computing 4 x 4 each
-__global__ void __launch_bounds__(256) h2_gemm_kernel(const float* __restrict__ A, const float* __restrict__ B,
-                                                      float* __restrict__ Cm, int M, int N, int K) {
-  __shared__ float As[16][64 + 4];
-  __shared__ float Bs[16][64 + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  float acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = threadIdx.x + 256 * r;
-      // A tile: 64 rows x 16 k (k fastest), stored transposed
-      const int am = e >> 4, ak = e & 15;
-      As[ak][am] = (m0 + am < M && k0 + ak < K) ? __ldg(A + (size_t)(m0 + am) * K + k0 + ak) : 0.0f;
-      // B tile: 16 k x 64 columns (columns fastest)
-      const int bk = e >> 6, bn = e & 63;
-      Bs[bk][bn] = (k0 + bk < K && n0 + bn < N) ? __ldg(B + (size_t)(k0 + bk) * N + n0 + bn) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int m = m0 + ty * 4 + a;
-    if (m >= M) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int n = n0 + tx * 4 + b;
-      if (n < N) Cm[(size_t)m * N + n] = acc[a][b];
+    if (!act) continue;
+    const size_t row0 = (size_t)n * CP;
+    for (int c = 0; c < CP; ++c) {
+      float v;
+      if (c == 0) v = a;
+      else if (c <= NZ) v = d1 * __ldg(w + c - 1);
+      else if (c < C2) v = d2 * __ldg(w + k_pj[c - 1 - NZ]) * __ldg(w + k_pm[c - 1 - NZ]);
+      else v = 0.0f;
+      split_store(xh, xl, (row0 + c) * hs + i, v);
     }
   }
 }
 
-// hidden-layer activation: one thread per (neuron i, node n, column c)
-__global__ void h2_act_kernel(const float* __restrict__ Z, const float* __restrict__ bias, int h,
-                              int n_nodes, float* __restrict__ X) {
-  const long long cols = (long long)C2 * n_nodes;
-  const long long total = (long long)h * cols;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols);
-    const long long rem = e % cols;
-    const int c = (int)(rem % C2);
-    const float* z = Z + (size_t)i * cols + (rem - c);  // the node's 171 columns
-    const float a = tanhf(z[0] + bias[i]), d1 = 1.0f - a * a, d2 = -2.0f * a * d1;
-    float v;
-    if (c == 0) v = a;
-    else if (c <= NZ) v = d1 * z[c];
-    else {
-      const int p = c - 1 - NZ;
-      v = fmaf(d2, z[1 + k_pj[p]] * z[1 + k_pm[p]], d1 * z[c]);
-    }
-    X[(size_t)i * cols + rem] = v;
-  }
-}
-
-// output layer (linear, NOUT = 3 or 6 rows): one thread per (node n, column
-// c); writes f_D [n][NOUT], J_D [n][NOUT][17] and H_D [n][NOUT][17][17]
-// (both triangles)
+// --------------------------------------------------------------- output layer
+// one warp per (node n, column c < 171): out_r = WL_r . (xh + xl)[row], the
+// lanes splitting K; writes f_D [n][NOUT], J_D [n][NOUT][17] and H_D
+// [n][NOUT][17][17] (both triangles)
 template <int NOUT>
-__global__ void h2_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL, int h, int n_nodes,
-                              const float* __restrict__ X, float* __restrict__ fD, float* __restrict__ JD,
-                              float* __restrict__ HD) {
-  const long long cols = (long long)C2 * n_nodes;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cols;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int n = (int)(e / C2), c = (int)(e % C2);
+__global__ void __launch_bounds__(256) h2_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL,
+                                                     int h, int n_nodes, int hs, const float* __restrict__ xh,
+                                                     const float* __restrict__ xl, float* __restrict__ fD,
+                                                     float* __restrict__ JD, float* __restrict__ HD) {
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)n_nodes * C2;
+  for (long long wq = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wq < total;
+       wq += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int n = (int)(wq / C2), c = (int)(wq % C2);
+    const size_t row = ((size_t)n * CP + c) * hs;
     float acc[NOUT];
 #pragma unroll
     for (int r = 0; r < NOUT; ++r) acc[r] = 0.0f;
-    for (int k = 0; k < h; ++k) {
-      const float xv = __ldg(X + (size_t)k * cols + e);
+    for (int k = lane; k < h; k += 32) {
+      const float xv = __ldg(xh + row + k) + __ldg(xl + row + k);
 #pragma unroll
       for (int r = 0; r < NOUT; ++r) acc[r] = fmaf(__ldg(WL + (size_t)r * h + k), xv, acc[r]);
     }
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane != 0) continue;
 #pragma unroll
     for (int r = 0; r < NOUT; ++r) {
       if (c == 0) {
@@ -163,50 +167,378 @@ __global__ void h2_out_kernel(const float* __restrict__ WL, const float* __restr
   }
 }
 
-int grid_for(long long work) {
-  return (int)std::min<long long>((work + 255) / 256, 148LL * 32);
+// ------------------------------------------------- hidden layers (tcgen05)
+
+// the activated value of column C from its pre-activation z (C is a
+// compile-time constant, so the pair (j, m) of a second-derivative column
+// indexes the tangent registers statically)
+template <int C>
+__device__ __forceinline__ float h2_val(float z, float a, float d1, float d2, const float (&t)[NZ]) {
+  if constexpr (C == 0) {
+    return a;
+  } else if constexpr (C <= NZ) {
+    return d1 * z;
+  } else if constexpr (C < C2) {
+    constexpr int J = pair_j(C - 1 - NZ), M = pair_m(C - 1 - NZ);
+    return fmaf(d2, t[J] * t[M], d1 * z);
+  } else {
+    return 0.0f;
+  }
+}
+
+struct EpiOut {
+  float* yh;
+  float* yl;
+  size_t row0;  // first row of the node in X'
+  int hs, i;
+  bool active;
+};
+
+template <int K, int... Q>
+__device__ __forceinline__ void h2_emit(const float (&v)[16], float a, float d1, float d2, const float (&t)[NZ],
+                                        const EpiOut& o, std::integer_sequence<int, Q...>) {
+  if (o.active)
+    (split_store(o.yh, o.yl, (o.row0 + 16 * K + Q) * o.hs + o.i, h2_val<16 * K + Q>(v[Q], a, d1, d2, t)), ...);
+}
+
+// chunks K .. 10 of 16 columns: load from TMEM, activate, store
+template <int K>
+__device__ __forceinline__ void h2_rest(uint32_t taddr, float a, float d1, float d2, const float (&t)[NZ],
+                                        const EpiOut& o) {
+  if constexpr (K < CP / 16) {
+    float v[16];
+    tmem_ld16(taddr + 16 * K, v);
+    tmem_wait_ld();
+    h2_emit<K>(v, a, d1, d2, t, o, std::make_integer_sequence<int, 16>{});
+    h2_rest<K + 1>(taddr, a, d1, d2, t, o);
+  }
+}
+
+// One hidden->hidden layer: tiles (node n, neuron tile mt) in node-major
+// order over persistent CTAs (the MT tiles of a node read its X' block while
+// it is in L2); K in stages of 32, two stages; two TMEM accumulators so that
+// the epilogue of one tile overlaps the MMAs of the next.
+__global__ void __launch_bounds__(H2_THREADS, 1)
+    h2_tc_kernel(const __grid_constant__ H2Maps maps, const float* __restrict__ bias, int ho, int kp, int n_nodes,
+                 int hs, float* __restrict__ yh, float* __restrict__ yl, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t sraw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
+  uint8_t* sm = smem_raw + pad;
+  const uint32_t st0 = sraw + pad;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + H2_STAGES * H2_STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + H2_NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto bar = [&](int k) { return smem_u32(bars + k); };
+  auto full_bar = [&](int s) { return bar(s); };
+  auto empty_bar = [&](int s) { return bar(H2_STAGES + s); };
+  auto acc_full = [&](int a) { return bar(2 * H2_STAGES + a); };
+  auto tmem_free = [&](int a) { return bar(2 * H2_STAGES + 2 + a); };
+  const uint32_t mma_done = bar(2 * H2_STAGES + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int MT = (ho + 127) / 128;
+  const long long n_tiles = (long long)n_nodes * MT;
+  const int nkb = kp / H2_KB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < H2_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(acc_full(a), 1);
+      mbar_init(tmem_free(a), 4);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(H2_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.wh)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.xh)) : "memory");
+    }
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    uint32_t issued = 0, last_ph = 0;  // per stage: a load was issued / its phase parity
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      const int n = (int)(t / MT), mt = (int)(t % MT);
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!(ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, err))) break;
+        if (elect_one()) {
+          const uint32_t sa = st0 + s * H2_STAGE;
+          mbar_expect_tx(full_bar(s), H2_STAGE);
+          tma_load_2d(sa, &maps.wh, kb * H2_KB, mt * 128, full_bar(s));
+          tma_load_2d(sa + H2_A_BYTES, &maps.wl, kb * H2_KB, mt * 128, full_bar(s));
+          tma_load_2d(sa + 2 * H2_A_BYTES, &maps.xh, kb * H2_KB, n * CP, full_bar(s));
+          tma_load_2d(sa + 2 * H2_A_BYTES + H2_B_BYTES, &maps.xl, kb * H2_KB, n * CP, full_bar(s));
+        }
+        __syncwarp();
+        issued |= 1u << s;
+        last_ph = (last_ph & ~(1u << s)) | (ph << s);
+        if (++s == H2_STAGES) { s = 0; ph ^= 1u; }
+      }
+    }
+    // every issued copy has landed before the CTA exits (bounded)
+    for (int q = 0; q < H2_STAGES; ++q)
+      if (issued & (1u << q)) {
+        const long long t0 = clock64();
+        while (!mbar_try(full_bar(q), (last_ph >> q) & 1u) && clock64() - t0 < WAIT_CYCLES) {
+        }
+      }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_tf32(128, CP);
+    int s = 0, acc = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      if (!(ok = mbar_wait_warp(tmem_free(acc), aph ^ 1u, abort_flag, err))) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * 256u;
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, err))) break;
+        tc_fence_after();
+        const uint32_t sa = st0 + s * H2_STAGE;
+#pragma unroll
+        for (int ks = 0; ks < H2_KB / 8; ++ks) {
+          const uint64_t ah = kmajor_desc(sa + ks * 32u, 1024, 2);
+          const uint64_t al = kmajor_desc(sa + H2_A_BYTES + ks * 32u, 1024, 2);
+          const uint64_t bh = kmajor_desc(sa + 2 * H2_A_BYTES + ks * 32u, 1024, 2);
+          const uint64_t bl = kmajor_desc(sa + 2 * H2_A_BYTES + H2_B_BYTES + ks * 32u, 1024, 2);
+          mma_tf32_elect(d, ah, bh, idesc, (kb | ks) != 0);
+          mma_tf32_elect(d, ah, bl, idesc, 1u);
+          mma_tf32_elect(d, al, bh, idesc, 1u);
+        }
+        mma_commit_elect(empty_bar(s));
+        if (++s == H2_STAGES) { s = 0; ph ^= 1u; }
+      }
+      if (!ok) break;
+      mma_commit_elect(acc_full(acc));
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
+    }
+    // the MMAs issued so far have completed before TMEM is released (bounded)
+    mma_commit_elect(mma_done);
+    const long long t0 = clock64();
+    while (!mbar_try(mma_done, 0) && clock64() - t0 < WAIT_CYCLES) {
+    }
+  } else {
+    // ---------------- epilogue: TMEM lane quarter warp % 4
+    const int q = warp & 3;
+    int acc = 0;
+    uint32_t aph = 0;
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const int n = (int)(t / MT), mt = (int)(t % MT);
+      if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, err)) break;
+      tc_fence_after();
+      EpiOut o;
+      o.yh = yh;
+      o.yl = yl;
+      o.row0 = (size_t)n * CP;
+      o.hs = hs;
+      o.i = mt * 128 + q * 32 + lane;
+      o.active = o.i < ho;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
+      float v0[16], v1[16];
+      tmem_ld16(taddr, v0);
+      tmem_ld16(taddr + 16, v1);
+      tmem_wait_ld();
+      const float a = tanhf(v0[0] + (o.active ? __ldg(bias + o.i) : 0.0f));
+      const float d1 = 1.0f - a * a, d2 = -2.0f * a * d1;
+      float tz[NZ];
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) tz[j] = j < 15 ? v0[1 + j] : v1[j - 15];
+      h2_emit<0>(v0, a, d1, d2, tz, o, std::make_integer_sequence<int, 16>{});
+      h2_emit<1>(v1, a, d1, d2, tz, o, std::make_integer_sequence<int, 16>{});
+      h2_rest<2>(taddr, a, d1, d2, tz, o);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_free(acc));
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H2_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// FP32 -> TF32 with round-to-nearest-even on the 13 dropped mantissa bits
+float tf32_round(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x0fffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+  }
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
 }
 
 }  // namespace
 
-// the (j, m) pair table of the second-order columns (at context creation:
-// the forward pass itself stays capturable in a CUDA graph)
-cudaError_t mlp_hess_prepare() {
+cudaError_t mlp_hess_prepare(rtn_ctx* ctx, std::string& err) {
   unsigned char pj[NZ * (NZ + 1) / 2], pm[NZ * (NZ + 1) / 2];
-  int p = 0;
-  for (int j = 0; j < NZ; ++j)
-    for (int m = j; m < NZ; ++m) {
-      pj[p] = (unsigned char)j;
-      pm[p] = (unsigned char)m;
-      ++p;
-    }
+  for (int p = 0; p < NZ * (NZ + 1) / 2; ++p) {
+    pj[p] = (unsigned char)pair_j(p);
+    pm[p] = (unsigned char)pair_m(p);
+  }
   cudaError_t e = cudaMemcpyToSymbol(k_pj, pj, sizeof(pj));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(k_pm, pm, sizeof(pm));
-  return e;
+  if (e != cudaSuccess) return e;
+
+  Net& net = ctx->net;
+  const int L = net.n_layers, n = ctx->lay.n_nodes;
+  if ((long long)n * CP >= (1LL << 31)) {
+    err = "second order: more nodes than the 32-bit tensor coordinates address";
+    return cudaSuccess;
+  }
+  HessState* h = new (std::nothrow) HessState();
+  if (!h) return cudaErrorMemoryAllocation;
+  ctx->h2 = h;
+  int hmax = 0;
+  for (int l = 1; l < L; ++l) hmax = std::max(hmax, net.widths[l]);
+  h->hs = (hmax + 31) / 32 * 32;
+  const size_t xfl = (size_t)n * CP * h->hs;
+  for (int b = 0; b < 2; ++b)
+    for (int p = 0; p < 2; ++p) {
+      if ((e = cudaMalloc(&h->x[b][p], xfl * sizeof(float))) != cudaSuccess) return e;
+      // K entries a narrower layer never writes stay finite (zero): the
+      // zero weight padding then removes them from the next GEMM
+      if ((e = cudaMemset(h->x[b][p], 0, xfl * sizeof(float))) != cudaSuccess) return e;
+    }
+  TcNet& tc = net.tc;
+  if (!tc.err) {
+    if ((e = cudaMalloc(&tc.err, sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMemset(tc.err, 0, sizeof(int))) != cudaSuccess) return e;
+  }
+  if (L < 3) return cudaSuccess;  // one hidden layer: no GEMM
+
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+  if (e != cudaSuccess || !fn || qr != cudaDriverEntryPointSuccess) {
+    err = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  e = cudaFuncSetAttribute(h2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H2_SMEM);
+  if (e != cudaSuccess) return e;
+  for (int l = 1; l + 1 < L; ++l) {
+    const int hi = net.widths[l], ho = net.widths[l + 1];
+    const int kp = (hi + 31) / 32 * 32, rows = (ho + 127) / 128 * 128;
+    // split weights, zero padded to [rows][kp]
+    std::vector<float> W((size_t)ho * hi);
+    if ((e = cudaMemcpy(W.data(), net.W32 + net.w_off[l], W.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return e;
+    std::vector<float> wh((size_t)rows * kp, 0.0f), wl((size_t)rows * kp, 0.0f);
+    for (int r = 0; r < ho; ++r)
+      for (int k = 0; k < hi; ++k) {
+        const float v = W[(size_t)r * hi + k], vh = tf32_round(v);
+        wh[(size_t)r * kp + k] = vh;
+        wl[(size_t)r * kp + k] = tf32_round(v - vh);
+      }
+    float *dh = nullptr, *dl = nullptr;
+    if ((e = cudaMalloc(&dh, wh.size() * 4)) != cudaSuccess) return e;
+    h->wh.push_back(dh);
+    if ((e = cudaMalloc(&dl, wl.size() * 4)) != cudaSuccess) return e;
+    h->wl.push_back(dl);
+    if ((e = cudaMemcpy(dh, wh.data(), wh.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(dl, wl.data(), wl.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    h->kp.push_back(kp);
+    // tensor maps: W hi/lo [rows][kp], box 32 x 128; X' hi/lo of the buffer
+    // this layer reads, [n * 176][hs], box 32 x 176; 128 B swizzle.  No box
+    // reaches past its tensor (rows padded to 128, kp <= hs, 176 rows a node).
+    std::vector<unsigned char> m(sizeof(H2Maps));
+    H2Maps* mp = reinterpret_cast<H2Maps*>(m.data());
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint64_t wdims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t wstr[1] = {(cuuint64_t)kp * 4};
+    const cuuint32_t wbox[2] = {(cuuint32_t)H2_KB, 128};
+    const cuuint64_t xdims[2] = {(cuuint64_t)h->hs, (cuuint64_t)n * CP};
+    const cuuint64_t xstr[1] = {(cuuint64_t)h->hs * 4};
+    const cuuint32_t xbox[2] = {(cuuint32_t)H2_KB, (cuuint32_t)CP};
+    const int src = (l - 1) & 1;
+    struct Enc {
+      CUtensorMap* map;
+      void* ptr;
+      const cuuint64_t* dims;
+      const cuuint64_t* str;
+      const cuuint32_t* box;
+    } enc[4] = {{&mp->wh, dh, wdims, wstr, wbox},
+                {&mp->wl, dl, wdims, wstr, wbox},
+                {&mp->xh, h->x[src][0], xdims, xstr, xbox},
+                {&mp->xl, h->x[src][1], xdims, xstr, xbox}};
+    for (auto& q : enc) {
+      CUresult r = encode(q.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, q.ptr, q.dims, q.str, q.box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return cudaSuccess;
+      }
+    }
+    h->maps.push_back(std::move(m));
+  }
+  return cudaSuccess;
 }
 
-size_t mlp_hess_act_floats(const rtn_ctx* ctx) {
-  return (size_t)ctx->net.h_max * C2 * ctx->lay.n_nodes;
+void mlp_hess_release(rtn_ctx* ctx) {
+  HessState* h = ctx->h2;
+  if (!h) return;
+  for (int b = 0; b < 2; ++b)
+    for (int p = 0; p < 2; ++p)
+      if (h->x[b][p]) cudaFree(h->x[b][p]);
+  for (float* p : h->wh) cudaFree(p);
+  for (float* p : h->wl) cudaFree(p);
+  delete h;
+  ctx->h2 = nullptr;
 }
 
 cudaError_t mlp_hess_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD) {
   Net& net = ctx->net;
+  HessState* h = ctx->h2;
   const int n = ctx->lay.n_nodes, L = net.n_layers;
   cudaStream_t s = ctx->stream;
-  const long long cols = (long long)C2 * n;
   const int h1 = net.widths[1];
-  h2_in_kernel<<<grid_for((long long)h1 * cols), 256, 0, s>>>(x, u, ctx->lay.node_inst, n, net.W32 + net.w_off[0],
-                                                             net.b32 + net.b_off[0], h1, ctx->h2_x);
-  for (int l = 1; l + 1 < L; ++l) {
-    const int hi = net.widths[l], ho = net.widths[l + 1];
-    dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((ho + 63) / 64));
-    h2_gemm_kernel<<<grid, 256, 0, s>>>(net.W32 + net.w_off[l], ctx->h2_x, ctx->h2_z, ho, (int)cols, hi);
-    h2_act_kernel<<<grid_for((long long)ho * cols), 256, 0, s>>>(ctx->h2_z, net.b32 + net.b_off[l], ho, n,
-                                                                  ctx->h2_x);
+  {
+    dim3 grid((unsigned)((h1 + 31) / 32), (unsigned)std::min((n + 7) / 8, 65535));
+    h2_in_kernel<<<grid, dim3(32, 8), 0, s>>>(x, u, ctx->lay.node_inst, n, net.W32 + net.w_off[0],
+                                             net.b32 + net.b_off[0], h1, h->hs, h->x[0][0], h->x[0][1]);
   }
+  for (int l = 1; l + 1 < L; ++l) {
+    const int ho = net.widths[l + 1];
+    const int dst = l & 1;
+    const long long tiles = (long long)n * ((ho + 127) / 128);
+    const int grid = (int)std::min<long long>(tiles, 148);
+    const H2Maps* maps = reinterpret_cast<const H2Maps*>(h->maps[l - 1].data());
+    h2_tc_kernel<<<grid, H2_THREADS, H2_SMEM, s>>>(*maps, net.b32 + net.b_off[l], ho, h->kp[l - 1], n, h->hs,
+                                                  h->x[dst][0], h->x[dst][1], net.tc.err);
+  }
+  const int last = (L - 2) & 1;  // buffer the output layer reads
+  const long long warps = (long long)n * C2;
+  const int grid = (int)std::min<long long>((warps + 7) / 8, 148LL * 64);
   auto out = net.widths[L] == NO_FULL ? h2_out_kernel<NO_FULL> : h2_out_kernel<NO>;
-  out<<<grid_for(cols), 256, 0, s>>>(net.W32 + net.w_off[L - 1], net.b32 + net.b_off[L - 1], net.widths[L - 1], n,
-                                     ctx->h2_x, fD, JD, HD);
+  out<<<grid, 256, 0, s>>>(net.W32 + net.w_off[L - 1], net.b32 + net.b_off[L - 1], net.widths[L - 1], n, h->hs,
+                           h->x[last][0], h->x[last][1], fD, JD, HD);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,22 @@ struct DiState {
 };
 }  // namespace rtn
 
+namespace rtn {
+// Forward-over-forward second-order network evaluation (mlp_hess.cu): per
+// node 176 columns (value, 17 tangents, 153 second derivatives, 5 zero pad)
+// stored transposed, X' [node * 176 + column][hs], as TF32 hi + lo pairs in
+// two ping-pong buffers; the hidden->hidden weights split the same way,
+// rows padded to kp[l] (a multiple of 32) with zeros.
+struct HessState {
+  int hs = 0;                                 // row stride of X' (floats)
+  float* x[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [buffer][hi, lo]
+  std::vector<float*> wh, wl;                 // per hidden->hidden layer
+  std::vector<int> kp;
+  // per hidden->hidden layer: tensor maps of W hi, W lo, X hi, X lo
+  std::vector<std::vector<unsigned char>> maps;
+};
+}  // namespace rtn
+
 struct rtn_ctx {
   int B = 0;
   int nx = rtn::NX, nu = rtn::NU;   // 13, 4 (quadrotor) or 2, 1 (double integrator)
@@ -132,10 +148,9 @@ struct rtn_ctx {
   void *K = nullptr, *kff = nullptr;      // Riccati gains (float or double) [n][4][13], [n][4]
   float *act0 = nullptr, *act1 = nullptr; // FP32 network activations [h_max][18 n_nodes]
   // second-order local model (rtn_options.second_order): network Hessians
-  // [n_nodes][3][17][17] and the activations of forward-over-forward
-  // differentiation [h_max][171 n_nodes] (mlp_hess.cu)
+  // [n_nodes][n_out][17][17] and the forward-over-forward state (mlp_hess.cu)
   float* HD = nullptr;
-  float *h2_x = nullptr, *h2_z = nullptr;
+  rtn::HessState* h2 = nullptr;
   int* status = nullptr;                  // [B]
   int* dev_t = nullptr;                   // closed-loop step counter
   float* x0f = nullptr;                   // [B][13] float copy of the plant state
@@ -157,8 +172,10 @@ namespace rtn {
 
 // second-order local model (mlp_hess.cu): f_D, J_D, H_D of every node
 cudaError_t mlp_hess_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD);
-size_t mlp_hess_act_floats(const rtn_ctx* ctx);
-cudaError_t mlp_hess_prepare();
+// buffers, split weights and tensor maps (at rtn_create); err receives a
+// description when the tensor maps cannot be made
+cudaError_t mlp_hess_prepare(rtn_ctx* ctx, std::string& err);
+void mlp_hess_release(rtn_ctx* ctx);
 
 // f3, double integrator (di.cu): network value + Jacobian of every node,
 // linearisation (A [n][2][2], B [n][2], c [n][2]) and the RTI step
