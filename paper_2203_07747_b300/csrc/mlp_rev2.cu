@@ -15,8 +15,11 @@
 //   forward:  C_F = 64 value columns per CTA (42 used), N = 128;
 //   backward: C_B = 128 adjoint columns per CTA (3n + i, 126 used), N = 256.
 // The activation buffer X is N-major with 64 columns in the forward pass and
-// 128 in the backward pass (the two layouts share the buffer; the passes meet
-// only after the MMAs have read every block).  GEMMs of a tile, all on the
+// 128 in the backward pass.  The forward layout fills half of X, so forward
+// GEMMs alternate between the two halves: GEMM g (g <= nh) reads half g % 2
+// and its epilogue writes the other, whose last reader (GEMM g - 1) has
+// completed once GEMM g's accumulator has; the backward layout covers all of
+// X (the passes meet only after the MMAs have read every block).  GEMMs of a tile, all on the
 // stacked weights of the single-CTA reverse kernel:
 //   g < nh        W_{g+1}  forward hidden layer (a_{g+2} = tanh(W a + b))
 //   g = nh        W_L      output layer (rank 0's rows only): f_D
@@ -261,6 +264,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
           const int nks = L.two ? 2 * nkb : nkb;
           const uint32_t idesc = L.bwd ? id_b : id_f;
           const uint32_t lbo = (L.bwd ? R2_CB : R2_CF) * 16u;
+          const uint32_t xs_g = x_s + (L.bwd ? 0u : (uint32_t)(g & 1) * (xbytes / 2u));  // forward half
           long long w_x = 0, w_w = 0, w_t = 0;
           if (tr && lane == 0) rev2_trace(a, it, g, n_gemm, 0, gtime());
           for (int m = 0; m < L.mts && ok; ++m) {
@@ -301,7 +305,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t bo = (uint32_t)(kk * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
-                mma2_bf16(d, wdesc(as, ks), xdesc(x_s + bo, lbo), idesc, (kb | ks) != 0);
+                mma2_bf16(d, wdesc(as, ks), xdesc(xs_g + bo, lbo), idesc, (kb | ks) != 0);
               }
               commit2(empty_bar(s), 3);
               if (++s == STAGES) { s = 0; ph ^= 1u; }
@@ -415,7 +419,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
     };
     // after every warp wrote its rows of block j: publish the own half, push
     // the peer's half (`bytes` = one block of the current layout)
-    auto block_end = [&](int j, uint32_t bytes) -> bool {
+    auto block_end = [&](int j, uint32_t bytes, uint32_t base) -> bool {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(s_full);
@@ -427,8 +431,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
           const uint32_t bar = (rank == 0 ? lo1 : xr0) + 8u * j;
 #pragma unroll
           for (int c = 0; c < 4; ++c)  // four copies in flight, issued first
-            bulk_copy_to_peer(x_rem + (uint32_t)j * bytes + c * (bytes / 4), s_s + c * (bytes / 4), bytes / 4,
-                              bar);
+            bulk_copy_to_peer(x_rem + base + (uint32_t)j * bytes + c * (bytes / 4), s_s + c * (bytes / 4),
+                              bytes / 4, bar);
           if (rank == 0) {
             mbar_arrive(xready(j));                        // own hi half
             arrive_expect_tx_cluster_relaxed(bar, bytes);  // the copy's bytes
@@ -506,7 +510,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
         for (int c = 0; c < 3; ++c)
           *reinterpret_cast<uint4*>(S + xoff_n(R2_CF, i & 127, nb + 8 * c)) =
               make_uint4(peer[4 * c], peer[4 * c + 1], peer[4 * c + 2], peer[4 * c + 3]);
-        if (!block_end(j, 128u * R2_CF * 2u)) return false;
+        if (!block_end(j, 128u * R2_CF * 2u, 0u)) return false;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(z_free);
@@ -526,8 +530,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
         tc_fence_after();
         stamp(it_, g, m, 1);
         const int j = 2 * m + (int)rank;  // the block this CTA's rows produce
-        // the MMAs of GEMM g have read block j's old contents
-        if (!wwait(xfree(j), xfree_par(it_, g))) return false;
+        // written to the forward half GEMM g does not read (its last reader,
+        // GEMM g - 1, completed before GEMM g's accumulator)
+        const uint32_t xo = (uint32_t)((g + 1) & 1) * (xbytes / 2u);
         stamp(it_, g, m, 2);
         const int i = 128 * j + 32 * q + lane;
         const int nb = 24 * half, c0 = 16 * half;  // nodes nb..nb+23 lie in columns c0..c0+31
@@ -560,7 +565,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          *reinterpret_cast<uint4*>(X + xoff_n(R2_CF, i, nb + 8 * c)) =
+          *reinterpret_cast<uint4*>(X + xo + xoff_n(R2_CF, i, nb + 8 * c)) =
               make_uint4(own[4 * c], own[4 * c + 1], own[4 * c + 2], own[4 * c + 3]);
         stamp(it_, g, m, 4);
         if (!wait_staging()) return false;
@@ -570,7 +575,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
           *reinterpret_cast<uint4*>(S + xoff_n(R2_CF, i & 127, nb + 8 * c)) =
               make_uint4(peer[4 * c], peer[4 * c + 1], peer[4 * c + 2], peer[4 * c + 3]);
         stamp(it_, g, m, 6);
-        if (!block_end(j, 128u * R2_CF * 2u)) return false;
+        if (!block_end(j, 128u * R2_CF * 2u, xo)) return false;
         stamp(it_, g, m, 7);
       }
       mark_end(it_, g);
@@ -633,7 +638,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
       for (int c = 0; c < 8; ++c)
         *reinterpret_cast<uint4*>(S + xoff_n(R2_CB, i & 127, cb + 8 * c)) =
             make_uint4(peer[4 * c], peer[4 * c + 1], peer[4 * c + 2], peer[4 * c + 3]);
-      return block_end(j, 128u * R2_CB * 2u);
+      return block_end(j, 128u * R2_CB * 2u, 0u);
     };
     // d of the 22 nodes whose adjoint columns this half holds (node n0 + k);
     // column c of the half is component (c + half) % 3 of node n0 + (c + half) / 3
