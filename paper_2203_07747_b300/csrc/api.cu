@@ -70,8 +70,9 @@ __global__ void convert_state_kernel(const double* __restrict__ x, float* __rest
   if (i < n) y[i] = (float)x[i];
 }
 
+// f_D, J_D of every node (second-order contexts also refresh H_D)
 rtn_status run_mlp(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD) {
-  cudaError_t e = ctx->opt.precision == RTN_FP32 ? mlp_f32_forward(ctx, x, u, fD, JD)
+  cudaError_t e = ctx->opt.precision == RTN_FP32 ? mlp_tf32_forward(ctx, x, u, fD, JD, ctx->HD)
                                                  : mlp_tc_forward(ctx, x, u, fD, JD);
   if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("mlp: ") + cudaGetErrorString(e));
   return RTN_OK;
@@ -79,10 +80,7 @@ rtn_status run_mlp(rtn_ctx* ctx, const float* x, const float* u, float* fD, floa
 
 rtn_status linearize_impl(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD,
                           float* A, float* Bm, float* c) {
-  if (ctx->opt.second_order) {
-    cudaError_t e = mlp_hess_forward(ctx, x, u, fD, JD, ctx->HD);
-    if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("mlp_hess: ") + cudaGetErrorString(e));
-  } else if (ctx->has_mlp) {
+  if (ctx->has_mlp) {
     rtn_status st = run_mlp(ctx, x, u, fD, JD);
     if (st != RTN_OK) return st;
   }
@@ -326,17 +324,12 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
       CK(upload(&net.b32, bh.data(), bh.size()));
       CK(upload(&net.P64, P64.data(), P64.size()));
       if (o.precision == RTN_FP32) {
-        size_t na = (size_t)net.h_max * NC * us;
-        CK(dalloc(&ctx->act0, na));
-        CK(dalloc(&ctx->act1, na));
-        if (o.second_order) {
-          CK(dalloc(&ctx->HD, (size_t)us * ctx->n_out * NZ * NZ));
-          std::string e;
-          cudaError_t ce = mlp_hess_prepare(ctx, e);
-          if (ce != cudaSuccess || !e.empty()) {
-            ctx->err = e.empty() ? std::string("second-order prepare: ") + cudaGetErrorString(ce) : e;
-            return ce == cudaErrorMemoryAllocation ? RTN_E_NOMEM : (e.empty() ? RTN_E_CUDA : RTN_E_UNSUPPORTED);
-          }
+        if (o.second_order) CK(dalloc(&ctx->HD, (size_t)us * ctx->n_out * NZ * NZ));
+        std::string e;
+        cudaError_t ce = mlp_tf32_prepare(ctx, o.second_order ? 2 : 1, e);
+        if (ce != cudaSuccess || !e.empty()) {
+          ctx->err = e.empty() ? std::string("FP32 network prepare: ") + cudaGetErrorString(ce) : e;
+          return ce == cudaErrorMemoryAllocation ? RTN_E_NOMEM : (e.empty() ? RTN_E_CUDA : RTN_E_UNSUPPORTED);
         }
       } else {
         std::string e;
@@ -400,7 +393,7 @@ void rtn_destroy(rtn_ctx* ctx) {
   Layout& L = ctx->lay;
   void* ptrs[] = {L.N, L.dt, L.dt64, L.xoff, L.uoff, L.node_inst, L.order, ctx->net.W32, ctx->net.b32,
                   ctx->net.P64, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c, ctx->K,
-                  ctx->kff, ctx->act0, ctx->act1, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0,
+                  ctx->kff, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0,
                   ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters, ctx->HD};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -410,7 +403,7 @@ void rtn_destroy(rtn_ctx* ctx) {
       if (p) cudaFree(p);
     delete ctx->di;
   }
-  mlp_hess_release(ctx);
+  mlp_tf32_release(ctx);
   mlp_tc_release(ctx);
   train_release(ctx);
   delete ctx;
@@ -485,7 +478,7 @@ rtn_status rtn_mlp_hess(rtn_ctx* ctx, const float* x, const float* u, float* fD,
   if (!ctx) return RTN_E_INVAL;
   if (!x || !u || !fD || !JD || !HD) return fail(ctx, RTN_E_INVAL, "rtn_mlp_hess: NULL argument");
   if (!ctx->opt.second_order) return fail(ctx, RTN_E_UNSUPPORTED, "rtn_mlp_hess: context has no second-order model");
-  CK(mlp_hess_forward(ctx, x, u, fD, JD, HD));
+  CK(mlp_tf32_forward(ctx, x, u, fD, JD, HD));
   return RTN_OK;
 }
 

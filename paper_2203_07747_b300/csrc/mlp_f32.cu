@@ -1,4 +1,6 @@
-// mlp_f32.cu -- (a1) residual network value + input Jacobian, FP32 SIMT path.
+// mlp_f32.cu -- (a1) residual network value + input Jacobian, FP32 SIMT
+// kernels of the allocation-free entry point (noalloc.cu; controller contexts
+// evaluate the network on the tensor cores, mlp_tf32.cu).
 //
 // Forward-mode differentiation of f_D (Sec. III-A, Eq. 4): every node carries
 // 18 columns through the network, its value and the 17 tangent directions
@@ -12,30 +14,6 @@
 
 namespace rtn {
 namespace {
-
-// input layer: thread (neuron i, node n), n fastest so that consecutive
-// threads write consecutive 18-column blocks of row i
-__global__ void mlp_in_kernel(const float* __restrict__ x, const float* __restrict__ u,
-                              const int* __restrict__ node_inst, int n_nodes,
-                              const float* __restrict__ W0, const float* __restrict__ b0, int h0,
-                              float* __restrict__ X1) {
-  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)h0 * n_nodes) return;
-  int i = (int)(tid / n_nodes), n = (int)(tid % n_nodes);
-  const float* xr = x + (size_t)(n + node_inst[n]) * NX;
-  const float* ur = u + (size_t)n * NU;
-  const float* w = W0 + (size_t)i * NZ;
-  float s = b0[i];
-#pragma unroll
-  for (int j = 0; j < NX; ++j) s = fmaf(w[j], xr[j], s);
-#pragma unroll
-  for (int j = 0; j < NU; ++j) s = fmaf(w[NX + j], ur[j], s);
-  float a = tanhf(s), d = 1.0f - a * a;
-  float* o = X1 + (size_t)i * ((size_t)NC * n_nodes) + (size_t)NC * n;
-  o[0] = a;
-#pragma unroll
-  for (int j = 0; j < NZ; ++j) o[1 + j] = d * w[j];
-}
 
 // hidden layer GEMM with the fused tanh / tanh' epilogue.
 // Tile: 128 neurons x 8 nodes (144 columns), K in slices of 16.  Thread
@@ -144,42 +122,6 @@ __global__ void mlp_out_kernel(const float* __restrict__ WL, const float* __rest
 
 }  // namespace
 
-cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD) {
-  const Net& net = ctx->net;
-  const int nn = ctx->lay.n_nodes, L = net.n_layers;
-  cudaStream_t s = ctx->stream;
-  const float* W = net.W32;
-  const float* b = net.b32;
-  int h0 = net.widths[1];
-  {
-    long long tot = (long long)h0 * nn;
-    mlp_in_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, u, ctx->lay.node_inst, nn,
-                                                                W + net.w_off[0], b + net.b_off[0],
-                                                                h0, ctx->act0);
-  }
-  float* cur = ctx->act0;
-  float* nxt = ctx->act1;
-  for (int l = 1; l < L - 1; ++l) {
-    int K = net.widths[l], M = net.widths[l + 1];
-    dim3 grid((nn + BNN - 1) / BNN, (M + BM - 1) / BM);
-    mlp_hidden_kernel<<<grid, NTH, 0, s>>>(W + net.w_off[l], b + net.b_off[l], M, K, cur, nxt, nn);
-    float* t = cur; cur = nxt; nxt = t;
-  }
-  {
-    long long tot = (long long)nn * NC;
-    auto kern = net.widths[L] == NO_FULL ? mlp_out_kernel<NO_FULL> : mlp_out_kernel<NO>;
-    kern<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(W + net.w_off[L - 1], b + net.b_off[L - 1],
-                                                       net.widths[L - 1], cur, nn, fD, JD);
-  }
-  return cudaGetLastError();
-}
-
-}  // namespace rtn
-
-namespace rtn {
-
-// Thin launchers of the hidden-layer and output-layer kernels above for
-// callers that manage their own activation buffers.
 cudaError_t mlp_f32_hidden_launch(const float* W, const float* bias, int M, int K, const float* X,
                                   float* Y, int n_nodes, cudaStream_t s) {
   dim3 grid((n_nodes + BNN - 1) / BNN, (M + BM - 1) / BM);

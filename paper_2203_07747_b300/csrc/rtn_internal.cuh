@@ -110,12 +110,14 @@ struct DiState {
 }  // namespace rtn
 
 namespace rtn {
-// Forward-over-forward second-order network evaluation (mlp_hess.cu): per
-// node 176 columns (value, 17 tangents, 153 second derivatives, 5 zero pad)
-// stored transposed, X' [node * 176 + column][hs], as TF32 hi + lo pairs in
-// two ping-pong buffers; the hidden->hidden weights split the same way,
-// rows padded to kp[l] (a multiple of 32) with zeros.
-struct HessState {
+// FP32-accurate network evaluation on the tensor cores (mlp_tf32.cu):
+// forward mode with 18 columns per node (mode 1: value + tangents) or 176
+// (mode 2: + 153 second derivatives + 5 zero pad), stored transposed,
+// X' [node * columns + column][hs], as TF32 hi + lo pairs in two ping-pong
+// buffers; the hidden->hidden weights split the same way, rows padded to
+// kp[l] (a multiple of 32) with zeros.
+struct TfState {
+  int mode = 1;
   int hs = 0;                                 // row stride of X' (floats)
   float* x[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [buffer][hi, lo]
   std::vector<float*> wh, wl;                 // per hidden->hidden layer
@@ -146,11 +148,10 @@ struct rtn_ctx {
   // workspace
   float *fD = nullptr, *JD = nullptr, *A = nullptr, *Bm = nullptr, *c = nullptr;
   void *K = nullptr, *kff = nullptr;      // Riccati gains (float or double) [n][4][13], [n][4]
-  float *act0 = nullptr, *act1 = nullptr; // FP32 network activations [h_max][18 n_nodes]
   // second-order local model (rtn_options.second_order): network Hessians
-  // [n_nodes][n_out][17][17] and the forward-over-forward state (mlp_hess.cu)
+  // [n_nodes][n_out][17][17]; the FP32-accurate network state (mlp_tf32.cu)
   float* HD = nullptr;
-  rtn::HessState* h2 = nullptr;
+  rtn::TfState* tf = nullptr;             // RTN_FP32 networks (first or second order)
   int* status = nullptr;                  // [B]
   int* dev_t = nullptr;                   // closed-loop step counter
   float* x0f = nullptr;                   // [B][13] float copy of the plant state
@@ -170,12 +171,13 @@ namespace rtn {
 
 // ---- launchers (each returns cudaGetLastError()) --------------------------
 
-// second-order local model (mlp_hess.cu): f_D, J_D, H_D of every node
-cudaError_t mlp_hess_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD);
+// a1 / f4 for RTN_FP32 contexts (mlp_tf32.cu): f_D, J_D (and H_D in mode
+// 2, second order) of every node on the tensor cores with FP32 accuracy
+cudaError_t mlp_tf32_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD, float* HD);
 // buffers, split weights and tensor maps (at rtn_create); err receives a
 // description when the tensor maps cannot be made
-cudaError_t mlp_hess_prepare(rtn_ctx* ctx, std::string& err);
-void mlp_hess_release(rtn_ctx* ctx);
+cudaError_t mlp_tf32_prepare(rtn_ctx* ctx, int mode, std::string& err);
+void mlp_tf32_release(rtn_ctx* ctx);
 
 // f3, double integrator (di.cu): network value + Jacobian of every node,
 // linearisation (A [n][2][2], B [n][2], c [n][2]) and the RTI step
@@ -186,8 +188,7 @@ cudaError_t di_rti(rtn_ctx* ctx, const float* x0, const float* xref, const float
                    int* status);
 cudaError_t di_reset(rtn_ctx* ctx, const float* x0);
 
-// a1, FP32 SIMT path
-cudaError_t mlp_f32_forward(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+// a1, FP32 SIMT kernels of the allocation-free entry point
 cudaError_t mlp_f32_hidden_launch(const float* W, const float* bias, int M, int K, const float* X,
                                   float* Y, int n_nodes, cudaStream_t s);
 cudaError_t mlp_f32_out_launch(const float* WL, const float* bL, int K, const float* X,

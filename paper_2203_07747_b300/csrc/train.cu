@@ -290,7 +290,8 @@ rtn_status ensure_train(rtn_ctx* ctx, int bs) {
   return RTN_OK;
 }
 
-// after the FP32 master weights changed: FP64 plant copy and tensor-core pack
+// after the FP32 master weights changed: FP64 plant copy and the tensor-core
+// packs (split BF16, or the TF32 hi/lo weights of RTN_FP32 contexts)
 rtn_status refresh_network(rtn_ctx* ctx) {
   Net& net = ctx->net;
   const int L = net.n_layers;
@@ -314,6 +315,12 @@ rtn_status refresh_network(rtn_ctx* ctx) {
     if (ce != cudaSuccess || !e.empty()) return tfail(ctx, RTN_E_CUDA, "repacking the network: " + e);
     if (keep >= 0 && mlp_tc_variant_info(ctx, keep, nullptr, nullptr, nullptr) == 0)
       TCK(mlp_tc_select(ctx, keep));
+  } else if (ctx->tf) {
+    const int mode = ctx->tf->mode;
+    mlp_tf32_release(ctx);
+    std::string e;
+    cudaError_t ce = mlp_tf32_prepare(ctx, mode, e);
+    if (ce != cudaSuccess || !e.empty()) return tfail(ctx, RTN_E_CUDA, "repacking the network: " + e);
   }
   return RTN_OK;
 }
