@@ -551,16 +551,14 @@ def bench_second_order(config, bf16_burst, B=1024, reps=3):
         return r
 
     full = W.xavier_mlp(widths[:-1] + [6], 5)
-    # first order: FP32 SIMT network; second order: hidden layers on the
-    # tensor cores as kind::tf32 GEMMs with hi + lo split operands (three MMAs
-    # per product, so at most 1/3 of the TF32 peak in algorithmic FLOPs)
+    # first and second order: hidden layers on the tensor cores as kind::tf32
+    # GEMMs with hi + lo split operands (three MMAs per product, so at most
+    # 1/3 of the TF32 peak in algorithmic FLOPs)
     tf32_peak = bf16_burst * 1.1 / 2.25
     out = {"workload": f"{config} network and horizon, {B} instances ({nn} nodes), FP32-accurate paths",
-           "peak_kind": {"first order": "nominal FP32 FFMA: 148 SM x 128 lanes x 2 x 2.032 GHz",
-                         "second order": "TF32 dense = measured bf16 burst x 1.1/2.25 (nominal ratio); "
-                                         "the hi+lo split issues 3 MMAs per algorithmic product"},
+           "peak_kind": "TF32 dense = measured bf16 burst x 1.1/2.25 (nominal ratio); the hi+lo split issues "
+                        "3 MMAs per algorithmic product",
            "runs": []}
-    fp32_peak = 148 * 128 * 2 * 2.032e9 / 1e12
     for name, layers, second in (("first order, 3 outputs", prob["layers"], False),
                                  ("second order, 3 outputs", prob["layers"], True),
                                  ("first order, full residual (6 outputs)", full, False),
@@ -568,13 +566,12 @@ def bench_second_order(config, bf16_burst, B=1024, reps=3):
         r = run(layers, second)
         w = [wl.shape[1] for wl, _ in layers] + [layers[-1][0].shape[0]]
         fl = (hess_flops_per_node(w) if second else fwd_flops_per_node(w)) * nn
-        peak = tf32_peak if second else fp32_peak
         tf = fl / (r["ms_network"] * 1e-3) / 1e12
         out["runs"].append({"model": name, "widths": "-".join(map(str, w)),
                             "node_linearizations_per_s": nn / (r["ms_linearize"] * 1e-3),
                             "rti_steps_per_s": B / (r["ms_rti"] * 1e-3),
                             "network_ms": r["ms_network"], "network_tflops": tf,
-                            "roofline": {"bound": "tensor" if second else "alu", "peak": peak, "frac": tf / peak},
+                            "roofline": {"bound": "tensor", "peak": tf32_peak, "frac": tf / tf32_peak},
                             "failed_instances": r["failed_instances"]})
     return out
 
@@ -662,8 +659,10 @@ def main():
     rev = cfg.get("tile", {}).get("operand_mode") in (4, 5)  # reverse mode (one CTA / CTA pairs)
     flops = (rev_flops_per_node(widths) if rev else fwd_flops_per_node(widths)) * nn
     if prec == "fp32":
-        roof = {"bound": "alu", "peak": 148 * 128 * 2 * 2.032e9 / 1e12,
-                "peak_kind": "nominal FP32 FFMA: 148 SM x 128 lanes x 2 x 2.032 GHz"}
+        # FP32-accurate path: TF32 tensor cores with hi + lo split operands
+        # (3 MMAs per product: at most 1/3 of the peak in algorithmic FLOPs)
+        roof = {"bound": "tensor", "peak": bf16_burst * 1.1 / 2.25,
+                "peak_kind": f"TF32 dense = bf16 burst ({peak_src}) x 1.1/2.25 (nominal ratio); hi+lo split"}
     else:
         roof = {"bound": "tensor", "peak": bf16_burst, "peak_kind": f"bf16 burst ({peak_src})"}
     roof.update({"achieved": flops / (ms_mlp * 1e-3) / 1e12, "unit": "TFLOP/s",
