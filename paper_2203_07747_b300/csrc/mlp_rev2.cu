@@ -302,11 +302,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
               if (!ok) break;
               tc_fence_after();
               const uint32_t as = w_s + s * WT_BYTES;
+              uint64_t ad[4], bd[4];
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t bo = (uint32_t)(kk * 4 + ks) * 2u * lbo;  // 16 k = 2 k-groups
-                mma2_bf16(d, wdesc(as, ks), xdesc(xs_g + bo, lbo), idesc, (kb | ks) != 0);
+                ad[ks] = wdesc(as, ks);
+                bd[ks] = xdesc(xs_g + bo, lbo);
               }
+              mma2_bf16_x4(d, ad, bd, idesc, kb != 0);
               commit2(empty_bar(s), 3);
               if (++s == STAGES) { s = 0; ph ^= 1u; }
               // the GEMM's last read of block j: its producer may rewrite it

@@ -88,7 +88,7 @@ __device__ __forceinline__ void jvp_nominal(const QuadParams& P, const float* x,
 }
 
 template <int NOUT>
-__global__ void __launch_bounds__(256) rk4_sens_kernel(
+__global__ void __launch_bounds__(256, 2) rk4_sens_kernel(
     QuadParams P, const float* __restrict__ x, const float* __restrict__ u,
     const float* __restrict__ fD, const float* __restrict__ JD, const float* __restrict__ HD,
     const int* __restrict__ node_inst,
@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
   const int b = node_inst[n];
   const float h = dt_inst[b];
   const float* xk = x + (size_t)(n + b) * NX;
-  float x0[NX], uk[NU], fb[NOUT], J[NOUT][NZ];
+  float x0[NX], uk[NU], fb[NOUT];
+  // J_D is read from L1 where it is used (the 17 threads of a node share it)
+  // rather than held in registers: half the registers, twice the resident warps
+  const float* __restrict__ Jp = JD ? JD + (size_t)n * NOUT * NZ : nullptr;
 #pragma unroll
   for (int i = 0; i < NX; ++i) x0[i] = xk[i];
 #pragma unroll
@@ -112,11 +115,7 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
     for (int r = 0; r < NOUT; ++r) {
       fb[r] = fD[(size_t)n * NOUT + r];
       fin &= isfinite(fb[r]);
-#pragma unroll
-      for (int i = 0; i < NZ; ++i) {
-        J[r][i] = JD[(size_t)n * NOUT * NZ + r * NZ + i];
-        fin &= isfinite(J[r][i]);
-      }
+      for (int i = 0; i < NZ; ++i) fin &= isfinite(__ldg(Jp + r * NZ + i));
     }
     res = fin;  // non-finite residual: fall back to the nominal model
   }
@@ -151,11 +150,12 @@ __global__ void __launch_bounds__(256) rk4_sens_kernel(
         float v = fb[r], dv = 0.0f;
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
-          v = fmaf(J[r][i], xs[i] - x0[i], v);
-          dv = fmaf(J[r][i], Ss[i], dv);
+          const float Jri = __ldg(Jp + r * NZ + i);
+          v = fmaf(Jri, xs[i] - x0[i], v);
+          dv = fmaf(Jri, Ss[i], dv);
         }
 #pragma unroll
-        for (int i = 0; i < NU; ++i) dv = fmaf(J[r][NX + i], du[i], dv);
+        for (int i = 0; i < NU; ++i) dv = fmaf(__ldg(Jp + r * NZ + NX + i), du[i], dv);
         if (HD && s > 0) {
           // g = H_r dz (dz = xs - x0 on the state part): value + 1/2 dz'g,
           // directional derivative + g . [S; du]

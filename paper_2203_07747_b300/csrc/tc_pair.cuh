@@ -125,6 +125,22 @@ __device__ __forceinline__ void mma2_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
       : "memory");
 }
 
+// the four MMAs of one 64-wide K block under one election: accumulate
+// into D unless accum0 == 0 for the first (the later three always accumulate)
+__device__ __forceinline__ void mma2_bf16_x4(uint32_t d_tmem, const uint64_t (&a)[4], const uint64_t (&b)[4],
+                                             uint32_t idesc, uint32_t accum0) {
+  asm volatile(
+      "{\n\t.reg .pred p, t, e;\n\tsetp.ne.b32 p, %10, 0;\n\tsetp.eq.b32 t, %10, %10;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %9, p;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %3, %4, %9, t;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %5, %6, %9, t;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %7, %8, %9, t;\n\t}" ::"r"(d_tmem),
+      "l"(a[0]), "l"(b[0]), "l"(a[1]), "l"(b[1]), "l"(a[2]), "l"(b[2]), "l"(a[3]), "l"(b[3]), "r"(idesc),
+      "r"(accum0)
+      : "memory");
+}
+
 // arrive on the barrier at this offset in the CTAs of `mask` (bit r = rank r);
 // one elected lane of a converged warp
 __device__ __forceinline__ void commit2(uint32_t bar, uint16_t mask) {
