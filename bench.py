@@ -161,6 +161,31 @@ def launches_per_step(ctl):
     return mlp + 1 + 1 + 3  # network, RK4, Riccati, plant + record + advance
 
 
+def rank_barrier():
+    """Barrier over the ranks of a torchrun launch (no-op for one process)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def max_over_ranks(v, device):
+    """The maximum of a per-rank number over all ranks (the step time of a
+    weak-scaled run is the slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(instances_per_rank, world, ms_step_max):
+    """Whole-job RTI steps/s of a weak-scaled run: every rank steps its own
+    instances; the job's step takes the slowest rank's time."""
+    return instances_per_rank * world / (ms_step_max * 1e-3)
+
+
 def time_closed_loop(ctl, prob, steps, warmup):
     """Closed loop on the drag plant; every instance starts on its reference
     state (the random initial states of the workload recipe are used for the
@@ -180,10 +205,13 @@ def time_closed_loop(ctl, prob, steps, warmup):
     xr2, ur2 = xrt_d[:, warmup:].contiguous(), urt_d[:, warmup:].contiguous()
     with Clocks() as ck:
         torch.cuda.synchronize()
+        rank_barrier()
+        torch.cuda.synchronize()
         e0.record(s)
         traj, _ = ctl.closed_loop(steps, xr2, ur2, xp, plant="drag", record=True)
         e1.record(s)
         torch.cuda.synchronize()
+        rank_barrier()
     ms = e0.elapsed_time(e1)
     pos = traj[:, :, :3].double().cpu().numpy()
     err = np.linalg.norm(pos - xrt[:, warmup + 1:warmup + steps + 1, :3].transpose(1, 0, 2), axis=2)
@@ -597,7 +625,8 @@ def main():
     if args.second_order_only:
         print(json.dumps(bench_second_order(args.config, bf16_burst, B=args.second_order_only)))
         return
-    prob = W.make_problem(args.config, seed=0, bf16=True)
+    # weak scaling: every rank steps its own instances (seeded by rank)
+    prob = W.make_problem(args.config, seed=rank, bf16=True)
     widths = prob["widths"]
     B, nn = prob["B"], int(prob["N"].sum())
     cfg = {"workload": f"{args.config}: {B} instances, N={int(prob['N'].max())}, "
@@ -644,12 +673,8 @@ def main():
         cfg["tile"] = {"variant": vi, "nodes_per_cta": shape[0], "operand_mode": shape[1],
                        "stages": shape[2], "autotune_ms": vms}
     ms_step, clocks, rmse = time_closed_loop(ctl, prob, args.steps, args.warmup)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = B * world / (ms_step * 1e-3)
+    ms_step = max_over_ranks(ms_step, "cuda")
+    value = weak_value(B, world, ms_step)
 
     # node linearisations (a1 + a2) and the network kernel alone (a1)
     x, u = ctl.get_iterate()
