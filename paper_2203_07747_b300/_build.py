@@ -33,7 +33,7 @@ def build(force=False, verbose=False):
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + FLAGS + ["-o", tmp] + sources()
+    cmd = [nvcc] + ARCH + FLAGS + ["-o", tmp] + sources() + ["-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -85,6 +85,7 @@ struct TrainState {
   float *m = nullptr, *v = nullptr;    // Adam moments, same packing
   size_t nw = 0, nb = 0, b_base = 0;
   long long t = 0;                     // Adam step counter
+  void* blas = nullptr;                // cuBLAS handle of the training GEMMs
 };
 
 }  // namespace rtn

@@ -8,74 +8,37 @@
 //   backward  dW_l = G_l A_{l-1}',  db_l = sum_batch G_l,
 //             G_{l-1} = (W_l' G_l) * (1 - A_{l-1}^2)
 //   Adam      one fused launch over all parameters (FP32 master weights).
-// The GEMMs use one tiled FP32 SIMT kernel with optional transposes.
+// The GEMMs run in cuBLAS (FP32 emulated on the tensor cores), the rest in
+// the kernels below.
 #include <algorithm>
 #include <cmath>
 #include <string>
+
+#include <cublas_v2.h>
 
 #include "rtn_internal.cuh"
 
 namespace rtn {
 namespace {
 
-// C[M][N] (row-major, ldc) = op(A)[M][K] op(B)[K][N] (+ C if accumulate)
+// C[M][N] (row-major, ldc) = op(A)[M][K] op(B)[K][N]
 // op(A)(m,k) = TA ? A[k*lda + m] : A[m*lda + k];  op(B)(k,n) = TB ? B[n*ldb + k] : B[k*ldb + n]
-constexpr int GM = 64, GN = 64, GK = 16;
-
+// These are plain GEMMs (the bias, activation and loss epilogues are kernels
+// of their own), so they run in cuBLAS on the tensor cores with FP32
+// emulated by BF16 splits (CUBLAS_COMPUTE_32F_EMULATED_16BFX9, FP32-level
+// accuracy).  Row-major C = op(A) op(B) is column-major C' = op(B)' op(A)'.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, const float* __restrict__ A,
-                                                    int lda, const float* __restrict__ B, int ldb,
-                                                    float* __restrict__ C, int ldc) {
-  __shared__ float As[GK][GM + 4];
-  __shared__ float Bs[GK][GN + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = threadIdx.x; e < GK * GM; e += 256) {
-      int kk, mm;
-      if (TA) { mm = e % GM; kk = e / GM; } else { kk = e % GK; mm = e / GK; }
-      int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < K) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.0f;
-    }
-    for (int e = threadIdx.x; e < GK * GN; e += 256) {
-      int kk, nn;
-      if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % GN; kk = e / GN; }
-      int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < K) ? (TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int m = m0 + ty * 4 + i;
-    if (m >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int n = n0 + tx * 4 + j;
-      if (n < N) C[(size_t)m * ldc + n] = acc[i][j];
-    }
-  }
-}
-
-template <bool TA, bool TB>
-void sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-           cudaStream_t s) {
-  dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
-  sgemm_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+cudaError_t sgemm(TrainState& ts, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                  float* C, int ldc, cudaStream_t s) {
+  cublasHandle_t h = static_cast<cublasHandle_t>(ts.blas);
+  const float one = 1.0f, zero = 0.0f;
+  cublasStatus_t st = cublasSetStream(h, s);
+  if (st == CUBLAS_STATUS_SUCCESS)
+    st = cublasGemmEx(h, TB ? CUBLAS_OP_T : CUBLAS_OP_N, TA ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &one, B,
+                      CUDA_R_32F, ldb, A, CUDA_R_32F, lda, &zero, C, CUDA_R_32F, ldc,
+                      CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+  if (st == CUBLAS_STATUS_SUCCESS) return cudaSuccess;
+  return st == CUBLAS_STATUS_NOT_SUPPORTED ? cudaErrorNotSupported : cudaErrorUnknown;
 }
 
 // A_0 [17][bs] from samples [start, start + bs) of X [n][13], U [n][4]
@@ -193,7 +156,9 @@ cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float
   gather_input_kernel<<<blocks((size_t)NZ * bs), 256, 0, s>>>(X, U, start, bs, ts.act[0]);
   for (int l = 0; l < L; ++l) {
     const int fi = net.widths[l], fo = net.widths[l + 1];
-    sgemm<false, false>(fo, bs, fi, net.W32 + net.w_off[l], fi, ts.act[l], bs, ts.act[l + 1], bs, s);
+    cudaError_t e = sgemm<false, false>(ts, fo, bs, fi, net.W32 + net.w_off[l], fi, ts.act[l], bs, ts.act[l + 1],
+                                        bs, s);
+    if (e != cudaSuccess) return e;
     bias_act_kernel<<<blocks((size_t)fo * bs), 256, 0, s>>>(ts.act[l + 1], net.b32 + net.b_off[l], fo,
                                                             bs, l == L - 1);
   }
@@ -204,10 +169,12 @@ cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float
   float* Gn = ts.g1;
   for (int l = L - 1; l >= 0; --l) {
     const int fi = net.widths[l], fo = net.widths[l + 1];
-    sgemm<false, true>(fo, fi, bs, G, bs, ts.act[l], bs, ts.grad + net.w_off[l], fi, s);
+    cudaError_t e = sgemm<false, true>(ts, fo, fi, bs, G, bs, ts.act[l], bs, ts.grad + net.w_off[l], fi, s);
+    if (e != cudaSuccess) return e;
     rowsum_kernel<<<fo, 256, 0, s>>>(G, bs, ts.grad + ts.b_base + net.b_off[l]);
     if (l > 0) {
-      sgemm<true, false>(fi, bs, fo, net.W32 + net.w_off[l], fi, G, bs, Gn, bs, s);
+      e = sgemm<true, false>(ts, fi, bs, fo, net.W32 + net.w_off[l], fi, G, bs, Gn, bs, s);
+      if (e != cudaSuccess) return e;
       tanh_back_kernel<<<blocks((size_t)fi * bs), 256, 0, s>>>(Gn, ts.act[l], fi * bs);
       float* t = G; G = Gn; Gn = t;
     }
@@ -256,6 +223,15 @@ rtn_status ensure_train(rtn_ctx* ctx, int bs) {
   TrainState& ts = ctx->train;
   Net& net = ctx->net;
   const int L = net.n_layers;
+  if (!ts.blas) {
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return tfail(ctx, RTN_E_CUDA, "cublasCreate failed");
+    ts.blas = h;
+    // emulate FP32 on the tensor cores for every size (not only where the
+    // library expects a gain)
+    if (cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER) != CUBLAS_STATUS_SUCCESS)
+      return tfail(ctx, RTN_E_CUDA, "cublasSetEmulationStrategy failed");
+  }
   if (!ts.grad) {
     ts.nw = 0;
     ts.nb = 0;
@@ -422,6 +398,7 @@ void train_release(rtn_ctx* ctx) {
   for (float* p : ts.act) if (p) cudaFree(p);
   void* ptrs[] = {ts.g0, ts.g1, ts.grad, ts.m, ts.v};
   for (void* p : ptrs) if (p) cudaFree(p);
+  if (ts.blas) cublasDestroy(static_cast<cublasHandle_t>(ts.blas));
   ts = TrainState{};
 }
 }  // namespace rtn
