@@ -37,3 +37,72 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(rtn._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(rtn.RtnError):
         rtn.load()
+
+
+# ------------------------------------------------ argument checks (host only)
+# rtn_create validates every size and option before its first CUDA call, so
+# the rejections run without a GPU.
+
+def _create(lib, nx=13, nu=4, N=(5,), dt=(0.05,), widths=(17, 16, 3), opt=None, mlp=True, quad=True):
+    import paper_2203_07747_b300 as rtn
+    C = ctypes
+    B = len(N)
+    Na = (C.c_int * max(B, 1))(*N)
+    dta = (C.c_double * max(B, 1))(*dt)
+    Q = (C.c_double * 13)(*([1.0] * 13))
+    R = (C.c_double * 4)(*([0.1] * 4))
+    q = rtn._Quad(0.75, 2.5e-3, 2.1e-3, 4.3e-3, 0.14, 0.05, 8.5, 9.81)
+    keep = []
+    mp = None
+    if mlp:
+        w = (C.c_int * len(widths))(*widths)
+        Ws = [(C.c_float * (widths[l] * widths[l + 1]))() for l in range(len(widths) - 1)]
+        bs = [(C.c_float * widths[l + 1])() for l in range(len(widths) - 1)]
+        Wp = (C.POINTER(C.c_float) * len(Ws))(*[C.cast(a, C.POINTER(C.c_float)) for a in Ws])
+        bp = (C.POINTER(C.c_float) * len(bs))(*[C.cast(a, C.POINTER(C.c_float)) for a in bs])
+        keep += [w, Ws, bs, Wp, bp]
+        m = rtn._MLP(len(widths) - 1, w, Wp, bp)
+        keep.append(m)
+        mp = C.byref(m)
+    h = C.c_void_p()
+    o = rtn._Opt(*(opt or (0, 0, 1, 0, 0, 0)))
+    st = lib.rtn_create(C.byref(h), nx, nu, B, Na, dta, Q, R, None, C.byref(q) if quad else None, mp,
+                        C.byref(o), None)
+    assert not h.value  # no context on a rejected call
+    return st, lib.rtn_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,status,msg", [
+    (dict(N=()), 1, "bad batch"),                       # empty batch
+    (dict(N=(5, 0), dt=(0.05, 0.05)), 1, "N[b] >= 1"),   # an empty horizon
+    (dict(dt=(0.0,)), 1, "dt[b] > 0"),
+    (dict(dt=(float("nan"),)), 1, "dt[b] > 0"),
+    (dict(nx=12), 1, "nx, nu"),
+    (dict(widths=(16, 8, 3)), 1, "17 inputs"),
+    (dict(widths=(17, 8, 4)), 1, "17 inputs"),
+    (dict(widths=(17, 5000, 3)), 1, "hidden width"),
+    (dict(widths=(17, 3)), 1, "17 inputs"),             # no hidden layer
+    (dict(quad=False), 1, "bad batch"),
+    (dict(widths=(17, 8, 6), opt=(2, 0, 1, 0, 0, 0)), 7, "FP32 path"),   # 6 outputs on BF16 kernels
+    (dict(mlp=False, opt=(0, 0, 1, 0, 0, 1)), 7, "second_order"),       # second order, no network
+    (dict(opt=(1, 0, 1, 0, 0, 1)), 7, "second_order"),                  # second order, BF16
+    (dict(opt=(5, 0, 1, 0, 0, 0)), 1, "precision"),
+    (dict(opt=(0, 0, 1, 1, -1, 0)), 1, "box_max_iter"),
+    (dict(nx=2, nu=1, widths=(3, 8, 1), opt=(0, 0, 1, 1, 0, 0)), 7, "double-integrator"),
+    (dict(nx=2, nu=1, widths=(17, 8, 3)), 1, "double-integrator network"),
+])
+def test_create_rejects_bad_arguments(kw, status, msg):
+    import paper_2203_07747_b300 as rtn
+    lib = rtn.load(build_if_missing=True)
+    st, err = _create(lib, **kw)
+    assert st == status, (st, err)
+    assert msg in err, err
+
+
+def test_create_rejects_oversized_batch():
+    # more than 2^28 states and nodes: rejected before any allocation
+    import paper_2203_07747_b300 as rtn
+    lib = rtn.load(build_if_missing=True)
+    n = 1 << 20
+    st, err = _create(lib, N=(300,) * n, dt=(0.05,) * n)
+    assert st == 1 and "too large" in err
