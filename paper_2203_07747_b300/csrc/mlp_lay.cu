@@ -1,0 +1,550 @@
+// mlp_lay.cu -- (a1, reverse mode, layered) residual network value f_D and
+// input Jacobian J_D of every node, one layer of every node at a time.
+//
+// The fused kernels (mlp_rev.cu, mlp_rev2.cu) carry a tile of nodes through
+// all layers inside one CTA (pair), so each GEMM waits for the previous
+// layer's epilogue.  Here every layer is one GEMM over all nodes, its
+// activations passing through HBM/L2:
+//   input      a_1 = tanh(W_0 z + b_0), d_1 = 1 - a_1^2          (SIMT)
+//   forward    a_{l+1} = tanh(W_l a_l + b_l), d_{l+1}             (tcgen05)
+//   output     f_D = W_L a_L + b_L                               (SIMT)
+//   adjoints   D_L = d_L (.) W_L' (three columns per node)       (SIMT)
+//   backward   D_l = d_l (.) (W_l' D_{l+1})                      (tcgen05)
+//   Jacobian   J_D = W_0' D_1                                    (tcgen05)
+// with the split-BF16 arithmetic of the fused kernels: BF16 weights (W_0'
+// split hi + lo), activations and adjoints stored as BF16 hi + lo pairs (two
+// MMAs per K step, FP32 accumulation), d_l in FP32.  Layout: node-major rows,
+// X [node][hs] for values, [node * 3 + r][hs] for adjoints, so both operands
+// are K-major TMA tiles (128 B swizzle) and an epilogue lane (one neuron)
+// stores consecutive neurons of a node across the warp.
+// Tiles: M = 128 rows x N = 256 nodes (forward) or 80 nodes x 3 adjoints
+// (backward, Jacobian); persistent CTAs, K in stages of 64, two TMEM
+// accumulators so that the epilogue of one tile overlaps the next's MMAs.
+#include <algorithm>
+
+#include "tc_common.cuh"
+
+namespace rtn {
+namespace {
+
+constexpr int LY_KB = 64;                           // K per stage: 128 B of BF16
+constexpr uint32_t LY_A_BYTES = 128u * LY_KB * 2u;  // one 128-row weight tile
+constexpr int LY_NF = 256;                          // forward tile: nodes
+constexpr int LY_NBN = 80;                          // backward tile: nodes
+constexpr int LY_NODE_PAD = 1280;                   // node rows padded to a multiple of both
+constexpr int LY_THREADS = 320;                     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int LY_EPI_WARPS = 8;                     // two per TMEM lane quarter, alternate column chunks
+constexpr int LY_STAGES = 2;
+constexpr uint32_t LY_TMEM_COLS = 512;
+enum { LY_FWD = 0, LY_BWD = 1, LY_JD = 2 };
+
+template <int MODE>
+struct Ly {
+  static constexpr int N = MODE == LY_FWD ? LY_NF : 3 * LY_NBN;  // MMA N
+  static constexpr int NODES = MODE == LY_FWD ? LY_NF : LY_NBN;  // nodes per tile
+  static constexpr int NA = MODE == LY_JD ? 2 : 1;               // weight tiles per stage (JD: hi, lo)
+};
+template <int MODE>
+__host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * LY_KB * 2u; }
+template <int MODE>
+__host__ __device__ constexpr uint32_t ly_stage() { return Ly<MODE>::NA * LY_A_BYTES + 2u * ly_b_bytes<MODE>(); }
+template <int MODE>
+__host__ __device__ constexpr size_t ly_smem() { return LY_STAGES * ly_stage<MODE>() + 1024 + 256; }
+static_assert(ly_b_bytes<LY_FWD>() % 1024 == 0 && ly_b_bytes<LY_BWD>() % 1024 == 0, "1 KB aligned tiles");
+static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448, "shared memory");
+
+struct LyMaps {
+  CUtensorMap bh, bl;  // activations / adjoints hi, lo
+};
+
+struct LyArgs {
+  int a_row0;     // weight row of M tile 0 in the stacked weights
+  int a_lo;       // JD: row offset of the lo weights
+  int m_rows;     // real output rows
+  int mts;        // M tiles
+  int nkb;        // K blocks
+  int n_nodes, n_groups, hs;
+  const float* bias;   // FWD: bias of the produced layer
+  float* d_out;        // FWD: d of the produced layer [node][hs]
+  const float* d_in;   // BWD: d of the adjoint's layer [node][hs]
+  __nv_bfloat16* yh;   // FWD / BWD outputs
+  __nv_bfloat16* yl;
+  float* JD;           // JD output [node][3][17]
+  int* err;
+};
+
+__device__ __forceinline__ void split_bf(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// one GEMM layer over all nodes (see the file comment); MODE selects the
+// operands' shape and the epilogue
+template <int MODE>
+__global__ void __launch_bounds__(LY_THREADS, 1)
+    lay_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ LyMaps bm, LyArgs a) {
+  using T = Ly<MODE>;
+  constexpr uint32_t B_BYTES = ly_b_bytes<MODE>(), STAGE = ly_stage<MODE>();
+  constexpr uint32_t B0 = T::NA * LY_A_BYTES;  // offset of the B tiles in a stage
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t sraw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
+  uint8_t* sm = smem_raw + pad;
+  const uint32_t st0 = sraw + pad;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + LY_STAGES * STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * LY_STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto bar = [&](int k) { return smem_u32(bars + k); };
+  auto full_bar = [&](int s) { return bar(s); };
+  auto empty_bar = [&](int s) { return bar(LY_STAGES + s); };
+  auto acc_full = [&](int c) { return bar(2 * LY_STAGES + c); };
+  auto tmem_free = [&](int c) { return bar(2 * LY_STAGES + 2 + c); };
+  const uint32_t mma_done = bar(2 * LY_STAGES + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n_tiles = (long long)a.n_groups * a.mts;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < LY_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int c = 0; c < 2; ++c) {
+      mbar_init(acc_full(c), 1);
+      mbar_init(tmem_free(c), LY_EPI_WARPS);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(LY_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&amap)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bm.bh)) : "memory");
+    }
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    uint32_t issued = 0, last_ph = 0;
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
+      for (int kb = 0; kb < a.nkb; ++kb) {
+        if (!(ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
+        if (elect_one()) {
+          const uint32_t sa = st0 + s * STAGE;
+          mbar_expect_tx(full_bar(s), STAGE);
+          tma_load_2d(sa, &amap, kb * LY_KB, a.a_row0 + mt * 128, full_bar(s));
+          if (MODE == LY_JD) tma_load_2d(sa + LY_A_BYTES, &amap, kb * LY_KB, a.a_row0 + a.a_lo, full_bar(s));
+          tma_load_2d(sa + B0, &bm.bh, kb * LY_KB, grp * T::N, full_bar(s));
+          tma_load_2d(sa + B0 + B_BYTES, &bm.bl, kb * LY_KB, grp * T::N, full_bar(s));
+        }
+        __syncwarp();
+        issued |= 1u << s;
+        last_ph = (last_ph & ~(1u << s)) | (ph << s);
+        if (++s == LY_STAGES) { s = 0; ph ^= 1u; }
+      }
+    }
+    for (int q = 0; q < LY_STAGES; ++q)
+      if (issued & (1u << q)) {
+        const long long t0 = clock64();
+        while (!mbar_try(full_bar(q), (last_ph >> q) & 1u) && clock64() - t0 < WAIT_CYCLES) {
+        }
+      }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(128, T::N);  // both operands K-major
+    int s = 0, acc = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      if (!(ok = mbar_wait_warp(tmem_free(acc), aph ^ 1u, abort_flag, a.err))) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * 256u;
+      for (int kb = 0; kb < a.nkb; ++kb) {
+        if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err))) break;
+        tc_fence_after();
+        const uint32_t sa = st0 + s * STAGE;
+#pragma unroll
+        for (int ks = 0; ks < LY_KB / 16; ++ks) {
+          const uint64_t ah = kmajor_desc(sa + ks * 32u, 1024, 2);
+          const uint64_t bh = kmajor_desc(sa + B0 + ks * 32u, 1024, 2);
+          const uint64_t bl = kmajor_desc(sa + B0 + B_BYTES + ks * 32u, 1024, 2);
+          mma_bf16_elect(d, ah, bh, idesc, (kb | ks) != 0);
+          mma_bf16_elect(d, ah, bl, idesc, 1u);
+          if (MODE == LY_JD) mma_bf16_elect(d, kmajor_desc(sa + LY_A_BYTES + ks * 32u, 1024, 2), bh, idesc, 1u);
+        }
+        mma_commit_elect(empty_bar(s));
+        if (++s == LY_STAGES) { s = 0; ph ^= 1u; }
+      }
+      if (!ok) break;
+      mma_commit_elect(acc_full(acc));
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
+    }
+    mma_commit_elect(mma_done);
+    const long long t0 = clock64();
+    while (!mbar_try(mma_done, 0) && clock64() - t0 < WAIT_CYCLES) {
+    }
+  } else {
+    // ---------------- epilogue: TMEM lane quarter warp % 4, one output row
+    // per lane; the two warps of a quarter take alternate 16-column chunks.
+    // Each chunk issues its loads first and predicates only the stores, so
+    // the loads and the activation arithmetic of 16 columns overlap.
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    int acc = 0;
+    uint32_t aph = 0;
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
+      if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err)) break;
+      tc_fence_after();
+      const int i = mt * 128 + q * 32 + lane;
+      const bool active = i < a.m_rows;
+      const int ic = active ? i : 0;  // a row that exists, for the loads
+      const int node0 = grp * T::NODES;
+      const float bi = MODE == LY_FWD ? __ldg(a.bias + ic) : 0.0f;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
+      for (int ch = half; ch < T::N / 16; ch += 2) {
+        float v[16];
+        tmem_ld16(taddr + 16 * ch, v);
+        tmem_wait_ld();
+        if (MODE == LY_FWD) {
+          float av[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) av[k] = v[k] + bi;
+          tanh_batch<16>(av);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int node = node0 + 16 * ch + k;
+            if (active && node < a.n_nodes) {
+              const size_t o = (size_t)node * a.hs + i;
+              a.d_out[o] = 1.0f - av[k] * av[k];
+              __nv_bfloat16 h, l;
+              split_bf(av[k], h, l);
+              a.yh[o] = h;
+              a.yl[o] = l;
+            }
+          }
+        } else if (MODE == LY_BWD) {
+          float dv[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int node = min(node0 + (16 * ch + k) / 3, a.n_nodes - 1);
+            dv[k] = __ldg(a.d_in + (size_t)node * a.hs + ic);
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int c = 16 * ch + k, node = node0 + c / 3, r = c % 3;
+            if (active && node < a.n_nodes) {
+              const size_t o = ((size_t)node * 3 + r) * a.hs + i;
+              __nv_bfloat16 h, l;
+              split_bf(v[k] * dv[k], h, l);
+              a.yh[o] = h;
+              a.yl[o] = l;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int c = 16 * ch + k, node = node0 + c / 3, r = c % 3;
+            if (active && node < a.n_nodes) a.JD[((size_t)node * 3 + r) * NZ + i] = v[k];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_free(acc));
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LY_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// input layer: thread (neuron i, node n): a_1 = tanh(W_0 z + b_0), d_1
+__global__ void __launch_bounds__(256) lay_in_kernel(const float* __restrict__ x, const float* __restrict__ u,
+                                                     const int* __restrict__ node_inst, int n_nodes,
+                                                     const float* __restrict__ W0t, const float* __restrict__ b0,
+                                                     int h1, int HP, int hs, float* __restrict__ d1,
+                                                     __nv_bfloat16* __restrict__ xh, __nv_bfloat16* __restrict__ xl) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  if (i >= h1) return;
+  float w[NZ];
+#pragma unroll
+  for (int j = 0; j < NZ; ++j) w[j] = __ldg(W0t + (size_t)j * HP + i);
+  const float bi = __ldg(b0 + i);
+  // four nodes per step (their input loads and arithmetic overlap)
+  for (int n0 = (blockIdx.y * 8 + threadIdx.y) * 4; n0 < n_nodes; n0 += gridDim.y * 8 * 4) {
+    float sv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int n = min(n0 + t, n_nodes - 1);
+      const float* xr = x + (size_t)(n + node_inst[n]) * NX;
+      const float* ur = u + (size_t)n * NU;
+      float s = bi;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) s = fmaf(w[j], __ldg(xr + j), s);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) s = fmaf(w[NX + j], __ldg(ur + j), s);
+      sv[t] = s;
+    }
+    tanh_batch<4>(sv);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (n0 + t >= n_nodes) break;
+      const size_t o = (size_t)(n0 + t) * hs + i;
+      d1[o] = 1.0f - sv[t] * sv[t];
+      __nv_bfloat16 h, l;
+      split_bf(sv[t], h, l);
+      xh[o] = h;
+      xl[o] = l;
+    }
+  }
+}
+
+// output layer f_D = W_L a_L + b_L (warp per node) and the last layer's
+// adjoints D_L[node * 3 + r][i] = d_L[i] W_L[r][i] (split hi + lo)
+__global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL,
+                                                      int h, int n_nodes, int hs, const __nv_bfloat16* __restrict__ xh,
+                                                      const __nv_bfloat16* __restrict__ xl,
+                                                      const float* __restrict__ dL, float* __restrict__ fD,
+                                                      __nv_bfloat16* __restrict__ Dh, __nv_bfloat16* __restrict__ Dl,
+                                                      int HP) {
+  const int lane = threadIdx.x & 31;
+  for (long long node = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; node < n_nodes;
+       node += ((long long)gridDim.x * blockDim.x) >> 5) {
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    const size_t row = (size_t)node * hs;
+    // four columns per lane per step, loads first
+    for (int i0 = lane; i0 < h; i0 += 128) {
+      float av[4], dv[4], w0[4], w1[4], w2[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = min(i0 + 32 * t, h - 1);
+        av[t] = __bfloat162float(xh[row + i]) + __bfloat162float(xl[row + i]);
+        dv[t] = dL[row + i];
+        w0[t] = __ldg(WL + i);
+        w1[t] = __ldg(WL + HP + i);
+        w2[t] = __ldg(WL + 2 * HP + i);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = i0 + 32 * t;
+        if (i >= h) break;
+        f0 = fmaf(w0[t], av[t], f0);
+        f1 = fmaf(w1[t], av[t], f1);
+        f2 = fmaf(w2[t], av[t], f2);
+        __nv_bfloat16 hh, ll;
+        const size_t o = (size_t)node * 3 * hs + i;
+        split_bf(dv[t] * w0[t], hh, ll);
+        Dh[o] = hh;
+        Dl[o] = ll;
+        split_bf(dv[t] * w1[t], hh, ll);
+        Dh[o + hs] = hh;
+        Dl[o + hs] = ll;
+        split_bf(dv[t] * w2[t], hh, ll);
+        Dh[o + 2 * hs] = hh;
+        Dl[o + 2 * hs] = ll;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+    }
+    if (lane == 0) {
+      fD[node * NO + 0] = f0 + bL[0];
+      fD[node * NO + 1] = f1 + bL[1];
+      fD[node * NO + 2] = f2 + bL[2];
+    }
+  }
+}
+
+}  // namespace
+
+const void* mlp_lay_fn() { return reinterpret_cast<const void*>(&lay_kernel<LY_FWD>); }
+size_t mlp_lay_smem() { return ly_smem<LY_JD>(); }
+
+cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
+  TcNet& tc = ctx->net.tc;
+  if (tc.lay) return cudaSuccess;
+  Net& net = ctx->net;
+  const int L = net.n_layers, n = ctx->lay.n_nodes, HP = tc.h_pad;
+  const long long npad = ((long long)n + LY_NODE_PAD - 1) / LY_NODE_PAD * LY_NODE_PAD;
+  if (3 * npad >= (1LL << 31)) {
+    err = "layered reverse mode: more nodes than the 32-bit tensor coordinates address";
+    return cudaSuccess;
+  }
+  LayState* s = new (std::nothrow) LayState();
+  if (!s) return cudaErrorMemoryAllocation;
+  tc.lay = s;
+  s->hs = HP;
+  s->npad = (int)npad;
+  cudaError_t e;
+  for (int b = 0; b < 2; ++b)
+    for (int p = 0; p < 2; ++p) {
+      if ((e = cudaMalloc(&s->xf[b][p], (size_t)npad * HP * 2)) != cudaSuccess) return e;
+      if ((e = cudaMemset(s->xf[b][p], 0, (size_t)npad * HP * 2)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&s->xb[b][p], (size_t)3 * npad * HP * 2)) != cudaSuccess) return e;
+      if ((e = cudaMemset(s->xb[b][p], 0, (size_t)3 * npad * HP * 2)) != cudaSuccess) return e;
+    }
+  if ((e = cudaMalloc(&s->d, (size_t)(L - 1) * npad * HP * 4)) != cudaSuccess) return e;
+
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+  if (e != cudaSuccess || !fn || qr != cudaDriverEntryPointSuccess) {
+    err = "cuTensorMapEncodeTiled unavailable";
+    return cudaSuccess;
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t str[1] = {(cuuint64_t)HP * 2};
+  auto enc = [&](void* mp, void* ptr, long long rows, int box_rows) -> bool {
+    const cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)rows};
+    const cuuint32_t box[2] = {(cuuint32_t)LY_KB, (cuuint32_t)box_rows};
+    return encode(reinterpret_cast<CUtensorMap*>(mp), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, str, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  // maps of each buffer: forward tiles read values (box 256 rows), backward
+  // and Jacobian tiles read adjoints (box 240 rows); no box reaches past its
+  // tensor (rows padded to a multiple of both tiles)
+  for (int b = 0; b < 2; ++b)
+    for (int p = 0; p < 2; ++p) {
+      if (!enc(s->mf[b][p], s->xf[b][p], npad, LY_NF) || !enc(s->mb[b][p], s->xb[b][p], 3 * npad, 3 * LY_NBN)) {
+        err = "cuTensorMapEncodeTiled failed";
+        return cudaSuccess;
+      }
+    }
+  if ((e = cudaFuncSetAttribute(lay_kernel<LY_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ly_smem<LY_FWD>())) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(lay_kernel<LY_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ly_smem<LY_BWD>())) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(lay_kernel<LY_JD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ly_smem<LY_JD>());
+}
+
+void mlp_lay_release(rtn_ctx* ctx) {
+  LayState* s = ctx->net.tc.lay;
+  if (!s) return;
+  for (int b = 0; b < 2; ++b)
+    for (int p = 0; p < 2; ++p) {
+      if (s->xf[b][p]) cudaFree(s->xf[b][p]);
+      if (s->xb[b][p]) cudaFree(s->xb[b][p]);
+    }
+  if (s->d) cudaFree(s->d);
+  delete s;
+  ctx->net.tc.lay = nullptr;
+}
+
+cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD) {
+  TcNet& tc = ctx->net.tc;
+  LayState* s = tc.lay;
+  if (!s) return cudaErrorInvalidValue;
+  Net& net = ctx->net;
+  const int L = net.n_layers, n = ctx->lay.n_nodes, HP = tc.h_pad, hs = s->hs;
+  const int nh = L - 2;
+  const size_t dstride = (size_t)s->npad * hs;
+  cudaStream_t st = ctx->stream;
+  const CUtensorMap* wmap = reinterpret_cast<const CUtensorMap*>(tc.tmap_bytes);
+  const CUtensorMap* rmap = reinterpret_cast<const CUtensorMap*>(tc.tmapR_bytes);
+  auto maps = [&](unsigned char (&h)[128], unsigned char (&l)[128]) {
+    LyMaps m;
+    memcpy(&m.bh, h, sizeof(CUtensorMap));
+    memcpy(&m.bl, l, sizeof(CUtensorMap));
+    return m;
+  };
+  auto grid_of = [&](long long tiles) { return (int)std::min<long long>(tiles, std::max(1, tc.n_sm)); };
+  // input layer -> values buffer 0, d_1
+  {
+    dim3 grid((unsigned)((net.widths[1] + 31) / 32), (unsigned)std::min((n + 31) / 32, 65535));
+    lay_in_kernel<<<grid, dim3(32, 8), 0, st>>>(x, u, ctx->lay.node_inst, n, tc.W0, tc.b0, net.widths[1], HP, hs,
+                                                s->d, s->xf[0][0], s->xf[0][1]);
+  }
+  // forward hidden layers: GEMM g reads buffer g % 2, writes the other and d_{g+2}
+  const int gf = (n + LY_NF - 1) / LY_NF;
+  for (int g = 0; g < nh; ++g) {
+    const int src = g & 1, dst = src ^ 1, ho = net.widths[g + 2];
+    LyArgs a{};
+    a.a_row0 = g * HP;
+    a.m_rows = ho;
+    a.mts = (ho + 127) / 128;
+    a.nkb = HP / LY_KB;
+    a.n_nodes = n;
+    a.n_groups = gf;
+    a.hs = hs;
+    a.bias = tc.bias + (size_t)g * HP;
+    a.d_out = s->d + (size_t)(g + 1) * dstride;
+    a.yh = s->xf[dst][0];
+    a.yl = s->xf[dst][1];
+    a.err = tc.err;
+    lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD>(), st>>>(
+        *wmap, maps(s->mf[src][0], s->mf[src][1]), a);
+  }
+  // f_D and the last layer's adjoints -> adjoint buffer 0
+  {
+    const int last = nh & 1;
+    const long long warps = n;
+    lay_out_kernel<<<(int)std::min<long long>((warps + 7) / 8, 148LL * 64), 256, 0, st>>>(
+        tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs, s->xf[last][0], s->xf[last][1],
+        s->d + (size_t)(L - 2) * dstride, fD, s->xb[0][0], s->xb[0][1], HP);
+  }
+  // backward hidden layers: D_l = d_l (.) (W_l' D_{l+1}), l = L - 2 .. 1
+  const int gb = (n + LY_NBN - 1) / LY_NBN;
+  const int tb = nh * HP + 128;  // first transposed row in the reverse-mode stack
+  for (int k = 0; k < nh; ++k) {
+    const int l = L - 2 - k, src = k & 1, dst = src ^ 1, hl = net.widths[l];
+    LyArgs a{};
+    a.a_row0 = tb + (l - 1) * HP;
+    a.m_rows = hl;
+    a.mts = (hl + 127) / 128;
+    a.nkb = HP / LY_KB;
+    a.n_nodes = n;
+    a.n_groups = gb;
+    a.hs = hs;
+    a.d_in = s->d + (size_t)(l - 1) * dstride;
+    a.yh = s->xb[dst][0];
+    a.yl = s->xb[dst][1];
+    a.err = tc.err;
+    lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD>(), st>>>(
+        *rmap, maps(s->mb[src][0], s->mb[src][1]), a);
+  }
+  // J_D = W_0' D_1 (W_0' hi and lo rows)
+  {
+    const int src = nh & 1;
+    LyArgs a{};
+    a.a_row0 = tb + nh * HP;
+    a.a_lo = 128;
+    a.m_rows = NZ;
+    a.mts = 1;
+    a.nkb = HP / LY_KB;
+    a.n_nodes = n;
+    a.n_groups = gb;
+    a.hs = hs;
+    a.JD = JD;
+    a.err = tc.err;
+    lay_kernel<LY_JD><<<grid_of(gb), LY_THREADS, ly_smem<LY_JD>(), st>>>(*rmap, maps(s->mb[src][0], s->mb[src][1]),
+                                                                          a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rtn

@@ -370,7 +370,8 @@ struct Variant {
   int npc;
   int mode;  // 0 single, 1 split (two MMAs), 2 split (hi|lo along N), 3 split on a CTA pair,
              // 4 split, reverse mode (value forward, three adjoints backward),
-             // 5 split, reverse mode on a CTA pair
+             // 5 split, reverse mode on a CTA pair,
+             // 6 split, reverse mode layered (one GEMM per layer over all nodes)
   int stages;
   const void* fn;
   bool split() const { return mode != 0; }
@@ -387,6 +388,7 @@ struct Variant {
     return (pair() ? std::max(2, HP / 256) : HP / 128) * tmem_per_mtile();
   }
   size_t smem(int HP) const {
+    if (mode == 6) return mlp_lay_smem();
     if (mode == 5) return mlp_rev2_smem(HP, stages);
     if (rev())
       return 1024 + (size_t)128 * HP * 2 + (size_t)stages * WT_BYTES + 8 * (2 * stages + 20) + 16 +
@@ -419,6 +421,8 @@ Variant rev2_variant() {
   return Variant{42, 5, STAGES, mlp_rev2_fn(42, STAGES)};
 }
 
+Variant lay_variant() { return Variant{0, 6, 2, mlp_lay_fn()}; }
+
 // every compiled tile shape; the autotuner times those that fit
 const std::vector<Variant>& all_variants() {
   static const std::vector<Variant> v = {
@@ -427,7 +431,7 @@ const std::vector<Variant>& all_variants() {
       variant<5, 1, 6>(),  variant<4, 1, 3>(),  variant<3, 1, 6>(),  variant<7, 2, 5>(),
       variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>(),  pair_variant<7, 4>(),
       pair_variant<6, 5>(), pair_variant<7, 8>(), pair_variant<4, 6>(), rev_variant<21, 6>(),
-      rev_variant<21, 4>(), rev_variant<16, 6>(), rev2_variant<3>(), rev2_variant<6>()};
+      rev_variant<21, 4>(), rev_variant<16, 6>(), rev2_variant<3>(), rev2_variant<6>(), lay_variant()};
   return v;
 }
 
@@ -476,6 +480,13 @@ cudaError_t select_variant(rtn_ctx* ctx, int idx) {
   int ncol = 32;
   while (ncol < v.tmem_columns(tc.h_pad)) ncol *= 2;
   tc.tmem_cols = ncol;
+  if (v.mode == 6) {  // buffers and maps of the layered path (once)
+    std::string e;
+    cudaError_t ce = mlp_lay_prepare(ctx, e);
+    if (ce != cudaSuccess) return ce;
+    if (!e.empty()) return cudaErrorNotSupported;
+    return cudaSuccess;
+  }
   return cudaFuncSetAttribute(tc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
 }
 
@@ -644,6 +655,7 @@ cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* 
   void* args[] = {(void*)map, (void*)&a};
   const int n_tiles = (a.n_nodes + tc.npc - 1) / tc.npc;
   const Variant& v = all_variants()[tc.variant];
+  if (v.mode == 6) return mlp_lay_launch(ctx, x, u, fD, JD);
   if (v.mode == 5) return mlp_rev2_launch(ctx, x, u, fD, JD);
   if (v.rev()) return mlp_rev_launch(ctx, x, u, fD, JD);
   dim3 grid = v.pair() ? dim3(2 * std::min(n_tiles, std::max(1, tc.n_sm / 2)))
@@ -667,6 +679,7 @@ int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages
 cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx) { return select_variant(ctx, idx); }
 
 void mlp_tc_release(rtn_ctx* ctx) {
+  mlp_lay_release(ctx);
   TcNet& tc = ctx->net.tc;
   void* ptrs[] = {tc.W, tc.bias, tc.W0, tc.b0, tc.err, tc.trace, tc.WR, tc.WL32, tc.dscr};
   for (void* p : ptrs)

@@ -43,6 +43,18 @@ struct Layout {
   int* order = nullptr;      // [B] instances sorted by decreasing N_b
 };
 
+// Layered reverse mode (mlp_lay.cu): values [npad][hs] and adjoints
+// [3 npad][hs] as BF16 hi + lo in ping-pong buffers, d_l of every hidden
+// layer [L-1][npad][hs] in FP32, tensor maps of every buffer.
+struct LayState {
+  int hs = 0, npad = 0;
+  __nv_bfloat16* xf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  __nv_bfloat16* xb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  float* d = nullptr;
+  alignas(64) unsigned char mf[2][2][128];  // values, box 64 x 256
+  alignas(64) unsigned char mb[2][2][128];  // adjoints, box 64 x 240
+};
+
 // Packed network for the tensor-core path -- see mlp_tc.cu.
 struct TcNet {
   int h_pad = 0;                // hidden width padded to a multiple of 128
@@ -63,6 +75,7 @@ struct TcNet {
   float* WL32 = nullptr;                // output layer FP32 [3][h_pad]
   float* dscr = nullptr;                // per-CTA d_l scratch
   alignas(64) unsigned char tmapR_bytes[128];  // CUtensorMap of WR
+  LayState* lay = nullptr;              // layered reverse mode (tile mode 6)
 };
 
 struct Net {
@@ -212,6 +225,13 @@ cudaError_t mlp_rev_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
 const void* mlp_rev2_fn(int npc, int stages);
 size_t mlp_rev2_smem(int HP, int stages);
 cudaError_t mlp_rev2_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+// layered reverse mode (mlp_lay.cu): kernel of its forward GEMM, shared
+// memory of its largest GEMM, buffers and maps, launch sequence
+const void* mlp_lay_fn();
+size_t mlp_lay_smem();
+cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err);
+void mlp_lay_release(rtn_ctx* ctx);
+cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
