@@ -78,6 +78,32 @@ __device__ __forceinline__ void split_bf(float v, __nv_bfloat16& h, __nv_bfloat1
   l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// backward epilogue of one 16-node group (48 accumulator columns, node k
+// in columns 3k .. 3k + 2): the warp of half H stores nodes 8H .. 8H + 7,
+// D = acc * d with d loaded once per node
+template <int H>
+__device__ __forceinline__ void bwd_group(const float (&v)[48], const float* __restrict__ d_in, int node_g,
+                                          int n_nodes, int hs, int i, int ic, bool active,
+                                          __nv_bfloat16* __restrict__ yh, __nv_bfloat16* __restrict__ yl) {
+  float dv[8];
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) dv[kk] = __ldg(d_in + (size_t)min(node_g + 8 * H + kk, n_nodes - 1) * hs + ic);
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const int k = 8 * H + kk, node = node_g + k;
+    if (active && node < n_nodes) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const size_t o = ((size_t)node * 3 + r) * hs + i;
+        __nv_bfloat16 h, l;
+        split_bf(v[3 * k + r] * dv[kk], h, l);
+        yh[o] = h;
+        yl[o] = l;
+      }
+    }
+  }
+}
+
 // one GEMM layer over all nodes (see the file comment); MODE selects the
 // operands' shape and the epilogue
 template <int MODE>
@@ -214,7 +240,22 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       const int node0 = grp * T::NODES;
       const float bi = MODE == LY_FWD ? __ldg(a.bias + ic) : 0.0f;
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
-      for (int ch = half; ch < T::N / 16; ch += 2) {
+      if (MODE == LY_BWD) {
+        // 16-node groups: both warps of the quarter read the group's 48
+        // columns, each stores its 8 nodes
+        for (int g = 0; g < T::NODES / 16; ++g) {
+          float v[48];
+          tmem_ld16(taddr + 48 * g, v);
+          tmem_ld16(taddr + 48 * g + 16, v + 16);
+          tmem_ld16(taddr + 48 * g + 32, v + 32);
+          tmem_wait_ld();
+          if (half == 0)
+            bwd_group<0>(v, a.d_in, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
+          else
+            bwd_group<1>(v, a.d_in, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
+        }
+      }
+      for (int ch = half; MODE != LY_BWD && ch < T::N / 16; ch += 2) {
         float v[16];
         tmem_ld16(taddr + 16 * ch, v);
         tmem_wait_ld();
@@ -231,24 +272,6 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
               a.d_out[o] = 1.0f - av[k] * av[k];
               __nv_bfloat16 h, l;
               split_bf(av[k], h, l);
-              a.yh[o] = h;
-              a.yl[o] = l;
-            }
-          }
-        } else if (MODE == LY_BWD) {
-          float dv[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int node = min(node0 + (16 * ch + k) / 3, a.n_nodes - 1);
-            dv[k] = __ldg(a.d_in + (size_t)node * a.hs + ic);
-          }
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int c = 16 * ch + k, node = node0 + c / 3, r = c % 3;
-            if (active && node < a.n_nodes) {
-              const size_t o = ((size_t)node * 3 + r) * a.hs + i;
-              __nv_bfloat16 h, l;
-              split_bf(v[k] * dv[k], h, l);
               a.yh[o] = h;
               a.yl[o] = l;
             }
@@ -475,7 +498,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
   auto grid_of = [&](long long tiles) { return (int)std::min<long long>(tiles, std::max(1, tc.n_sm)); };
   // input layer -> values buffer 0, d_1
   {
-    dim3 grid((unsigned)((net.widths[1] + 31) / 32), (unsigned)std::min((n + 31) / 32, 65535));
+    dim3 grid((unsigned)((net.widths[1] + 31) / 32), (unsigned)std::min((n + 127) / 128, 65535));
     lay_in_kernel<<<grid, dim3(32, 8), 0, st>>>(x, u, ctx->lay.node_inst, n, tc.W0, tc.b0, net.widths[1], HP, hs,
                                                 s->d, s->xf[0][0], s->xf[0][1]);
   }
