@@ -40,14 +40,14 @@ def peaks():
 
 
 KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc2.cu", "mlp_rev.cu", "mlp_rev2.cu", "tc_common.cuh", "tc_pair.cuh")
-PROFILES = ("mlp_rev2_kernel_cfg3_h512_bf16x2.md", "mlp_rev_kernel_cfg3_h512_bf16x2.md",
+PROFILES = ("mlp_lay_cfg3_h512_bf16x2.md", "mlp_rev2_kernel_cfg3_h512_bf16x2.md", "mlp_rev_kernel_cfg3_h512_bf16x2.md",
             "mlp_tc2_kernel_cfg3_h512_bf16x2.md", "mlp_tc_kernel_cfg3_h512_bf16x2.md")
 
 
-def kernel_md5():
-    """md5 over the tensor-core network kernel sources (the profiles record it)."""
+def kernel_md5(files=KERNEL_SOURCES):
+    """md5 over kernel sources (each profile records it with its file list)."""
     h = hashlib.md5()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2203_07747_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -58,19 +58,21 @@ def profiled_traffic(tile):
     summary, if the kernel sources and the tile shape are the captured ones."""
     if tile is None:
         return None
-    try:
-        md5 = kernel_md5()
-        for name in PROFILES:
+    for name in PROFILES:
+        try:
             text = open(os.path.join(ROOT, "profiles", name)).read()
-            m = re.search(r"kernel sources md5 at capture: (\w+)", text)
+            m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
             shape = re.search(r"tile shape: npc=(\d+) mode=(\d+) stages=(\d+)", text)
-            if not m or not shape or m.group(1) != md5:
+            if not m or not shape:
+                continue
+            files = tuple(f.strip() for f in m.group(2).split("+"))
+            if m.group(1) != kernel_md5(files):
                 continue
             if (tile["nodes_per_cta"], int(tile["operand_mode"]), tile["stages"]) != tuple(map(int, shape.groups())):
                 continue
             return int(re.search(r"dram_bytes_per_launch: (\d+)", text).group(1))
-    except (OSError, AttributeError):
-        pass
+        except (OSError, AttributeError):
+            continue
     return None
 
 
@@ -155,9 +157,11 @@ def make(prob, precision, riccati_f64=False, box_qp=False):
                           box_qp=box_qp)
 
 
-def launches_per_step(ctl):
+def launches_per_step(ctl, tile_mode=None):
     L = len(ctl.layers) if ctl.layers else 0
-    mlp = 0 if not L else (1 if ctl.precision != "fp32" else L)
+    # network: one fused launch, the layered reverse mode 2 L - 1, the FP32
+    # path L (input, hidden GEMMs, output)
+    mlp = 0 if not L else (L if ctl.precision == "fp32" else 2 * L - 1 if tile_mode == 6 else 1)
     return mlp + 1 + 1 + 3  # network, RK4, Riccati, plant + record + advance
 
 
@@ -549,6 +553,22 @@ def hess_flops_per_node(widths):
     return f
 
 
+def bench_network_pass(config, B, reps=3):
+    """The network pass (a1) of the workload's network on B instances with
+    the layered reverse-mode shape: ms per pass after one warm-up pass."""
+    import torch
+    prob = W.make_problem(config, seed=0, B=B, bf16=True)
+    ctl = make(prob, "bf16x2")
+    vi = [v[0] for v in ctl.tc_variants() if v[2] == 6][0]
+    ctl.tc_select(vi)
+    x, u = ctl.get_iterate()
+    fD, JD = ctl.mlp_eval(x, u)
+    ms = time_calls(lambda: ctl.mlp_eval(x, u, fD, JD), reps, warm=1)
+    out = {"instances": B, "nodes": ctl.n_nodes, "variant": vi, "ms_per_pass": ms, "device_error": ctl.device_error()}
+    ctl.close()
+    return out
+
+
 def bench_second_order(config, bf16_burst, B=1024, reps=3):
     """f4: the second-order local model (network Hessian H_D, Eq. 4) and the
     6-output full residual (Eq. 7) on the FP32 path, B instances of the
@@ -629,6 +649,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged and learned workloads")
     ap.add_argument("--second-order-only", type=int, default=0, metavar="B",
                     help="run only the second-order / full-residual measurement with B instances")
+    ap.add_argument("--network-pass", type=int, default=0, metavar="B",
+                    help="time only the network pass (a1) of the workload's network on B instances with "
+                         "the layered reverse-mode tile shape (the profiling command of its summary)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -636,6 +659,9 @@ def main():
     hbm, bf16_burst, bf16_sus, peak_src = peaks()
     if args.second_order_only:
         print(json.dumps(bench_second_order(args.config, bf16_burst, B=args.second_order_only)))
+        return
+    if args.network_pass:
+        print(json.dumps(bench_network_pass(args.config, args.network_pass)))
         return
     # weak scaling: every rank steps its own instances (seeded by rank)
     prob = W.make_problem(args.config, seed=rank, bf16=True)
@@ -693,7 +719,8 @@ def main():
     out = ctl.linearize(x, u)
     ms_lin = time_calls(lambda: ctl.linearize(x, u, out), max(5, args.steps))
     ms_mlp = time_calls(lambda: ctl.mlp_eval(x, u, out[0], out[1]), max(5, args.steps))
-    rev = cfg.get("tile", {}).get("operand_mode") in (4, 5)  # reverse mode (one CTA / CTA pairs)
+    mode = cfg.get("tile", {}).get("operand_mode")
+    rev = mode in (4, 5, 6)  # reverse mode (one CTA / CTA pairs / layered)
     flops = (rev_flops_per_node(widths) if rev else fwd_flops_per_node(widths)) * nn
     if prec == "fp32":
         # FP32-accurate path: TF32 tensor cores with hi + lo split operands
@@ -704,11 +731,19 @@ def main():
         roof = {"bound": "tensor", "peak": bf16_burst, "peak_kind": f"bf16 burst ({peak_src})"}
     roof.update({"achieved": flops / (ms_mlp * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "algorithmic_flops_per_launch": flops, "ms_per_launch": ms_mlp,
-                 "kernel": ("network value + reverse-mode Jacobian (a1, three adjoint rows)" if rev
+                 "kernel": ("network pass of the layered reverse mode (a1): input layer, one tensor-core GEMM per "
+                            "forward layer, output layer and last-layer adjoints, one GEMM per backward layer, "
+                            "the W_0' Jacobian GEMM (11 launches at 5 hidden layers)" if mode == 6 else
+                            "network value + reverse-mode Jacobian (a1, three adjoint rows)" if rev
                             else "network value + forward-mode Jacobian (a1)"),
                  "forward_mode_equivalent_tflops": fwd_flops_per_node(widths) * nn / (ms_mlp * 1e-3) / 1e12,
                  "traffic": profiled_traffic(cfg.get("tile")) if args.config == "cfg3_bf16_precision" else None})
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if roof.get("traffic"):
+        # what the pass moves through DRAM per launch at the timed rate (the
+        # layered shape streams every layer's operands through HBM)
+        roof["dram_tbs_at_traffic"] = roof["traffic"] / (ms_mlp * 1e-3) / 1e12
+        roof["hbm_peak_tbs"] = hbm / 1e3
 
     ms_e2e, bi, bo = e2e_rti(ctl, prob, max(5, args.steps))
     etab = error_table(prob, prec) if rank == 0 and world == 1 and prec != "fp32" else None
@@ -722,7 +757,7 @@ def main():
             "roofline": roof, "error_table": etab,
             "e2e": {"value": B / (ms_e2e * 1e-3), "unit": "RTI steps/s", "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo, "path": "rtn_rti_step with pinned host buffers"},
-            "gpu_launches": launches_per_step(ctl) * args.steps, "clocks": clocks}
+            "gpu_launches": launches_per_step(ctl, mode) * args.steps, "clocks": clocks}
     ctl.close()
     if prec != "fp32" and not args.no_fp32:
         c32 = make(prob, "fp32")
