@@ -36,13 +36,17 @@ constexpr int LY_THREADS = 320;                     // warp 0 TMA, warp 1 MMA, w
 constexpr int LY_EPI_WARPS = 8;                     // two per TMEM lane quarter, alternate column chunks
 constexpr int LY_STAGES = 2;
 constexpr uint32_t LY_TMEM_COLS = 512;
-enum { LY_FWD = 0, LY_BWD = 1, LY_JD = 2 };
+// FWD forward layer; BWD backward layer; JD the W_0' Jacobian; BW0 the
+// first backward layer with the last-layer adjoints folded into its weights
+// (M_r = W_{L-2}' diag(W_L[r]), B = d_{L-1}), see mlp_lay_launch
+enum { LY_FWD = 0, LY_BWD = 1, LY_JD = 2, LY_BW0 = 3 };
 
 template <int MODE>
 struct Ly {
-  static constexpr int N = MODE == LY_FWD ? LY_NF : 3 * LY_NBN;  // MMA N
-  static constexpr int NODES = MODE == LY_FWD ? LY_NF : LY_NBN;  // nodes per tile
-  static constexpr int NA = MODE == LY_JD ? 2 : 1;               // weight tiles per stage (JD: hi, lo)
+  static constexpr bool BYNODE = MODE == LY_FWD || MODE == LY_BW0;  // one column per node
+  static constexpr int N = BYNODE ? LY_NF : 3 * LY_NBN;            // MMA N
+  static constexpr int NODES = BYNODE ? LY_NF : LY_NBN;            // nodes per tile
+  static constexpr int NA = (MODE == LY_JD || MODE == LY_BW0) ? 2 : 1;  // weight tiles per stage (hi, lo)
 };
 template <int MODE>
 __host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * LY_KB * 2u; }
@@ -51,7 +55,8 @@ __host__ __device__ constexpr uint32_t ly_stage() { return Ly<MODE>::NA * LY_A_B
 template <int MODE>
 __host__ __device__ constexpr size_t ly_smem() { return LY_STAGES * ly_stage<MODE>() + 1024 + 256; }
 static_assert(ly_b_bytes<LY_FWD>() % 1024 == 0 && ly_b_bytes<LY_BWD>() % 1024 == 0, "1 KB aligned tiles");
-static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448, "shared memory");
+static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448 && ly_smem<LY_BW0>() <= 232448,
+              "shared memory");
 
 struct LyMaps {
   CUtensorMap bh, bl;  // activations / adjoints hi, lo
@@ -62,10 +67,13 @@ struct LyArgs {
   int a_lo;       // JD: row offset of the lo weights
   int m_rows;     // real output rows
   int mts;        // M tiles
+  int mtpr;       // BW0: M tiles per output component r
   int nkb;        // K blocks
   int n_nodes, n_groups, hs;
   const float* bias;   // FWD: bias of the produced layer
-  float* d_out;        // FWD: d of the produced layer [node][hs]
+  float* d_out;        // FWD: d of the produced layer [node][hs] (FP32), or
+  __nv_bfloat16* dh;   //      into dh / dl as BF16 hi + lo when dh is set
+  __nv_bfloat16* dl;
   const float* d_in;   // BWD: d of the adjoint's layer [node][hs]
   __nv_bfloat16* yh;   // FWD / BWD outputs
   __nv_bfloat16* yl;
@@ -172,7 +180,8 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
           const uint32_t sa = st0 + s * STAGE;
           mbar_expect_tx(full_bar(s), STAGE);
           tma_load_2d(sa, &amap, kb * LY_KB, a.a_row0 + mt * 128, full_bar(s));
-          if (MODE == LY_JD) tma_load_2d(sa + LY_A_BYTES, &amap, kb * LY_KB, a.a_row0 + a.a_lo, full_bar(s));
+          if (T::NA == 2)
+            tma_load_2d(sa + LY_A_BYTES, &amap, kb * LY_KB, a.a_row0 + a.a_lo + mt * 128, full_bar(s));
           tma_load_2d(sa + B0, &bm.bh, kb * LY_KB, grp * T::N, full_bar(s));
           tma_load_2d(sa + B0 + B_BYTES, &bm.bl, kb * LY_KB, grp * T::N, full_bar(s));
         }
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
           const uint64_t bl = kmajor_desc(sa + B0 + B_BYTES + ks * 32u, 1024, 2);
           mma_bf16_elect(d, ah, bh, idesc, (kb | ks) != 0);
           mma_bf16_elect(d, ah, bl, idesc, 1u);
-          if (MODE == LY_JD) mma_bf16_elect(d, kmajor_desc(sa + LY_A_BYTES + ks * 32u, 1024, 2), bh, idesc, 1u);
+          if (T::NA == 2) mma_bf16_elect(d, kmajor_desc(sa + LY_A_BYTES + ks * 32u, 1024, 2), bh, idesc, 1u);
         }
         mma_commit_elect(empty_bar(s));
         if (++s == LY_STAGES) { s = 0; ph ^= 1u; }
@@ -234,7 +243,9 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
       if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err)) break;
       tc_fence_after();
-      const int i = mt * 128 + q * 32 + lane;
+      // output row i (BW0: row k of component r)
+      const int r0 = MODE == LY_BW0 ? mt / a.mtpr : 0;
+      const int i = (MODE == LY_BW0 ? mt % a.mtpr : mt) * 128 + q * 32 + lane;
       const bool active = i < a.m_rows;
       const int ic = active ? i : 0;  // a row that exists, for the loads
       const int node0 = grp * T::NODES;
@@ -269,9 +280,32 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
             const int node = node0 + 16 * ch + k;
             if (active && node < a.n_nodes) {
               const size_t o = (size_t)node * a.hs + i;
-              a.d_out[o] = 1.0f - av[k] * av[k];
               __nv_bfloat16 h, l;
+              if (a.dh) {
+                split_bf(1.0f - av[k] * av[k], h, l);
+                a.dh[o] = h;
+                a.dl[o] = l;
+              } else {
+                a.d_out[o] = 1.0f - av[k] * av[k];
+              }
               split_bf(av[k], h, l);
+              a.yh[o] = h;
+              a.yl[o] = l;
+            }
+          }
+        } else if (MODE == LY_BW0) {
+          // D_{L-2}[node * 3 + r][i] = acc * d_{L-2}[node][i], loads first
+          float dv[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            dv[k] = __ldg(a.d_in + (size_t)min(node0 + 16 * ch + k, a.n_nodes - 1) * a.hs + ic);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int node = node0 + 16 * ch + k;
+            if (active && node < a.n_nodes) {
+              const size_t o = ((size_t)node * 3 + r0) * a.hs + i;
+              __nv_bfloat16 h, l;
+              split_bf(v[k] * dv[k], h, l);
               a.yh[o] = h;
               a.yl[o] = l;
             }
@@ -360,7 +394,7 @@ __global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ 
       for (int t = 0; t < 4; ++t) {
         const int i = min(i0 + 32 * t, h - 1);
         av[t] = __bfloat162float(xh[row + i]) + __bfloat162float(xl[row + i]);
-        dv[t] = dL[row + i];
+        dv[t] = Dh ? dL[row + i] : 0.0f;
         w0[t] = __ldg(WL + i);
         w1[t] = __ldg(WL + HP + i);
         w2[t] = __ldg(WL + 2 * HP + i);
@@ -372,6 +406,7 @@ __global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ 
         f0 = fmaf(w0[t], av[t], f0);
         f1 = fmaf(w1[t], av[t], f1);
         f2 = fmaf(w2[t], av[t], f2);
+        if (!Dh) continue;  // the adjoints are folded into the first backward GEMM
         __nv_bfloat16 hh, ll;
         const size_t o = (size_t)node * 3 * hs + i;
         split_bf(dv[t] * w0[t], hh, ll);
@@ -402,7 +437,7 @@ __global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ 
 }  // namespace
 
 const void* mlp_lay_fn() { return reinterpret_cast<const void*>(&lay_kernel<LY_FWD>); }
-size_t mlp_lay_smem() { return ly_smem<LY_JD>(); }
+size_t mlp_lay_smem() { return std::max(ly_smem<LY_JD>(), ly_smem<LY_BW0>()); }
 
 cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   TcNet& tc = ctx->net.tc;
@@ -428,6 +463,32 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
       if ((e = cudaMemset(s->xb[b][p], 0, (size_t)3 * npad * HP * 2)) != cudaSuccess) return e;
     }
   if ((e = cudaMalloc(&s->d, (size_t)(L - 1) * npad * HP * 4)) != cudaSuccess) return e;
+  const int nh = L - 2;
+  if (nh >= 1) {
+    for (int p = 0; p < 2; ++p) {
+      if ((e = cudaMalloc(&s->dd[p], (size_t)npad * HP * 2)) != cudaSuccess) return e;
+      if ((e = cudaMemset(s->dd[p], 0, (size_t)npad * HP * 2)) != cudaSuccess) return e;
+    }
+    // M_r[k][i] = W_{L-2}[i][k] W_L[r][i] with the BF16-rounded hidden
+    // weights of the other shapes and the FP32 output layer, split hi + lo
+    const int hk = net.widths[L - 2], hi_ = net.widths[L - 1];
+    std::vector<float> Wa((size_t)hi_ * hk), Wl((size_t)NO * hi_);
+    if ((e = cudaMemcpy(Wa.data(), net.W32 + net.w_off[L - 2], Wa.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpy(Wl.data(), net.W32 + net.w_off[L - 1], Wl.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return e;
+    std::vector<__nv_bfloat16> M((size_t)6 * HP * HP, __float2bfloat16_rn(0.0f));
+    for (int r = 0; r < NO; ++r)
+      for (int k = 0; k < hk; ++k)
+        for (int i = 0; i < hi_; ++i) {
+          const float m = __bfloat162float(__float2bfloat16_rn(Wa[(size_t)i * hk + k])) * Wl[(size_t)r * hi_ + i];
+          const __nv_bfloat16 h = __float2bfloat16_rn(m);
+          M[((size_t)r * HP + k) * HP + i] = h;
+          M[((size_t)(3 + r) * HP + k) * HP + i] = __float2bfloat16_rn(m - __bfloat162float(h));
+        }
+    if ((e = cudaMalloc(&s->mw, M.size() * 2)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(s->mw, M.data(), M.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  }
 
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult qr;
@@ -456,6 +517,14 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
         return cudaSuccess;
       }
     }
+  if (nh >= 1 && (!enc(s->mmap, s->mw, 6LL * HP, 128) || !enc(s->mdd[0], s->dd[0], npad, LY_NF) ||
+                  !enc(s->mdd[1], s->dd[1], npad, LY_NF))) {
+    err = "cuTensorMapEncodeTiled failed";
+    return cudaSuccess;
+  }
+  if ((e = cudaFuncSetAttribute(lay_kernel<LY_BW0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ly_smem<LY_BW0>())) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(lay_kernel<LY_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ly_smem<LY_FWD>())) != cudaSuccess)
     return e;
@@ -474,6 +543,9 @@ void mlp_lay_release(rtn_ctx* ctx) {
       if (s->xb[b][p]) cudaFree(s->xb[b][p]);
     }
   if (s->d) cudaFree(s->d);
+  if (s->mw) cudaFree(s->mw);
+  for (int p = 0; p < 2; ++p)
+    if (s->dd[p]) cudaFree(s->dd[p]);
   delete s;
   ctx->net.tc.lay = nullptr;
 }
@@ -516,25 +588,53 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.hs = hs;
     a.bias = tc.bias + (size_t)g * HP;
     a.d_out = s->d + (size_t)(g + 1) * dstride;
+    if (g == nh - 1) {  // d_{L-1}: the B operand of the folded first backward GEMM
+      a.dh = s->dd[0];
+      a.dl = s->dd[1];
+    }
     a.yh = s->xf[dst][0];
     a.yl = s->xf[dst][1];
     a.err = tc.err;
     lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD>(), st>>>(
         *wmap, maps(s->mf[src][0], s->mf[src][1]), a);
   }
-  // f_D and the last layer's adjoints -> adjoint buffer 0
+  // f_D (and, with no hidden->hidden layer, the last layer's adjoints into
+  // adjoint buffer 0)
   {
     const int last = nh & 1;
     const long long warps = n;
     lay_out_kernel<<<(int)std::min<long long>((warps + 7) / 8, 148LL * 64), 256, 0, st>>>(
         tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs, s->xf[last][0], s->xf[last][1],
-        s->d + (size_t)(L - 2) * dstride, fD, s->xb[0][0], s->xb[0][1], HP);
+        s->d + (size_t)(L - 2) * dstride, fD, nh >= 1 ? nullptr : s->xb[0][0], s->xb[0][1], HP);
   }
-  // backward hidden layers: D_l = d_l (.) (W_l' D_{l+1}), l = L - 2 .. 1
+  // first backward layer with the last layer's adjoints folded in:
+  // D_{L-2}[n, r] = d_{L-2} (.) (M_r d_{L-1}[n]) -> adjoint buffer 0
+  if (nh >= 1) {
+    LyArgs a{};
+    a.a_row0 = 0;
+    a.a_lo = 3 * HP;
+    a.m_rows = net.widths[L - 2];
+    a.mtpr = HP / 128;
+    a.mts = 3 * a.mtpr;
+    a.nkb = HP / LY_KB;
+    a.n_nodes = n;
+    a.n_groups = gf;
+    a.hs = hs;
+    a.d_in = s->d + (size_t)(L - 3) * dstride;
+    a.yh = s->xb[0][0];
+    a.yl = s->xb[0][1];
+    a.err = tc.err;
+    LyMaps m;
+    memcpy(&m.bh, s->mdd[0], sizeof(CUtensorMap));
+    memcpy(&m.bl, s->mdd[1], sizeof(CUtensorMap));
+    lay_kernel<LY_BW0><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_BW0>(), st>>>(
+        *reinterpret_cast<const CUtensorMap*>(s->mmap), m, a);
+  }
+  // the other backward hidden layers: D_l = d_l (.) (W_l' D_{l+1}), l = L - 3 .. 1
   const int gb = (n + LY_NBN - 1) / LY_NBN;
   const int tb = nh * HP + 128;  // first transposed row in the reverse-mode stack
-  for (int k = 0; k < nh; ++k) {
-    const int l = L - 2 - k, src = k & 1, dst = src ^ 1, hl = net.widths[l];
+  for (int k = 1; k < nh; ++k) {
+    const int l = L - 2 - k, src = (k - 1) & 1, dst = src ^ 1, hl = net.widths[l];
     LyArgs a{};
     a.a_row0 = tb + (l - 1) * HP;
     a.m_rows = hl;
@@ -552,7 +652,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
   }
   // J_D = W_0' D_1 (W_0' hi and lo rows)
   {
-    const int src = nh & 1;
+    const int src = nh >= 1 ? (nh - 1) & 1 : 0;
     LyArgs a{};
     a.a_row0 = tb + nh * HP;
     a.a_lo = 128;
