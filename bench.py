@@ -649,6 +649,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged and learned workloads")
     ap.add_argument("--second-order-only", type=int, default=0, metavar="B",
                     help="run only the second-order / full-residual measurement with B instances")
+    ap.add_argument("--tile", type=int, default=-1, metavar="V",
+                    help="use tile shape V instead of autotuning (to profile the shape a plain run chose: "
+                         "ncu's per-launch overhead changes the autotuner's ranking)")
     ap.add_argument("--network-pass", type=int, default=0, metavar="B",
                     help="time only the network pass (a1) of the workload's network on B instances with "
                          "the layered reverse-mode tile shape (the profiling command of its summary)")
@@ -706,7 +709,11 @@ def main():
     cfg["precision"] = prec
     if prec != "fp32":
         # pick the tensor-core tile shape for this network and batch
-        vi, vms = ctl.autotune()
+        if args.tile >= 0:
+            ctl.tc_select(args.tile)
+            vi, vms = args.tile, None
+        else:
+            vi, vms = ctl.autotune()
         shape = dict((v[0], v[1:]) for v in ctl.tc_variants())[vi]
         cfg["tile"] = {"variant": vi, "nodes_per_cta": shape[0], "operand_mode": shape[1],
                        "stages": shape[2], "autotune_ms": vms}
