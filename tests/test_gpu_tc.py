@@ -160,9 +160,10 @@ def test_cfg3_error_table_against_oracle(rtn, orc):
 @pytest.mark.gpu
 @pytest.mark.parametrize("widths", [[17, 512, 512, 512, 3], [17, 512, 3], [17, 256, 256, 3]])
 def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
-    # reverse-mode shapes (one CTA: 21 nodes per tile; CTA pairs: 42) with
-    # several tiles per CTA or pair and a ragged tail: f_D and J_D of sampled
-    # nodes against the oracle, every node finite
+    # reverse-mode shapes (one CTA: 21 nodes per tile; CTA pairs: 42; the
+    # layered pass: tiles of 256 / 80 nodes, with and without hidden->hidden
+    # layers) with several tiles per CTA or pair and a ragged tail: f_D and
+    # J_D of sampled nodes against the oracle, every node finite
     layers = [(Wl, W.round_bf16(np.random.default_rng(40 + i).normal(0, 0.05, bl.shape)))
               for i, (Wl, bl) in enumerate(W.xavier_mlp(widths, 7, bf16=True))]
     N = np.array([20] * 400 + [13], np.int32)  # 8013 nodes
@@ -179,7 +180,7 @@ def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
     ud = torch.as_tensor(U, dtype=torch.float32, device="cuda")
     seen = set()
     for vi, npc, mode, stages in ctl.tc_variants():
-        if mode not in (4, 5):
+        if mode not in (4, 5, 6):
             continue
         seen.add(mode)
         ctl.tc_select(vi)
@@ -190,4 +191,4 @@ def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
         ej = max(np.linalg.norm(J[n] - r[1]) / np.linalg.norm(r[1]) for n, r in zip(idx, ref))
         ef = max(np.abs(F[n] - r[0]).max() / max(np.abs(r[0]).max(), 1e-3) for n, r in zip(idx, ref))
         assert ej < 1e-3 and ef < 1e-3, (vi, npc, mode, stages, ej, ef)
-    assert 4 in seen and (5 in seen or widths[1] < 256)
+    assert 4 in seen and 6 in seen and (5 in seen or widths[1] < 256)
