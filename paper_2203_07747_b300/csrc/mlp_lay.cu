@@ -27,14 +27,19 @@
 namespace rtn {
 namespace {
 
-constexpr int LY_KB = 64;                           // K per stage: 128 B of BF16
+// K per stage: one 64 B row of BF16 (64 B swizzle), so that four stages of
+// every mode fit and the TMA runs four K blocks ahead of the MMAs (with two
+// stages of 128 B rows the GEMMs waited on each stage's DRAM latency)
+constexpr int LY_KB = 32;
+constexpr uint32_t LY_SBO = 512;   // 8 rows x 64 B between 8-row groups
+constexpr uint32_t LY_SWZ = 4;     // descriptor swizzle mode: 64 B
 constexpr uint32_t LY_A_BYTES = 128u * LY_KB * 2u;  // one 128-row weight tile
 constexpr int LY_NF = 256;                          // forward tile: nodes
 constexpr int LY_NBN = 80;                          // backward tile: nodes
 constexpr int LY_NODE_PAD = 1280;                   // node rows padded to a multiple of both
 constexpr int LY_THREADS = 320;                     // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int LY_EPI_WARPS = 8;                     // two per TMEM lane quarter, alternate column chunks
-constexpr int LY_STAGES = 2;
+constexpr int LY_STAGES = 4;
 constexpr uint32_t LY_TMEM_COLS = 512;
 // FWD forward layer; BWD backward layer; JD the W_0' Jacobian; BW0 the
 // first backward layer with the last-layer adjoints folded into its weights
@@ -213,12 +218,12 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
         const uint32_t sa = st0 + s * STAGE;
 #pragma unroll
         for (int ks = 0; ks < LY_KB / 16; ++ks) {
-          const uint64_t ah = kmajor_desc(sa + ks * 32u, 1024, 2);
-          const uint64_t bh = kmajor_desc(sa + B0 + ks * 32u, 1024, 2);
-          const uint64_t bl = kmajor_desc(sa + B0 + B_BYTES + ks * 32u, 1024, 2);
+          const uint64_t ah = kmajor_desc(sa + ks * 32u, LY_SBO, LY_SWZ);
+          const uint64_t bh = kmajor_desc(sa + B0 + ks * 32u, LY_SBO, LY_SWZ);
+          const uint64_t bl = kmajor_desc(sa + B0 + B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
           mma_bf16_elect(d, ah, bh, idesc, (kb | ks) != 0);
           mma_bf16_elect(d, ah, bl, idesc, 1u);
-          if (T::NA == 2) mma_bf16_elect(d, kmajor_desc(sa + LY_A_BYTES + ks * 32u, 1024, 2), bh, idesc, 1u);
+          if (T::NA == 2) mma_bf16_elect(d, kmajor_desc(sa + LY_A_BYTES + ks * 32u, LY_SBO, LY_SWZ), bh, idesc, 1u);
         }
         mma_commit_elect(empty_bar(s));
         if (++s == LY_STAGES) { s = 0; ph ^= 1u; }
@@ -504,7 +509,7 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
     const cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)rows};
     const cuuint32_t box[2] = {(cuuint32_t)LY_KB, (cuuint32_t)box_rows};
     return encode(reinterpret_cast<CUtensorMap*>(mp), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, str, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
   // maps of each buffer: forward tiles read values (box 256 rows), backward
@@ -517,6 +522,13 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
         return cudaSuccess;
       }
     }
+  // the stacked forward weights (W_1 .. W_L) and the reverse-mode stack
+  // (transposes, W_0' hi / lo) in this path's 64 B swizzled tiles
+  const long long rows_r = (long long)nh * HP + 128 + (long long)nh * HP + 256;
+  if (!enc(s->wmap, tc.W, tc.rows_total, 128) || !enc(s->rmap, tc.WR, rows_r, 128)) {
+    err = "cuTensorMapEncodeTiled failed";
+    return cudaSuccess;
+  }
   if (nh >= 1 && (!enc(s->mmap, s->mw, 6LL * HP, 128) || !enc(s->mdd[0], s->dd[0], npad, LY_NF) ||
                   !enc(s->mdd[1], s->dd[1], npad, LY_NF))) {
     err = "cuTensorMapEncodeTiled failed";
@@ -559,8 +571,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
   const int nh = L - 2;
   const size_t dstride = (size_t)s->npad * hs;
   cudaStream_t st = ctx->stream;
-  const CUtensorMap* wmap = reinterpret_cast<const CUtensorMap*>(tc.tmap_bytes);
-  const CUtensorMap* rmap = reinterpret_cast<const CUtensorMap*>(tc.tmapR_bytes);
+  const CUtensorMap* wmap = reinterpret_cast<const CUtensorMap*>(s->wmap);
+  const CUtensorMap* rmap = reinterpret_cast<const CUtensorMap*>(s->rmap);
   auto maps = [&](unsigned char (&h)[128], unsigned char (&l)[128]) {
     LyMaps m;
     memcpy(&m.bh, h, sizeof(CUtensorMap));

@@ -51,14 +51,16 @@ struct LayState {
   __nv_bfloat16* xf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   __nv_bfloat16* xb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   float* d = nullptr;
-  alignas(64) unsigned char mf[2][2][128];  // values, box 64 x 256
-  alignas(64) unsigned char mb[2][2][128];  // adjoints, box 64 x 240
+  alignas(64) unsigned char mf[2][2][128];  // values, box 32 x 256
+  alignas(64) unsigned char mb[2][2][128];  // adjoints, box 32 x 240
   // folded first backward layer: M_r = W_{L-2}' diag(W_L[r]) as BF16 hi rows
   // [3 HP][HP] then lo rows, and d_{L-1} as BF16 hi + lo [npad][hs]
   __nv_bfloat16* mw = nullptr;
   __nv_bfloat16* dd[2] = {nullptr, nullptr};
-  alignas(64) unsigned char mmap[128];      // M, box 64 x 128
-  alignas(64) unsigned char mdd[2][128];    // d_{L-1}, box 64 x 256
+  alignas(64) unsigned char mmap[128];      // M, box 32 x 128
+  alignas(64) unsigned char wmap[128];      // the stacked forward weights, box 32 x 128
+  alignas(64) unsigned char rmap[128];      // the reverse-mode weight stack, box 32 x 128
+  alignas(64) unsigned char mdd[2][128];    // d_{L-1}, box 32 x 256
 };
 
 // Packed network for the tensor-core path -- see mlp_tc.cu.
