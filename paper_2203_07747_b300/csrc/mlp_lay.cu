@@ -5,7 +5,7 @@
 // all layers inside one CTA (pair), so each GEMM waits for the previous
 // layer's epilogue.  Here every layer is one GEMM over all nodes, its
 // activations passing through HBM/L2:
-//   input      a_1 = tanh(W_0 z + b_0), d_1 = 1 - a_1^2          (SIMT)
+//   input      a_1 = tanh(W_0 z + b_0), d_1 = 1 - a_1^2          (tcgen05, K = 17 -> 32)
 //   forward    a_{l+1} = tanh(W_l a_l + b_l), d_{l+1}             (tcgen05)
 //   output     f_D = W_L a_L + b_L                               (SIMT)
 //   adjoints   D_L = d_L (.) W_L' (three columns per node)       (SIMT)
@@ -44,14 +44,17 @@ constexpr uint32_t LY_TMEM_COLS = 512;
 // FWD forward layer; BWD backward layer; JD the W_0' Jacobian; BW0 the
 // first backward layer with the last-layer adjoints folded into its weights
 // (M_r = W_{L-2}' diag(W_L[r]), B = d_{L-1}), see mlp_lay_launch
-enum { LY_FWD = 0, LY_BWD = 1, LY_JD = 2, LY_BW0 = 3 };
+// IN the input layer as a GEMM (W_0 hi / lo against z hi / lo, K = 17
+// padded to 32) with the forward epilogue
+enum { LY_FWD = 0, LY_BWD = 1, LY_JD = 2, LY_BW0 = 3, LY_IN = 4 };
 
 template <int MODE>
 struct Ly {
-  static constexpr bool BYNODE = MODE == LY_FWD || MODE == LY_BW0;  // one column per node
+  static constexpr bool ACT = MODE == LY_FWD || MODE == LY_IN;      // tanh epilogue
+  static constexpr bool BYNODE = ACT || MODE == LY_BW0;             // one column per node
   static constexpr int N = BYNODE ? LY_NF : 3 * LY_NBN;            // MMA N
   static constexpr int NODES = BYNODE ? LY_NF : LY_NBN;            // nodes per tile
-  static constexpr int NA = (MODE == LY_JD || MODE == LY_BW0) ? 2 : 1;  // weight tiles per stage (hi, lo)
+  static constexpr int NA = (MODE == LY_JD || MODE == LY_BW0 || MODE == LY_IN) ? 2 : 1;  // weight tiles (hi, lo)
 };
 template <int MODE>
 __host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * LY_KB * 2u; }
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       const bool active = i < a.m_rows;
       const int ic = active ? i : 0;  // a row that exists, for the loads
       const int node0 = grp * T::NODES;
-      const float bi = MODE == LY_FWD ? __ldg(a.bias + ic) : 0.0f;
+      const float bi = T::ACT ? __ldg(a.bias + ic) : 0.0f;
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
       if (MODE == LY_BWD) {
         // 16-node groups: both warps of the quarter read the group's 48
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
         float v[16];
         tmem_ld16(taddr + 16 * ch, v);
         tmem_wait_ld();
-        if (MODE == LY_FWD) {
+        if (T::ACT) {
           float av[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) av[k] = v[k] + bi;
@@ -338,45 +341,19 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
   }
 }
 
-// input layer: thread (neuron i, node n): a_1 = tanh(W_0 z + b_0), d_1
-__global__ void __launch_bounds__(256) lay_in_kernel(const float* __restrict__ x, const float* __restrict__ u,
-                                                     const int* __restrict__ node_inst, int n_nodes,
-                                                     const float* __restrict__ W0t, const float* __restrict__ b0,
-                                                     int h1, int HP, int hs, float* __restrict__ d1,
-                                                     __nv_bfloat16* __restrict__ xh, __nv_bfloat16* __restrict__ xl) {
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  if (i >= h1) return;
-  float w[NZ];
-#pragma unroll
-  for (int j = 0; j < NZ; ++j) w[j] = __ldg(W0t + (size_t)j * HP + i);
-  const float bi = __ldg(b0 + i);
-  // four nodes per step (their input loads and arithmetic overlap)
-  for (int n0 = (blockIdx.y * 8 + threadIdx.y) * 4; n0 < n_nodes; n0 += gridDim.y * 8 * 4) {
-    float sv[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int n = min(n0 + t, n_nodes - 1);
-      const float* xr = x + (size_t)(n + node_inst[n]) * NX;
-      const float* ur = u + (size_t)n * NU;
-      float s = bi;
-#pragma unroll
-      for (int j = 0; j < NX; ++j) s = fmaf(w[j], __ldg(xr + j), s);
-#pragma unroll
-      for (int j = 0; j < NU; ++j) s = fmaf(w[NX + j], __ldg(ur + j), s);
-      sv[t] = s;
-    }
-    tanh_batch<4>(sv);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (n0 + t >= n_nodes) break;
-      const size_t o = (size_t)(n0 + t) * hs + i;
-      d1[o] = 1.0f - sv[t] * sv[t];
-      __nv_bfloat16 h, l;
-      split_bf(sv[t], h, l);
-      xh[o] = h;
-      xl[o] = l;
-    }
-  }
+// node inputs z = [x; u] as the K-major B operand of the input-layer GEMM:
+// [node][32] BF16 hi + lo (columns 17..31 stay zero)
+__global__ void __launch_bounds__(256) lay_z_kernel(const float* __restrict__ x, const float* __restrict__ u,
+                                                    const int* __restrict__ node_inst, int n_nodes,
+                                                    __nv_bfloat16* __restrict__ zh, __nv_bfloat16* __restrict__ zl) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n_nodes * NZ) return;
+  const int n = (int)(e / NZ), j = (int)(e % NZ);
+  const float v = j < NX ? x[(size_t)(n + node_inst[n]) * NX + j] : u[(size_t)n * NU + (j - NX)];
+  __nv_bfloat16 h, l;
+  split_bf(v, h, l);
+  zh[(size_t)n * LY_KB + j] = h;
+  zl[(size_t)n * LY_KB + j] = l;
 }
 
 // output layer f_D = W_L a_L + b_L (warp per node) and the last layer's
@@ -442,7 +419,7 @@ __global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ 
 }  // namespace
 
 const void* mlp_lay_fn() { return reinterpret_cast<const void*>(&lay_kernel<LY_FWD>); }
-size_t mlp_lay_smem() { return std::max(ly_smem<LY_JD>(), ly_smem<LY_BW0>()); }
+size_t mlp_lay_smem() { return std::max(std::max(ly_smem<LY_JD>(), ly_smem<LY_BW0>()), ly_smem<LY_IN>()); }
 
 cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   TcNet& tc = ctx->net.tc;
@@ -468,6 +445,25 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
       if ((e = cudaMemset(s->xb[b][p], 0, (size_t)3 * npad * HP * 2)) != cudaSuccess) return e;
     }
   if ((e = cudaMalloc(&s->d, (size_t)(L - 1) * npad * HP * 4)) != cudaSuccess) return e;
+  for (int p = 0; p < 2; ++p) {
+    if ((e = cudaMalloc(&s->z[p], (size_t)npad * LY_KB * 2)) != cudaSuccess) return e;
+    if ((e = cudaMemset(s->z[p], 0, (size_t)npad * LY_KB * 2)) != cudaSuccess) return e;
+  }
+  {
+    // W_0 rows (FP32 [17][HP] transposed in the tensor-core pack) split hi + lo
+    std::vector<float> W0((size_t)NZ * HP);
+    if ((e = cudaMemcpy(W0.data(), tc.W0, W0.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+    std::vector<__nv_bfloat16> w((size_t)2 * HP * LY_KB, __float2bfloat16_rn(0.0f));
+    for (int i = 0; i < HP; ++i)
+      for (int j = 0; j < NZ; ++j) {
+        const float v = W0[(size_t)j * HP + i];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        w[(size_t)i * LY_KB + j] = h;
+        w[(size_t)(HP + i) * LY_KB + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+      }
+    if ((e = cudaMalloc(&s->w0s, w.size() * 2)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(s->w0s, w.data(), w.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  }
   const int nh = L - 2;
   if (nh >= 1) {
     for (int p = 0; p < 2; ++p) {
@@ -504,14 +500,24 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   }
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   const cuuint32_t estr[2] = {1, 1};
-  const cuuint64_t str[1] = {(cuuint64_t)HP * 2};
-  auto enc = [&](void* mp, void* ptr, long long rows, int box_rows) -> bool {
-    const cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)rows};
+  auto enc_k = [&](void* mp, void* ptr, int inner, long long rows, int box_rows) -> bool {
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t str[1] = {(cuuint64_t)inner * 2};
     const cuuint32_t box[2] = {(cuuint32_t)LY_KB, (cuuint32_t)box_rows};
     return encode(reinterpret_cast<CUtensorMap*>(mp), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, str, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
+  auto enc = [&](void* mp, void* ptr, long long rows, int box_rows) { return enc_k(mp, ptr, HP, rows, box_rows); };
+  if (!enc_k(s->mw0, s->w0s, LY_KB, 2LL * HP, 128) || !enc_k(s->mz[0], s->z[0], LY_KB, npad, LY_NF) ||
+      !enc_k(s->mz[1], s->z[1], LY_KB, npad, LY_NF)) {
+    err = "cuTensorMapEncodeTiled failed";
+    return cudaSuccess;
+  }
+  if ((e = cudaFuncSetAttribute(lay_kernel<LY_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ly_smem<LY_IN>())) != cudaSuccess)
+    return e;
+
   // maps of each buffer: forward tiles read values (box 256 rows), backward
   // and Jacobian tiles read adjoints (box 240 rows); no box reaches past its
   // tensor (rows padded to a multiple of both tiles)
@@ -556,6 +562,9 @@ void mlp_lay_release(rtn_ctx* ctx) {
     }
   if (s->d) cudaFree(s->d);
   if (s->mw) cudaFree(s->mw);
+  if (s->w0s) cudaFree(s->w0s);
+  for (int p = 0; p < 2; ++p)
+    if (s->z[p]) cudaFree(s->z[p]);
   for (int p = 0; p < 2; ++p)
     if (s->dd[p]) cudaFree(s->dd[p]);
   delete s;
@@ -580,14 +589,30 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     return m;
   };
   auto grid_of = [&](long long tiles) { return (int)std::min<long long>(tiles, std::max(1, tc.n_sm)); };
-  // input layer -> values buffer 0, d_1
+  // input layer -> values buffer 0, d_1: z split into BF16 hi + lo, then a
+  // GEMM against W_0 hi / lo with the forward epilogue
+  const int gf = (n + LY_NF - 1) / LY_NF;
   {
-    dim3 grid((unsigned)((net.widths[1] + 31) / 32), (unsigned)std::min((n + 127) / 128, 65535));
-    lay_in_kernel<<<grid, dim3(32, 8), 0, st>>>(x, u, ctx->lay.node_inst, n, tc.W0, tc.b0, net.widths[1], HP, hs,
-                                                s->d, s->xf[0][0], s->xf[0][1]);
+    const long long ne = (long long)n * NZ;
+    lay_z_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(x, u, ctx->lay.node_inst, n, s->z[0], s->z[1]);
+    LyArgs a{};
+    a.a_row0 = 0;
+    a.a_lo = HP;
+    a.m_rows = net.widths[1];
+    a.mts = (net.widths[1] + 127) / 128;
+    a.nkb = 1;
+    a.n_nodes = n;
+    a.n_groups = gf;
+    a.hs = hs;
+    a.bias = tc.b0;
+    a.d_out = s->d;
+    a.yh = s->xf[0][0];
+    a.yl = s->xf[0][1];
+    a.err = tc.err;
+    lay_kernel<LY_IN><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_IN>(), st>>>(
+        *reinterpret_cast<const CUtensorMap*>(s->mw0), maps(s->mz[0], s->mz[1]), a);
   }
   // forward hidden layers: GEMM g reads buffer g % 2, writes the other and d_{g+2}
-  const int gf = (n + LY_NF - 1) / LY_NF;
   for (int g = 0; g < nh; ++g) {
     const int src = g & 1, dst = src ^ 1, ho = net.widths[g + 2];
     LyArgs a{};

@@ -58,6 +58,12 @@ struct LayState {
   __nv_bfloat16* mw = nullptr;
   __nv_bfloat16* dd[2] = {nullptr, nullptr};
   alignas(64) unsigned char mmap[128];      // M, box 32 x 128
+  // input layer as a GEMM: z = [x; u] [npad][32] and W_0 [2 HP][32] (hi
+  // rows, then lo rows) as BF16
+  __nv_bfloat16* z[2] = {nullptr, nullptr};
+  __nv_bfloat16* w0s = nullptr;
+  alignas(64) unsigned char mz[2][128];     // z, box 32 x 256
+  alignas(64) unsigned char mw0[128];       // W_0, box 32 x 128
   alignas(64) unsigned char wmap[128];      // the stacked forward weights, box 32 x 128
   alignas(64) unsigned char rmap[128];      // the reverse-mode weight stack, box 32 x 128
   alignas(64) unsigned char mdd[2][128];    // d_{L-1}, box 32 x 256
