@@ -159,9 +159,10 @@ def make(prob, precision, riccati_f64=False, box_qp=False):
 
 def launches_per_step(ctl, tile_mode=None):
     L = len(ctl.layers) if ctl.layers else 0
-    # network: one fused launch, the layered reverse mode 2 L - 1, the FP32
-    # path L (input, hidden GEMMs, output)
-    mlp = 0 if not L else (L if ctl.precision == "fp32" else 2 * L - 1 if tile_mode == 6 else 1)
+    # network: one fused launch, the layered reverse mode 2 L (inputs, input
+    # GEMM, forward GEMMs, output, backward GEMMs, Jacobian), the FP32 path L
+    # (input, hidden GEMMs, output)
+    mlp = 0 if not L else (L if ctl.precision == "fp32" else 2 * L if tile_mode == 6 else 1)
     return mlp + 1 + 1 + 3  # network, RK4, Riccati, plant + record + advance
 
 
@@ -738,9 +739,10 @@ def main():
         roof = {"bound": "tensor", "peak": bf16_burst, "peak_kind": f"bf16 burst ({peak_src})"}
     roof.update({"achieved": flops / (ms_mlp * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "algorithmic_flops_per_launch": flops, "ms_per_launch": ms_mlp,
-                 "kernel": ("network pass of the layered reverse mode (a1): input layer, one tensor-core GEMM per "
-                            "forward layer, output layer and last-layer adjoints, one GEMM per backward layer, "
-                            "the W_0' Jacobian GEMM (11 launches at 5 hidden layers)" if mode == 6 else
+                 "kernel": ("network pass of the layered reverse mode (a1): inputs split, one tensor-core GEMM per "
+                            "layer forward (input layer included), output layer, one GEMM per backward layer "
+                            "(the first with the last-layer adjoints folded in), the W_0' Jacobian GEMM "
+                            "(12 launches at 5 hidden layers)" if mode == 6 else
                             "network value + reverse-mode Jacobian (a1, three adjoint rows)" if rev
                             else "network value + forward-mode Jacobian (a1)"),
                  "forward_mode_equivalent_tflops": fwd_flops_per_node(widths) * nn / (ms_mlp * 1e-3) / 1e12,

@@ -255,7 +255,7 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
  * in *split (0 single BF16; 1, 2 split hi + lo on one CTA; 3 split on a CTA
  * pair, M = 256; 4 split, reverse mode: values forward, three output
  * adjoints backward; 5 the same on CTA pairs; 6 split, reverse mode layered:
- * one GEMM per layer over all nodes, 2 L - 1 launches, its buffers allocated
+ * one GEMM per layer over all nodes, 2 L launches, its buffers allocated
  * when the shape is first selected) and pipeline depth of shape idx,
  * *fits = 1 if it can run this context's network and precision.  rtn_tc_select: use shape idx
  * (RTN_E_UNSUPPORTED if it does not fit).  rtn_autotune: time every fitting
