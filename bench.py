@@ -542,6 +542,70 @@ def bench_runtime_analysis(steps=200):
     return out
 
 
+LAY_KERNELS = {"input GEMM": "lay_kernel<4>", "forward GEMM": "lay_kernel<0>", "first backward GEMM": "lay_kernel<3>",
+               "backward GEMM": "lay_kernel<1>", "Jacobian GEMM": "lay_kernel<2>", "output layer": "lay_out_kernel",
+               "inputs": "lay_z_kernel"}
+
+
+def lay_flops(kind, widths, nn):
+    """Algorithmic FLOPs of all launches of one kind in a layered pass."""
+    w, L = widths, len(widths) - 1
+    if kind == "input GEMM":
+        return 2 * 17 * w[1] * nn
+    if kind == "forward GEMM":
+        return sum(2 * w[l] * w[l + 1] for l in range(1, L - 1)) * nn
+    if kind == "first backward GEMM":
+        return 2 * 3 * w[L - 2] * w[L - 1] * nn
+    if kind == "backward GEMM":
+        return sum(2 * 3 * w[l] * w[l + 1] for l in range(1, L - 2)) * nn
+    if kind == "Jacobian GEMM":
+        return 2 * 3 * 17 * w[1] * nn
+    return 0
+
+
+def layered_roofline(ctl, x, u, out, widths, nn, pass_roof):
+    """Roofline of the dominant kernel of the layered pass: every launch of
+    one pass timed with CUDA events on the context's stream, the kind with
+    the largest total time, its algorithmic FLOPs per launch over its mean
+    launch time; the pass-level figures kept under "pass"."""
+    ctl.mlp_eval(x, u, out[0], out[1])
+    ctl.tc_launch_times(True)
+    ctl.mlp_eval(x, u, out[0], out[1])
+    times = ctl.tc_launch_times(False)
+    tot = {}
+    for k, ms in times:
+        c, t = tot.get(k, (0, 0.0))
+        tot[k] = (c + 1, t + ms)
+    dom = max((k for k in tot if lay_flops(k, widths, nn) > 0), key=lambda k: tot[k][1])
+    c, t = tot[dom]
+    fl = lay_flops(dom, widths, nn) / c
+    ms = t / c
+    roof = dict(pass_roof)
+    pass_view = {k: pass_roof[k] for k in ("achieved", "frac", "ms_per_launch", "algorithmic_flops_per_launch")}
+    pass_view["kernel"] = pass_roof["kernel"]
+    pass_view["dram_bytes"] = profiled_pass_traffic()
+    roof.update({"kernel": f"{LAY_KERNELS[dom]}: {dom} of the layered reverse mode ({c} per pass, "
+                           f"{100 * t / sum(v[1] for v in tot.values()):.0f}% of the pass)",
+                 "achieved": fl / (ms * 1e-3) / 1e12, "ms_per_launch": ms, "algorithmic_flops_per_launch": fl,
+                 "launches_per_pass": c, "pass": pass_view,
+                 "launch_ms": [[k, round(v, 4)] for k, v in times]})
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return roof
+
+
+def profiled_pass_traffic():
+    """DRAM bytes of a whole layered pass from its committed summary."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "mlp_lay_cfg3_h512_bf16x2.md")).read()
+        m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
+        files = tuple(f.strip() for f in m.group(2).split("+"))
+        if m.group(1) != kernel_md5(files):
+            return None
+        return int(re.search(r"dram_bytes_per_pass: (\d+)", text).group(1))
+    except (OSError, AttributeError):
+        return None
+
+
 def hess_flops_per_node(widths):
     """Second-order (forward-over-forward) algorithmic FLOPs per node: 171
     columns per node (value, 17 tangents, 153 second derivatives) through
@@ -748,6 +812,8 @@ def main():
                  "forward_mode_equivalent_tflops": fwd_flops_per_node(widths) * nn / (ms_mlp * 1e-3) / 1e12,
                  "traffic": profiled_traffic(cfg.get("tile")) if args.config == "cfg3_bf16_precision" else None})
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if mode == 6:
+        roof = layered_roofline(ctl, x, u, out, widths, nn, roof)
     if roof.get("traffic"):
         # what the pass moves through DRAM per launch at the timed rate (the
         # layered shape streams every layer's operands through HBM)

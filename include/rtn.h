@@ -292,6 +292,17 @@ rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms);
 rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable);
 rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n);
 
+/* Per-launch times of the layered reverse mode (tile mode 6; profiling aid).
+ * enable != 0: record a CUDA event around every launch of the following
+ * network passes (not inside a captured graph).  enable == 0: wait for the
+ * last recorded pass, write the duration [ms] of each of its launches to
+ * ms (host float [cap]) and its kind to kind (host int [cap]: 0 inputs
+ * split, 1 input-layer GEMM, 2 forward GEMM, 3 output layer, 4 first
+ * backward GEMM, 5 backward GEMM, 6 Jacobian GEMM), the number of launches
+ * to *count, and stop recording.  Synchronous.  RTN_E_UNSUPPORTED unless the
+ * context's selected tile shape is mode 6. */
+rtn_status rtn_tc_launch_times(rtn_ctx* ctx, int enable, float* ms, int* kind, int cap, int* count);
+
 /* Synchronous: the first device-side failure recorded since the last call
  * (RTN_OK if none), then clears it.  Device-side failures are bounded waits of
  * the tensor-core pipeline that gave up (RTN_E_TIMEOUT); the affected outputs

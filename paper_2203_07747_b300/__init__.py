@@ -27,7 +27,7 @@ EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_rese
            "rtn_mlp_eval_f32_noalloc", "rtn_device_error", "rtn_tc_variants",
            "rtn_tc_variant_info", "rtn_tc_select", "rtn_autotune", "rtn_tc_trace",
            "rtn_tc_trace_read", "rtn_drag_targets", "rtn_mse_grad", "rtn_train",
-           "rtn_get_params", "rtn_box_iterations", "rtn_mlp_hess"]
+           "rtn_get_params", "rtn_box_iterations", "rtn_mlp_hess", "rtn_tc_launch_times"]
 
 _lib = None
 
@@ -81,6 +81,8 @@ def load(build_if_missing=False):
     L.rtn_get_iterate.argtypes = [vp, vp, vp]
     L.rtn_mlp_eval.argtypes = [vp] * 5
     L.rtn_mlp_hess.argtypes = [vp] * 6
+    L.rtn_tc_launch_times.argtypes = [vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), C.c_int,
+                                      C.POINTER(C.c_int)]
     L.rtn_linearize.argtypes = [vp] * 8
     L.rtn_qp_solve.argtypes = [vp] * 12
     L.rtn_rti_step.argtypes = [vp] * 6
@@ -248,6 +250,21 @@ class Controller:
         buf = (C.c_ulonglong * n)()
         self._check(load().rtn_tc_trace_read(self._h, buf, n), "rtn_tc_trace_read")
         return np.frombuffer(buf, dtype=np.uint64).copy()
+
+    LAUNCH_KINDS = ("inputs", "input GEMM", "forward GEMM", "output layer", "first backward GEMM",
+                    "backward GEMM", "Jacobian GEMM")
+
+    def tc_launch_times(self, enable):
+        """Layered reverse mode: enable=True records every launch of the
+        following network passes; enable=False returns [(kind, ms)] of the
+        last recorded pass and stops recording."""
+        if enable:
+            self._check(load().rtn_tc_launch_times(self._h, 1, None, None, 0, None), "rtn_tc_launch_times")
+            return None
+        cap = 64
+        ms, kind, cnt = (C.c_float * cap)(), (C.c_int * cap)(), C.c_int()
+        self._check(load().rtn_tc_launch_times(self._h, 0, ms, kind, cap, C.byref(cnt)), "rtn_tc_launch_times")
+        return [(self.LAUNCH_KINDS[kind[i]], float(ms[i])) for i in range(min(cnt.value, cap))]
 
     # -- learned part (a6) --------------------------------------------------
     def n_params(self):

@@ -629,6 +629,28 @@ rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n) {
   return RTN_OK;
 }
 
+rtn_status rtn_tc_launch_times(rtn_ctx* ctx, int enable, float* ms, int* kind, int cap, int* count) {
+  if (!ctx) return RTN_E_INVAL;
+  if (ctx->di) return di_unsupported(ctx, "rtn_tc_launch_times");
+  if (!ctx->net.tc.lay || ctx->net.tc.variant < 0 || mlp_tc_variant_info(ctx, ctx->net.tc.variant, nullptr, nullptr, nullptr) != 0)
+    return fail(ctx, RTN_E_UNSUPPORTED, "rtn_tc_launch_times: the layered reverse mode is not selected");
+  {
+    int mode = 0;
+    mlp_tc_variant_info(ctx, ctx->net.tc.variant, nullptr, &mode, nullptr);
+    if (mode != 6) return fail(ctx, RTN_E_UNSUPPORTED, "rtn_tc_launch_times: the layered reverse mode is not selected");
+  }
+  if (enable) {
+    CK(mlp_lay_timing(ctx, true));
+    if (count) *count = 0;
+    return RTN_OK;
+  }
+  if (!ms || !kind || !count || cap < 0) return fail(ctx, RTN_E_INVAL, "rtn_tc_launch_times: NULL argument");
+  if (!ctx->net.tc.lay->timing) return fail(ctx, RTN_E_INVAL, "rtn_tc_launch_times: timing is not enabled");
+  CK(mlp_lay_times(ctx, ms, kind, cap, count));
+  CK(mlp_lay_timing(ctx, false));
+  return RTN_OK;
+}
+
 rtn_status rtn_device_error(rtn_ctx* ctx, int* code) {
   if (!ctx || !code) return RTN_E_INVAL;
   if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));

@@ -561,6 +561,7 @@ void mlp_lay_release(rtn_ctx* ctx) {
       if (s->xb[b][p]) cudaFree(s->xb[b][p]);
     }
   if (s->d) cudaFree(s->d);
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->mw) cudaFree(s->mw);
   if (s->w0s) cudaFree(s->w0s);
   for (int p = 0; p < 2; ++p)
@@ -589,11 +590,19 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     return m;
   };
   auto grid_of = [&](long long tiles) { return (int)std::min<long long>(tiles, std::max(1, tc.n_sm)); };
+  // an event before each launch when the pass is timed
+  s->n_marks = 0;
+  auto mark = [&](int kind) {
+    if (!s->timing || s->n_marks >= (int)s->ev.size()) return;
+    cudaEventRecord(s->ev[s->n_marks], st);
+    s->kind[s->n_marks++] = kind;
+  };
   // input layer -> values buffer 0, d_1: z split into BF16 hi + lo, then a
   // GEMM against W_0 hi / lo with the forward epilogue
   const int gf = (n + LY_NF - 1) / LY_NF;
   {
     const long long ne = (long long)n * NZ;
+    mark(0);
     lay_z_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(x, u, ctx->lay.node_inst, n, s->z[0], s->z[1]);
     LyArgs a{};
     a.a_row0 = 0;
@@ -609,6 +618,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.yh = s->xf[0][0];
     a.yl = s->xf[0][1];
     a.err = tc.err;
+    mark(1);
     lay_kernel<LY_IN><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_IN>(), st>>>(
         *reinterpret_cast<const CUtensorMap*>(s->mw0), maps(s->mz[0], s->mz[1]), a);
   }
@@ -632,6 +642,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.yh = s->xf[dst][0];
     a.yl = s->xf[dst][1];
     a.err = tc.err;
+    mark(2);
     lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD>(), st>>>(
         *wmap, maps(s->mf[src][0], s->mf[src][1]), a);
   }
@@ -640,6 +651,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
   {
     const int last = nh & 1;
     const long long warps = n;
+    mark(3);
     lay_out_kernel<<<(int)std::min<long long>((warps + 7) / 8, 148LL * 64), 256, 0, st>>>(
         tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs, s->xf[last][0], s->xf[last][1],
         s->d + (size_t)(L - 2) * dstride, fD, nh >= 1 ? nullptr : s->xb[0][0], s->xb[0][1], HP);
@@ -664,6 +676,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     LyMaps m;
     memcpy(&m.bh, s->mdd[0], sizeof(CUtensorMap));
     memcpy(&m.bl, s->mdd[1], sizeof(CUtensorMap));
+    mark(4);
     lay_kernel<LY_BW0><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_BW0>(), st>>>(
         *reinterpret_cast<const CUtensorMap*>(s->mmap), m, a);
   }
@@ -684,6 +697,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.yh = s->xb[dst][0];
     a.yl = s->xb[dst][1];
     a.err = tc.err;
+    mark(5);
     lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD>(), st>>>(
         *rmap, maps(s->mb[src][0], s->mb[src][1]), a);
   }
@@ -701,10 +715,42 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.hs = hs;
     a.JD = JD;
     a.err = tc.err;
+    mark(6);
     lay_kernel<LY_JD><<<grid_of(gb), LY_THREADS, ly_smem<LY_JD>(), st>>>(*rmap, maps(s->mb[src][0], s->mb[src][1]),
                                                                           a);
   }
+  if (s->timing && s->n_marks < (int)s->ev.size()) cudaEventRecord(s->ev[s->n_marks], st);
   return cudaGetLastError();
+}
+
+cudaError_t mlp_lay_timing(rtn_ctx* ctx, bool enable) {
+  LayState* s = ctx->net.tc.lay;
+  if (!s) return cudaErrorInvalidValue;
+  if (enable && s->ev.empty()) {
+    const int n_ev = 2 * ctx->net.n_layers + 2;  // 2 L launches and the end
+    s->ev.resize(n_ev);
+    s->kind.assign(n_ev, -1);
+    for (auto& e : s->ev) {
+      const cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+    }
+  }
+  s->timing = enable;
+  s->n_marks = 0;
+  return cudaSuccess;
+}
+
+cudaError_t mlp_lay_times(rtn_ctx* ctx, float* ms, int* kind, int cap, int* count) {
+  LayState* s = ctx->net.tc.lay;
+  if (!s || s->ev.empty()) return cudaErrorInvalidValue;
+  const int n = s->n_marks;
+  cudaError_t e = cudaEventSynchronize(s->ev[n]);
+  for (int i = 0; i < n && i < cap && e == cudaSuccess; ++i) {
+    e = cudaEventElapsedTime(ms + i, s->ev[i], s->ev[i + 1]);
+    kind[i] = s->kind[i];
+  }
+  *count = n;
+  return e;
 }
 
 }  // namespace rtn

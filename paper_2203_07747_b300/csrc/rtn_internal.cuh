@@ -64,6 +64,12 @@ struct LayState {
   __nv_bfloat16* w0s = nullptr;
   alignas(64) unsigned char mz[2][128];     // z, box 32 x 256
   alignas(64) unsigned char mw0[128];       // W_0, box 32 x 128
+  // per-launch timing of a pass (rtn_tc_launch_times): an event before
+  // every launch and after the last, and each launch's kind
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  int n_marks = 0;
   alignas(64) unsigned char wmap[128];      // the stacked forward weights, box 32 x 128
   alignas(64) unsigned char rmap[128];      // the reverse-mode weight stack, box 32 x 128
   alignas(64) unsigned char mdd[2][128];    // d_{L-1}, box 32 x 256
@@ -246,6 +252,11 @@ size_t mlp_lay_smem();
 cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err);
 void mlp_lay_release(rtn_ctx* ctx);
 cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+// per-launch times of the last timed pass [ms] and kinds (0 inputs, 1 input
+// GEMM, 2 forward GEMM, 3 output layer, 4 first backward GEMM, 5 backward
+// GEMM, 6 Jacobian GEMM); returns the number of launches
+cudaError_t mlp_lay_timing(rtn_ctx* ctx, bool enable);
+cudaError_t mlp_lay_times(rtn_ctx* ctx, float* ms, int* kind, int cap, int* count);
 
 // a2
 cudaError_t rk4_sens(rtn_ctx* ctx, const float* x, const float* u, const float* fD,
