@@ -543,7 +543,7 @@ def bench_runtime_analysis(steps=200):
 
 
 LAY_KERNELS = {"input GEMM": "lay_kernel<4>", "forward GEMM": "lay_kernel<0>", "first backward GEMM": "lay_kernel<3>",
-               "backward GEMM": "lay_kernel<1>", "Jacobian GEMM": "lay_kernel<2>", "output layer": "lay_out_kernel",
+               "backward GEMM": "lay_kernel<1>", "Jacobian GEMM": "lay_kernel<2>", "output layer": "lay_fd_kernel",
                "inputs": "lay_z_kernel"}
 
 
@@ -563,11 +563,38 @@ def lay_flops(kind, widths, nn):
     return 0
 
 
-def layered_roofline(ctl, x, u, out, widths, nn, pass_roof):
+def lay_bytes(kind, widths, nn):
+    """Algorithmic DRAM bytes of all launches of one kind in a layered pass:
+    every operand a layer GEMM reads and every result it writes, once, 4 B
+    per value (FP32, or a BF16 hi + lo pair); weights (L2-resident) and the
+    zero padding of z are not counted."""
+    w, L = widths, len(widths) - 1
+    if kind == "inputs":
+        return (17 * 4 + 17 * 4) * nn
+    if kind == "input GEMM":
+        return (17 + 2 * w[1]) * 4 * nn
+    if kind == "forward GEMM":
+        return sum((w[l] + 2 * w[l + 1]) * 4 for l in range(1, L - 1)) * nn
+    if kind == "output layer":
+        return (w[L - 1] + 3) * 4 * nn
+    if kind == "first backward GEMM":
+        return (w[L - 1] + w[L - 2] + 3 * w[L - 2]) * 4 * nn
+    if kind == "backward GEMM":
+        return sum((3 * w[l + 1] + w[l] + 3 * w[l]) * 4 for l in range(1, L - 2)) * nn
+    if kind == "Jacobian GEMM":
+        return (3 * w[1] + 3 * 17) * 4 * nn
+    return 0
+
+
+def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, peak_src):
     """Roofline of the dominant kernel of the layered pass: every launch of
     one pass timed with CUDA events on the context's stream, the kind with
-    the largest total time, its algorithmic FLOPs per launch over its mean
-    launch time; the pass-level figures kept under "pass"."""
+    the largest total time, against HBM: each layer GEMM moves its operands
+    and results through DRAM at an arithmetic intensity (~110 FLOP/B for a
+    512-wide backward layer) below the BF16 ridge point (peak FLOP/s over
+    HBM bytes/s, ~270 FLOP/B), so its bound is bytes.  Its algorithmic bytes
+    per launch over its mean launch time, the tensor-core view beside it;
+    the pass-level figures kept under "pass"."""
     ctl.mlp_eval(x, u, out[0], out[1])
     ctl.tc_launch_times(True)
     ctl.mlp_eval(x, u, out[0], out[1])
@@ -579,18 +606,24 @@ def layered_roofline(ctl, x, u, out, widths, nn, pass_roof):
     dom = max((k for k in tot if lay_flops(k, widths, nn) > 0), key=lambda k: tot[k][1])
     c, t = tot[dom]
     fl = lay_flops(dom, widths, nn) / c
+    by = lay_bytes(dom, widths, nn) / c
     ms = t / c
-    roof = dict(pass_roof)
-    pass_view = {k: pass_roof[k] for k in ("achieved", "frac", "ms_per_launch", "algorithmic_flops_per_launch")}
+    pass_view = {k: pass_roof[k] for k in ("achieved", "unit", "frac", "ms_per_launch",
+                                           "algorithmic_flops_per_launch", "peak", "peak_kind")}
     pass_view["kernel"] = pass_roof["kernel"]
     pass_view["dram_bytes"] = profiled_pass_traffic()
-    roof.update({"kernel": f"{LAY_KERNELS[dom]}: {dom} of the layered reverse mode ({c} per pass, "
-                           f"{100 * t / sum(v[1] for v in tot.values()):.0f}% of the pass)",
-                 "achieved": fl / (ms * 1e-3) / 1e12, "ms_per_launch": ms, "algorithmic_flops_per_launch": fl,
-                 "launches_per_pass": c, "pass": pass_view,
-                 "launch_ms": [[k, round(v, 4)] for k, v in times]})
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    return roof
+    pass_view["algorithmic_bytes"] = sum(lay_bytes(k, widths, nn) for k in tot)
+    achieved = by / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "peak": hbm, "peak_kind": f"HBM copy ({peak_src})", "unit": "GB/s",
+            "achieved": achieved, "frac": achieved / hbm, "traffic": pass_roof.get("traffic"),
+            "algorithmic_bytes_per_launch": by, "ms_per_launch": ms, "launches_per_pass": c,
+            "kernel": f"{LAY_KERNELS[dom]}: {dom} of the layered reverse mode ({c} per pass, "
+                      f"{100 * t / sum(v[1] for v in tot.values()):.0f}% of the pass)",
+            "arithmetic_intensity_flop_per_byte": fl / by, "ridge_flop_per_byte": bf16_burst * 1e12 / (hbm * 1e9),
+            "tensor_view": {"achieved_tflops": fl / (ms * 1e-3) / 1e12, "frac_of_bf16_burst": fl / (ms * 1e-3) / 1e12
+                            / bf16_burst, "algorithmic_flops_per_launch": fl},
+            "pass": pass_view,
+            "launch_ms": [[k, round(v, 4)] for k, v in times]}
 
 
 def profiled_pass_traffic():
@@ -813,8 +846,8 @@ def main():
                  "traffic": profiled_traffic(cfg.get("tile")) if args.config == "cfg3_bf16_precision" else None})
     roof["frac"] = roof["achieved"] / roof["peak"]
     if mode == 6:
-        roof = layered_roofline(ctl, x, u, out, widths, nn, roof)
-    if roof.get("traffic"):
+        roof = layered_roofline(ctl, x, u, out, widths, nn, roof, hbm, bf16_burst, peak_src)
+    elif roof.get("traffic"):
         # what the pass moves through DRAM per launch at the timed rate (the
         # layered shape streams every layer's operands through HBM)
         roof["dram_tbs_at_traffic"] = roof["traffic"] / (ms_mlp * 1e-3) / 1e12

@@ -5,15 +5,17 @@
 // all layers inside one CTA (pair), so each GEMM waits for the previous
 // layer's epilogue.  Here every layer is one GEMM over all nodes, its
 // activations passing through HBM/L2:
-//   input      a_1 = tanh(W_0 z + b_0), d_1 = 1 - a_1^2          (tcgen05, K = 17 -> 32)
-//   forward    a_{l+1} = tanh(W_l a_l + b_l), d_{l+1}             (tcgen05)
+//   input      a_1 = tanh(W_0 z + b_0)                           (tcgen05, K = 17 -> 32)
+//   forward    a_{l+1} = tanh(W_l a_l + b_l)                     (tcgen05)
 //   output     f_D = W_L a_L + b_L                               (SIMT)
 //   adjoints   D_L = d_L (.) W_L' (three columns per node)       (SIMT)
-//   backward   D_l = d_l (.) (W_l' D_{l+1})                      (tcgen05)
+//   backward   D_l = d_l (.) (W_l' D_{l+1}), d_l = 1 - a_l^2     (tcgen05)
 //   Jacobian   J_D = W_0' D_1                                    (tcgen05)
 // with the split-BF16 arithmetic of the fused kernels: BF16 weights (W_0'
 // split hi + lo), activations and adjoints stored as BF16 hi + lo pairs (two
-// MMAs per K step, FP32 accumulation), d_l in FP32.  Layout: node-major rows,
+// MMAs per K step, FP32 accumulation).  Every layer's activations are kept
+// and d_l is recomputed from them in the backward epilogues (a stored d_l
+// would be one more write of every layer).  Layout: node-major rows,
 // X [node][hs] for values, [node * 3 + r][hs] for adjoints, so both operands
 // are K-major TMA tiles (128 B swizzle) and an epilogue lane (one neuron)
 // stores consecutive neurons of a node across the warp.
@@ -72,6 +74,7 @@ struct LyMaps {
 
 struct LyArgs {
   int a_row0;     // weight row of M tile 0 in the stacked weights
+  int b_row0;     // FWD: first row of the source layer in the stacked activations
   int a_lo;       // JD: row offset of the lo weights
   int m_rows;     // real output rows
   int mts;        // M tiles
@@ -79,10 +82,10 @@ struct LyArgs {
   int nkb;        // K blocks
   int n_nodes, n_groups, hs;
   const float* bias;   // FWD: bias of the produced layer
-  float* d_out;        // FWD: d of the produced layer [node][hs] (FP32), or
-  __nv_bfloat16* dh;   //      into dh / dl as BF16 hi + lo when dh is set
-  __nv_bfloat16* dl;
-  const float* d_in;   // BWD: d of the adjoint's layer [node][hs]
+  __nv_bfloat16* dh;   // FWD, last hidden layer: its d as BF16 hi + lo (the
+  __nv_bfloat16* dl;   //      B operand of the folded first backward GEMM)
+  const __nv_bfloat16* ah;  // BW0 / BWD: a_l of the adjoint's layer [node][hs]
+  const __nv_bfloat16* al;  //            hi / lo, d_l = 1 - a_l^2
   __nv_bfloat16* yh;   // FWD / BWD outputs
   __nv_bfloat16* yl;
   float* JD;           // JD output [node][3][17]
@@ -94,16 +97,24 @@ __device__ __forceinline__ void split_bf(float v, __nv_bfloat16& h, __nv_bfloat1
   l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// d_l = 1 - a_l^2 of node row o from the stored activation pair
+__device__ __forceinline__ float d_of(const __nv_bfloat16* __restrict__ ah, const __nv_bfloat16* __restrict__ al,
+                                     size_t o) {
+  const float av = __bfloat162float(ah[o]) + __bfloat162float(al[o]);
+  return 1.0f - av * av;
+}
+
 // backward epilogue of one 16-node group (48 accumulator columns, node k
 // in columns 3k .. 3k + 2): the warp of half H stores nodes 8H .. 8H + 7,
-// D = acc * d with d loaded once per node
+// D = acc * d with d computed once per node
 template <int H>
-__device__ __forceinline__ void bwd_group(const float (&v)[48], const float* __restrict__ d_in, int node_g,
-                                          int n_nodes, int hs, int i, int ic, bool active,
-                                          __nv_bfloat16* __restrict__ yh, __nv_bfloat16* __restrict__ yl) {
+__device__ __forceinline__ void bwd_group(const float (&v)[48], const __nv_bfloat16* __restrict__ ah,
+                                          const __nv_bfloat16* __restrict__ al, int node_g, int n_nodes, int hs,
+                                          int i, int ic, bool active, __nv_bfloat16* __restrict__ yh,
+                                          __nv_bfloat16* __restrict__ yl) {
   float dv[8];
 #pragma unroll
-  for (int kk = 0; kk < 8; ++kk) dv[kk] = __ldg(d_in + (size_t)min(node_g + 8 * H + kk, n_nodes - 1) * hs + ic);
+  for (int kk = 0; kk < 8; ++kk) dv[kk] = d_of(ah, al, (size_t)min(node_g + 8 * H + kk, n_nodes - 1) * hs + ic);
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
     const int k = 8 * H + kk, node = node_g + k;
@@ -190,8 +201,8 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
           tma_load_2d(sa, &amap, kb * LY_KB, a.a_row0 + mt * 128, full_bar(s));
           if (T::NA == 2)
             tma_load_2d(sa + LY_A_BYTES, &amap, kb * LY_KB, a.a_row0 + a.a_lo + mt * 128, full_bar(s));
-          tma_load_2d(sa + B0, &bm.bh, kb * LY_KB, grp * T::N, full_bar(s));
-          tma_load_2d(sa + B0 + B_BYTES, &bm.bl, kb * LY_KB, grp * T::N, full_bar(s));
+          tma_load_2d(sa + B0, &bm.bh, kb * LY_KB, a.b_row0 + grp * T::N, full_bar(s));
+          tma_load_2d(sa + B0 + B_BYTES, &bm.bl, kb * LY_KB, a.b_row0 + grp * T::N, full_bar(s));
         }
         __syncwarp();
         issued |= 1u << s;
@@ -269,9 +280,9 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
           tmem_ld16(taddr + 48 * g + 32, v + 32);
           tmem_wait_ld();
           if (half == 0)
-            bwd_group<0>(v, a.d_in, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
+            bwd_group<0>(v, a.ah, a.al, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
           else
-            bwd_group<1>(v, a.d_in, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
+            bwd_group<1>(v, a.ah, a.al, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
         }
       }
       for (int ch = half; MODE != LY_BWD && ch < T::N / 16; ch += 2) {
@@ -293,8 +304,6 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
                 split_bf(1.0f - av[k] * av[k], h, l);
                 a.dh[o] = h;
                 a.dl[o] = l;
-              } else {
-                a.d_out[o] = 1.0f - av[k] * av[k];
               }
               split_bf(av[k], h, l);
               a.yh[o] = h;
@@ -305,8 +314,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
           // D_{L-2}[node * 3 + r][i] = acc * d_{L-2}[node][i], loads first
           float dv[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k)
-            dv[k] = __ldg(a.d_in + (size_t)min(node0 + 16 * ch + k, a.n_nodes - 1) * a.hs + ic);
+          for (int k = 0; k < 16; ++k) dv[k] = d_of(a.ah, a.al, (size_t)min(node0 + 16 * ch + k, a.n_nodes - 1) * a.hs + ic);
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int node = node0 + 16 * ch + k;
@@ -357,11 +365,12 @@ __global__ void __launch_bounds__(256) lay_z_kernel(const float* __restrict__ x,
 }
 
 // output layer f_D = W_L a_L + b_L (warp per node) and the last layer's
-// adjoints D_L[node * 3 + r][i] = d_L[i] W_L[r][i] (split hi + lo)
+// adjoints D_L[node * 3 + r][i] = d_L[i] W_L[r][i] (split hi + lo), for a
+// network with no hidden -> hidden layer or a last width that is not a
+// multiple of 8
 __global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ WL, const float* __restrict__ bL,
                                                       int h, int n_nodes, int hs, const __nv_bfloat16* __restrict__ xh,
-                                                      const __nv_bfloat16* __restrict__ xl,
-                                                      const float* __restrict__ dL, float* __restrict__ fD,
+                                                      const __nv_bfloat16* __restrict__ xl, float* __restrict__ fD,
                                                       __nv_bfloat16* __restrict__ Dh, __nv_bfloat16* __restrict__ Dl,
                                                       int HP) {
   const int lane = threadIdx.x & 31;
@@ -376,7 +385,7 @@ __global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ 
       for (int t = 0; t < 4; ++t) {
         const int i = min(i0 + 32 * t, h - 1);
         av[t] = __bfloat162float(xh[row + i]) + __bfloat162float(xl[row + i]);
-        dv[t] = Dh ? dL[row + i] : 0.0f;
+        dv[t] = 1.0f - av[t] * av[t];
         w0[t] = __ldg(WL + i);
         w1[t] = __ldg(WL + HP + i);
         w2[t] = __ldg(WL + 2 * HP + i);
@@ -416,6 +425,63 @@ __global__ void __launch_bounds__(256) lay_out_kernel(const float* __restrict__ 
   }
 }
 
+// output layer f_D = W_L a_L + b_L with no adjoints (h <= 512, h % 8 == 0):
+// a warp per node, each lane reading 8 consecutive neurons of a_L hi and lo
+// as one 16 B load each, both steps' loads issued before the arithmetic
+__global__ void __launch_bounds__(256) lay_fd_kernel(const float* __restrict__ WL, const float* __restrict__ bL,
+                                                     int h, int n_nodes, int hs,
+                                                     const __nv_bfloat16* __restrict__ xh,
+                                                     const __nv_bfloat16* __restrict__ xl, float* __restrict__ fD,
+                                                     int HP) {
+  const int lane = threadIdx.x & 31;
+  for (long long node = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; node < n_nodes;
+       node += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const size_t row = (size_t)node * hs;
+    uint4 ph[2], pl[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int c = lane * 8 + 256 * k;
+      if (c < h) {
+        ph[k] = __ldg(reinterpret_cast<const uint4*>(xh + row + c));
+        pl[k] = __ldg(reinterpret_cast<const uint4*>(xl + row + c));
+      }
+    }
+    float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int c = lane * 8 + 256 * k;
+      if (c >= h) break;
+      const __nv_bfloat16* eh = reinterpret_cast<const __nv_bfloat16*>(&ph[k]);
+      const __nv_bfloat16* el = reinterpret_cast<const __nv_bfloat16*>(&pl[k]);
+      float av[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) av[t] = __bfloat162float(eh[t]) + __bfloat162float(el[t]);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float4 w0 = __ldg(reinterpret_cast<const float4*>(WL + (size_t)r * HP + c));
+        const float4 w1 = __ldg(reinterpret_cast<const float4*>(WL + (size_t)r * HP + c + 4));
+        float v = f[r];
+        v = fmaf(w0.x, av[0], v);
+        v = fmaf(w0.y, av[1], v);
+        v = fmaf(w0.z, av[2], v);
+        v = fmaf(w0.w, av[3], v);
+        v = fmaf(w1.x, av[4], v);
+        v = fmaf(w1.y, av[5], v);
+        v = fmaf(w1.z, av[6], v);
+        v = fmaf(w1.w, av[7], v);
+        f[r] = v;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) f[r] += __shfl_xor_sync(0xffffffffu, f[r], o);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) fD[node * NO + r] = f[r] + bL[r];
+  }
+}
+
 }  // namespace
 
 const void* mlp_lay_fn() { return reinterpret_cast<const void*>(&lay_kernel<LY_FWD>); }
@@ -427,7 +493,7 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   Net& net = ctx->net;
   const int L = net.n_layers, n = ctx->lay.n_nodes, HP = tc.h_pad;
   const long long npad = ((long long)n + LY_NODE_PAD - 1) / LY_NODE_PAD * LY_NODE_PAD;
-  if (3 * npad >= (1LL << 31)) {
+  if (3 * npad >= (1LL << 31) || (long long)(L - 1) * npad >= (1LL << 31)) {
     err = "layered reverse mode: more nodes than the 32-bit tensor coordinates address";
     return cudaSuccess;
   }
@@ -439,12 +505,14 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   cudaError_t e;
   for (int b = 0; b < 2; ++b)
     for (int p = 0; p < 2; ++p) {
-      if ((e = cudaMalloc(&s->xf[b][p], (size_t)npad * HP * 2)) != cudaSuccess) return e;
-      if ((e = cudaMemset(s->xf[b][p], 0, (size_t)npad * HP * 2)) != cudaSuccess) return e;
       if ((e = cudaMalloc(&s->xb[b][p], (size_t)3 * npad * HP * 2)) != cudaSuccess) return e;
       if ((e = cudaMemset(s->xb[b][p], 0, (size_t)3 * npad * HP * 2)) != cudaSuccess) return e;
     }
-  if ((e = cudaMalloc(&s->d, (size_t)(L - 1) * npad * HP * 4)) != cudaSuccess) return e;
+  for (int p = 0; p < 2; ++p) {
+    const size_t bytes = (size_t)(L - 1) * npad * HP * 2;
+    if ((e = cudaMalloc(&s->act[p], bytes)) != cudaSuccess) return e;
+    if ((e = cudaMemset(s->act[p], 0, bytes)) != cudaSuccess) return e;
+  }
   for (int p = 0; p < 2; ++p) {
     if ((e = cudaMalloc(&s->z[p], (size_t)npad * LY_KB * 2)) != cudaSuccess) return e;
     if ((e = cudaMemset(s->z[p], 0, (size_t)npad * LY_KB * 2)) != cudaSuccess) return e;
@@ -518,12 +586,17 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
                                 (int)ly_smem<LY_IN>())) != cudaSuccess)
     return e;
 
-  // maps of each buffer: forward tiles read values (box 256 rows), backward
-  // and Jacobian tiles read adjoints (box 240 rows); no box reaches past its
-  // tensor (rows padded to a multiple of both tiles)
+  // maps: forward tiles read the stacked activations (box 256 rows),
+  // backward and Jacobian tiles read adjoints (box 240 rows); no box reaches
+  // past its layer (rows padded to a multiple of both tiles)
+  for (int p = 0; p < 2; ++p)
+    if (!enc(s->ma[p], s->act[p], (long long)(L - 1) * npad, LY_NF)) {
+      err = "cuTensorMapEncodeTiled failed";
+      return cudaSuccess;
+    }
   for (int b = 0; b < 2; ++b)
     for (int p = 0; p < 2; ++p) {
-      if (!enc(s->mf[b][p], s->xf[b][p], npad, LY_NF) || !enc(s->mb[b][p], s->xb[b][p], 3 * npad, 3 * LY_NBN)) {
+      if (!enc(s->mb[b][p], s->xb[b][p], 3 * npad, 3 * LY_NBN)) {
         err = "cuTensorMapEncodeTiled failed";
         return cudaSuccess;
       }
@@ -556,11 +629,10 @@ void mlp_lay_release(rtn_ctx* ctx) {
   LayState* s = ctx->net.tc.lay;
   if (!s) return;
   for (int b = 0; b < 2; ++b)
-    for (int p = 0; p < 2; ++p) {
-      if (s->xf[b][p]) cudaFree(s->xf[b][p]);
+    for (int p = 0; p < 2; ++p)
       if (s->xb[b][p]) cudaFree(s->xb[b][p]);
-    }
-  if (s->d) cudaFree(s->d);
+  for (int p = 0; p < 2; ++p)
+    if (s->act[p]) cudaFree(s->act[p]);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->mw) cudaFree(s->mw);
   if (s->w0s) cudaFree(s->w0s);
@@ -614,17 +686,16 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.n_groups = gf;
     a.hs = hs;
     a.bias = tc.b0;
-    a.d_out = s->d;
-    a.yh = s->xf[0][0];
-    a.yl = s->xf[0][1];
+    a.yh = s->act[0];
+    a.yl = s->act[1];
     a.err = tc.err;
     mark(1);
     lay_kernel<LY_IN><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_IN>(), st>>>(
         *reinterpret_cast<const CUtensorMap*>(s->mw0), maps(s->mz[0], s->mz[1]), a);
   }
-  // forward hidden layers: GEMM g reads buffer g % 2, writes the other and d_{g+2}
+  // forward hidden layers: GEMM g reads a_{g+1}, writes a_{g+2}
   for (int g = 0; g < nh; ++g) {
-    const int src = g & 1, dst = src ^ 1, ho = net.widths[g + 2];
+    const int ho = net.widths[g + 2];
     LyArgs a{};
     a.a_row0 = g * HP;
     a.m_rows = ho;
@@ -634,27 +705,32 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.n_groups = gf;
     a.hs = hs;
     a.bias = tc.bias + (size_t)g * HP;
-    a.d_out = s->d + (size_t)(g + 1) * dstride;
+    a.b_row0 = g * s->npad;
     if (g == nh - 1) {  // d_{L-1}: the B operand of the folded first backward GEMM
       a.dh = s->dd[0];
       a.dl = s->dd[1];
     }
-    a.yh = s->xf[dst][0];
-    a.yl = s->xf[dst][1];
+    a.yh = s->act[0] + (size_t)(g + 1) * dstride;
+    a.yl = s->act[1] + (size_t)(g + 1) * dstride;
     a.err = tc.err;
     mark(2);
     lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD>(), st>>>(
-        *wmap, maps(s->mf[src][0], s->mf[src][1]), a);
+        *wmap, maps(s->ma[0], s->ma[1]), a);
   }
   // f_D (and, with no hidden->hidden layer, the last layer's adjoints into
   // adjoint buffer 0)
   {
-    const int last = nh & 1;
+    const __nv_bfloat16* aLh = s->act[0] + (size_t)(L - 2) * dstride;
+    const __nv_bfloat16* aLl = s->act[1] + (size_t)(L - 2) * dstride;
     const long long warps = n;
+    const int blocks = (int)std::min<long long>((warps + 7) / 8, 148LL * 64);
     mark(3);
-    lay_out_kernel<<<(int)std::min<long long>((warps + 7) / 8, 148LL * 64), 256, 0, st>>>(
-        tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs, s->xf[last][0], s->xf[last][1],
-        s->d + (size_t)(L - 2) * dstride, fD, nh >= 1 ? nullptr : s->xb[0][0], s->xb[0][1], HP);
+    if (nh >= 1 && net.widths[L - 1] % 8 == 0)
+      lay_fd_kernel<<<blocks, 256, 0, st>>>(tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs, aLh, aLl,
+                                            fD, HP);
+    else
+      lay_out_kernel<<<blocks, 256, 0, st>>>(tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs, aLh, aLl,
+                                             fD, nh >= 1 ? nullptr : s->xb[0][0], s->xb[0][1], HP);
   }
   // first backward layer with the last layer's adjoints folded in:
   // D_{L-2}[n, r] = d_{L-2} (.) (M_r d_{L-1}[n]) -> adjoint buffer 0
@@ -669,7 +745,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.n_nodes = n;
     a.n_groups = gf;
     a.hs = hs;
-    a.d_in = s->d + (size_t)(L - 3) * dstride;
+    a.ah = s->act[0] + (size_t)(L - 3) * dstride;
+    a.al = s->act[1] + (size_t)(L - 3) * dstride;
     a.yh = s->xb[0][0];
     a.yl = s->xb[0][1];
     a.err = tc.err;
@@ -693,7 +770,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.n_nodes = n;
     a.n_groups = gb;
     a.hs = hs;
-    a.d_in = s->d + (size_t)(l - 1) * dstride;
+    a.ah = s->act[0] + (size_t)(l - 1) * dstride;
+    a.al = s->act[1] + (size_t)(l - 1) * dstride;
     a.yh = s->xb[dst][0];
     a.yl = s->xb[dst][1];
     a.err = tc.err;

@@ -48,10 +48,11 @@ struct Layout {
 // layer [L-1][npad][hs] in FP32, tensor maps of every buffer.
 struct LayState {
   int hs = 0, npad = 0;
-  __nv_bfloat16* xf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // activations a_1 .. a_{L-1} as BF16 hi (0) and lo (1), layer l at rows
+  // (l - 1) npad; the backward epilogues recompute d_l = 1 - a_l^2 from them
+  __nv_bfloat16* act[2] = {nullptr, nullptr};
   __nv_bfloat16* xb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  float* d = nullptr;
-  alignas(64) unsigned char mf[2][2][128];  // values, box 32 x 256
+  alignas(64) unsigned char ma[2][128];     // activations hi / lo, box 32 x 256
   alignas(64) unsigned char mb[2][2][128];  // adjoints, box 32 x 240
   // folded first backward layer: M_r = W_{L-2}' diag(W_L[r]) as BF16 hi rows
   // [3 HP][HP] then lo rows, and d_{L-1} as BF16 hi + lo [npad][hs]
