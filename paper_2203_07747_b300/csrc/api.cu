@@ -292,6 +292,13 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     qp.d = (float)(quad->arm / std::sqrt(2.0)); qp.c_tau = (float)quad->c_tau;
     qp.u_max = (float)quad->u_max; qp.g = (float)quad->g;
     qp.hover = (float)(quad->mass * quad->g / 4.0);
+    {
+      const double d = quad->arm / std::sqrt(2.0);
+      qp.tq[0] = (float)(d / quad->Jx); qp.tq[1] = (float)(d / quad->Jy); qp.tq[2] = (float)(quad->c_tau / quad->Jz);
+      qp.gy[0] = (float)((quad->Jz - quad->Jy) / quad->Jx);
+      qp.gy[1] = (float)((quad->Jx - quad->Jz) / quad->Jy);
+      qp.gy[2] = (float)((quad->Jy - quad->Jx) / quad->Jz);
+    }
     for (int i = 0; i < NX; ++i) { ctx->cost.Q[i] = Q[i]; ctx->cost.QN[i] = Q_N ? Q_N[i] : Q[i]; }
     for (int i = 0; i < NU; ++i) ctx->cost.R[i] = R[i];
 

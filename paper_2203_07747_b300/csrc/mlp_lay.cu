@@ -97,24 +97,46 @@ __device__ __forceinline__ void split_bf(float v, __nv_bfloat16& h, __nv_bfloat1
   l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// d_l = 1 - a_l^2 of node row o from the stored activation pair
-__device__ __forceinline__ float d_of(const __nv_bfloat16* __restrict__ ah, const __nv_bfloat16* __restrict__ al,
-                                     size_t o) {
-  const float av = __bfloat162float(ah[o]) + __bfloat162float(al[o]);
-  return 1.0f - av * av;
+// the activation pairs a_l[node][ic] of the 8 nodes that the warp of half H
+// stores in the 16-node group starting at node_g
+template <int H>
+__device__ __forceinline__ void bwd_load(const __nv_bfloat16* __restrict__ ah, const __nv_bfloat16* __restrict__ al,
+                                         int node_g, int n_nodes, int hs, int ic, __nv_bfloat16 (&ph)[8],
+                                         __nv_bfloat16 (&pl)[8]) {
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const size_t o = (size_t)min(node_g + 8 * H + kk, n_nodes - 1) * hs + ic;
+    ph[kk] = ah[o];
+    pl[kk] = al[o];
+  }
+}
+
+// the activation pairs a_l[node][ic] of the 16 nodes of one chunk
+__device__ __forceinline__ void chunk_load(const __nv_bfloat16* __restrict__ ah, const __nv_bfloat16* __restrict__ al,
+                                           int node_c, int n_nodes, int hs, int ic, __nv_bfloat16 (&ph)[16],
+                                           __nv_bfloat16 (&pl)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const size_t o = (size_t)min(node_c + k, n_nodes - 1) * hs + ic;
+    ph[k] = ah[o];
+    pl[k] = al[o];
+  }
 }
 
 // backward epilogue of one 16-node group (48 accumulator columns, node k
 // in columns 3k .. 3k + 2): the warp of half H stores nodes 8H .. 8H + 7,
-// D = acc * d with d computed once per node
+// D = acc * d with d = 1 - a^2 computed once per node from the loaded pairs
 template <int H>
-__device__ __forceinline__ void bwd_group(const float (&v)[48], const __nv_bfloat16* __restrict__ ah,
-                                          const __nv_bfloat16* __restrict__ al, int node_g, int n_nodes, int hs,
-                                          int i, int ic, bool active, __nv_bfloat16* __restrict__ yh,
+__device__ __forceinline__ void bwd_group(const float (&v)[48], const __nv_bfloat16 (&ph)[8],
+                                          const __nv_bfloat16 (&pl)[8], int node_g, int n_nodes, int hs, int i,
+                                          bool active, __nv_bfloat16* __restrict__ yh,
                                           __nv_bfloat16* __restrict__ yl) {
   float dv[8];
 #pragma unroll
-  for (int kk = 0; kk < 8; ++kk) dv[kk] = d_of(ah, al, (size_t)min(node_g + 8 * H + kk, n_nodes - 1) * hs + ic);
+  for (int kk = 0; kk < 8; ++kk) {
+    const float av = __bfloat162float(ph[kk]) + __bfloat162float(pl[kk]);
+    dv[kk] = 1.0f - av * av;
+  }
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
     const int k = 8 * H + kk, node = node_g + k;
@@ -260,8 +282,6 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
     uint32_t aph = 0;
     for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
       const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
-      if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err)) break;
-      tc_fence_after();
       // output row i (BW0: row k of component r)
       const int r0 = MODE == LY_BW0 ? mt / a.mtpr : 0;
       const int i = (MODE == LY_BW0 ? mt % a.mtpr : mt) * 128 + q * 32 + lane;
@@ -269,25 +289,55 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       const int ic = active ? i : 0;  // a row that exists, for the loads
       const int node0 = grp * T::NODES;
       const float bi = T::ACT ? __ldg(a.bias + ic) : 0.0f;
+      // backward: the first group's activations are loaded while the
+      // accumulator is still being computed, each later group's while the
+      // one before it is stored
+      __nv_bfloat16 ph[8], pl[8], qh[16], ql[16];
+      if (MODE == LY_BWD) {
+        if (half == 0)
+          bwd_load<0>(a.ah, a.al, node0, a.n_nodes, a.hs, ic, ph, pl);
+        else
+          bwd_load<1>(a.ah, a.al, node0, a.n_nodes, a.hs, ic, ph, pl);
+      }
+      if (MODE == LY_BW0) chunk_load(a.ah, a.al, node0 + 16 * half, a.n_nodes, a.hs, ic, qh, ql);
+      if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err)) break;
+      tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
       if (MODE == LY_BWD) {
         // 16-node groups: both warps of the quarter read the group's 48
         // columns, each stores its 8 nodes
+#pragma unroll
         for (int g = 0; g < T::NODES / 16; ++g) {
           float v[48];
           tmem_ld16(taddr + 48 * g, v);
           tmem_ld16(taddr + 48 * g + 16, v + 16);
           tmem_ld16(taddr + 48 * g + 32, v + 32);
+          __nv_bfloat16 nh[8], nl[8];
+          if (g + 1 < T::NODES / 16) {
+            if (half == 0)
+              bwd_load<0>(a.ah, a.al, node0 + 16 * (g + 1), a.n_nodes, a.hs, ic, nh, nl);
+            else
+              bwd_load<1>(a.ah, a.al, node0 + 16 * (g + 1), a.n_nodes, a.hs, ic, nh, nl);
+          }
           tmem_wait_ld();
           if (half == 0)
-            bwd_group<0>(v, a.ah, a.al, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
+            bwd_group<0>(v, ph, pl, node0 + 16 * g, a.n_nodes, a.hs, i, active, a.yh, a.yl);
           else
-            bwd_group<1>(v, a.ah, a.al, node0 + 16 * g, a.n_nodes, a.hs, i, ic, active, a.yh, a.yl);
+            bwd_group<1>(v, ph, pl, node0 + 16 * g, a.n_nodes, a.hs, i, active, a.yh, a.yl);
+          if (g + 1 < T::NODES / 16) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              ph[kk] = nh[kk];
+              pl[kk] = nl[kk];
+            }
+          }
         }
       }
       for (int ch = half; MODE != LY_BWD && ch < T::N / 16; ch += 2) {
         float v[16];
         tmem_ld16(taddr + 16 * ch, v);
+        __nv_bfloat16 nh[16], nl[16];
+        if (MODE == LY_BW0 && ch + 2 < T::N / 16) chunk_load(a.ah, a.al, node0 + 16 * (ch + 2), a.n_nodes, a.hs, ic, nh, nl);
         tmem_wait_ld();
         if (T::ACT) {
           float av[16];
@@ -311,10 +361,14 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
             }
           }
         } else if (MODE == LY_BW0) {
-          // D_{L-2}[node * 3 + r][i] = acc * d_{L-2}[node][i], loads first
+          // D_{L-2}[node * 3 + r][i] = acc * d_{L-2}[node][i], the chunk's
+          // activations loaded one chunk ahead
           float dv[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) dv[k] = d_of(a.ah, a.al, (size_t)min(node0 + 16 * ch + k, a.n_nodes - 1) * a.hs + ic);
+          for (int k = 0; k < 16; ++k) {
+            const float av = __bfloat162float(qh[k]) + __bfloat162float(ql[k]);
+            dv[k] = 1.0f - av * av;
+          }
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int node = node0 + 16 * ch + k;
@@ -324,6 +378,13 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
               split_bf(v[k] * dv[k], h, l);
               a.yh[o] = h;
               a.yl[o] = l;
+            }
+          }
+          if (ch + 2 < T::N / 16) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              qh[k] = nh[k];
+              ql[k] = nl[k];
             }
           }
         } else {

@@ -96,8 +96,12 @@ struct KArgs {
   int* box_iters;
 };
 
+// Each warp's sweep is one dependent chain, so throughput comes from
+// resident warps: at least five blocks per SM (registers capped at 96, a
+// few bytes spilled), which at 8192 instances leaves three rounds of warps
+// instead of four.
 template <typename T, int WPB, bool BOX>
-__global__ void __launch_bounds__(WPB * 32) qp_kernel(KArgs ka) {
+__global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
   __shared__ Slot<T> slots[WPB];
   const QpArgs& a = ka.a;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

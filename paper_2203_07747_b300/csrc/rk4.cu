@@ -44,13 +44,11 @@ __device__ __forceinline__ void f_nominal(const QuadParams& P, const float* x, c
   xd[7] = T * P.inv_mass * r[0];
   xd[8] = T * P.inv_mass * r[1];
   xd[9] = T * P.inv_mass * r[2] - P.g;
-  float tx = P.d * ((u[2] + u[3]) - (u[0] + u[1]));
-  float ty = P.d * ((u[1] + u[2]) - (u[0] + u[3]));
-  float tz = P.c_tau * ((u[1] + u[3]) - (u[0] + u[2]));
-  float wx = x[10], wy = x[11], wz = x[12];
-  xd[10] = (tx - (P.Jz - P.Jy) * wy * wz) / P.Jx;
-  xd[11] = (ty - (P.Jx - P.Jz) * wz * wx) / P.Jy;
-  xd[12] = (tz - (P.Jy - P.Jx) * wx * wy) / P.Jz;
+  // J^-1 (tau - w x J w) with J^-1 folded into the coefficients
+  const float wx = x[10], wy = x[11], wz = x[12];
+  xd[10] = P.tq[0] * ((u[2] + u[3]) - (u[0] + u[1])) - P.gy[0] * wy * wz;
+  xd[11] = P.tq[1] * ((u[1] + u[2]) - (u[0] + u[3])) - P.gy[1] * wz * wx;
+  xd[12] = P.tq[2] * ((u[1] + u[3]) - (u[0] + u[2])) - P.gy[2] * wx * wy;
 }
 
 // directional derivative of f_nominal at (x, u) along (dx, du)
@@ -78,13 +76,10 @@ __device__ __forceinline__ void jvp_nominal(const QuadParams& P, const float* x,
 #pragma unroll
   for (int i = 0; i < 3; ++i) o[7 + i] = P.inv_mass * (dT * r[i] + T * dr[i]);
   // d(J^-1 (tau - w x J w))
-  float dtx = P.d * ((du[2] + du[3]) - (du[0] + du[1]));
-  float dty = P.d * ((du[1] + du[2]) - (du[0] + du[3]));
-  float dtz = P.c_tau * ((du[1] + du[3]) - (du[0] + du[2]));
-  float wx = x[10], wy = x[11], wz = x[12], dwx = dx[10], dwy = dx[11], dwz = dx[12];
-  o[10] = (dtx - (P.Jz - P.Jy) * (dwy * wz + wy * dwz)) / P.Jx;
-  o[11] = (dty - (P.Jx - P.Jz) * (dwz * wx + wz * dwx)) / P.Jy;
-  o[12] = (dtz - (P.Jy - P.Jx) * (dwx * wy + wx * dwy)) / P.Jz;
+  const float wx = x[10], wy = x[11], wz = x[12], dwx = dx[10], dwy = dx[11], dwz = dx[12];
+  o[10] = P.tq[0] * ((du[2] + du[3]) - (du[0] + du[1])) - P.gy[0] * (dwy * wz + wy * dwz);
+  o[11] = P.tq[1] * ((du[1] + du[2]) - (du[0] + du[3])) - P.gy[1] * (dwz * wx + wz * dwx);
+  o[12] = P.tq[2] * ((du[1] + du[3]) - (du[0] + du[2])) - P.gy[2] * (dwx * wy + wx * dwy);
 }
 
 template <int NOUT>

@@ -23,6 +23,10 @@ constexpr int NC = 18;   // columns per node in forward mode: value + 17 tangent
 // Quadrotor constants in FP32 for the linearisation kernels (by value).
 struct QuadParams {
   float mass, inv_mass, Jx, Jy, Jz, d, c_tau, u_max, g, hover;
+  // Eq. 6 torque and gyroscopic coefficients with J^-1 folded in (rounded
+  // once from FP64): d / Jx, d / Jy, c_tau / Jz and (Jz - Jy) / Jx,
+  // (Jx - Jz) / Jy, (Jy - Jx) / Jz
+  float tq[3], gy[3];
 };
 
 // Diagonal tracking weights (Sec. V cost), kept in FP64 so that the FP64
