@@ -572,14 +572,18 @@ def lay_bytes(kind, widths, nn):
     if kind == "inputs":
         return (17 * 4 + 17 * 4) * nn
     if kind == "input GEMM":
-        return (17 + 2 * w[1]) * 4 * nn
+        return (17 + w[1]) * 4 * nn
     if kind == "forward GEMM":
-        return sum((w[l] + 2 * w[l + 1]) * 4 for l in range(1, L - 1)) * nn
+        # a_l in, a_{l+1} out; the last also writes d_{L-1} (the folded
+        # first backward GEMM's operand)
+        return (sum((w[l] + w[l + 1]) * 4 for l in range(1, L - 1)) + w[L - 1] * 4) * nn
     if kind == "output layer":
         return (w[L - 1] + 3) * 4 * nn
     if kind == "first backward GEMM":
+        # d_{L-1} in, a_{L-2} in (d_{L-2} = 1 - a^2), D_{L-2} out
         return (w[L - 1] + w[L - 2] + 3 * w[L - 2]) * 4 * nn
     if kind == "backward GEMM":
+        # D_{l+1} in, a_l in (d_l = 1 - a_l^2), D_l out
         return sum((3 * w[l + 1] + w[l] + 3 * w[l]) * 4 for l in range(1, L - 2)) * nn
     if kind == "Jacobian GEMM":
         return (3 * w[1] + 3 * 17) * 4 * nn
@@ -663,6 +667,29 @@ def bench_network_pass(config, B, reps=3):
     fD, JD = ctl.mlp_eval(x, u)
     ms = time_calls(lambda: ctl.mlp_eval(x, u, fD, JD), reps, warm=1)
     out = {"instances": B, "nodes": ctl.n_nodes, "variant": vi, "ms_per_pass": ms, "device_error": ctl.device_error()}
+    ctl.close()
+    return out
+
+
+def bench_rti_step(config, B, reps=3):
+    """One RTI step (a1 network pass, a2 RK4 + sensitivities, a3 + a4
+    Riccati QP and feedback) of the workload on B instances with the layered
+    reverse-mode shape: ms per step after one warm-up step (the profiling
+    command of the RK4 and QP kernels' summaries)."""
+    import torch
+    prob = W.make_problem(config, seed=0, B=B, bf16=True)
+    ctl = make(prob, "bf16x2")
+    vi = [v[0] for v in ctl.tc_variants() if v[2] == 6][0]
+    ctl.tc_select(vi)
+    xref, uref = W.node_refs(prob)
+    xref_d = torch.as_tensor(xref, dtype=torch.float32, device="cuda")
+    uref_d = torch.as_tensor(uref, dtype=torch.float32, device="cuda")
+    xo = np.concatenate([[0], np.cumsum(prob["N"] + 1)])[:-1]
+    x0_d = xref_d[torch.as_tensor(xo, device="cuda")] + 0.02
+    u0 = torch.empty((B, 4), dtype=torch.float32, device="cuda")
+    st = torch.empty(B, dtype=torch.int32, device="cuda")
+    ms = time_calls(lambda: ctl.rti_step(x0_d, xref_d, uref_d, u0, st), reps, warm=1)
+    out = {"instances": B, "nodes": ctl.n_nodes, "variant": vi, "ms_per_step": ms, "device_error": ctl.device_error()}
     ctl.close()
     return out
 
@@ -753,6 +780,9 @@ def main():
     ap.add_argument("--network-pass", type=int, default=0, metavar="B",
                     help="time only the network pass (a1) of the workload's network on B instances with "
                          "the layered reverse-mode tile shape (the profiling command of its summary)")
+    ap.add_argument("--rti-step", type=int, default=0, metavar="B",
+                    help="time only one RTI step of the workload on B instances with the layered reverse-mode "
+                         "tile shape (the profiling command of the RK4 and QP kernels' summaries)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -763,6 +793,9 @@ def main():
         return
     if args.network_pass:
         print(json.dumps(bench_network_pass(args.config, args.network_pass)))
+        return
+    if args.rti_step:
+        print(json.dumps(bench_rti_step(args.config, args.rti_step)))
         return
     # weak scaling: every rank steps its own instances (seeded by rank)
     prob = W.make_problem(args.config, seed=rank, bf16=True)
