@@ -1,0 +1,41 @@
+"""The bench's roofline accounting for the layered reverse mode (host
+arithmetic only): algorithmic FLOPs and DRAM bytes per launch kind, checked
+against totals derived by hand for the 17-512x5-3 network of the cfg3
+workload, and against the reverse-mode FLOP count of the whole network."""
+import bench
+
+W = [17, 512, 512, 512, 512, 512, 3]
+
+
+def test_layered_flops_sum_to_reverse_mode_minus_output_layer():
+    # every layer GEMM is counted once; the output layer (2 x 3 x h per
+    # node) runs on the SIMT cores and carries no GEMM FLOPs
+    nn = 1000
+    total = sum(bench.lay_flops(k, W, nn) for k in bench.LAY_KERNELS)
+    assert total == (bench.rev_flops_per_node(W) - 2 * 3 * W[-2]) * nn
+
+
+def test_layered_bytes_per_node_by_hand():
+    # 4 B per value (FP32, or a BF16 hi + lo pair), per node:
+    #   inputs:          x, u in (17) and z out (17)                 136
+    #   input GEMM:      z in, a_1 out                 (17 + 512) * 4 = 2116
+    #   forward GEMMs:   a_l in, a_{l+1} out, x4; d_5 out        4 * 4096 + 2048 = 18432
+    #   output layer:    a_5 in, f_D out               (512 + 3) * 4 = 2060
+    #   first backward:  d_5 in, a_4 in, D_4 out (3 rows)  (512 + 512 + 1536) * 4 = 10240
+    #   backward x3:     D_{l+1} in, a_l in, D_l out     3 * 14336 = 43008
+    #   Jacobian:        D_1 in, J_D out               (1536 + 51) * 4 = 6348
+    per_node = {"inputs": 136, "input GEMM": 2116, "forward GEMM": 18432, "output layer": 2060,
+                "first backward GEMM": 10240, "backward GEMM": 43008, "Jacobian GEMM": 6348}
+    for kind, b in per_node.items():
+        assert bench.lay_bytes(kind, W, 1) == b, kind
+    assert sum(bench.lay_bytes(k, W, 163840) for k in bench.LAY_KERNELS) == 82340 * 163840
+
+
+def test_backward_gemm_is_below_the_ridge():
+    # arithmetic intensity of one backward layer: 2 x 3 x 512 x 512 FLOP per
+    # 14,336 B = 109.7 FLOP/B, below any BF16 ridge above ~110 FLOP/B (the
+    # measured peaks put it near 274), so the bench reports it against HBM
+    fl = bench.lay_flops("backward GEMM", W, 1) / 3
+    by = bench.lay_bytes("backward GEMM", W, 1) / 3
+    assert abs(fl / by - 2 * 3 * 512 * 512 / 14336) < 1e-9
+    assert fl / by < 111
