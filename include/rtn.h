@@ -197,6 +197,20 @@ rtn_status rtn_qp_solve(rtn_ctx* ctx, const float* A, const float* B, const floa
 rtn_status rtn_rti_step(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
                         float* u0_out, int* inst_status);
 
+/* rtn_rti_step with HOST buffers (Sec. III-B): x0 host [B][13], xref host
+ * [sum(N_b+1)][13], uref host [sum N_b][4] in, u0_out host [B][4] and
+ * inst_status host int [B] (may be NULL) out.  The inputs are read only by
+ * the QP, so they are copied to device buffers owned by the context on a
+ * second stream while the network pass and RK4 run on the context's stream;
+ * the QP waits for the copies, u0 and the status are copied back on the
+ * context's stream.  Asynchronous like the other calls: the host inputs
+ * must stay unchanged and the outputs are valid only after the context's
+ * stream has been synchronised.  Page-locked host memory lets the copies
+ * overlap; pageable memory gives the same results with the copies staged
+ * by the driver.  RTN_E_UNSUPPORTED for the double-integrator model. */
+rtn_status rtn_rti_step_host(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
+                             float* u0_out, int* inst_status);
+
 /* Subproblems (masked Riccati sweeps) each instance's last box-constrained QP
  * needed: host int [B] (1 = the unconstrained solution was feasible).
  * Synchronous.  RTN_E_UNSUPPORTED unless the context was created with box_qp. */

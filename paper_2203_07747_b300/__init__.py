@@ -23,7 +23,7 @@ STATUS = {0: "RTN_OK", 1: "RTN_E_INVAL", 2: "RTN_E_CUDA", 3: "RTN_E_NONFINITE",
 # every symbol include/rtn.h declares
 EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_reset",
            "rtn_set_iterate", "rtn_get_iterate", "rtn_mlp_eval", "rtn_linearize",
-           "rtn_qp_solve", "rtn_rti_step", "rtn_plant_step", "rtn_closed_loop",
+           "rtn_qp_solve", "rtn_rti_step", "rtn_rti_step_host", "rtn_plant_step", "rtn_closed_loop",
            "rtn_mlp_eval_f32_noalloc", "rtn_device_error", "rtn_tc_variants",
            "rtn_tc_variant_info", "rtn_tc_select", "rtn_autotune", "rtn_tc_trace",
            "rtn_tc_trace_read", "rtn_drag_targets", "rtn_mse_grad", "rtn_train",
@@ -86,6 +86,7 @@ def load(build_if_missing=False):
     L.rtn_linearize.argtypes = [vp] * 8
     L.rtn_qp_solve.argtypes = [vp] * 12
     L.rtn_rti_step.argtypes = [vp] * 6
+    L.rtn_rti_step_host.argtypes = [vp] * 6
     L.rtn_plant_step.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     L.rtn_closed_loop.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp, vp, vp]
     L.rtn_device_error.argtypes = [vp, C.POINTER(C.c_int)]
@@ -116,6 +117,22 @@ def _ptr(t, dtype, shape, name):
         return None
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise RtnError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise RtnError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise RtnError(f"{name}: must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise RtnError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(t, dtype, shape, name):
+    """A contiguous host tensor's address (page-locked lets the copies overlap)."""
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise RtnError(f"{name}: expected a host tensor")
     if t.dtype != dtype:
         raise RtnError(f"{name}: expected {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -401,6 +418,18 @@ class Controller:
             self._h, _ptr(x0, f, (self.B, NX), "x0"), _ptr(xref, f, (self.n_states, NX), "xref"),
             _ptr(uref, f, (self.n_nodes, NU), "uref"), _ptr(u0, f, (self.B, NU), "u0"),
             _ptr(status, torch.int32, (self.B,), "status")), "rtn_rti_step")
+        return u0, status
+
+    def rti_step_host(self, x0, xref, uref, u0, status=None):
+        """rti_step with host tensors (rtn_rti_step_host): the inputs are
+        copied on a second stream while the linearisation runs; u0 (and
+        status) are valid once the context's stream is synchronised."""
+        import torch
+        f = torch.float32
+        self._check(load().rtn_rti_step_host(
+            self._h, _hptr(x0, f, (self.B, NX), "x0"), _hptr(xref, f, (self.n_states, NX), "xref"),
+            _hptr(uref, f, (self.n_nodes, NU), "uref"), _hptr(u0, f, (self.B, NU), "u0"),
+            _hptr(status, torch.int32, (self.B,), "status")), "rtn_rti_step_host")
         return u0, status
 
     def plant_step(self, x, u, kind="nominal", nsub=4, out=None):

@@ -92,10 +92,10 @@ rtn_status linearize_impl(rtn_ctx* ctx, const float* x, const float* u, float* f
 
 // one RTI step on the context's iterate; refs addressed by strides (0 =
 // node-packed), t read from t_dev when given
-rtn_status rti_impl(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
-                    int xref_stride, int uref_stride, const int* t_dev, float* u0, int* status) {
-  rtn_status st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);
-  if (st != RTN_OK) return st;
+// the QP, feedback and iterate update of an RTI step whose linearisation
+// is in ctx->A, Bm, c
+static rtn_status rti_qp(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
+                         int xref_stride, int uref_stride, const int* t_dev, float* u0, int* status) {
   QpArgs a{};
   a.A = ctx->A; a.Bm = ctx->Bm; a.c = ctx->c;
   a.x = ctx->x; a.u = ctx->u;
@@ -110,6 +110,13 @@ rtn_status rti_impl(rtn_ctx* ctx, const float* x0, const float* xref, const floa
   cudaError_t e = qp_solve(ctx, a);
   if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("qp: ") + cudaGetErrorString(e));
   return RTN_OK;
+}
+
+rtn_status rti_impl(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
+                    int xref_stride, int uref_stride, const int* t_dev, float* u0, int* status) {
+  rtn_status st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);
+  if (st != RTN_OK) return st;
+  return rti_qp(ctx, x0, xref, uref, xref_stride, uref_stride, t_dev, u0, status);
 }
 
 // ragged node-packed layout of the batch (both models)
@@ -410,6 +417,15 @@ void rtn_destroy(rtn_ctx* ctx) {
       if (p) cudaFree(p);
     delete ctx->di;
   }
+  {
+    auto& io = ctx->hio;
+    void* hp[] = {io.x0, io.xref, io.uref, io.u0, io.st};
+    for (void* p : hp)
+      if (p) cudaFree(p);
+    if (io.free_ev) cudaEventDestroy(io.free_ev);
+    if (io.in_ev) cudaEventDestroy(io.in_ev);
+    if (io.copy) cudaStreamDestroy(io.copy);
+  }
   mlp_tf32_release(ctx);
   mlp_tc_release(ctx);
   train_release(ctx);
@@ -529,6 +545,43 @@ rtn_status rtn_rti_step(rtn_ctx* ctx, const float* x0, const float* xref, const 
     return RTN_OK;
   }
   return rti_impl(ctx, x0, xref, uref, 0, 0, nullptr, u0_out, inst_status);
+}
+
+rtn_status rtn_rti_step_host(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
+                             float* u0_out, int* inst_status) {
+  if (!ctx) return RTN_E_INVAL;
+  if (!x0 || !xref || !uref || !u0_out) return fail(ctx, RTN_E_INVAL, "rtn_rti_step_host: NULL argument");
+  if (ctx->di) return di_unsupported(ctx, "rtn_rti_step_host");
+  auto& io = ctx->hio;
+  const Layout& L = ctx->lay;
+  const size_t bx0 = (size_t)L.B * NX * 4, bxr = (size_t)L.n_states * NX * 4, bur = (size_t)L.n_nodes * NU * 4;
+  if (!io.copy) {
+    CK(cudaStreamCreateWithFlags(&io.copy, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&io.free_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&io.in_ev, cudaEventDisableTiming));
+    CK(cudaMalloc(&io.x0, bx0));
+    CK(cudaMalloc(&io.xref, bxr));
+    CK(cudaMalloc(&io.uref, bur));
+    CK(cudaMalloc(&io.u0, (size_t)L.B * NU * 4));
+    CK(cudaMalloc(&io.st, (size_t)L.B * 4));
+  }
+  // the inputs are read only by the QP: copy them on the side stream while
+  // the network pass and RK4 run, once the previous step's QP has read the
+  // device copies
+  CK(cudaEventRecord(io.free_ev, ctx->stream));
+  CK(cudaStreamWaitEvent(io.copy, io.free_ev, 0));
+  CK(cudaMemcpyAsync(io.x0, x0, bx0, cudaMemcpyHostToDevice, io.copy));
+  CK(cudaMemcpyAsync(io.xref, xref, bxr, cudaMemcpyHostToDevice, io.copy));
+  CK(cudaMemcpyAsync(io.uref, uref, bur, cudaMemcpyHostToDevice, io.copy));
+  CK(cudaEventRecord(io.in_ev, io.copy));
+  rtn_status st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);
+  if (st != RTN_OK) return st;
+  CK(cudaStreamWaitEvent(ctx->stream, io.in_ev, 0));
+  st = rti_qp(ctx, io.x0, io.xref, io.uref, 0, 0, nullptr, io.u0, io.st);
+  if (st != RTN_OK) return st;
+  CK(cudaMemcpyAsync(u0_out, io.u0, (size_t)L.B * NU * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (inst_status) CK(cudaMemcpyAsync(inst_status, io.st, (size_t)L.B * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  return RTN_OK;
 }
 
 rtn_status rtn_plant_step(rtn_ctx* ctx, int kind, const double* x, const float* u, double* x_next,

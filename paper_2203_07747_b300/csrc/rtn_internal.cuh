@@ -203,6 +203,14 @@ struct rtn_ctx {
   signed char* box_act = nullptr;         // [n_nodes][4] -1 lower, +1 upper, 0 free
   int* box_iters = nullptr;               // [B] subproblems of the last QP
   rtn::TrainState train;
+  // rtn_rti_step_host: device copies of the step's inputs and outputs, a
+  // copy stream and its events (allocated on first use)
+  struct HostIO {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t free_ev = nullptr, in_ev = nullptr;
+    float *x0 = nullptr, *xref = nullptr, *uref = nullptr, *u0 = nullptr;
+    int* st = nullptr;
+  } hio;
   std::string err;
 };
 

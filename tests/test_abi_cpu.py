@@ -106,3 +106,20 @@ def test_create_rejects_oversized_batch():
     n = 1 << 20
     st, err = _create(lib, N=(300,) * n, dt=(0.05,) * n)
     assert st == 1 and "too large" in err
+
+
+def test_rti_step_host_rejects_null_context_and_device_tensors():
+    # no GPU needed: a NULL context is an argument error, and the binding
+    # only takes contiguous host tensors of the right dtype and shape
+    import torch
+    import paper_2203_07747_b300 as rtn
+    lib = rtn.load(build_if_missing=True)
+    assert lib.rtn_rti_step_host(None, None, None, None, None, None) == 1
+    with pytest.raises(rtn.RtnError):
+        rtn._hptr(torch.zeros((4, 13), dtype=torch.float64), torch.float32, (4, 13), "x0")
+    with pytest.raises(rtn.RtnError):
+        rtn._hptr(torch.zeros((4, 12), dtype=torch.float32), torch.float32, (4, 13), "x0")
+    with pytest.raises(rtn.RtnError):
+        rtn._hptr(torch.zeros((13, 4), dtype=torch.float32).t(), torch.float32, (4, 13), "x0")
+    assert rtn._hptr(torch.zeros((4, 13), dtype=torch.float32), torch.float32, (4, 13), "x0") is not None
+
