@@ -730,11 +730,16 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
   if (steps == 0) return RTN_OK;
   if (plant_kind == RTN_PLANT_MLP && (!ctx->has_mlp || ctx->net.h_max > 64))
     return fail(ctx, RTN_E_UNSUPPORTED, "plant network needs widths <= 64 and a network");
-  // capture one control step on a private stream ordered after the caller's
-  // stream, then replay it `steps` times; the kernels read the step index
-  // from ctx->dev_t, which the graph advances
-  cudaStream_t user = ctx->stream, cs = nullptr;
-  cudaEvent_t ev = nullptr;
+  // one control step is an RTI step (linearise at the iterate, QP from the
+  // measured state) and a plant step.  Step k + 1's linearisation reads only
+  // the iterate that step k's QP left, not the plant state, so the replayed
+  // graph runs step k's plant step (and its record and the step counter) on
+  // a second branch beside step k + 1's linearisation and joins them before
+  // step k + 1's QP; the first step's RTI step and the last step's plant step
+  // run outside the graph.  The kernels read the step index from
+  // ctx->dev_t, which the plant branch advances.
+  cudaStream_t user = ctx->stream, cs = nullptr, cs2 = nullptr;
+  cudaEvent_t ev = nullptr, fork = nullptr, join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   rtn_status st = RTN_OK;
@@ -742,40 +747,67 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (ev) cudaEventDestroy(ev);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     if (cs) cudaStreamDestroy(cs);
+    if (cs2) cudaStreamDestroy(cs2);
     ctx->stream = user;
   };
+  // plant step of the current step index, its record, then the next index
+  auto plant_branch = [&](cudaStream_t s) -> cudaError_t {
+    ctx->stream = s;
+    cudaError_t r = plant_step(ctx, plant_kind, x_plant, ctx->u0, x_plant, 4, ctx->x0f);
+    record_kernel<<<(ctx->B * NX + 255) / 256, 256, 0, s>>>(ctx->dev_t, ctx->B, x_plant, ctx->u0, traj_out,
+                                                            u_out);
+    advance_kernel<<<1, 1, 0, s>>>(ctx->dev_t);
+    ctx->stream = cs;
+    return r != cudaSuccess ? r : cudaGetLastError();
+  };
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_t, 0, sizeof(int), user);
   if (e == cudaSuccess) e = cudaEventRecord(ev, user);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
   if (e != cudaSuccess) { ctx->err = cudaGetErrorString(e); cleanup(); return RTN_E_CUDA; }
   ctx->stream = cs;
-  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    // the plant state in float is the measured x0 of the RTI step
-    st = rti_impl(ctx, ctx->x0f, xref_traj, uref_traj, T, T - 1, ctx->dev_t, ctx->u0, ctx->status);
-    if (st == RTN_OK) {
-      e = plant_step(ctx, plant_kind, x_plant, ctx->u0, x_plant, 4, ctx->x0f);
-      record_kernel<<<(ctx->B * NX + 255) / 256, 256, 0, cs>>>(ctx->dev_t, ctx->B, x_plant, ctx->u0,
-                                                               traj_out, u_out);
-      advance_kernel<<<1, 1, 0, cs>>>(ctx->dev_t);
+  if (steps > 1) {
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = cudaEventRecord(fork, cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs2, fork, 0);
+      if (e == cudaSuccess) e = plant_branch(cs2);  // step k
+      if (e == cudaSuccess) {
+        st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);  // step k + 1
+        ctx->stream = cs;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(join, cs2);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, join, 0);
+      // the plant state in float is the measured x0 of the RTI step
+      if (e == cudaSuccess && st == RTN_OK)
+        st = rti_qp(ctx, ctx->x0f, xref_traj, uref_traj, T, T - 1, ctx->dev_t, ctx->u0, ctx->status);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = e2;
     }
-    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-    if (e == cudaSuccess) e = e2;
+    if (st != RTN_OK || e != cudaSuccess) {
+      if (st == RTN_OK) { ctx->err = std::string("capture: ") + cudaGetErrorString(e); st = RTN_E_CUDA; }
+      cleanup();
+      return st;
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
   }
-  if (st != RTN_OK || e != cudaSuccess) {
-    if (st == RTN_OK) { ctx->err = std::string("capture: ") + cudaGetErrorString(e); st = RTN_E_CUDA; }
-    cleanup();
-    return st;
-  }
-  e = cudaGraphInstantiate(&exec, graph, 0);
   if (e == cudaSuccess) {
     convert_state_kernel<<<(ctx->B * NX + 255) / 256, 256, 0, cs>>>(x_plant, ctx->x0f, ctx->B * NX);
     e = cudaGetLastError();
   }
-  for (int s = 0; s < steps && e == cudaSuccess; ++s) e = cudaGraphLaunch(exec, cs);
+  if (e == cudaSuccess) {
+    st = rti_impl(ctx, ctx->x0f, xref_traj, uref_traj, T, T - 1, ctx->dev_t, ctx->u0, ctx->status);
+    ctx->stream = cs;
+  }
+  for (int s = 1; s < steps && e == cudaSuccess && st == RTN_OK; ++s) e = cudaGraphLaunch(exec, cs);
+  if (e == cudaSuccess && st == RTN_OK) e = plant_branch(cs);
   if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ev, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
