@@ -57,3 +57,30 @@ def test_rti_step_host_matches_device_buffers(rtn):
     assert dev.device_error() == 0 and host.device_error() == 0
     dev.close()
     host.close()
+
+
+def test_rti_step_host_pageable_buffers(rtn):
+    # pageable host memory: the driver stages the copies, results unchanged
+    prob = W.make_problem("cfg3_bf16_precision", seed=2, B=32, bf16=True)
+    N, B = prob["N"], len(prob["N"])
+    dt = np.asarray(prob["dt"], np.float32).astype(np.float64)
+
+    def make():
+        return rtn.Controller(N, dt, prob["Q"], prob["R"], QN=prob["QN"], quad=QUAD, layers=prob["layers"],
+                              precision="bf16x2")
+
+    dev, host = make(), make()
+    xref, uref = W.node_refs(prob)
+    h_xr = torch.as_tensor(xref, dtype=torch.float32)
+    h_ur = torch.as_tensor(uref, dtype=torch.float32)
+    xo = np.concatenate([[0], np.cumsum(N + 1)])[:-1]
+    h_x0 = (h_xr[torch.as_tensor(xo)] + 0.05).contiguous()
+    assert not h_x0.is_pinned()
+    h_u0 = torch.empty((B, 4), dtype=torch.float32)
+    for step in range(2):
+        u0, _ = dev.rti_step(h_x0.cuda(), h_xr.cuda(), h_ur.cuda())
+        host.rti_step_host(h_x0, h_xr, h_ur, h_u0)
+        torch.cuda.synchronize()
+        assert torch.equal(u0.cpu(), h_u0), step
+    dev.close()
+    host.close()
