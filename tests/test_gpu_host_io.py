@@ -20,8 +20,10 @@ def rtn():
     return rtn
 
 
-def test_rti_step_host_matches_device_buffers(rtn):
-    prob = W.make_problem("cfg3_bf16_precision", seed=1, B=96, bf16=True)
+@pytest.mark.parametrize("config", ["cfg3_bf16_precision", "cfg4_ragged_batch"])
+def test_rti_step_host_matches_device_buffers(rtn, config):
+    # uniform horizons, and ragged ones (N_b in {10..50}, per-instance dt_b)
+    prob = W.make_problem(config, seed=1, B=96, bf16=True)
     N, B = prob["N"], len(prob["N"])
     dt = np.asarray(prob["dt"], np.float32).astype(np.float64)
 
