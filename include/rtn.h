@@ -97,7 +97,10 @@ typedef struct {
 
 typedef struct {
   int precision;    /* RTN_FP32 / RTN_BF16 / RTN_BF16X2 */
-  int riccati_f64;  /* 0: FP32 sweep (Cholesky of R+B'PB in FP32); 1: FP64 sweep */
+  int riccati_f64;  /* Riccati sweep arithmetic: 0 FP32 (the Cholesky of
+                       R + B'PB in FP32); 1 FP64 throughout; 2 FP32 with the
+                       Cholesky of R + B'PB and the solves for the gains
+                       [K | k] in FP64 */
   int shift;        /* 1: shift the iterate by one stage after every RTI step */
   int box_qp;       /* 1: the QP carries the thrust bounds 0 <= u_k + du_k <= u_max
                        (Sec. V) and is solved by a primal-dual active-set method
@@ -322,6 +325,27 @@ rtn_status rtn_tc_launch_times(rtn_ctx* ctx, int enable, float* ms, int* kind, i
  * the tensor-core pipeline that gave up (RTN_E_TIMEOUT); the affected outputs
  * are then undefined. */
 rtn_status rtn_device_error(rtn_ctx* ctx, int* code);
+
+/* Budget of the bounded waits inside the layered tensor-core network kernels
+ * (tile mode 6; a fault-injection aid for failure-detection tests).  Every
+ * mbarrier wait of those kernels gives up after `cycles` SM clock cycles
+ * (0 restores the default, 4e9 cycles, about 2 s at 2 GHz): the CTA records
+ * RTN_E_TIMEOUT (read and cleared by rtn_device_error), lets the copies and
+ * MMAs it already issued finish (bounded by the default budget), frees its
+ * tensor memory and returns; the outputs of that network pass are then
+ * undefined.  A budget of a few cycles makes a pass give up at its first
+ * wait that is not already satisfied.  Takes effect at the next launch;
+ * RTN_E_INVAL for a negative budget. */
+rtn_status rtn_set_wait_budget(rtn_ctx* ctx, long long cycles);
+
+/* Fault injection for failure-detection tests (no GPU fault involved):
+ * enable != 0 makes the TMA producer of every later layered network kernel
+ * (tile mode 6) first wait on a barrier that nothing completes, before it
+ * issues any copy; the wait runs out after the budget of
+ * rtn_set_wait_budget, the pass returns with RTN_E_TIMEOUT recorded
+ * (rtn_device_error) and nothing in flight, and its outputs are undefined.
+ * enable == 0 restores normal passes. */
+rtn_status rtn_inject_wait_stall(rtn_ctx* ctx, int enable);
 
 /* Size of the fixed activation array used by rtn_mlp_eval_f32_noalloc. */
 #define RTN_NOALLOC_SCRATCH_BYTES (16u << 20)

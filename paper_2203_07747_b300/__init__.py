@@ -27,7 +27,8 @@ EXPORTS = ["rtn_create", "rtn_destroy", "rtn_last_error", "rtn_sizes", "rtn_rese
            "rtn_mlp_eval_f32_noalloc", "rtn_device_error", "rtn_tc_variants",
            "rtn_tc_variant_info", "rtn_tc_select", "rtn_autotune", "rtn_tc_trace",
            "rtn_tc_trace_read", "rtn_drag_targets", "rtn_mse_grad", "rtn_train",
-           "rtn_get_params", "rtn_box_iterations", "rtn_mlp_hess", "rtn_tc_launch_times"]
+           "rtn_get_params", "rtn_box_iterations", "rtn_mlp_hess", "rtn_tc_launch_times",
+           "rtn_set_wait_budget", "rtn_inject_wait_stall"]
 
 _lib = None
 
@@ -90,6 +91,8 @@ def load(build_if_missing=False):
     L.rtn_plant_step.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     L.rtn_closed_loop.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp, vp, vp]
     L.rtn_device_error.argtypes = [vp, C.POINTER(C.c_int)]
+    L.rtn_set_wait_budget.argtypes = [vp, C.c_longlong]
+    L.rtn_inject_wait_stall.argtypes = [vp, C.c_int]
     ip = C.POINTER(C.c_int)
     L.rtn_tc_variants.argtypes = [vp, ip]
     L.rtn_tc_variant_info.argtypes = [vp, C.c_int, ip, ip, ip, ip]
@@ -181,7 +184,10 @@ class Controller:
             self._keep += [Wp, bp]
             mlp = _MLP(len(layers), w, Wp, bp)
             mlp_p = C.byref(mlp)
-        opt = _Opt(PRECISION[precision], int(bool(riccati_f64)), int(bool(shift)), int(bool(box_qp)),
+        # riccati_f64: False/0 FP32 sweep, True/1 FP64 sweep, "chol64"/2 FP32 sweep
+        # with the factorisation of R + B'PB and the gain solves in FP64
+        ric = 2 if riccati_f64 == "chol64" else int(riccati_f64)
+        opt = _Opt(PRECISION[precision], ric, int(bool(shift)), int(bool(box_qp)),
                    int(box_max_iter), int(bool(second_order)))
         self.box_qp = bool(box_qp)
         self.second_order = bool(second_order)
@@ -229,6 +235,16 @@ class Controller:
         self._check(load().rtn_box_iterations(self._h, out.ctypes.data_as(C.POINTER(C.c_int))),
                     "rtn_box_iterations")
         return out
+
+    def set_wait_budget(self, cycles):
+        """Budget [SM cycles] of the layered tensor-core kernels' bounded waits
+        (0: the default); a fault-injection aid (rtn_set_wait_budget)."""
+        self._check(load().rtn_set_wait_budget(self._h, int(cycles)), "rtn_set_wait_budget")
+
+    def inject_wait_stall(self, enable=True):
+        """Fault injection: the layered network kernels first wait on a barrier
+        that nothing completes (rtn_inject_wait_stall)."""
+        self._check(load().rtn_inject_wait_stall(self._h, int(bool(enable))), "rtn_inject_wait_stall")
 
     def device_error(self):
         """Synchronise and return (and clear) the device-side status code."""

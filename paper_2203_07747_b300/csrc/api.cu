@@ -235,6 +235,7 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
   if (opt) o = *opt;
   if (o.precision < RTN_FP32 || o.precision > RTN_BF16X2) { g_create_err = "bad precision"; return RTN_E_INVAL; }
   if (o.box_max_iter < 0) { g_create_err = "box_max_iter must be >= 0"; return RTN_E_INVAL; }
+  if (o.riccati_f64 < 0 || o.riccati_f64 > 2) { g_create_err = "riccati_f64 must be 0, 1 or 2"; return RTN_E_INVAL; }
   if (o.box_max_iter == 0) o.box_max_iter = 20;
   o.box_qp = o.box_qp ? 1 : 0;
   o.second_order = o.second_order ? 1 : 0;
@@ -359,7 +360,7 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     }
 
     // iterate and workspace
-    size_t gsz = ctx->opt.riccati_f64 ? sizeof(double) : sizeof(float);
+    size_t gsz = ctx->opt.riccati_f64 == 1 ? sizeof(double) : sizeof(float);
     CK(dalloc(&ctx->x, (size_t)xs * NX));
     CK(dalloc(&ctx->u, (size_t)us * NU));
     CK(dalloc(&ctx->fD, (size_t)us * ctx->n_out));
@@ -716,6 +717,19 @@ rtn_status rtn_device_error(rtn_ctx* ctx, int* code) {
   if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
   else CK(cudaDeviceSynchronize());
   *code = mlp_tc_take_error(ctx);
+  return RTN_OK;
+}
+
+rtn_status rtn_set_wait_budget(rtn_ctx* ctx, long long cycles) {
+  if (!ctx) return RTN_E_INVAL;
+  if (cycles < 0) return fail(ctx, RTN_E_INVAL, "rtn_set_wait_budget: negative budget");
+  ctx->net.tc.wait_cycles = cycles;
+  return RTN_OK;
+}
+
+rtn_status rtn_inject_wait_stall(rtn_ctx* ctx, int enable) {
+  if (!ctx) return RTN_E_INVAL;
+  ctx->net.tc.inject_stall = enable ? 1 : 0;
   return RTN_OK;
 }
 

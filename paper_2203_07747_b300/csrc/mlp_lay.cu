@@ -90,6 +90,8 @@ struct LyArgs {
   __nv_bfloat16* yl;
   float* JD;           // JD output [node][3][17]
   int* err;
+  long long wait_cycles;  // budget of every bounded pipeline wait [SM cycles]
+  int stall;              // fault injection: the TMA producer first waits on a barrier nothing completes
 };
 
 __device__ __forceinline__ void split_bf(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
   uint8_t* sm = smem_raw + pad;
   const uint32_t st0 = sraw + pad;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + LY_STAGES * STAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * LY_STAGES + 5);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * LY_STAGES + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
   auto acc_full = [&](int c) { return bar(2 * LY_STAGES + c); };
   auto tmem_free = [&](int c) { return bar(2 * LY_STAGES + 2 + c); };
   const uint32_t mma_done = bar(2 * LY_STAGES + 4);
+  const uint32_t stall_bar = bar(2 * LY_STAGES + 5);  // fault injection: nothing completes it
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_tiles = (long long)a.n_groups * a.mts;
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       mbar_init(tmem_free(c), LY_EPI_WARPS);
     }
     mbar_init(mma_done, 1);
+    mbar_init(stall_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -213,10 +217,13 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
     uint32_t ph = 0;
     bool ok = true;
     uint32_t issued = 0, last_ph = 0;
+    // fault injection: a bounded wait on a barrier that nothing completes, run
+    // out before any copy is issued, so the CTA returns with nothing in flight
+    if (a.stall) ok = mbar_wait_warp(stall_bar, 0, abort_flag, a.err, a.wait_cycles);
     for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
       for (int kb = 0; kb < a.nkb; ++kb) {
-        if (!(ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err))) break;
+        if (!(ok = mbar_wait_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err, a.wait_cycles))) break;
         if (elect_one()) {
           const uint32_t sa = st0 + s * STAGE;
           mbar_expect_tx(full_bar(s), STAGE);
@@ -245,11 +252,11 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
     uint32_t ph = 0, aph = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-      if (!(ok = mbar_wait_warp(tmem_free(acc), aph ^ 1u, abort_flag, a.err))) break;
+      if (!(ok = mbar_wait_warp(tmem_free(acc), aph ^ 1u, abort_flag, a.err, a.wait_cycles))) break;
       tc_fence_after();
       const uint32_t d = tmem + acc * 256u;
       for (int kb = 0; kb < a.nkb; ++kb) {
-        if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err))) break;
+        if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err, a.wait_cycles))) break;
         tc_fence_after();
         const uint32_t sa = st0 + s * STAGE;
 #pragma unroll
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
           bwd_load<1>(a.ah, a.al, node0, a.n_nodes, a.hs, ic, ph, pl);
       }
       if (MODE == LY_BW0) chunk_load(a.ah, a.al, node0 + 16 * half, a.n_nodes, a.hs, ic, qh, ql);
-      if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err)) break;
+      if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err, a.wait_cycles)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
       if (MODE == LY_BWD) {
@@ -723,6 +730,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     return m;
   };
   auto grid_of = [&](long long tiles) { return (int)std::min<long long>(tiles, std::max(1, tc.n_sm)); };
+  const long long budget = tc.wait_cycles > 0 ? tc.wait_cycles : WAIT_CYCLES;
+  const int stall = tc.inject_stall;
   // an event before each launch when the pass is timed
   s->n_marks = 0;
   auto mark = [&](int kind) {
@@ -750,6 +759,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.yh = s->act[0];
     a.yl = s->act[1];
     a.err = tc.err;
+    a.wait_cycles = budget;
+    a.stall = stall;
     mark(1);
     lay_kernel<LY_IN><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_IN>(), st>>>(
         *reinterpret_cast<const CUtensorMap*>(s->mw0), maps(s->mz[0], s->mz[1]), a);
@@ -774,6 +785,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.yh = s->act[0] + (size_t)(g + 1) * dstride;
     a.yl = s->act[1] + (size_t)(g + 1) * dstride;
     a.err = tc.err;
+    a.wait_cycles = budget;
+    a.stall = stall;
     mark(2);
     lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD>(), st>>>(
         *wmap, maps(s->ma[0], s->ma[1]), a);
@@ -811,6 +824,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.yh = s->xb[0][0];
     a.yl = s->xb[0][1];
     a.err = tc.err;
+    a.wait_cycles = budget;
+    a.stall = stall;
     LyMaps m;
     memcpy(&m.bh, s->mdd[0], sizeof(CUtensorMap));
     memcpy(&m.bl, s->mdd[1], sizeof(CUtensorMap));
@@ -836,6 +851,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.yh = s->xb[dst][0];
     a.yl = s->xb[dst][1];
     a.err = tc.err;
+    a.wait_cycles = budget;
+    a.stall = stall;
     mark(5);
     lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD>(), st>>>(
         *rmap, maps(s->mb[src][0], s->mb[src][1]), a);
@@ -854,6 +871,8 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.hs = hs;
     a.JD = JD;
     a.err = tc.err;
+    a.wait_cycles = budget;
+    a.stall = stall;
     mark(6);
     lay_kernel<LY_JD><<<grid_of(gb), LY_THREADS, ly_smem<LY_JD>(), st>>>(*rmap, maps(s->mb[src][0], s->mb[src][1]),
                                                                           a);

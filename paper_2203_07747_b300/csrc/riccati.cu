@@ -21,16 +21,22 @@
 // shared-memory slot with rows padded to 16 elements, so that every row a
 // lane needs whole is read with 16-byte broadcast loads.  The Cholesky of
 // Huu (4x4) is computed by one lane and the 14 triangular solves of [K | k]
-// on 14 lanes, all in the sweep precision: Huu is formed in that precision,
-// so a wider factorisation would not change the error's order, and one FP64
-// factorisation per node costs more than the rest of the FP32 sweep on this
-// part's FP64 pipe.  The FP64 sweep (rtn_options.riccati_f64) is the wide path.
+// on 14 lanes.  Three arithmetic choices (rtn_options.riccati_f64):
+//   0  everything in FP32 (Huu is formed in FP32, so a wider factor does
+//      not change the error's order, and an FP64 factorisation per node
+//      costs more than the rest of the FP32 sweep on this part's FP64 pipe);
+//   1  everything in FP64;
+//   2  the FP32 sweep with the factorisation of Huu = R + B'PB and the
+//      solves of [K | k] in FP64 (FP64 kept only where the QP divides).
+#include <type_traits>
+
 #include "rtn_internal.cuh"
 
 namespace rtn {
 namespace {
 
-template <typename T>
+// TC: the type of the factorisation of Huu and of the solves for [K | k]
+template <typename T, typename TC>
 struct __align__(16) Slot {
   T A[NX][16];    // A_k
   T PA[NX][16];   // P A
@@ -40,7 +46,7 @@ struct __align__(16) Slot {
   T Bm[NX][NU], PB[NX][NU];
   T c[16], g[16];  // c_k, p + P c
   T Huu[NU * NU], hu[NU], k[NU];
-  T Lt[NU * NU], Linvt[NU];  // Cholesky factor of Huu (strict lower part) and 1/diag
+  TC Lt[NU * NU], Linvt[NU];  // Cholesky factor of Huu (strict lower part) and 1/diag
   T dx[16], du[NU];
   int notpd;
 };
@@ -100,15 +106,16 @@ struct KArgs {
 // resident warps: at least five blocks per SM (registers capped at 96, a
 // few bytes spilled), which at 8192 instances leaves three rounds of warps
 // instead of four.
-template <typename T, int WPB, bool BOX>
+template <typename T, int WPB, bool BOX, bool CH64>
 __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
-  __shared__ Slot<T> slots[WPB];
+  using TC = typename std::conditional<CH64, double, T>::type;
+  __shared__ Slot<T, TC> slots[WPB];
   const QpArgs& a = ka.a;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slot = blockIdx.x * WPB + warp;
   if (slot >= ka.B) return;
   const int b = ka.order ? ka.order[slot] : slot;
-  Slot<T>& S = slots[warp];
+  Slot<T, TC>& S = slots[warp];
   const int N = ka.N[b], xo = ka.xoff[b], uo = ka.uoff[b];
   const int t = a.t_dev ? *a.t_dev : 0;
   const int xr0 = (a.xref_stride > 0 ? b * a.xref_stride : xo) + t;
@@ -229,27 +236,27 @@ __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
       if (BOX && lane < NU) ka.box_gam[node * NU + lane] = (float)S.Huu[lane * NU + lane];
       // held inputs: identity rows/columns of Huu, zero rows of Hux, right-hand
       // side -a; their coupling moves to the free rows' right-hand side
-      auto Hm = [&](int i, int j) -> T {
-        return (fx[i] || fx[j]) ? (i == j ? (T)1 : (T)0) : S.Huu[i * NU + j];
+      auto Hm = [&](int i, int j) -> TC {
+        return (fx[i] || fx[j]) ? (i == j ? (TC)1 : (TC)0) : (TC)S.Huu[i * NU + j];
       };
       // Cholesky of Huu by one lane (one reciprocal square root per pivot)
       if (lane == 0) {
-        T L[NU][NU];
+        TC L[NU][NU];
         bool pd = true;
   #pragma unroll
         for (int j = 0; j < NU; ++j) {
-          T s = Hm(j, j);
+          TC s = Hm(j, j);
   #pragma unroll
           for (int q = 0; q < j; ++q) s -= L[j][q] * L[j][q];
-          pd &= (s > (T)0);
-          T inv;
-          if constexpr (sizeof(T) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
+          pd &= (s > (TC)0);
+          TC inv;
+          if constexpr (sizeof(TC) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
           else inv = rsqrt(fmax(s, 1e-300));
           L[j][j] = s * inv;
-          S.Linvt[j] = (T)inv;
+          S.Linvt[j] = inv;
   #pragma unroll
           for (int i = j + 1; i < NU; ++i) {
-            T v = Hm(i, j);
+            TC v = Hm(i, j);
   #pragma unroll
             for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
             L[i][j] = v * inv;
@@ -258,24 +265,24 @@ __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
   #pragma unroll
         for (int i = 0; i < NU; ++i)
   #pragma unroll
-          for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (T)0;
+          for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (TC)0;
         if (!pd) S.notpd = 1;
       }
       __syncwarp();
       // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `lane` (13 = hu)
       if (lane < NX + 1) {
-        T y[NU];
+        TC y[NU];
   #pragma unroll
         for (int i = 0; i < NU; ++i) {
-          T v;
+          TC v;
           if (fx[i]) {
-            v = (lane < NX) ? (T)0 : -av[i];
+            v = (lane < NX) ? (TC)0 : -(TC)av[i];
           } else {
-            v = (lane < NX) ? S.Hux[i][lane] : S.hu[i];
+            v = (lane < NX) ? (TC)S.Hux[i][lane] : (TC)S.hu[i];
             if (lane == NX) {
   #pragma unroll
               for (int n = 0; n < NU; ++n)
-                if (fx[n]) v += S.Huu[i * NU + n] * av[n];
+                if (fx[n]) v += (TC)S.Huu[i * NU + n] * (TC)av[n];
             }
           }
   #pragma unroll
@@ -284,15 +291,15 @@ __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
         }
   #pragma unroll
         for (int i = NU - 1; i >= 0; --i) {
-          T v = y[i];
+          TC v = y[i];
   #pragma unroll
           for (int q = i + 1; q < NU; ++q) v -= S.Lt[q * NU + i] * y[q];
           y[i] = v * S.Linvt[i];
         }
   #pragma unroll
         for (int i = 0; i < NU; ++i) {
-          if (lane < NX) S.K[i][lane] = -y[i];
-          else S.k[i] = -y[i];
+          if (lane < NX) S.K[i][lane] = (T)(-y[i]);
+          else S.k[i] = (T)(-y[i]);
         }
       }
       __syncwarp();
@@ -549,11 +556,11 @@ __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
   else forward(2, st == RTN_E_NOT_CONVERGED);
 }
 
-template <typename T, int WPB>
+template <typename T, int WPB, bool CH64 = false>
 cudaError_t launch(const KArgs& ka, cudaStream_t s) {
   const int grid = (ka.B + WPB - 1) / WPB;
-  if (ka.box) qp_kernel<T, WPB, true><<<grid, WPB * 32, 0, s>>>(ka);
-  else qp_kernel<T, WPB, false><<<grid, WPB * 32, 0, s>>>(ka);
+  if (ka.box) qp_kernel<T, WPB, true, CH64><<<grid, WPB * 32, 0, s>>>(ka);
+  else qp_kernel<T, WPB, false, CH64><<<grid, WPB * 32, 0, s>>>(ka);
   return cudaGetLastError();
 }
 
@@ -578,7 +585,8 @@ cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a) {
   ka.box_gam = ctx->box_gam;
   ka.box_act = ctx->box_act;
   ka.box_iters = ctx->box_iters;
-  if (ctx->opt.riccati_f64) return launch<double, 2>(ka, ctx->stream);
+  if (ctx->opt.riccati_f64 == 1) return launch<double, 2>(ka, ctx->stream);
+  if (ctx->opt.riccati_f64 == 2) return launch<float, 4, true>(ka, ctx->stream);
   return launch<float, 4>(ka, ctx->stream);
 }
 

@@ -101,6 +101,8 @@ struct TcNet {
   float* dscr = nullptr;                // per-CTA d_l scratch
   alignas(64) unsigned char tmapR_bytes[128];  // CUtensorMap of WR
   LayState* lay = nullptr;              // layered reverse mode (tile mode 6)
+  long long wait_cycles = 0;            // budget of the layered kernels' bounded waits (0: default)
+  int inject_stall = 0;                 // fault injection (rtn_inject_wait_stall)
 };
 
 struct Net {

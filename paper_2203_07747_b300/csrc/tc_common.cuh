@@ -85,13 +85,15 @@ __device__ __forceinline__ uint32_t mbar_try_sleep(uint32_t bar, uint32_t parity
 
 constexpr uint32_t WAIT_SLEEP_NS = 2000;  // longest suspension per try
 
-// bounded wait by one thread; false on timeout or when another role aborted
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
+// bounded wait by one thread; false on timeout (after `budget` SM clock
+// cycles) or when another role aborted
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                          long long budget = WAIT_CYCLES) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_sleep(bar, parity, WAIT_SLEEP_NS)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       atomicExch(err, (int)RTN_E_TIMEOUT);
       return false;
@@ -105,8 +107,8 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
 // elected lane: their loop values stay warp-uniform, and a phase that has
 // already completed costs one try_wait and a vote.
 __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                               int* err) {
-  const bool ok = mbar_try(bar, parity) || mbar_wait(bar, parity, abort_flag, err);
+                                               int* err, long long budget = WAIT_CYCLES) {
+  const bool ok = mbar_try(bar, parity) || mbar_wait(bar, parity, abort_flag, err, budget);
   return __all_sync(0xffffffffu, ok);
 }
 

@@ -31,11 +31,16 @@ def test_layered_bytes_per_node_by_hand():
     assert sum(bench.lay_bytes(k, W, 163840) for k in bench.LAY_KERNELS) == 82340 * 163840
 
 
-def test_backward_gemm_is_below_the_ridge():
-    # arithmetic intensity of one backward layer: 2 x 3 x 512 x 512 FLOP per
-    # 14,336 B = 109.7 FLOP/B, below any BF16 ridge above ~110 FLOP/B (the
-    # measured peaks put it near 274), so the bench reports it against HBM
-    fl = bench.lay_flops("backward GEMM", W, 1) / 3
+def test_backward_gemm_flops_and_intensity():
+    # reverse-mode algorithmic FLOPs of one backward GEMM launch at the cfg3
+    # workload: 3 adjoint rows x 2 x 512 x 512 per node, 163,840 nodes; the
+    # bench reports this kernel tensor-bound against the BF16 peak.  Its
+    # design moves 14,336 B per node (adjoints and a_l through HBM), an
+    # intensity of 109.7 FLOP/B, below the BF16 ridge (~274 FLOP/B on the
+    # measured peaks): reported beside it as the HBM view
+    nn = 163840
+    fl = bench.lay_flops("backward GEMM", W, nn) / 3
+    assert fl == 3 * 2 * 512 * 512 * nn
     by = bench.lay_bytes("backward GEMM", W, 1) / 3
-    assert abs(fl / by - 2 * 3 * 512 * 512 / 14336) < 1e-9
-    assert fl / by < 111
+    assert abs(bench.lay_flops("backward GEMM", W, 1) / 3 / by - 2 * 3 * 512 * 512 / 14336) < 1e-9
+    assert bench.A1_METHOD_BYTES_PER_NODE == 284
