@@ -13,7 +13,7 @@ LIB = os.path.join(HERE, "librtn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"]
-LIBS = ["-lcublas"]
+LIBS = []
 
 
 def sources():

@@ -116,16 +116,28 @@ struct Net {
   TcNet tc;
 };
 
-// Training buffers (allocated on the first rtn_train / rtn_mse_grad call).
+// Training buffers (allocated on the first rtn_train / rtn_mse_grad call;
+// train_tc.cu).  Per layer l = 0..L-1 the input activations A_l and per
+// layer output the loss gradient G_{l+1} = dLoss/dZ_{l+1}, each as BF16 hi +
+// lo pairs node-major [rows][ld] (K = features) and feature-major
+// [feature rows][ldf] (K = batch); the weights split hi + lo as W_l and its
+// transpose; the weight gradients as one partial product per batch range.
 struct TrainState {
-  int bs = 0;                          // minibatch size the buffers fit
-  std::vector<float*> act;             // A_0 .. A_L, [h_l][bs]
-  float *g0 = nullptr, *g1 = nullptr;  // backward signals [h_max][bs]
+  int cap = 0;                         // samples the buffers hold
+  int rows = 0, ldf = 0;               // node rows, feature-major row length (cap rounded up to 256)
+  int bs = 0;                          // samples the current plan runs on
+  std::vector<__nv_bfloat16*> an, af;  // A_l node-major hi, lo (an[2l], an[2l+1]), feature-major (af)
+  std::vector<__nv_bfloat16*> gn, gf;  // G_{l+1}: the same layouts
+  std::vector<__nv_bfloat16*> ws;      // W_l hi, lo, W_l' hi, lo (4 per layer)
+  float* z = nullptr;                  // output layer [cap][n_out]
+  float* part = nullptr;               // weight-gradient partials of every layer
+  std::vector<size_t> part_off;        // per layer
+  std::vector<int> ksplit;             // per layer
+  void* plan = nullptr;                // the step's planned GEMMs (train_tc.cu)
   float* grad = nullptr;               // dW (packed like W32) then db (like b32)
   float *m = nullptr, *v = nullptr;    // Adam moments, same packing
   size_t nw = 0, nb = 0, b_base = 0;
   long long t = 0;                     // Adam step counter
-  void* blas = nullptr;                // cuBLAS handle of the training GEMMs
 };
 
 }  // namespace rtn
@@ -295,12 +307,20 @@ struct QpArgs {
 };
 cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a);
 
-// a6
+// a6 (train.cu: targets; train_tc.cu: the training step on the tensor cores)
 cudaError_t drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y);
-cudaError_t train_step(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
-                       int start, float lr, float* loss);
+// buffers for minibatches of up to cap samples, the weight splits, and the
+// plan of a step on bs samples (err receives a description on failure)
+cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::string& err);
+// loss and gradient of the minibatch [start, start + ts.bs): weight-gradient
+// partials and db (into ts.grad); loss (device scalar) accumulated
 cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
                        int start, float* loss);
+// the partials summed into ts.grad (weights part)
+cudaError_t train_reduce(rtn_ctx* ctx, TrainState& ts);
+// one Adam step of every parameter from the partials and db, with the
+// weight splits refreshed
+cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr);
 void train_release(rtn_ctx* ctx);
 
 // a5
