@@ -447,6 +447,30 @@ def bench_box(prob, precision, tile, steps=20):
                 "not_converged": int((st == 8).sum())}}
 
 
+def bench_riccati(prob, precision, tile, steps=20):
+    """The headline closed loop with the other Riccati arithmetics: the FP32
+    sweep with the factorisation of R + B'PB and the gain solves in FP64
+    (riccati_f64 = 2) and the FP64 sweep (riccati_f64 = 1); RTI steps/s, the
+    QP kernel's time per call and tracking RMSE of each."""
+    out = {}
+    for name, ric in (("fp32_sweep_fp64_cholesky", "chol64"), ("fp64_sweep", 1)):
+        ctl = make(prob, precision, riccati_f64=ric)
+        if tile is not None:
+            ctl.tc_select(tile["variant"])
+        ms, _, rmse = time_closed_loop(ctl, prob, steps, 3)
+        x, u = ctl.get_iterate()
+        A, Bm, c = ctl.linearize(x, u)[2:]
+        xref, uref = W.node_refs(prob)
+        import torch
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+        args = (A, Bm, c, x, u, dev(xref), dev(uref), dev(prob["x0"]))
+        ms_qp = time_calls(lambda: ctl.qp_solve(*args), 5)
+        ctl.close()
+        out[name] = {"rti_steps_per_s": prob["B"] / (ms * 1e-3), "ms_per_step": ms, "ms_qp": ms_qp,
+                     "tracking_rmse_m": rmse}
+    return out
+
+
 def bench_learned(bf16_burst, epochs=2, steps=100):
     """cfg5: 2^20 seeded samples -> drag residual targets, train 17-512x6-3
     (Adam, lr 1e-3, batch 4096), then a 4096-instance closed loop on the drag
@@ -482,12 +506,13 @@ def bench_learned(bf16_burst, epochs=2, steps=100):
                             n, "-".join(map(str, w)), epochs, steps),
             "train_samples_per_s": epochs * (n // prob["cfg"]["batch"]) * prob["cfg"]["batch"] / t_train,
             "train_tflops": flops / t_train / 1e12,
-            "train_precision": "fp32 GEMMs emulated on the tensor cores (cuBLAS, 3 BF16 parts per operand), "
-                               "own bias/activation/loss/Adam kernels",
+            "train_precision": "own tcgen05 GEMMs (forward + bias/tanh, backward + tanh', weight gradient split "
+                               "over the batch) with BF16 hi + lo operands (3 MMAs per product), FP32 accumulation; "
+                               "fused Adam",
             "train_roofline": {"bound": "tensor", "peak": bf16_burst, "frac": flops / t_train / 1e12 / bf16_burst,
-                               "note": "peak = measured BF16 burst; the FP32 emulation issues several BF16 "
-                                       "products per algorithmic product, and the timing includes the Adam "
-                                       "launches and the final repack of the network"},
+                               "note": "peak = measured BF16 burst; the split operands issue 3 BF16 MMAs per "
+                                       "algorithmic product (frac <= 1/3), and the timing includes the loss, Adam "
+                                       "and gather launches and the final repack of the network"},
             "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
             "tracking_rmse_m": {"learned": rmse_l, "nominal": rmse_n}}
 
@@ -991,6 +1016,7 @@ def main():
         c32.close()
     if rank == 0 and world == 1 and not args.no_extra:
         line["box_qp"] = bench_box(prob, prec, cfg.get("tile"))
+        line["riccati_arithmetic"] = bench_riccati(prob, prec, cfg.get("tile"))
         line["ragged_batch"], ragged_smp = bench_ragged()
         line["learned_part"] = bench_learned(bf16_burst)
         line["runtime_analysis"] = bench_runtime_analysis()

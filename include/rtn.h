@@ -60,7 +60,9 @@ typedef enum {
 
 /* arithmetic of the network evaluation (a1) */
 enum {
-  RTN_FP32 = 0,   /* SIMT FP32 */
+  RTN_FP32 = 0,   /* FP32-accurate: tcgen05 kind::tf32 with weights and
+                     activations split hi + lo in TF32 (three MMAs per
+                     product), FP32 accumulation */
   RTN_BF16 = 1,   /* tcgen05, BF16 operands, FP32 accumulation, one pass */
   RTN_BF16X2 = 2  /* tcgen05, activations/tangents split hi+lo in BF16
                      (two passes), FP32 accumulation */
@@ -247,19 +249,25 @@ rtn_status rtn_drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y);
 
 /* (a6) Mean-squared-error loss 1/(no n) sum |f_D(x, u) - y|^2 of the context's
  * network on n samples (X dev [n][13], U dev [n][4], Y dev [n][no]) and its
- * gradient, FP32: grad dev [n_weights + n_biases] packed as all W[l]
- * (row-major, layer order) then all b[l]; loss dev float [1]. */
+ * gradient: grad dev float [n_weights + n_biases] packed as all W[l]
+ * (row-major, layer order) then all b[l]; loss dev float [1].  The GEMMs of
+ * rtn_train (split BF16 operands, FP32 accumulation: relative error ~1e-5)
+ * and FP32 elementwise steps. */
 rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,
                         float* grad, float* loss);
 
 /* (a6) Train the context's network in place (Sec. VI: MSE, Adam with
  * b1 = 0.9, b2 = 0.999, eps = 1e-8, bias correction): `epochs` passes over
  * the n samples in consecutive minibatches of `batch` (the remainder of each
- * pass is skipped), learning rate lr.  FP32 master weights, FP32 SIMT
- * forward/backward, one fused Adam launch per parameter block.  Adam state
- * persists across calls.  loss_out (host, may be NULL) receives the loss of
- * every step [epochs * (n / batch)].  Afterwards the tensor-core and plant
- * copies of the network are refreshed.  Synchronous. */
+ * pass is skipped), learning rate lr.  FP32 master weights; the forward,
+ * backward and weight-gradient GEMMs run on the tcgen05 tensor cores with
+ * BF16 hi + lo split operands (three MMAs per product) and FP32
+ * accumulation, their bias / tanh / tanh' epilogues fused; one fused Adam
+ * launch per weight matrix (which also refreshes the split weights) and one
+ * for the biases.  Adam state persists across calls.  loss_out (host, may be
+ * NULL) receives the loss of every step [epochs * (n / batch)].  Afterwards
+ * the network copies of the inference kernels and of the plant are
+ * refreshed.  Synchronous. */
 rtn_status rtn_train(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,
                      int epochs, int batch, float lr, float* loss_out);
 
@@ -370,7 +378,9 @@ rtn_status rtn_inject_wait_stall(rtn_ctx* ctx, int enable);
  * Requires 2 * max hidden width * 18 * n_nodes * 4 bytes <= 16 MiB, else
  * RTN_E_INVAL with the needed size in err.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * current, and looks it up again when the device's context has changed
+ * (after cudaDeviceReset); make that first call, and the first call after a
+ * reset, before any stream capture.  All calls share
  * the one array: calls whose kernels overlap on the GPU race on it.
  * Asynchronous on cuda_stream. */
 rtn_status rtn_mlp_eval_f32_noalloc(int n_layers, const int* widths, const float* W,

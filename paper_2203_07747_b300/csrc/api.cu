@@ -556,15 +556,31 @@ rtn_status rtn_rti_step_host(rtn_ctx* ctx, const float* x0, const float* xref, c
   auto& io = ctx->hio;
   const Layout& L = ctx->lay;
   const size_t bx0 = (size_t)L.B * NX * 4, bxr = (size_t)L.n_states * NX * 4, bur = (size_t)L.n_nodes * NU * 4;
-  if (!io.copy) {
-    CK(cudaStreamCreateWithFlags(&io.copy, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&io.free_ev, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&io.in_ev, cudaEventDisableTiming));
-    CK(cudaMalloc(&io.x0, bx0));
-    CK(cudaMalloc(&io.xref, bxr));
-    CK(cudaMalloc(&io.uref, bur));
-    CK(cudaMalloc(&io.u0, (size_t)L.B * NU * 4));
-    CK(cudaMalloc(&io.st, (size_t)L.B * 4));
+  if (!io.st) {
+    // set up on first use; a failure releases what was made, so that the
+    // next call starts over (io.st, made last, marks a complete set-up)
+    auto release = [&]() {
+      void* hp[] = {io.x0, io.xref, io.uref, io.u0};
+      for (void* p : hp)
+        if (p) cudaFree(p);
+      if (io.free_ev) cudaEventDestroy(io.free_ev);
+      if (io.in_ev) cudaEventDestroy(io.in_ev);
+      if (io.copy) cudaStreamDestroy(io.copy);
+      io = rtn_ctx::HostIO{};
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&io.copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.free_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io.in_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&io.x0, bx0);
+    if (e == cudaSuccess) e = cudaMalloc(&io.xref, bxr);
+    if (e == cudaSuccess) e = cudaMalloc(&io.uref, bur);
+    if (e == cudaSuccess) e = cudaMalloc(&io.u0, (size_t)L.B * NU * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&io.st, (size_t)L.B * 4);
+    if (e != cudaSuccess) {
+      release();
+      return fail(ctx, e == cudaErrorMemoryAllocation ? RTN_E_NOMEM : RTN_E_CUDA,
+                  std::string("rtn_rti_step_host set-up: ") + cudaGetErrorString(e));
+    }
   }
   // the inputs are read only by the QP: copy them on the side stream while
   // the network pass and RK4 run, once the previous step's QP has read the

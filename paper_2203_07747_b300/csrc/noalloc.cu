@@ -15,6 +15,9 @@
 // calls whose kernels overlap on the GPU (different streams, other threads)
 // race on it.  Its previous contents never matter: every element a kernel
 // reads was written earlier in the same call.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 #include <string>
 
@@ -29,15 +32,42 @@ static __device__ __align__(256) float g_noalloc_scratch[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// per device: the array's device address and the context it was looked up
+// in (a device reset makes a new primary context; the address is looked up
+// again there)
 float* g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
-// input layer for nodes given as separate rows x[n][13], u[n][4]
+// the calling thread's current driver context (null if none or unavailable)
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    looked = true;
+  }
+  CUcontext c = nullptr;
+  if (fn) fn(&c);
+  return c;
+}
+
+// input layer for nodes given as separate rows x[n][13], u[n][4]: one thread
+// per (neuron i, node n, column c) with c fastest, so that a warp stores
+// consecutive floats of the [h0][18 n_nodes] block (each thread recomputes
+// its node's 17-term dot product)
 __global__ void noalloc_in_kernel(const float* __restrict__ x, const float* __restrict__ u,
                                   int n_nodes, const float* __restrict__ W0,
                                   const float* __restrict__ b0, int h0, float* __restrict__ X1) {
-  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)h0 * n_nodes) return;
-  int i = (int)(tid / n_nodes), n = (int)(tid % n_nodes);
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per_row = (long long)NC * n_nodes;
+  if (tid >= (long long)h0 * per_row) return;
+  const int i = (int)(tid / per_row);
+  const long long r = tid % per_row;
+  const int n = (int)(r / NC), c = (int)(r % NC);
   const float* xr = x + (size_t)n * NX;
   const float* ur = u + (size_t)n * NU;
   const float* w = W0 + (size_t)i * NZ;
@@ -46,11 +76,8 @@ __global__ void noalloc_in_kernel(const float* __restrict__ x, const float* __re
   for (int j = 0; j < NX; ++j) s = fmaf(w[j], xr[j], s);
 #pragma unroll
   for (int j = 0; j < NU; ++j) s = fmaf(w[NX + j], ur[j], s);
-  float a = tanhf(s), d = 1.0f - a * a;
-  float* o = X1 + (size_t)i * ((size_t)NC * n_nodes) + (size_t)NC * n;
-  o[0] = a;
-#pragma unroll
-  for (int j = 0; j < NZ; ++j) o[1 + j] = d * w[j];
+  const float a = tanhf(s);
+  X1[(size_t)i * per_row + r] = c == 0 ? a : (1.0f - a * a) * w[c - 1];
 }
 
 rtn_status fail(char* err, size_t len, rtn_status st, const std::string& msg) {
@@ -85,7 +112,8 @@ extern "C" rtn_status rtn_mlp_eval_f32_noalloc(int n_layers, const int* widths, 
                 "buffer holds " + std::to_string((long long)RTN_NOALLOC_SCRATCH_BYTES) +
                 " (reduce n_nodes or the hidden width)");
 
-  // once per device, with that device current: the device address of the array
+  // once per device (and again after a device reset), with that device
+  // current: the device address of the array
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(err, err_len, RTN_E_CUDA, cudaGetErrorString(e));
@@ -93,12 +121,14 @@ extern "C" rtn_status rtn_mlp_eval_f32_noalloc(int n_layers, const int* widths, 
   float* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    const CUcontext cur = current_context();
+    if (!g_scratch_ptr[dev] || (cur && cur != g_scratch_ctx[dev])) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess)
         return fail(err, err_len, RTN_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_scratch_ptr[dev] = static_cast<float*>(p);
+      g_scratch_ctx[dev] = current_context();
     }
     scratch = g_scratch_ptr[dev];
   }
@@ -109,7 +139,7 @@ extern "C" rtn_status rtn_mlp_eval_f32_noalloc(int n_layers, const int* widths, 
   size_t wo = 0, bo = 0;
   {
     int h0 = widths[1];
-    long long tot = (long long)h0 * n_nodes;
+    long long tot = (long long)h0 * NC * n_nodes;
     noalloc_in_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, u, n_nodes, W, b, h0, cur);
     e = cudaGetLastError();
     wo += (size_t)h0 * NZ;
