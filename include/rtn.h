@@ -64,8 +64,19 @@ enum {
                      activations split hi + lo in TF32 (three MMAs per
                      product), FP32 accumulation */
   RTN_BF16 = 1,   /* tcgen05, BF16 operands, FP32 accumulation, one pass */
-  RTN_BF16X2 = 2  /* tcgen05, activations/tangents split hi+lo in BF16
+  RTN_BF16X2 = 2, /* tcgen05, activations/tangents split hi+lo in BF16
                      (two passes), FP32 accumulation */
+  RTN_FP8 = 3     /* tcgen05 kind::f8f6f4: every weight matrix quantised
+                     at create to e4m3 with a per-layer scale amax/448 (the
+                     context's network is then the dequantised one); the
+                     hidden->hidden GEMMs forward and backward multiply the
+                     e4m3 weights with activations / adjoints stored as three
+                     e4m3 pieces (hi + mid + lo, ~12 significant bits) in
+                     three MMAs with FP32 accumulation; the input layer, the
+                     folded first backward layer and the Jacobian GEMM as in
+                     RTN_BF16X2.  Layered reverse mode only (tile mode 6);
+                     3-output networks with at least one hidden->hidden
+                     layer */
 };
 
 /* plant residual used by rtn_plant_step / rtn_closed_loop */
@@ -98,7 +109,7 @@ typedef struct {
 } rtn_quad;
 
 typedef struct {
-  int precision;    /* RTN_FP32 / RTN_BF16 / RTN_BF16X2 */
+  int precision;    /* RTN_FP32 / RTN_BF16 / RTN_BF16X2 / RTN_FP8 */
   int riccati_f64;  /* Riccati sweep arithmetic: 0 FP32 (the Cholesky of
                        R + B'PB in FP32); 1 FP64 throughout; 2 FP32 with the
                        Cholesky of R + B'PB and the solves for the gains
@@ -286,7 +297,8 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
  * (RTN_E_UNSUPPORTED if it does not fit).  rtn_autotune: time every fitting
  * shape on the context's current iterate (synchronous; 1 warm-up + 3 timed
  * calls each), keep the fastest, return its index and time per call [ms].
- * Only for contexts created with RTN_BF16 / RTN_BF16X2. */
+ * Only for contexts created with RTN_BF16 / RTN_BF16X2 / RTN_FP8 (FP8: the
+ * layered shape only). */
 rtn_status rtn_tc_variants(rtn_ctx* ctx, int* count);
 rtn_status rtn_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages,
                                int* fits);

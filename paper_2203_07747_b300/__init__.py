@@ -14,7 +14,7 @@ import numpy as np
 from . import _build
 
 NX, NU, NZ, NO = 13, 4, 17, 3
-PRECISION = {"fp32": 0, "bf16": 1, "bf16x2": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "bf16x2": 2, "fp8": 3}
 PLANT = {"nominal": 0, "drag": 1, "mlp": 2}
 STATUS = {0: "RTN_OK", 1: "RTN_E_INVAL", 2: "RTN_E_CUDA", 3: "RTN_E_NONFINITE",
           4: "RTN_E_NOT_PD", 5: "RTN_E_TIMEOUT", 6: "RTN_E_NOMEM", 7: "RTN_E_UNSUPPORTED",

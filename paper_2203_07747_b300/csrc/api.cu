@@ -233,7 +233,7 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
   if (nn + batch > (1LL << 28)) { g_create_err = "batch too large"; return RTN_E_INVAL; }
   rtn_options o{RTN_FP32, 0, 1, 0, 0, 0};
   if (opt) o = *opt;
-  if (o.precision < RTN_FP32 || o.precision > RTN_BF16X2) { g_create_err = "bad precision"; return RTN_E_INVAL; }
+  if (o.precision < RTN_FP32 || o.precision > RTN_FP8) { g_create_err = "bad precision"; return RTN_E_INVAL; }
   if (o.box_max_iter < 0) { g_create_err = "box_max_iter must be >= 0"; return RTN_E_INVAL; }
   if (o.riccati_f64 < 0 || o.riccati_f64 > 2) { g_create_err = "riccati_f64 must be 0, 1 or 2"; return RTN_E_INVAL; }
   if (o.box_max_iter == 0) o.box_max_iter = 20;
@@ -273,6 +273,10 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
         (mlp->widths[mlp->n_layers] != NO && mlp->widths[mlp->n_layers] != NO_FULL)) {
       g_create_err = "network must map 17 inputs to 3 outputs (or 6: full residual) with >= 1 hidden layer";
       return RTN_E_INVAL;
+    }
+    if (o.precision == RTN_FP8 && mlp->n_layers < 3) {
+      g_create_err = "RTN_FP8 needs at least one hidden->hidden layer (the FP8 GEMMs)";
+      return RTN_E_UNSUPPORTED;
     }
     if (mlp->widths[mlp->n_layers] == NO_FULL && o.precision != RTN_FP32) {
       g_create_err = "the 6-output full residual runs on the FP32 path (the tensor-core kernels take 3 outputs)";
@@ -330,8 +334,12 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
         net.w_off.push_back(Wh.size());
         net.b_off.push_back(bh.size());
         Wh.insert(Wh.end(), mlp->W[l], mlp->W[l] + (size_t)fo * fi);
+        // RTN_FP8: the layer quantised to e4m3 with scale amax/448; the
+        // context's network is the dequantised one (every path and the plant
+        // see the same weights)
+        if (o.precision == RTN_FP8) net.fp8_scale.push_back(quantize_e4m3(Wh.data() + net.w_off[l], (size_t)fo * fi));
         bh.insert(bh.end(), mlp->b[l], mlp->b[l] + fo);
-        P64.insert(P64.end(), mlp->W[l], mlp->W[l] + (size_t)fo * fi);
+        P64.insert(P64.end(), Wh.begin() + net.w_off[l], Wh.begin() + net.w_off[l] + (size_t)fo * fi);
         P64.insert(P64.end(), mlp->b[l], mlp->b[l] + fo);
         net.h_max = std::max(net.h_max, std::max(fi, fo));
       }

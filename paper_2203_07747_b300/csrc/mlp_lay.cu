@@ -22,6 +22,8 @@
 // Tiles: M = 128 rows x N = 256 nodes (forward) or 80 nodes x 3 adjoints
 // (backward, Jacobian); persistent CTAs, K in stages of 64, two TMEM
 // accumulators so that the epilogue of one tile overlaps the next's MMAs.
+#include <cuda_fp8.h>
+
 #include <algorithm>
 
 #include "tc_common.cuh"
@@ -50,26 +52,35 @@ constexpr uint32_t LY_TMEM_COLS = 512;
 // padded to 32) with the forward epilogue
 enum { LY_FWD = 0, LY_BWD = 1, LY_JD = 2, LY_BW0 = 3, LY_IN = 4 };
 
-template <int MODE>
+// F8: the FP8 variant of the forward and backward hidden GEMMs (RTN_FP8):
+// e4m3 weights against activations / adjoints held as three e4m3 pieces, K
+// blocks of 64 one-byte elements (the same 64 B rows), three B tiles per
+// stage and three kind::f8f6f4 MMAs per K step
+template <int MODE, bool F8 = false>
 struct Ly {
   static constexpr bool ACT = MODE == LY_FWD || MODE == LY_IN;      // tanh epilogue
   static constexpr bool BYNODE = ACT || MODE == LY_BW0;             // one column per node
   static constexpr int N = BYNODE ? LY_NF : 3 * LY_NBN;            // MMA N
   static constexpr int NODES = BYNODE ? LY_NF : LY_NBN;            // nodes per tile
   static constexpr int NA = (MODE == LY_JD || MODE == LY_BW0 || MODE == LY_IN) ? 2 : 1;  // weight tiles (hi, lo)
+  static constexpr int NB = F8 ? 3 : 2;                             // B tiles: pieces
+  static constexpr int KB = F8 ? 64 : LY_KB;                        // K elements per stage
 };
-template <int MODE>
-__host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * LY_KB * 2u; }
-template <int MODE>
-__host__ __device__ constexpr uint32_t ly_stage() { return Ly<MODE>::NA * LY_A_BYTES + 2u * ly_b_bytes<MODE>(); }
-template <int MODE>
-__host__ __device__ constexpr size_t ly_smem() { return LY_STAGES * ly_stage<MODE>() + 1024 + 256; }
+template <int MODE, bool F8 = false>
+__host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * 64u; }
+template <int MODE, bool F8 = false>
+__host__ __device__ constexpr uint32_t ly_stage() {
+  return Ly<MODE, F8>::NA * LY_A_BYTES + Ly<MODE, F8>::NB * ly_b_bytes<MODE>();
+}
+template <int MODE, bool F8 = false>
+__host__ __device__ constexpr size_t ly_smem() { return LY_STAGES * ly_stage<MODE, F8>() + 1024 + 256; }
 static_assert(ly_b_bytes<LY_FWD>() % 1024 == 0 && ly_b_bytes<LY_BWD>() % 1024 == 0, "1 KB aligned tiles");
-static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448 && ly_smem<LY_BW0>() <= 232448,
+static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448 && ly_smem<LY_BW0>() <= 232448 &&
+                  ly_smem<LY_FWD, true>() <= 232448 && ly_smem<LY_BWD, true>() <= 232448,
               "shared memory");
 
 struct LyMaps {
-  CUtensorMap bh, bl;  // activations / adjoints hi, lo
+  CUtensorMap bh, bl, b3;  // activations / adjoints hi, lo (F8: hi, mid, lo)
 };
 
 struct LyArgs {
@@ -92,7 +103,69 @@ struct LyArgs {
   int* err;
   long long wait_cycles;  // budget of every bounded pipeline wait [SM cycles]
   int stall;              // fault injection: the TMA producer first waits on a barrier nothing completes
+  // RTN_FP8: F8 GEMMs scale the accumulator by sc (weight scale over the
+  // B operand's scale); y8 (if set) receives the output as three e4m3
+  // pieces of (value * s8); a8: the F8 backward GEMM's a_l pieces (a * 448)
+  float sc, s8;
+  uint8_t *y8h, *y8m, *y8l;
+  const uint8_t *a8h, *a8m, *a8l;
 };
+
+// four values as e4m3 pieces, four codes per word (byte k = value k): wh the
+// roundings, wm the roundings of the residuals, wl of the residuals' residuals
+__device__ __forceinline__ void split3x4(const float* v, uint32_t& wh, uint32_t& wm, uint32_t& wl) {
+  float r[4] = {v[0], v[1], v[2], v[3]};
+  uint32_t w[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const uint32_t a = __nv_cvt_float2_to_fp8x2(make_float2(r[0], r[1]), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t b = __nv_cvt_float2_to_fp8x2(make_float2(r[2], r[3]), __NV_SATFINITE, __NV_E4M3);
+    w[p] = a | (b << 16);
+    if (p < 2) {
+      const float2 fa = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)a, __NV_E4M3)));
+      const float2 fb = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)b, __NV_E4M3)));
+      r[0] -= fa.x; r[1] -= fa.y; r[2] -= fb.x; r[3] -= fb.y;
+    }
+  }
+  wh = w[0]; wm = w[1]; wl = w[2];
+}
+
+// the four values of a word of e4m3 codes
+__device__ __forceinline__ void e4m3x4(uint32_t w, float* f) {
+  const float2 a = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3)));
+  const float2 b = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3)));
+  f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y;
+}
+
+// 4 x 4 byte transpose across the lanes of a quad (t = lane & 3): lane t
+// holds a word whose byte k is element (t, k); returns the word whose byte
+// k is element (k, t).  An epilogue lane owns one output row for several
+// nodes; after the transpose it owns four rows of one node, which it stores
+// (or, for loads, the reverse) as one 4-byte word.
+__device__ __forceinline__ uint32_t quad_transpose(uint32_t x, int t) {
+  const uint32_t y = __shfl_xor_sync(0xffffffffu, x, 2);
+  x = (t & 2) ? __byte_perm(x, y, 0x3276) : __byte_perm(x, y, 0x5410);
+  const uint32_t z = __shfl_xor_sync(0xffffffffu, x, 1);
+  return (t & 1) ? __byte_perm(x, z, 0x3715) : __byte_perm(x, z, 0x6240);
+}
+
+// 4 m .. 4 m + 3 of a lane's values (one row, consecutive nodes) as e4m3
+// pieces, stored through quad transposes: lane t writes the word of rows
+// i & ~3 .. + 3 of node n0 + t at dst_p + (n0 + t) * stride + (i & ~3)
+__device__ __forceinline__ void store_pieces4(const float* v, int t, int n0, int n_nodes, size_t stride, int i4,
+                                              uint8_t* dh, uint8_t* dm, uint8_t* dl) {
+  uint32_t wh, wm, wl;
+  split3x4(v, wh, wm, wl);
+  wh = quad_transpose(wh, t);
+  wm = quad_transpose(wm, t);
+  wl = quad_transpose(wl, t);
+  if (n0 + t < n_nodes) {
+    const size_t o = (size_t)(n0 + t) * stride + i4;
+    *reinterpret_cast<uint32_t*>(dh + o) = wh;
+    *reinterpret_cast<uint32_t*>(dm + o) = wm;
+    *reinterpret_cast<uint32_t*>(dl + o) = wl;
+  }
+}
 
 __device__ __forceinline__ void split_bf(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
   h = __float2bfloat16_rn(v);
@@ -155,13 +228,81 @@ __device__ __forceinline__ void bwd_group(const float (&v)[48], const __nv_bfloa
   }
 }
 
+// F8 backward: a_l (= pieces / 448) of the 8 nodes the warp of half H
+// stores in the 16-node group starting at node_g, for the lane's row: each
+// lane loads the words of rows i & ~3 .. + 3 of one node per piece and quad
+// transposes turn them into the lane's row for four nodes (one word per
+// piece and four nodes, byte k = node k)
+template <int H>
+__device__ __forceinline__ void bwd_load8(const LyArgs& a, int node_g, int i, int t, uint32_t (&w)[6]) {
+  const int i4 = i & ~3;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const size_t o = (size_t)min(node_g + 8 * H + 4 * m + t, a.n_nodes - 1) * a.hs + i4;
+    w[3 * m] = *reinterpret_cast<const uint32_t*>(a.a8h + o);
+    w[3 * m + 1] = *reinterpret_cast<const uint32_t*>(a.a8m + o);
+    w[3 * m + 2] = *reinterpret_cast<const uint32_t*>(a.a8l + o);
+  }
+}
+
+// F8 backward epilogue of one 16-node group: D = acc * sc * d, d = 1 - a^2,
+// stored as e4m3 pieces of D * s8 (y8, through quad transposes) or as BF16
+// hi + lo (yh, yl)
+template <int H>
+__device__ __forceinline__ void bwd_group8(const float (&v)[48], const uint32_t (&w)[6], int node_g, int i, int t,
+                                           bool active, const LyArgs& a) {
+  constexpr float inv448 = 1.0f / 448.0f;
+  float dv[8];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    float ah[4], am[4], al[4];
+    e4m3x4(quad_transpose(w[3 * m], t), ah);
+    e4m3x4(quad_transpose(w[3 * m + 1], t), am);
+    e4m3x4(quad_transpose(w[3 * m + 2], t), al);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float av = (ah[k] + am[k] + al[k]) * inv448;
+      dv[4 * m + k] = active ? (1.0f - av * av) * a.sc : 0.0f;
+    }
+  }
+  if (a.y8h) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        float d4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d4[k] = v[3 * (8 * H + 4 * m + k) + r] * dv[4 * m + k] * a.s8;
+        // node n = node_g + 8H + 4m + t, row block i & ~3, component r
+        const int n0 = node_g + 8 * H + 4 * m;
+        store_pieces4(d4, t, n0, a.n_nodes, (size_t)3 * a.hs, (i & ~3) + r * a.hs, a.y8h, a.y8m, a.y8l);
+      }
+    return;
+  }
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const int k = 8 * H + kk, node = node_g + k;
+    if (active && node < a.n_nodes) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const size_t o = ((size_t)node * 3 + r) * a.hs + i;
+        __nv_bfloat16 h, l;
+        split_bf(v[3 * k + r] * dv[kk], h, l);
+        a.yh[o] = h;
+        a.yl[o] = l;
+      }
+    }
+  }
+}
+
 // one GEMM layer over all nodes (see the file comment); MODE selects the
 // operands' shape and the epilogue
-template <int MODE>
+template <int MODE, bool F8 = false>
 __global__ void __launch_bounds__(LY_THREADS, 1)
     lay_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ LyMaps bm, LyArgs a) {
-  using T = Ly<MODE>;
-  constexpr uint32_t B_BYTES = ly_b_bytes<MODE>(), STAGE = ly_stage<MODE>();
+  using T = Ly<MODE, F8>;
+  static_assert(!F8 || MODE == LY_FWD || MODE == LY_BWD, "FP8 hidden GEMMs only");
+  constexpr uint32_t B_BYTES = ly_b_bytes<MODE>(), STAGE = ly_stage<MODE, F8>();
   constexpr uint32_t B0 = T::NA * LY_A_BYTES;  // offset of the B tiles in a stage
   extern __shared__ uint8_t smem_raw[];
   const uint32_t sraw = smem_u32(smem_raw);
@@ -227,11 +368,12 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
         if (elect_one()) {
           const uint32_t sa = st0 + s * STAGE;
           mbar_expect_tx(full_bar(s), STAGE);
-          tma_load_2d(sa, &amap, kb * LY_KB, a.a_row0 + mt * 128, full_bar(s));
+          tma_load_2d(sa, &amap, kb * T::KB, a.a_row0 + mt * 128, full_bar(s));
           if (T::NA == 2)
-            tma_load_2d(sa + LY_A_BYTES, &amap, kb * LY_KB, a.a_row0 + a.a_lo + mt * 128, full_bar(s));
-          tma_load_2d(sa + B0, &bm.bh, kb * LY_KB, a.b_row0 + grp * T::N, full_bar(s));
-          tma_load_2d(sa + B0 + B_BYTES, &bm.bl, kb * LY_KB, a.b_row0 + grp * T::N, full_bar(s));
+            tma_load_2d(sa + LY_A_BYTES, &amap, kb * T::KB, a.a_row0 + a.a_lo + mt * 128, full_bar(s));
+          tma_load_2d(sa + B0, &bm.bh, kb * T::KB, a.b_row0 + grp * T::N, full_bar(s));
+          tma_load_2d(sa + B0 + B_BYTES, &bm.bl, kb * T::KB, a.b_row0 + grp * T::N, full_bar(s));
+          if (F8) tma_load_2d(sa + B0 + 2 * B_BYTES, &bm.b3, kb * T::KB, a.b_row0 + grp * T::N, full_bar(s));
         }
         __syncwarp();
         issued |= 1u << s;
@@ -247,7 +389,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       }
   } else if (warp == 1) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(128, T::N);  // both operands K-major
+    constexpr uint32_t idesc = F8 ? idesc_e4m3(128, T::N) : idesc_bf16(128, T::N);  // both operands K-major
     int s = 0, acc = 0;
     uint32_t ph = 0, aph = 0;
     bool ok = true;
@@ -259,14 +401,22 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
         if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err, a.wait_cycles))) break;
         tc_fence_after();
         const uint32_t sa = st0 + s * STAGE;
+        // two K steps per 64 B row: 16 BF16 or 32 e4m3 elements each
 #pragma unroll
-        for (int ks = 0; ks < LY_KB / 16; ++ks) {
+        for (int ks = 0; ks < 2; ++ks) {
           const uint64_t ah = kmajor_desc(sa + ks * 32u, LY_SBO, LY_SWZ);
           const uint64_t bh = kmajor_desc(sa + B0 + ks * 32u, LY_SBO, LY_SWZ);
           const uint64_t bl = kmajor_desc(sa + B0 + B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
-          mma_bf16_elect(d, ah, bh, idesc, (kb | ks) != 0);
-          mma_bf16_elect(d, ah, bl, idesc, 1u);
-          if (T::NA == 2) mma_bf16_elect(d, kmajor_desc(sa + LY_A_BYTES + ks * 32u, LY_SBO, LY_SWZ), bh, idesc, 1u);
+          if constexpr (F8) {
+            const uint64_t b3 = kmajor_desc(sa + B0 + 2 * B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+            mma_f8_elect(d, ah, bh, idesc, (kb | ks) != 0);
+            mma_f8_elect(d, ah, bl, idesc, 1u);
+            mma_f8_elect(d, ah, b3, idesc, 1u);
+          } else {
+            mma_bf16_elect(d, ah, bh, idesc, (kb | ks) != 0);
+            mma_bf16_elect(d, ah, bl, idesc, 1u);
+            if (T::NA == 2) mma_bf16_elect(d, kmajor_desc(sa + LY_A_BYTES + ks * 32u, LY_SBO, LY_SWZ), bh, idesc, 1u);
+          }
         }
         mma_commit_elect(empty_bar(s));
         if (++s == LY_STAGES) { s = 0; ph ^= 1u; }
@@ -300,17 +450,50 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       // accumulator is still being computed, each later group's while the
       // one before it is stored
       __nv_bfloat16 ph[8], pl[8], qh[16], ql[16];
-      if (MODE == LY_BWD) {
+      uint32_t p8[6];
+      const int tq = lane & 3;
+      if (MODE == LY_BWD && !F8) {
         if (half == 0)
           bwd_load<0>(a.ah, a.al, node0, a.n_nodes, a.hs, ic, ph, pl);
         else
           bwd_load<1>(a.ah, a.al, node0, a.n_nodes, a.hs, ic, ph, pl);
       }
+      if (MODE == LY_BWD && F8) {
+        if (half == 0)
+          bwd_load8<0>(a, node0, ic, tq, p8);
+        else
+          bwd_load8<1>(a, node0, ic, tq, p8);
+      }
       if (MODE == LY_BW0) chunk_load(a.ah, a.al, node0 + 16 * half, a.n_nodes, a.hs, ic, qh, ql);
       if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err, a.wait_cycles)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
-      if (MODE == LY_BWD) {
+      if (MODE == LY_BWD && F8) {
+#pragma unroll
+        for (int g = 0; g < T::NODES / 16; ++g) {
+          float v[48];
+          tmem_ld16(taddr + 48 * g, v);
+          tmem_ld16(taddr + 48 * g + 16, v + 16);
+          tmem_ld16(taddr + 48 * g + 32, v + 32);
+          uint32_t n8[6];
+          if (g + 1 < T::NODES / 16) {
+            if (half == 0)
+              bwd_load8<0>(a, node0 + 16 * (g + 1), ic, tq, n8);
+            else
+              bwd_load8<1>(a, node0 + 16 * (g + 1), ic, tq, n8);
+          }
+          tmem_wait_ld();
+          if (half == 0)
+            bwd_group8<0>(v, p8, node0 + 16 * g, i, tq, active, a);
+          else
+            bwd_group8<1>(v, p8, node0 + 16 * g, i, tq, active, a);
+          if (g + 1 < T::NODES / 16) {
+#pragma unroll
+            for (int q8 = 0; q8 < 6; ++q8) p8[q8] = n8[q8];
+          }
+        }
+      }
+      if (MODE == LY_BWD && !F8) {
         // 16-node groups: both warps of the quarter read the group's 48
         // columns, each stores its 8 nodes
 #pragma unroll
@@ -349,7 +532,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
         if (T::ACT) {
           float av[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) av[k] = v[k] + bi;
+          for (int k = 0; k < 16; ++k) av[k] = (F8 ? v[k] * a.sc : v[k]) + bi;
           tanh_batch<16>(av);
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
@@ -362,9 +545,21 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
                 a.dh[o] = h;
                 a.dl[o] = l;
               }
-              split_bf(av[k], h, l);
-              a.yh[o] = h;
-              a.yl[o] = l;
+              if (a.yh) {
+                split_bf(av[k], h, l);
+                a.yh[o] = h;
+                a.yl[o] = l;
+              }
+            }
+          }
+          if (a.y8h) {  // RTN_FP8: a * 448 as e4m3 pieces, four nodes per store
+            const int tq = lane & 3;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              float a4[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) a4[k] = active ? av[4 * m + k] * 448.0f : 0.0f;
+              store_pieces4(a4, tq, node0 + 16 * ch + 4 * m, a.n_nodes, a.hs, i & ~3, a.y8h, a.y8m, a.y8l);
             }
           }
         } else if (MODE == LY_BW0) {
@@ -376,15 +571,27 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
             const float av = __bfloat162float(qh[k]) + __bfloat162float(ql[k]);
             dv[k] = 1.0f - av * av;
           }
+          if (a.y8h) {  // RTN_FP8: D * s8 as e4m3 pieces, four nodes per store
+            const int tq = lane & 3;
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int node = node0 + 16 * ch + k;
-            if (active && node < a.n_nodes) {
-              const size_t o = ((size_t)node * 3 + r0) * a.hs + i;
-              __nv_bfloat16 h, l;
-              split_bf(v[k] * dv[k], h, l);
-              a.yh[o] = h;
-              a.yl[o] = l;
+            for (int m = 0; m < 4; ++m) {
+              float d4[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) d4[k] = active ? v[4 * m + k] * dv[4 * m + k] * a.s8 : 0.0f;
+              store_pieces4(d4, tq, node0 + 16 * ch + 4 * m, a.n_nodes, (size_t)3 * a.hs, (i & ~3) + r0 * a.hs,
+                            a.y8h, a.y8m, a.y8l);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int node = node0 + 16 * ch + k;
+              if (active && node < a.n_nodes) {
+                const size_t o = ((size_t)node * 3 + r0) * a.hs + i;
+                __nv_bfloat16 h, l;
+                split_bf(v[k] * dv[k], h, l);
+                a.yh[o] = h;
+                a.yl[o] = l;
+              }
             }
           }
           if (ch + 2 < T::N / 16) {
@@ -552,6 +759,18 @@ __global__ void __launch_bounds__(256) lay_fd_kernel(const float* __restrict__ W
 
 }  // namespace
 
+float quantize_e4m3(float* w, size_t n) {
+  float amax = 0.0f;
+  for (size_t i = 0; i < n; ++i) amax = std::max(amax, std::fabs(w[i]));
+  if (!(amax > 0.0f)) return 1.0f;
+  const float sc = amax / 448.0f;
+  for (size_t i = 0; i < n; ++i) {
+    const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(w[i] / sc, __NV_SATFINITE, __NV_E4M3);
+    w[i] = sc * __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3)));
+  }
+  return sc;
+}
+
 const void* mlp_lay_fn() { return reinterpret_cast<const void*>(&lay_kernel<LY_FWD>); }
 size_t mlp_lay_smem() { return std::max(std::max(ly_smem<LY_JD>(), ly_smem<LY_BW0>()), ly_smem<LY_IN>()); }
 
@@ -570,6 +789,7 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   tc.lay = s;
   s->hs = HP;
   s->npad = (int)npad;
+  s->fp8 = ctx->opt.precision == RTN_FP8;
   cudaError_t e;
   for (int b = 0; b < 2; ++b)
     for (int p = 0; p < 2; ++p) {
@@ -618,7 +838,10 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
     for (int r = 0; r < NO; ++r)
       for (int k = 0; k < hk; ++k)
         for (int i = 0; i < hi_; ++i) {
-          const float m = __bfloat162float(__float2bfloat16_rn(Wa[(size_t)i * hk + k])) * Wl[(size_t)r * hi_ + i];
+          // the hidden weight as the other BF16 GEMMs see it (RTN_FP8: the
+          // dequantised weight itself)
+          const float wa = s->fp8 ? Wa[(size_t)i * hk + k] : __bfloat162float(__float2bfloat16_rn(Wa[(size_t)i * hk + k]));
+          const float m = wa * Wl[(size_t)r * hi_ + i];
           const __nv_bfloat16 h = __float2bfloat16_rn(m);
           M[((size_t)r * HP + k) * HP + i] = h;
           M[((size_t)(3 + r) * HP + k) * HP + i] = __float2bfloat16_rn(m - __bfloat162float(h));
@@ -684,6 +907,89 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   if ((e = cudaFuncSetAttribute(lay_kernel<LY_BW0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ly_smem<LY_BW0>())) != cudaSuccess)
     return e;
+  if (s->fp8 && nh >= 1) {
+    // e4m3 codes of the hidden->hidden weights and their transposes
+    std::vector<uint8_t> q((size_t)nh * HP * HP, 0), qt((size_t)nh * HP * HP, 0);
+    for (int l = 1; l <= nh; ++l) {
+      const int fi = net.widths[l], fo = net.widths[l + 1];
+      std::vector<float> Wl((size_t)fo * fi);
+      if ((e = cudaMemcpy(Wl.data(), net.W32 + net.w_off[l], Wl.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+      const float sc = net.fp8_scale[l];
+      for (int i = 0; i < fo; ++i)
+        for (int k = 0; k < fi; ++k) {
+          const uint8_t c = (uint8_t)__nv_cvt_float_to_fp8(Wl[(size_t)i * fi + k] / sc, __NV_SATFINITE, __NV_E4M3);
+          q[((size_t)(l - 1) * HP + i) * HP + k] = c;
+          qt[((size_t)(l - 1) * HP + k) * HP + i] = c;
+        }
+    }
+    if ((e = cudaMalloc(&s->q8, q.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(s->q8, q.data(), q.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s->q8t, qt.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(s->q8t, qt.data(), qt.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    for (int p = 0; p < 3; ++p) {
+      const size_t ab = (size_t)(L - 1) * npad * HP, bb = (size_t)3 * npad * HP;
+      if ((e = cudaMalloc(&s->act8[p], ab)) != cudaSuccess) return e;
+      if ((e = cudaMemset(s->act8[p], 0, ab)) != cudaSuccess) return e;
+      for (int b = 0; b < 2; ++b) {
+        if ((e = cudaMalloc(&s->xb8[b][p], bb)) != cudaSuccess) return e;
+        if ((e = cudaMemset(s->xb8[b][p], 0, bb)) != cudaSuccess) return e;
+      }
+    }
+    // scales of the adjoints kept in e4m3 (D_l, l = 2 .. L-2): 448 / (8 x the
+    // largest element of the adjoints of the linearised network (d = 1),
+    // D_{L-1}[r] = W_{L-1}[r], D_l = W_l' D_{l+1}), so that typical
+    // adjoints sit well inside e4m3's range with 8x headroom
+    s->adj_scale.assign(L, 1.0f);
+    {
+      const int hl = net.widths[L - 1];
+      std::vector<double> D((size_t)NO * hl);
+      std::vector<float> WL((size_t)NO * hl);
+      if ((e = cudaMemcpy(WL.data(), net.W32 + net.w_off[L - 1], WL.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+      for (size_t i = 0; i < D.size(); ++i) D[i] = WL[i];
+      for (int l = L - 2; l >= 2; --l) {
+        const int fi = net.widths[l], fo = net.widths[l + 1];
+        std::vector<float> Wl((size_t)fo * fi);
+        if ((e = cudaMemcpy(Wl.data(), net.W32 + net.w_off[l], Wl.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+          return e;
+        std::vector<double> Dn((size_t)NO * fi, 0.0);
+        double amax = 0.0;
+        for (int r = 0; r < NO; ++r)
+          for (int i = 0; i < fi; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < fo; ++k) acc += (double)Wl[(size_t)k * fi + i] * D[(size_t)r * fo + k];
+            Dn[(size_t)r * fi + i] = acc;
+            amax = std::max(amax, std::fabs(acc));
+          }
+        s->adj_scale[l] = amax > 0.0 ? (float)(448.0 / (8.0 * amax)) : 1.0f;
+        D.swap(Dn);
+      }
+    }
+    auto enc8 = [&](void* mp, void* ptr, long long rows, int box_rows) -> bool {
+      const cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)rows};
+      const cuuint64_t str[1] = {(cuuint64_t)HP};
+      const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+      return encode(reinterpret_cast<CUtensorMap*>(mp), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ptr, dims, str, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    bool ok = enc8(s->q8map, s->q8, (long long)nh * HP, 128) && enc8(s->q8tmap, s->q8t, (long long)nh * HP, 128);
+    for (int p = 0; p < 3 && ok; ++p) {
+      ok = enc8(s->a8map[p], s->act8[p], (long long)(L - 1) * npad, LY_NF);
+      for (int b = 0; b < 2 && ok; ++b) ok = enc8(s->b8map[b][p], s->xb8[b][p], 3 * npad, 3 * LY_NBN);
+    }
+    if (!ok) {
+      err = "cuTensorMapEncodeTiled failed (FP8 operands)";
+      return cudaSuccess;
+    }
+    if ((e = cudaFuncSetAttribute(lay_kernel<LY_FWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ly_smem<LY_FWD, true>())) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(lay_kernel<LY_BWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ly_smem<LY_BWD, true>())) != cudaSuccess)
+      return e;
+  }
   if ((e = cudaFuncSetAttribute(lay_kernel<LY_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ly_smem<LY_FWD>())) != cudaSuccess)
     return e;
@@ -708,6 +1014,13 @@ void mlp_lay_release(rtn_ctx* ctx) {
     if (s->z[p]) cudaFree(s->z[p]);
   for (int p = 0; p < 2; ++p)
     if (s->dd[p]) cudaFree(s->dd[p]);
+  if (s->q8) cudaFree(s->q8);
+  if (s->q8t) cudaFree(s->q8t);
+  for (int p = 0; p < 3; ++p) {
+    if (s->act8[p]) cudaFree(s->act8[p]);
+    for (int b = 0; b < 2; ++b)
+      if (s->xb8[b][p]) cudaFree(s->xb8[b][p]);
+  }
   delete s;
   ctx->net.tc.lay = nullptr;
 }
@@ -732,6 +1045,15 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
   auto grid_of = [&](long long tiles) { return (int)std::min<long long>(tiles, std::max(1, tc.n_sm)); };
   const long long budget = tc.wait_cycles > 0 ? tc.wait_cycles : WAIT_CYCLES;
   const int stall = tc.inject_stall;
+  const bool fp8 = s->fp8 && nh >= 1;
+  const size_t dstride8 = (size_t)s->npad * hs;  // one layer of an FP8 piece array (bytes)
+  auto maps8 = [&](unsigned char (&m)[3][128]) {
+    LyMaps r;
+    memcpy(&r.bh, m[0], sizeof(CUtensorMap));
+    memcpy(&r.bl, m[1], sizeof(CUtensorMap));
+    memcpy(&r.b3, m[2], sizeof(CUtensorMap));
+    return r;
+  };
   // an event before each launch when the pass is timed
   s->n_marks = 0;
   auto mark = [&](int kind) {
@@ -758,6 +1080,11 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.bias = tc.b0;
     a.yh = s->act[0];
     a.yl = s->act[1];
+    if (fp8) {
+      a.y8h = s->act8[0];
+      a.y8m = s->act8[1];
+      a.y8l = s->act8[2];
+    }
     a.err = tc.err;
     a.wait_cycles = budget;
     a.stall = stall;
@@ -788,8 +1115,21 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.wait_cycles = budget;
     a.stall = stall;
     mark(2);
-    lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD>(), st>>>(
-        *wmap, maps(s->ma[0], s->ma[1]), a);
+    if (fp8) {
+      // e4m3 W_{g+1} against the pieces of 448 a_{g+1}; a_{g+2} out as pieces,
+      // and as BF16 hi + lo where a BF16 GEMM reads it (a_{L-2}, a_{L-1})
+      a.nkb = HP / 64;
+      a.sc = net.fp8_scale[g + 1] / 448.0f;
+      a.y8h = s->act8[0] + (size_t)(g + 1) * dstride8;
+      a.y8m = s->act8[1] + (size_t)(g + 1) * dstride8;
+      a.y8l = s->act8[2] + (size_t)(g + 1) * dstride8;
+      if (g < nh - 2) a.yh = a.yl = nullptr;
+      lay_kernel<LY_FWD, true><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD, true>(), st>>>(
+          *reinterpret_cast<const CUtensorMap*>(s->q8map), maps8(s->a8map), a);
+    } else {
+      lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD>(), st>>>(
+          *wmap, maps(s->ma[0], s->ma[1]), a);
+    }
   }
   // f_D (and, with no hidden->hidden layer, the last layer's adjoints into
   // adjoint buffer 0)
@@ -823,6 +1163,13 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.al = s->act[1] + (size_t)(L - 3) * dstride;
     a.yh = s->xb[0][0];
     a.yl = s->xb[0][1];
+    if (fp8 && nh >= 2) {  // D_{L-2} feeds an FP8 backward GEMM: e4m3 pieces
+      a.yh = a.yl = nullptr;
+      a.y8h = s->xb8[0][0];
+      a.y8m = s->xb8[0][1];
+      a.y8l = s->xb8[0][2];
+      a.s8 = s->adj_scale[L - 2];
+    }
     a.err = tc.err;
     a.wait_cycles = budget;
     a.stall = stall;
@@ -854,8 +1201,29 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     a.wait_cycles = budget;
     a.stall = stall;
     mark(5);
-    lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD>(), st>>>(
-        *rmap, maps(s->mb[src][0], s->mb[src][1]), a);
+    if (fp8) {
+      // e4m3 W_l' against the pieces of D_{l+1} * s_{l+1}; d_l from the pieces
+      // of 448 a_l; D_l out as pieces (scale s_l) or, for the Jacobian GEMM
+      // (l = 1), as BF16 hi + lo
+      a.nkb = HP / 64;
+      a.sc = net.fp8_scale[l] / s->adj_scale[l + 1];
+      a.a8h = s->act8[0] + (size_t)(l - 1) * dstride8;
+      a.a8m = s->act8[1] + (size_t)(l - 1) * dstride8;
+      a.a8l = s->act8[2] + (size_t)(l - 1) * dstride8;
+      if (l >= 2) {
+        a.yh = a.yl = nullptr;
+        a.y8h = s->xb8[dst][0];
+        a.y8m = s->xb8[dst][1];
+        a.y8l = s->xb8[dst][2];
+        a.s8 = s->adj_scale[l];
+      }
+      a.a_row0 = (l - 1) * HP;
+      lay_kernel<LY_BWD, true><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD, true>(), st>>>(
+          *reinterpret_cast<const CUtensorMap*>(s->q8tmap), maps8(s->b8map[src]), a);
+    } else {
+      lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD>(), st>>>(
+          *rmap, maps(s->mb[src][0], s->mb[src][1]), a);
+    }
   }
   // J_D = W_0' D_1 (W_0' hi and lo rows)
   {

@@ -460,6 +460,14 @@ int default_variant(int HP, bool split) {
   return best;
 }
 
+// the layered reverse-mode shape (tile mode 6), the only one of RTN_FP8
+int layered_variant(int HP) {
+  const auto& vs = all_variants();
+  for (int i = 0; i < (int)vs.size(); ++i)
+    if (vs[i].mode == 6 && fits(vs[i], HP)) return i;
+  return -1;
+}
+
 uint16_t f2bf(float f) {
   uint32_t u;
   memcpy(&u, &f, 4);
@@ -507,8 +515,8 @@ cudaError_t mlp_tc_prepare(rtn_ctx* ctx, std::string& err) {
   tc.h_pad = HP;
   tc.n_mm = nh;
   tc.rows_total = nh * HP + 256;  // output layer padded to one 256-row pair tile
-  const bool split = ctx->opt.precision == RTN_BF16X2;
-  const int vi = default_variant(HP, split);
+  const bool split = ctx->opt.precision != RTN_BF16;
+  const int vi = ctx->opt.precision == RTN_FP8 ? layered_variant(HP) : default_variant(HP, split);
   if (vi < 0) {
     err = "no tensor-core tile configuration fits";
     return cudaSuccess;
@@ -672,7 +680,8 @@ int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages
   if (npc) *npc = vs[idx].npc;
   if (split) *split = vs[idx].mode;
   if (stages) *stages = vs[idx].stages;
-  const bool want = ctx->opt.precision == RTN_BF16X2;
+  const bool want = ctx->opt.precision != RTN_BF16;
+  if (ctx->opt.precision == RTN_FP8 && vs[idx].mode != 6) return 1;
   return (vs[idx].split() == want && fits(vs[idx], ctx->net.tc.h_pad)) ? 0 : 1;
 }
 

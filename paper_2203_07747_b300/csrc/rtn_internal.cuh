@@ -78,6 +78,18 @@ struct LayState {
   alignas(64) unsigned char wmap[128];      // the stacked forward weights, box 32 x 128
   alignas(64) unsigned char rmap[128];      // the reverse-mode weight stack, box 32 x 128
   alignas(64) unsigned char mdd[2][128];    // d_{L-1}, box 32 x 256
+  // RTN_FP8: e4m3 codes of the hidden->hidden weights W_1 .. W_{L-2} [nh HP][HP]
+  // and of their transposes; activations a_1 .. a_{L-1} and adjoints as
+  // three e4m3 pieces (hi, mid, lo) node-major (one byte per element)
+  bool fp8 = false;
+  uint8_t* q8 = nullptr;
+  uint8_t* q8t = nullptr;
+  uint8_t* act8[3] = {nullptr, nullptr, nullptr};
+  uint8_t* xb8[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  std::vector<float> adj_scale;            // per layer l: the adjoints D_l stored as D_l * adj_scale[l]
+  alignas(64) unsigned char q8map[128], q8tmap[128];  // box 64 x 128
+  alignas(64) unsigned char a8map[3][128];           // box 64 x 256
+  alignas(64) unsigned char b8map[2][3][128];        // box 64 x 240
 };
 
 // Packed network for the tensor-core path -- see mlp_tc.cu.
@@ -113,8 +125,13 @@ struct Net {
   std::vector<size_t> w_off, b_off; // offsets into W32 / b32
   double* P64 = nullptr;            // FP64 copy for the plant (W then b per layer)
   int h_max = 0;
+  std::vector<float> fp8_scale;     // RTN_FP8: per layer, W = scale * e4m3 code
   TcNet tc;
 };
+
+// RTN_FP8: quantise n weights in place to scale * e4m3(w / scale) with
+// scale = amax / 448 (round to nearest even, saturating); returns the scale
+float quantize_e4m3(float* w, size_t n);
 
 // Training buffers (allocated on the first rtn_train / rtn_mse_grad call;
 // train_tc.cu).  Per layer l = 0..L-1 the input activations A_l and per
@@ -321,6 +338,8 @@ cudaError_t train_reduce(rtn_ctx* ctx, TrainState& ts);
 // one Adam step of every parameter from the partials and db, with the
 // weight splits refreshed
 cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr);
+// the split weight copies of the training GEMMs from the current W32
+cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts);
 void train_release(rtn_ctx* ctx);
 
 // a5

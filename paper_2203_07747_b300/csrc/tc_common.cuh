@@ -191,6 +191,23 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// instruction descriptor, kind::f8f6f4: D f32, A = B = e4m3 (format 0), both
+// K-major
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// one kind::f8f6f4 MMA (K = 32 one-byte elements), issued by one elected
+// lane of a converged warp
+__device__ __forceinline__ void mma_f8_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                             uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
 // the same, issued by one elected lane of a converged warp
 __device__ __forceinline__ void mma_bf16_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                                uint32_t accum) {

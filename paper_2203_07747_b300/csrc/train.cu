@@ -82,6 +82,14 @@ rtn_status refresh_network(rtn_ctx* ctx) {
   TCK(cudaStreamSynchronize(ctx->stream));
   TCK(cudaMemcpy(W.data(), net.W32, ts.nw * 4, cudaMemcpyDeviceToHost));
   TCK(cudaMemcpy(b.data(), net.b32, ts.nb * 4, cudaMemcpyDeviceToHost));
+  if (ctx->opt.precision == RTN_FP8) {
+    // the trained master weights quantised again (e4m3, scale amax/448)
+    for (int l = 0; l < L; ++l)
+      net.fp8_scale[l] = quantize_e4m3(W.data() + net.w_off[l], (size_t)net.widths[l + 1] * net.widths[l]);
+    TCK(cudaMemcpy(net.W32, W.data(), ts.nw * 4, cudaMemcpyHostToDevice));
+    // the split copies the training GEMMs use follow the quantised weights
+    TCK(train_resplit(ctx, ts));
+  }
   std::vector<double> P;
   for (int l = 0; l < L; ++l) {
     const size_t nwl = (size_t)net.widths[l + 1] * net.widths[l];

@@ -711,6 +711,20 @@ cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr) {
   return cudaGetLastError();
 }
 
+cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts) {
+  Net& net = ctx->net;
+  const std::vector<int>& w = net.widths;
+  if (ts.ws.empty()) return cudaSuccess;
+  for (int l = 0; l < net.n_layers; ++l) {
+    const size_t n = (size_t)w[l + 1] * w[l];
+    tg_weights_kernel<<<nblk(n), 256, 0, ctx->stream>>>(net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0,
+                                                        nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, ts.ws[4 * l],
+                                                        ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2],
+                                                        ts.ws[4 * l + 3], rup(w[l + 1], 32));
+  }
+  return cudaGetLastError();
+}
+
 void train_release(rtn_ctx* ctx) {
   TrainState& ts = ctx->train;
   free_bufs(ts);

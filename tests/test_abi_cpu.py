@@ -123,3 +123,40 @@ def test_rti_step_host_rejects_null_context_and_device_tensors():
         rtn._hptr(torch.zeros((13, 4), dtype=torch.float32).t(), torch.float32, (4, 13), "x0")
     assert rtn._hptr(torch.zeros((4, 13), dtype=torch.float32), torch.float32, (4, 13), "x0") is not None
 
+
+
+def test_round_e4m3_grid():
+    import numpy as np
+    # the e4m3 grid of the FP8 workloads' weight quantisation: 3 mantissa
+    # bits, exponent bias 7, subnormal spacing 2^-9, largest 448, ties to even
+    import workload as W
+    assert W.round_e4m3(448.0) == 448.0 and W.round_e4m3(1000.0) == 448.0 and W.round_e4m3(-500.0) == -448.0
+    assert W.round_e4m3(2.0 ** -9) == 2.0 ** -9 and W.round_e4m3(2.0 ** -10) == 0.0  # tie -> even (0)
+    assert W.round_e4m3(3 * 2.0 ** -10) == 2.0 ** -8                                 # tie -> even (2 x 2^-9)
+    assert W.round_e4m3(1.0625) == 1.0 and W.round_e4m3(1.1875) == 1.25              # ties at 1 + 1/16, 1 + 3/16
+    assert W.round_e4m3(1.07) == 1.125 and W.round_e4m3(-0.3) == -0.3125
+    # every value between the grid points rounds to one of its two neighbours
+    grid = sorted({W.round_e4m3(float(k) * 2.0 ** -9) for k in range(0, 1 << 18)})
+    assert len(grid) == 127  # 0 and the 126 finite positive codes below 480 (7 subnormal, 119 normal + 448)
+    x = np.random.default_rng(0).uniform(-448, 448, 10000)
+    r = W.round_e4m3(x)
+    assert np.all(np.isin(np.abs(r), grid))
+    g = np.array(grid)
+    lo = g[np.searchsorted(g, np.abs(x), side="right") - 1]
+    hi = g[np.minimum(np.searchsorted(g, np.abs(x), side="left"), len(g) - 1)]
+    assert np.all((np.abs(r) == lo) | (np.abs(r) == hi))
+    assert np.all(np.abs(np.abs(r) - np.abs(x)) <= np.minimum(np.abs(x) - lo, hi - np.abs(x)) + 1e-12)
+
+
+def test_quantize_e4m3_per_layer_scale():
+    import numpy as np
+    import workload as W
+    layers = W.xavier_mlp([17, 64, 32, 3], 1)
+    for (Wq, bq), (W0, b0) in zip(W.quantize_e4m3(layers), layers):
+        s = np.float32(np.abs(np.float32(W0)).max()) / np.float32(448.0)
+        codes = Wq / np.float64(s)
+        amax = float(np.float32(np.abs(np.float32(W0)).max()))
+        assert abs(np.abs(Wq).max() - amax) <= 2.0 ** -23 * amax           # amax maps to the code 448
+        assert np.allclose(W.round_e4m3(codes), codes, rtol=1e-6, atol=0)    # every weight on the e4m3 grid
+        assert np.abs(Wq - W0).max() <= 2.0 ** -4 * np.abs(W0).max()          # half a unit in the last place at most
+        assert np.array_equal(bq, b0)

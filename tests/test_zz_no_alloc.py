@@ -3,9 +3,10 @@
 rtn_mlp_eval_f32_noalloc serves callers that may not call cudaMalloc (for
 example a real-time loop or a host that owns all device memory); it keeps
 its activations in a fixed array inside the library.  Its result must equal
-that of rtn_mlp_eval on an FP32 context (the entry point that allocates) and
-that of the FP64 oracle, within the 1e-5 relative FP32 tolerance of the
-other parity tests, on two calls in a row with different inputs (the array
+that of the FP64 oracle within the 1e-5 relative FP32 tolerance of the
+other parity tests, and that of rtn_mlp_eval on an FP32 context (the entry
+point that allocates, another FP32 path within 1e-5 of the oracle) within
+2e-5, on two calls in a row with different inputs (the array
 keeps the previous call's contents, which must not leak into the next
 result), with hidden widths on and off the kernels' tile sizes and a node
 count just under the array's limit.  This file is named to be collected
@@ -65,12 +66,14 @@ def test_noalloc_matches_allocating_entry_point_and_oracle_twice(orc, widths, N)
         assert st == 0, err.value
         torch.cuda.synchronize()
         fD, JD = fD.double().cpu().numpy(), JD.double().cpu().numpy()
-        # against the allocating entry point and the FP64 oracle; f_D rows
-        # relative to max(|row|, 1e-3) as in the FP32 network parity test
+        # against the FP64 oracle at the FP32 bar of 1e-5, and against the
+        # allocating entry point (another FP32 path, itself within 1e-5 of
+        # the oracle) at twice that; f_D rows relative to max(|row|, 1e-3)
+        # as in the FP32 network parity test
         fr, Jr, *_ = orc.linearize(W.QUAD, layers, N, dt, X, U)
-        for Jb, fb in ((J_ref.double().cpu().numpy(), f_ref.double().cpu().numpy()), (Jr, fr)):
-            assert _rel_rows(JD, Jb) < 1e-5
-            assert _rel_rows(fD, fb, 1e-3) < 1e-5
+        for Jb, fb, tol in ((Jr, fr, 1e-5), (J_ref.double().cpu().numpy(), f_ref.double().cpu().numpy(), 2e-5)):
+            assert _rel_rows(JD, Jb) < tol
+            assert _rel_rows(fD, fb, 1e-3) < tol
 
 
 def test_noalloc_rejects_oversized_problem():

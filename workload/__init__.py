@@ -51,6 +51,31 @@ def round_bf16(a):
     return r.view(np.float32).astype(np.float64)
 
 
+def round_e4m3(x):
+    """Round to the nearest e4m3 value (OCP FP8: 3 mantissa bits, exponent
+    bias 7, subnormal spacing 2^-9, largest 448), ties to even, saturating."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.minimum(np.abs(x), 448.0)
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -6)))
+    step = 2.0 ** (e - 3)
+    r = np.round(a / step) * step  # numpy rounds halves to even
+    return np.sign(x) * np.minimum(r, 448.0)
+
+
+def quantize_e4m3(layers):
+    """Every weight matrix as float32(s * e4m3(W / s)) with the per-layer scale
+    s = amax / 448 (in float32), biases unchanged: the weights of the FP8
+    workloads, which the library derives the same way and the oracle then
+    evaluates as given."""
+    out = []
+    for W, b in layers:
+        W32 = np.asarray(W, np.float32)
+        s = np.float32(np.abs(W32).max()) / np.float32(448.0)
+        q = round_e4m3(W32.astype(np.float64) / np.float64(np.float32(s))).astype(np.float32)
+        out.append(((q * s).astype(np.float32).astype(np.float64), np.asarray(b, np.float64)))
+    return out
+
+
 def xavier_mlp(widths, seed, bf16=False):
     """List of (W[out][in], b[out]) float64 arrays, Xavier-uniform, b = 0."""
     g = rng(seed, 1)
