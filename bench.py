@@ -311,6 +311,10 @@ def error_sample(prob, precision, nb=64):
         master["layers"] = W.xavier_mlp(prob["widths"], prob["seed"], bf16=False)
         smp["master"] = master
         smp["gpu_master_JD"] = run(master)[1]
+    if precision == "fp8":
+        # the GPU's J_D (quantised weights) against the oracle on the
+        # unquantised ones: the effect of the e4m3 weights
+        smp["gpu_master_JD"] = smp["gpu"][1]
     return smp
 
 
@@ -388,6 +392,13 @@ def bench_ragged(steps=200):
     ms_box, _, rmse_box = time_closed_loop(cb, prob, steps, 3)
     r_box = time_closed_loop.per_instance
     cb.close()
+    import paper_2203_07747_b300 as rtn
+    cf = rtn.Controller(prob["N"], prob["dt"], prob["Q"], prob["R"], QN=prob["QN"], quad=prob["quad"],
+                        layers=prob["layers"], precision="bf16x2", fused_qp=True)
+    cf.tc_select(vi)
+    ms_fused, _, rmse_fused = time_closed_loop(cf, prob, steps, 3)
+    cf.close()
+    L = len(prob["layers"])
     smp = error_sample(prob, "bf16x2")
     line = {"workload": "cfg4_ragged_batch: 4096 instances, N_b in {10..50} (sum %d nodes), "
                         "dt_b in [0.02, 0.1] s, MLP 17-256x4-3 split BF16, %d-step closed loop, "
@@ -402,6 +413,14 @@ def bench_ragged(steps=200):
                               "QP every instance tracks (box_qp)"),
             "box_qp": {"rti_steps_per_s": prob["B"] / (ms_box * 1e-3), "tracking_rmse_m": rmse_box,
                        "tracking_rmse_per_instance_m": rmse_distribution(r_box)},
+            "launches_per_step": 2 * L + 5,
+            "fused_lin_qp": {"what": "RK4 linearisation and QP in one persistent launch with a work queue "
+                                     "(rtn_options.fused_qp)",
+                             "rti_steps_per_s": prob["B"] / (ms_fused * 1e-3), "ms_per_step": ms_fused,
+                             "tracking_rmse_m": rmse_fused,
+                             "launches_per_step": 2 * L + 4,
+                             "note": "the RK4 and QP launches become one launch (its last warp returns the "
+                                     "work-queue counters to zero for the next)"},
             "tile_variant": vi}
     return line, smp
 
@@ -445,6 +464,43 @@ def bench_box(prob, precision, tile, steps=20):
                 "subproblems": {"mean": float(its.mean()), "p99": float(np.percentile(its, 99)),
                                 "max": int(its.max()), "frac_more_than_one": float((its > 1).mean())},
                 "not_converged": int((st == 8).sum())}}
+
+
+def bench_fp8(prob, bf16_burst, steps=20):
+    """The precision workload with the FP8 network path: weights quantised to
+    e4m3 with per-layer scale amax/448 (the oracle of the error table gets the
+    same dequantised weights), closed loop RTI steps/s, node linearisations/s,
+    the network pass against the FP8 tensor peak; the GPU side of its error
+    table (the oracle side runs in the CPU-baseline leg)."""
+    q = dict(prob)
+    q["layers"] = W.quantize_e4m3(prob["layers"])
+    q["bf16"] = False
+    ctl = make(q, "fp8")
+    ms, _, rmse = time_closed_loop(ctl, q, steps, 3)
+    x, u = ctl.get_iterate()
+    out = ctl.linearize(x, u)
+    nn = int(q["N"].sum())
+    ms_lin = time_calls(lambda: ctl.linearize(x, u, out), 10)
+    ms_mlp = time_calls(lambda: ctl.mlp_eval(x, u, out[0], out[1]), 10)
+    flops = rev_flops_per_node(q["widths"]) * nn
+    ctl.close()
+    smp = error_sample(q, "fp8")
+    # J_D against the unquantised network (weight quantisation included)
+    master = dict(smp["sub"])
+    master["layers"] = prob["layers"]
+    smp["master"] = master
+    peak8 = 2.0 * bf16_burst
+    return {"workload": "cfg3 workload, weights e4m3 with per-layer scale amax/448, FP8 network path "
+                        "(hidden GEMMs kind::f8f6f4, activations/adjoints as three e4m3 pieces)",
+            "rti_steps_per_s": q["B"] / (ms * 1e-3), "ms_per_step": ms,
+            "node_linearizations_per_s": nn / (ms_lin * 1e-3), "ms_network_pass": ms_mlp,
+            "tracking_rmse_m": rmse,
+            "roofline": {"bound": "tensor", "peak": peak8, "unit": "TFLOP/s",
+                         "peak_kind": "fp8 dense = measured bf16 burst x 2 (nominal ratio 4.5 / 2.25)",
+                         "achieved": flops / (ms_mlp * 1e-3) / 1e12,
+                         "frac": flops / (ms_mlp * 1e-3) / 1e12 / peak8,
+                         "note": "whole pass (reverse-mode FLOPs); three e4m3 MMAs per product in the hidden "
+                                 "GEMMs, the input / first backward / Jacobian GEMMs in split BF16"}}, smp
 
 
 def bench_riccati(prob, precision, tile, steps=20):
@@ -1017,6 +1073,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_extra:
         line["box_qp"] = bench_box(prob, prec, cfg.get("tile"))
         line["riccati_arithmetic"] = bench_riccati(prob, prec, cfg.get("tile"))
+        if args.config == "cfg3_bf16_precision":
+            line["fp8"], fp8_smp = bench_fp8(prob, bf16_burst)
         line["ragged_batch"], ragged_smp = bench_ragged()
         line["learned_part"] = bench_learned(bf16_burst)
         line["runtime_analysis"] = bench_runtime_analysis()
@@ -1027,6 +1085,9 @@ def main():
         line["cpu_baseline"] = cpu_baseline(prob)
         line["error_table"] = error_table(smp)
         line["jac_rel_err_max"] = line["error_table"]["J_D"]["max"]
+        if "fp8" in line:
+            line["fp8"]["error_table"] = error_table(fp8_smp)
+            line["fp8"]["jac_rel_err_max"] = line["fp8"]["error_table"]["J_D"]["max"]
         if "ragged_batch" in line:
             line["ragged_batch"]["error_table"] = error_table(ragged_smp)
             line["ragged_batch"]["jac_rel_err_max"] = line["ragged_batch"]["error_table"]["J_D"]["max"]

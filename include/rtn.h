@@ -127,6 +127,16 @@ typedef struct {
                        RK4 stages see the quadratic term along the state
                        deviation (u is held over the interval). 0: Eq. 4 to
                        first order (J_D only) */
+  int fused_qp;     /* 1: every RTI step runs the RK4 linearisation (a2) and
+                       the QP with the feedback (a3 + a4) in one persistent
+                       launch: warps take RK4 work (node columns, longest
+                       horizon first) from an atomic queue, then one
+                       instance's QP each, which waits (bounded, ~2 s, then
+                       RTN_E_TIMEOUT for that instance) until its nodes are
+                       linearised; applies to the quadrotor model with a
+                       3-output first-order residual, the FP32 sweep and no
+                       bounds in the QP (other contexts run the separate
+                       launches).  0: separate launches */
 } rtn_options;
 
 /* Create a controller batch of `batch` instances with horizons N[b] >= 1 and
@@ -364,7 +374,11 @@ rtn_status rtn_set_wait_budget(rtn_ctx* ctx, long long cycles);
  * issues any copy; the wait runs out after the budget of
  * rtn_set_wait_budget, the pass returns with RTN_E_TIMEOUT recorded
  * (rtn_device_error) and nothing in flight, and its outputs are undefined.
- * enable == 0 restores normal passes. */
+ * In the fused launch (rtn_options.fused_qp) every instance's QP waits for
+ * one linearised column more than exist: each wait runs out after the same
+ * budget, the instance gets status RTN_E_TIMEOUT, no step and the
+ * reference input as command.  enable == 0 restores normal passes.  The
+ * budget of rtn_set_wait_budget applies to the fused launch's waits too. */
 rtn_status rtn_inject_wait_stall(rtn_ctx* ctx, int enable);
 
 /* Size of the fixed activation array used by rtn_mlp_eval_f32_noalloc. */

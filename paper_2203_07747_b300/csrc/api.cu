@@ -94,6 +94,14 @@ rtn_status linearize_impl(rtn_ctx* ctx, const float* x, const float* u, float* f
 // node-packed), t read from t_dev when given
 // the QP, feedback and iterate update of an RTI step whose linearisation
 // is in ctx->A, Bm, c
+// The part of an RTI step that needs only the iterate (Sec. III-B's
+// preparation): the network pass and, unless the RK4 linearisation runs in
+// the fused launch with the QP, the RK4 linearisation
+rtn_status rti_prep(rtn_ctx* ctx) {
+  if (lin_qp_fusable(ctx)) return ctx->has_mlp ? run_mlp(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD) : RTN_OK;
+  return linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);
+}
+
 static rtn_status rti_qp(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
                          int xref_stride, int uref_stride, const int* t_dev, float* u0, int* status) {
   QpArgs a{};
@@ -107,14 +115,16 @@ static rtn_status rti_qp(rtn_ctx* ctx, const float* x0, const float* xref, const
   a.status = status ? status : ctx->status;
   a.update = 1;
   a.shift = ctx->opt.shift;
-  cudaError_t e = qp_solve(ctx, a);
+  cudaError_t e = lin_qp_fusable(ctx) ? lin_qp_solve(ctx, a, ctx->has_mlp ? ctx->fD : nullptr,
+                                                     ctx->has_mlp ? ctx->JD : nullptr)
+                                      : qp_solve(ctx, a);
   if (e != cudaSuccess) return fail(ctx, RTN_E_CUDA, std::string("qp: ") + cudaGetErrorString(e));
   return RTN_OK;
 }
 
 rtn_status rti_impl(rtn_ctx* ctx, const float* x0, const float* xref, const float* uref,
                     int xref_stride, int uref_stride, const int* t_dev, float* u0, int* status) {
-  rtn_status st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);
+  rtn_status st = rti_prep(ctx);
   if (st != RTN_OK) return st;
   return rti_qp(ctx, x0, xref, uref, xref_stride, uref_stride, t_dev, u0, status);
 }
@@ -138,6 +148,15 @@ rtn_status make_layout(rtn_ctx* ctx, int batch, const int* N, const double* dt) 
     for (int k = 0; k < N[b]; ++k) node_inst[uoff[b] + k] = b;
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return N[a] > N[c]; });
+  // every node, instances in that order (the fused linearisation + QP
+  // launch hands out RK4 work in this order)
+  std::vector<int> rk_nodes;
+  rk_nodes.reserve(us);
+  for (int b : order)
+    for (int k = 0; k < N[b]; ++k) rk_nodes.push_back(uoff[b] + k);
+  CK(upload(&L.rk_nodes, rk_nodes.data(), us));
+  CK(dalloc(&L.counters, (size_t)batch + 3));
+  CK(cudaMemset(L.counters, 0, ((size_t)batch + 3) * sizeof(int)));
   CK(upload(&L.N, N, batch));
   CK(upload(&L.dt, dtf.data(), batch));
   CK(upload(&L.dt64, dt, batch));
@@ -231,11 +250,12 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
     nn += N[b];
   }
   if (nn + batch > (1LL << 28)) { g_create_err = "batch too large"; return RTN_E_INVAL; }
-  rtn_options o{RTN_FP32, 0, 1, 0, 0, 0};
+  rtn_options o{RTN_FP32, 0, 1, 0, 0, 0, 0};
   if (opt) o = *opt;
   if (o.precision < RTN_FP32 || o.precision > RTN_FP8) { g_create_err = "bad precision"; return RTN_E_INVAL; }
   if (o.box_max_iter < 0) { g_create_err = "box_max_iter must be >= 0"; return RTN_E_INVAL; }
   if (o.riccati_f64 < 0 || o.riccati_f64 > 2) { g_create_err = "riccati_f64 must be 0, 1 or 2"; return RTN_E_INVAL; }
+  o.fused_qp = o.fused_qp ? 1 : 0;
   if (o.box_max_iter == 0) o.box_max_iter = 20;
   o.box_qp = o.box_qp ? 1 : 0;
   o.second_order = o.second_order ? 1 : 0;
@@ -367,6 +387,12 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
       ctx->opt.precision = RTN_FP32;
     }
 
+    // the device status word of the fused launch's bounded waits (network
+    // contexts already have one)
+    if (o.fused_qp && !ctx->net.tc.err) {
+      CK(dalloc(&ctx->net.tc.err, 1));
+      CK(cudaMemset(ctx->net.tc.err, 0, sizeof(int)));
+    }
     // iterate and workspace
     size_t gsz = ctx->opt.riccati_f64 == 1 ? sizeof(double) : sizeof(float);
     CK(dalloc(&ctx->x, (size_t)xs * NX));
@@ -414,7 +440,7 @@ void rtn_destroy(rtn_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   Layout& L = ctx->lay;
-  void* ptrs[] = {L.N, L.dt, L.dt64, L.xoff, L.uoff, L.node_inst, L.order, ctx->net.W32, ctx->net.b32,
+  void* ptrs[] = {L.N, L.dt, L.dt64, L.xoff, L.uoff, L.node_inst, L.order, L.rk_nodes, L.counters, ctx->net.W32, ctx->net.b32,
                   ctx->net.P64, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c, ctx->K,
                   ctx->kff, ctx->status, ctx->dev_t, ctx->x0f, ctx->u0,
                   ctx->box_dx, ctx->box_du, ctx->box_gam, ctx->box_act, ctx->box_iters, ctx->HD};
@@ -599,7 +625,7 @@ rtn_status rtn_rti_step_host(rtn_ctx* ctx, const float* x0, const float* xref, c
   CK(cudaMemcpyAsync(io.xref, xref, bxr, cudaMemcpyHostToDevice, io.copy));
   CK(cudaMemcpyAsync(io.uref, uref, bur, cudaMemcpyHostToDevice, io.copy));
   CK(cudaEventRecord(io.in_ev, io.copy));
-  rtn_status st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);
+  rtn_status st = rti_prep(ctx);
   if (st != RTN_OK) return st;
   CK(cudaStreamWaitEvent(ctx->stream, io.in_ev, 0));
   st = rti_qp(ctx, io.x0, io.xref, io.uref, 0, 0, nullptr, io.u0, io.st);
@@ -818,7 +844,7 @@ rtn_status rtn_closed_loop(rtn_ctx* ctx, int steps, int plant_kind, const float*
       if (e == cudaSuccess) e = cudaStreamWaitEvent(cs2, fork, 0);
       if (e == cudaSuccess) e = plant_branch(cs2);  // step k
       if (e == cudaSuccess) {
-        st = linearize_impl(ctx, ctx->x, ctx->u, ctx->fD, ctx->JD, ctx->A, ctx->Bm, ctx->c);  // step k + 1
+        st = rti_prep(ctx);  // step k + 1
         ctx->stream = cs;
       }
       if (e == cudaSuccess) e = cudaEventRecord(join, cs2);

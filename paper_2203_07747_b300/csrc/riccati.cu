@@ -28,8 +28,10 @@
 //   1  everything in FP64;
 //   2  the FP32 sweep with the factorisation of Huu = R + B'PB and the
 //      solves of [K | k] in FP64 (FP64 kept only where the QP divides).
+#include <algorithm>
 #include <type_traits>
 
+#include "rk4_dev.cuh"
 #include "rtn_internal.cuh"
 
 namespace rtn {
@@ -106,16 +108,15 @@ struct KArgs {
 // resident warps: at least five blocks per SM (registers capped at 96, a
 // few bytes spilled), which at 8192 instances leaves three rounds of warps
 // instead of four.
-template <typename T, int WPB, bool BOX, bool CH64>
-__global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
+template <typename T, bool CH64>
+using SlotOf = Slot<T, typename std::conditional<CH64, double, T>::type>;
+
+// the QP, feedback and iterate update of instance b by one warp (lane =
+// lane index), with the warp's shared-memory slot S
+template <typename T, bool BOX, bool CH64>
+__device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH64>& S, int lane) {
   using TC = typename std::conditional<CH64, double, T>::type;
-  __shared__ Slot<T, TC> slots[WPB];
   const QpArgs& a = ka.a;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = blockIdx.x * WPB + warp;
-  if (slot >= ka.B) return;
-  const int b = ka.order ? ka.order[slot] : slot;
-  Slot<T, TC>& S = slots[warp];
   const int N = ka.N[b], xo = ka.xoff[b], uo = ka.uoff[b];
   const int t = a.t_dev ? *a.t_dev : 0;
   const int xr0 = (a.xref_stride > 0 ? b * a.xref_stride : xo) + t;
@@ -556,6 +557,128 @@ __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
   else forward(2, st == RTN_E_NOT_CONVERGED);
 }
 
+template <typename T, int WPB, bool BOX, bool CH64>
+__global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
+  __shared__ SlotOf<T, CH64> slots[WPB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = blockIdx.x * WPB + warp;
+  if (slot >= ka.B) return;
+  const int b = ka.order ? ka.order[slot] : slot;
+  qp_instance<T, BOX, CH64>(ka, b, slots[warp], lane);
+}
+
+// ---------------------------------------------------------------- fused
+// The RK4 linearisation (a2) and the QP (a3 + a4) of every instance in one
+// persistent launch.  Warps first take units of 32 (node, column) RK4
+// threads from an atomic ticket, nodes in longest-horizon-first instance
+// order, and count the columns they finish per instance; when the units
+// are exhausted they take instances (same order) and run each one's QP once
+// all of its columns are counted.  Every unit a QP waits for was taken by a
+// running warp, so the waits end; they are bounded all the same.  The
+// latency-bound sweeps of the long instances overlap the issue-bound RK4
+// work of the short ones.
+constexpr int FQ_WPB = 4;
+
+struct FusedArgs {
+  KArgs ka;
+  QuadParams P;
+  const float *x, *u, *fD, *JD;
+  const int *node_inst, *rk_nodes;
+  const float* dt;
+  int n_nodes;
+  int* counters;  // [0] RK4 unit ticket, [1] QP ticket, [2] warps finished, [3 + b] columns of instance b finished
+  int* err;       // device status word (RTN_E_TIMEOUT)
+  long long wait_cycles;
+  int stall;      // fault injection: every QP waits for one column more than exists
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(FQ_WPB * 32, 4) lin_qp_kernel(FusedArgs fa) {
+  __shared__ SlotOf<float, false> slots[FQ_WPB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long total = (long long)fa.n_nodes * NZ;
+  const long long n_units = (total + 31) / 32;
+  int* rk_next = fa.counters;
+  int* qp_next = fa.counters + 1;
+  int* finished = fa.counters + 2;
+  int* done = fa.counters + 3;
+  const QpArgs& a = fa.ka.a;
+  for (;;) {
+    int unit = 0;
+    if (lane == 0) unit = atomicAdd(rk_next, 1);
+    unit = __shfl_sync(0xffffffffu, unit, 0);
+    if (unit >= n_units) break;
+    const long long tid = (long long)unit * 32 + lane;
+    int b = -1;
+    if (tid < total) {
+      const int n = fa.rk_nodes[tid / NZ];
+      rk4_column<NO>(fa.P, fa.x, fa.u, fa.fD, fa.JD, nullptr, fa.node_inst, fa.dt, n, (int)(tid % NZ), const_cast<float*>(a.A),
+                     const_cast<float*>(a.Bm), const_cast<float*>(a.c));
+      b = fa.node_inst[n];
+    }
+    // publish the finished columns: one atomic per instance in the unit
+    __threadfence();
+    const unsigned grp = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && lane == __ffs(grp) - 1) atomicAdd(done + b, __popc(grp));
+  }
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(qp_next, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= fa.ka.B) break;
+    const int b = fa.ka.order[t];
+    const int need = fa.ka.N[b] * NZ + fa.stall;
+    int ok = 1;
+    if (lane == 0) {
+      if (ld_acquire(done + b) < need) {
+        const long long t0 = clock64();
+        while (ld_acquire(done + b) < need) {
+          if (clock64() - t0 > fa.wait_cycles) {
+            ok = 0;
+            atomicExch(fa.err, (int)RTN_E_TIMEOUT);
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __threadfence();
+    if (!ok) {
+      // the instance's linearisation never completed: no step, reference input
+      if (lane == 0 && a.status) a.status[b] = RTN_E_TIMEOUT;
+      if (a.u0 && lane < NU) {
+        const int ur0 = (a.uref_stride > 0 ? b * a.uref_stride : fa.ka.uoff[b]) + (a.t_dev ? *a.t_dev : 0);
+        a.u0[(size_t)b * NU + lane] = a.uref[(size_t)ur0 * NU + lane];
+      }
+      continue;
+    }
+    qp_instance<float, false, false>(fa.ka, b, slots[warp], lane);
+  }
+  // the last warp to finish (every other warp has taken its last ticket and
+  // finished its work) returns the counters to zero for the next launch
+  int last = 0;
+  if (lane == 0) {
+    __threadfence();
+    last = atomicAdd(finished, 1) == (int)(gridDim.x * FQ_WPB) - 1;
+  }
+  if (__shfl_sync(0xffffffffu, last, 0)) {
+    __threadfence();
+    for (int e = lane; e < fa.ka.B; e += 32) done[e] = 0;
+    if (lane == 0) {
+      *rk_next = 0;
+      *qp_next = 0;
+      *finished = 0;
+    }
+    __threadfence();
+  }
+}
+
 template <typename T, int WPB, bool CH64 = false>
 cudaError_t launch(const KArgs& ka, cudaStream_t s) {
   const int grid = (ka.B + WPB - 1) / WPB;
@@ -564,9 +687,8 @@ cudaError_t launch(const KArgs& ka, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-}  // namespace
 
-cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a) {
+KArgs make_kargs(rtn_ctx* ctx, const QpArgs& a) {
   KArgs ka;
   ka.a = a;
   ka.cost = ctx->cost;
@@ -585,9 +707,51 @@ cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a) {
   ka.box_gam = ctx->box_gam;
   ka.box_act = ctx->box_act;
   ka.box_iters = ctx->box_iters;
+  return ka;
+}
+
+}  // namespace
+
+cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a) {
+  const KArgs ka = make_kargs(ctx, a);
   if (ctx->opt.riccati_f64 == 1) return launch<double, 2>(ka, ctx->stream);
   if (ctx->opt.riccati_f64 == 2) return launch<float, 4, true>(ka, ctx->stream);
   return launch<float, 4>(ka, ctx->stream);
+}
+
+bool lin_qp_fusable(const rtn_ctx* ctx) {
+  return ctx->opt.fused_qp && !ctx->di && ctx->n_out == NO && !ctx->opt.second_order && !ctx->opt.box_qp &&
+         ctx->opt.riccati_f64 == 0;
+}
+
+cudaError_t lin_qp_solve(rtn_ctx* ctx, const QpArgs& a, const float* fD, const float* JD) {
+  FusedArgs fa;
+  fa.ka = make_kargs(ctx, a);
+  fa.P = ctx->quad;
+  fa.x = a.x;
+  fa.u = a.u;
+  fa.fD = fD;
+  fa.JD = JD;
+  fa.node_inst = ctx->lay.node_inst;
+  fa.rk_nodes = ctx->lay.rk_nodes;
+  fa.dt = ctx->lay.dt;
+  fa.n_nodes = ctx->lay.n_nodes;
+  fa.counters = ctx->lay.counters;
+  fa.err = ctx->net.tc.err;
+  fa.wait_cycles = ctx->net.tc.wait_cycles > 0 ? ctx->net.tc.wait_cycles : 4000000000LL;
+  fa.stall = ctx->net.tc.inject_stall ? 1 : 0;
+  if (!fa.err) return cudaErrorInvalidValue;
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 148, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lin_qp_kernel, FQ_WPB * 32, 0);
+    grid = sms * std::max(occ, 1);
+  }
+  // the counters are zero from create and returned to zero by each launch's last warp
+  lin_qp_kernel<<<grid, FQ_WPB * 32, 0, ctx->stream>>>(fa);
+  return cudaGetLastError();
 }
 
 }  // namespace rtn

@@ -45,6 +45,8 @@ struct Layout {
   int* uoff = nullptr;       // [B] first node row of instance b
   int* node_inst = nullptr;  // [n_nodes] instance of every node
   int* order = nullptr;      // [B] instances sorted by decreasing N_b
+  int* rk_nodes = nullptr;   // [n_nodes] every node, instances in `order`
+  int* counters = nullptr;   // [B + 3] work queue of the fused linearisation + QP launch (zero between launches)
 };
 
 // Layered reverse mode (mlp_lay.cu): values [npad][hs] and adjoints
@@ -323,6 +325,11 @@ struct QpArgs {
   int shift;
 };
 cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a);
+// a2 + a3 + a4 in one persistent launch (first-order 3-output model, FP32
+// sweep without bounds): RK4 work units and then one QP per warp from a
+// work queue; x, u, fD, JD as rk4_sens, A, Bm, c written on the way
+bool lin_qp_fusable(const rtn_ctx* ctx);
+cudaError_t lin_qp_solve(rtn_ctx* ctx, const QpArgs& a, const float* fD, const float* JD);
 
 // a6 (train.cu: targets; train_tc.cu: the training step on the tensor cores)
 cudaError_t drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y);
