@@ -813,12 +813,15 @@ def hess_flops_per_node(widths):
     return f
 
 
-def bench_network_pass(config, B, reps=3):
+def bench_network_pass(config, B, reps=3, precision="bf16x2"):
     """The network pass (a1) of the workload's network on B instances with
-    the layered reverse-mode shape: ms per pass after one warm-up pass."""
+    the layered reverse-mode shape (split BF16, or FP8 on the e4m3-quantised
+    weights): ms per pass after one warm-up pass."""
     import torch
     prob = W.make_problem(config, seed=0, B=B, bf16=True)
-    ctl = make(prob, "bf16x2")
+    if precision == "fp8":
+        prob["layers"] = W.quantize_e4m3(prob["layers"])
+    ctl = make(prob, precision)
     vi = [v[0] for v in ctl.tc_variants() if v[2] == 6][0]
     ctl.tc_select(vi)
     x, u = ctl.get_iterate()
@@ -941,6 +944,9 @@ def main():
     ap.add_argument("--rti-step", type=int, default=0, metavar="B",
                     help="time only one RTI step of the workload on B instances with the layered reverse-mode "
                          "tile shape (the profiling command of the RK4 and QP kernels' summaries)")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="run only the training measurement (one epoch) and a short learned closed loop "
+                         "(the profiling command of the training kernels' summary)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -950,7 +956,12 @@ def main():
         print(json.dumps(bench_second_order(args.config, bf16_burst, B=args.second_order_only)))
         return
     if args.network_pass:
-        print(json.dumps(bench_network_pass(args.config, args.network_pass)))
+        print(json.dumps(bench_network_pass(args.config, args.network_pass,
+                                            precision="fp8" if args.precision == "fp8" else "bf16x2")))
+        return
+    if args.learned_only:
+        import torch  # noqa: F401
+        print(json.dumps(bench_learned(bf16_burst, epochs=1, steps=10)))
         return
     if args.rti_step:
         print(json.dumps(bench_rti_step(args.config, args.rti_step)))
