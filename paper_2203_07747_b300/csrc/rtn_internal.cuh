@@ -156,7 +156,8 @@ struct TrainState {
   float* grad = nullptr;               // dW (packed like W32) then db (like b32)
   float *m = nullptr, *v = nullptr;    // Adam moments, same packing
   size_t nw = 0, nb = 0, b_base = 0;
-  long long t = 0;                     // Adam step counter
+  long long t = 0;                     // Adam step counter (host mirror)
+  int* t_dev = nullptr;                // Adam step counter on the device
 };
 
 }  // namespace rtn
@@ -340,6 +341,12 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
 // partials and db (into ts.grad); loss (device scalar) accumulated
 cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
                        int start, float* loss);
+// the same for a step captured once and replayed: minibatch (k mod
+// per_epoch) and loss entry losses[k] for k = *k_dev, which
+// train_next_step advances at the end of the step
+cudaError_t train_grad_dev(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
+                           const int* k_dev, int per_epoch, float* losses);
+cudaError_t train_next_step(rtn_ctx* ctx, int* k_dev);
 // the partials summed into ts.grad (weights part)
 cudaError_t train_reduce(rtn_ctx* ctx, TrainState& ts);
 // one Adam step of every parameter from the partials and db, with the

@@ -169,14 +169,54 @@ rtn_status rtn_train(rtn_ctx* ctx, const float* X, const float* U, const float* 
   TCK(cudaMalloc(&dloss, std::max<long long>(steps, 1) * sizeof(float)));
   TCK(cudaMemsetAsync(dloss, 0, std::max<long long>(steps, 1) * sizeof(float), ctx->stream));
   cudaError_t e = cudaSuccess;
-  for (long long k = 0; k < steps && e == cudaSuccess; ++k) {
-    e = train_grad(ctx, ts, X, U, Y, (int)(k % per_epoch) * batch, dloss + k);
-    if (e == cudaSuccess) e = train_adam(ctx, ts, lr);
+  // one training step (~5 L launches) captured as a CUDA graph on a stream of
+  // its own and replayed `steps` times: the minibatch and the loss entry come
+  // from a step counter on the device that the step advances at its end, and
+  // the Adam step counter lives on the device too
+  cudaStream_t user = ctx->stream, cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev = nullptr;
+  int* k_dev = nullptr;
+  if (steps > 0) {
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&k_dev, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(k_dev, 0, sizeof(int), user);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e == cudaSuccess) {
+      ctx->stream = cs;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        e = train_grad_dev(ctx, ts, X, U, Y, k_dev, per_epoch, dloss);
+        if (e == cudaSuccess) e = train_adam(ctx, ts, lr);
+        if (e == cudaSuccess) e = train_next_step(ctx, k_dev);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      ts.t -= 1;  // train_adam advanced the host mirror while recording
+    }
+    for (long long k = 0; k < steps && e == cudaSuccess; ++k) {
+      e = cudaGraphLaunch(exec, cs);
+      ts.t += 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ev, 0);
+    ctx->stream = user;
   }
   if (e == cudaSuccess && loss_out && steps > 0)
     e = cudaMemcpyAsync(loss_out, dloss, steps * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
+  if (cs) cudaStreamSynchronize(cs);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (ev) cudaEventDestroy(ev);
+  if (cs) cudaStreamDestroy(cs);
+  if (k_dev) cudaFree(k_dev);
   cudaFree(dloss);
+  ctx->stream = user;
   TCK(e);
   return refresh_network(ctx);
 }

@@ -23,17 +23,23 @@ namespace rtn {
 namespace {
 
 constexpr int TG_KB = 32;
-constexpr int TG_N = 256;
-constexpr int TG_STAGES = 4;
 constexpr int TG_THREADS = 320;
 constexpr int TG_EPI_WARPS = 8;
 constexpr uint32_t TG_SBO = 512;  // 8 rows x 64 B
 constexpr uint32_t TG_SWZ = 4;    // 64 B swizzle
 constexpr uint32_t TG_A_BYTES = 128u * TG_KB * 2u;
-constexpr uint32_t TG_B_BYTES = (uint32_t)TG_N * TG_KB * 2u;
-constexpr uint32_t TG_STAGE = 2u * TG_A_BYTES + 2u * TG_B_BYTES;
-constexpr size_t TG_SMEM = TG_STAGES * TG_STAGE + 1024 + 256;
-static_assert(TG_SMEM <= 232448, "shared memory");
+// N tile NT: 128 columns for the forward and backward GEMMs (twice the
+// tiles of a 512 x batch GEMM, so that more SMs pull operands) with six
+// stages, 256 for the weight gradient (already split over the batch) with four
+template <int NT>
+struct Tg {
+  static constexpr int STAGES = NT == 128 ? 6 : 4;
+  static constexpr uint32_t B_BYTES = (uint32_t)NT * TG_KB * 2u;
+  static constexpr uint32_t STAGE = 2u * TG_A_BYTES + 2u * B_BYTES;
+  static constexpr size_t SMEM = STAGES * STAGE + 1024 + 256;
+  static constexpr uint32_t TMEM_COLS = 2 * NT;
+};
+static_assert(Tg<128>::SMEM <= 232448 && Tg<256>::SMEM <= 232448, "shared memory");
 
 enum { TG_FWD = 0, TG_OUT = 1, TG_BWD = 2, TG_WG = 3 };
 
@@ -57,8 +63,10 @@ struct TgArgs {
   int* err;
 };
 
-template <int MODE>
+template <int MODE, int NT>
 __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant__ TgMaps mp, TgArgs a) {
+  constexpr int TG_STAGES = Tg<NT>::STAGES, TG_N = NT;
+  constexpr uint32_t TG_B_BYTES = Tg<NT>::B_BYTES, TG_STAGE = Tg<NT>::STAGE;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t sraw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
@@ -92,7 +100,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(512)
+                 "r"(Tg<NT>::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -143,7 +151,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
     for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       if (!(ok = mbar_wait_warp(tmem_free(acc), aph ^ 1u, abort_flag, a.err))) break;
       tc_fence_after();
-      const uint32_t d = tmem + acc * 256u;
+      const uint32_t d = tmem + acc * (uint32_t)NT;
       for (int kb = 0; kb < a.nkb; ++kb) {
         if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err))) break;
         tc_fence_after();
@@ -182,7 +190,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
       const float bi = (MODE == TG_FWD || MODE == TG_OUT) && row_ok ? __ldg(a.bias + i) : 0.0f;
       if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err)) break;
       tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)NT;
       for (int ch = half; ch < TG_N / 16; ch += 2) {
         // every lane runs the tensor-memory loads (warp-collective); only
         // the stores depend on the lane's row
@@ -271,7 +279,8 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Tg<NT>::TMEM_COLS)
+                 : "memory");
   }
 }
 
@@ -291,6 +300,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 // One planned GEMM of the training step (operand tensor maps and epilogue).
 struct TgGemm {
   int mode = 0;
+  int nt = 256;  // N tile
   TgMaps maps;
   TgArgs args;
   int grid = 0;
@@ -318,12 +328,13 @@ bool tg_plan(TgGemm& g, int mode, const __nv_bfloat16* ah, const __nv_bfloat16* 
              int lda, const __nv_bfloat16* bh, const __nv_bfloat16* bl, long long rows_b, int ldb, int k_blocks,
              int m_rows, int n_cols, int n_sm) {
   g.mode = mode;
+  g.nt = mode == TG_WG ? 256 : 128;
   TgArgs& a = g.args;
   a = TgArgs{};
   a.m_rows = m_rows;
   a.n_cols = n_cols;
   a.mts = (m_rows + 127) / 128;
-  a.nts = (n_cols + TG_N - 1) / TG_N;
+  a.nts = (n_cols + g.nt - 1) / g.nt;
   a.ksplit = 1;
   a.nkb = k_blocks;
   if (mode == TG_WG) {
@@ -335,7 +346,7 @@ bool tg_plan(TgGemm& g, int mode, const __nv_bfloat16* ah, const __nv_bfloat16* 
   }
   const int kx = k_blocks * TG_KB;
   if (!tg_map(&g.maps.ah, ah, rows_a, kx, lda, 128) || !tg_map(&g.maps.al, al, rows_a, kx, lda, 128) ||
-      !tg_map(&g.maps.bh, bh, rows_b, kx, ldb, TG_N) || !tg_map(&g.maps.bl, bl, rows_b, kx, ldb, TG_N))
+      !tg_map(&g.maps.bh, bh, rows_b, kx, ldb, g.nt) || !tg_map(&g.maps.bl, bl, rows_b, kx, ldb, g.nt))
     return false;
   g.grid = (int)std::min<long long>((long long)a.mts * a.nts * a.ksplit, std::max(1, n_sm));
   return true;
@@ -343,13 +354,17 @@ bool tg_plan(TgGemm& g, int mode, const __nv_bfloat16* ah, const __nv_bfloat16* 
 
 cudaError_t tg_setup() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(tg_kernel<TG_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM)))
+  if ((e = cudaFuncSetAttribute(tg_kernel<TG_FWD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Tg<128>::SMEM)))
     return e;
-  if ((e = cudaFuncSetAttribute(tg_kernel<TG_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM)))
+  if ((e = cudaFuncSetAttribute(tg_kernel<TG_OUT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Tg<128>::SMEM)))
     return e;
-  if ((e = cudaFuncSetAttribute(tg_kernel<TG_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM)))
+  if ((e = cudaFuncSetAttribute(tg_kernel<TG_BWD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Tg<128>::SMEM)))
     return e;
-  return cudaFuncSetAttribute(tg_kernel<TG_WG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM);
+  return cudaFuncSetAttribute(tg_kernel<TG_WG, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Tg<256>::SMEM);
 }
 
 // err: the context's device status word (re-read at every launch: the
@@ -358,10 +373,10 @@ cudaError_t tg_launch(const TgGemm& g, int* err, cudaStream_t s) {
   TgArgs a = g.args;
   a.err = err;
   switch (g.mode) {
-    case TG_FWD: tg_kernel<TG_FWD><<<g.grid, TG_THREADS, TG_SMEM, s>>>(g.maps, a); break;
-    case TG_OUT: tg_kernel<TG_OUT><<<g.grid, TG_THREADS, TG_SMEM, s>>>(g.maps, a); break;
-    case TG_BWD: tg_kernel<TG_BWD><<<g.grid, TG_THREADS, TG_SMEM, s>>>(g.maps, a); break;
-    default: tg_kernel<TG_WG><<<g.grid, TG_THREADS, TG_SMEM, s>>>(g.maps, a); break;
+    case TG_FWD: tg_kernel<TG_FWD, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
+    case TG_OUT: tg_kernel<TG_OUT, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
+    case TG_BWD: tg_kernel<TG_BWD, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
+    default: tg_kernel<TG_WG, 256><<<g.grid, TG_THREADS, Tg<256>::SMEM, s>>>(g.maps, a); break;
   }
   return cudaGetLastError();
 }
@@ -392,7 +407,10 @@ __device__ __forceinline__ void split2(float v, __nv_bfloat16& h, __nv_bfloat16&
 // (features 17..31 zero) and feature-major [17][ldf]; samples j >= bs are 0
 __global__ void tg_gather_kernel(const float* __restrict__ X, const float* __restrict__ U, int start, int bs,
                                  int ldf, __nv_bfloat16* __restrict__ nh, __nv_bfloat16* __restrict__ nl,
-                                 __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl) {
+                                 __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl,
+                                 const int* __restrict__ k_dev, int per_epoch) {
+  // a replayed step: its minibatch from the step counter on the device
+  if (k_dev) start = (*k_dev % per_epoch) * bs;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)ldf * 32) return;
   const int j = (int)(e >> 5), f = (int)(e & 31);
@@ -416,7 +434,13 @@ __global__ void tg_gather_kernel(const float* __restrict__ X, const float* __res
 // j >= bs zero); the loss summed per block into *loss
 __global__ void tg_loss_kernel(const float* __restrict__ Z, const float* __restrict__ Y, int start, int bs, int no,
                                int ldf, __nv_bfloat16* __restrict__ nh, __nv_bfloat16* __restrict__ nl,
-                               __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl, float* __restrict__ loss) {
+                               __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl, float* loss,
+                               const int* __restrict__ k_dev, int per_epoch) {
+  // a replayed step: its minibatch and loss entry from the step counter on the device
+  if (k_dev) {
+    start = (*k_dev % per_epoch) * bs;
+    loss += *k_dev;
+  }
   __shared__ float red[256];
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float e2 = 0.0f;
@@ -477,7 +501,7 @@ __global__ void tg_reduce_kernel(const float* __restrict__ part, int ks, size_t 
 // [fo][ldw] and W' (hi, lo) [fi][ldwt]
 __global__ void tg_weights_kernel(float* __restrict__ P, const float* __restrict__ part, int ks, int fo, int fi,
                                   int adam, float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                                  float eps, float c1, float c2, __nv_bfloat16* __restrict__ wh,
+                                  float eps, const int* __restrict__ t_dev, __nv_bfloat16* __restrict__ wh,
                                   __nv_bfloat16* __restrict__ wl, int ldw, __nv_bfloat16* __restrict__ th,
                                   __nv_bfloat16* __restrict__ tl, int ldwt) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -485,6 +509,7 @@ __global__ void tg_weights_kernel(float* __restrict__ P, const float* __restrict
   if (e >= n) return;
   float p = P[e];
   if (adam) {
+    const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
     float g = 0.0f;
     for (int k = 0; k < ks; ++k) g += part[(size_t)k * n + e];
     const float mi = b1 * m[e] + (1.0f - b1) * g;
@@ -505,10 +530,11 @@ __global__ void tg_weights_kernel(float* __restrict__ P, const float* __restrict
 
 // fused Adam of the biases
 __global__ void tg_adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
-                               float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
-                               float c2) {
+                               float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
+                               const int* __restrict__ t_dev) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
   const float g = G[i];
   const float mi = b1 * m[i] + (1.0f - b1) * g;
   const float vi = b2 * v[i] + (1.0f - b2) * g * g;
@@ -526,7 +552,7 @@ struct TgPlan {
 // batch ranges of the weight gradient of a fo x fi layer for up to cap
 // samples (tg_plan never splits a smaller batch into more)
 int wg_ksplit_max(int fo, int fi, int cap, int n_sm) {
-  const int base = ((fo + 127) / 128) * ((fi + TG_N - 1) / TG_N), kb = rup(cap, 32) / 32;
+  const int base = ((fo + 127) / 128) * ((fi + 255) / 256), kb = rup(cap, 32) / 32;
   return std::max(1, std::min(kb, n_sm / std::max(base, 1)));
 }
 
@@ -566,6 +592,7 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
     if ((e = zalloc(&ts.grad, ts.nw + ts.nb))) return e;
     if ((e = zalloc(&ts.m, ts.nw + ts.nb))) return e;
     if ((e = zalloc(&ts.v, ts.nw + ts.nb))) return e;
+    if ((e = zalloc(&ts.t_dev, 1))) return e;
     ts.t = 0;
     if ((e = tg_setup())) return e;
     // split copies of the weights
@@ -576,7 +603,7 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
         if ((e = zalloc(&ts.ws[4 * l + k], k < 2 ? nwl : ntl))) return e;
       const size_t n = (size_t)w[l + 1] * w[l];
       tg_weights_kernel<<<nblk(n), 256, 0, ctx->stream>>>(net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0,
-                                                          nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f,
+                                                          nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr,
                                                           ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32),
                                                           ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
     }
@@ -659,8 +686,29 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
   return cudaSuccess;
 }
 
+// the step counter of a replayed training step, advanced at the step's end
+__global__ void tg_next_step_kernel(int* k_dev) { *k_dev += 1; }
+
+static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
+                             int start, float* loss, const int* k_dev, int per_epoch);
+
 cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y, int start,
                        float* loss) {
+  return grad_impl(ctx, ts, X, U, Y, start, loss, nullptr, 1);
+}
+
+cudaError_t train_grad_dev(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
+                           const int* k_dev, int per_epoch, float* losses) {
+  return grad_impl(ctx, ts, X, U, Y, 0, losses, k_dev, per_epoch);
+}
+
+cudaError_t train_next_step(rtn_ctx* ctx, int* k_dev) {
+  tg_next_step_kernel<<<1, 1, 0, ctx->stream>>>(k_dev);
+  return cudaGetLastError();
+}
+
+static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
+                             int start, float* loss, const int* k_dev, int per_epoch) {
   Net& net = ctx->net;
   const int L = net.n_layers, no = net.widths[L], bs = ts.bs;
   const TgPlan* P = static_cast<const TgPlan*>(ts.plan);
@@ -668,12 +716,12 @@ cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float
   cudaStream_t s = ctx->stream;
   cudaError_t e;
   tg_gather_kernel<<<nblk((size_t)ts.ldf * 32), 256, 0, s>>>(X, U, start, bs, ts.ldf, ts.an[0], ts.an[1], ts.af[0],
-                                                               ts.af[1]);
+                                                               ts.af[1], k_dev, per_epoch);
   for (int l = 0; l < L; ++l)
     if ((e = tg_launch(P->fwd[l], net.tc.err, s))) return e;
   tg_loss_kernel<<<nblk((size_t)ts.ldf * 32), 256, 0, s>>>(ts.z, Y, start, bs, no, ts.ldf, ts.gn[2 * (L - 1)],
                                                              ts.gn[2 * (L - 1) + 1], ts.gf[2 * (L - 1)],
-                                                             ts.gf[2 * (L - 1) + 1], loss);
+                                                             ts.gf[2 * (L - 1) + 1], loss, k_dev, per_epoch);
   for (int l = L - 1; l >= 0; --l) {
     if ((e = tg_launch(P->wg[l], net.tc.err, s))) return e;
     tg_rowsum_kernel<<<net.widths[l + 1], 256, 0, s>>>(ts.gf[2 * l], ts.gf[2 * l + 1], ts.ldf,
@@ -693,21 +741,25 @@ cudaError_t train_reduce(rtn_ctx* ctx, TrainState& ts) {
   return cudaGetLastError();
 }
 
+// the Adam step counter (on the device, so that a captured step can be
+// replayed) advanced by one
+__global__ void tg_step_kernel(int* t_dev) { *t_dev += 1; }
+
 cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr) {
   Net& net = ctx->net;
   const std::vector<int>& w = net.widths;
   ts.t += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float c1 = 1.0f - powf(b1, (float)ts.t), c2 = 1.0f - powf(b2, (float)ts.t);
+  tg_step_kernel<<<1, 1, 0, ctx->stream>>>(ts.t_dev);
   for (int l = 0; l < net.n_layers; ++l) {
     const size_t n = (size_t)w[l + 1] * w[l];
     tg_weights_kernel<<<nblk(n), 256, 0, ctx->stream>>>(
         net.W32 + net.w_off[l], ts.part + ts.part_off[l], ts.ksplit[l], w[l + 1], w[l], 1, ts.m + net.w_off[l],
-        ts.v + net.w_off[l], lr, b1, b2, eps, c1, c2, ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2],
-        ts.ws[4 * l + 3], rup(w[l + 1], 32));
+        ts.v + net.w_off[l], lr, b1, b2, eps, ts.t_dev, ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32),
+        ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
   }
   tg_adam_kernel<<<nblk(ts.nb), 256, 0, ctx->stream>>>(net.b32, ts.grad + ts.b_base, ts.m + ts.nw, ts.v + ts.nw,
-                                                       ts.nb, lr, b1, b2, eps, c1, c2);
+                                                       ts.nb, lr, b1, b2, eps, ts.t_dev);
   return cudaGetLastError();
 }
 
@@ -718,7 +770,7 @@ cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts) {
   for (int l = 0; l < net.n_layers; ++l) {
     const size_t n = (size_t)w[l + 1] * w[l];
     tg_weights_kernel<<<nblk(n), 256, 0, ctx->stream>>>(net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0,
-                                                        nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, ts.ws[4 * l],
+                                                        nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr, ts.ws[4 * l],
                                                         ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2],
                                                         ts.ws[4 * l + 3], rup(w[l + 1], 32));
   }
@@ -729,7 +781,7 @@ void train_release(rtn_ctx* ctx) {
   TrainState& ts = ctx->train;
   free_bufs(ts);
   for (auto* p : ts.ws) if (p) cudaFree(p);
-  for (void* p : {(void*)ts.grad, (void*)ts.m, (void*)ts.v}) if (p) cudaFree(p);
+  for (void* p : {(void*)ts.grad, (void*)ts.m, (void*)ts.v, (void*)ts.t_dev}) if (p) cudaFree(p);
   delete static_cast<TgPlan*>(ts.plan);
   ts = TrainState{};
 }
