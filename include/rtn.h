@@ -315,7 +315,9 @@ rtn_status rtn_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int*
 rtn_status rtn_tc_select(rtn_ctx* ctx, int idx);
 rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms);
 
-/* Phase tracing of the tensor-core kernel (profiling aid).  enable != 0
+/* Phase tracing of the fused tensor-core kernels (profiling aid, compiled in
+ * only when the library is built with -DRTN_TRACE=1; otherwise enable != 0
+ * returns RTN_E_UNSUPPORTED).  enable != 0
  * makes every later network evaluation record %globaltimer stamps [ns] of
  * CTA 0 into a device buffer of RTN_TC_TRACE_LEN entries: entry
  * ((i * (L + 1) + l) * 8 + f) for the i-th tile of CTA 0, layer l < L

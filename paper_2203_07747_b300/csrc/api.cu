@@ -722,6 +722,8 @@ rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable) {
   TcNet& tc = ctx->net.tc;
   if (!ctx->has_mlp || ctx->opt.precision == RTN_FP32)
     return fail(ctx, RTN_E_UNSUPPORTED, "no tensor-core network on this context");
+  if (!RTN_TRACE && enable)
+    return fail(ctx, RTN_E_UNSUPPORTED, "rtn_tc_trace: built without phase tracing (compile with -DRTN_TRACE=1)");
   if (enable && !tc.trace) {
     CK(cudaMalloc(&tc.trace, RTN_TC_TRACE_LEN * sizeof(unsigned long long)));
     CK(cudaMemset(tc.trace, 0, RTN_TC_TRACE_LEN * sizeof(unsigned long long)));

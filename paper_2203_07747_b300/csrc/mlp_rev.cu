@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int s = 0;
       uint32_t ph = 0, used = 0, tf_par = 0, xr_par = 0;
       bool ok = true;
-      const bool tr = a.trace != nullptr && blockIdx.x == 0;
+      const bool tr = RTN_TRACE && a.trace != nullptr && blockIdx.x == 0;
       WaitClock wc(tr);
       for (int tile = blockIdx.x, it = 0; tile < n_tiles && ok; tile += gridDim.x, ++it)
         for (int g = 0; g < n_gemm && ok; ++g) {
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     prefetch_z(blockIdx.x);
     uint32_t acc_par = 0, xf_par = 0, zf_par = 0, zr_ph = 0, fd_par = 0, bd_par = 0;
     bool ok = true, first = true;
-    const bool etr = a.trace != nullptr && blockIdx.x == 0 && e == 0 && lane == 0;
+    const bool etr = RTN_TRACE && a.trace != nullptr && blockIdx.x == 0 && e == 0 && lane == 0;
     long long ew = 0;  // wait cycles of the current phase (traced thread)
     auto wwait = [&](uint32_t bar, uint32_t par) -> bool {
       int w_ok = 0;

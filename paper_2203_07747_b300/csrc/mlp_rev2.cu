@@ -256,7 +256,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
       int s = 0;
       uint32_t ph = 0, used = 0, tf_par = 0, xr_par = 0, xi_par = 0;
       bool ok = true;
-      const bool tr = a.trace != nullptr && blockIdx.x == 0;
+      const bool tr = RTN_TRACE && a.trace != nullptr && blockIdx.x == 0;
       WaitClock wc(tr);
       for (int tile = pair, it = 0; tile < n_tiles && ok; tile += n_pairs, ++it)
         for (int g = 0; g < n_gemm && ok; ++g) {
@@ -383,7 +383,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(R2_THREADS, 1)
     // xfree[j] completes once per GEMM: completion c (from 1) of the pair's
     // tile it, GEMM g is c = n_gemm it + g + 1; wait parity (c - 1) & 1
     auto xfree_par = [&](int it_, int g) -> uint32_t { return (uint32_t)(n_gemm * it_ + g) & 1u; };
-    const bool etr = a.trace != nullptr && blockIdx.x == 0 && e == 0 && lane == 0;
+    const bool etr = RTN_TRACE && a.trace != nullptr && blockIdx.x == 0 && e == 0 && lane == 0;
     long long ew = 0;
     auto wwait = [&](uint32_t bar, uint32_t par) -> bool {
       int w_ok = 0;

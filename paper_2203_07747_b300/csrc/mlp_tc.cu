@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       int it = 0;
       WaitClock wc(a.trace != nullptr && blockIdx.x == 0);
-      const bool tl = lane == 0;
+      const bool tl = RTN_TRACE && lane == 0;
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it)
         for (int l = 0; l < n_layers && ok; ++l) {
           if (tl) trace(a, it, l, n_layers, 0);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     float zpref = (et < NZV) ? load_z(a, blockIdx.x * NPC + et / NZ, et % NZ) : 0.0f;
     uint32_t acc_par = 0, xf_par = 0, zf_par = 0, zr_ph = 0;
     bool ok = true, first_input = true;
-    const bool tr = (e == 0 && lane == 0);
+    const bool tr = RTN_TRACE && (e == 0 && lane == 0);
 
     // bounded wait by lane 0, result shared with the warp
     long long epi_wait = 0;

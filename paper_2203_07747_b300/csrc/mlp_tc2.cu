@@ -245,7 +245,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
       int it = 0;
       WaitClock wc(a.trace != nullptr && blockIdx.x == 0);
       long long w_odd = 0, w_even = 0;
-      const bool tl = lane == 0;
+      const bool tl = RTN_TRACE && lane == 0;
       for (int tile = pair; tile < n_tiles && ok; tile += n_pairs, ++it)
         for (int l = 0; l < n_layers && ok; ++l) {
           if (tl) trace(a, it, l, n_layers, 0);
@@ -354,7 +354,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     float zpref = (et < NZV) ? load_z(a, pair * NPC + et / NZ, et % NZ) : 0.0f;
     uint32_t acc_par = 0, sf_ph = 0, ss_par = 0, zf_par = 0, zr_ph = 0;
     bool ok = true;
-    const bool tr = (rank == 0 && e == 0 && lane == 0);
+    const bool tr = RTN_TRACE && (rank == 0 && e == 0 && lane == 0);
     const uint32_t tf0 = mapa(tmem_free(0), 0);
     const uint32_t xr0 = mapa(xready(0), 0), lo1 = mapa(lo_in(0), 1), xi0 = mapa(xin(0), 0);
     // xfree[j] completes once per MMA layer: completion c (from 1) of this

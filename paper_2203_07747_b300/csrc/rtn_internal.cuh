@@ -11,6 +11,14 @@
 
 #include "../../include/rtn.h"
 
+// Phase tracing of the fused tensor-core network kernels (rtn_tc_trace) is a
+// profiling aid compiled in only with -DRTN_TRACE=1; otherwise every trace
+// branch is removed at compile time and rtn_tc_trace reports
+// RTN_E_UNSUPPORTED.
+#ifndef RTN_TRACE
+#define RTN_TRACE 0
+#endif
+
 namespace rtn {
 
 constexpr int NX = 13;

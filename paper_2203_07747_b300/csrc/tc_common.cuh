@@ -120,7 +120,7 @@ __device__ __forceinline__ unsigned long long gtime() {
 
 // trace slot of (tile index within this CTA, layer, field): CTA 0 only
 __device__ __forceinline__ void trace(const TcArgs& a, int it, int l, int n_layers, int f) {
-  if (a.trace && blockIdx.x == 0) {
+  if (RTN_TRACE && a.trace && blockIdx.x == 0) {
     const int idx = ((it * (n_layers + 1) + l) * 8 + f);
     if (idx < (1 << 16)) a.trace[idx] = gtime();
   }
@@ -129,7 +129,7 @@ __device__ __forceinline__ void trace(const TcArgs& a, int it, int l, int n_laye
 // trace slot written with a value (cycle counts of the waits, fields 4..7)
 __device__ __forceinline__ void trace_put(const TcArgs& a, int it, int l, int n_layers, int f,
                                           long long v) {
-  if (a.trace && blockIdx.x == 0) {
+  if (RTN_TRACE && a.trace && blockIdx.x == 0) {
     const int idx = ((it * (n_layers + 1) + l) * 8 + f);
     if (idx < (1 << 16)) a.trace[idx] = (unsigned long long)v;
   }
@@ -139,7 +139,7 @@ __device__ __forceinline__ void trace_put(const TcArgs& a, int it, int l, int n_
 struct WaitClock {
   bool on;
   long long t0 = 0;
-  __device__ __forceinline__ explicit WaitClock(bool on_) : on(on_) {}
+  __device__ __forceinline__ explicit WaitClock(bool on_) : on(RTN_TRACE && on_) {}
   __device__ __forceinline__ void start() {
     if (on) t0 = clock64();
   }
