@@ -154,11 +154,11 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make(prob, precision, riccati_f64=False, box_qp=False):
+def make(prob, precision, riccati_f64=False, box_qp=False, train_bf16=False):
     import paper_2203_07747_b300 as rtn
     return rtn.Controller(prob["N"], prob["dt"], prob["Q"], prob["R"], QN=prob["QN"], quad=prob["quad"],
                           layers=prob["layers"], precision=precision, riccati_f64=riccati_f64,
-                          box_qp=box_qp)
+                          box_qp=box_qp, train_bf16=train_bf16)
 
 
 def launches_per_step(ctl, tile_mode=None):
@@ -529,46 +529,61 @@ def bench_riccati(prob, precision, tile, steps=20):
 
 def bench_learned(bf16_burst, epochs=2, steps=100):
     """cfg5: 2^20 seeded samples -> drag residual targets, train 17-512x6-3
-    (Adam, lr 1e-3, batch 4096), then a 4096-instance closed loop on the drag
-    plant with the learned network vs the nominal model."""
+    (Adam, lr 1e-3, batch 4096) with BF16 GEMM operands and FP32
+    accumulation (and, timed beside it, with split BF16 hi + lo operands),
+    then a 4096-instance closed loop on the drag plant with the learned
+    network vs the nominal model."""
     import torch
     prob = W.make_problem("cfg5_learned", seed=0, bf16=True)
     n = prob["cfg"]["n_samples"]
     X, U = W.training_samples(n, 0)
     Xd = torch.as_tensor(X, dtype=torch.float32, device="cuda")
     Ud = torch.as_tensor(U, dtype=torch.float32, device="cuda")
-    learn = make(prob, "bf16x2")
-    Yd = learn.drag_targets(Xd)
-    # untimed warm-up on a throwaway controller: the first training GEMMs of
-    # a process pay the library's one-time setup
-    bs = prob["cfg"]["batch"]
-    warm = make(prob, "bf16x2")
-    warm.train(Xd[:2 * bs], Ud[:2 * bs], Yd[:2 * bs], epochs=1, batch=bs, lr=prob["cfg"]["lr"])
-    warm.close()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    losses = learn.train(Xd, Ud, Yd, epochs=epochs, batch=prob["cfg"]["batch"], lr=prob["cfg"]["lr"])
-    t_train = time.perf_counter() - t0
+    bs, lr = prob["cfg"]["batch"], prob["cfg"]["lr"]
     w = prob["widths"]
     fwd = 2 * sum(a * b for a, b in zip(w[:-1], w[1:]))
-    flops = 3 * fwd * epochs * (n // prob["cfg"]["batch"]) * prob["cfg"]["batch"]
+    flops = 3 * fwd * epochs * (n // bs) * bs
+    runs = {}
+    for mode in (True, False):
+        learn = make(prob, "bf16x2", train_bf16=mode)
+        Yd = learn.drag_targets(Xd)
+        # untimed warm-up on a throwaway controller: the first training GEMMs
+        # of a process pay the one-time setup
+        warm = make(prob, "bf16x2", train_bf16=mode)
+        warm.train(Xd[:2 * bs], Ud[:2 * bs], Yd[:2 * bs], epochs=1, batch=bs, lr=lr)
+        warm.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = learn.train(Xd, Ud, Yd, epochs=epochs, batch=bs, lr=lr)
+        t_train = time.perf_counter() - t0
+        runs[mode] = (learn, losses, t_train)
+    learn, losses, t_train = runs[True]
+    split, losses_s, t_split = runs[False]
+    split.close()
     learn.autotune()
     _, _, rmse_l = time_closed_loop(learn, prob, steps, 3)
     nominal = make(dict(prob, layers=None), "fp32")
     _, _, rmse_n = time_closed_loop(nominal, prob, steps, 3)
     learn.close(); nominal.close()
+    samples = epochs * (n // bs) * bs
     return {"workload": "cfg5_learned: %d samples, MLP %s, Adam lr 1e-3 batch 4096, %d epochs, "
                         "then %d-step closed loop of 4096 instances on the drag plant" % (
                             n, "-".join(map(str, w)), epochs, steps),
-            "train_samples_per_s": epochs * (n // prob["cfg"]["batch"]) * prob["cfg"]["batch"] / t_train,
+            "train_samples_per_s": samples / t_train,
             "train_tflops": flops / t_train / 1e12,
+            "ms_per_train_step": 1e3 * t_train / (epochs * (n // bs)),
             "train_precision": "own tcgen05 GEMMs (forward + bias/tanh, backward + tanh', weight gradient split "
-                               "over the batch) with BF16 hi + lo operands (3 MMAs per product), FP32 accumulation; "
-                               "fused Adam",
+                               "over the batch) with BF16 operands (one MMA per product), FP32 accumulation, FP32 "
+                               "master weights; fused Adam",
             "train_roofline": {"bound": "tensor", "peak": bf16_burst, "frac": flops / t_train / 1e12 / bf16_burst,
-                               "note": "peak = measured BF16 burst; the split operands issue 3 BF16 MMAs per "
-                                       "algorithmic product (frac <= 1/3), and the timing includes the loss, Adam "
-                                       "and gather launches and the final repack of the network"},
+                               "note": "peak = measured BF16 burst; the timing includes the loss, Adam and gather "
+                                       "launches and the final repack of the network"},
+            "split_operands": {"train_tflops": flops / t_split / 1e12,
+                               "ms_per_train_step": 1e3 * t_split / (epochs * (n // bs)),
+                               "frac": flops / t_split / 1e12 / bf16_burst,
+                               "note": "BF16 hi + lo operands, 3 MMAs per product (frac <= 1/3), the precision of "
+                                       "the gradient tests against the oracle (~1e-5)",
+                               "loss_last": float(losses_s[-10:].mean())},
             "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
             "tracking_rmse_m": {"learned": rmse_l, "nominal": rmse_n}}
 

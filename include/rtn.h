@@ -137,6 +137,11 @@ typedef struct {
                        3-output first-order residual, the FP32 sweep and no
                        bounds in the QP (other contexts run the separate
                        launches).  0: separate launches */
+  int train_bf16;   /* GEMMs of rtn_train and rtn_mse_grad: 0 BF16 hi + lo
+                       split operands (three MMAs per product, relative error
+                       ~1e-5); 1 operands rounded to BF16 (one MMA per product:
+                       a third of the tensor work and half the operand bytes),
+                       FP32 accumulation and FP32 master weights in either */
 } rtn_options;
 
 /* Create a controller batch of `batch` instances with horizons N[b] >= 1 and
@@ -272,8 +277,9 @@ rtn_status rtn_drag_targets(rtn_ctx* ctx, const float* X, int n, float* Y);
  * network on n samples (X dev [n][13], U dev [n][4], Y dev [n][no]) and its
  * gradient: grad dev float [n_weights + n_biases] packed as all W[l]
  * (row-major, layer order) then all b[l]; loss dev float [1].  The GEMMs of
- * rtn_train (split BF16 operands, FP32 accumulation: relative error ~1e-5)
- * and FP32 elementwise steps. */
+ * rtn_train (split BF16 operands, FP32 accumulation: relative error ~1e-5;
+ * with rtn_options.train_bf16 BF16 operands, ~1e-2) and FP32 elementwise
+ * steps. */
 rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const float* Y, int n,
                         float* grad, float* loss);
 
@@ -282,8 +288,9 @@ rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const floa
  * the n samples in consecutive minibatches of `batch` (the remainder of each
  * pass is skipped), learning rate lr.  FP32 master weights; the forward,
  * backward and weight-gradient GEMMs run on the tcgen05 tensor cores with
- * BF16 hi + lo split operands (three MMAs per product) and FP32
- * accumulation, their bias / tanh / tanh' epilogues fused; one fused Adam
+ * BF16 hi + lo split operands (three MMAs per product; with
+ * rtn_options.train_bf16 BF16 operands, one MMA) and FP32 accumulation,
+ * their bias / tanh / tanh' epilogues fused; one fused Adam
  * launch per weight matrix (which also refreshes the split weights) and one
  * for the biases.  Adam state persists across calls.  loss_out (host, may be
  * NULL) receives the loss of every step [epochs * (n / batch)].  Afterwards

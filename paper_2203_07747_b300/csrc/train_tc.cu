@@ -6,7 +6,9 @@
 //   weight gradient dW_l = G_{l+1} A_l'  (split over the batch)          (TG_WG)
 // Operands are split into BF16 hi + lo pairs (x = hi + lo to ~2^-17), and
 // each product is the three MMAs hi*hi + hi*lo + lo*hi with FP32
-// accumulation in tensor memory.  Both operands of every GEMM are K-major:
+// accumulation in tensor memory; in the BF16 mode (TgArgs::split = 0) only
+// the hi tiles are loaded and each product is the one MMA hi*hi (operands
+// rounded to BF16, FP32 accumulation), and the epilogues write hi only.  Both operands of every GEMM are K-major:
 // the forward and backward GEMMs contract over features, so they read the
 // activations / gradients node-major ([node][feature]); the weight gradient
 // contracts over the batch, so it reads them feature-major ([feature][node]).
@@ -51,6 +53,7 @@ struct TgArgs {
   int m_rows, n_cols;   // real output rows / columns
   int mts, nts, nkb;    // M tiles, N tiles, K blocks per tile
   int ksplit;           // TG_WG: K ranges (one partial product each)
+  int split;            // 1: hi + lo operands, three MMAs; 0: hi only, one MMA
   const float* bias;    // TG_FWD, TG_OUT: [m_rows]
   // TG_FWD / TG_BWD outputs: node-major [node][ldn] and feature-major
   // [row][ldf], BF16 hi + lo; columns n >= n_cols of the feature-major rows
@@ -123,11 +126,13 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
         if (elect_one()) {
           const uint32_t sa = st0 + s * TG_STAGE;
           const int kx = (ks * a.nkb + kb) * TG_KB;
-          mbar_expect_tx(full_bar(s), TG_STAGE);
+          mbar_expect_tx(full_bar(s), a.split ? TG_STAGE : TG_A_BYTES + TG_B_BYTES);
           tma_load_2d(sa, &mp.ah, kx, mt * 128, full_bar(s));
-          tma_load_2d(sa + TG_A_BYTES, &mp.al, kx, mt * 128, full_bar(s));
           tma_load_2d(sa + 2 * TG_A_BYTES, &mp.bh, kx, nt * TG_N, full_bar(s));
-          tma_load_2d(sa + 2 * TG_A_BYTES + TG_B_BYTES, &mp.bl, kx, nt * TG_N, full_bar(s));
+          if (a.split) {
+            tma_load_2d(sa + TG_A_BYTES, &mp.al, kx, mt * 128, full_bar(s));
+            tma_load_2d(sa + 2 * TG_A_BYTES + TG_B_BYTES, &mp.bl, kx, nt * TG_N, full_bar(s));
+          }
         }
         __syncwarp();
         issued |= 1u << s;
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
         }
       }
   } else if (warp == 1) {
-    // ---------------- MMA issuer: hi*hi + hi*lo + lo*hi per K step
+    // ---------------- MMA issuer: hi*hi (+ hi*lo + lo*hi when split) per K step
     constexpr uint32_t idesc = idesc_bf16(128, TG_N);
     int s = 0, acc = 0;
     uint32_t ph = 0, aph = 0;
@@ -163,8 +168,10 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
           const uint64_t bh = kmajor_desc(sa + 2 * TG_A_BYTES + k * 32u, TG_SBO, TG_SWZ);
           const uint64_t bl = kmajor_desc(sa + 2 * TG_A_BYTES + TG_B_BYTES + k * 32u, TG_SBO, TG_SWZ);
           mma_bf16_elect(d, ah, bh, idesc, (kb | k) != 0);
-          mma_bf16_elect(d, ah, bl, idesc, 1u);
-          mma_bf16_elect(d, al, bh, idesc, 1u);
+          if (a.split) {
+            mma_bf16_elect(d, ah, bl, idesc, 1u);
+            mma_bf16_elect(d, al, bh, idesc, 1u);
+          }
         }
         mma_commit_elect(empty_bar(s));
         if (++s == TG_STAGES) { s = 0; ph ^= 1u; }
@@ -203,7 +210,12 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
           const int ir = row_ok ? i : 0;
           const uint4* h4 = reinterpret_cast<const uint4*>(a.afh + (size_t)ir * a.ldf + j0);
           const uint4* l4 = reinterpret_cast<const uint4*>(a.afl + (size_t)ir * a.ldf + j0);
-          pa[0] = h4[0]; pa[1] = h4[1]; pa[2] = l4[0]; pa[3] = l4[1];
+          pa[0] = h4[0]; pa[1] = h4[1];
+          if (a.split) {
+            pa[2] = l4[0]; pa[3] = l4[1];
+          } else {
+            pa[2] = pa[3] = make_uint4(0u, 0u, 0u, 0u);
+          }
         }
         tmem_wait_ld();
         if (MODE == TG_WG) {
@@ -254,15 +266,17 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
             uint4* fl = reinterpret_cast<uint4*>(a.yfl + (size_t)i * a.ldf + j0);
             fh[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
             fh[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
-            fl[0] = make_uint4(lp[0], lp[1], lp[2], lp[3]);
-            fl[1] = make_uint4(lp[4], lp[5], lp[6], lp[7]);
+            if (a.split) {
+              fl[0] = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+              fl[1] = make_uint4(lp[4], lp[5], lp[6], lp[7]);
+            }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
               if (j0 + k < a.n_cols) {
                 const uint32_t hw = hp[k >> 1] >> (16 * (k & 1)), lw = lp[k >> 1] >> (16 * (k & 1));
                 const size_t o = (size_t)(j0 + k) * a.ldn + i;
                 reinterpret_cast<uint16_t*>(a.ynh)[o] = (uint16_t)(hw & 0xffffu);
-                reinterpret_cast<uint16_t*>(a.ynl)[o] = (uint16_t)(lw & 0xffffu);
+                if (a.split) reinterpret_cast<uint16_t*>(a.ynl)[o] = (uint16_t)(lw & 0xffffu);
               }
             }
           }
@@ -326,11 +340,12 @@ bool tg_map(CUtensorMap* m, const __nv_bfloat16* p, long long rows, int k_extent
 // cannot be encoded.
 bool tg_plan(TgGemm& g, int mode, const __nv_bfloat16* ah, const __nv_bfloat16* al, long long rows_a,
              int lda, const __nv_bfloat16* bh, const __nv_bfloat16* bl, long long rows_b, int ldb, int k_blocks,
-             int m_rows, int n_cols, int n_sm) {
+             int m_rows, int n_cols, int n_sm, bool split) {
   g.mode = mode;
   g.nt = mode == TG_WG ? 256 : 128;
   TgArgs& a = g.args;
   a = TgArgs{};
+  a.split = split ? 1 : 0;
   a.m_rows = m_rows;
   a.n_cols = n_cols;
   a.mts = (m_rows + 127) / 128;
@@ -496,37 +511,65 @@ __global__ void tg_reduce_kernel(const float* __restrict__ part, int ks, size_t 
   g[e] = s;
 }
 
-// one layer's weights W [fo][fi]: with adam, the Adam step (bias-corrected,
-// step t) from the summed partials; then the split copies W (hi, lo)
-// [fo][ldw] and W' (hi, lo) [fi][ldwt]
-__global__ void tg_weights_kernel(float* __restrict__ P, const float* __restrict__ part, int ks, int fo, int fi,
-                                  int adam, float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                                  float eps, const int* __restrict__ t_dev, __nv_bfloat16* __restrict__ wh,
-                                  __nv_bfloat16* __restrict__ wl, int ldw, __nv_bfloat16* __restrict__ th,
-                                  __nv_bfloat16* __restrict__ tl, int ldwt) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+// one layer's weights W [fo][fi] in 32 x 32 tiles (block 32 x 8): with adam,
+// the Adam step (bias-corrected, step t) from the summed partials; then the
+// split copies W (hi, lo) [fo][ldw] and W' (hi, lo) [fi][ldwt], the
+// transpose through shared memory so that both copies are stored coalesced
+__global__ void __launch_bounds__(256) tg_weights_kernel(float* __restrict__ P, const float* __restrict__ part, int ks,
+                                                         int fo, int fi, int adam, float* __restrict__ m,
+                                                         float* __restrict__ v, float lr, float b1, float b2, float eps,
+                                                         const int* __restrict__ t_dev, __nv_bfloat16* __restrict__ wh,
+                                                         __nv_bfloat16* __restrict__ wl, int ldw,
+                                                         __nv_bfloat16* __restrict__ th, __nv_bfloat16* __restrict__ tl,
+                                                         int ldwt) {
+  __shared__ uint32_t tile[32][33];  // hi | lo << 16
   const size_t n = (size_t)fo * fi;
-  if (e >= n) return;
-  float p = P[e];
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  float c1 = 1.0f, c2 = 1.0f;
   if (adam) {
-    const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
-    float g = 0.0f;
-    for (int k = 0; k < ks; ++k) g += part[(size_t)k * n + e];
-    const float mi = b1 * m[e] + (1.0f - b1) * g;
-    const float vi = b2 * v[e] + (1.0f - b2) * g * g;
-    m[e] = mi;
-    v[e] = vi;
-    p -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    P[e] = p;
+    c1 = 1.0f - powf(b1, (float)*t_dev);
+    c2 = 1.0f - powf(b2, (float)*t_dev);
   }
-  const int i = (int)(e / fi), j = (int)(e % fi);
-  __nv_bfloat16 h, l;
-  split2(p, h, l);
-  wh[(size_t)i * ldw + j] = h;
-  wl[(size_t)i * ldw + j] = l;
-  th[(size_t)j * ldwt + i] = h;
-  tl[(size_t)j * ldwt + i] = l;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = threadIdx.y + 8 * k, i = blockIdx.y * 32 + r;
+    uint32_t packed = 0u;
+    if (i < fo && j < fi) {
+      const size_t e = (size_t)i * fi + j;
+      float p = P[e];
+      if (adam) {
+        float g = 0.0f;
+        for (int q = 0; q < ks; ++q) g += part[(size_t)q * n + e];
+        const float mi = b1 * m[e] + (1.0f - b1) * g;
+        const float vi = b2 * v[e] + (1.0f - b2) * g * g;
+        m[e] = mi;
+        v[e] = vi;
+        p -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        P[e] = p;
+      }
+      __nv_bfloat16 h, l;
+      split2(p, h, l);
+      wh[(size_t)i * ldw + j] = h;
+      wl[(size_t)i * ldw + j] = l;
+      packed = (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+    }
+    tile[r][threadIdx.x] = packed;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = threadIdx.y + 8 * k;
+    const int jt = blockIdx.x * 32 + c, it = blockIdx.y * 32 + threadIdx.x;
+    if (jt < fi && it < fo) {
+      const uint32_t pk = tile[threadIdx.x][c];
+      th[(size_t)jt * ldwt + it] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
+      tl[(size_t)jt * ldwt + it] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+    }
+  }
 }
+
+inline dim3 wgrid(int fo, int fi) { return dim3((unsigned)((fi + 31) / 32), (unsigned)((fo + 31) / 32)); }
+const dim3 WBLOCK(32, 8);
 
 // fused Adam of the biases
 __global__ void tg_adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
@@ -601,11 +644,9 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
       const size_t nwl = (size_t)rup(w[l + 1], 128) * rup(w[l], 32), ntl = (size_t)rup(w[l], 128) * rup(w[l + 1], 32);
       for (int k = 0; k < 4; ++k)
         if ((e = zalloc(&ts.ws[4 * l + k], k < 2 ? nwl : ntl))) return e;
-      const size_t n = (size_t)w[l + 1] * w[l];
-      tg_weights_kernel<<<nblk(n), 256, 0, ctx->stream>>>(net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0,
-                                                          nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr,
-                                                          ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32),
-                                                          ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
+      tg_weights_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(
+          net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr,
+          ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
     }
     if ((e = cudaGetLastError())) return e;
   }
@@ -644,11 +685,12 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
   P->wg.assign(L, TgGemm{});
   P->bwd.assign(L, TgGemm{});
   int* derr = net.tc.err;
+  const bool split = !ctx->opt.train_bf16;
   for (int l = 0; l < L; ++l) {
     const bool out = l == L - 1;
     TgGemm& g = P->fwd[l];
     if (!tg_plan(g, out ? TG_OUT : TG_FWD, ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l + 1], 128), rup(w[l], 32),
-                 ts.an[2 * l], ts.an[2 * l + 1], ts.rows, rup(w[l], 32), rup(w[l], 32) / 32, w[l + 1], bs, n_sm)) {
+                 ts.an[2 * l], ts.an[2 * l + 1], ts.rows, rup(w[l], 32), rup(w[l], 32) / 32, w[l + 1], bs, n_sm, split)) {
       err = "training: tensor map encoding failed";
       return cudaSuccess;
     }
@@ -660,7 +702,7 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
     // dW_l = G_{l+1} A_l' over the batch
     TgGemm& gw = P->wg[l];
     if (!tg_plan(gw, TG_WG, ts.gf[2 * l], ts.gf[2 * l + 1], rup(w[l + 1], 256), ts.ldf, ts.af[2 * l],
-                 ts.af[2 * l + 1], rup(w[l], 256), ts.ldf, rup(bs, 32) / 32, w[l + 1], w[l], n_sm)) {
+                 ts.af[2 * l + 1], rup(w[l], 256), ts.ldf, rup(bs, 32) / 32, w[l + 1], w[l], n_sm, split)) {
       err = "training: tensor map encoding failed";
       return cudaSuccess;
     }
@@ -674,7 +716,7 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
     if (l >= 1) {
       TgGemm& gb = P->bwd[l];
       if (!tg_plan(gb, TG_BWD, ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l], 128), rup(w[l + 1], 32), ts.gn[2 * l],
-                   ts.gn[2 * l + 1], ts.rows, rup(w[l + 1], 32), rup(w[l + 1], 32) / 32, w[l], bs, n_sm)) {
+                   ts.gn[2 * l + 1], ts.rows, rup(w[l + 1], 32), rup(w[l + 1], 32) / 32, w[l], bs, n_sm, split)) {
         err = "training: tensor map encoding failed";
         return cudaSuccess;
       }
@@ -752,8 +794,7 @@ cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   tg_step_kernel<<<1, 1, 0, ctx->stream>>>(ts.t_dev);
   for (int l = 0; l < net.n_layers; ++l) {
-    const size_t n = (size_t)w[l + 1] * w[l];
-    tg_weights_kernel<<<nblk(n), 256, 0, ctx->stream>>>(
+    tg_weights_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(
         net.W32 + net.w_off[l], ts.part + ts.part_off[l], ts.ksplit[l], w[l + 1], w[l], 1, ts.m + net.w_off[l],
         ts.v + net.w_off[l], lr, b1, b2, eps, ts.t_dev, ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32),
         ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
@@ -768,11 +809,9 @@ cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts) {
   const std::vector<int>& w = net.widths;
   if (ts.ws.empty()) return cudaSuccess;
   for (int l = 0; l < net.n_layers; ++l) {
-    const size_t n = (size_t)w[l + 1] * w[l];
-    tg_weights_kernel<<<nblk(n), 256, 0, ctx->stream>>>(net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0,
-                                                        nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr, ts.ws[4 * l],
-                                                        ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2],
-                                                        ts.ws[4 * l + 3], rup(w[l + 1], 32));
+    tg_weights_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(
+        net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr,
+        ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
   }
   return cudaGetLastError();
 }

@@ -26,9 +26,9 @@ def f32(a):
     return np.asarray(a, np.float32).astype(np.float64)
 
 
-def ctl_for(rtn, layers, B=2, precision="fp32"):
+def ctl_for(rtn, layers, B=2, precision="fp32", train_bf16=False):
     return rtn.Controller(np.full(B, 5, np.int32), np.full(B, 0.05), W.Q_DIAG, W.R_DIAG, quad=QUAD,
-                          layers=layers, precision=precision)
+                          layers=layers, precision=precision, train_bf16=train_bf16)
 
 
 def test_drag_targets_match_oracle(rtn, orc):
@@ -63,6 +63,59 @@ def test_mse_gradient_matches_oracle(rtn, orc, widths, n):
         assert np.linalg.norm(gb - br) / np.linalg.norm(br) < 1e-5
         ow += Wr.size
         ob += br.size
+
+
+@pytest.mark.parametrize("widths,n", [([17, 32, 32, 3], 256), ([17, 100, 60, 70, 3], 333),
+                                      ([17, 512, 512, 512, 3], 1024)])
+def test_mse_gradient_bf16_operands(rtn, orc, widths, n):
+    # train_bf16: every GEMM operand rounded to BF16 (one MMA per product),
+    # FP32 accumulation.  Each rounding moves an operand by <= 2^-9 relative;
+    # a gradient passes through ~2 L of them (activations forward, gradients
+    # backward), so its norm-relative error stays near 2^-9 sqrt(2 L) < 1e-2:
+    # gate 2e-2 per layer, and the loss (one forward pass) 5e-3
+    layers = [(f32(w), f32(np.random.default_rng(i).normal(0, 0.1, b.shape))) for i, (w, b) in
+              enumerate(W.xavier_mlp(widths, 1))]
+    X, U = W.training_samples(n, 4)
+    X, U = f32(X), f32(U)
+    Y = orc.drag_targets(X)
+    Z = np.concatenate([X, U], 1)
+    loss_r, G_r = orc.mse_grad(layers, Z, Y)
+    ctl = ctl_for(rtn, layers, train_bf16=True)
+    loss, g = ctl.mse_grad(dev(X), dev(U), dev(Y))
+    g = g.double().cpu().numpy()
+    assert abs(loss - loss_r) / loss_r < 5e-3
+    nw = sum(w.size for w, _ in layers)
+    ow, ob = 0, nw
+    errs = []
+    for (Wr, br) in G_r:
+        gw = g[ow:ow + Wr.size].reshape(Wr.shape)
+        gb = g[ob:ob + br.size]
+        errs.append((np.linalg.norm(gw - Wr) / np.linalg.norm(Wr), np.linalg.norm(gb - br) / np.linalg.norm(br)))
+        ow += Wr.size
+        ob += br.size
+    assert max(max(e) for e in errs) < 2e-2, errs
+    # and it is a BF16 result, not the split one: some layer is off by > 1e-5
+    assert max(max(e) for e in errs) > 1e-5, errs
+
+
+def test_bf16_training_follows_split_training(rtn, orc):
+    # the same 64 Adam steps with BF16 and with split operands: the BF16
+    # losses stay within 2% of the split ones and both fall
+    widths = [17, 128, 128, 128, 3]
+    layers = [(f32(w), f32(b)) for w, b in W.xavier_mlp(widths, 6)]
+    n, bs = 8192, 256
+    X, U = W.training_samples(n, 9)
+    X, U = f32(X), f32(U)
+    Y = f32(orc.drag_targets(X))
+    out = {}
+    for mode in (False, True):
+        ctl = ctl_for(rtn, layers, train_bf16=mode)
+        out[mode] = ctl.train(dev(X), dev(U), dev(Y), epochs=2, batch=bs, lr=1e-3)
+        ctl.close()
+    a, b = out[False], out[True]
+    assert len(a) == len(b) == 2 * (n // bs)
+    assert a[-8:].mean() < 0.5 * a[:8].mean() and b[-8:].mean() < 0.5 * b[:8].mean()
+    assert np.max(np.abs(b - a) / a) < 2e-2, np.max(np.abs(b - a) / a)
 
 
 def test_adam_training_trajectory_matches_oracle(rtn, orc):
