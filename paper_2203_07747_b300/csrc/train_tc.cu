@@ -13,8 +13,8 @@
 // activations / gradients node-major ([node][feature]); the weight gradient
 // contracts over the batch, so it reads them feature-major ([feature][node]).
 // The epilogues write every activation and gradient in both layouts.
-// Tiles: M = 128 rows x N = 256 columns, K in blocks of 32 (64 B swizzle),
-// four TMA stages, two TMEM accumulators; persistent CTAs; one warp issues
+// Tiles: M = 128 rows x N = 128 columns, K in blocks of 32 (64 B swizzle),
+// six TMA stages, two TMEM accumulators; persistent CTAs; one warp issues
 // the TMA copies, one the MMAs, eight run the epilogue.
 #include <algorithm>
 #include <vector>
@@ -30,9 +30,10 @@ constexpr int TG_EPI_WARPS = 8;
 constexpr uint32_t TG_SBO = 512;  // 8 rows x 64 B
 constexpr uint32_t TG_SWZ = 4;    // 64 B swizzle
 constexpr uint32_t TG_A_BYTES = 128u * TG_KB * 2u;
-// N tile NT: 128 columns for the forward and backward GEMMs (twice the
-// tiles of a 512 x batch GEMM, so that more SMs pull operands) with six
-// stages, 256 for the weight gradient (already split over the batch) with four
+// N tile NT: 128 columns (twice the tiles of a 512 x batch GEMM, so that
+// more SMs pull operands) with six stages; the weight gradient too (with 256
+// columns it ran 9% slower per training step: its batch split twice as
+// deep, so the Adam launch summed twice the partial products)
 template <int NT>
 struct Tg {
   static constexpr int STAGES = NT == 128 ? 6 : 4;
@@ -44,6 +45,8 @@ struct Tg {
 static_assert(Tg<128>::SMEM <= 232448 && Tg<256>::SMEM <= 232448, "shared memory");
 
 enum { TG_FWD = 0, TG_OUT = 1, TG_BWD = 2, TG_WG = 3 };
+// N tile of the weight gradient
+constexpr int TG_WG_NT = 128;
 
 struct TgMaps {
   CUtensorMap ah, al, bh, bl;
@@ -62,6 +65,9 @@ struct TgArgs {
   int ldn, ldf;
   // TG_BWD: the layer's activations A_l feature-major [row][ldf], hi + lo
   const __nv_bfloat16 *afh, *afl;
+  // TG_BWD: the bias gradient of the produced layer, sum over the batch of
+  // G_l, accumulated atomically (zeroed before the step)
+  float* db;
   float* out;  // TG_OUT: Z [node][m_rows]; TG_WG: partials [ksplit][m_rows][n_cols]
   int* err;
 };
@@ -194,6 +200,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
       const int mt = (int)(t % a.mts), nt = (int)((t / a.mts) % a.nts), ks = (int)(t / ((long long)a.mts * a.nts));
       const int i = mt * 128 + q * 32 + lane;
       const bool row_ok = i < a.m_rows;
+      float rsum = 0.0f;  // TG_BWD: the lane's row summed over its columns
       const float bi = (MODE == TG_FWD || MODE == TG_OUT) && row_ok ? __ldg(a.bias + i) : 0.0f;
       if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err)) break;
       tc_fence_after();
@@ -255,6 +262,10 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
 #pragma unroll
           for (int k = 0; k < 16; ++k)
             if (j0 + k >= a.n_cols) v[k] = 0.0f;
+          if (MODE == TG_BWD) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) rsum += v[k];
+          }
           uint32_t hp[8], lp[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
@@ -287,6 +298,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
       __syncwarp();
       if (lane == 0) mbar_arrive(tmem_free(acc));
       if (++acc == 2) { acc = 0; aph ^= 1u; }
+      if (MODE == TG_BWD && a.db && row_ok) atomicAdd(a.db + i, rsum);
     }
   }
 
@@ -342,7 +354,7 @@ bool tg_plan(TgGemm& g, int mode, const __nv_bfloat16* ah, const __nv_bfloat16* 
              int lda, const __nv_bfloat16* bh, const __nv_bfloat16* bl, long long rows_b, int ldb, int k_blocks,
              int m_rows, int n_cols, int n_sm, bool split) {
   g.mode = mode;
-  g.nt = mode == TG_WG ? 256 : 128;
+  g.nt = mode == TG_WG ? TG_WG_NT : 128;
   TgArgs& a = g.args;
   a = TgArgs{};
   a.split = split ? 1 : 0;
@@ -378,8 +390,8 @@ cudaError_t tg_setup() {
   if ((e = cudaFuncSetAttribute(tg_kernel<TG_BWD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Tg<128>::SMEM)))
     return e;
-  return cudaFuncSetAttribute(tg_kernel<TG_WG, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Tg<256>::SMEM);
+  return cudaFuncSetAttribute(tg_kernel<TG_WG, TG_WG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Tg<TG_WG_NT>::SMEM);
 }
 
 // err: the context's device status word (re-read at every launch: the
@@ -391,15 +403,17 @@ cudaError_t tg_launch(const TgGemm& g, int* err, cudaStream_t s) {
     case TG_FWD: tg_kernel<TG_FWD, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
     case TG_OUT: tg_kernel<TG_OUT, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
     case TG_BWD: tg_kernel<TG_BWD, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
-    default: tg_kernel<TG_WG, 256><<<g.grid, TG_THREADS, Tg<256>::SMEM, s>>>(g.maps, a); break;
+    default: tg_kernel<TG_WG, TG_WG_NT><<<g.grid, TG_THREADS, Tg<TG_WG_NT>::SMEM, s>>>(g.maps, a); break;
   }
   return cudaGetLastError();
 }
 
 // epilogue operands of a planned GEMM
 void tg_set_out(TgGemm& g, const float* bias, __nv_bfloat16* ynh, __nv_bfloat16* ynl, int ldn, __nv_bfloat16* yfh,
-                __nv_bfloat16* yfl, int ldf, const __nv_bfloat16* afh, const __nv_bfloat16* afl, float* out, int* err) {
+                __nv_bfloat16* yfl, int ldf, const __nv_bfloat16* afh, const __nv_bfloat16* afl, float* out, int* err,
+                float* db = nullptr) {
   TgArgs& a = g.args;
+  a.db = db;
   a.bias = bias;
   a.ynh = ynh; a.ynl = ynl; a.ldn = ldn;
   a.yfh = yfh; a.yfl = yfl; a.ldf = ldf;
@@ -446,17 +460,21 @@ __global__ void tg_gather_kernel(const float* __restrict__ X, const float* __res
 
 // G_L = 2 (Z - Y) / (no bs) (loss 1/(no bs) sum (Z - Y)^2): node-major
 // [rows][32] (columns >= no zero) and feature-major [no][ldf] (samples
-// j >= bs zero); the loss summed per block into *loss
+// j >= bs zero); the loss summed per block into *loss, and the output
+// layer's bias gradient (G_L summed over the batch) per block into db
 __global__ void tg_loss_kernel(const float* __restrict__ Z, const float* __restrict__ Y, int start, int bs, int no,
                                int ldf, __nv_bfloat16* __restrict__ nh, __nv_bfloat16* __restrict__ nl,
                                __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl, float* loss,
-                               const int* __restrict__ k_dev, int per_epoch) {
+                               float* __restrict__ db, const int* __restrict__ k_dev, int per_epoch) {
   // a replayed step: its minibatch and loss entry from the step counter on the device
   if (k_dev) {
     start = (*k_dev % per_epoch) * bs;
     loss += *k_dev;
   }
   __shared__ float red[256];
+  __shared__ float rsum[32];
+  if (threadIdx.x < 32) rsum[threadIdx.x] = 0.0f;
+  __syncthreads();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float e2 = 0.0f;
   if (e < (long long)ldf * 32) {
@@ -474,6 +492,7 @@ __global__ void tg_loss_kernel(const float* __restrict__ Z, const float* __restr
     if (r < no) {
       fh[(size_t)r * ldf + j] = h;
       fl[(size_t)r * ldf + j] = l;
+      atomicAdd(&rsum[r], g);
     }
   }
   red[threadIdx.x] = e2;
@@ -483,23 +502,7 @@ __global__ void tg_loss_kernel(const float* __restrict__ Z, const float* __restr
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(loss, red[0] / ((float)no * bs));
-}
-
-// db[i] = sum over the batch of G[i][:] (feature-major hi + lo; the columns
-// past the batch are zero), one block per row
-__global__ void tg_rowsum_kernel(const __nv_bfloat16* __restrict__ fh, const __nv_bfloat16* __restrict__ fl, int ldf,
-                                 float* __restrict__ db) {
-  __shared__ float red[256];
-  float s = 0.0f;
-  const size_t row = (size_t)blockIdx.x * ldf;
-  for (int j = threadIdx.x; j < ldf; j += 256) s += __bfloat162float(fh[row + j]) + __bfloat162float(fl[row + j]);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) db[blockIdx.x] = red[0];
+  if (threadIdx.x < no) atomicAdd(db + threadIdx.x, rsum[threadIdx.x]);
 }
 
 // weight-gradient partials of one layer summed: g[e] = sum_s part[s][e]
@@ -511,10 +514,19 @@ __global__ void tg_reduce_kernel(const float* __restrict__ part, int ks, size_t 
   g[e] = s;
 }
 
-// one layer's weights W [fo][fi] in 32 x 32 tiles (block 32 x 8): with adam,
-// the Adam step (bias-corrected, step t) from the summed partials; then the
-// split copies W (hi, lo) [fo][ldw] and W' (hi, lo) [fi][ldwt], the
-// transpose through shared memory so that both copies are stored coalesced
+// one layer's weights W [fo][fi] in 32 x 32 tiles, 256 threads, four
+// consecutive elements of a row per thread (float4 loads where the row length
+// allows): with adam, the Adam step (bias-corrected, step t) from the summed
+// partials; then the split copies W (hi, lo) [fo][ldw] and W' (hi, lo)
+// [fi][ldwt], the transpose through shared memory so that both copies are
+// stored as 8-byte runs
+__device__ __forceinline__ float adam_elem(float p, float g, float& m, float& v, float lr, float b1, float b2,
+                                           float eps, float c1, float c2) {
+  m = b1 * m + (1.0f - b1) * g;
+  v = b2 * v + (1.0f - b2) * g * g;
+  return p - lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
 __global__ void __launch_bounds__(256) tg_weights_kernel(float* __restrict__ P, const float* __restrict__ part, int ks,
                                                          int fo, int fi, int adam, float* __restrict__ m,
                                                          float* __restrict__ v, float lr, float b1, float b2, float eps,
@@ -524,52 +536,95 @@ __global__ void __launch_bounds__(256) tg_weights_kernel(float* __restrict__ P, 
                                                          int ldwt) {
   __shared__ uint32_t tile[32][33];  // hi | lo << 16
   const size_t n = (size_t)fo * fi;
-  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int r = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
+  const int i = blockIdx.y * 32 + r, j = blockIdx.x * 32 + c4;
   float c1 = 1.0f, c2 = 1.0f;
   if (adam) {
     c1 = 1.0f - powf(b1, (float)*t_dev);
     c2 = 1.0f - powf(b2, (float)*t_dev);
   }
+  float pv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (i < fo && j < fi) {
+    const size_t e = (size_t)i * fi + j;
+    if ((fi & 3) == 0) {  // j + 3 < fi and 16-byte aligned
+      float4 p4 = *reinterpret_cast<const float4*>(P + e);
+      pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
+      if (adam) {
+        float4 g4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 6
+        for (int q = 0; q < ks; ++q) {
+          const float4 x = *reinterpret_cast<const float4*>(part + (size_t)q * n + e);
+          g4.x += x.x; g4.y += x.y; g4.z += x.z; g4.w += x.w;
+        }
+        float4 m4 = *reinterpret_cast<const float4*>(m + e), v4 = *reinterpret_cast<const float4*>(v + e);
+        pv[0] = adam_elem(pv[0], g4.x, m4.x, v4.x, lr, b1, b2, eps, c1, c2);
+        pv[1] = adam_elem(pv[1], g4.y, m4.y, v4.y, lr, b1, b2, eps, c1, c2);
+        pv[2] = adam_elem(pv[2], g4.z, m4.z, v4.z, lr, b1, b2, eps, c1, c2);
+        pv[3] = adam_elem(pv[3], g4.w, m4.w, v4.w, lr, b1, b2, eps, c1, c2);
+        *reinterpret_cast<float4*>(m + e) = m4;
+        *reinterpret_cast<float4*>(v + e) = v4;
+        *reinterpret_cast<float4*>(P + e) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+      }
+    } else {
+      for (int k = 0; k < 4 && j + k < fi; ++k) {
+        float p = P[e + k];
+        if (adam) {
+          float g = 0.0f;
+          for (int q = 0; q < ks; ++q) g += part[(size_t)q * n + e + k];
+          p = adam_elem(p, g, m[e + k], v[e + k], lr, b1, b2, eps, c1, c2);
+          P[e + k] = p;
+        }
+        pv[k] = p;
+      }
+    }
+  }
+  uint32_t hw[2] = {0u, 0u}, lw[2] = {0u, 0u};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int r = threadIdx.y + 8 * k, i = blockIdx.y * 32 + r;
-    uint32_t packed = 0u;
-    if (i < fo && j < fi) {
-      const size_t e = (size_t)i * fi + j;
-      float p = P[e];
-      if (adam) {
-        float g = 0.0f;
-        for (int q = 0; q < ks; ++q) g += part[(size_t)q * n + e];
-        const float mi = b1 * m[e] + (1.0f - b1) * g;
-        const float vi = b2 * v[e] + (1.0f - b2) * g * g;
-        m[e] = mi;
-        v[e] = vi;
-        p -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        P[e] = p;
+    __nv_bfloat16 h, l;
+    split2(pv[k], h, l);
+    const uint32_t hb = __bfloat16_as_ushort(h), lb = __bfloat16_as_ushort(l);
+    hw[k >> 1] |= hb << (16 * (k & 1));
+    lw[k >> 1] |= lb << (16 * (k & 1));
+    tile[r][c4 + k] = hb | (lb << 16);
+  }
+  if (i < fo && j < fi) {
+    if ((fi & 3) == 0) {  // ldw is a multiple of 32: 8-byte aligned runs
+      *reinterpret_cast<uint2*>(wh + (size_t)i * ldw + j) = make_uint2(hw[0], hw[1]);
+      *reinterpret_cast<uint2*>(wl + (size_t)i * ldw + j) = make_uint2(lw[0], lw[1]);
+    } else {
+      for (int k = 0; k < 4 && j + k < fi; ++k) {
+        wh[(size_t)i * ldw + j + k] = __ushort_as_bfloat16((unsigned short)(tile[r][c4 + k] & 0xffffu));
+        wl[(size_t)i * ldw + j + k] = __ushort_as_bfloat16((unsigned short)(tile[r][c4 + k] >> 16));
       }
-      __nv_bfloat16 h, l;
-      split2(p, h, l);
-      wh[(size_t)i * ldw + j] = h;
-      wl[(size_t)i * ldw + j] = l;
-      packed = (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
     }
-    tile[r][threadIdx.x] = packed;
   }
   __syncthreads();
+  // W': row jt = column j of W, four consecutive rows of W per thread
+  const int jt = blockIdx.x * 32 + r, it = blockIdx.y * 32 + c4;
+  if (jt < fi && it < fo) {
+    uint32_t th2[2] = {0u, 0u}, tl2[2] = {0u, 0u};
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int c = threadIdx.y + 8 * k;
-    const int jt = blockIdx.x * 32 + c, it = blockIdx.y * 32 + threadIdx.x;
-    if (jt < fi && it < fo) {
-      const uint32_t pk = tile[threadIdx.x][c];
-      th[(size_t)jt * ldwt + it] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
-      tl[(size_t)jt * ldwt + it] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t pk = tile[c4 + k][r];
+      th2[k >> 1] |= (pk & 0xffffu) << (16 * (k & 1));
+      tl2[k >> 1] |= (pk >> 16) << (16 * (k & 1));
+    }
+    if (it + 3 < fo) {  // ldwt is a multiple of 32
+      *reinterpret_cast<uint2*>(th + (size_t)jt * ldwt + it) = make_uint2(th2[0], th2[1]);
+      *reinterpret_cast<uint2*>(tl + (size_t)jt * ldwt + it) = make_uint2(tl2[0], tl2[1]);
+    } else {
+      for (int k = 0; it + k < fo; ++k) {
+        const uint32_t pk = tile[c4 + k][r];
+        th[(size_t)jt * ldwt + it + k] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
+        tl[(size_t)jt * ldwt + it + k] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+      }
     }
   }
 }
 
 inline dim3 wgrid(int fo, int fi) { return dim3((unsigned)((fi + 31) / 32), (unsigned)((fo + 31) / 32)); }
-const dim3 WBLOCK(32, 8);
+const dim3 WBLOCK(256);
 
 // fused Adam of the biases
 __global__ void tg_adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
@@ -595,7 +650,7 @@ struct TgPlan {
 // batch ranges of the weight gradient of a fo x fi layer for up to cap
 // samples (tg_plan never splits a smaller batch into more)
 int wg_ksplit_max(int fo, int fi, int cap, int n_sm) {
-  const int base = ((fo + 127) / 128) * ((fi + 255) / 256), kb = rup(cap, 32) / 32;
+  const int base = ((fo + 127) / 128) * ((fi + TG_WG_NT - 1) / TG_WG_NT), kb = rup(cap, 32) / 32;
   return std::max(1, std::min(kb, n_sm / std::max(base, 1)));
 }
 
@@ -721,7 +776,8 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
         return cudaSuccess;
       }
       tg_set_out(gb, nullptr, ts.gn[2 * (l - 1)], ts.gn[2 * (l - 1) + 1], rup(w[l], 32), ts.gf[2 * (l - 1)],
-                 ts.gf[2 * (l - 1) + 1], ts.ldf, ts.af[2 * l], ts.af[2 * l + 1], nullptr, derr);
+                 ts.gf[2 * (l - 1) + 1], ts.ldf, ts.af[2 * l], ts.af[2 * l + 1], nullptr, derr,
+                 ts.grad + ts.b_base + net.b_off[l - 1]);
     }
   }
   ts.bs = bs;
@@ -757,17 +813,18 @@ static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const
   if (!P) return cudaErrorInvalidValue;
   cudaStream_t s = ctx->stream;
   cudaError_t e;
+  // the bias gradients are accumulated atomically by the loss and backward launches
+  if ((e = cudaMemsetAsync(ts.grad + ts.b_base, 0, ts.nb * sizeof(float), s))) return e;
   tg_gather_kernel<<<nblk((size_t)ts.ldf * 32), 256, 0, s>>>(X, U, start, bs, ts.ldf, ts.an[0], ts.an[1], ts.af[0],
                                                                ts.af[1], k_dev, per_epoch);
   for (int l = 0; l < L; ++l)
     if ((e = tg_launch(P->fwd[l], net.tc.err, s))) return e;
   tg_loss_kernel<<<nblk((size_t)ts.ldf * 32), 256, 0, s>>>(ts.z, Y, start, bs, no, ts.ldf, ts.gn[2 * (L - 1)],
                                                              ts.gn[2 * (L - 1) + 1], ts.gf[2 * (L - 1)],
-                                                             ts.gf[2 * (L - 1) + 1], loss, k_dev, per_epoch);
+                                                             ts.gf[2 * (L - 1) + 1], loss,
+                                                             ts.grad + ts.b_base + net.b_off[L - 1], k_dev, per_epoch);
   for (int l = L - 1; l >= 0; --l) {
     if ((e = tg_launch(P->wg[l], net.tc.err, s))) return e;
-    tg_rowsum_kernel<<<net.widths[l + 1], 256, 0, s>>>(ts.gf[2 * l], ts.gf[2 * l + 1], ts.ldf,
-                                                        ts.grad + ts.b_base + net.b_off[l]);
     if (l >= 1 && (e = tg_launch(P->bwd[l], net.tc.err, s))) return e;
   }
   return cudaGetLastError();
