@@ -43,9 +43,8 @@ def peaks():
     return 6400.0, 1800.0, 1400.0, "fallback"
 
 
-KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc2.cu", "mlp_rev.cu", "mlp_rev2.cu", "tc_common.cuh", "tc_pair.cuh")
-PROFILES = ("mlp_lay_cfg3_h512_bf16x2.md", "mlp_rev2_kernel_cfg3_h512_bf16x2.md", "mlp_rev_kernel_cfg3_h512_bf16x2.md",
-            "mlp_tc2_kernel_cfg3_h512_bf16x2.md", "mlp_tc_kernel_cfg3_h512_bf16x2.md")
+KERNEL_SOURCES = ("mlp_tc.cu", "mlp_rev.cu", "mlp_rev2.cu", "tc_common.cuh", "tc_pair.cuh")
+PROFILES = ("mlp_lay_cfg3_h512_bf16x2.md", "mlp_rev2_kernel_cfg3_h512_bf16x2.md", "mlp_rev_kernel_cfg3_h512_bf16x2.md", "mlp_tc_kernel_cfg3_h512_bf16x2.md")
 
 
 def kernel_md5(files=KERNEL_SOURCES):

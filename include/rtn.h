@@ -304,9 +304,9 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
 
 /* Tile shapes of the tensor-core network kernel (the autotuner's search
  * space).  rtn_tc_variants: number of compiled shapes.  rtn_tc_variant_info:
- * nodes per CTA (per CTA pair in modes 3 and 5; 0 in mode 6), operand mode
- * in *split (0 single BF16; 1, 2 split hi + lo on one CTA; 3 split on a CTA
- * pair, M = 256; 4 split, reverse mode: values forward, three output
+ * nodes per CTA (per CTA pair in mode 5; 0 in mode 6), operand mode
+ * in *split (0 single BF16; 1, 2 split hi + lo on one CTA; 3 is not used;
+ * 4 split, reverse mode: values forward, three output
  * adjoints backward; 5 the same on CTA pairs; 6 split, reverse mode layered:
  * one GEMM per layer over all nodes, 2 L launches, its buffers allocated
  * when the shape is first selected) and pipeline depth of shape idx,

@@ -254,7 +254,7 @@ class Controller:
         return code.value
 
     def tc_variants(self):
-        """[(index, nodes per CTA (per CTA pair in mode 3), operand mode 0|1|2|3, stages)]
+        """[(index, nodes per CTA (per CTA pair in mode 5), operand mode 0|1|2|4|5|6, stages)]
         of the tile shapes that fit."""
         L = load()
         n = C.c_int()

@@ -28,9 +28,8 @@
 // with d_l = 1 - a_l^2 in a per-pair FP32 scratch (node-major, L2-resident):
 // D_L = d_L (.) W_L' (SIMT), D_l = d_l (.) (W_l' D_{l+1}).
 //
-// Exchange of a block (128 rows of X) between the CTAs is that of
-// mlp_tc2.cu: block j is produced by rank j % 2 (the accumulator rows it
-// holds); the producer writes its own half into its X, stages the peer's half
+// Exchange of a block (128 rows of X) between the CTAs: block j is produced
+// by rank j % 2 (the accumulator rows it holds); the producer writes its own half into its X, stages the peer's half
 // and pushes it with a bulk copy that completes on a barrier of the peer; the
 // exchange warps relay the completion and free the staging block.  The input
 // layer (FP32 dot products over the 17 inputs) is exchanged the same way:

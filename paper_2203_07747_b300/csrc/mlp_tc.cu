@@ -9,8 +9,7 @@
 //     (RTN_BF16) or as a BF16 hi + lo pair (RTN_BF16X2: X = hi + lo, ~16
 //     significant bits), either in two buffers with two MMAs per K step
 //     (mode 1) or side by side along N in one MMA of twice the width whose
-//     two accumulator halves the epilogue adds (mode 2); mlp_tc2.cu runs the
-//     split on CTA pairs when one SM cannot hold it;
+//     two accumulator halves the epilogue adds (mode 2);
 //   * the weights W_l (M = output neurons, K-major) stream from L2 by TMA in
 //     128 x 64 tiles (128B swizzle) through an mbarrier pipeline;
 //   * the accumulators of all output neurons (M tiles of 128 lanes x N
@@ -368,14 +367,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 struct Variant {
   int npc;
-  int mode;  // 0 single, 1 split (two MMAs), 2 split (hi|lo along N), 3 split on a CTA pair,
+  int mode;  // 0 single, 1 split (two MMAs), 2 split (hi|lo along N), (3: the forward mode
+             // on CTA pairs, no longer compiled: it won no shape / batch size),
              // 4 split, reverse mode (value forward, three adjoints backward),
              // 5 split, reverse mode on a CTA pair,
              // 6 split, reverse mode layered (one GEMM per layer over all nodes)
   int stages;
   const void* fn;
   bool split() const { return mode != 0; }
-  bool pair() const { return mode == 3 || mode == 5; }
+  bool pair() const { return mode == 5; }
   bool rev() const { return mode == 4 || mode == 5; }
   int threads() const { return pair() ? THREADS + 32 : THREADS; }
   int cols() const { return rev() ? 128 : 16 * npc + ((2 * npc + 15) / 16) * 16; }
@@ -393,9 +393,6 @@ struct Variant {
     if (rev())
       return 1024 + (size_t)128 * HP * 2 + (size_t)stages * WT_BYTES + 8 * (2 * stages + 20) + 16 +
              (size_t)npc * ZS * 4;
-    if (pair())
-      return 1024 + (size_t)cols() * HP * 2 + (size_t)cols() * 256 + (size_t)stages * WT_BYTES +
-             8 * (2 * stages + 24) + 16 + (size_t)npc * NZ * 4;
     return 1024 + (mode != 0 ? 2 : 1) * (size_t)cols() * HP * 2 + (size_t)stages * WT_BYTES +
            8 * (2 * stages + 18) + 16 + (size_t)npc * NZ * 4;
   }
@@ -404,11 +401,6 @@ struct Variant {
 template <int NPC, int MODE, int STAGES>
 Variant variant() {
   return Variant{NPC, MODE, STAGES, (const void*)&mlp_tc_kernel<NPC, MODE, STAGES>};
-}
-
-template <int NPC, int STAGES>
-Variant pair_variant() {
-  return Variant{NPC, 3, STAGES, mlp_tc2_fn(NPC, STAGES)};
 }
 
 template <int NPC, int STAGES>
@@ -429,8 +421,7 @@ const std::vector<Variant>& all_variants() {
       variant<14, 0, 6>(), variant<14, 0, 5>(), variant<8, 0, 8>(), variant<7, 0, 5>(),
       variant<6, 0, 6>(),  variant<4, 0, 8>(),  variant<8, 1, 4>(),
       variant<5, 1, 6>(),  variant<4, 1, 3>(),  variant<3, 1, 6>(),  variant<7, 2, 5>(),
-      variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>(),  pair_variant<7, 4>(),
-      pair_variant<6, 5>(), pair_variant<7, 8>(), pair_variant<4, 6>(), rev_variant<21, 6>(),
+      variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>(),  rev_variant<21, 6>(),
       rev_variant<21, 4>(), rev_variant<16, 6>(), rev2_variant<3>(), rev2_variant<6>(), lay_variant()};
   return v;
 }
@@ -666,8 +657,7 @@ cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* 
   if (v.mode == 6) return mlp_lay_launch(ctx, x, u, fD, JD);
   if (v.mode == 5) return mlp_rev2_launch(ctx, x, u, fD, JD);
   if (v.rev()) return mlp_rev_launch(ctx, x, u, fD, JD);
-  dim3 grid = v.pair() ? dim3(2 * std::min(n_tiles, std::max(1, tc.n_sm / 2)))
-                       : dim3(std::min(n_tiles, std::max(1, tc.n_sm)));
+  const dim3 grid(std::min(n_tiles, std::max(1, tc.n_sm)));
   return cudaLaunchKernel(tc.fn, grid, dim3(v.threads()), args, tc.smem, ctx->stream);
 }
 

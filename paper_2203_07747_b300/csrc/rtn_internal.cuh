@@ -291,7 +291,6 @@ int mlp_tc_variant_count();
 int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages);
 cudaError_t mlp_tc_select(rtn_ctx* ctx, int idx);
 // kernel of the CTA-pair variant (npc nodes per pair, stages weight stages), or null
-const void* mlp_tc2_fn(int npc, int stages);
 // kernel of the reverse-mode variant, or null
 const void* mlp_rev_fn(int npc, int stages);
 // arguments of the reverse-mode kernel (mlp_rev.cu)

@@ -1,5 +1,6 @@
 // tc_common.cuh -- PTX wrappers and operand layouts shared by the tensor-core
-// network kernels (mlp_tc.cu: one CTA per tile; mlp_tc2.cu: CTA pairs).
+// kernels (network: mlp_tc.cu, mlp_rev.cu, mlp_rev2.cu, mlp_lay.cu; training:
+// train_tc.cu).
 // Internal to librtn.
 #pragma once
 

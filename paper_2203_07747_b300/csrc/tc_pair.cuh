@@ -1,5 +1,5 @@
-// tc_pair.cuh -- cluster (CTA pair) primitives shared by the pair kernels
-// (mlp_tc2.cu: forward mode; mlp_rev2.cu: reverse mode).  Internal to librtn.
+// tc_pair.cuh -- cluster (CTA pair) primitives of the reverse-mode pair
+// kernel (mlp_rev2.cu).  Internal to librtn.
 #pragma once
 
 #include "tc_common.cuh"
