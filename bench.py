@@ -101,10 +101,17 @@ def rev_flops_per_node(widths):
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples during the timed region: every sample carries its
+    host arrival time, and the summary keeps those that arrived inside the
+    window set by mark() (the timed region, plus 150 ms for the sampler's
+    reporting lag), or the two nearest if none did (nvidia-smi refreshes
+    its readings about every 100 ms)."""
 
     def __init__(self):
-        self.rows, self.p = [], None
+        self.rows, self.p, self.window = [], None, None
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1 + 0.15)
 
     def __enter__(self):
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -113,7 +120,7 @@ class Clocks:
         try:
             dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
             self.p = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -126,7 +133,7 @@ class Clocks:
         for line in self.p.stdout:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) == 7:
-                self.rows.append(parts)
+                self.rows.append((time.time(), parts))
 
     def __exit__(self, *a):
         if self.p:
@@ -145,12 +152,22 @@ class Clocks:
                 return float(v)
             except ValueError:
                 return None
-        sm = [v for v in (num(r[0]) for r in self.rows) if v is not None]
-        mx = [v for v in (num(r[1]) for r in self.rows) if v is not None]
+        rows = [r for t, r in self.rows]
+        if self.window:
+            t0, t1 = self.window
+            inside = [r for t, r in self.rows if t0 <= t <= t1]
+            if not inside:
+                mid = 0.5 * (t0 + t1)
+                inside = [r for t, r in sorted(self.rows, key=lambda tr: abs(tr[0] - mid))[:2]]
+            rows = inside
+        sm = [v for v in (num(r[0]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[1]) for r in rows) if v is not None]
+        pw = [v for v in (num(r[2]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i] == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "sm_min_mhz": min(sm) if sm else None, "power_w_max": max(pw) if pw else None,
+                "reasons": reasons, "samples": len(rows)}
 
 
 def make(prob, precision, riccati_f64=False, box_qp=False, train_bf16=False):
@@ -215,10 +232,12 @@ def time_closed_loop(ctl, prob, steps, warmup):
         torch.cuda.synchronize()
         rank_barrier()
         torch.cuda.synchronize()
+        t0 = time.time()
         e0.record(s)
         traj, _ = ctl.closed_loop(steps, xr2, ur2, xp, plant="drag", record=True)
         e1.record(s)
         torch.cuda.synchronize()
+        ck.mark(t0, time.time())
         rank_barrier()
     ms = e0.elapsed_time(e1)
     pos = traj[:, :, :3].double().cpu().numpy()

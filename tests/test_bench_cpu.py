@@ -44,3 +44,20 @@ def test_backward_gemm_flops_and_intensity():
     by = bench.lay_bytes("backward GEMM", W, 1) / 3
     assert abs(bench.lay_flops("backward GEMM", W, 1) / 3 / by - 2 * 3 * 512 * 512 / 14336) < 1e-9
     assert bench.A1_METHOD_BYTES_PER_NODE == 284
+
+
+def test_clock_summary_keeps_the_timed_window():
+    # samples outside the timed region (idle before it, the power-capped
+    # tail after it) must not decide the reported clocks
+    import bench
+    ck = bench.Clocks()
+    row = lambda sm, cap: [str(sm), "2032", "500.0", "Not Active", "Not Active", "Not Active", cap]
+    ck.rows = [(0.0, row(2032, "Not Active")), (1.0, row(1732, "Active")), (1.1, row(1800, "Active")),
+               (5.0, row(2032, "Not Active"))]
+    ck.mark(0.95, 1.05)
+    s = ck.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == 1766.0 and s["sm_min_mhz"] == 1732.0
+    assert s["reasons"] == ["sw_power_cap"]
+    ck.mark(3.0, 3.01)  # no sample inside: the two nearest
+    s = ck.summary()
+    assert s["samples"] == 2 and s["sm_min_mhz"] == 1800.0
