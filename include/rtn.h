@@ -142,6 +142,16 @@ typedef struct {
                        ~1e-5); 1 operands rounded to BF16 (one MMA per product:
                        a third of the tensor work and half the operand bytes),
                        FP32 accumulation and FP32 master weights in either */
+  int qp_group;     /* lanes per instance in the Riccati sweep and feedback:
+                       32 (one warp per instance) or 16 (two instances per
+                       warp: half the warps, twice the instances in flight;
+                       faster when the batch is throughput-bound or the
+                       factorisation is in FP64, slower when the longest
+                       horizon's sequential chain decides or with box_qp);
+                       0 chooses: 32 with box_qp, 16 with riccati_f64 = 2,
+                       else 16 when the batch's nodes exceed the resident
+                       warps of the sweep x the longest horizon, else 32.
+                       The result does not depend on it */
 } rtn_options;
 
 /* Create a controller batch of `batch` instances with horizons N[b] >= 1 and

@@ -49,7 +49,7 @@ class _MLP(C.Structure):
 class _Opt(C.Structure):
     _fields_ = [("precision", C.c_int), ("riccati_f64", C.c_int), ("shift", C.c_int),
                 ("box_qp", C.c_int), ("box_max_iter", C.c_int), ("second_order", C.c_int),
-                ("fused_qp", C.c_int), ("train_bf16", C.c_int)]
+                ("fused_qp", C.c_int), ("train_bf16", C.c_int), ("qp_group", C.c_int)]
 
 
 def lib_path():
@@ -157,7 +157,7 @@ class Controller:
 
     def __init__(self, N, dt, Q, R, QN=None, quad=None, layers=None, precision="fp32",
                  riccati_f64=False, shift=True, stream=None, box_qp=False, box_max_iter=20,
-                 second_order=False, fused_qp=False, train_bf16=False):
+                 second_order=False, fused_qp=False, train_bf16=False, qp_group=0):
         import torch
         L = load()
         self.N = np.ascontiguousarray(N, dtype=np.int32)
@@ -189,7 +189,8 @@ class Controller:
         # with the factorisation of R + B'PB and the gain solves in FP64
         ric = 2 if riccati_f64 == "chol64" else int(riccati_f64)
         opt = _Opt(PRECISION[precision], ric, int(bool(shift)), int(bool(box_qp)),
-                   int(box_max_iter), int(bool(second_order)), int(bool(fused_qp)), int(bool(train_bf16)))
+                   int(box_max_iter), int(bool(second_order)), int(bool(fused_qp)), int(bool(train_bf16)),
+                   int(qp_group))
         self.box_qp = bool(box_qp)
         self.second_order = bool(second_order)
         # network outputs: 3 (linear acceleration) or 6 (the full residual of

@@ -111,10 +111,13 @@ struct KArgs {
 template <typename T, bool CH64>
 using SlotOf = Slot<T, typename std::conditional<CH64, double, T>::type>;
 
-// the QP, feedback and iterate update of instance b by one warp (lane =
-// lane index), with the warp's shared-memory slot S
-template <typename T, bool BOX, bool CH64>
-__device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH64>& S, int lane) {
+// the QP, feedback and iterate update of instance b by a group of G lanes
+// (G = 32: one warp; G = 16: a half warp, two instances per warp) with mask
+// gm in the warp, lane = the lane's index in the group, and the group's
+// shared-memory slot S.  Nothing is exchanged between the groups of a warp.
+template <typename T, bool BOX, bool CH64, int G>
+__device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH64>& S, int lane, unsigned gm) {
+  static_assert(G == 16 || G == 32, "a group is a half warp or a warp");
   using TC = typename std::conditional<CH64, double, T>::type;
   const QpArgs& a = ka.a;
   const int N = ka.N[b], xo = ka.xoff[b], uo = ka.uoff[b];
@@ -131,7 +134,7 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
 
   // measured state
   float x0m = lane < NX ? a.x0[(size_t)b * NX + lane] : 0.0f;
-  const bool finite = __all_sync(0xffffffffu, isfinite(x0m));
+  const bool finite = __all_sync(gm, isfinite(x0m));
 
   // ---------------- backward Riccati sweep (box mode: inputs flagged in
   // box_act are held at their bounds); gains to Kg, kg; S.notpd on failure
@@ -141,17 +144,18 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
     for (int j = 0; j < NX; ++j) Prow[j] = (lane < NX && j == lane) ? (T)C.QN[lane] : (T)0;
     if (lane < NX) p_i = (T)C.QN[lane] * ((T)x[(size_t)N * NX + lane] - (T)xr[(size_t)N * NX + lane]);
     if (lane == 0) S.notpd = 0;
-    __syncwarp();
+    __syncwarp(gm);
     // stage data of node k (A 169, B 52, c 13 floats) as 8 registers per lane,
     // loaded one node ahead so that the global-memory latency overlaps the
     // previous node's arithmetic
     constexpr int NSTAGE = NX * NX + NX * NU + NX;
-    float pf[8];
+    constexpr int NPF = (NSTAGE + G - 1) / G;
+    float pf[NPF];
     auto prefetch = [&](int k) {
       const size_t node = (size_t)uo + k;
   #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int e = lane + 32 * q;
+      for (int q = 0; q < NPF; ++q) {
+        const int e = lane + G * q;
         float v = 0.0f;
         if (e < NX * NX) v = a.A[node * NX * NX + e];
         else if (e < NX * NX + NX * NU) v = a.Bm[node * NX * NU + (e - NX * NX)];
@@ -164,13 +168,13 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
     for (int k = N - 1; k >= 0 && finite; --k) {
       const size_t node = (size_t)uo + k;
   #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int e = lane + 32 * q;
+      for (int q = 0; q < NPF; ++q) {
+        const int e = lane + G * q;
         if (e < NX * NX) S.A[e / NX][e % NX] = (T)pf[q];
         else if (e < NX * NX + NX * NU) S.Bm[(e - NX * NX) / NU][(e - NX * NX) % NU] = (T)pf[q];
         else if (e < NSTAGE) S.c[e - NX * NX - NX * NU] = (T)pf[q];
       }
-      __syncwarp();
+      __syncwarp(gm);
       if (k > 0) prefetch(k - 1);
       // box mode: inputs held at a bound in this subproblem (fx) and their values
       int fx[NU];
@@ -210,9 +214,9 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
         for (int m = 0; m < NU; ++m) S.PB[lane][m] = pb[m];
         S.g[lane] = gi;
       }
-      __syncwarp();
+      __syncwarp(gm);
       // Hux = B'PA (52), Huu = R + B'PB (16), hu = r + B'g (4) over the warp
-      for (int o = lane; o < NU * NX + NU * NU + NU; o += 32) {
+      for (int o = lane; o < NU * NX + NU * NU + NU; o += G) {
         T s = 0;
         if (o < NU * NX) {
           const int m = o / NX, j = o % NX;
@@ -233,7 +237,7 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
           S.hu[m] = s;
         }
       }
-      __syncwarp();
+      __syncwarp(gm);
       if (BOX && lane < NU) ka.box_gam[node * NU + lane] = (float)S.Huu[lane * NU + lane];
       // held inputs: identity rows/columns of Huu, zero rows of Hux, right-hand
       // side -a; their coupling moves to the free rows' right-hand side
@@ -269,7 +273,7 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
           for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (TC)0;
         if (!pd) S.notpd = 1;
       }
-      __syncwarp();
+      __syncwarp(gm);
       // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `lane` (13 = hu)
       if (lane < NX + 1) {
         TC y[NU];
@@ -303,8 +307,8 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
           else S.k[i] = (T)(-y[i]);
         }
       }
-      __syncwarp();
-      for (int e = lane; e < NU * NX + NU; e += 32) {
+      __syncwarp(gm);
+      for (int e = lane; e < NU * NX + NU; e += G) {
         if (e < NU * NX) Kg[node * NU * NX + e] = S.K[e / NX][e % NX];
         else kg[node * NU + (e - NU * NX)] = S.k[e - NU * NX];
       }
@@ -335,13 +339,13 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
   #pragma unroll
         for (int j = 0; j < NX; ++j) S.P2[lane][j] = P2row[j];
       }
-      __syncwarp();
+      __syncwarp(gm);
       if (lane < NX) {
   #pragma unroll
         for (int j = 0; j < NX; ++j) Prow[j] = (T)0.5 * (P2row[j] + S.P2[j][lane]);
         p_i = p2;
       }
-      __syncwarp();
+      __syncwarp(gm);
     }
   };
 
@@ -360,7 +364,7 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
   auto forward = [&](int mode, bool clamp) {
     const bool final_out = mode != 1;
     if (lane < NX) S.dx[lane] = (T)x0m - (T)x[lane];
-    __syncwarp();
+    __syncwarp(gm);
     if (lane < NX) {
       if (final_out && a.dx) a.dx[(size_t)xo * NX + lane] = (float)S.dx[lane];
       if (mode == 1) bdx[lane] = (float)S.dx[lane];
@@ -413,7 +417,7 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
         }
         S.du[lane] = s;
       }
-      __syncwarp();
+      __syncwarp(gm);
       T dxn = 0;
       if (lane < NX) {
         T s = (T)cc;
@@ -456,9 +460,9 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
           }
         }
       }
-      __syncwarp();
+      __syncwarp(gm);
       if (lane < NX) S.dx[lane] = dxn;
-      __syncwarp();
+      __syncwarp(gm);
     }
   };
 
@@ -473,10 +477,10 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
     bool changed = false;
     for (int k = N - 1; k >= 0; --k) {
       const size_t node = (size_t)uo + k;
-      for (int e = lane; e < NX * NX; e += 32) S.A[e / NX][e % NX] = (T)a.A[node * NX * NX + e];
-      for (int e = lane; e < NX * NU; e += 32) S.Bm[e / NU][e % NU] = (T)a.Bm[node * NX * NU + e];
+      for (int e = lane; e < NX * NX; e += G) S.A[e / NX][e % NX] = (T)a.A[node * NX * NX + e];
+      for (int e = lane; e < NX * NU; e += G) S.Bm[e / NU][e % NU] = (T)a.Bm[node * NX * NU + e];
       if (lane < NX) S.g[lane] = lam;
-      __syncwarp();
+      __syncwarp(gm);
       if (lane < NU) {
         const T um = (T)u[(size_t)k * NU + lane];
         const T dum = (T)bdu[(size_t)k * NU + lane];
@@ -497,20 +501,20 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
 #pragma unroll
         for (int l = 0; l < NX; ++l) ln += S.A[l][lane] * S.g[l];
       }
-      __syncwarp();
+      __syncwarp(gm);
       lam = ln;
     }
-    return __any_sync(0xffffffffu, changed);
+    return __any_sync(gm, changed);
   };
 
   // every du of the scratch step within 0 <= u + du <= u_max
   auto feasible = [&]() -> bool {
     bool ok = true;
-    for (int e = lane; e < N * NU; e += 32) {
+    for (int e = lane; e < N * NU; e += G) {
       const float um = u[e], d = bdu[e];
       ok &= (d >= -um) && (d <= ka.u_max - um);
     }
-    return __all_sync(0xffffffffu, ok);
+    return __all_sync(gm, ok);
   };
 
   int st = finite ? RTN_OK : RTN_E_NONFINITE;
@@ -521,8 +525,8 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
     // primal-dual active set: solve without bounds; while the step leaves
     // the box, update the sets and solve with the active inputs held at
     // their bounds, until the sets repeat (at most box_max_iter solves)
-    for (int e = lane; e < N * NU; e += 32) ka.box_act[(size_t)uo * NU + e] = 0;
-    __syncwarp();
+    for (int e = lane; e < N * NU; e += G) ka.box_act[(size_t)uo * NU + e] = 0;
+    __syncwarp(gm);
     sweep();
     int its = 1;
     if (S.notpd) {
@@ -547,9 +551,9 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
   if (st != RTN_OK && st != RTN_E_NOT_CONVERGED) {
     // failed instance: zero step, iterate untouched, send the reference input
     if (a.dx)
-      for (int e = lane; e < (N + 1) * NX; e += 32) a.dx[(size_t)xo * NX + e] = 0.0f;
+      for (int e = lane; e < (N + 1) * NX; e += G) a.dx[(size_t)xo * NX + e] = 0.0f;
     if (a.du)
-      for (int e = lane; e < N * NU; e += 32) a.du[(size_t)uo * NU + e] = 0.0f;
+      for (int e = lane; e < N * NU; e += G) a.du[(size_t)uo * NU + e] = 0.0f;
     if (a.u0 && lane < NU) a.u0[(size_t)b * NU + lane] = ur[lane];
     return;
   }
@@ -557,14 +561,19 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
   else forward(2, st == RTN_E_NOT_CONVERGED);
 }
 
-template <typename T, int WPB, bool BOX, bool CH64>
+// WPB warps per block, 32 / G instances per warp (consecutive in the
+// longest-first order, so the two halves of a warp mostly share N)
+template <typename T, int WPB, bool BOX, bool CH64, int G>
 __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
-  __shared__ SlotOf<T, CH64> slots[WPB];
+  constexpr int GPW = 32 / G;
+  __shared__ SlotOf<T, CH64> slots[WPB * GPW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = blockIdx.x * WPB + warp;
+  const int grp = warp * GPW + lane / G;
+  const int slot = blockIdx.x * WPB * GPW + grp;
   if (slot >= ka.B) return;
   const int b = ka.order ? ka.order[slot] : slot;
-  qp_instance<T, BOX, CH64>(ka, b, slots[warp], lane);
+  const unsigned gm = G == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+  qp_instance<T, BOX, CH64, G>(ka, b, slots[grp], lane % G, gm);
 }
 
 // ---------------------------------------------------------------- fused
@@ -658,7 +667,7 @@ __global__ void __launch_bounds__(FQ_WPB * 32, 4) lin_qp_kernel(FusedArgs fa) {
       }
       continue;
     }
-    qp_instance<float, false, false>(fa.ka, b, slots[warp], lane);
+    qp_instance<float, false, false, 32>(fa.ka, b, slots[warp], lane, 0xffffffffu);
   }
   // the last warp to finish (every other warp has taken its last ticket and
   // finished its work) returns the counters to zero for the next launch
@@ -679,11 +688,12 @@ __global__ void __launch_bounds__(FQ_WPB * 32, 4) lin_qp_kernel(FusedArgs fa) {
   }
 }
 
-template <typename T, int WPB, bool CH64 = false>
+template <typename T, int WPB, bool CH64 = false, int G = 32>
 cudaError_t launch(const KArgs& ka, cudaStream_t s) {
-  const int grid = (ka.B + WPB - 1) / WPB;
-  if (ka.box) qp_kernel<T, WPB, true, CH64><<<grid, WPB * 32, 0, s>>>(ka);
-  else qp_kernel<T, WPB, false, CH64><<<grid, WPB * 32, 0, s>>>(ka);
+  const int per_block = WPB * (32 / G);
+  const int grid = (ka.B + per_block - 1) / per_block;
+  if (ka.box) qp_kernel<T, WPB, true, CH64, G><<<grid, WPB * 32, 0, s>>>(ka);
+  else qp_kernel<T, WPB, false, CH64, G><<<grid, WPB * 32, 0, s>>>(ka);
   return cudaGetLastError();
 }
 
@@ -712,11 +722,36 @@ KArgs make_kargs(rtn_ctx* ctx, const QpArgs& a) {
 
 }  // namespace
 
+// lanes per instance of the FP32 sweeps (rtn_options.qp_group; 0: automatic).
+// Measured on 1024..16384 instances (N = 20, and N in 10..50): the box QP
+// is faster on whole warps at every size (its active-set loop diverges
+// between the instances of a warp); the sweep with the FP64 factorisation on
+// half warps at every size (its FP64 instructions serve two instances); the
+// FP32 sweep on half warps once the batch's work exceeds what the resident
+// warps finish in the longest horizon's chain (sum N_b > resident x N_max),
+// on whole warps below (a half-warp step is ~1.2x slower unloaded)
+int qp_group(const rtn_ctx* ctx) {
+  if (ctx->opt.qp_group) return ctx->opt.qp_group;
+  if (ctx->opt.box_qp) return 32;
+  if (ctx->opt.riccati_f64 == 2) return 16;
+  static int resident = 0;                   // warps of qp_kernel resident on the GPU
+  if (!resident) {
+    int dev = 0, sms = 148, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qp_kernel<float, 4, false, false, 32>, 128, 0);
+    resident = std::max(1, sms * std::max(occ, 1) * 4);
+  }
+  return (long long)ctx->lay.n_nodes > (long long)resident * ctx->lay.N_max ? 16 : 32;
+}
+
 cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a) {
   const KArgs ka = make_kargs(ctx, a);
   if (ctx->opt.riccati_f64 == 1) return launch<double, 2>(ka, ctx->stream);
-  if (ctx->opt.riccati_f64 == 2) return launch<float, 4, true>(ka, ctx->stream);
-  return launch<float, 4>(ka, ctx->stream);
+  const bool g16 = qp_group(ctx) == 16;
+  if (ctx->opt.riccati_f64 == 2)
+    return g16 ? launch<float, 4, true, 16>(ka, ctx->stream) : launch<float, 4, true, 32>(ka, ctx->stream);
+  return g16 ? launch<float, 4, false, 16>(ka, ctx->stream) : launch<float, 4, false, 32>(ka, ctx->stream);
 }
 
 bool lin_qp_fusable(const rtn_ctx* ctx) {

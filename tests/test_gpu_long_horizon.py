@@ -85,11 +85,13 @@ def oracle_qp(orc, N, A, Bm, c, x, u, xref, uref, x0):
     return np.concatenate(dxs), np.concatenate(dus)
 
 
-@pytest.mark.parametrize("ric", [0, "chol64", 1])
-def test_qp_long_horizons_match_oracle(rtn, orc, ric):
+@pytest.mark.parametrize("ric,group", [(0, 32), (0, 16), ("chol64", 32), ("chol64", 16), (1, 0)])
+def test_qp_long_horizons_match_oracle(rtn, orc, ric, group):
+    # group: lanes per instance (32: a warp; 16: two instances per warp, the
+    # odd ninth instance alone in its warp)
     N, dt = long_batch()
     A, Bm, c, x, u, xref, uref, x0 = qp_inputs(orc, N, dt, 21)
-    ctl = rtn.Controller(N, dt, W.Q_DIAG, W.R_DIAG, quad=QUAD, riccati_f64=ric)
+    ctl = rtn.Controller(N, dt, W.Q_DIAG, W.R_DIAG, quad=QUAD, riccati_f64=ric, qp_group=group)
     dx, du, st = ctl.qp_solve(*[dev(a) for a in (A, Bm, c, x, u, xref, uref, x0)])
     assert (st.cpu().numpy() == 0).all()
     rdx, rdu = oracle_qp(orc, N, A, Bm, c, x, u, xref, uref, x0)
@@ -104,6 +106,31 @@ def test_qp_long_horizons_match_oracle(rtn, orc, ric):
         eu = np.abs(du[uo:uo + n] - rdu[uo:uo + n]).max() / np.abs(rdu[uo:uo + n]).max()
         assert ex < 1e-5 and eu < 1e-5, (ric, b, n, dt[b], ex, eu)
         xo += n + 1; uo += n
+
+
+@pytest.mark.parametrize("ric,box", [(0, False), ("chol64", False), (0, True)])
+def test_qp_group_sizes_agree(rtn, orc, ric, box):
+    # the sweep on half warps (two instances per warp) and on whole warps:
+    # every lane runs the same arithmetic in the same order, so the steps,
+    # the statuses (and with the bounds the active-set iterations) agree;
+    # 37 instances with N in 1..50, so warps pair instances of unequal
+    # horizons and the last one is alone
+    g = np.random.default_rng(31)
+    N = g.integers(1, 51, 37).astype(np.int32)
+    dt = f32(g.uniform(0.02, 0.1, 37))
+    A, Bm, c, x, u, xref, uref, x0 = qp_inputs(orc, N, dt, 32)
+    out = {}
+    for group in (16, 32):
+        ctl = rtn.Controller(N, dt, W.Q_DIAG, W.R_DIAG, quad=QUAD, riccati_f64=ric, box_qp=box, qp_group=group)
+        dx, du, st = ctl.qp_solve(*[dev(a) for a in (A, Bm, c, x, u, xref, uref, x0)])
+        out[group] = (npy(dx), npy(du), st.cpu().numpy(), ctl.box_iterations() if box else None)
+        ctl.close()
+    (dx1, du1, s1, i1), (dx2, du2, s2, i2) = out[16], out[32]
+    assert (s1 == s2).all()
+    if box:
+        assert np.array_equal(i1, i2)
+    for p, q in ((dx1, dx2), (du1, du2)):
+        assert np.abs(p - q).max() <= 1e-6 * np.abs(q).max(), np.abs(p - q).max()
 
 
 def rel_rows(a, b):
