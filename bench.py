@@ -43,40 +43,16 @@ def peaks():
     return 6400.0, 1800.0, 1400.0, "fallback"
 
 
-KERNEL_SOURCES = ("mlp_tc.cu", "mlp_rev.cu", "mlp_rev2.cu", "tc_common.cuh", "tc_pair.cuh")
-PROFILES = ("mlp_lay_cfg3_h512_bf16x2.md", "mlp_rev2_kernel_cfg3_h512_bf16x2.md", "mlp_rev_kernel_cfg3_h512_bf16x2.md", "mlp_tc_kernel_cfg3_h512_bf16x2.md")
+LAYERED_PROFILE = "mlp_lay_pass_2048x20_h512x5_bf16x2.md"
 
 
-def kernel_md5(files=KERNEL_SOURCES):
+def kernel_md5(files):
     """md5 over kernel sources (each profile records it with its file list)."""
     h = hashlib.md5()
     for f in files:
         with open(os.path.join(ROOT, "paper_2203_07747_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
-
-
-def profiled_traffic(tile):
-    """DRAM bytes per launch of the network kernel from a committed ncu
-    summary, if the kernel sources and the tile shape are the captured ones."""
-    if tile is None:
-        return None
-    for name in PROFILES:
-        try:
-            text = open(os.path.join(ROOT, "profiles", name)).read()
-            m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
-            shape = re.search(r"tile shape: npc=(\d+) mode=(\d+) stages=(\d+)", text)
-            if not m or not shape:
-                continue
-            files = tuple(f.strip() for f in m.group(2).split("+"))
-            if m.group(1) != kernel_md5(files):
-                continue
-            if (tile["nodes_per_cta"], int(tile["operand_mode"]), tile["stages"]) != tuple(map(int, shape.groups())):
-                continue
-            return int(re.search(r"dram_bytes_per_launch: (\d+)", text).group(1))
-        except (OSError, AttributeError):
-            continue
-    return None
 
 
 def fwd_flops_per_node(widths):
@@ -766,10 +742,22 @@ def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, pea
     its DRAM bytes per launch (ncu); the HBM view beside it compares them with
     the activations and adjoints the layered design moves and with the ~284 B
     per node that the method itself needs."""
+    import torch
     ctl.mlp_eval(x, u, out[0], out[1])
-    ctl.tc_launch_times(True)
-    ctl.mlp_eval(x, u, out[0], out[1])
-    times = ctl.tc_launch_times(False)
+    # five recorded passes, each launch's median: the GPU's power management
+    # moves the SM clock between passes (sw_power_cap), and the clocks seen
+    # are reported beside the times
+    runs = []
+    with Clocks() as ck:
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for _ in range(5):
+            ctl.tc_launch_times(True)
+            ctl.mlp_eval(x, u, out[0], out[1])
+            runs.append(ctl.tc_launch_times(False))
+        torch.cuda.synchronize()
+        ck.mark(t0, time.time())
+    times = [(runs[0][i][0], float(np.median([r[i][1] for r in runs]))) for i in range(len(runs[0]))]
     tot = {}
     for k, ms in times:
         c, t = tot.get(k, (0, 0.0))
@@ -801,7 +789,9 @@ def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, pea
                          "arithmetic_intensity_flop_per_byte": fl / by,
                          "ridge_flop_per_byte": bf16_burst * 1e12 / (hbm * 1e9)},
             "pass": pass_view,
-            "launch_ms": [[k, round(v, 4)] for k, v in times]}
+            "launch_ms": [[k, round(v, 4)] for k, v in times],
+            "launch_ms_note": "median of 5 recorded passes per launch",
+            "clocks": ck.summary()}
 
 
 def profiled_layer_traffic(kind):
@@ -809,7 +799,7 @@ def profiled_layer_traffic(kind):
     summary (measured on a smaller case and scaled by nodes), or None when the
     kernel sources changed since."""
     try:
-        text = open(os.path.join(ROOT, "profiles", "mlp_lay_cfg3_h512_bf16x2.md")).read()
+        text = open(os.path.join(ROOT, "profiles", LAYERED_PROFILE)).read()
         m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
         files = tuple(f.strip() for f in m.group(2).split("+"))
         if m.group(1) != kernel_md5(files):
@@ -824,7 +814,7 @@ def profiled_layer_traffic(kind):
 def profiled_pass_traffic():
     """DRAM bytes of a whole layered pass from its committed summary."""
     try:
-        text = open(os.path.join(ROOT, "profiles", "mlp_lay_cfg3_h512_bf16x2.md")).read()
+        text = open(os.path.join(ROOT, "profiles", LAYERED_PROFILE)).read()
         m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
         files = tuple(f.strip() for f in m.group(2).split("+"))
         if m.group(1) != kernel_md5(files):
@@ -846,16 +836,17 @@ def hess_flops_per_node(widths):
     return f
 
 
-def bench_network_pass(config, B, reps=3, precision="bf16x2"):
+def bench_network_pass(config, B, reps=3, precision="bf16x2", tile=-1):
     """The network pass (a1) of the workload's network on B instances with
-    the layered reverse-mode shape (split BF16, or FP8 on the e4m3-quantised
-    weights): ms per pass after one warm-up pass."""
+    the layered reverse-mode shape, or tile shape `tile` if >= 0 (split
+    BF16, or FP8 on the e4m3-quantised weights): ms per pass after one
+    warm-up pass."""
     import torch
     prob = W.make_problem(config, seed=0, B=B, bf16=True)
     if precision == "fp8":
         prob["layers"] = W.quantize_e4m3(prob["layers"])
     ctl = make(prob, precision)
-    vi = [v[0] for v in ctl.tc_variants() if v[2] == 6][0]
+    vi = tile if tile >= 0 else [v[0] for v in ctl.tc_variants() if v[2] == 6][0]
     ctl.tc_select(vi)
     x, u = ctl.get_iterate()
     fD, JD = ctl.mlp_eval(x, u)
@@ -973,7 +964,7 @@ def main():
                          "ncu's per-launch overhead changes the autotuner's ranking)")
     ap.add_argument("--network-pass", type=int, default=0, metavar="B",
                     help="time only the network pass (a1) of the workload's network on B instances with "
-                         "the layered reverse-mode tile shape (the profiling command of its summary)")
+                         "the layered reverse-mode tile shape, or --tile V (the profiling command of its summary)")
     ap.add_argument("--rti-step", type=int, default=0, metavar="B",
                     help="time only one RTI step of the workload on B instances with the layered reverse-mode "
                          "tile shape (the profiling command of the RK4 and QP kernels' summaries)")
@@ -990,7 +981,8 @@ def main():
         return
     if args.network_pass:
         print(json.dumps(bench_network_pass(args.config, args.network_pass,
-                                            precision="fp8" if args.precision == "fp8" else "bf16x2")))
+                                            precision="fp8" if args.precision == "fp8" else "bf16x2",
+                                            tile=args.tile)))
         return
     if args.learned_only:
         import torch  # noqa: F401
@@ -1078,15 +1070,10 @@ def main():
                             "network value + reverse-mode Jacobian (a1, three adjoint rows)" if rev
                             else "network value + forward-mode Jacobian (a1)"),
                  "forward_mode_equivalent_tflops": fwd_flops_per_node(widths) * nn / (ms_mlp * 1e-3) / 1e12,
-                 "traffic": profiled_traffic(cfg.get("tile")) if args.config == "cfg3_bf16_precision" else None})
+                 "traffic": None})
     roof["frac"] = roof["achieved"] / roof["peak"]
     if mode == 6:
         roof = layered_roofline(ctl, x, u, out, widths, nn, roof, hbm, bf16_burst, peak_src)
-    elif roof.get("traffic"):
-        # what the pass moves through DRAM per launch at the timed rate (the
-        # layered shape streams every layer's operands through HBM)
-        roof["dram_tbs_at_traffic"] = roof["traffic"] / (ms_mlp * 1e-3) / 1e12
-        roof["hbm_peak_tbs"] = hbm / 1e3
 
     ms_e2e, bi, bo = e2e_rti(ctl, prob, max(5, args.steps))
     smp = error_sample(prob, prec) if rank == 0 and world == 1 and not args.no_cpu else None
