@@ -361,8 +361,22 @@ def cpu_baseline(prob, budget_s=15.0):
         if total + 2.2 * el > budget_s:
             break
         nb *= 2
+    # one core: single-instance calls (the OpenMP loop then runs on one thread)
+    sub = W.subset(prob, 1)
+    N, dt, x0 = sub["N"], sub["dt"], sub["x0"]
+    xref, uref = W.node_refs(sub)
+    x = np.repeat(x0[0:1], N[0] + 1, 0)
+    u = np.full((int(N.sum()), 4), W.hover_thrust())
+    t0, k = time.perf_counter(), 0
+    while k < 8 and (k == 0 or time.perf_counter() - t0 < 4.0):
+        oracle.rti_step(sub["quad"], sub["layers"], N, dt, sub["Q"], sub["R"], sub["QN"], x.copy(), u.copy(),
+                        xref, uref, x0)
+        k += 1
+    single = k / (time.perf_counter() - t0)
     return {"value": rate, "unit": "RTI steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {prob['B']} instances, one RTI step (FP64 C, OpenMP over instances)"}
+            "sample": f"{done} of {prob['B']} instances, one RTI step (FP64 C, OpenMP over instances)",
+            "single_core": {"value": single, "unit": "RTI steps/s",
+                            "sample": f"{k} single-instance RTI steps, one thread"}}
 
 
 def bench_ragged(steps=200):
