@@ -50,7 +50,6 @@ namespace {
 constexpr int R2_NPC = 42;        // nodes per pair tile
 constexpr int R2_CF = 64;         // forward columns per CTA
 constexpr int R2_CB = 128;        // backward columns per CTA
-constexpr int R2_HALF = 21;       // nodes per epilogue warp half
 constexpr int R2_THREADS = THREADS + 32;  // warp 10: exchange
 constexpr uint32_t R2_SBYTES = 128u * R2_CB * 2u;  // staging block (backward size)
 

@@ -484,10 +484,10 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
       if (lane < NU) {
         const T um = (T)u[(size_t)k * NU + lane];
         const T dum = (T)bdu[(size_t)k * NU + lane];
-        T G = (T)C.R[lane] * (um + dum - (T)ur[(size_t)k * NU + lane]);
+        T gr = (T)C.R[lane] * (um + dum - (T)ur[(size_t)k * NU + lane]);  // the cost's gradient
 #pragma unroll
-        for (int l = 0; l < NX; ++l) G += S.Bm[l][lane] * S.g[l];
-        const T v = dum - G / (T)ka.box_gam[node * NU + lane];
+        for (int l = 0; l < NX; ++l) gr += S.Bm[l][lane] * S.g[l];
+        const T v = dum - gr / (T)ka.box_gam[node * NU + lane];
         const signed char nw = v < -um ? -1 : (v > (T)ka.u_max - um ? 1 : 0);
         if (nw != ka.box_act[node * NU + lane]) {
           changed = true;

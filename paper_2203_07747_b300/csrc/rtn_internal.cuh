@@ -166,6 +166,8 @@ struct TrainState {
   size_t nw = 0, nb = 0, b_base = 0;
   long long t = 0;                     // Adam step counter (host mirror)
   int* t_dev = nullptr;                // Adam step counter on the device
+  void* wjobs = nullptr;               // per-layer Adam + repack jobs of the one per-step launch
+  int wjob_blocks = 0;                 // blocks of that launch
 };
 
 }  // namespace rtn

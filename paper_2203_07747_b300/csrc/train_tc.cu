@@ -42,7 +42,7 @@ struct Tg {
   static constexpr size_t SMEM = STAGES * STAGE + 1024 + 256;
   static constexpr uint32_t TMEM_COLS = 2 * NT;
 };
-static_assert(Tg<128>::SMEM <= 232448 && Tg<256>::SMEM <= 232448, "shared memory");
+static_assert(Tg<128>::SMEM <= 232448, "shared memory");
 
 enum { TG_FWD = 0, TG_OUT = 1, TG_BWD = 2, TG_WG = 3 };
 // N tile of the weight gradient
@@ -514,12 +514,6 @@ __global__ void tg_reduce_kernel(const float* __restrict__ part, int ks, size_t 
   g[e] = s;
 }
 
-// one layer's weights W [fo][fi] in 32 x 32 tiles, 256 threads, four
-// consecutive elements of a row per thread (float4 loads where the row length
-// allows): with adam, the Adam step (bias-corrected, step t) from the summed
-// partials; then the split copies W (hi, lo) [fo][ldw] and W' (hi, lo)
-// [fi][ldwt], the transpose through shared memory so that both copies are
-// stored as 8-byte runs
 __device__ __forceinline__ float adam_elem(float p, float g, float& m, float& v, float lr, float b1, float b2,
                                            float eps, float c1, float c2) {
   m = b1 * m + (1.0f - b1) * g;
@@ -527,22 +521,32 @@ __device__ __forceinline__ float adam_elem(float p, float g, float& m, float& v,
   return p - lr * (m / c1) / (sqrtf(v / c2) + eps);
 }
 
-__global__ void __launch_bounds__(256) tg_weights_kernel(float* __restrict__ P, const float* __restrict__ part, int ks,
-                                                         int fo, int fi, int adam, float* __restrict__ m,
-                                                         float* __restrict__ v, float lr, float b1, float b2, float eps,
-                                                         const int* __restrict__ t_dev, __nv_bfloat16* __restrict__ wh,
-                                                         __nv_bfloat16* __restrict__ wl, int ldw,
-                                                         __nv_bfloat16* __restrict__ th, __nv_bfloat16* __restrict__ tl,
-                                                         int ldwt) {
+// one layer's Adam + repack job (the per-step launch covers every layer)
+struct WJob {
+  float* P;            // W_l [fo][fi] (FP32 master)
+  const float* part;   // weight-gradient partials [ks][fo][fi]
+  float *m, *v;        // Adam moments of W_l
+  __nv_bfloat16 *wh, *wl, *th, *tl;
+  int ks, fo, fi, ldw, ldwt;
+  int bx, blk0;        // 32-column tiles per row of tiles; first block of the layer
+};
+
+// one 32 x 32 tile of a layer's weights W [fo][fi], 256 threads, four
+// consecutive elements of a row per thread (float4 loads where the row length
+// allows): with adam, the Adam step from the summed partials; then the split
+// copies W (hi, lo) [fo][ldw] and W' (hi, lo) [fi][ldwt], the transpose
+// through shared memory so that both copies are stored as 8-byte runs
+__device__ __forceinline__ void weights_tile(const WJob& J, int bx, int by, int adam, float lr, float b1, float b2,
+                                             float eps, float c1, float c2) {
   __shared__ uint32_t tile[32][33];  // hi | lo << 16
+  float* __restrict__ P = J.P;
+  const float* __restrict__ part = J.part;
+  float* __restrict__ m = J.m;
+  float* __restrict__ v = J.v;
+  const int fo = J.fo, fi = J.fi, ks = J.ks, ldw = J.ldw, ldwt = J.ldwt;
   const size_t n = (size_t)fo * fi;
   const int r = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
-  const int i = blockIdx.y * 32 + r, j = blockIdx.x * 32 + c4;
-  float c1 = 1.0f, c2 = 1.0f;
-  if (adam) {
-    c1 = 1.0f - powf(b1, (float)*t_dev);
-    c2 = 1.0f - powf(b2, (float)*t_dev);
-  }
+  const int i = by * 32 + r, j = bx * 32 + c4;
   float pv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (i < fo && j < fi) {
     const size_t e = (size_t)i * fi + j;
@@ -590,18 +594,18 @@ __global__ void __launch_bounds__(256) tg_weights_kernel(float* __restrict__ P, 
   }
   if (i < fo && j < fi) {
     if ((fi & 3) == 0) {  // ldw is a multiple of 32: 8-byte aligned runs
-      *reinterpret_cast<uint2*>(wh + (size_t)i * ldw + j) = make_uint2(hw[0], hw[1]);
-      *reinterpret_cast<uint2*>(wl + (size_t)i * ldw + j) = make_uint2(lw[0], lw[1]);
+      *reinterpret_cast<uint2*>(J.wh + (size_t)i * ldw + j) = make_uint2(hw[0], hw[1]);
+      *reinterpret_cast<uint2*>(J.wl + (size_t)i * ldw + j) = make_uint2(lw[0], lw[1]);
     } else {
       for (int k = 0; k < 4 && j + k < fi; ++k) {
-        wh[(size_t)i * ldw + j + k] = __ushort_as_bfloat16((unsigned short)(tile[r][c4 + k] & 0xffffu));
-        wl[(size_t)i * ldw + j + k] = __ushort_as_bfloat16((unsigned short)(tile[r][c4 + k] >> 16));
+        J.wh[(size_t)i * ldw + j + k] = __ushort_as_bfloat16((unsigned short)(tile[r][c4 + k] & 0xffffu));
+        J.wl[(size_t)i * ldw + j + k] = __ushort_as_bfloat16((unsigned short)(tile[r][c4 + k] >> 16));
       }
     }
   }
   __syncthreads();
   // W': row jt = column j of W, four consecutive rows of W per thread
-  const int jt = blockIdx.x * 32 + r, it = blockIdx.y * 32 + c4;
+  const int jt = bx * 32 + r, it = by * 32 + c4;
   if (jt < fi && it < fo) {
     uint32_t th2[2] = {0u, 0u}, tl2[2] = {0u, 0u};
 #pragma unroll
@@ -611,20 +615,59 @@ __global__ void __launch_bounds__(256) tg_weights_kernel(float* __restrict__ P, 
       tl2[k >> 1] |= (pk >> 16) << (16 * (k & 1));
     }
     if (it + 3 < fo) {  // ldwt is a multiple of 32
-      *reinterpret_cast<uint2*>(th + (size_t)jt * ldwt + it) = make_uint2(th2[0], th2[1]);
-      *reinterpret_cast<uint2*>(tl + (size_t)jt * ldwt + it) = make_uint2(tl2[0], tl2[1]);
+      *reinterpret_cast<uint2*>(J.th + (size_t)jt * ldwt + it) = make_uint2(th2[0], th2[1]);
+      *reinterpret_cast<uint2*>(J.tl + (size_t)jt * ldwt + it) = make_uint2(tl2[0], tl2[1]);
     } else {
       for (int k = 0; it + k < fo; ++k) {
         const uint32_t pk = tile[c4 + k][r];
-        th[(size_t)jt * ldwt + it + k] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
-        tl[(size_t)jt * ldwt + it + k] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+        J.th[(size_t)jt * ldwt + it + k] = __ushort_as_bfloat16((unsigned short)(pk & 0xffffu));
+        J.tl[(size_t)jt * ldwt + it + k] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
       }
     }
   }
 }
 
+// the BF16 copies of one layer's weights from its FP32 master (no Adam)
+__global__ void __launch_bounds__(256) tg_split_kernel(WJob J) {
+  weights_tile(J, blockIdx.x, blockIdx.y, 0, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f);
+}
+
+// the Adam step (bias-corrected, step t) of every layer's weights in one
+// launch: block -> (layer, 32 x 32 tile) by the jobs' first blocks
+__global__ void __launch_bounds__(256) tg_weights_kernel(const WJob* __restrict__ jobs, int n_jobs, float lr, float b1,
+                                                         float b2, float eps, const int* __restrict__ t_dev) {
+  int li = 0;
+  while (li + 1 < n_jobs && (int)blockIdx.x >= jobs[li + 1].blk0) ++li;
+  const WJob J = jobs[li];
+  const int b = (int)blockIdx.x - J.blk0;
+  const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
+  weights_tile(J, b % J.bx, b / J.bx, 1, lr, b1, b2, eps, c1, c2);
+}
+
 inline dim3 wgrid(int fo, int fi) { return dim3((unsigned)((fi + 31) / 32), (unsigned)((fo + 31) / 32)); }
 const dim3 WBLOCK(256);
+
+// layer l's Adam + repack job (part, ks, m, v are read only with Adam)
+WJob weight_job(const Net& net, const TrainState& ts, int l) {
+  const std::vector<int>& w = net.widths;
+  WJob J;
+  J.P = net.W32 + net.w_off[l];
+  J.part = ts.part ? ts.part + ts.part_off[l] : nullptr;
+  J.ks = ts.ksplit.empty() ? 0 : ts.ksplit[l];
+  J.m = ts.m + net.w_off[l];
+  J.v = ts.v + net.w_off[l];
+  J.wh = ts.ws[4 * l];
+  J.wl = ts.ws[4 * l + 1];
+  J.th = ts.ws[4 * l + 2];
+  J.tl = ts.ws[4 * l + 3];
+  J.fo = w[l + 1];
+  J.fi = w[l];
+  J.ldw = rup(w[l], 32);
+  J.ldwt = rup(w[l + 1], 32);
+  J.bx = (w[l] + 31) / 32;
+  J.blk0 = 0;
+  return J;
+}
 
 // fused Adam of the biases
 __global__ void tg_adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
@@ -699,9 +742,7 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
       const size_t nwl = (size_t)rup(w[l + 1], 128) * rup(w[l], 32), ntl = (size_t)rup(w[l], 128) * rup(w[l + 1], 32);
       for (int k = 0; k < 4; ++k)
         if ((e = zalloc(&ts.ws[4 * l + k], k < 2 ? nwl : ntl))) return e;
-      tg_weights_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(
-          net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr,
-          ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
+      tg_split_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(weight_job(net, ts, l));
     }
     if ((e = cudaGetLastError())) return e;
   }
@@ -780,6 +821,19 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
                  ts.grad + ts.b_base + net.b_off[l - 1]);
     }
   }
+  // the Adam jobs of every layer, for the one per-step launch
+  {
+    std::vector<WJob> jobs(L);
+    int blk = 0;
+    for (int l = 0; l < L; ++l) {
+      jobs[l] = weight_job(net, ts, l);
+      jobs[l].blk0 = blk;
+      blk += jobs[l].bx * ((w[l + 1] + 31) / 32);
+    }
+    if (!ts.wjobs && (e = cudaMalloc(&ts.wjobs, sizeof(WJob) * L))) return e;
+    if ((e = cudaMemcpy(ts.wjobs, jobs.data(), sizeof(WJob) * L, cudaMemcpyHostToDevice))) return e;
+    ts.wjob_blocks = blk;
+  }
   ts.bs = bs;
   return cudaSuccess;
 }
@@ -846,16 +900,11 @@ __global__ void tg_step_kernel(int* t_dev) { *t_dev += 1; }
 
 cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr) {
   Net& net = ctx->net;
-  const std::vector<int>& w = net.widths;
   ts.t += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   tg_step_kernel<<<1, 1, 0, ctx->stream>>>(ts.t_dev);
-  for (int l = 0; l < net.n_layers; ++l) {
-    tg_weights_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(
-        net.W32 + net.w_off[l], ts.part + ts.part_off[l], ts.ksplit[l], w[l + 1], w[l], 1, ts.m + net.w_off[l],
-        ts.v + net.w_off[l], lr, b1, b2, eps, ts.t_dev, ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32),
-        ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
-  }
+  tg_weights_kernel<<<ts.wjob_blocks, WBLOCK, 0, ctx->stream>>>(static_cast<const WJob*>(ts.wjobs), net.n_layers, lr,
+                                                                b1, b2, eps, ts.t_dev);
   tg_adam_kernel<<<nblk(ts.nb), 256, 0, ctx->stream>>>(net.b32, ts.grad + ts.b_base, ts.m + ts.nw, ts.v + ts.nw,
                                                        ts.nb, lr, b1, b2, eps, ts.t_dev);
   return cudaGetLastError();
@@ -865,11 +914,8 @@ cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts) {
   Net& net = ctx->net;
   const std::vector<int>& w = net.widths;
   if (ts.ws.empty()) return cudaSuccess;
-  for (int l = 0; l < net.n_layers; ++l) {
-    tg_weights_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(
-        net.W32 + net.w_off[l], nullptr, 0, w[l + 1], w[l], 0, nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, nullptr,
-        ts.ws[4 * l], ts.ws[4 * l + 1], rup(w[l], 32), ts.ws[4 * l + 2], ts.ws[4 * l + 3], rup(w[l + 1], 32));
-  }
+  for (int l = 0; l < net.n_layers; ++l)
+    tg_split_kernel<<<wgrid(w[l + 1], w[l]), WBLOCK, 0, ctx->stream>>>(weight_job(net, ts, l));
   return cudaGetLastError();
 }
 
@@ -877,7 +923,7 @@ void train_release(rtn_ctx* ctx) {
   TrainState& ts = ctx->train;
   free_bufs(ts);
   for (auto* p : ts.ws) if (p) cudaFree(p);
-  for (void* p : {(void*)ts.grad, (void*)ts.m, (void*)ts.v, (void*)ts.t_dev}) if (p) cudaFree(p);
+  for (void* p : {(void*)ts.grad, (void*)ts.m, (void*)ts.v, (void*)ts.t_dev, ts.wjobs}) if (p) cudaFree(p);
   delete static_cast<TgPlan*>(ts.plan);
   ts = TrainState{};
 }
