@@ -689,7 +689,64 @@ def bench_runtime_analysis(steps=200):
         r = one(n_hidden, width, B=B, graph=False)
         out["batch"].append({"instances": B, "hidden_layers": n_hidden, "width": width,
                              "rti_steps_per_s": B / (r["ms_api"] * 1e-3), "ms_per_step": r["ms_api"]})
+    out["quadrotor_one_controller"] = bench_one_quadrotor(steps)
     return out
+
+
+# Table III (Sec. VI): networks N-L-W (hidden layers x width) and the paper's
+# average optimisation time of RTN-MPC on one CPU core [ms] (context only)
+TABLE3 = [(3, 32, 2.2), (4, 64, 2.3), (5, 128, 3.2)]
+
+
+def bench_one_quadrotor(steps=200):
+    """One quadrotor controller (N = 10, dt = 0.05 s, the residual networks of
+    Table III): one RTI step (network + Jacobian, RK4 + sensitivities, QP,
+    feedback) captured in a CUDA graph and replayed, split BF16 (tile shape
+    autotuned) and FP32-accurate; control frequency against the paper's
+    optimisation time on one CPU core (context)."""
+    import torch
+    import paper_2203_07747_b300 as rtn
+    rows = []
+    for n_hidden, width, paper_ms in TABLE3:
+        prob = W.make_problem("cfg1_single_fp64", seed=0, bf16=True)
+        prob["layers"] = W.xavier_mlp([17] + [width] * n_hidden + [3], 0, bf16=True)
+        row = {"hidden_layers": n_hidden, "width": width, "paper_cpu_ms": paper_ms}
+        for prec in ("bf16x2", "fp32"):
+            s = torch.cuda.Stream()
+            ctl = rtn.Controller(prob["N"], prob["dt"], prob["Q"], prob["R"], QN=prob["QN"], quad=prob["quad"],
+                                 layers=prob["layers"], precision=prec, stream=s)
+            if prec != "fp32":
+                ctl.autotune()
+            xref, uref = W.node_refs(prob)
+            xr = torch.as_tensor(xref, dtype=torch.float32, device="cuda")
+            ur = torch.as_tensor(uref, dtype=torch.float32, device="cuda")
+            x0 = xr[:1].clone() + 0.02
+            u0 = torch.empty((1, 4), device="cuda")
+            st = torch.empty(1, dtype=torch.int32, device="cuda")
+            with torch.cuda.stream(s):
+                for _ in range(10):
+                    ctl.rti_step(x0, xr, ur, u0, st)
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    ctl.rti_step(x0, xr, ur, u0, st)
+                for _ in range(10):
+                    g.replay()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                e0.record(s)
+                for _ in range(steps):
+                    g.replay()
+                e1.record(s)
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            assert int(st.item()) == 0
+            row[prec] = {"ms_per_rti_step": ms, "hz": 1e3 / ms}
+            ctl.close()
+        rows.append(row)
+    return {"what": "one quadrotor controller, N = 10, one RTI step per control step, CUDA graph replayed; "
+                    "paper_cpu_ms = the paper's RTN-MPC optimisation time on one CPU core (Table III, context)",
+            "rows": rows}
 
 
 LAY_KERNELS = {"input GEMM": "lay_kernel<4>", "forward GEMM": "lay_kernel<0>", "first backward GEMM": "lay_kernel<3>",
