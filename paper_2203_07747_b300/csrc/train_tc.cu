@@ -72,6 +72,15 @@ struct TgArgs {
   int* err;
 };
 
+// Programmatic dependent launch: the launches of a training step carry the
+// programmatic-serialisation attribute, so a kernel may start (its prologue:
+// barriers, tensor memory, descriptor prefetch) while its predecessor
+// drains; pdl_wait() then blocks until every prerequisite grid has completed
+// and its memory is visible (a no-op for an ordinary launch), and
+// pdl_trigger() lets the next launch start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <int MODE, int NT>
 __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant__ TgMaps mp, TgArgs a) {
   constexpr int TG_STAGES = Tg<NT>::STAGES, TG_N = NT;
@@ -117,6 +126,8 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
 
   // tile t: M tile t % mts, N tile (t / mts) % nts, K range t / (mts nts)
   if (warp == 0) {
@@ -394,18 +405,34 @@ cudaError_t tg_setup() {
                               (int)Tg<TG_WG_NT>::SMEM);
 }
 
+// a launch with the programmatic-serialisation attribute (see pdl_wait)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // err: the context's device status word (re-read at every launch: the
 // network packs, and with them the word, are rebuilt after training)
 cudaError_t tg_launch(const TgGemm& g, int* err, cudaStream_t s) {
   TgArgs a = g.args;
   a.err = err;
   switch (g.mode) {
-    case TG_FWD: tg_kernel<TG_FWD, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
-    case TG_OUT: tg_kernel<TG_OUT, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
-    case TG_BWD: tg_kernel<TG_BWD, 128><<<g.grid, TG_THREADS, Tg<128>::SMEM, s>>>(g.maps, a); break;
-    default: tg_kernel<TG_WG, TG_WG_NT><<<g.grid, TG_THREADS, Tg<TG_WG_NT>::SMEM, s>>>(g.maps, a); break;
+    case TG_FWD: return launch_pdl(tg_kernel<TG_FWD, 128>, dim3(g.grid), dim3(TG_THREADS), Tg<128>::SMEM, s, g.maps, a);
+    case TG_OUT: return launch_pdl(tg_kernel<TG_OUT, 128>, dim3(g.grid), dim3(TG_THREADS), Tg<128>::SMEM, s, g.maps, a);
+    case TG_BWD: return launch_pdl(tg_kernel<TG_BWD, 128>, dim3(g.grid), dim3(TG_THREADS), Tg<128>::SMEM, s, g.maps, a);
+    default:
+      return launch_pdl(tg_kernel<TG_WG, TG_WG_NT>, dim3(g.grid), dim3(TG_THREADS), Tg<TG_WG_NT>::SMEM, s, g.maps, a);
   }
-  return cudaGetLastError();
 }
 
 // epilogue operands of a planned GEMM
@@ -427,6 +454,7 @@ int tg_ksplit(const TgGemm& g) { return g.args.ksplit; }
 inline int rup(int x, int m) { return (x + m - 1) / m * m; }
 inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+
 __device__ __forceinline__ void split2(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
   h = __float2bfloat16_rn(v);
   l = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -437,7 +465,12 @@ __device__ __forceinline__ void split2(float v, __nv_bfloat16& h, __nv_bfloat16&
 __global__ void tg_gather_kernel(const float* __restrict__ X, const float* __restrict__ U, int start, int bs,
                                  int ldf, __nv_bfloat16* __restrict__ nh, __nv_bfloat16* __restrict__ nl,
                                  __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl,
-                                 const int* __restrict__ k_dev, int per_epoch) {
+                                 const int* __restrict__ k_dev, int per_epoch, float* __restrict__ db, int nb) {
+  pdl_wait();
+  pdl_trigger();
+  // the bias gradients, which the loss and backward launches accumulate
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nb; e += (long long)gridDim.x * blockDim.x)
+    db[e] = 0.0f;
   // a replayed step: its minibatch from the step counter on the device
   if (k_dev) start = (*k_dev % per_epoch) * bs;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -466,6 +499,8 @@ __global__ void tg_loss_kernel(const float* __restrict__ Z, const float* __restr
                                int ldf, __nv_bfloat16* __restrict__ nh, __nv_bfloat16* __restrict__ nl,
                                __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl, float* loss,
                                float* __restrict__ db, const int* __restrict__ k_dev, int per_epoch) {
+  pdl_wait();
+  pdl_trigger();
   // a replayed step: its minibatch and loss entry from the step counter on the device
   if (k_dev) {
     start = (*k_dev % per_epoch) * bs;
@@ -636,6 +671,8 @@ __global__ void __launch_bounds__(256) tg_split_kernel(WJob J) {
 // launch: block -> (layer, 32 x 32 tile) by the jobs' first blocks
 __global__ void __launch_bounds__(256) tg_weights_kernel(const WJob* __restrict__ jobs, int n_jobs, float lr, float b1,
                                                          float b2, float eps, const int* __restrict__ t_dev) {
+  pdl_wait();
+  pdl_trigger();
   int li = 0;
   while (li + 1 < n_jobs && (int)blockIdx.x >= jobs[li + 1].blk0) ++li;
   const WJob J = jobs[li];
@@ -673,6 +710,8 @@ WJob weight_job(const Net& net, const TrainState& ts, int l) {
 __global__ void tg_adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
                                float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
                                const int* __restrict__ t_dev) {
+  pdl_wait();
+  pdl_trigger();
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
@@ -839,7 +878,11 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
 }
 
 // the step counter of a replayed training step, advanced at the step's end
-__global__ void tg_next_step_kernel(int* k_dev) { *k_dev += 1; }
+__global__ void tg_next_step_kernel(int* k_dev) {
+  pdl_wait();
+  pdl_trigger();
+  *k_dev += 1;
+}
 
 static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
                              int start, float* loss, const int* k_dev, int per_epoch);
@@ -855,8 +898,7 @@ cudaError_t train_grad_dev(rtn_ctx* ctx, TrainState& ts, const float* X, const f
 }
 
 cudaError_t train_next_step(rtn_ctx* ctx, int* k_dev) {
-  tg_next_step_kernel<<<1, 1, 0, ctx->stream>>>(k_dev);
-  return cudaGetLastError();
+  return launch_pdl(tg_next_step_kernel, dim3(1), dim3(1), 0, ctx->stream, k_dev);
 }
 
 static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
@@ -867,16 +909,17 @@ static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const
   if (!P) return cudaErrorInvalidValue;
   cudaStream_t s = ctx->stream;
   cudaError_t e;
-  // the bias gradients are accumulated atomically by the loss and backward launches
-  if ((e = cudaMemsetAsync(ts.grad + ts.b_base, 0, ts.nb * sizeof(float), s))) return e;
-  tg_gather_kernel<<<nblk((size_t)ts.ldf * 32), 256, 0, s>>>(X, U, start, bs, ts.ldf, ts.an[0], ts.an[1], ts.af[0],
-                                                               ts.af[1], k_dev, per_epoch);
+  // the gather also zeroes the bias gradients, which the loss and backward
+  // launches accumulate atomically
+  if ((e = launch_pdl(tg_gather_kernel, dim3(nblk((size_t)ts.ldf * 32)), dim3(256), 0, s, X, U, start, bs, ts.ldf,
+                      ts.an[0], ts.an[1], ts.af[0], ts.af[1], k_dev, per_epoch, ts.grad + ts.b_base, (int)ts.nb)))
+    return e;
   for (int l = 0; l < L; ++l)
     if ((e = tg_launch(P->fwd[l], net.tc.err, s))) return e;
-  tg_loss_kernel<<<nblk((size_t)ts.ldf * 32), 256, 0, s>>>(ts.z, Y, start, bs, no, ts.ldf, ts.gn[2 * (L - 1)],
-                                                             ts.gn[2 * (L - 1) + 1], ts.gf[2 * (L - 1)],
-                                                             ts.gf[2 * (L - 1) + 1], loss,
-                                                             ts.grad + ts.b_base + net.b_off[L - 1], k_dev, per_epoch);
+  if ((e = launch_pdl(tg_loss_kernel, dim3(nblk((size_t)ts.ldf * 32)), dim3(256), 0, s, (const float*)ts.z, Y, start,
+                      bs, no, ts.ldf, ts.gn[2 * (L - 1)], ts.gn[2 * (L - 1) + 1], ts.gf[2 * (L - 1)],
+                      ts.gf[2 * (L - 1) + 1], loss, ts.grad + ts.b_base + net.b_off[L - 1], k_dev, per_epoch)))
+    return e;
   for (int l = L - 1; l >= 0; --l) {
     if ((e = tg_launch(P->wg[l], net.tc.err, s))) return e;
     if (l >= 1 && (e = tg_launch(P->bwd[l], net.tc.err, s))) return e;
@@ -896,18 +939,24 @@ cudaError_t train_reduce(rtn_ctx* ctx, TrainState& ts) {
 
 // the Adam step counter (on the device, so that a captured step can be
 // replayed) advanced by one
-__global__ void tg_step_kernel(int* t_dev) { *t_dev += 1; }
+__global__ void tg_step_kernel(int* t_dev) {
+  pdl_wait();
+  pdl_trigger();
+  *t_dev += 1;
+}
 
 cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr) {
   Net& net = ctx->net;
   ts.t += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  tg_step_kernel<<<1, 1, 0, ctx->stream>>>(ts.t_dev);
-  tg_weights_kernel<<<ts.wjob_blocks, WBLOCK, 0, ctx->stream>>>(static_cast<const WJob*>(ts.wjobs), net.n_layers, lr,
-                                                                b1, b2, eps, ts.t_dev);
-  tg_adam_kernel<<<nblk(ts.nb), 256, 0, ctx->stream>>>(net.b32, ts.grad + ts.b_base, ts.m + ts.nw, ts.v + ts.nw,
-                                                       ts.nb, lr, b1, b2, eps, ts.t_dev);
-  return cudaGetLastError();
+  cudaError_t e;
+  if ((e = launch_pdl(tg_step_kernel, dim3(1), dim3(1), 0, ctx->stream, ts.t_dev))) return e;
+  if ((e = launch_pdl(tg_weights_kernel, dim3(ts.wjob_blocks), WBLOCK, 0, ctx->stream,
+                      static_cast<const WJob*>(ts.wjobs), net.n_layers, lr, b1, b2, eps, (const int*)ts.t_dev)))
+    return e;
+  return launch_pdl(tg_adam_kernel, dim3(nblk(ts.nb)), dim3(256), 0, ctx->stream, net.b32,
+                    (const float*)(ts.grad + ts.b_base), ts.m + ts.nw, ts.v + ts.nw, ts.nb, lr, b1, b2, eps,
+                    (const int*)ts.t_dev);
 }
 
 cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts) {
