@@ -65,7 +65,17 @@ struct Ly {
   static constexpr int NA = (MODE == LY_JD || MODE == LY_BW0 || MODE == LY_IN) ? 2 : 1;  // weight tiles (hi, lo)
   static constexpr int NB = F8 ? 3 : 2;                             // B tiles: pieces
   static constexpr int KB = F8 ? 64 : LY_KB;                        // K elements per stage
+  // split-BF16 backward: the tile's activations a_l (hi, lo) reach the
+  // epilogue through shared memory, one 16-node group per buffer of a ring of
+  // LY_NBN / 16 loaded by TMA from an eleventh warp (global loads of 2 B per
+  // lane were the epilogue's largest cost)
+  static constexpr bool STAGE_ACT = MODE == LY_BWD && !F8;
+  static constexpr int STAGES = LY_STAGES;
+  static constexpr int THREADS = STAGE_ACT ? LY_THREADS + 32 : LY_THREADS;
 };
+// one ring buffer: the activations of 16 nodes x 128 neurons, hi then lo
+constexpr int LY_ACT_RING = LY_NBN / 16;
+constexpr uint32_t LY_ACT_BYTES = 2u * 16u * 128u * 2u;
 template <int MODE, bool F8 = false>
 __host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * 64u; }
 template <int MODE, bool F8 = false>
@@ -73,14 +83,20 @@ __host__ __device__ constexpr uint32_t ly_stage() {
   return Ly<MODE, F8>::NA * LY_A_BYTES + Ly<MODE, F8>::NB * ly_b_bytes<MODE>();
 }
 template <int MODE, bool F8 = false>
-__host__ __device__ constexpr size_t ly_smem() { return LY_STAGES * ly_stage<MODE, F8>() + 1024 + 256; }
+__host__ __device__ constexpr size_t ly_smem() {
+  return Ly<MODE, F8>::STAGES * ly_stage<MODE, F8>() + (Ly<MODE, F8>::STAGE_ACT ? LY_ACT_RING * LY_ACT_BYTES : 0) + 1024 +
+         256;
+}
 static_assert(ly_b_bytes<LY_FWD>() % 1024 == 0 && ly_b_bytes<LY_BWD>() % 1024 == 0, "1 KB aligned tiles");
 static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448 && ly_smem<LY_BW0>() <= 232448 &&
-                  ly_smem<LY_FWD, true>() <= 232448 && ly_smem<LY_BWD, true>() <= 232448,
+                  ly_smem<LY_FWD, true>() <= 232448 && ly_smem<LY_BWD, true>() <= 232448 &&
+                  ly_smem<LY_BWD>() <= 232448,
               "shared memory");
+static_assert(ly_stage<LY_BWD>() % 1024 == 0 && LY_ACT_BYTES % 1024 == 0, "1 KB aligned activation buffers");
 
 struct LyMaps {
   CUtensorMap bh, bl, b3;  // activations / adjoints hi, lo (F8: hi, mid, lo)
+  CUtensorMap sh, sl;      // split-BF16 backward: the activations a_l hi, lo, box 128 x 16
 };
 
 struct LyArgs {
@@ -95,6 +111,7 @@ struct LyArgs {
   const float* bias;   // FWD: bias of the produced layer
   __nv_bfloat16* dh;   // FWD, last hidden layer: its d as BF16 hi + lo (the
   __nv_bfloat16* dl;   //      B operand of the folded first backward GEMM)
+  int act_row0;        // split-BF16 BWD: row of node 0 of a_l in the stacked activations
   const __nv_bfloat16* ah;  // BW0 / BWD: a_l of the adjoint's layer [node][hs]
   const __nv_bfloat16* al;  //            hi / lo, d_l = 1 - a_l^2
   __nv_bfloat16* yh;   // FWD / BWD outputs
@@ -172,17 +189,17 @@ __device__ __forceinline__ void split_bf(float v, __nv_bfloat16& h, __nv_bfloat1
   l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// the activation pairs a_l[node][ic] of the 8 nodes that the warp of half H
-// stores in the 16-node group starting at node_g
+// the activation pairs a_l of the 8 nodes that the warp of half H stores in
+// a 16-node group of a backward tile, from the group's shared-memory buffer
+// [16 nodes][128 neurons] (hi, then lo at +16 x 128), column col
 template <int H>
-__device__ __forceinline__ void bwd_load(const __nv_bfloat16* __restrict__ ah, const __nv_bfloat16* __restrict__ al,
-                                         int node_g, int n_nodes, int hs, int ic, __nv_bfloat16 (&ph)[8],
-                                         __nv_bfloat16 (&pl)[8]) {
+__device__ __forceinline__ void bwd_load_s(const __nv_bfloat16* __restrict__ sh, int col, __nv_bfloat16 (&ph)[8],
+                                           __nv_bfloat16 (&pl)[8]) {
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
-    const size_t o = (size_t)min(node_g + 8 * H + kk, n_nodes - 1) * hs + ic;
-    ph[kk] = ah[o];
-    pl[kk] = al[o];
+    const int o = (8 * H + kk) * 128 + col;
+    ph[kk] = sh[o];
+    pl[kk] = sh[16 * 128 + o];
   }
 }
 
@@ -298,9 +315,10 @@ __device__ __forceinline__ void bwd_group8(const float (&v)[48], const uint32_t 
 // one GEMM layer over all nodes (see the file comment); MODE selects the
 // operands' shape and the epilogue
 template <int MODE, bool F8 = false>
-__global__ void __launch_bounds__(LY_THREADS, 1)
+__global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
     lay_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ LyMaps bm, LyArgs a) {
   using T = Ly<MODE, F8>;
+  constexpr int NS = T::STAGES;
   static_assert(!F8 || MODE == LY_FWD || MODE == LY_BWD, "FP8 hidden GEMMs only");
   constexpr uint32_t B_BYTES = ly_b_bytes<MODE>(), STAGE = ly_stage<MODE, F8>();
   constexpr uint32_t B0 = T::NA * LY_A_BYTES;  // offset of the B tiles in a stage
@@ -309,28 +327,35 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
   const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
   uint8_t* sm = smem_raw + pad;
   const uint32_t st0 = sraw + pad;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + LY_STAGES * STAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * LY_STAGES + 6);
+  const uint32_t act_s = st0 + NS * STAGE;  // activation buffers (STAGE_ACT)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + (T::STAGE_ACT ? LY_ACT_RING * LY_ACT_BYTES : 0));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * LY_ACT_RING);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
-  auto empty_bar = [&](int s) { return bar(LY_STAGES + s); };
-  auto acc_full = [&](int c) { return bar(2 * LY_STAGES + c); };
-  auto tmem_free = [&](int c) { return bar(2 * LY_STAGES + 2 + c); };
-  const uint32_t mma_done = bar(2 * LY_STAGES + 4);
-  const uint32_t stall_bar = bar(2 * LY_STAGES + 5);  // fault injection: nothing completes it
+  auto empty_bar = [&](int s) { return bar(NS + s); };
+  auto acc_full = [&](int c) { return bar(2 * NS + c); };
+  auto tmem_free = [&](int c) { return bar(2 * NS + 2 + c); };
+  const uint32_t mma_done = bar(2 * NS + 4);
+  const uint32_t stall_bar = bar(2 * NS + 5);  // fault injection: nothing completes it
+  auto act_full = [&](int b) { return bar(2 * NS + 6 + b); };
+  auto act_empty = [&](int b) { return bar(2 * NS + 6 + LY_ACT_RING + b); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_tiles = (long long)a.n_groups * a.mts;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < LY_STAGES; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
     for (int c = 0; c < 2; ++c) {
       mbar_init(acc_full(c), 1);
       mbar_init(tmem_free(c), LY_EPI_WARPS);
+    }
+    for (int c = 0; c < LY_ACT_RING; ++c) {
+      mbar_init(act_full(c), 1);
+      mbar_init(act_empty(c), LY_EPI_WARPS);
     }
     mbar_init(mma_done, 1);
     mbar_init(stall_bar, 1);
@@ -378,10 +403,10 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
         __syncwarp();
         issued |= 1u << s;
         last_ph = (last_ph & ~(1u << s)) | (ph << s);
-        if (++s == LY_STAGES) { s = 0; ph ^= 1u; }
+        if (++s == NS) { s = 0; ph ^= 1u; }
       }
     }
-    for (int q = 0; q < LY_STAGES; ++q)
+    for (int q = 0; q < NS; ++q)
       if (issued & (1u << q)) {
         const long long t0 = clock64();
         while (!mbar_try(full_bar(q), (last_ph >> q) & 1u) && clock64() - t0 < WAIT_CYCLES) {
@@ -419,7 +444,7 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
           }
         }
         mma_commit_elect(empty_bar(s));
-        if (++s == LY_STAGES) { s = 0; ph ^= 1u; }
+        if (++s == NS) { s = 0; ph ^= 1u; }
       }
       if (!ok) break;
       mma_commit_elect(acc_full(acc));
@@ -429,7 +454,39 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
     const long long t0 = clock64();
     while (!mbar_try(mma_done, 0) && clock64() - t0 < WAIT_CYCLES) {
     }
-  } else {
+  } else if (T::STAGE_ACT && warp == LY_THREADS / 32) {
+    // ---------------- activation loader (split-BF16 backward): group g of
+    // each tile (16 nodes x 128 neurons, hi and lo) into ring buffer g once
+    // the epilogue has released the buffer's previous group
+    if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bm.sh)) : "memory");
+    bool ok = true;
+    uint32_t issued = 0, last_ph = 0;
+    long long j = 0;
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++j) {
+      const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
+      const uint32_t ph = (uint32_t)(j & 1);
+      for (int g = 0; g < LY_ACT_RING; ++g) {
+        if (!(ok = mbar_wait_warp(act_empty(g), ph ^ 1u, abort_flag, a.err, a.wait_cycles))) break;
+        if (elect_one()) {
+          const uint32_t dst = act_s + (uint32_t)g * LY_ACT_BYTES;
+          const int row = a.act_row0 + grp * LY_NBN + 16 * g;
+          mbar_expect_tx(act_full(g), LY_ACT_BYTES);
+          tma_load_2d(dst, &bm.sh, mt * 128, row, act_full(g));
+          tma_load_2d(dst + LY_ACT_BYTES / 2, &bm.sl, mt * 128, row, act_full(g));
+        }
+        __syncwarp();
+        issued |= 1u << g;
+        last_ph = (last_ph & ~(1u << g)) | (ph << g);
+      }
+    }
+    // the ring's last copies have landed before the CTA may exit
+    for (int g = 0; g < LY_ACT_RING; ++g)
+      if (issued & (1u << g)) {
+        const long long t0 = clock64();
+        while (!mbar_try(act_full(g), (last_ph >> g) & 1u) && clock64() - t0 < a.wait_cycles) {
+        }
+      }
+  } else if (warp < LY_THREADS / 32) {
     // ---------------- epilogue: TMEM lane quarter warp % 4, one output row
     // per lane; the two warps of a quarter take alternate 16-column chunks.
     // Each chunk issues its loads first and predicates only the stores, so
@@ -437,7 +494,8 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
     const int q = warp & 3, half = (warp - 2) >> 2;
     int acc = 0;
     uint32_t aph = 0;
-    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    long long j = 0;  // the CTA's tile count (activation buffer j % 2)
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++j) {
       const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
       // output row i (BW0: row k of component r)
       const int r0 = MODE == LY_BW0 ? mt / a.mtpr : 0;
@@ -449,15 +507,9 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
       // backward: the first group's activations are loaded while the
       // accumulator is still being computed, each later group's while the
       // one before it is stored
-      __nv_bfloat16 ph[8], pl[8], qh[16], ql[16];
+      __nv_bfloat16 qh[16], ql[16];
       uint32_t p8[6];
       const int tq = lane & 3;
-      if (MODE == LY_BWD && !F8) {
-        if (half == 0)
-          bwd_load<0>(a.ah, a.al, node0, a.n_nodes, a.hs, ic, ph, pl);
-        else
-          bwd_load<1>(a.ah, a.al, node0, a.n_nodes, a.hs, ic, ph, pl);
-      }
       if (MODE == LY_BWD && F8) {
         if (half == 0)
           bwd_load8<0>(a, node0, ic, tq, p8);
@@ -497,34 +549,37 @@ __global__ void __launch_bounds__(LY_THREADS, 1)
         }
       }
       if (MODE == LY_BWD && !F8) {
-        // 16-node groups: both warps of the quarter read the group's 48
-        // columns, each stores its 8 nodes
+        // the tile's activations from shared memory (loaded by the
+        // activation warp, group g in ring buffer g), 16-node groups: both
+        // warps of the quarter read the group's 48 columns, each stores its
+        // 8 nodes
+        const int col = q * 32 + lane;
+        bool ok = true;
 #pragma unroll 1
         for (int g = 0; g < T::NODES / 16; ++g) {
           float v[48];
           tmem_ld16(taddr + 48 * g, v);
           tmem_ld16(taddr + 48 * g + 16, v + 16);
           tmem_ld16(taddr + 48 * g + 32, v + 32);
-          __nv_bfloat16 nh[8], nl[8];
-          if (g + 1 < T::NODES / 16) {
-            if (half == 0)
-              bwd_load<0>(a.ah, a.al, node0 + 16 * (g + 1), a.n_nodes, a.hs, ic, nh, nl);
-            else
-              bwd_load<1>(a.ah, a.al, node0 + 16 * (g + 1), a.n_nodes, a.hs, ic, nh, nl);
+          if (!(ok = mbar_wait_warp(act_full(g), (uint32_t)(j & 1), abort_flag, a.err, a.wait_cycles))) {
+            tmem_wait_ld();
+            break;
           }
+          const __nv_bfloat16* sa = reinterpret_cast<const __nv_bfloat16*>(sm + NS * STAGE + (uint32_t)g * LY_ACT_BYTES);
+          __nv_bfloat16 ph[8], pl[8];
+          if (half == 0)
+            bwd_load_s<0>(sa, col, ph, pl);
+          else
+            bwd_load_s<1>(sa, col, ph, pl);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(act_empty(g));
           tmem_wait_ld();
           if (half == 0)
             bwd_group<0>(v, ph, pl, node0 + 16 * g, a.n_nodes, a.hs, i, active, a.yh, a.yl);
           else
             bwd_group<1>(v, ph, pl, node0 + 16 * g, a.n_nodes, a.hs, i, active, a.yh, a.yl);
-          if (g + 1 < T::NODES / 16) {
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-              ph[kk] = nh[kk];
-              pl[kk] = nl[kk];
-            }
-          }
         }
+        if (!ok) break;
       }
       for (int ch = half; MODE != LY_BWD && ch < T::N / 16; ch += 2) {
         float v[16];
@@ -888,6 +943,19 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
       err = "cuTensorMapEncodeTiled failed";
       return cudaSuccess;
     }
+  // the backward epilogues' activation blocks: 128 neurons x LY_NBN nodes,
+  // unswizzled (a lane reads its neuron's column)
+  for (int p = 0; p < 2; ++p) {
+    const cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)(L - 1) * npad};
+    const cuuint64_t str[1] = {(cuuint64_t)HP * 2};
+    const cuuint32_t box[2] = {128, 16};
+    if (encode(reinterpret_cast<CUtensorMap*>(s->mact[p]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, s->act[p], dims, str,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      err = "cuTensorMapEncodeTiled failed (activation blocks)";
+      return cudaSuccess;
+    }
+  }
   for (int b = 0; b < 2; ++b)
     for (int p = 0; p < 2; ++p) {
       if (!enc(s->mb[b][p], s->xb[b][p], 3 * npad, 3 * LY_NBN)) {
@@ -1224,8 +1292,11 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
       lay_kernel<LY_BWD, true><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD, true>(), st>>>(
           *reinterpret_cast<const CUtensorMap*>(s->q8tmap), maps8(s->b8map[src]), a);
     } else {
-      lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD>(), st>>>(
-          *rmap, maps(s->mb[src][0], s->mb[src][1]), a);
+      LyMaps m = maps(s->mb[src][0], s->mb[src][1]);
+      memcpy(&m.sh, s->mact[0], sizeof(CUtensorMap));
+      memcpy(&m.sl, s->mact[1], sizeof(CUtensorMap));
+      a.act_row0 = (l - 1) * s->npad;
+      lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), Ly<LY_BWD>::THREADS, ly_smem<LY_BWD>(), st>>>(*rmap, m, a);
     }
   }
   // J_D = W_0' D_1 (W_0' hi and lo rows)

@@ -68,6 +68,7 @@ struct LayState {
   __nv_bfloat16* xb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   alignas(64) unsigned char ma[2][128];     // activations hi / lo, box 32 x 256
   alignas(64) unsigned char mb[2][2][128];  // adjoints, box 32 x 240
+  alignas(64) unsigned char mact[2][128];   // activations hi / lo, box 128 x 80 unswizzled (backward epilogues)
   // folded first backward layer: M_r = W_{L-2}' diag(W_L[r]) as BF16 hi rows
   // [3 HP][HP] then lo rows, and d_{L-1} as BF16 hi + lo [npad][hs]
   __nv_bfloat16* mw = nullptr;
