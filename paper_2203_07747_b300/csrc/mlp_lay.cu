@@ -69,12 +69,16 @@ struct Ly {
   // epilogue through shared memory, one 16-node group per buffer of a ring of
   // LY_NBN / 16 loaded by TMA from an eleventh warp (global loads of 2 B per
   // lane were the epilogue's largest cost)
-  static constexpr bool STAGE_ACT = MODE == LY_BWD && !F8;
+  // The first backward GEMM (its d_{L-2} from a_{L-2}) reads them the same
+  // way, 16-node chunks through a ring of four.
+  static constexpr bool STAGE_ACT = (MODE == LY_BWD || MODE == LY_BW0) && !F8;
   static constexpr int STAGES = LY_STAGES;
   static constexpr int THREADS = STAGE_ACT ? LY_THREADS + 32 : LY_THREADS;
+  static constexpr int ACT_RING = MODE == LY_BW0 ? 4 : LY_NBN / 16;   // ring buffers
+  static constexpr int ACT_CHUNKS = NODES / 16;                      // 16-node chunks per tile
+  static constexpr int ACT_READERS = MODE == LY_BW0 ? LY_EPI_WARPS / 2 : LY_EPI_WARPS;  // warps reading a chunk
 };
 // one ring buffer: the activations of 16 nodes x 128 neurons, hi then lo
-constexpr int LY_ACT_RING = LY_NBN / 16;
 constexpr uint32_t LY_ACT_BYTES = 2u * 16u * 128u * 2u;
 template <int MODE, bool F8 = false>
 __host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * 64u; }
@@ -84,15 +88,16 @@ __host__ __device__ constexpr uint32_t ly_stage() {
 }
 template <int MODE, bool F8 = false>
 __host__ __device__ constexpr size_t ly_smem() {
-  return Ly<MODE, F8>::STAGES * ly_stage<MODE, F8>() + (Ly<MODE, F8>::STAGE_ACT ? LY_ACT_RING * LY_ACT_BYTES : 0) + 1024 +
-         256;
+  return Ly<MODE, F8>::STAGES * ly_stage<MODE, F8>() +
+         (Ly<MODE, F8>::STAGE_ACT ? Ly<MODE, F8>::ACT_RING * LY_ACT_BYTES : 0) + 1024 + 256;
 }
 static_assert(ly_b_bytes<LY_FWD>() % 1024 == 0 && ly_b_bytes<LY_BWD>() % 1024 == 0, "1 KB aligned tiles");
 static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448 && ly_smem<LY_BW0>() <= 232448 &&
                   ly_smem<LY_FWD, true>() <= 232448 && ly_smem<LY_BWD, true>() <= 232448 &&
                   ly_smem<LY_BWD>() <= 232448,
               "shared memory");
-static_assert(ly_stage<LY_BWD>() % 1024 == 0 && LY_ACT_BYTES % 1024 == 0, "1 KB aligned activation buffers");
+static_assert(ly_stage<LY_BWD>() % 1024 == 0 && ly_stage<LY_BW0>() % 1024 == 0 && LY_ACT_BYTES % 1024 == 0,
+              "1 KB aligned activation buffers");
 
 struct LyMaps {
   CUtensorMap bh, bl, b3;  // activations / adjoints hi, lo (F8: hi, mid, lo)
@@ -111,7 +116,7 @@ struct LyArgs {
   const float* bias;   // FWD: bias of the produced layer
   __nv_bfloat16* dh;   // FWD, last hidden layer: its d as BF16 hi + lo (the
   __nv_bfloat16* dl;   //      B operand of the folded first backward GEMM)
-  int act_row0;        // split-BF16 BWD: row of node 0 of a_l in the stacked activations
+  int act_row0;        // split-BF16 BWD / BW0: row of node 0 of a_l in the stacked activations
   const __nv_bfloat16* ah;  // BW0 / BWD: a_l of the adjoint's layer [node][hs]
   const __nv_bfloat16* al;  //            hi / lo, d_l = 1 - a_l^2
   __nv_bfloat16* yh;   // FWD / BWD outputs
@@ -200,18 +205,6 @@ __device__ __forceinline__ void bwd_load_s(const __nv_bfloat16* __restrict__ sh,
     const int o = (8 * H + kk) * 128 + col;
     ph[kk] = sh[o];
     pl[kk] = sh[16 * 128 + o];
-  }
-}
-
-// the activation pairs a_l[node][ic] of the 16 nodes of one chunk
-__device__ __forceinline__ void chunk_load(const __nv_bfloat16* __restrict__ ah, const __nv_bfloat16* __restrict__ al,
-                                           int node_c, int n_nodes, int hs, int ic, __nv_bfloat16 (&ph)[16],
-                                           __nv_bfloat16 (&pl)[16]) {
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const size_t o = (size_t)min(node_c + k, n_nodes - 1) * hs + ic;
-    ph[k] = ah[o];
-    pl[k] = al[o];
   }
 }
 
@@ -328,8 +321,8 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   uint8_t* sm = smem_raw + pad;
   const uint32_t st0 = sraw + pad;
   const uint32_t act_s = st0 + NS * STAGE;  // activation buffers (STAGE_ACT)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + (T::STAGE_ACT ? LY_ACT_RING * LY_ACT_BYTES : 0));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * LY_ACT_RING);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + (T::STAGE_ACT ? T::ACT_RING * LY_ACT_BYTES : 0));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * T::ACT_RING);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
@@ -339,7 +332,7 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   const uint32_t mma_done = bar(2 * NS + 4);
   const uint32_t stall_bar = bar(2 * NS + 5);  // fault injection: nothing completes it
   auto act_full = [&](int b) { return bar(2 * NS + 6 + b); };
-  auto act_empty = [&](int b) { return bar(2 * NS + 6 + LY_ACT_RING + b); };
+  auto act_empty = [&](int b) { return bar(2 * NS + 6 + T::ACT_RING + b); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_tiles = (long long)a.n_groups * a.mts;
@@ -353,9 +346,9 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
       mbar_init(acc_full(c), 1);
       mbar_init(tmem_free(c), LY_EPI_WARPS);
     }
-    for (int c = 0; c < LY_ACT_RING; ++c) {
+    for (int c = 0; c < T::ACT_RING; ++c) {
       mbar_init(act_full(c), 1);
-      mbar_init(act_empty(c), LY_EPI_WARPS);
+      mbar_init(act_empty(c), T::ACT_READERS);
     }
     mbar_init(mma_done, 1);
     mbar_init(stall_bar, 1);
@@ -455,35 +448,38 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
     while (!mbar_try(mma_done, 0) && clock64() - t0 < WAIT_CYCLES) {
     }
   } else if (T::STAGE_ACT && warp == LY_THREADS / 32) {
-    // ---------------- activation loader (split-BF16 backward): group g of
-    // each tile (16 nodes x 128 neurons, hi and lo) into ring buffer g once
-    // the epilogue has released the buffer's previous group
+    // ---------------- activation loader (split-BF16 backward GEMMs): chunk
+    // c of every tile (16 nodes x 128 neurons, hi and lo) into ring buffer
+    // n % ACT_RING (n the CTA's chunk count) once the epilogue has released
+    // the buffer's previous chunk
     if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bm.sh)) : "memory");
     bool ok = true;
     uint32_t issued = 0, last_ph = 0;
-    long long j = 0;
-    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++j) {
+    long long n = 0;
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int grp = (int)(t / a.mts), mt = (int)(t % a.mts);
-      const uint32_t ph = (uint32_t)(j & 1);
-      for (int g = 0; g < LY_ACT_RING; ++g) {
-        if (!(ok = mbar_wait_warp(act_empty(g), ph ^ 1u, abort_flag, a.err, a.wait_cycles))) break;
+      const int mc = MODE == LY_BW0 ? mt % a.mtpr : mt;  // neuron block (BW0: of component r)
+      for (int c = 0; c < T::ACT_CHUNKS; ++c, ++n) {
+        const int b = (int)(n % T::ACT_RING);
+        const uint32_t ph = (uint32_t)((n / T::ACT_RING) & 1);
+        if (!(ok = mbar_wait_warp(act_empty(b), ph ^ 1u, abort_flag, a.err, a.wait_cycles))) break;
         if (elect_one()) {
-          const uint32_t dst = act_s + (uint32_t)g * LY_ACT_BYTES;
-          const int row = a.act_row0 + grp * LY_NBN + 16 * g;
-          mbar_expect_tx(act_full(g), LY_ACT_BYTES);
-          tma_load_2d(dst, &bm.sh, mt * 128, row, act_full(g));
-          tma_load_2d(dst + LY_ACT_BYTES / 2, &bm.sl, mt * 128, row, act_full(g));
+          const uint32_t dst = act_s + (uint32_t)b * LY_ACT_BYTES;
+          const int row = a.act_row0 + grp * T::NODES + 16 * c;
+          mbar_expect_tx(act_full(b), LY_ACT_BYTES);
+          tma_load_2d(dst, &bm.sh, mc * 128, row, act_full(b));
+          tma_load_2d(dst + LY_ACT_BYTES / 2, &bm.sl, mc * 128, row, act_full(b));
         }
         __syncwarp();
-        issued |= 1u << g;
-        last_ph = (last_ph & ~(1u << g)) | (ph << g);
+        issued |= 1u << b;
+        last_ph = (last_ph & ~(1u << b)) | (ph << b);
       }
     }
     // the ring's last copies have landed before the CTA may exit
-    for (int g = 0; g < LY_ACT_RING; ++g)
-      if (issued & (1u << g)) {
+    for (int b = 0; b < T::ACT_RING; ++b)
+      if (issued & (1u << b)) {
         const long long t0 = clock64();
-        while (!mbar_try(act_full(g), (last_ph >> g) & 1u) && clock64() - t0 < a.wait_cycles) {
+        while (!mbar_try(act_full(b), (last_ph >> b) & 1u) && clock64() - t0 < a.wait_cycles) {
         }
       }
   } else if (warp < LY_THREADS / 32) {
@@ -516,7 +512,6 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
         else
           bwd_load8<1>(a, node0, ic, tq, p8);
       }
-      if (MODE == LY_BW0) chunk_load(a.ah, a.al, node0 + 16 * half, a.n_nodes, a.hs, ic, qh, ql);
       if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err, a.wait_cycles)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
@@ -561,7 +556,8 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
           tmem_ld16(taddr + 48 * g, v);
           tmem_ld16(taddr + 48 * g + 16, v + 16);
           tmem_ld16(taddr + 48 * g + 32, v + 32);
-          if (!(ok = mbar_wait_warp(act_full(g), (uint32_t)(j & 1), abort_flag, a.err, a.wait_cycles))) {
+          if (!(ok = mbar_wait_warp(act_full(g), (uint32_t)((j * T::ACT_CHUNKS + g) / T::ACT_RING & 1), abort_flag,
+                                    a.err, a.wait_cycles))) {
             tmem_wait_ld();
             break;
           }
@@ -584,8 +580,24 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
       for (int ch = half; MODE != LY_BWD && ch < T::N / 16; ch += 2) {
         float v[16];
         tmem_ld16(taddr + 16 * ch, v);
-        __nv_bfloat16 nh[16], nl[16];
-        if (MODE == LY_BW0 && ch + 2 < T::N / 16) chunk_load(a.ah, a.al, node0 + 16 * (ch + 2), a.n_nodes, a.hs, ic, nh, nl);
+        if (MODE == LY_BW0) {
+          // the chunk's activations from the ring (chunk ch of the tile)
+          const long long n = j * T::ACT_CHUNKS + ch;
+          const int b = (int)(n % T::ACT_RING);
+          if (!mbar_wait_warp(act_full(b), (uint32_t)((n / T::ACT_RING) & 1), abort_flag, a.err, a.wait_cycles)) {
+            tmem_wait_ld();
+            break;
+          }
+          const __nv_bfloat16* sa = reinterpret_cast<const __nv_bfloat16*>(sm + NS * STAGE + (uint32_t)b * LY_ACT_BYTES);
+          const int col = q * 32 + lane;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            qh[k] = sa[k * 128 + col];
+            ql[k] = sa[16 * 128 + k * 128 + col];
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(act_empty(b));
+        }
         tmem_wait_ld();
         if (T::ACT) {
           float av[16];
@@ -621,8 +633,7 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
             }
           }
         } else if (MODE == LY_BW0) {
-          // D_{L-2}[node * 3 + r][i] = acc * d_{L-2}[node][i], the chunk's
-          // activations loaded one chunk ahead
+          // D_{L-2}[node * 3 + r][i] = acc * d_{L-2}[node][i]
           float dv[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
@@ -650,13 +661,6 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
                 a.yh[o] = h;
                 a.yl[o] = l;
               }
-            }
-          }
-          if (ch + 2 < T::N / 16) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              qh[k] = nh[k];
-              ql[k] = nl[k];
             }
           }
         } else {
@@ -1247,8 +1251,11 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     LyMaps m;
     memcpy(&m.bh, s->mdd[0], sizeof(CUtensorMap));
     memcpy(&m.bl, s->mdd[1], sizeof(CUtensorMap));
+    memcpy(&m.sh, s->mact[0], sizeof(CUtensorMap));
+    memcpy(&m.sl, s->mact[1], sizeof(CUtensorMap));
+    a.act_row0 = (L - 3) * s->npad;
     mark(4);
-    lay_kernel<LY_BW0><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_BW0>(), st>>>(
+    lay_kernel<LY_BW0><<<grid_of((long long)gf * a.mts), Ly<LY_BW0>::THREADS, ly_smem<LY_BW0>(), st>>>(
         *reinterpret_cast<const CUtensorMap*>(s->mmap), m, a);
   }
   // the other backward hidden layers: D_l = d_l (.) (W_l' D_{l+1}), l = L - 3 .. 1
