@@ -73,10 +73,11 @@ struct Ly {
   // way, 16-node chunks through a ring of four.
   static constexpr bool STAGE_ACT = (MODE == LY_BWD || MODE == LY_BW0) && !F8;
   static constexpr int STAGES = LY_STAGES;
-  // epilogue warps: 4 per TMEM lane quarter in the split-BF16 forward and
-  // input GEMMs (their epilogue, tanh and stores with no loads, bounds them:
-  // forward GEMM 0.184 -> 0.174 ms with 16 instead of 8), else 2
-  static constexpr int EPI = ((MODE == LY_FWD || MODE == LY_IN) && !F8) ? 16 : LY_EPI_WARPS;
+  // epilogue warps: 4 per TMEM lane quarter in the forward and input GEMMs
+  // (their epilogue, tanh and stores with no loads, bounds them: split-BF16
+  // forward GEMM 0.184 -> 0.174 ms, input 0.157 -> 0.111, FP8 forward 0.195
+  // -> 0.165 with 16 instead of 8), else 2
+  static constexpr int EPI = (MODE == LY_FWD || MODE == LY_IN) ? 16 : LY_EPI_WARPS;
   static constexpr int THREADS = 64 + 32 * EPI + (STAGE_ACT ? 32 : 0);
   static constexpr int ACT_RING = MODE == LY_BW0 ? 4 : LY_NBN / 16;   // ring buffers
   static constexpr int ACT_CHUNKS = NODES / 16;                      // 16-node chunks per tile
@@ -1203,7 +1204,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
       a.y8m = s->act8[1] + (size_t)(g + 1) * dstride8;
       a.y8l = s->act8[2] + (size_t)(g + 1) * dstride8;
       if (g < nh - 2) a.yh = a.yl = nullptr;
-      lay_kernel<LY_FWD, true><<<grid_of((long long)gf * a.mts), LY_THREADS, ly_smem<LY_FWD, true>(), st>>>(
+      lay_kernel<LY_FWD, true><<<grid_of((long long)gf * a.mts), Ly<LY_FWD, true>::THREADS, ly_smem<LY_FWD, true>(), st>>>(
           *reinterpret_cast<const CUtensorMap*>(s->q8map), maps8(s->a8map), a);
     } else {
       lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), Ly<LY_FWD>::THREADS, ly_smem<LY_FWD>(), st>>>(
