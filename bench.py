@@ -158,7 +158,7 @@ def launches_per_step(ctl, tile_mode=None):
     # network: one fused launch, the layered reverse mode 2 L (inputs, input
     # GEMM, forward GEMMs, output, backward GEMMs, Jacobian), the FP32 path L
     # (input, hidden GEMMs, output)
-    mlp = 0 if not L else (L if ctl.precision == "fp32" else 2 * L if tile_mode == 6 else 1)
+    mlp = 0 if not L else (L if ctl.precision == "fp32" else 2 * L if tile_mode in (6, 7) else 1)
     return mlp + 1 + 1 + 3  # network, RK4, Riccati, plant + record + advance
 
 
@@ -754,6 +754,12 @@ LAY_KERNELS = {"input GEMM": "lay_kernel<4>", "forward GEMM": "lay_kernel<0>", "
                "inputs": "lay_z_kernel"}
 
 
+def lay_kernel_name(kind, mode):
+    """Kernel of one kind of layered launch (tile mode 7: the hidden backward
+    GEMMs on CTA pairs)."""
+    return "lay_bwd2_kernel (CTA pairs)" if mode == 7 and kind == "backward GEMM" else LAY_KERNELS[kind]
+
+
 def lay_flops(kind, widths, nn):
     """Algorithmic FLOPs of all launches of one kind in a layered pass."""
     w, L = widths, len(widths) - 1
@@ -802,7 +808,7 @@ def lay_bytes(kind, widths, nn):
 A1_METHOD_BYTES_PER_NODE = (17 + 3 + 51) * 4
 
 
-def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, peak_src):
+def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, peak_src, mode=6):
     """Roofline of the dominant kernel of the layered pass, tensor-bound: every
     launch of one pass timed with CUDA events on the context's stream, the
     kind with the largest total time; its reverse-mode algorithmic FLOPs per
@@ -841,16 +847,16 @@ def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, pea
     pass_view = {k: pass_roof[k] for k in ("achieved", "unit", "frac", "ms_per_launch",
                                            "algorithmic_flops_per_launch", "peak", "peak_kind")}
     pass_view["kernel"] = pass_roof["kernel"]
-    pass_view["dram_bytes"] = profiled_pass_traffic()
+    pass_view["dram_bytes"] = profiled_pass_traffic(mode)
     pass_view["design_bytes"] = sum(lay_bytes(k, widths, nn) for k in tot)
     pass_view["method_bytes"] = A1_METHOD_BYTES_PER_NODE * nn
     tflops = fl / (ms * 1e-3) / 1e12
-    traffic = profiled_layer_traffic(dom)
+    traffic = profiled_layer_traffic(dom, mode)
     return {"bound": "tensor", "peak": bf16_burst, "peak_kind": f"bf16 burst ({peak_src})", "unit": "TFLOP/s",
             "achieved": tflops, "frac": tflops / bf16_burst, "traffic": traffic,
             "algorithmic_flops_per_launch": fl, "flop_count": "reverse mode (3 adjoint rows per node)",
             "ms_per_launch": ms, "launches_per_pass": c,
-            "kernel": f"{LAY_KERNELS[dom]}: {dom} of the layered reverse mode ({c} per pass, "
+            "kernel": f"{lay_kernel_name(dom, mode)}: {dom} of the layered reverse mode ({c} per pass, "
                       f"{100 * t / sum(v[1] for v in tot.values()):.0f}% of the pass)",
             "split_operands": "BF16 hi + lo activations/adjoints: 2 MMAs per product, frac <= 0.5",
             "hbm_view": {"design_bytes_per_launch": by, "achieved_gbs": by / (ms * 1e-3) / 1e9,
@@ -865,15 +871,22 @@ def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, pea
             "clocks": ck.summary()}
 
 
-def profiled_layer_traffic(kind):
+def _profile_current(text, mode):
+    """The committed layered summary was captured on the current kernel
+    sources and the same tile mode."""
+    m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
+    files = tuple(f.strip() for f in m.group(2).split("+"))
+    t = re.search(r"tile shape: npc=\d+ mode=(\d+)", text)
+    return m.group(1) == kernel_md5(files) and t is not None and int(t.group(1)) == mode
+
+
+def profiled_layer_traffic(kind, mode=6):
     """DRAM bytes per launch of one kind of layered launch from the committed
     summary (measured on a smaller case and scaled by nodes), or None when the
-    kernel sources changed since."""
+    kernel sources or the tile mode differ from the capture's."""
     try:
         text = open(os.path.join(ROOT, "profiles", LAYERED_PROFILE)).read()
-        m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
-        files = tuple(f.strip() for f in m.group(2).split("+"))
-        if m.group(1) != kernel_md5(files):
+        if not _profile_current(text, mode):
             return None
         key = {"backward GEMM": "bwd", "first backward GEMM": "bw0", "forward GEMM": "fwd"}.get(kind)
         r = re.search(r"dram_bytes_per_launch_%s: (\d+)" % key, text) if key else None
@@ -882,13 +895,11 @@ def profiled_layer_traffic(kind):
         return None
 
 
-def profiled_pass_traffic():
+def profiled_pass_traffic(mode=6):
     """DRAM bytes of a whole layered pass from its committed summary."""
     try:
         text = open(os.path.join(ROOT, "profiles", LAYERED_PROFILE)).read()
-        m = re.search(r"kernel sources md5 at capture: (\w+)\s+\(([^)]*)\)", text)
-        files = tuple(f.strip() for f in m.group(2).split("+"))
-        if m.group(1) != kernel_md5(files):
+        if not _profile_current(text, mode):
             return None
         return int(re.search(r"dram_bytes_per_pass: (\d+)", text).group(1))
     except (OSError, AttributeError):
@@ -1123,7 +1134,7 @@ def main():
     ms_lin = time_calls(lambda: ctl.linearize(x, u, out), max(5, args.steps))
     ms_mlp = time_calls(lambda: ctl.mlp_eval(x, u, out[0], out[1]), max(5, args.steps))
     mode = cfg.get("tile", {}).get("operand_mode")
-    rev = mode in (4, 5, 6)  # reverse mode (one CTA / CTA pairs / layered)
+    rev = mode in (4, 5, 6, 7)  # reverse mode (one CTA / CTA pairs / layered)
     flops = (rev_flops_per_node(widths) if rev else fwd_flops_per_node(widths)) * nn
     if prec == "fp32":
         # FP32-accurate path: TF32 tensor cores with hi + lo split operands
@@ -1137,14 +1148,15 @@ def main():
                  "kernel": ("network pass of the layered reverse mode (a1): inputs split, one tensor-core GEMM per "
                             "layer forward (input layer included), output layer, one GEMM per backward layer "
                             "(the first with the last-layer adjoints folded in), the W_0' Jacobian GEMM "
-                            "(12 launches at 5 hidden layers)" if mode == 6 else
+                            "(12 launches at 5 hidden layers)" + ("; the hidden backward GEMMs on CTA pairs"
+                                                                   if mode == 7 else "") if mode in (6, 7) else
                             "network value + reverse-mode Jacobian (a1, three adjoint rows)" if rev
                             else "network value + forward-mode Jacobian (a1)"),
                  "forward_mode_equivalent_tflops": fwd_flops_per_node(widths) * nn / (ms_mlp * 1e-3) / 1e12,
                  "traffic": None})
     roof["frac"] = roof["achieved"] / roof["peak"]
-    if mode == 6:
-        roof = layered_roofline(ctl, x, u, out, widths, nn, roof, hbm, bf16_burst, peak_src)
+    if mode in (6, 7):
+        roof = layered_roofline(ctl, x, u, out, widths, nn, roof, hbm, bf16_burst, peak_src, mode)
 
     ms_e2e, bi, bo = e2e_rti(ctl, prob, max(5, args.steps))
     smp = error_sample(prob, prec) if rank == 0 and world == 1 and not args.no_cpu else None

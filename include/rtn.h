@@ -314,12 +314,13 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
 
 /* Tile shapes of the tensor-core network kernel (the autotuner's search
  * space).  rtn_tc_variants: number of compiled shapes.  rtn_tc_variant_info:
- * nodes per CTA (per CTA pair in mode 5; 0 in mode 6), operand mode
+ * nodes per CTA (per CTA pair in mode 5; 0 in modes 6, 7), operand mode
  * in *split (0 single BF16; 1, 2 split hi + lo on one CTA; 3 is not used;
  * 4 split, reverse mode: values forward, three output
  * adjoints backward; 5 the same on CTA pairs; 6 split, reverse mode layered:
  * one GEMM per layer over all nodes, 2 L launches, its buffers allocated
- * when the shape is first selected) and pipeline depth of shape idx,
+ * when the shape is first selected; 7 as 6 with the hidden backward GEMMs
+ * on CTA pairs, hidden width a multiple of 256) and pipeline depth of shape idx,
  * *fits = 1 if it can run this context's network and precision.  rtn_tc_select: use shape idx
  * (RTN_E_UNSUPPORTED if it does not fit).  rtn_autotune: time every fitting
  * shape on the context's current iterate (synchronous; 1 warm-up + 3 timed
@@ -358,7 +359,7 @@ rtn_status rtn_autotune(rtn_ctx* ctx, int* best_idx, float* best_ms);
 rtn_status rtn_tc_trace(rtn_ctx* ctx, int enable);
 rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n);
 
-/* Per-launch times of the layered reverse mode (tile mode 6; profiling aid).
+/* Per-launch times of the layered reverse mode (tile modes 6, 7; profiling aid).
  * enable != 0: record a CUDA event around every launch of the following
  * network passes (not inside a captured graph).  enable == 0: wait for the
  * last recorded pass, write the duration [ms] of each of its launches to
@@ -366,7 +367,7 @@ rtn_status rtn_tc_trace_read(rtn_ctx* ctx, unsigned long long* host, int n);
  * split, 1 input-layer GEMM, 2 forward GEMM, 3 output layer, 4 first
  * backward GEMM, 5 backward GEMM, 6 Jacobian GEMM), the number of launches
  * to *count, and stop recording.  Synchronous.  RTN_E_UNSUPPORTED unless the
- * context's selected tile shape is mode 6. */
+ * context's selected tile shape is mode 6 or 7. */
 rtn_status rtn_tc_launch_times(rtn_ctx* ctx, int enable, float* ms, int* kind, int cap, int* count);
 
 /* Synchronous: the first device-side failure recorded since the last call
@@ -376,7 +377,7 @@ rtn_status rtn_tc_launch_times(rtn_ctx* ctx, int enable, float* ms, int* kind, i
 rtn_status rtn_device_error(rtn_ctx* ctx, int* code);
 
 /* Budget of the bounded waits inside the layered tensor-core network kernels
- * (tile mode 6; a fault-injection aid for failure-detection tests).  Every
+ * (tile modes 6, 7; a fault-injection aid for failure-detection tests).  Every
  * mbarrier wait of those kernels gives up after `cycles` SM clock cycles
  * (0 restores the default, 4e9 cycles, about 2 s at 2 GHz): the CTA records
  * RTN_E_TIMEOUT (read and cleared by rtn_device_error), lets the copies and
@@ -389,7 +390,7 @@ rtn_status rtn_set_wait_budget(rtn_ctx* ctx, long long cycles);
 
 /* Fault injection for failure-detection tests (no GPU fault involved):
  * enable != 0 makes the TMA producer of every later layered network kernel
- * (tile mode 6) first wait on a barrier that nothing completes, before it
+ * (tile modes 6, 7) first wait on a barrier that nothing completes, before it
  * issues any copy; the wait runs out after the budget of
  * rtn_set_wait_budget, the pass returns with RTN_E_TIMEOUT recorded
  * (rtn_device_error) and nothing in flight, and its outputs are undefined.

@@ -255,7 +255,7 @@ class Controller:
         return code.value
 
     def tc_variants(self):
-        """[(index, nodes per CTA (per CTA pair in mode 5), operand mode 0|1|2|4|5|6, stages)]
+        """[(index, nodes per CTA (per CTA pair in mode 5), operand mode 0|1|2|4|5|6|7, stages)]
         of the tile shapes that fit."""
         L = load()
         n = C.c_int()

@@ -752,7 +752,8 @@ rtn_status rtn_tc_launch_times(rtn_ctx* ctx, int enable, float* ms, int* kind, i
   {
     int mode = 0;
     mlp_tc_variant_info(ctx, ctx->net.tc.variant, nullptr, &mode, nullptr);
-    if (mode != 6) return fail(ctx, RTN_E_UNSUPPORTED, "rtn_tc_launch_times: the layered reverse mode is not selected");
+    if (mode != 6 && mode != 7)
+      return fail(ctx, RTN_E_UNSUPPORTED, "rtn_tc_launch_times: the layered reverse mode is not selected");
   }
   if (enable) {
     CK(mlp_lay_timing(ctx, true));

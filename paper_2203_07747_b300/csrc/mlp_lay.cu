@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "tc_common.cuh"
+#include "tc_pair.cuh"
 
 namespace rtn {
 namespace {
@@ -67,11 +68,17 @@ struct Ly {
   static constexpr int KB = F8 ? 64 : LY_KB;                        // K elements per stage
   // split-BF16 backward: the tile's activations a_l (hi, lo) reach the
   // epilogue through shared memory, one 16-node group per buffer of a ring of
-  // LY_NBN / 16 loaded by TMA from an eleventh warp (global loads of 2 B per
-  // lane were the epilogue's largest cost)
+  // three loaded by TMA from an eleventh warp (global loads of 2 B per lane
+  // were the epilogue's largest cost)
   // The first backward GEMM (its d_{L-2} from a_{L-2}) reads them the same
   // way, 16-node chunks through a ring of four.
   static constexpr bool STAGE_ACT = (MODE == LY_BWD || MODE == LY_BW0) && !F8;
+  // split-BF16 backward: the adjoints D_l leave through shared memory, each
+  // half of the epilogue staging its 24 rows (8 nodes x 3) x 128 neurons of a
+  // group (hi, lo; two buffers per half) for TMA tensor stores (2-byte stores
+  // per lane competed with the operand loads: 0.51 vs 0.40 ms per launch
+  // without them)
+  static constexpr bool STAGE_OUT = MODE == LY_BWD && !F8;
   static constexpr int STAGES = LY_STAGES;
   // epilogue warps: 4 per TMEM lane quarter in the forward and input GEMMs
   // (their epilogue, tanh and stores with no loads, bounds them: split-BF16
@@ -79,12 +86,14 @@ struct Ly {
   // -> 0.165 with 16 instead of 8), else 2
   static constexpr int EPI = (MODE == LY_FWD || MODE == LY_IN) ? 16 : LY_EPI_WARPS;
   static constexpr int THREADS = 64 + 32 * EPI + (STAGE_ACT ? 32 : 0);
-  static constexpr int ACT_RING = MODE == LY_BW0 ? 4 : LY_NBN / 16;   // ring buffers
+  static constexpr int ACT_RING = MODE == LY_BW0 ? 4 : 3;             // ring buffers
   static constexpr int ACT_CHUNKS = NODES / 16;                      // 16-node chunks per tile
   static constexpr int ACT_READERS = MODE == LY_BW0 ? LY_EPI_WARPS / 2 : LY_EPI_WARPS;  // warps reading a chunk
 };
 // one ring buffer: the activations of 16 nodes x 128 neurons, hi then lo
 constexpr uint32_t LY_ACT_BYTES = 2u * 16u * 128u * 2u;
+// one output staging buffer: 24 adjoint rows x 128 neurons, hi then lo
+constexpr uint32_t LY_OUT_BYTES = 2u * 24u * 128u * 2u;
 template <int MODE, bool F8 = false>
 __host__ __device__ constexpr uint32_t ly_b_bytes() { return (uint32_t)Ly<MODE>::N * 64u; }
 template <int MODE, bool F8 = false>
@@ -94,19 +103,22 @@ __host__ __device__ constexpr uint32_t ly_stage() {
 template <int MODE, bool F8 = false>
 __host__ __device__ constexpr size_t ly_smem() {
   return Ly<MODE, F8>::STAGES * ly_stage<MODE, F8>() +
-         (Ly<MODE, F8>::STAGE_ACT ? Ly<MODE, F8>::ACT_RING * LY_ACT_BYTES : 0) + 1024 + 256;
+         (Ly<MODE, F8>::STAGE_ACT ? Ly<MODE, F8>::ACT_RING * LY_ACT_BYTES : 0) +
+         (Ly<MODE, F8>::STAGE_OUT ? 4 * LY_OUT_BYTES : 0) + 1024 + 256;
 }
 static_assert(ly_b_bytes<LY_FWD>() % 1024 == 0 && ly_b_bytes<LY_BWD>() % 1024 == 0, "1 KB aligned tiles");
 static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448 && ly_smem<LY_BW0>() <= 232448 &&
                   ly_smem<LY_FWD, true>() <= 232448 && ly_smem<LY_BWD, true>() <= 232448 &&
                   ly_smem<LY_BWD>() <= 232448,
               "shared memory");
-static_assert(ly_stage<LY_BWD>() % 1024 == 0 && ly_stage<LY_BW0>() % 1024 == 0 && LY_ACT_BYTES % 1024 == 0,
-              "1 KB aligned activation buffers");
+static_assert(ly_stage<LY_BWD>() % 1024 == 0 && ly_stage<LY_BW0>() % 1024 == 0 && LY_ACT_BYTES % 1024 == 0 &&
+                  LY_OUT_BYTES % 1024 == 0,
+              "1 KB aligned activation and output buffers");
 
 struct LyMaps {
   CUtensorMap bh, bl, b3;  // activations / adjoints hi, lo (F8: hi, mid, lo)
   CUtensorMap sh, sl;      // split-BF16 backward: the activations a_l hi, lo, box 128 x 16
+  CUtensorMap oh, ol;      // split-BF16 backward: its output D_l hi, lo, box 128 x 24 (stores)
 };
 
 struct LyArgs {
@@ -214,33 +226,105 @@ __device__ __forceinline__ void bwd_load_s(const __nv_bfloat16* __restrict__ sh,
 }
 
 // backward epilogue of one 16-node group (48 accumulator columns, node k
-// in columns 3k .. 3k + 2): the warp of half H stores nodes 8H .. 8H + 7,
-// D = acc * d with d = 1 - a^2 computed once per node from the loaded pairs
+// in columns 3k .. 3k + 2): the warp of half H computes nodes 8H .. 8H + 7,
+// D = acc * d with d = 1 - a^2 computed once per node from the loaded pairs,
+// into the half's staging buffer [24 rows (node, r)][128 neurons] hi, then
+// lo, column col.  Rows of nodes past the end and columns past the layer's
+// width are written as zeros (the values the buffer's padding holds).
 template <int H>
-__device__ __forceinline__ void bwd_group(const float (&v)[48], const __nv_bfloat16 (&ph)[8],
-                                          const __nv_bfloat16 (&pl)[8], int node_g, int n_nodes, int hs, int i,
-                                          bool active, __nv_bfloat16* __restrict__ yh,
-                                          __nv_bfloat16* __restrict__ yl) {
+__device__ __forceinline__ void bwd_group_s(const float (&v)[48], const __nv_bfloat16 (&ph)[8],
+                                            const __nv_bfloat16 (&pl)[8], int node_g, int n_nodes, bool active,
+                                            __nv_bfloat16* __restrict__ so, int col) {
   float dv[8];
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
     const float av = __bfloat162float(ph[kk]) + __bfloat162float(pl[kk]);
-    dv[kk] = 1.0f - av * av;
+    dv[kk] = (active && node_g + 8 * H + kk < n_nodes) ? 1.0f - av * av : 0.0f;
   }
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
-    const int k = 8 * H + kk, node = node_g + k;
-    if (active && node < n_nodes) {
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const size_t o = ((size_t)node * 3 + r) * hs + i;
-        __nv_bfloat16 h, l;
-        split_bf(v[3 * k + r] * dv[kk], h, l);
-        yh[o] = h;
-        yl[o] = l;
-      }
+    for (int r = 0; r < 3; ++r) {
+      __nv_bfloat16 h, l;
+      split_bf(v[3 * (8 * H + kk) + r] * dv[kk], h, l);
+      so[(3 * kk + r) * 128 + col] = h;
+      so[24 * 128 + (3 * kk + r) * 128 + col] = l;
     }
   }
+}
+
+// split-BF16 backward epilogue of one tile (LY_NBN nodes x 3 adjoints) for
+// one warp: TMEM lane quarter q (32 neurons of M tile mcol), half `half` of
+// each 16-node group.  Group g's activations come from ring buffer n % RING
+// (n = j * groups + g, j the CTA's tile count; filled by the activation warp,
+// both warps of the quarter read the group's 48 columns); the warp computes
+// D = acc * (1 - a^2) of its 8 nodes into its half's staging buffer n & 1;
+// the half's warp of quarter 2 stores the buffer (24 rows x 128 neurons, hi
+// and lo) with two TMA stores once the half's four warps have written it,
+// and releases it when the stores have read it.  Barriers 8 B apart:
+// act_full / act_empty [RING], out_full / out_empty [half][buffer].
+// Returns false when a wait ran out.
+template <int RING>
+__device__ __forceinline__ bool bwd_tile_epilogue(uint32_t taddr, long long j, int node0, int mcol, bool active,
+                                                  int n_nodes, int half, int q, int lane, const uint8_t* ring,
+                                                  uint8_t* outp, uint32_t out_s, uint32_t act_full0,
+                                                  uint32_t act_empty0, uint32_t out_full0, uint32_t out_empty0,
+                                                  const CUtensorMap* oh, const CUtensorMap* ol,
+                                                  volatile int* abort_flag, int* err, long long budget) {
+  constexpr int GROUPS = LY_NBN / 16;
+  const int col = q * 32 + lane;
+#pragma unroll 1
+  for (int g = 0; g < GROUPS; ++g) {
+    float v[48];
+    tmem_ld16(taddr + 48 * g, v);
+    tmem_ld16(taddr + 48 * g + 16, v + 16);
+    tmem_ld16(taddr + 48 * g + 32, v + 32);
+    const long long n = j * GROUPS + g;
+    const int b = (int)(n % RING);
+    if (!mbar_wait_warp(act_full0 + 8u * b, (uint32_t)((n / RING) & 1), abort_flag, err, budget)) {
+      tmem_wait_ld();
+      return false;
+    }
+    const __nv_bfloat16* sa = reinterpret_cast<const __nv_bfloat16*>(ring + (size_t)b * LY_ACT_BYTES);
+    __nv_bfloat16 ph[8], pl[8];
+    if (half == 0)
+      bwd_load_s<0>(sa, col, ph, pl);
+    else
+      bwd_load_s<1>(sa, col, ph, pl);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(act_empty0 + 8u * b);
+    // staging buffer ob, use u = n >> 1: free once its stores of use u - 1 have read it
+    const int ob = (int)(n & 1), slot = 2 * half + ob;
+    const uint32_t u = (uint32_t)((n >> 1) & 1);
+    if (!mbar_wait_warp(out_empty0 + 8u * slot, u ^ 1u, abort_flag, err, budget)) {
+      tmem_wait_ld();
+      return false;
+    }
+    const uint32_t so = out_s + (uint32_t)slot * LY_OUT_BYTES;
+    __nv_bfloat16* sop = reinterpret_cast<__nv_bfloat16*>(outp + (size_t)slot * LY_OUT_BYTES);
+    tmem_wait_ld();
+    if (half == 0)
+      bwd_group_s<0>(v, ph, pl, node0 + 16 * g, n_nodes, active, sop, col);
+    else
+      bwd_group_s<1>(v, ph, pl, node0 + 16 * g, n_nodes, active, sop, col);
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(out_full0 + 8u * slot);
+    if (q == 2) {
+      if (!mbar_wait_warp(out_full0 + 8u * slot, u, abort_flag, err, budget)) return false;
+      if (lane == 0) {
+        const int row = (node0 + 16 * g + 8 * half) * 3;
+        tma_store_2d(oh, so, mcol * 128, row);
+        tma_store_2d(ol, so + LY_OUT_BYTES / 2, mcol * 128, row);
+        bulk_commit();
+        // the previous group's stores (the other buffer) have read it
+        bulk_wait_read<1>();
+        if (n >= 1) mbar_arrive(out_empty0 + 8u * (slot ^ 1));
+      }
+      __syncwarp();
+    }
+  }
+  return true;
 }
 
 // F8 backward: a_l (= pieces / 448) of the 8 nodes the warp of half H
@@ -326,8 +410,11 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   uint8_t* sm = smem_raw + pad;
   const uint32_t st0 = sraw + pad;
   const uint32_t act_s = st0 + NS * STAGE;  // activation buffers (STAGE_ACT)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + (T::STAGE_ACT ? T::ACT_RING * LY_ACT_BYTES : 0));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * T::ACT_RING);
+  const uint32_t act_bytes = T::STAGE_ACT ? T::ACT_RING * LY_ACT_BYTES : 0;
+  const uint32_t out_s = act_s + act_bytes;  // output staging (STAGE_OUT): [half][buffer]
+  constexpr int OUT_BARS = T::STAGE_OUT ? 8 : 0;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + act_bytes + (T::STAGE_OUT ? 4 * LY_OUT_BYTES : 0));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * T::ACT_RING + OUT_BARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
@@ -338,6 +425,10 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   const uint32_t stall_bar = bar(2 * NS + 5);  // fault injection: nothing completes it
   auto act_full = [&](int b) { return bar(2 * NS + 6 + b); };
   auto act_empty = [&](int b) { return bar(2 * NS + 6 + T::ACT_RING + b); };
+  // staging buffer (half h, buffer b) written by the half's four warps /
+  // read out by its TMA stores
+  auto out_full = [&](int h, int b) { return bar(2 * NS + 6 + 2 * T::ACT_RING + 2 * h + b); };
+  auto out_empty = [&](int h, int b) { return bar(2 * NS + 6 + 2 * T::ACT_RING + 4 + 2 * h + b); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_tiles = (long long)a.n_groups * a.mts;
@@ -354,6 +445,10 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
     for (int c = 0; c < T::ACT_RING; ++c) {
       mbar_init(act_full(c), 1);
       mbar_init(act_empty(c), T::ACT_READERS);
+    }
+    for (int c = 0; T::STAGE_OUT && c < 4; ++c) {
+      mbar_init(out_full(c >> 1, c & 1), 4);
+      mbar_init(out_empty(c >> 1, c & 1), 1);
     }
     mbar_init(mma_done, 1);
     mbar_init(stall_bar, 1);
@@ -549,38 +644,11 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
         }
       }
       if (MODE == LY_BWD && !F8) {
-        // the tile's activations from shared memory (loaded by the
-        // activation warp, group g in ring buffer g), 16-node groups: both
-        // warps of the quarter read the group's 48 columns, each stores its
-        // 8 nodes
-        const int col = q * 32 + lane;
-        bool ok = true;
-#pragma unroll 1
-        for (int g = 0; g < T::NODES / 16; ++g) {
-          float v[48];
-          tmem_ld16(taddr + 48 * g, v);
-          tmem_ld16(taddr + 48 * g + 16, v + 16);
-          tmem_ld16(taddr + 48 * g + 32, v + 32);
-          if (!(ok = mbar_wait_warp(act_full(g), (uint32_t)((j * T::ACT_CHUNKS + g) / T::ACT_RING & 1), abort_flag,
-                                    a.err, a.wait_cycles))) {
-            tmem_wait_ld();
-            break;
-          }
-          const __nv_bfloat16* sa = reinterpret_cast<const __nv_bfloat16*>(sm + NS * STAGE + (uint32_t)g * LY_ACT_BYTES);
-          __nv_bfloat16 ph[8], pl[8];
-          if (half == 0)
-            bwd_load_s<0>(sa, col, ph, pl);
-          else
-            bwd_load_s<1>(sa, col, ph, pl);
-          __syncwarp();
-          if (lane == 0) mbar_arrive(act_empty(g));
-          tmem_wait_ld();
-          if (half == 0)
-            bwd_group<0>(v, ph, pl, node0 + 16 * g, a.n_nodes, a.hs, i, active, a.yh, a.yl);
-          else
-            bwd_group<1>(v, ph, pl, node0 + 16 * g, a.n_nodes, a.hs, i, active, a.yh, a.yl);
-        }
-        if (!ok) break;
+        if (!bwd_tile_epilogue<T::ACT_RING>(taddr, j, node0, mt, active, a.n_nodes, half, q, lane,
+                                            sm + NS * STAGE, sm + (out_s - st0), out_s, act_full(0), act_empty(0),
+                                            out_full(0, 0), out_empty(0, 0), &bm.oh, &bm.ol, abort_flag, a.err,
+                                            a.wait_cycles))
+          break;
       }
       for (int ch = half; MODE != LY_BWD && ch < T::N / 16; ch += T::EPI / 4) {
         float v[16];
@@ -681,6 +749,8 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
       if (lane == 0) mbar_arrive(tmem_free(acc));
       if (++acc == 2) { acc = 0; aph ^= 1u; }
     }
+    // the staged stores have completed before the CTA's shared memory goes
+    if (T::STAGE_OUT && lane == 0 && (warp & 3) == 2) bulk_wait_all();
   }
 
   __syncthreads();
@@ -691,6 +761,274 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- CTA pairs
+// The split-BF16 backward GEMM on CTA pairs (cta_group::2): one pair tile is
+// M = 256 neurons (128 per CTA, its own weight rows) x N = 240 (80 nodes x 3
+// adjoints; each CTA loads 120 adjoint rows of B, which the MMA reads across
+// the pair) x K.  Each CTA's tensor memory holds its 128 rows x 240 columns,
+// so the epilogue is the single-CTA one (activation ring, staged TMA
+// stores).  Every adjoint row of a node group is read by two pair tiles
+// instead of four M tiles: per SM 23 KB instead of 38 KB per K block, the
+// traffic through L2 that bounds the single-CTA kernel.  Rank 0 issues the
+// MMAs; both CTAs' TMA loads complete on rank 0's stage barriers and both
+// release their stages on the MMAs' multicast commits; both CTAs' epilogues
+// free an accumulator on rank 0's barrier.
+constexpr int LB2_STAGES = 6;
+constexpr int LB2_RING = 3;
+constexpr uint32_t LB2_B_BYTES = (uint32_t)(3 * LY_NBN / 2) * 64u;  // 120 rows x 64 B
+constexpr uint32_t LB2_LOAD = LY_A_BYTES + 2u * LB2_B_BYTES;          // bytes one CTA loads per stage
+constexpr uint32_t LB2_STAGE = (LB2_LOAD + 1023u) / 1024u * 1024u;    // 1 KB aligned stages
+constexpr int LB2_THREADS = 64 + 32 * LY_EPI_WARPS + 32;              // TMA, MMA, epilogue, activation loader
+constexpr size_t lb2_smem() {
+  return LB2_STAGES * LB2_STAGE + LB2_RING * LY_ACT_BYTES + 4 * LY_OUT_BYTES + 1024 + 512;  // + alignment, barriers
+}
+static_assert(lb2_smem() <= 232448, "shared memory");
+static_assert(LB2_B_BYTES % 512 == 0, "swizzle atoms");
+
+// bounded wait with cluster-scope acquire (barriers with arrivals from the
+// peer CTA), every lane of a warp, warp-uniform result
+__device__ __forceinline__ bool wait_cl_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                             long long budget) {
+  bool ok = mbar_try_cl(bar, parity);
+  if (!ok) {
+    const long long t0 = clock64();
+    for (;;) {
+      if (mbar_try_cl_sleep(bar, parity, WAIT_SLEEP_NS)) {
+        ok = true;
+        break;
+      }
+      if (*abort_flag) break;
+      if (clock64() - t0 > budget) {
+        *abort_flag = 1;
+        atomicExch(err, (int)RTN_E_TIMEOUT);
+        break;
+      }
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
+    lay_bwd2_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ LyMaps bm, LyArgs a) {
+  using T = Ly<LY_BWD>;
+  constexpr int NS = LB2_STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t sraw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
+  uint8_t* sm = smem_raw + pad;
+  const uint32_t st0 = sraw + pad;
+  const uint32_t ring_s = st0 + NS * LB2_STAGE;
+  const uint32_t out_s = ring_s + LB2_RING * LY_ACT_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (out_s - st0) + 4 * LY_OUT_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * LB2_RING + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto bar = [&](int k) { return smem_u32(bars + k); };
+  auto full_bar = [&](int s) { return bar(s); };
+  auto empty_bar = [&](int s) { return bar(NS + s); };
+  auto acc_full = [&](int c) { return bar(2 * NS + c); };
+  auto tmem_free = [&](int c) { return bar(2 * NS + 2 + c); };
+  const uint32_t mma_done = bar(2 * NS + 4);
+  const uint32_t stall_bar = bar(2 * NS + 5);  // fault injection: nothing completes it
+  auto act_full = [&](int b) { return bar(2 * NS + 6 + b); };
+  auto act_empty = [&](int b) { return bar(2 * NS + 6 + LB2_RING + b); };
+  const uint32_t out_full0 = bar(2 * NS + 6 + 2 * LB2_RING), out_empty0 = bar(2 * NS + 6 + 2 * LB2_RING + 4);
+
+  const uint32_t rank = cluster_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
+  const int mps = a.mts >> 1;  // pair tiles per node group
+  const long long n_tiles = (long long)a.n_groups * mps;
+  const long long budget = a.wait_cycles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int c = 0; c < 2; ++c) {
+      mbar_init(acc_full(c), 1);
+      mbar_init(tmem_free(c), 2 * LY_EPI_WARPS);
+    }
+    mbar_init(mma_done, 1);
+    mbar_init(stall_bar, 1);
+    for (int c = 0; c < LB2_RING; ++c) {
+      mbar_init(act_full(c), 1);
+      mbar_init(act_empty(c), LY_EPI_WARPS);
+    }
+    for (int c = 0; c < 4; ++c) {
+      mbar_init(out_full0 + 8u * c, 4);
+      mbar_init(out_empty0 + 8u * c, 1);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(LY_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // both CTAs must address the same tensor-memory columns
+  if (threadIdx.x == 0 && rank == 1) {
+    uint32_t other;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(other) : "r"(mapa(smem_u32(tmem_slot), 0)) : "memory");
+    if (other != tmem) {
+      atomicExch(a.err, (int)RTN_E_UNSUPPORTED);
+      *abort_flag = 1;
+      asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(mapa(smem_u32((const void*)abort_flag), 0)), "r"(1)
+                   : "memory");
+    }
+  }
+  cluster_sync();
+  const bool run = *abort_flag == 0;
+
+  if (run && warp == 0) {
+    // ---------------- TMA producer (both CTAs): this CTA's 128 weight rows
+    // and its 120 adjoint rows (hi, lo) of every K block, onto rank 0's
+    // stage barrier
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&amap)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bm.bh)) : "memory");
+    }
+    const uint32_t full0 = mapa(full_bar(0), 0);
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    // fault injection: a bounded wait on a barrier that nothing completes, run
+    // out before any copy is issued
+    if (a.stall) ok = mbar_wait_warp(stall_bar, 0, abort_flag, a.err, budget);
+    for (long long t = pair; t < n_tiles && ok; t += n_pairs) {
+      const int grp = (int)(t / mps), mp = (int)(t % mps);
+      const int arow = a.a_row0 + (mp * 2 + (int)rank) * 128;
+      const int brow = a.b_row0 + grp * T::N + (int)rank * (T::N / 2);
+      for (int kb = 0; kb < a.nkb; ++kb) {
+        if (!(ok = wait_cl_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err, budget))) break;
+        if (elect_one()) {
+          const uint32_t sa = st0 + s * LB2_STAGE, fb = full0 + 8u * s;
+          if (rank == 0) mbar_expect_tx(full_bar(s), 2u * LB2_LOAD);
+          tma_load_2d_pair(sa, &amap, kb * LY_KB, arow, fb);
+          tma_load_2d_pair(sa + LY_A_BYTES, &bm.bh, kb * LY_KB, brow, fb);
+          tma_load_2d_pair(sa + LY_A_BYTES + LB2_B_BYTES, &bm.bl, kb * LY_KB, brow, fb);
+        }
+        __syncwarp();
+        if (++s == NS) { s = 0; ph ^= 1u; }
+      }
+    }
+    // tail: every stage released, so no copy or commit lands after exit
+    for (int i = 0; i < NS && ok; ++i) {
+      ok = wait_cl_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err, budget);
+      if (++s == NS) { s = 0; ph ^= 1u; }
+    }
+  } else if (run && warp == 1 && rank == 0) {
+    // ---------------- MMA issuer of the pair: two K steps per 64 B row, the
+    // adjoints' hi and lo halves, M = 256, N = 240
+    constexpr uint32_t idesc = idesc_bf16(256, T::N);
+    int s = 0, acc = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (long long t = pair; t < n_tiles && ok; t += n_pairs) {
+      if (!(ok = wait_cl_warp(tmem_free(acc), aph ^ 1u, abort_flag, a.err, budget))) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * 256u;
+      for (int kb = 0; kb < a.nkb; ++kb) {
+        if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err, budget))) break;
+        tc_fence_after();
+        const uint32_t sa = st0 + s * LB2_STAGE;
+        uint64_t ad[4], bd[4];
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t aw = kmajor_desc(sa + ks * 32u, LY_SBO, LY_SWZ);
+          ad[2 * ks] = aw;
+          ad[2 * ks + 1] = aw;
+          bd[2 * ks] = kmajor_desc(sa + LY_A_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+          bd[2 * ks + 1] = kmajor_desc(sa + LY_A_BYTES + LB2_B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+        }
+        mma2_bf16_x4(d, ad, bd, idesc, kb != 0);
+        commit2(empty_bar(s), 3);
+        if (++s == NS) { s = 0; ph ^= 1u; }
+      }
+      if (!ok) break;
+      commit2(acc_full(acc), 3);
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
+    }
+    commit2(mma_done, 3);
+    const long long t0 = clock64();
+    while (!mbar_try(mma_done, 0) && clock64() - t0 < budget) {
+    }
+  } else if (run && warp == 2 + LY_EPI_WARPS) {
+    // ---------------- activation loader (both CTAs): chunk c of every tile
+    // (16 nodes x this CTA's 128 neurons, hi and lo) into ring buffer
+    // n % LB2_RING once the epilogue has released it
+    if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bm.sh)) : "memory");
+    bool ok = true;
+    uint32_t issued = 0, last_ph = 0;
+    long long n = 0;
+    for (long long t = pair; t < n_tiles && ok; t += n_pairs) {
+      const int grp = (int)(t / mps), mc = (int)(t % mps) * 2 + (int)rank;
+      for (int c = 0; c < T::ACT_CHUNKS; ++c, ++n) {
+        const int b = (int)(n % LB2_RING);
+        const uint32_t ph = (uint32_t)((n / LB2_RING) & 1);
+        if (!(ok = mbar_wait_warp(act_empty(b), ph ^ 1u, abort_flag, a.err, budget))) break;
+        if (elect_one()) {
+          const uint32_t dst = ring_s + (uint32_t)b * LY_ACT_BYTES;
+          const int row = a.act_row0 + grp * T::NODES + 16 * c;
+          mbar_expect_tx(act_full(b), LY_ACT_BYTES);
+          tma_load_2d(dst, &bm.sh, mc * 128, row, act_full(b));
+          tma_load_2d(dst + LY_ACT_BYTES / 2, &bm.sl, mc * 128, row, act_full(b));
+        }
+        __syncwarp();
+        issued |= 1u << b;
+        last_ph = (last_ph & ~(1u << b)) | (ph << b);
+      }
+    }
+    // the ring's last copies have landed before the CTA may exit
+    for (int b = 0; b < LB2_RING; ++b)
+      if (issued & (1u << b)) {
+        const long long t0 = clock64();
+        while (!mbar_try(act_full(b), (last_ph >> b) & 1u) && clock64() - t0 < budget) {
+        }
+      }
+  } else if (run && warp >= 2 && warp < 2 + LY_EPI_WARPS) {
+    // ---------------- epilogue (both CTAs): this CTA's 128 rows, as the
+    // single-CTA backward epilogue
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t tfree0 = mapa(tmem_free(0), 0);
+    int acc = 0;
+    uint32_t aph = 0;
+    long long j = 0;
+    for (long long t = pair; t < n_tiles; t += n_pairs, ++j) {
+      const int grp = (int)(t / mps), mc = (int)(t % mps) * 2 + (int)rank;
+      const int i = mc * 128 + q * 32 + lane;
+      const bool active = i < a.m_rows;
+      if (!wait_cl_warp(acc_full(acc), aph, abort_flag, a.err, budget)) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
+      if (!bwd_tile_epilogue<LB2_RING>(taddr, j, grp * T::NODES, mc, active, a.n_nodes, half, q, lane,
+                                       sm + (ring_s - st0), sm + (out_s - st0), out_s, act_full(0), act_empty(0),
+                                       out_full0, out_empty0, &bm.oh, &bm.ol, abort_flag, a.err, budget))
+        break;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) arrive_cluster(tfree0 + 8u * acc);
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
+    }
+    // the staged stores have completed before the CTA's shared memory goes
+    if (lane == 0 && q == 2) bulk_wait_all();
+  }
+
+  __syncthreads();
+  cluster_sync();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LY_TMEM_COLS)
+                 : "memory");
+  }
+}
 // node inputs z = [x; u] as the K-major B operand of the input-layer GEMM:
 // [node][32] BF16 hi + lo (columns 17..31 stay zero)
 __global__ void __launch_bounds__(256) lay_z_kernel(const float* __restrict__ x, const float* __restrict__ u,
@@ -971,6 +1309,21 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
         err = "cuTensorMapEncodeTiled failed";
         return cudaSuccess;
       }
+      // one CTA's half of a pair tile's adjoint rows (120 of 240)
+      if (!enc(s->mb2[b][p], s->xb[b][p], 3 * npad, 3 * LY_NBN / 2)) {
+        err = "cuTensorMapEncodeTiled failed";
+        return cudaSuccess;
+      }
+      // the backward GEMM's output boxes: 24 rows (8 nodes x 3) x 128 neurons
+      const cuuint64_t dims[2] = {(cuuint64_t)HP, (cuuint64_t)3 * npad};
+      const cuuint64_t str[1] = {(cuuint64_t)HP * 2};
+      const cuuint32_t box[2] = {128, 24};
+      if (encode(reinterpret_cast<CUtensorMap*>(s->mout[b][p]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, s->xb[b][p], dims,
+                 str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        err = "cuTensorMapEncodeTiled failed (adjoint stores)";
+        return cudaSuccess;
+      }
     }
   // the stacked forward weights (W_1 .. W_L) and the reverse-mode stack
   // (transposes, W_0' hi / lo) in this path's 64 B swizzled tiles
@@ -1076,7 +1429,14 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   if ((e = cudaFuncSetAttribute(lay_kernel<LY_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ly_smem<LY_BWD>())) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(lay_bwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lb2_smem())) !=
+      cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(lay_kernel<LY_JD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ly_smem<LY_JD>());
+}
+
+void mlp_lay_set_pair(rtn_ctx* ctx, bool pair) {
+  if (ctx->net.tc.lay) ctx->net.tc.lay->pair_bwd = pair && (ctx->net.tc.h_pad / 128) % 2 == 0;
 }
 
 void mlp_lay_release(rtn_ctx* ctx) {
@@ -1307,8 +1667,20 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
       LyMaps m = maps(s->mb[src][0], s->mb[src][1]);
       memcpy(&m.sh, s->mact[0], sizeof(CUtensorMap));
       memcpy(&m.sl, s->mact[1], sizeof(CUtensorMap));
+      memcpy(&m.oh, s->mout[dst][0], sizeof(CUtensorMap));
+      memcpy(&m.ol, s->mout[dst][1], sizeof(CUtensorMap));
       a.act_row0 = (l - 1) * s->npad;
-      lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), Ly<LY_BWD>::THREADS, ly_smem<LY_BWD>(), st>>>(*rmap, m, a);
+      if (s->pair_bwd && a.mts % 2 == 0) {
+        // pair tiles of 256 neurons: each CTA loads half of the adjoint rows
+        memcpy(&m.bh, s->mb2[src][0], sizeof(CUtensorMap));
+        memcpy(&m.bl, s->mb2[src][1], sizeof(CUtensorMap));
+        const long long pt = (long long)gb * (a.mts / 2);
+        const int pairs = (int)std::min<long long>(pt, std::max(1, tc.n_sm / 2));
+        lay_bwd2_kernel<<<2 * pairs, LB2_THREADS, lb2_smem(), st>>>(*rmap, m, a);
+      } else {
+        lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), Ly<LY_BWD>::THREADS, ly_smem<LY_BWD>(), st>>>(*rmap, m,
+                                                                                                           a);
+      }
     }
   }
   // J_D = W_0' D_1 (W_0' hi and lo rows)

@@ -371,24 +371,27 @@ struct Variant {
              // on CTA pairs, no longer compiled: it won no shape / batch size),
              // 4 split, reverse mode (value forward, three adjoints backward),
              // 5 split, reverse mode on a CTA pair,
-             // 6 split, reverse mode layered (one GEMM per layer over all nodes)
+             // 6 split, reverse mode layered (one GEMM per layer over all nodes),
+             // 7 as 6 with the backward GEMMs on CTA pairs (hidden width a
+             //   multiple of 256)
   int stages;
   const void* fn;
   bool split() const { return mode != 0; }
   bool pair() const { return mode == 5; }
   bool rev() const { return mode == 4 || mode == 5; }
+  bool layered() const { return mode == 6 || mode == 7; }
   int threads() const { return pair() ? THREADS + 32 : THREADS; }
   int cols() const { return rev() ? 128 : 16 * npc + ((2 * npc + 15) / 16) * 16; }
   // tensor-memory columns of one accumulator tile (128 rows; 256 rows on a pair)
   int tmem_per_mtile() const { return mode == 5 ? 256 : rev() ? 128 : (mode >= 2 ? 2 * cols() : cols()); }
-  int rows_per_mtile() const { return pair() ? 256 : 128; }
+  int rows_per_mtile() const { return (pair() || mode == 7) ? 256 : 128; }
   // accumulator columns: one slot per M tile (a pair always has two slots:
   // its output layer accumulates in the second)
   int tmem_columns(int HP) const {
     return (pair() ? std::max(2, HP / 256) : HP / 128) * tmem_per_mtile();
   }
   size_t smem(int HP) const {
-    if (mode == 6) return mlp_lay_smem();
+    if (layered()) return mlp_lay_smem();
     if (mode == 5) return mlp_rev2_smem(HP, stages);
     if (rev())
       return 1024 + (size_t)128 * HP * 2 + (size_t)stages * WT_BYTES + 8 * (2 * stages + 20) + 16 +
@@ -413,7 +416,7 @@ Variant rev2_variant() {
   return Variant{42, 5, STAGES, mlp_rev2_fn(42, STAGES)};
 }
 
-Variant lay_variant() { return Variant{0, 6, 2, mlp_lay_fn()}; }
+Variant lay_variant(int mode) { return Variant{0, mode, 2, mlp_lay_fn()}; }
 
 // every compiled tile shape; the autotuner times those that fit
 const std::vector<Variant>& all_variants() {
@@ -422,7 +425,8 @@ const std::vector<Variant>& all_variants() {
       variant<6, 0, 6>(),  variant<4, 0, 8>(),  variant<8, 1, 4>(),
       variant<5, 1, 6>(),  variant<4, 1, 3>(),  variant<3, 1, 6>(),  variant<7, 2, 5>(),
       variant<7, 2, 8>(),  variant<4, 2, 6>(),  variant<3, 2, 5>(),  rev_variant<21, 6>(),
-      rev_variant<21, 4>(), rev_variant<16, 6>(), rev2_variant<3>(), rev2_variant<6>(), lay_variant()};
+      rev_variant<21, 4>(), rev_variant<16, 6>(), rev2_variant<3>(), rev2_variant<6>(), lay_variant(6),
+      lay_variant(7)};
   return v;
 }
 
@@ -479,11 +483,12 @@ cudaError_t select_variant(rtn_ctx* ctx, int idx) {
   int ncol = 32;
   while (ncol < v.tmem_columns(tc.h_pad)) ncol *= 2;
   tc.tmem_cols = ncol;
-  if (v.mode == 6) {  // buffers and maps of the layered path (once)
+  if (v.layered()) {  // buffers and maps of the layered path (once)
     std::string e;
     cudaError_t ce = mlp_lay_prepare(ctx, e);
     if (ce != cudaSuccess) return ce;
     if (!e.empty()) return cudaErrorNotSupported;
+    mlp_lay_set_pair(ctx, v.mode == 7);
     return cudaSuccess;
   }
   return cudaFuncSetAttribute(tc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc.smem);
@@ -654,7 +659,7 @@ cudaError_t mlp_tc_forward(rtn_ctx* ctx, const float* x, const float* u, float* 
   void* args[] = {(void*)map, (void*)&a};
   const int n_tiles = (a.n_nodes + tc.npc - 1) / tc.npc;
   const Variant& v = all_variants()[tc.variant];
-  if (v.mode == 6) return mlp_lay_launch(ctx, x, u, fD, JD);
+  if (v.layered()) return mlp_lay_launch(ctx, x, u, fD, JD);
   if (v.mode == 5) return mlp_rev2_launch(ctx, x, u, fD, JD);
   if (v.rev()) return mlp_rev_launch(ctx, x, u, fD, JD);
   const dim3 grid(std::min(n_tiles, std::max(1, tc.n_sm)));
@@ -671,7 +676,7 @@ int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages
   if (split) *split = vs[idx].mode;
   if (stages) *stages = vs[idx].stages;
   const bool want = ctx->opt.precision != RTN_BF16;
-  if (ctx->opt.precision == RTN_FP8 && vs[idx].mode != 6) return 1;
+  if (ctx->opt.precision == RTN_FP8 && vs[idx].mode != 6) return 1;  // FP8: single-CTA layered only
   return (vs[idx].split() == want && fits(vs[idx], ctx->net.tc.h_pad)) ? 0 : 1;
 }
 

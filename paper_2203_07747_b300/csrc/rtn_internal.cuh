@@ -68,6 +68,9 @@ struct LayState {
   __nv_bfloat16* xb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   alignas(64) unsigned char ma[2][128];     // activations hi / lo, box 32 x 256
   alignas(64) unsigned char mb[2][2][128];  // adjoints, box 32 x 240
+  alignas(64) unsigned char mout[2][2][128];  // adjoints, box 128 x 24 unswizzled (backward GEMM's stores)
+  alignas(64) unsigned char mb2[2][2][128];   // adjoints, box 32 x 120 (one CTA's half of a pair tile)
+  bool pair_bwd = false;                      // backward GEMMs on CTA pairs (tile mode 7)
   alignas(64) unsigned char mact[2][128];   // activations hi / lo, box 128 x 80 unswizzled (backward epilogues)
   // folded first backward layer: M_r = W_{L-2}' diag(W_L[r]) as BF16 hi rows
   // [3 HP][HP] then lo rows, and d_{L-1} as BF16 hi + lo [npad][hs]
@@ -309,6 +312,8 @@ size_t mlp_lay_smem();
 cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err);
 void mlp_lay_release(rtn_ctx* ctx);
 cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* fD, float* JD);
+// split-BF16 backward GEMMs of the layered path on CTA pairs (tile mode 7) or single CTAs (6)
+void mlp_lay_set_pair(rtn_ctx* ctx, bool pair);
 // per-launch times of the last timed pass [ms] and kinds (0 inputs, 1 input
 // GEMM, 2 forward GEMM, 3 output layer, 4 first backward GEMM, 5 backward
 // GEMM, 6 Jacobian GEMM); returns the number of launches

@@ -84,3 +84,35 @@ def test_cfg3_full_size_sampled_against_oracle(rtn, orc):
         assert _rel(xn[xs], rx) < 1e-3, ("x", b)
         assert _rel(un[us], ru) < 1e-3, ("u", b)
     ctl.close()
+
+
+@pytest.mark.parametrize("mode", [6, 7])
+def test_cfg3_full_size_layered_shapes(rtn, orc, mode):
+    # both layered reverse-mode shapes (backward GEMMs on single CTAs, tile
+    # mode 6, or on CTA pairs, mode 7) at 163,840 nodes: f_D and J_D of
+    # sampled nodes (the first, the last, and 40 spread over the batch)
+    # against the oracle
+    prob = W.make_problem("cfg3_bf16_precision", seed=0, bf16=True)
+    N = prob["N"]
+    B, nn = len(N), int(N.sum())
+    X, U = W.random_nodes(nn + B, 5)
+    X, U = f32(X), f32(U[:nn])
+    ctl = rtn.Controller(N, f32(prob["dt"]), prob["Q"], prob["R"], QN=prob["QN"], quad=QUAD,
+                         layers=prob["layers"], precision="bf16x2")
+    vi = [v[0] for v in ctl.tc_variants() if v[2] == mode]
+    assert vi, mode
+    ctl.tc_select(vi[0])
+    fD, JD = (t.double().cpu().numpy() for t in ctl.mlp_eval(_dev(X), _dev(U)))
+    assert ctl.device_error() == 0
+    assert np.isfinite(fD).all() and np.isfinite(JD).all()
+    xo = np.concatenate([[0], np.cumsum(N + 1)])[:-1]
+    uo = np.concatenate([[0], np.cumsum(N)])[:-1]
+    inst = np.repeat(np.arange(B), N)
+    rng = np.random.default_rng(11)
+    for n in sorted(set(rng.choice(nn, 40, replace=False).tolist()) | {0, nn - 1}):
+        b = inst[n]
+        z = np.concatenate([X[xo[b] + (n - uo[b])], U[n]])
+        rf, rJ = orc.mlp_fwd_jac(prob["layers"], z)
+        assert _rel(fD[n], rf) < 1e-3, ("f_D", mode, n)
+        assert _rel(JD[n], rJ) < 1e-3, ("J_D", mode, n)
+    ctl.close()

@@ -162,7 +162,8 @@ def test_cfg3_error_table_against_oracle(rtn, orc):
 def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
     # reverse-mode shapes (one CTA: 21 nodes per tile; CTA pairs: 42; the
     # layered pass: tiles of 256 / 80 nodes, with and without hidden->hidden
-    # layers) with several tiles per CTA or pair and a ragged tail: f_D and
+    # layers, its backward GEMMs on single CTAs or CTA pairs) with several
+    # tiles per CTA or pair and a ragged tail: f_D and
     # J_D of sampled nodes against the oracle, every node finite
     layers = [(Wl, W.round_bf16(np.random.default_rng(40 + i).normal(0, 0.05, bl.shape)))
               for i, (Wl, bl) in enumerate(W.xavier_mlp(widths, 7, bf16=True))]
@@ -180,7 +181,7 @@ def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
     ud = torch.as_tensor(U, dtype=torch.float32, device="cuda")
     seen = set()
     for vi, npc, mode, stages in ctl.tc_variants():
-        if mode not in (4, 5, 6):
+        if mode not in (4, 5, 6, 7):
             continue
         seen.add(mode)
         ctl.tc_select(vi)
@@ -191,4 +192,4 @@ def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
         ej = max(np.linalg.norm(J[n] - r[1]) / np.linalg.norm(r[1]) for n, r in zip(idx, ref))
         ef = max(np.abs(F[n] - r[0]).max() / max(np.abs(r[0]).max(), 1e-3) for n, r in zip(idx, ref))
         assert ej < 1e-3 and ef < 1e-3, (vi, npc, mode, stages, ej, ef)
-    assert 4 in seen and 6 in seen and (5 in seen or widths[1] < 256)
+    assert 4 in seen and 6 in seen and (5 in seen or widths[1] < 256) and (7 in seen or widths[1] < 256)
