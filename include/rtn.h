@@ -319,8 +319,9 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
  * 4 split, reverse mode: values forward, three output
  * adjoints backward; 5 the same on CTA pairs; 6 split, reverse mode layered:
  * one GEMM per layer over all nodes, 2 L launches, its buffers allocated
- * when the shape is first selected; 7 as 6 with the hidden backward GEMMs
- * on CTA pairs, hidden width a multiple of 256) and pipeline depth of shape idx,
+ * when the shape is first selected; 7 as 6 with the hidden forward and
+ * backward GEMMs on CTA pairs, hidden width a multiple of 256) and pipeline
+ * depth of shape idx,
  * *fits = 1 if it can run this context's network and precision.  rtn_tc_select: use shape idx
  * (RTN_E_UNSUPPORTED if it does not fit).  rtn_autotune: time every fitting
  * shape on the context's current iterate (synchronous; 1 warm-up + 3 timed

@@ -73,12 +73,14 @@ struct Ly {
   // The first backward GEMM (its d_{L-2} from a_{L-2}) reads them the same
   // way, 16-node chunks through a ring of four.
   static constexpr bool STAGE_ACT = (MODE == LY_BWD || MODE == LY_BW0) && !F8;
-  // split-BF16 backward: the adjoints D_l leave through shared memory, each
-  // half of the epilogue staging its 24 rows (8 nodes x 3) x 128 neurons of a
-  // group (hi, lo; two buffers per half) for TMA tensor stores (2-byte stores
-  // per lane competed with the operand loads: 0.51 vs 0.40 ms per launch
-  // without them)
-  static constexpr bool STAGE_OUT = MODE == LY_BWD && !F8;
+  // split-BF16 backward and forward: the outputs (adjoints D_l, activations
+  // a_{l+1}) leave through shared memory, each group of four epilogue warps
+  // (one per TMEM lane quarter) staging its rows x 128 neurons (hi, lo; two
+  // buffers per group) for TMA tensor stores (2-byte stores per lane
+  // competed with the operand loads: backward GEMM 0.51 vs 0.40 ms per
+  // launch without them).  Backward: 24 rows (8 nodes x 3 adjoints) per
+  // half-group; forward: a 16-node chunk.
+  static constexpr bool STAGE_OUT = (MODE == LY_BWD || MODE == LY_FWD) && !F8;
   static constexpr int STAGES = LY_STAGES;
   // epilogue warps: 4 per TMEM lane quarter in the forward and input GEMMs
   // (their epilogue, tanh and stores with no loads, bounds them: split-BF16
@@ -89,6 +91,10 @@ struct Ly {
   static constexpr int ACT_RING = MODE == LY_BW0 ? 4 : 3;             // ring buffers
   static constexpr int ACT_CHUNKS = NODES / 16;                      // 16-node chunks per tile
   static constexpr int ACT_READERS = MODE == LY_BW0 ? LY_EPI_WARPS / 2 : LY_EPI_WARPS;  // warps reading a chunk
+  static constexpr int OUT_GROUPS = EPI / 4;                                         // staging groups
+  static constexpr uint32_t OUT_BUF = MODE == LY_BWD ? 2u * 24u * 128u * 2u : 2u * 16u * 128u * 2u;  // bytes
+  static constexpr uint32_t OUT_BYTES = STAGE_OUT ? 2u * OUT_GROUPS * OUT_BUF : 0u;
+  static constexpr int OUT_BARS = STAGE_OUT ? 4 * OUT_GROUPS : 0;
 };
 // one ring buffer: the activations of 16 nodes x 128 neurons, hi then lo
 constexpr uint32_t LY_ACT_BYTES = 2u * 16u * 128u * 2u;
@@ -104,13 +110,14 @@ template <int MODE, bool F8 = false>
 __host__ __device__ constexpr size_t ly_smem() {
   return Ly<MODE, F8>::STAGES * ly_stage<MODE, F8>() +
          (Ly<MODE, F8>::STAGE_ACT ? Ly<MODE, F8>::ACT_RING * LY_ACT_BYTES : 0) +
-         (Ly<MODE, F8>::STAGE_OUT ? 4 * LY_OUT_BYTES : 0) + 1024 + 256;
+         Ly<MODE, F8>::OUT_BYTES + 1024 + 512;
 }
 static_assert(ly_b_bytes<LY_FWD>() % 1024 == 0 && ly_b_bytes<LY_BWD>() % 1024 == 0, "1 KB aligned tiles");
 static_assert(ly_smem<LY_JD>() <= 232448 && ly_smem<LY_FWD>() <= 232448 && ly_smem<LY_BW0>() <= 232448 &&
                   ly_smem<LY_FWD, true>() <= 232448 && ly_smem<LY_BWD, true>() <= 232448 &&
                   ly_smem<LY_BWD>() <= 232448,
               "shared memory");
+static_assert(Ly<LY_BWD>::OUT_BUF == LY_OUT_BYTES, "backward staging buffer");
 static_assert(ly_stage<LY_BWD>() % 1024 == 0 && ly_stage<LY_BW0>() % 1024 == 0 && LY_ACT_BYTES % 1024 == 0 &&
                   LY_OUT_BYTES % 1024 == 0,
               "1 KB aligned activation and output buffers");
@@ -118,7 +125,7 @@ static_assert(ly_stage<LY_BWD>() % 1024 == 0 && ly_stage<LY_BW0>() % 1024 == 0 &
 struct LyMaps {
   CUtensorMap bh, bl, b3;  // activations / adjoints hi, lo (F8: hi, mid, lo)
   CUtensorMap sh, sl;      // split-BF16 backward: the activations a_l hi, lo, box 128 x 16
-  CUtensorMap oh, ol;      // split-BF16 backward: its output D_l hi, lo, box 128 x 24 (stores)
+  CUtensorMap oh, ol;      // split-BF16 output stores: backward D_l hi, lo (box 128 x 24), forward a_{l+1} (128 x 16)
 };
 
 struct LyArgs {
@@ -134,6 +141,7 @@ struct LyArgs {
   __nv_bfloat16* dh;   // FWD, last hidden layer: its d as BF16 hi + lo (the
   __nv_bfloat16* dl;   //      B operand of the folded first backward GEMM)
   int act_row0;        // split-BF16 BWD / BW0: row of node 0 of a_l in the stacked activations
+  int out_row0;        // split-BF16 FWD: row of node 0 of the produced layer in the stacked activations
   const __nv_bfloat16* ah;  // BW0 / BWD: a_l of the adjoint's layer [node][hs]
   const __nv_bfloat16* al;  //            hi / lo, d_l = 1 - a_l^2
   __nv_bfloat16* yh;   // FWD / BWD outputs
@@ -327,6 +335,82 @@ __device__ __forceinline__ bool bwd_tile_epilogue(uint32_t taddr, long long j, i
   return true;
 }
 
+// split-BF16 forward epilogue of one tile (LY_NF nodes) for one warp: TMEM
+// lane quarter q (32 neurons of M tile mcol; this lane's neuron i, active
+// when it exists, bias bi), group h of G groups of four warps (one per lane
+// quarter) taking chunks h, h + G, ... of 16 nodes.  Per chunk a = tanh(acc
+// + b) and, for the last hidden layer (a.dh set), d = 1 - a^2 stored
+// directly as BF16 hi + lo; a goes through the group's staging buffer n & 1
+// (n the group's chunk count, [16 nodes][128 neurons] hi then lo; nodes past
+// the end and neurons past the width staged as zeros), stored by the
+// group's quarter-2 warp with two TMA stores at row a.out_row0 + node once
+// the group's four warps have written it, released when the stores have
+// read it.  Barriers 8 B apart: out_full / out_empty [group][buffer].
+// Returns false when a wait ran out.
+template <int G>
+__device__ __forceinline__ bool fwd_tile_epilogue(uint32_t taddr, long long j, int node0, int mcol, bool active,
+                                                  float bi, const LyArgs& a, int h, int q, int lane, uint8_t* outp,
+                                                  uint32_t out_s, uint32_t out_full0, uint32_t out_empty0,
+                                                  const CUtensorMap* oh, const CUtensorMap* ol,
+                                                  volatile int* abort_flag) {
+  constexpr int CPG = LY_NF / 16 / G;                 // chunks per group and tile
+  constexpr uint32_t BUF = 2u * 16u * 128u * 2u;      // one staging buffer
+  const int col = q * 32 + lane, i = mcol * 128 + col;
+#pragma unroll 1
+  for (int c = 0; c < CPG; ++c) {
+    const int ch = h + G * c;
+    float v[16];
+    tmem_ld16(taddr + 16 * ch, v);
+    tmem_wait_ld();
+    float av[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) av[k] = v[k] + bi;
+    tanh_batch<16>(av);
+    if (a.dh) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int node = node0 + 16 * ch + k;
+        if (active && node < a.n_nodes) {
+          const size_t o = (size_t)node * a.hs + i;
+          __nv_bfloat16 dh, dl;
+          split_bf(1.0f - av[k] * av[k], dh, dl);
+          a.dh[o] = dh;
+          a.dl[o] = dl;
+        }
+      }
+    }
+    const long long n = j * CPG + c;
+    const int slot = 2 * h + (int)(n & 1);
+    const uint32_t u = (uint32_t)((n >> 1) & 1);
+    if (!mbar_wait_warp(out_empty0 + 8u * slot, u ^ 1u, abort_flag, a.err, a.wait_cycles)) return false;
+    const uint32_t so = out_s + (uint32_t)slot * BUF;
+    __nv_bfloat16* sop = reinterpret_cast<__nv_bfloat16*>(outp + (size_t)slot * BUF);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      __nv_bfloat16 hv, lv;
+      split_bf((active && node0 + 16 * ch + k < a.n_nodes) ? av[k] : 0.0f, hv, lv);
+      sop[k * 128 + col] = hv;
+      sop[16 * 128 + k * 128 + col] = lv;
+    }
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(out_full0 + 8u * slot);
+    if (q == 2) {
+      if (!mbar_wait_warp(out_full0 + 8u * slot, u, abort_flag, a.err, a.wait_cycles)) return false;
+      if (lane == 0) {
+        const int row = a.out_row0 + node0 + 16 * ch;
+        tma_store_2d(oh, so, mcol * 128, row);
+        tma_store_2d(ol, so + BUF / 2, mcol * 128, row);
+        bulk_commit();
+        bulk_wait_read<1>();  // the group's previous chunk (the other buffer) has been read
+        if (n >= 1) mbar_arrive(out_empty0 + 8u * (slot ^ 1));
+      }
+      __syncwarp();
+    }
+  }
+  return true;
+}
+
 // F8 backward: a_l (= pieces / 448) of the 8 nodes the warp of half H
 // stores in the 16-node group starting at node_g, for the lane's row: each
 // lane loads the words of rows i & ~3 .. + 3 of one node per piece and quad
@@ -411,10 +495,9 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   const uint32_t st0 = sraw + pad;
   const uint32_t act_s = st0 + NS * STAGE;  // activation buffers (STAGE_ACT)
   const uint32_t act_bytes = T::STAGE_ACT ? T::ACT_RING * LY_ACT_BYTES : 0;
-  const uint32_t out_s = act_s + act_bytes;  // output staging (STAGE_OUT): [half][buffer]
-  constexpr int OUT_BARS = T::STAGE_OUT ? 8 : 0;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + act_bytes + (T::STAGE_OUT ? 4 * LY_OUT_BYTES : 0));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * T::ACT_RING + OUT_BARS);
+  const uint32_t out_s = act_s + act_bytes;  // output staging (STAGE_OUT): [group][buffer]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + act_bytes + T::OUT_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * T::ACT_RING + T::OUT_BARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
@@ -425,10 +508,10 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   const uint32_t stall_bar = bar(2 * NS + 5);  // fault injection: nothing completes it
   auto act_full = [&](int b) { return bar(2 * NS + 6 + b); };
   auto act_empty = [&](int b) { return bar(2 * NS + 6 + T::ACT_RING + b); };
-  // staging buffer (half h, buffer b) written by the half's four warps /
+  // staging buffer (group h, buffer b) written by the group's four warps /
   // read out by its TMA stores
   auto out_full = [&](int h, int b) { return bar(2 * NS + 6 + 2 * T::ACT_RING + 2 * h + b); };
-  auto out_empty = [&](int h, int b) { return bar(2 * NS + 6 + 2 * T::ACT_RING + 4 + 2 * h + b); };
+  auto out_empty = [&](int h, int b) { return bar(2 * NS + 6 + 2 * T::ACT_RING + 2 * T::OUT_GROUPS + 2 * h + b); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_tiles = (long long)a.n_groups * a.mts;
@@ -446,7 +529,7 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
       mbar_init(act_full(c), 1);
       mbar_init(act_empty(c), T::ACT_READERS);
     }
-    for (int c = 0; T::STAGE_OUT && c < 4; ++c) {
+    for (int c = 0; T::STAGE_OUT && c < 2 * T::OUT_GROUPS; ++c) {
       mbar_init(out_full(c >> 1, c & 1), 4);
       mbar_init(out_empty(c >> 1, c & 1), 1);
     }
@@ -650,7 +733,12 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
                                             a.wait_cycles))
           break;
       }
-      for (int ch = half; MODE != LY_BWD && ch < T::N / 16; ch += T::EPI / 4) {
+      if (MODE == LY_FWD && !F8) {
+        if (!fwd_tile_epilogue<T::OUT_GROUPS>(taddr, j, node0, mt, active, bi, a, half, q, lane, sm + (out_s - st0),
+                                              out_s, out_full(0, 0), out_empty(0, 0), &bm.oh, &bm.ol, abort_flag))
+          break;
+      }
+      for (int ch = half; MODE != LY_BWD && !(MODE == LY_FWD && !F8) && ch < T::N / 16; ch += T::EPI / 4) {
         float v[16];
         tmem_ld16(taddr + 16 * ch, v);
         if (MODE == LY_BW0) {
@@ -762,28 +850,34 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
 }
 
 // ---------------------------------------------------------------- CTA pairs
-// The split-BF16 backward GEMM on CTA pairs (cta_group::2): one pair tile is
-// M = 256 neurons (128 per CTA, its own weight rows) x N = 240 (80 nodes x 3
-// adjoints; each CTA loads 120 adjoint rows of B, which the MMA reads across
-// the pair) x K.  Each CTA's tensor memory holds its 128 rows x 240 columns,
-// so the epilogue is the single-CTA one (activation ring, staged TMA
-// stores).  Every adjoint row of a node group is read by two pair tiles
-// instead of four M tiles: per SM 23 KB instead of 38 KB per K block, the
-// traffic through L2 that bounds the single-CTA kernel.  Rank 0 issues the
-// MMAs; both CTAs' TMA loads complete on rank 0's stage barriers and both
-// release their stages on the MMAs' multicast commits; both CTAs' epilogues
-// free an accumulator on rank 0's barrier.
+// The split-BF16 backward and forward hidden GEMMs on CTA pairs
+// (cta_group::2): one pair tile is M = 256 neurons (128 per CTA, its own
+// weight rows) x N (backward 240 = 80 nodes x 3 adjoints, forward 256 nodes;
+// each CTA loads N / 2 rows of B, which the MMA reads across the pair) x K.
+// Each CTA's tensor memory holds its 128 rows x N columns, so the epilogues
+// are the single-CTA ones (activation ring and staged TMA stores).  Every B
+// row of a node group is read by two pair tiles instead of four M tiles:
+// per SM 23-24 KB instead of 38-40 KB per K block, the traffic through L2
+// that bounds the single-CTA kernels.  Rank 0 issues the MMAs; both CTAs'
+// TMA loads complete on rank 0's stage barriers and both release their
+// stages on the MMAs' multicast commits; both CTAs' epilogues free an
+// accumulator on rank 0's barrier.
 constexpr int LB2_STAGES = 6;
-constexpr int LB2_RING = 3;
-constexpr uint32_t LB2_B_BYTES = (uint32_t)(3 * LY_NBN / 2) * 64u;  // 120 rows x 64 B
-constexpr uint32_t LB2_LOAD = LY_A_BYTES + 2u * LB2_B_BYTES;          // bytes one CTA loads per stage
-constexpr uint32_t LB2_STAGE = (LB2_LOAD + 1023u) / 1024u * 1024u;    // 1 KB aligned stages
-constexpr int LB2_THREADS = 64 + 32 * LY_EPI_WARPS + 32;              // TMA, MMA, epilogue, activation loader
-constexpr size_t lb2_smem() {
-  return LB2_STAGES * LB2_STAGE + LB2_RING * LY_ACT_BYTES + 4 * LY_OUT_BYTES + 1024 + 512;  // + alignment, barriers
-}
-static_assert(lb2_smem() <= 232448, "shared memory");
-static_assert(LB2_B_BYTES % 512 == 0, "swizzle atoms");
+constexpr int LB2_RING = 3;  // backward: activation ring buffers
+template <int MODE>
+struct Lb2 {
+  using T = Ly<MODE>;
+  static constexpr bool RING = MODE == LY_BWD;                        // activation loader warp + ring
+  static constexpr uint32_t B_BYTES = (uint32_t)(T::N / 2) * 64u;     // one CTA's half of a B tile
+  static constexpr uint32_t LOAD = LY_A_BYTES + 2u * B_BYTES;          // bytes one CTA loads per stage
+  static constexpr uint32_t STAGE = (LOAD + 1023u) / 1024u * 1024u;   // 1 KB aligned stages
+  static constexpr uint32_t RING_BYTES = RING ? LB2_RING * LY_ACT_BYTES : 0u;
+  static constexpr int THREADS = 64 + 32 * T::EPI + (RING ? 32 : 0);  // TMA, MMA, epilogue, [loader]
+  static constexpr int N_RING = RING ? LB2_RING : 0;
+  static constexpr size_t SMEM = LB2_STAGES * STAGE + RING_BYTES + T::OUT_BYTES + 1024 + 512;
+};
+static_assert(Lb2<LY_BWD>::SMEM <= 232448 && Lb2<LY_FWD>::SMEM <= 232448, "shared memory");
+static_assert(Lb2<LY_BWD>::B_BYTES % 512 == 0 && Lb2<LY_FWD>::B_BYTES % 512 == 0, "swizzle atoms");
 
 // bounded wait with cluster-scope acquire (barriers with arrivals from the
 // peer CTA), every lane of a warp, warp-uniform result
@@ -808,19 +902,21 @@ __device__ __forceinline__ bool wait_cl_warp(uint32_t bar, uint32_t parity, vola
   return __all_sync(0xffffffffu, ok);
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
-    lay_bwd2_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ LyMaps bm, LyArgs a) {
-  using T = Ly<LY_BWD>;
-  constexpr int NS = LB2_STAGES;
+template <int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 1)
+    lay2_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ LyMaps bm, LyArgs a) {
+  using T = Ly<MODE>;
+  using P = Lb2<MODE>;
+  constexpr int NS = LB2_STAGES, NR = P::N_RING;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t sraw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
   uint8_t* sm = smem_raw + pad;
   const uint32_t st0 = sraw + pad;
-  const uint32_t ring_s = st0 + NS * LB2_STAGE;
-  const uint32_t out_s = ring_s + LB2_RING * LY_ACT_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (out_s - st0) + 4 * LY_OUT_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * LB2_RING + 8);
+  const uint32_t ring_s = st0 + NS * P::STAGE;
+  const uint32_t out_s = ring_s + P::RING_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (out_s - st0) + T::OUT_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * NR + T::OUT_BARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
@@ -830,8 +926,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
   const uint32_t mma_done = bar(2 * NS + 4);
   const uint32_t stall_bar = bar(2 * NS + 5);  // fault injection: nothing completes it
   auto act_full = [&](int b) { return bar(2 * NS + 6 + b); };
-  auto act_empty = [&](int b) { return bar(2 * NS + 6 + LB2_RING + b); };
-  const uint32_t out_full0 = bar(2 * NS + 6 + 2 * LB2_RING), out_empty0 = bar(2 * NS + 6 + 2 * LB2_RING + 4);
+  auto act_empty = [&](int b) { return bar(2 * NS + 6 + NR + b); };
+  const uint32_t out_full0 = bar(2 * NS + 6 + 2 * NR), out_empty0 = bar(2 * NS + 6 + 2 * NR + 2 * T::OUT_GROUPS);
 
   const uint32_t rank = cluster_rank();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -847,15 +943,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
     }
     for (int c = 0; c < 2; ++c) {
       mbar_init(acc_full(c), 1);
-      mbar_init(tmem_free(c), 2 * LY_EPI_WARPS);
+      mbar_init(tmem_free(c), 2 * T::EPI);
     }
     mbar_init(mma_done, 1);
     mbar_init(stall_bar, 1);
-    for (int c = 0; c < LB2_RING; ++c) {
+    for (int c = 0; c < NR; ++c) {
       mbar_init(act_full(c), 1);
-      mbar_init(act_empty(c), LY_EPI_WARPS);
+      mbar_init(act_empty(c), T::EPI);
     }
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 2 * T::OUT_GROUPS; ++c) {
       mbar_init(out_full0 + 8u * c, 4);
       mbar_init(out_empty0 + 8u * c, 1);
     }
@@ -889,8 +985,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
 
   if (run && warp == 0) {
     // ---------------- TMA producer (both CTAs): this CTA's 128 weight rows
-    // and its 120 adjoint rows (hi, lo) of every K block, onto rank 0's
-    // stage barrier
+    // and its N / 2 rows of B (hi, lo) of every K block, onto rank 0's stage
+    // barrier
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&amap)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bm.bh)) : "memory");
@@ -909,11 +1005,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
       for (int kb = 0; kb < a.nkb; ++kb) {
         if (!(ok = wait_cl_warp(empty_bar(s), ph ^ 1u, abort_flag, a.err, budget))) break;
         if (elect_one()) {
-          const uint32_t sa = st0 + s * LB2_STAGE, fb = full0 + 8u * s;
-          if (rank == 0) mbar_expect_tx(full_bar(s), 2u * LB2_LOAD);
+          const uint32_t sa = st0 + s * P::STAGE, fb = full0 + 8u * s;
+          if (rank == 0) mbar_expect_tx(full_bar(s), 2u * P::LOAD);
           tma_load_2d_pair(sa, &amap, kb * LY_KB, arow, fb);
           tma_load_2d_pair(sa + LY_A_BYTES, &bm.bh, kb * LY_KB, brow, fb);
-          tma_load_2d_pair(sa + LY_A_BYTES + LB2_B_BYTES, &bm.bl, kb * LY_KB, brow, fb);
+          tma_load_2d_pair(sa + LY_A_BYTES + P::B_BYTES, &bm.bl, kb * LY_KB, brow, fb);
         }
         __syncwarp();
         if (++s == NS) { s = 0; ph ^= 1u; }
@@ -925,8 +1021,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
       if (++s == NS) { s = 0; ph ^= 1u; }
     }
   } else if (run && warp == 1 && rank == 0) {
-    // ---------------- MMA issuer of the pair: two K steps per 64 B row, the
-    // adjoints' hi and lo halves, M = 256, N = 240
+    // ---------------- MMA issuer of the pair: two K steps per 64 B row, B's
+    // hi and lo halves, M = 256
     constexpr uint32_t idesc = idesc_bf16(256, T::N);
     int s = 0, acc = 0;
     uint32_t ph = 0, aph = 0;
@@ -938,7 +1034,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
       for (int kb = 0; kb < a.nkb; ++kb) {
         if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err, budget))) break;
         tc_fence_after();
-        const uint32_t sa = st0 + s * LB2_STAGE;
+        const uint32_t sa = st0 + s * P::STAGE;
         uint64_t ad[4], bd[4];
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
@@ -946,7 +1042,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
           ad[2 * ks] = aw;
           ad[2 * ks + 1] = aw;
           bd[2 * ks] = kmajor_desc(sa + LY_A_BYTES + ks * 32u, LY_SBO, LY_SWZ);
-          bd[2 * ks + 1] = kmajor_desc(sa + LY_A_BYTES + LB2_B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+          bd[2 * ks + 1] = kmajor_desc(sa + LY_A_BYTES + P::B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
         }
         mma2_bf16_x4(d, ad, bd, idesc, kb != 0);
         commit2(empty_bar(s), 3);
@@ -960,10 +1056,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
     const long long t0 = clock64();
     while (!mbar_try(mma_done, 0) && clock64() - t0 < budget) {
     }
-  } else if (run && warp == 2 + LY_EPI_WARPS) {
-    // ---------------- activation loader (both CTAs): chunk c of every tile
-    // (16 nodes x this CTA's 128 neurons, hi and lo) into ring buffer
-    // n % LB2_RING once the epilogue has released it
+  } else if (run && P::RING && warp == 2 + T::EPI) {
+    // ---------------- activation loader (backward, both CTAs): chunk c of
+    // every tile (16 nodes x this CTA's 128 neurons, hi and lo) into ring
+    // buffer n % LB2_RING once the epilogue has released it
     if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bm.sh)) : "memory");
     bool ok = true;
     uint32_t issued = 0, last_ph = 0;
@@ -993,9 +1089,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
         while (!mbar_try(act_full(b), (last_ph >> b) & 1u) && clock64() - t0 < budget) {
         }
       }
-  } else if (run && warp >= 2 && warp < 2 + LY_EPI_WARPS) {
+  } else if (run && warp >= 2 && warp < 2 + T::EPI) {
     // ---------------- epilogue (both CTAs): this CTA's 128 rows, as the
-    // single-CTA backward epilogue
+    // single-CTA epilogue
     const int q = warp & 3, half = (warp - 2) >> 2;
     const uint32_t tfree0 = mapa(tmem_free(0), 0);
     int acc = 0;
@@ -1005,13 +1101,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(LB2_THREADS, 1)
       const int grp = (int)(t / mps), mc = (int)(t % mps) * 2 + (int)rank;
       const int i = mc * 128 + q * 32 + lane;
       const bool active = i < a.m_rows;
+      const float bi = MODE == LY_FWD ? __ldg(a.bias + (active ? i : 0)) : 0.0f;
       if (!wait_cl_warp(acc_full(acc), aph, abort_flag, a.err, budget)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
-      if (!bwd_tile_epilogue<LB2_RING>(taddr, j, grp * T::NODES, mc, active, a.n_nodes, half, q, lane,
-                                       sm + (ring_s - st0), sm + (out_s - st0), out_s, act_full(0), act_empty(0),
-                                       out_full0, out_empty0, &bm.oh, &bm.ol, abort_flag, a.err, budget))
-        break;
+      bool ok;
+      if constexpr (MODE == LY_BWD)
+        ok = bwd_tile_epilogue<LB2_RING>(taddr, j, grp * T::NODES, mc, active, a.n_nodes, half, q, lane,
+                                         sm + (ring_s - st0), sm + (out_s - st0), out_s, act_full(0), act_empty(0),
+                                         out_full0, out_empty0, &bm.oh, &bm.ol, abort_flag, a.err, budget);
+      else
+        ok = fwd_tile_epilogue<T::OUT_GROUPS>(taddr, j, grp * T::NODES, mc, active, bi, a, half, q, lane,
+                                              sm + (out_s - st0), out_s, out_full0, out_empty0, &bm.oh, &bm.ol,
+                                              abort_flag);
+      if (!ok) break;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) arrive_cluster(tfree0 + 8u * acc);
@@ -1286,7 +1389,8 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   // backward and Jacobian tiles read adjoints (box 240 rows); no box reaches
   // past its layer (rows padded to a multiple of both tiles)
   for (int p = 0; p < 2; ++p)
-    if (!enc(s->ma[p], s->act[p], (long long)(L - 1) * npad, LY_NF)) {
+    if (!enc(s->ma[p], s->act[p], (long long)(L - 1) * npad, LY_NF) ||
+        !enc(s->ma2[p], s->act[p], (long long)(L - 1) * npad, LY_NF / 2)) {
       err = "cuTensorMapEncodeTiled failed";
       return cudaSuccess;
     }
@@ -1429,8 +1533,11 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   if ((e = cudaFuncSetAttribute(lay_kernel<LY_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ly_smem<LY_BWD>())) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(lay_bwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lb2_smem())) !=
-      cudaSuccess)
+  if ((e = cudaFuncSetAttribute(lay2_kernel<LY_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Lb2<LY_BWD>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(lay2_kernel<LY_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Lb2<LY_FWD>::SMEM)) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(lay_kernel<LY_JD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ly_smem<LY_JD>());
 }
@@ -1567,8 +1674,21 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
       lay_kernel<LY_FWD, true><<<grid_of((long long)gf * a.mts), Ly<LY_FWD, true>::THREADS, ly_smem<LY_FWD, true>(), st>>>(
           *reinterpret_cast<const CUtensorMap*>(s->q8map), maps8(s->a8map), a);
     } else {
-      lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), Ly<LY_FWD>::THREADS, ly_smem<LY_FWD>(), st>>>(
-          *wmap, maps(s->ma[0], s->ma[1]), a);
+      LyMaps m = maps(s->ma[0], s->ma[1]);
+      memcpy(&m.oh, s->mact[0], sizeof(CUtensorMap));  // a_{g+2}: box 128 neurons x 16 nodes
+      memcpy(&m.ol, s->mact[1], sizeof(CUtensorMap));
+      a.out_row0 = (g + 1) * s->npad;
+      if (s->pair_bwd && a.mts % 2 == 0) {
+        // pair tiles of 256 neurons: each CTA loads half of the tile's 256 node rows
+        memcpy(&m.bh, s->ma2[0], sizeof(CUtensorMap));
+        memcpy(&m.bl, s->ma2[1], sizeof(CUtensorMap));
+        const long long pt = (long long)gf * (a.mts / 2);
+        const int pairs = (int)std::min<long long>(pt, std::max(1, tc.n_sm / 2));
+        lay2_kernel<LY_FWD><<<2 * pairs, Lb2<LY_FWD>::THREADS, Lb2<LY_FWD>::SMEM, st>>>(*wmap, m, a);
+      } else {
+        lay_kernel<LY_FWD><<<grid_of((long long)gf * a.mts), Ly<LY_FWD>::THREADS, ly_smem<LY_FWD>(), st>>>(*wmap, m,
+                                                                                                             a);
+      }
     }
   }
   // f_D (and, with no hidden->hidden layer, the last layer's adjoints into
@@ -1676,7 +1796,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
         memcpy(&m.bl, s->mb2[src][1], sizeof(CUtensorMap));
         const long long pt = (long long)gb * (a.mts / 2);
         const int pairs = (int)std::min<long long>(pt, std::max(1, tc.n_sm / 2));
-        lay_bwd2_kernel<<<2 * pairs, LB2_THREADS, lb2_smem(), st>>>(*rmap, m, a);
+        lay2_kernel<LY_BWD><<<2 * pairs, Lb2<LY_BWD>::THREADS, Lb2<LY_BWD>::SMEM, st>>>(*rmap, m, a);
       } else {
         lay_kernel<LY_BWD><<<grid_of((long long)gb * a.mts), Ly<LY_BWD>::THREADS, ly_smem<LY_BWD>(), st>>>(*rmap, m,
                                                                                                            a);

@@ -372,8 +372,8 @@ struct Variant {
              // 4 split, reverse mode (value forward, three adjoints backward),
              // 5 split, reverse mode on a CTA pair,
              // 6 split, reverse mode layered (one GEMM per layer over all nodes),
-             // 7 as 6 with the backward GEMMs on CTA pairs (hidden width a
-             //   multiple of 256)
+             // 7 as 6 with the hidden forward and backward GEMMs on CTA
+             //   pairs (hidden width a multiple of 256)
   int stages;
   const void* fn;
   bool split() const { return mode != 0; }
