@@ -411,6 +411,73 @@ __device__ __forceinline__ bool fwd_tile_epilogue(uint32_t taddr, long long j, i
   return true;
 }
 
+// epilogue of the first backward GEMM (last-layer adjoints folded in) for
+// one tile (LY_NF nodes; component r0 of the M tile's 128 neurons, this
+// lane's neuron i, active when it exists) and one warp: TMEM lane quarter q,
+// chunks h, h + G, ... of 16 nodes.  Chunk c's activations a_{L-2} come from
+// ring buffer n % RING (n = j * 16 + c, j the CTA's tile count; filled by the
+// activation warp); D_{L-2}[node * 3 + r0][i] = acc * (1 - a^2) is stored as
+// BF16 hi + lo, or (RTN_FP8, a.y8h set) as e4m3 pieces of D * s8.  Barriers
+// 8 B apart: act_full / act_empty [RING].  Returns false when a wait ran out.
+template <int RING, int G>
+__device__ __forceinline__ bool bw0_tile_epilogue(uint32_t taddr, long long j, int node0, int i, int r0, bool active,
+                                                  int h, int q, int lane, const uint8_t* ring, uint32_t act_full0,
+                                                  uint32_t act_empty0, const LyArgs& a, volatile int* abort_flag) {
+  constexpr int CH = LY_NF / 16;
+  const int col = q * 32 + lane;
+#pragma unroll 1
+  for (int ch = h; ch < CH; ch += G) {
+    float v[16];
+    tmem_ld16(taddr + 16 * ch, v);
+    const long long n = j * CH + ch;
+    const int b = (int)(n % RING);
+    if (!mbar_wait_warp(act_full0 + 8u * b, (uint32_t)((n / RING) & 1), abort_flag, a.err, a.wait_cycles)) {
+      tmem_wait_ld();
+      return false;
+    }
+    const __nv_bfloat16* sa = reinterpret_cast<const __nv_bfloat16*>(ring + (size_t)b * LY_ACT_BYTES);
+    __nv_bfloat16 qh[16], ql[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      qh[k] = sa[k * 128 + col];
+      ql[k] = sa[16 * 128 + k * 128 + col];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(act_empty0 + 8u * b);
+    tmem_wait_ld();
+    float dv[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float av = __bfloat162float(qh[k]) + __bfloat162float(ql[k]);
+      dv[k] = 1.0f - av * av;
+    }
+    if (a.y8h) {  // RTN_FP8: D * s8 as e4m3 pieces, four nodes per store
+      const int tq = lane & 3;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        float d4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d4[k] = active ? v[4 * m + k] * dv[4 * m + k] * a.s8 : 0.0f;
+        store_pieces4(d4, tq, node0 + 16 * ch + 4 * m, a.n_nodes, (size_t)3 * a.hs, (i & ~3) + r0 * a.hs, a.y8h,
+                      a.y8m, a.y8l);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int node = node0 + 16 * ch + k;
+        if (active && node < a.n_nodes) {
+          const size_t o = ((size_t)node * 3 + r0) * a.hs + i;
+          __nv_bfloat16 hv, lv;
+          split_bf(v[k] * dv[k], hv, lv);
+          a.yh[o] = hv;
+          a.yl[o] = lv;
+        }
+      }
+    }
+  }
+  return true;
+}
+
 // F8 backward: a_l (= pieces / 448) of the 8 nodes the warp of half H
 // stores in the 16-node group starting at node_g, for the lane's row: each
 // lane loads the words of rows i & ~3 .. + 3 of one node per piece and quad
@@ -683,10 +750,9 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
       const int ic = active ? i : 0;  // a row that exists, for the loads
       const int node0 = grp * T::NODES;
       const float bi = T::ACT ? __ldg(a.bias + ic) : 0.0f;
-      // backward: the first group's activations are loaded while the
+      // F8 backward: the first group's activations are loaded while the
       // accumulator is still being computed, each later group's while the
       // one before it is stored
-      __nv_bfloat16 qh[16], ql[16];
       uint32_t p8[6];
       const int tq = lane & 3;
       if (MODE == LY_BWD && F8) {
@@ -738,27 +804,15 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
                                               out_s, out_full(0, 0), out_empty(0, 0), &bm.oh, &bm.ol, abort_flag))
           break;
       }
-      for (int ch = half; MODE != LY_BWD && !(MODE == LY_FWD && !F8) && ch < T::N / 16; ch += T::EPI / 4) {
+      if (MODE == LY_BW0) {
+        if (!bw0_tile_epilogue<T::ACT_RING, T::EPI / 4>(taddr, j, node0, i, r0, active, half, q, lane,
+                                                         sm + NS * STAGE, act_full(0), act_empty(0), a, abort_flag))
+          break;
+      }
+      for (int ch = half; MODE != LY_BWD && MODE != LY_BW0 && !(MODE == LY_FWD && !F8) && ch < T::N / 16;
+           ch += T::EPI / 4) {
         float v[16];
         tmem_ld16(taddr + 16 * ch, v);
-        if (MODE == LY_BW0) {
-          // the chunk's activations from the ring (chunk ch of the tile)
-          const long long n = j * T::ACT_CHUNKS + ch;
-          const int b = (int)(n % T::ACT_RING);
-          if (!mbar_wait_warp(act_full(b), (uint32_t)((n / T::ACT_RING) & 1), abort_flag, a.err, a.wait_cycles)) {
-            tmem_wait_ld();
-            break;
-          }
-          const __nv_bfloat16* sa = reinterpret_cast<const __nv_bfloat16*>(sm + NS * STAGE + (uint32_t)b * LY_ACT_BYTES);
-          const int col = q * 32 + lane;
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            qh[k] = sa[k * 128 + col];
-            ql[k] = sa[16 * 128 + k * 128 + col];
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(act_empty(b));
-        }
         tmem_wait_ld();
         if (T::ACT) {
           float av[16];
@@ -791,37 +845,6 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
 #pragma unroll
               for (int k = 0; k < 4; ++k) a4[k] = active ? av[4 * m + k] * 448.0f : 0.0f;
               store_pieces4(a4, tq, node0 + 16 * ch + 4 * m, a.n_nodes, a.hs, i & ~3, a.y8h, a.y8m, a.y8l);
-            }
-          }
-        } else if (MODE == LY_BW0) {
-          // D_{L-2}[node * 3 + r][i] = acc * d_{L-2}[node][i]
-          float dv[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const float av = __bfloat162float(qh[k]) + __bfloat162float(ql[k]);
-            dv[k] = 1.0f - av * av;
-          }
-          if (a.y8h) {  // RTN_FP8: D * s8 as e4m3 pieces, four nodes per store
-            const int tq = lane & 3;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              float d4[4];
-#pragma unroll
-              for (int k = 0; k < 4; ++k) d4[k] = active ? v[4 * m + k] * dv[4 * m + k] * a.s8 : 0.0f;
-              store_pieces4(d4, tq, node0 + 16 * ch + 4 * m, a.n_nodes, (size_t)3 * a.hs, (i & ~3) + r0 * a.hs,
-                            a.y8h, a.y8m, a.y8l);
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int node = node0 + 16 * ch + k;
-              if (active && node < a.n_nodes) {
-                const size_t o = ((size_t)node * 3 + r0) * a.hs + i;
-                __nv_bfloat16 h, l;
-                split_bf(v[k] * dv[k], h, l);
-                a.yh[o] = h;
-                a.yl[o] = l;
-              }
             }
           }
         } else {
@@ -861,19 +884,22 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
 // that bounds the single-CTA kernels.  Rank 0 issues the MMAs; both CTAs'
 // TMA loads complete on rank 0's stage barriers and both release their
 // stages on the MMAs' multicast commits; both CTAs' epilogues free an
-// accumulator on rank 0's barrier.
+// accumulator on rank 0's barrier.  (The first backward GEMM on pairs
+// measured slower, 0.602 vs 0.592 ms per launch: its epilogue bounds it.)
 constexpr int LB2_STAGES = 6;
 constexpr int LB2_RING = 3;  // backward: activation ring buffers
 template <int MODE>
 struct Lb2 {
   using T = Ly<MODE>;
+  static_assert(T::NA == 1, "one weight tile per stage");
   static constexpr bool RING = MODE == LY_BWD;                        // activation loader warp + ring
-  static constexpr uint32_t B_BYTES = (uint32_t)(T::N / 2) * 64u;     // one CTA's half of a B tile
-  static constexpr uint32_t LOAD = LY_A_BYTES + 2u * B_BYTES;          // bytes one CTA loads per stage
-  static constexpr uint32_t STAGE = (LOAD + 1023u) / 1024u * 1024u;   // 1 KB aligned stages
-  static constexpr uint32_t RING_BYTES = RING ? LB2_RING * LY_ACT_BYTES : 0u;
-  static constexpr int THREADS = 64 + 32 * T::EPI + (RING ? 32 : 0);  // TMA, MMA, epilogue, [loader]
   static constexpr int N_RING = RING ? LB2_RING : 0;
+  static constexpr uint32_t B_BYTES = (uint32_t)(T::N / 2) * 64u;     // one CTA's half of a B tile
+  static constexpr uint32_t B0 = LY_A_BYTES;                          // B's offset in a stage
+  static constexpr uint32_t LOAD = B0 + 2u * B_BYTES;                  // bytes one CTA loads per stage
+  static constexpr uint32_t STAGE = (LOAD + 1023u) / 1024u * 1024u;   // 1 KB aligned stages
+  static constexpr uint32_t RING_BYTES = (uint32_t)N_RING * LY_ACT_BYTES;
+  static constexpr int THREADS = 64 + 32 * T::EPI + (RING ? 32 : 0);  // TMA, MMA, epilogue, [loader]
   static constexpr size_t SMEM = LB2_STAGES * STAGE + RING_BYTES + T::OUT_BYTES + 1024 + 512;
 };
 static_assert(Lb2<LY_BWD>::SMEM <= 232448 && Lb2<LY_FWD>::SMEM <= 232448, "shared memory");
@@ -917,6 +943,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
   const uint32_t out_s = ring_s + P::RING_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (out_s - st0) + T::OUT_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * NR + T::OUT_BARS);
+  static_assert(2 * NS + 6 + 2 * NR + T::OUT_BARS <= 60, "barrier area");
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
@@ -949,9 +976,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
     mbar_init(stall_bar, 1);
     for (int c = 0; c < NR; ++c) {
       mbar_init(act_full(c), 1);
-      mbar_init(act_empty(c), T::EPI);
+      mbar_init(act_empty(c), T::ACT_READERS);
     }
-    for (int c = 0; c < 2 * T::OUT_GROUPS; ++c) {
+    for (int c = 0; T::STAGE_OUT && c < 2 * T::OUT_GROUPS; ++c) {
       mbar_init(out_full0 + 8u * c, 4);
       mbar_init(out_empty0 + 8u * c, 1);
     }
@@ -1008,8 +1035,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
           const uint32_t sa = st0 + s * P::STAGE, fb = full0 + 8u * s;
           if (rank == 0) mbar_expect_tx(full_bar(s), 2u * P::LOAD);
           tma_load_2d_pair(sa, &amap, kb * LY_KB, arow, fb);
-          tma_load_2d_pair(sa + LY_A_BYTES, &bm.bh, kb * LY_KB, brow, fb);
-          tma_load_2d_pair(sa + LY_A_BYTES + P::B_BYTES, &bm.bl, kb * LY_KB, brow, fb);
+          tma_load_2d_pair(sa + P::B0, &bm.bh, kb * LY_KB, brow, fb);
+          tma_load_2d_pair(sa + P::B0 + P::B_BYTES, &bm.bl, kb * LY_KB, brow, fb);
         }
         __syncwarp();
         if (++s == NS) { s = 0; ph ^= 1u; }
@@ -1041,8 +1068,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
           const uint64_t aw = kmajor_desc(sa + ks * 32u, LY_SBO, LY_SWZ);
           ad[2 * ks] = aw;
           ad[2 * ks + 1] = aw;
-          bd[2 * ks] = kmajor_desc(sa + LY_A_BYTES + ks * 32u, LY_SBO, LY_SWZ);
-          bd[2 * ks + 1] = kmajor_desc(sa + LY_A_BYTES + P::B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+          bd[2 * ks] = kmajor_desc(sa + P::B0 + ks * 32u, LY_SBO, LY_SWZ);
+          bd[2 * ks + 1] = kmajor_desc(sa + P::B0 + P::B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
         }
         mma2_bf16_x4(d, ad, bd, idesc, kb != 0);
         commit2(empty_bar(s), 3);
@@ -1067,8 +1094,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
     for (long long t = pair; t < n_tiles && ok; t += n_pairs) {
       const int grp = (int)(t / mps), mc = (int)(t % mps) * 2 + (int)rank;
       for (int c = 0; c < T::ACT_CHUNKS; ++c, ++n) {
-        const int b = (int)(n % LB2_RING);
-        const uint32_t ph = (uint32_t)((n / LB2_RING) & 1);
+        constexpr int NRD = NR > 0 ? NR : 1;  // (no ring in the forward GEMM)
+        const int b = (int)(n % NRD);
+        const uint32_t ph = (uint32_t)((n / NRD) & 1);
         if (!(ok = mbar_wait_warp(act_empty(b), ph ^ 1u, abort_flag, a.err, budget))) break;
         if (elect_one()) {
           const uint32_t dst = ring_s + (uint32_t)b * LY_ACT_BYTES;
@@ -1083,7 +1111,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
       }
     }
     // the ring's last copies have landed before the CTA may exit
-    for (int b = 0; b < LB2_RING; ++b)
+    for (int b = 0; b < NR; ++b)
       if (issued & (1u << b)) {
         const long long t0 = clock64();
         while (!mbar_try(act_full(b), (last_ph >> b) & 1u) && clock64() - t0 < budget) {
@@ -1121,7 +1149,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
       if (++acc == 2) { acc = 0; aph ^= 1u; }
     }
     // the staged stores have completed before the CTA's shared memory goes
-    if (lane == 0 && q == 2) bulk_wait_all();
+    if (T::STAGE_OUT && lane == 0 && q == 2) bulk_wait_all();
   }
 
   __syncthreads();
@@ -1539,6 +1567,7 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   if ((e = cudaFuncSetAttribute(lay2_kernel<LY_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Lb2<LY_FWD>::SMEM)) != cudaSuccess)
     return e;
+
   return cudaFuncSetAttribute(lay_kernel<LY_JD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ly_smem<LY_JD>());
 }
 

@@ -71,7 +71,7 @@ struct LayState {
   alignas(64) unsigned char mout[2][2][128];  // adjoints, box 128 x 24 unswizzled (backward GEMM's stores)
   alignas(64) unsigned char mb2[2][2][128];   // adjoints, box 32 x 120 (one CTA's half of a pair tile)
   alignas(64) unsigned char ma2[2][128];      // activations, box 32 x 128 (one CTA's half of a forward pair tile)
-  bool pair_bwd = false;                      // hidden backward and forward GEMMs on CTA pairs (tile mode 7)
+  bool pair_bwd = false;                      // hidden forward and backward GEMMs on CTA pairs (tile mode 7)
   alignas(64) unsigned char mact[2][128];   // activations hi / lo, box 128 x 80 unswizzled (backward epilogues)
   // folded first backward layer: M_r = W_{L-2}' diag(W_L[r]) as BF16 hi rows
   // [3 HP][HP] then lo rows, and d_{L-1} as BF16 hi + lo [npad][hs]
