@@ -755,9 +755,10 @@ LAY_KERNELS = {"input GEMM": "lay_kernel<4>", "forward GEMM": "lay_kernel<0>", "
 
 
 def lay_kernel_name(kind, mode):
-    """Kernel of one kind of layered launch (tile mode 7: the hidden backward
-    GEMMs on CTA pairs)."""
-    return "lay_bwd2_kernel (CTA pairs)" if mode == 7 and kind == "backward GEMM" else LAY_KERNELS[kind]
+    """Kernel of one kind of layered launch (tile mode 7: the hidden forward
+    and backward GEMMs on CTA pairs)."""
+    pairs = {"backward GEMM": "lay2_kernel<1> (CTA pairs)", "forward GEMM": "lay2_kernel<0> (CTA pairs)"}
+    return pairs[kind] if mode == 7 and kind in pairs else LAY_KERNELS[kind]
 
 
 def lay_flops(kind, widths, nn):
@@ -1148,8 +1149,9 @@ def main():
                  "kernel": ("network pass of the layered reverse mode (a1): inputs split, one tensor-core GEMM per "
                             "layer forward (input layer included), output layer, one GEMM per backward layer "
                             "(the first with the last-layer adjoints folded in), the W_0' Jacobian GEMM "
-                            "(12 launches at 5 hidden layers)" + ("; the hidden backward GEMMs on CTA pairs"
-                                                                   if mode == 7 else "") if mode in (6, 7) else
+                            "(12 launches at 5 hidden layers)" + ("; the hidden forward and backward GEMMs on "
+                                                                   "CTA pairs" if mode == 7 else "")
+                            if mode in (6, 7) else
                             "network value + reverse-mode Jacobian (a1, three adjoint rows)" if rev
                             else "network value + forward-mode Jacobian (a1)"),
                  "forward_mode_equivalent_tflops": fwd_flops_per_node(widths) * nn / (ms_mlp * 1e-3) / 1e12,
