@@ -175,6 +175,32 @@ struct TrainState {
   int wjob_blocks = 0;                 // blocks of that launch
 };
 
+// Programmatic dependent launch: the launches of a training step carry the
+// programmatic-serialisation attribute, so a kernel may
+// start (its prologue: barriers, tensor memory, descriptor prefetch) while
+// its predecessor drains; pdl_wait() then blocks until every prerequisite
+// grid has completed and its memory is visible (a no-op for an ordinary
+// launch), and pdl_trigger() lets the next launch start early (once every
+// CTA of this grid has called it or exited).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// a launch with the programmatic-serialisation attribute (see pdl_wait)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 }  // namespace rtn
 
 namespace rtn {
