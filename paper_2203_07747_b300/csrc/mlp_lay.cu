@@ -71,7 +71,7 @@ struct Ly {
   // three loaded by TMA from an eleventh warp (global loads of 2 B per lane
   // were the epilogue's largest cost)
   // The first backward GEMM (its d_{L-2} from a_{L-2}) reads them the same
-  // way, 16-node chunks through a ring of four.
+  // way, 16-node chunks through a ring of ten.
   static constexpr bool STAGE_ACT = (MODE == LY_BWD || MODE == LY_BW0) && !F8;
   // split-BF16 backward and forward: the outputs (adjoints D_l, activations
   // a_{l+1}) leave through shared memory, each group of four epilogue warps
@@ -81,14 +81,17 @@ struct Ly {
   // launch without them).  Backward: 24 rows (8 nodes x 3 adjoints) per
   // half-group; forward: a 16-node chunk.
   static constexpr bool STAGE_OUT = (MODE == LY_BWD || MODE == LY_FWD) && !F8;
-  static constexpr int STAGES = LY_STAGES;
+  // the first backward GEMM trades a stage for a deeper activation ring
+  // (its epilogue, two activation loads per output, bounds it; three stages
+  // and ten ring buffers 0.586 -> 0.567 ms per launch)
+  static constexpr int STAGES = MODE == LY_BW0 ? 3 : LY_STAGES;
   // epilogue warps: 4 per TMEM lane quarter in the forward and input GEMMs
   // (their epilogue, tanh and stores with no loads, bounds them: split-BF16
   // forward GEMM 0.184 -> 0.174 ms, input 0.157 -> 0.111, FP8 forward 0.195
   // -> 0.165 with 16 instead of 8), else 2
   static constexpr int EPI = (MODE == LY_FWD || MODE == LY_IN) ? 16 : LY_EPI_WARPS;
   static constexpr int THREADS = 64 + 32 * EPI + (STAGE_ACT ? 32 : 0);
-  static constexpr int ACT_RING = MODE == LY_BW0 ? 4 : 3;             // ring buffers
+  static constexpr int ACT_RING = MODE == LY_BW0 ? 10 : 3;            // ring buffers
   static constexpr int ACT_CHUNKS = NODES / 16;                      // 16-node chunks per tile
   static constexpr int ACT_READERS = MODE == LY_BW0 ? LY_EPI_WARPS / 2 : LY_EPI_WARPS;  // warps reading a chunk
   static constexpr int OUT_GROUPS = EPI / 4;                                         // staging groups
@@ -565,6 +568,7 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
   const uint32_t out_s = act_s + act_bytes;  // output staging (STAGE_OUT): [group][buffer]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * STAGE + act_bytes + T::OUT_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6 + 2 * T::ACT_RING + T::OUT_BARS);
+  static_assert(2 * NS + 6 + 2 * T::ACT_RING + T::OUT_BARS <= 60, "barrier area");
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int k) { return smem_u32(bars + k); };
   auto full_bar = [&](int s) { return bar(s); };
