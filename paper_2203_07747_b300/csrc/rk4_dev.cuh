@@ -122,6 +122,9 @@ __device__ __forceinline__ void rk4_column(
   for (int i = 0; i < NU; ++i) du[i] = (j == NX + i) ? 1.0f : 0.0f;
 #pragma unroll
   for (int i = 0; i < NX; ++i) S[i] = (i == j) ? 1.0f : 0.0f;
+  // at the first stage (xs = x0, Ss = e_j) the local model's value is f_D
+  // itself and its directional derivative the entry J_D[r][j]: exact, the
+  // results of the full products bit for bit, without their 17 loads
   float xs[NX], Ss[NX], k[NX], dk[NX], ksum[NX], dksum[NX];
 #pragma unroll
   for (int i = 0; i < NX; ++i) { ksum[i] = 0.0f; dksum[i] = 0.0f; }
@@ -144,15 +147,20 @@ __device__ __forceinline__ void rk4_column(
     if (res) {
 #pragma unroll
       for (int r = 0; r < NOUT; ++r) {
-        float v = fb[r], dv = 0.0f;
+        float v = fb[r], dv;
+        if (s == 0) {
+          dv = __ldg(Jp + r * NZ + j);
+        } else {
+          dv = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NX; ++i) {
-          const float Jri = __ldg(Jp + r * NZ + i);
-          v = fmaf(Jri, xs[i] - x0[i], v);
-          dv = fmaf(Jri, Ss[i], dv);
+          for (int i = 0; i < NX; ++i) {
+            const float Jri = __ldg(Jp + r * NZ + i);
+            v = fmaf(Jri, xs[i] - x0[i], v);
+            dv = fmaf(Jri, Ss[i], dv);
+          }
+#pragma unroll
+          for (int i = 0; i < NU; ++i) dv = fmaf(__ldg(Jp + r * NZ + NX + i), du[i], dv);
         }
-#pragma unroll
-        for (int i = 0; i < NU; ++i) dv = fmaf(__ldg(Jp + r * NZ + NX + i), du[i], dv);
         if (HD && s > 0) {
           // g = H_r dz (dz = xs - x0 on the state part): value + 1/2 dz'g,
           // directional derivative + g . [S; du]
