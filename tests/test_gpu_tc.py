@@ -193,3 +193,39 @@ def test_tc_reverse_mode_several_tiles_per_cta(rtn, orc, widths):
         ef = max(np.abs(F[n] - r[0]).max() / max(np.abs(r[0]).max(), 1e-3) for n, r in zip(idx, ref))
         assert ej < 1e-3 and ef < 1e-3, (vi, npc, mode, stages, ej, ef)
     assert 4 in seen and 6 in seen and (5 in seen or widths[1] < 256) and (7 in seen or widths[1] < 256)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", [6, 7])
+def test_layered_uneven_widths(rtn, orc, mode):
+    # the layered shapes on hidden widths that are not multiples of 128 and
+    # differ by layer (17-200-512-300-3, padded to 512): the epilogues' staged
+    # stores write zeros past each layer's width, and tile mode 7 runs the
+    # layers with an even number of 128-neuron tiles on CTA pairs and the
+    # others (300 neurons: 3 tiles) on single CTAs; several tiles per CTA and
+    # a ragged tail; f_D and J_D of sampled nodes against the oracle
+    widths = [17, 200, 512, 300, 3]
+    layers = [(Wl, W.round_bf16(np.random.default_rng(60 + i).normal(0, 0.05, bl.shape)))
+              for i, (Wl, bl) in enumerate(W.xavier_mlp(widths, 11, bf16=True))]
+    N = np.array([20] * 300 + [9], np.int32)
+    ctl = rtn.Controller(N, np.full(len(N), 0.05), W.Q_DIAG, W.R_DIAG, quad=QUAD, layers=layers,
+                         precision="bf16x2")
+    vi = [v[0] for v in ctl.tc_variants() if v[2] == mode]
+    assert vi, mode
+    ctl.tc_select(vi[0])
+    X, U = W.random_nodes(ctl.n_states, 13)
+    X = X.astype(np.float32).astype(np.float64)
+    U = U[:ctl.n_nodes].astype(np.float32).astype(np.float64)
+    inst = np.repeat(np.arange(len(N)), N)
+    idx = np.concatenate([np.random.default_rng(3).choice(ctl.n_nodes - 1, 40, replace=False),
+                          np.arange(ctl.n_nodes - 12, ctl.n_nodes)])
+    fD, JD = ctl.mlp_eval(torch.as_tensor(X, dtype=torch.float32, device="cuda"),
+                          torch.as_tensor(U, dtype=torch.float32, device="cuda"))
+    assert ctl.device_error() == 0
+    F, J = fD.double().cpu().numpy(), JD.double().cpu().numpy()
+    assert np.isfinite(F).all() and np.isfinite(J).all()
+    for n in idx:
+        rf, rJ = orc.mlp_fwd_jac(layers, np.concatenate([X[n + inst[n]], U[n]]))
+        assert np.linalg.norm(J[n] - rJ) / np.linalg.norm(rJ) < 1e-3, ("J_D", mode, n)
+        assert np.abs(F[n] - rf).max() / max(np.abs(rf).max(), 1e-3) < 1e-3, ("f_D", mode, n)
+    ctl.close()
