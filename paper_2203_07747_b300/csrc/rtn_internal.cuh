@@ -173,6 +173,11 @@ struct TrainState {
   int* t_dev = nullptr;                // Adam step counter on the device
   void* wjobs = nullptr;               // per-layer Adam + repack jobs of the one per-step launch
   int wjob_blocks = 0;                 // blocks of that launch
+  // the weight-gradient GEMMs run on a second stream beside the backward
+  // GEMMs (both read only the adjoints of the layer above): the stream and
+  // one event per layer for the fork plus one for the join
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> evs;
 };
 
 // Programmatic dependent launch: the launches of a training step carry the

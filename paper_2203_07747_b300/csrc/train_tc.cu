@@ -737,6 +737,12 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
   const int n_sm = std::max(1, ctx->net.tc.n_sm);
   const std::vector<int>& w = net.widths;
   cudaError_t e;
+  if (!ts.side) {
+    if ((e = cudaStreamCreateWithFlags(&ts.side, cudaStreamNonBlocking))) return e;
+    ts.evs.assign(L + 1, nullptr);
+    for (auto& ev : ts.evs)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return e;
+  }
   if (!ts.grad) {
     ts.nw = ts.nb = 0;
     for (int l = 0; l < L; ++l) {
@@ -895,10 +901,17 @@ static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const
                       bs, no, ts.ldf, ts.gn[2 * (L - 1)], ts.gn[2 * (L - 1) + 1], ts.gf[2 * (L - 1)],
                       ts.gf[2 * (L - 1) + 1], loss, ts.grad + ts.b_base + net.b_off[L - 1], k_dev, per_epoch)))
     return e;
+  // the weight gradient of layer l (dW_l = G_{l+1} A_l') and the backward
+  // GEMM below it (G_l) read only G_{l+1}: the weight gradients go to the
+  // side stream, forked once G_{l+1} is complete, joined before the return
   for (int l = L - 1; l >= 0; --l) {
-    if ((e = tg_launch(P->wg[l], net.tc.err, s))) return e;
+    if ((e = cudaEventRecord(ts.evs[l], s))) return e;
+    if ((e = cudaStreamWaitEvent(ts.side, ts.evs[l], 0))) return e;
+    if ((e = tg_launch(P->wg[l], net.tc.err, ts.side))) return e;
     if (l >= 1 && (e = tg_launch(P->bwd[l], net.tc.err, s))) return e;
   }
+  if ((e = cudaEventRecord(ts.evs[L], ts.side))) return e;
+  if ((e = cudaStreamWaitEvent(s, ts.evs[L], 0))) return e;
   return cudaGetLastError();
 }
 
@@ -945,6 +958,9 @@ cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts) {
 
 void train_release(rtn_ctx* ctx) {
   TrainState& ts = ctx->train;
+  for (cudaEvent_t ev : ts.evs)
+    if (ev) cudaEventDestroy(ev);
+  if (ts.side) cudaStreamDestroy(ts.side);
   free_bufs(ts);
   for (auto* p : ts.ws) if (p) cudaFree(p);
   for (void* p : {(void*)ts.grad, (void*)ts.m, (void*)ts.v, (void*)ts.t_dev, ts.wjobs}) if (p) cudaFree(p);
