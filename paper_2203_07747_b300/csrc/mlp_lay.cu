@@ -1327,6 +1327,10 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
   LayState* s = new (std::nothrow) LayState();
   if (!s) return cudaErrorMemoryAllocation;
   tc.lay = s;
+  cudaError_t es = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+  if (es == cudaSuccess) es = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+  if (es == cudaSuccess) es = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+  if (es != cudaSuccess) return es;
   s->hs = HP;
   s->npad = (int)npad;
   s->fp8 = ctx->opt.precision == RTN_FP8;
@@ -1582,6 +1586,9 @@ void mlp_lay_set_pair(rtn_ctx* ctx, bool pair) {
 void mlp_lay_release(rtn_ctx* ctx) {
   LayState* s = ctx->net.tc.lay;
   if (!s) return;
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->side) cudaStreamDestroy(s->side);
   for (int b = 0; b < 2; ++b)
     for (int p = 0; p < 2; ++p)
       if (s->xb[b][p]) cudaFree(s->xb[b][p]);
@@ -1634,6 +1641,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     memcpy(&r.b3, m[2], sizeof(CUtensorMap));
     return r;
   };
+  cudaError_t le = cudaSuccess;
   // an event before each launch when the pass is timed
   s->n_marks = 0;
   auto mark = [&](int kind) {
@@ -1725,14 +1733,22 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     }
   }
   // f_D (and, with no hidden->hidden layer, the last layer's adjoints into
-  // adjoint buffer 0)
+  // adjoint buffer 0).  With hidden->hidden layers f_D reads only a_{L-1}
+  // and nothing in the pass reads f_D, so it runs on the side stream beside
+  // the first backward GEMM (launched first, so that its CTAs are placed
+  // before the output layer's blocks take the SMs' other slots) and joins at
+  // the pass's end; in a timed pass it stays in line
+  const bool side_fd = nh >= 1 && net.widths[L - 1] % 8 == 0 && !s->timing;
+  if (side_fd && (le = cudaEventRecord(s->ev_fork, st)) != cudaSuccess) return le;
   {
     const __nv_bfloat16* aLh = s->act[0] + (size_t)(L - 2) * dstride;
     const __nv_bfloat16* aLl = s->act[1] + (size_t)(L - 2) * dstride;
     const long long warps = n;
     const int blocks = (int)std::min<long long>((warps + 7) / 8, 148LL * 64);
     mark(3);
-    if (nh >= 1 && net.widths[L - 1] % 8 == 0)
+    if (side_fd) {
+      // launched on the side stream after the first backward GEMM (below)
+    } else if (nh >= 1 && net.widths[L - 1] % 8 == 0)
       lay_fd_kernel<<<blocks, 256, 0, st>>>(tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs, aLh, aLl,
                                             fD, HP);
     else
@@ -1775,6 +1791,16 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
     mark(4);
     lay_kernel<LY_BW0><<<grid_of((long long)gf * a.mts), Ly<LY_BW0>::THREADS, ly_smem<LY_BW0>(), st>>>(
         *reinterpret_cast<const CUtensorMap*>(s->mmap), m, a);
+  }
+  if (side_fd) {
+    const long long warps = n;
+    const int blocks = (int)std::min<long long>((warps + 7) / 8, 148LL * 64);
+    if ((le = cudaStreamWaitEvent(s->side, s->ev_fork, 0)) != cudaSuccess) return le;
+    lay_fd_kernel<<<blocks, 256, 0, s->side>>>(tc.WL32, tc.bias + (size_t)nh * HP, net.widths[L - 1], n, hs,
+                                               s->act[0] + (size_t)(L - 2) * dstride,
+                                               s->act[1] + (size_t)(L - 2) * dstride, fD, HP);
+    if ((le = cudaGetLastError()) != cudaSuccess || (le = cudaEventRecord(s->ev_join, s->side)) != cudaSuccess)
+      return le;
   }
   // the other backward hidden layers: D_l = d_l (.) (W_l' D_{l+1}), l = L - 3 .. 1
   const int gb = (n + LY_NBN - 1) / LY_NBN;
@@ -1857,6 +1883,7 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
                                                                           a);
   }
   if (s->timing && s->n_marks < (int)s->ev.size()) cudaEventRecord(s->ev[s->n_marks], st);
+  if (side_fd && (le = cudaStreamWaitEvent(st, s->ev_join, 0)) != cudaSuccess) return le;
   return cudaGetLastError();
 }
 

@@ -86,6 +86,10 @@ struct LayState {
   alignas(64) unsigned char mw0[128];       // W_0, box 32 x 128
   // per-launch timing of a pass (rtn_tc_launch_times): an event before
   // every launch and after the last, and each launch's kind
+  // the output layer (f_D) runs on a second stream beside the first
+  // backward GEMM (both read only the last forward layer's outputs)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> kind;
