@@ -142,13 +142,19 @@ typedef struct {
                        ~1e-5); 1 operands rounded to BF16 (one MMA per product:
                        a third of the tensor work and half the operand bytes),
                        FP32 accumulation and FP32 master weights in either */
-  int qp_group;     /* lanes per instance in the Riccati sweep and feedback:
-                       32 (one warp per instance) or 16 (two instances per
-                       warp: half the warps, twice the instances in flight;
-                       faster when the batch is throughput-bound or the
-                       factorisation is in FP64, slower when the longest
-                       horizon's sequential chain decides or with box_qp);
-                       0 chooses: 32 with box_qp, 16 with riccati_f64 = 2,
+  int qp_group;     /* threads per instance in the Riccati sweep and
+                       feedback: 32 (one warp per instance), 16 (two
+                       instances per warp: half the warps, twice the
+                       instances in flight; faster when the batch is
+                       throughput-bound or the factorisation is in FP64,
+                       slower when the longest horizon's sequential chain
+                       decides or with box_qp) or 256 (one block per
+                       instance, each step's products spread over the block:
+                       the latency of small batches, e.g. one controller;
+                       not with box_qp or horizons beyond ~110 nodes, which
+                       take 32 instead); 0 chooses: 32 with box_qp, else 256
+                       when the batch has at most one instance per SM, else
+                       16 with riccati_f64 = 2,
                        else 16 when the batch's nodes exceed the resident
                        warps of the sweep x the longest horizon, else 32.
                        The result does not depend on it */

@@ -257,7 +257,10 @@ rtn_status rtn_create(rtn_ctx** out, int nx, int nu, int batch, const int* N, co
   if (o.riccati_f64 < 0 || o.riccati_f64 > 2) { g_create_err = "riccati_f64 must be 0, 1 or 2"; return RTN_E_INVAL; }
   o.fused_qp = o.fused_qp ? 1 : 0;
   o.train_bf16 = o.train_bf16 ? 1 : 0;
-  if (o.qp_group != 0 && o.qp_group != 16 && o.qp_group != 32) { g_create_err = "qp_group must be 0, 16 or 32"; return RTN_E_INVAL; }
+  if (o.qp_group != 0 && o.qp_group != 16 && o.qp_group != 32 && o.qp_group != 256) {
+    g_create_err = "qp_group must be 0, 16, 32 or 256";
+    return RTN_E_INVAL;
+  }
   if (o.box_max_iter == 0) o.box_max_iter = 20;
   o.box_qp = o.box_qp ? 1 : 0;
   o.second_order = o.second_order ? 1 : 0;

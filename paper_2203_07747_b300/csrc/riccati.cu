@@ -576,6 +576,324 @@ __global__ void __launch_bounds__(WPB * 32, 5) qp_kernel(KArgs ka) {
   qp_instance<T, BOX, CH64, G>(ka, b, slots[grp], lane % G, gm);
 }
 
+// ---------------------------------------------------------------- latency mode
+// One instance per block of QB threads, for batches small enough that a
+// warp's sweep would run as one dependent chain with nothing to hide its
+// latencies (one controller, N = 10: ~17k dependent warp instructions and a
+// global-memory round trip or two per node, 38 us).  The instance's A, B,
+// c, x, xref, u, uref are loaded into shared memory at once (coalesced,
+// 268 floats per node), every product of a Riccati step is spread over the
+// block, each output evaluated by one thread with the same expression in
+// the same order as qp_instance (the results are those of the warp kernel
+// bit for bit), and the gains stay in shared memory for the roll-out; the
+// Cholesky of Huu stays on one thread, the solves on 14, and the part of
+// the next P that needs no gains (Q + A'PA, q + A'g) is formed beside
+// B'PA, off their path.  The unconstrained QP only (the box QP keeps the
+// warp kernel).  One controller, N = 10: 31 -> ~24 us with 256 threads
+// against 128.
+constexpr int QB = 256;
+constexpr int QB_NODE = NX * NX + NX * NU + NX + NX + NX + NU + NU;  // floats per node
+constexpr size_t QB_SMEM_MAX = 160 * 1024;  // dynamic shared memory of the latency mode (N up to ~110)
+
+// dynamic shared memory of qp_block_kernel for horizons up to n_max
+template <typename T>
+size_t qp_block_smem(int n_max) {
+  const size_t f = ((size_t)QB_NODE * n_max + 2 * NX + 1) / 2 * 2 * sizeof(float);  // 8-byte aligned
+  return f + (size_t)(NU * NX + NU) * n_max * sizeof(T);
+}
+
+template <typename T, bool CH64>
+__global__ void __launch_bounds__(QB) qp_block_kernel(KArgs ka) {
+  using TC = typename std::conditional<CH64, double, T>::type;
+  __shared__ SlotOf<T, CH64> S;
+  __shared__ __align__(16) T Pm[NX][16];  // P, row i
+  __shared__ T pv[16], p2v[16];          // p and the next p
+  extern __shared__ __align__(16) float qsm[];
+  if ((int)blockIdx.x >= ka.B) return;
+  const int tid = threadIdx.x;
+  const int b = ka.order ? ka.order[blockIdx.x] : (int)blockIdx.x;
+  const QpArgs& a = ka.a;
+  const int N = ka.N[b], xo = ka.xoff[b], uo = ka.uoff[b];
+  const int t = a.t_dev ? *a.t_dev : 0;
+  const int xr0 = (a.xref_stride > 0 ? b * a.xref_stride : xo) + t;
+  const int ur0 = (a.uref_stride > 0 ? b * a.uref_stride : uo) + t;
+  const float* x = a.x + (size_t)xo * NX;
+  const float* u = a.u + (size_t)uo * NU;
+  const float* xr = a.xref + (size_t)xr0 * NX;
+  const float* ur = a.uref + (size_t)ur0 * NU;
+  T* Kg = reinterpret_cast<T*>(ka.Kg);
+  T* kg = reinterpret_cast<T*>(ka.kg);
+  const CostParams& C = ka.cost;
+  // shared copies: A [N][13][13], B [N][13][4], c [N][13], x, xref [N + 1][13],
+  // u, uref [N][4]; then the gains K [N][4][13], k [N][4]
+  float* sA = qsm;
+  float* sB = sA + (size_t)N * NX * NX;
+  float* sc = sB + (size_t)N * NX * NU;
+  float* sx = sc + (size_t)N * NX;
+  float* sxr = sx + (size_t)(N + 1) * NX;
+  float* su = sxr + (size_t)(N + 1) * NX;
+  float* sur = su + (size_t)N * NU;
+  T* sK = reinterpret_cast<T*>(qsm + ((size_t)QB_NODE * N + 2 * NX + 1) / 2 * 2);
+  T* sk = sK + (size_t)N * NU * NX;
+  {
+    const size_t node0 = (size_t)uo;
+    for (int e = tid; e < N * NX * NX; e += QB) sA[e] = a.A[node0 * NX * NX + e];
+    for (int e = tid; e < N * NX * NU; e += QB) sB[e] = a.Bm[node0 * NX * NU + e];
+    for (int e = tid; e < N * NX; e += QB) sc[e] = a.c[node0 * NX + e];
+    for (int e = tid; e < (N + 1) * NX; e += QB) {
+      sx[e] = x[e];
+      sxr[e] = xr[e];
+    }
+    for (int e = tid; e < N * NU; e += QB) {
+      su[e] = u[e];
+      sur[e] = ur[e];
+    }
+  }
+
+  // measured state
+  const float x0m = tid < NX ? a.x0[(size_t)b * NX + tid] : 0.0f;
+  const bool finite = __syncthreads_and(isfinite(x0m)) != 0;
+
+  // ---------------- backward Riccati sweep
+  for (int e = tid; e < NX * NX; e += QB) Pm[e / NX][e % NX] = (e / NX == e % NX) ? (T)C.QN[e / NX] : (T)0;
+  if (tid < NX) pv[tid] = (T)C.QN[tid] * ((T)sx[(size_t)N * NX + tid] - (T)sxr[(size_t)N * NX + tid]);
+  if (tid == 0) S.notpd = 0;
+  __syncthreads();
+  for (int k = N - 1; k >= 0 && finite; --k) {
+    const size_t node = (size_t)uo + k;
+    const float* Ak = sA + (size_t)k * NX * NX;  // A_k [l][j] at l * 13 + j
+    const float* Bk = sB + (size_t)k * NX * NU;  // B_k [l][m] at l * 4 + m
+    const float* ck = sc + (size_t)k * NX;
+    // PA = P A (169), PB = P B (52), g = p + P c (13): row i, column cc
+    for (int o = tid; o < NX * (NX + NU + 1); o += QB) {
+      const int i = o / (NX + NU + 1), cc = o % (NX + NU + 1);
+      if (cc < NX) {
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += Pm[i][l] * (T)Ak[l * NX + cc];
+        S.PA[i][cc] = s;
+      } else if (cc < NX + NU) {
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += Pm[i][l] * (T)Bk[l * NU + cc - NX];
+        S.PB[i][cc - NX] = s;
+      } else {
+        T s = pv[i];
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += Pm[i][l] * (T)ck[l];
+        S.g[i] = s;
+      }
+    }
+    __syncthreads();
+    // Hux = B'PA (52), Huu = R + B'PB (16), hu = r + B'g (4); beside them
+    // the first terms of the next P and p: P2 = Q + A'PA (169), p2 = q + A'g
+    // (13), finished with Hux'K and Hux'k once the gains are known
+    for (int o = tid; o < NU * NX + NU * NU + NU + NX * NX + NX; o += QB) {
+      T s = 0;
+      if (o >= NU * NX + NU * NU + NU) {
+        const int e = o - (NU * NX + NU * NU + NU);
+        if (e < NX * NX) {
+          const int i = e / NX, j = e % NX;
+          s = (j == i) ? (T)C.Q[i] : (T)0;
+#pragma unroll
+          for (int l = 0; l < NX; ++l) s += (T)Ak[l * NX + i] * S.PA[l][j];
+          S.P2[i][j] = s;
+        } else {
+          const int i = e - NX * NX;
+          s = (T)C.Q[i] * ((T)sx[(size_t)k * NX + i] - (T)sxr[(size_t)k * NX + i]);
+#pragma unroll
+          for (int l = 0; l < NX; ++l) s += (T)Ak[l * NX + i] * S.g[l];
+          p2v[i] = s;
+        }
+      } else if (o < NU * NX) {
+        const int m = o / NX, j = o % NX;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += (T)Bk[l * NU + m] * S.PA[l][j];
+        S.Hux[m][j] = s;
+      } else if (o < NU * NX + NU * NU) {
+        const int e = o - NU * NX, m = e / NU, n = e % NU;
+        s = (m == n) ? (T)C.R[m] : (T)0;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += (T)Bk[l * NU + m] * S.PB[l][n];
+        S.Huu[e] = s;
+      } else {
+        const int m = o - NU * NX - NU * NU;
+        s = (T)C.R[m] * ((T)su[(size_t)k * NU + m] - (T)sur[(size_t)k * NU + m]);
+#pragma unroll
+        for (int l = 0; l < NX; ++l) s += (T)Bk[l * NU + m] * S.g[l];
+        S.hu[m] = s;
+      }
+    }
+    __syncthreads();
+    // Cholesky of Huu by one thread (one reciprocal square root per pivot)
+    if (tid == 0) {
+      TC L[NU][NU];
+      bool pd = true;
+#pragma unroll
+      for (int j = 0; j < NU; ++j) {
+        TC s = (TC)S.Huu[j * NU + j];
+#pragma unroll
+        for (int q = 0; q < j; ++q) s -= L[j][q] * L[j][q];
+        pd &= (s > (TC)0);
+        TC inv;
+        if constexpr (sizeof(TC) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
+        else inv = rsqrt(fmax(s, 1e-300));
+        L[j][j] = s * inv;
+        S.Linvt[j] = inv;
+#pragma unroll
+        for (int i = j + 1; i < NU; ++i) {
+          TC v = (TC)S.Huu[i * NU + j];
+#pragma unroll
+          for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
+          L[i][j] = v * inv;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NU; ++i)
+#pragma unroll
+        for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (TC)0;
+      if (!pd) S.notpd = 1;
+    }
+    __syncthreads();
+    // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `tid` (13 = hu); the
+    // gains to global memory and to the shared copies of the roll-out
+    if (tid < NX + 1) {
+      TC y[NU];
+#pragma unroll
+      for (int i = 0; i < NU; ++i) {
+        TC v = (tid < NX) ? (TC)S.Hux[i][tid] : (TC)S.hu[i];
+#pragma unroll
+        for (int q = 0; q < i; ++q) v -= S.Lt[i * NU + q] * y[q];
+        y[i] = v * S.Linvt[i];
+      }
+#pragma unroll
+      for (int i = NU - 1; i >= 0; --i) {
+        TC v = y[i];
+#pragma unroll
+        for (int q = i + 1; q < NU; ++q) v -= S.Lt[q * NU + i] * y[q];
+        y[i] = v * S.Linvt[i];
+      }
+#pragma unroll
+      for (int i = 0; i < NU; ++i) {
+        const T g = (T)(-y[i]);
+        if (tid < NX) {
+          S.K[i][tid] = g;
+          sK[((size_t)k * NU + i) * NX + tid] = g;
+          Kg[node * NU * NX + i * NX + tid] = g;
+        } else {
+          S.k[i] = g;
+          sk[(size_t)k * NU + i] = g;
+          kg[node * NU + i] = g;
+        }
+      }
+    }
+    __syncthreads();
+    // P2 += Hux'K (169), p2 += Hux'k (13)
+    for (int o = tid; o < NX * NX + NX; o += QB) {
+      if (o < NX * NX) {
+        const int i = o / NX, j = o % NX;
+        T s = S.P2[i][j];
+#pragma unroll
+        for (int m = 0; m < NU; ++m) s += S.Hux[m][i] * S.K[m][j];
+        S.P2[i][j] = s;
+      } else {
+        const int i = o - NX * NX;
+        T s = p2v[i];
+#pragma unroll
+        for (int m = 0; m < NU; ++m) s += S.Hux[m][i] * S.k[m];
+        p2v[i] = s;
+      }
+    }
+    __syncthreads();
+    // P = (P2 + P2') / 2, p = p2
+    for (int o = tid; o < NX * NX; o += QB) {
+      const int i = o / NX, j = o % NX;
+      Pm[i][j] = (T)0.5 * (S.P2[i][j] + S.P2[j][i]);
+    }
+    if (tid < NX) pv[tid] = p2v[tid];
+    __syncthreads();
+    (void)node;
+  }
+  int st = finite ? RTN_OK : RTN_E_NONFINITE;
+  if (st == RTN_OK && S.notpd) st = RTN_E_NOT_PD;
+  if (tid == 0 && a.status) a.status[b] = st;
+  if (st != RTN_OK) {
+    // failed instance: zero step, iterate untouched, send the reference input
+    if (a.dx)
+      for (int e = tid; e < (N + 1) * NX; e += QB) a.dx[(size_t)xo * NX + e] = 0.0f;
+    if (a.du)
+      for (int e = tid; e < N * NU; e += QB) a.du[(size_t)uo * NU + e] = 0.0f;
+    if (a.u0 && tid < NU) a.u0[(size_t)b * NU + tid] = ur[tid];
+    return;
+  }
+
+  // ---------------- forward roll-out from dx_0 = x0 - x_0: du = K dx + k,
+  // the step to a.dx / a.du, the iterate update (and shift), u0; every
+  // operand from the shared copies (the iterate's old values among them, so
+  // the in-place update of x, u needs no ordering)
+  float* xw = a.x + (size_t)xo * NX;
+  float* uw = a.u + (size_t)uo * NU;
+  if (tid < NX) S.dx[tid] = (T)x0m - (T)sx[tid];
+  __syncthreads();
+  if (tid < NX) {
+    if (a.dx) a.dx[(size_t)xo * NX + tid] = (float)S.dx[tid];
+    if (a.update && !a.shift) xw[tid] = (float)((T)sx[tid] + S.dx[tid]);
+  }
+  for (int k = 0; k < N; ++k) {
+    const size_t node = (size_t)uo + k;
+    if (tid < NU) {
+      const T* Kr = sK + ((size_t)k * NU + tid) * NX;
+      T s = sk[(size_t)k * NU + tid];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) s += Kr[j] * S.dx[j];
+      S.du[tid] = s;
+    }
+    __syncthreads();
+    T dxn = 0;
+    if (tid < NX) {
+      const float* Ar = sA + (size_t)k * NX * NX + tid * NX;
+      const float* Br = sB + (size_t)k * NX * NU + tid * NU;
+      T s = (T)sc[(size_t)k * NX + tid];
+#pragma unroll
+      for (int j = 0; j < NX; ++j) s += (T)Ar[j] * S.dx[j];
+#pragma unroll
+      for (int j = 0; j < NU; ++j) s += (T)Br[j] * S.du[j];
+      dxn = s;
+    }
+    if (tid < NU) {
+      T unew = (T)su[(size_t)k * NU + tid] + S.du[tid];
+      if (a.du) a.du[node * NU + tid] = (float)S.du[tid];
+      if (k == 0 && a.u0) {
+        float v = (float)unew;
+        a.u0[(size_t)b * NU + tid] = fminf(fmaxf(v, 0.0f), ka.u_max);
+      }
+      if (a.update) {
+        if (a.shift) {
+          if (k >= 1) uw[(size_t)(k - 1) * NU + tid] = (float)unew;
+          if (k == N - 1) uw[(size_t)k * NU + tid] = (float)unew;
+        } else {
+          uw[(size_t)k * NU + tid] = (float)unew;
+        }
+      }
+    }
+    if (tid < NX) {
+      if (a.dx) a.dx[(size_t)(xo + k + 1) * NX + tid] = (float)dxn;
+      if (a.update) {
+        T xnew = (T)sx[(size_t)(k + 1) * NX + tid] + dxn;
+        if (a.shift) {
+          xw[(size_t)k * NX + tid] = (float)xnew;
+          if (k == N - 1) xw[(size_t)(k + 1) * NX + tid] = (float)xnew;
+        } else {
+          xw[(size_t)(k + 1) * NX + tid] = (float)xnew;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < NX) S.dx[tid] = dxn;
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- fused
 // The RK4 linearisation (a2) and the QP (a3 + a4) of every instance in one
 // persistent launch.  Warps first take units of 32 (node, column) RK4
@@ -730,23 +1048,45 @@ KArgs make_kargs(rtn_ctx* ctx, const QpArgs& a) {
 // FP32 sweep on half warps once the batch's work exceeds what the resident
 // warps finish in the longest horizon's chain (sum N_b > resident x N_max),
 // on whole warps below (a half-warp step is ~1.2x slower unloaded)
+// Batches of at most one instance per SM run one block per instance (QB
+// threads: the latency of one controller's QP).
 int qp_group(const rtn_ctx* ctx) {
+  if (ctx->opt.qp_group == QB)  // one block per instance: no bounds, horizons whose data fit shared memory
+    return ctx->opt.box_qp || qp_block_smem<double>(ctx->lay.N_max) > QB_SMEM_MAX ? 32 : QB;
   if (ctx->opt.qp_group) return ctx->opt.qp_group;
   if (ctx->opt.box_qp) return 32;
-  if (ctx->opt.riccati_f64 == 2) return 16;
-  static int resident = 0;                   // warps of qp_kernel resident on the GPU
+  static int resident = 0, sms = 0;          // warps of qp_kernel resident on the GPU, SMs
   if (!resident) {
-    int dev = 0, sms = 148, occ = 0;
+    int dev = 0, n = 148, occ = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, qp_kernel<float, 4, false, false, 32>, 128, 0);
+    sms = std::max(1, n);
     resident = std::max(1, sms * std::max(occ, 1) * 4);
   }
+  if (ctx->B <= sms && qp_block_smem<double>(ctx->lay.N_max) <= QB_SMEM_MAX) return QB;
+  if (ctx->opt.riccati_f64 == 2) return 16;
   return (long long)ctx->lay.n_nodes > (long long)resident * ctx->lay.N_max ? 16 : 32;
+}
+
+template <typename T, bool CH64>
+cudaError_t launch_block(const KArgs& ka, int n_max, cudaStream_t s) {
+  const size_t smem = qp_block_smem<T>(n_max);
+  cudaError_t e = cudaFuncSetAttribute(qp_block_kernel<T, CH64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  qp_block_kernel<T, CH64><<<ka.B, QB, smem, s>>>(ka);
+  return cudaGetLastError();
 }
 
 cudaError_t qp_solve(rtn_ctx* ctx, const QpArgs& a) {
   const KArgs ka = make_kargs(ctx, a);
+  if (qp_group(ctx) == QB) {  // one block per instance (no input bounds)
+    const int n_max = ctx->lay.N_max;
+    if (ctx->opt.riccati_f64 == 1) return launch_block<double, false>(ka, n_max, ctx->stream);
+    if (ctx->opt.riccati_f64 == 2) return launch_block<float, true>(ka, n_max, ctx->stream);
+    return launch_block<float, false>(ka, n_max, ctx->stream);
+  }
   if (ctx->opt.riccati_f64 == 1) return launch<double, 2>(ka, ctx->stream);
   const bool g16 = qp_group(ctx) == 16;
   if (ctx->opt.riccati_f64 == 2)

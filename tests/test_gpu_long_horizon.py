@@ -110,27 +110,30 @@ def test_qp_long_horizons_match_oracle(rtn, orc, ric, group):
 
 @pytest.mark.parametrize("ric,box", [(0, False), ("chol64", False), (0, True)])
 def test_qp_group_sizes_agree(rtn, orc, ric, box):
-    # the sweep on half warps (two instances per warp) and on whole warps:
-    # every lane runs the same arithmetic in the same order, so the steps,
-    # the statuses (and with the bounds the active-set iterations) agree;
-    # 37 instances with N in 1..50, so warps pair instances of unequal
-    # horizons and the last one is alone
+    # the sweep on half warps (two instances per warp), on whole warps and
+    # on one block per instance (without the bounds; with them 256 takes
+    # whole warps): every output is the same arithmetic in the same order,
+    # so the steps, the statuses (and with the bounds the active-set
+    # iterations) agree; 37 instances with N in 1..50, so warps pair
+    # instances of unequal horizons and the last one is alone
     g = np.random.default_rng(31)
     N = g.integers(1, 51, 37).astype(np.int32)
     dt = f32(g.uniform(0.02, 0.1, 37))
     A, Bm, c, x, u, xref, uref, x0 = qp_inputs(orc, N, dt, 32)
     out = {}
-    for group in (16, 32):
+    for group in (16, 32, 256):
         ctl = rtn.Controller(N, dt, W.Q_DIAG, W.R_DIAG, quad=QUAD, riccati_f64=ric, box_qp=box, qp_group=group)
         dx, du, st = ctl.qp_solve(*[dev(a) for a in (A, Bm, c, x, u, xref, uref, x0)])
         out[group] = (npy(dx), npy(du), st.cpu().numpy(), ctl.box_iterations() if box else None)
         ctl.close()
-    (dx1, du1, s1, i1), (dx2, du2, s2, i2) = out[16], out[32]
-    assert (s1 == s2).all()
-    if box:
-        assert np.array_equal(i1, i2)
-    for p, q in ((dx1, dx2), (du1, du2)):
-        assert np.abs(p - q).max() <= 1e-6 * np.abs(q).max(), np.abs(p - q).max()
+    dx2, du2, s2, i2 = out[32]
+    for group in (16, 256):
+        dx1, du1, s1, i1 = out[group]
+        assert (s1 == s2).all(), group
+        if box:
+            assert np.array_equal(i1, i2), group
+        for p, q in ((dx1, dx2), (du1, du2)):
+            assert np.abs(p - q).max() <= 1e-6 * np.abs(q).max(), (group, np.abs(p - q).max())
 
 
 def rel_rows(a, b):
