@@ -74,7 +74,9 @@ enum {
                      e4m3 pieces (hi + mid + lo, ~12 significant bits) in
                      three MMAs with FP32 accumulation; the input layer, the
                      folded first backward layer and the Jacobian GEMM as in
-                     RTN_BF16X2.  Layered reverse mode only (tile mode 6);
+                     RTN_BF16X2.  Layered reverse mode only: tile mode 6
+                     by default, mode 7 (the hidden GEMMs on CTA pairs)
+                     selectable where the padded width is a multiple of 256;
                      3-output networks with at least one hidden->hidden
                      layer */
 };
@@ -333,7 +335,7 @@ rtn_status rtn_get_params(rtn_ctx* ctx, float* W, float* b);
  * shape on the context's current iterate (synchronous; 1 warm-up + 3 timed
  * calls each), keep the fastest, return its index and time per call [ms].
  * Only for contexts created with RTN_BF16 / RTN_BF16X2 / RTN_FP8 (FP8: the
- * layered shape only). */
+ * layered shapes, tile modes 6 and 7, only). */
 rtn_status rtn_tc_variants(rtn_ctx* ctx, int* count);
 rtn_status rtn_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages,
                                int* fits);

@@ -548,6 +548,91 @@ __device__ __forceinline__ void bwd_group8(const float (&v)[48], const uint32_t 
   }
 }
 
+// F8 backward: the activations of the tile's first 16-node group (see
+// bwd_load8), loaded before the accumulator is ready
+__device__ __forceinline__ void bwd8_first(const LyArgs& a, int half, int node0, int ic, int tq, uint32_t (&p8)[6]) {
+  if (half == 0)
+    bwd_load8<0>(a, node0, ic, tq, p8);
+  else
+    bwd_load8<1>(a, node0, ic, tq, p8);
+}
+
+// F8 backward epilogue of one tile of NODES nodes: each group's activations
+// are loaded while the one before it is stored.  The group loop is kept
+// rolled: unrolled, the epilogue's code overflows the instruction cache (ncu:
+// no_instruction the top stall, 0.79 ms per launch at the precision workload;
+// rolled 0.53 ms).
+template <int NODES>
+__device__ __forceinline__ void bwd8_tile_epilogue(uint32_t taddr, uint32_t (&p8)[6], int node0, int i, int ic,
+                                                   int tq, bool active, int half, const LyArgs& a) {
+#pragma unroll 1
+  for (int g = 0; g < NODES / 16; ++g) {
+    float v[48];
+    tmem_ld16(taddr + 48 * g, v);
+    tmem_ld16(taddr + 48 * g + 16, v + 16);
+    tmem_ld16(taddr + 48 * g + 32, v + 32);
+    uint32_t n8[6];
+    if (g + 1 < NODES / 16) {
+      if (half == 0)
+        bwd_load8<0>(a, node0 + 16 * (g + 1), ic, tq, n8);
+      else
+        bwd_load8<1>(a, node0 + 16 * (g + 1), ic, tq, n8);
+    }
+    tmem_wait_ld();
+    if (half == 0)
+      bwd_group8<0>(v, p8, node0 + 16 * g, i, tq, active, a);
+    else
+      bwd_group8<1>(v, p8, node0 + 16 * g, i, tq, active, a);
+    if (g + 1 < NODES / 16) {
+#pragma unroll
+      for (int q8 = 0; q8 < 6; ++q8) p8[q8] = n8[q8];
+    }
+  }
+}
+
+// forward / input epilogue of one 16-node chunk ch of the accumulator, row i:
+// a = tanh(acc [* sc] + b) out as BF16 hi + lo (yh, yl), d = 1 - a^2 (dh,
+// dl) and, for RTN_FP8, a * 448 as e4m3 pieces (y8)
+template <bool F8>
+__device__ __forceinline__ void act_chunk_epilogue(uint32_t taddr, int ch, int node0, int i, bool active, float bi,
+                                                   int lane, const LyArgs& a) {
+  float v[16];
+  tmem_ld16(taddr + 16 * ch, v);
+  tmem_wait_ld();
+  float av[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) av[k] = (F8 ? v[k] * a.sc : v[k]) + bi;
+  tanh_batch<16>(av);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int node = node0 + 16 * ch + k;
+    if (active && node < a.n_nodes) {
+      const size_t o = (size_t)node * a.hs + i;
+      __nv_bfloat16 h, l;
+      if (a.dh) {
+        split_bf(1.0f - av[k] * av[k], h, l);
+        a.dh[o] = h;
+        a.dl[o] = l;
+      }
+      if (a.yh) {
+        split_bf(av[k], h, l);
+        a.yh[o] = h;
+        a.yl[o] = l;
+      }
+    }
+  }
+  if (a.y8h) {  // RTN_FP8: a * 448 as e4m3 pieces, four nodes per store
+    const int tq = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float a4[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a4[k] = active ? av[4 * m + k] * 448.0f : 0.0f;
+      store_pieces4(a4, tq, node0 + 16 * ch + 4 * m, a.n_nodes, a.hs, i & ~3, a.y8h, a.y8m, a.y8l);
+    }
+  }
+}
+
 // one GEMM layer over all nodes (see the file comment); MODE selects the
 // operands' shape and the epilogue
 template <int MODE, bool F8 = false>
@@ -759,43 +844,11 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
       // one before it is stored
       uint32_t p8[6];
       const int tq = lane & 3;
-      if (MODE == LY_BWD && F8) {
-        if (half == 0)
-          bwd_load8<0>(a, node0, ic, tq, p8);
-        else
-          bwd_load8<1>(a, node0, ic, tq, p8);
-      }
+      if (MODE == LY_BWD && F8) bwd8_first(a, half, node0, ic, tq, p8);
       if (!mbar_wait_warp(acc_full(acc), aph, abort_flag, a.err, a.wait_cycles)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
-      if (MODE == LY_BWD && F8) {
-        // the group loop is kept rolled: unrolled, the F8 epilogue's code
-        // overflows the instruction cache (ncu: no_instruction the top stall,
-        // 0.79 ms per launch at the precision workload; rolled 0.53 ms)
-#pragma unroll 1
-        for (int g = 0; g < T::NODES / 16; ++g) {
-          float v[48];
-          tmem_ld16(taddr + 48 * g, v);
-          tmem_ld16(taddr + 48 * g + 16, v + 16);
-          tmem_ld16(taddr + 48 * g + 32, v + 32);
-          uint32_t n8[6];
-          if (g + 1 < T::NODES / 16) {
-            if (half == 0)
-              bwd_load8<0>(a, node0 + 16 * (g + 1), ic, tq, n8);
-            else
-              bwd_load8<1>(a, node0 + 16 * (g + 1), ic, tq, n8);
-          }
-          tmem_wait_ld();
-          if (half == 0)
-            bwd_group8<0>(v, p8, node0 + 16 * g, i, tq, active, a);
-          else
-            bwd_group8<1>(v, p8, node0 + 16 * g, i, tq, active, a);
-          if (g + 1 < T::NODES / 16) {
-#pragma unroll
-            for (int q8 = 0; q8 < 6; ++q8) p8[q8] = n8[q8];
-          }
-        }
-      }
+      if (MODE == LY_BWD && F8) bwd8_tile_epilogue<T::NODES>(taddr, p8, node0, i, ic, tq, active, half, a);
       if (MODE == LY_BWD && !F8) {
         if (!bwd_tile_epilogue<T::ACT_RING>(taddr, j, node0, mt, active, a.n_nodes, half, q, lane,
                                             sm + NS * STAGE, sm + (out_s - st0), out_s, act_full(0), act_empty(0),
@@ -815,43 +868,12 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
       }
       for (int ch = half; MODE != LY_BWD && MODE != LY_BW0 && !(MODE == LY_FWD && !F8) && ch < T::N / 16;
            ch += T::EPI / 4) {
-        float v[16];
-        tmem_ld16(taddr + 16 * ch, v);
-        tmem_wait_ld();
         if (T::ACT) {
-          float av[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) av[k] = (F8 ? v[k] * a.sc : v[k]) + bi;
-          tanh_batch<16>(av);
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int node = node0 + 16 * ch + k;
-            if (active && node < a.n_nodes) {
-              const size_t o = (size_t)node * a.hs + i;
-              __nv_bfloat16 h, l;
-              if (a.dh) {
-                split_bf(1.0f - av[k] * av[k], h, l);
-                a.dh[o] = h;
-                a.dl[o] = l;
-              }
-              if (a.yh) {
-                split_bf(av[k], h, l);
-                a.yh[o] = h;
-                a.yl[o] = l;
-              }
-            }
-          }
-          if (a.y8h) {  // RTN_FP8: a * 448 as e4m3 pieces, four nodes per store
-            const int tq = lane & 3;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              float a4[4];
-#pragma unroll
-              for (int k = 0; k < 4; ++k) a4[k] = active ? av[4 * m + k] * 448.0f : 0.0f;
-              store_pieces4(a4, tq, node0 + 16 * ch + 4 * m, a.n_nodes, a.hs, i & ~3, a.y8h, a.y8m, a.y8l);
-            }
-          }
+          act_chunk_epilogue<F8>(taddr, ch, node0, i, active, bi, lane, a);
         } else {
+          float v[16];
+          tmem_ld16(taddr + 16 * ch, v);
+          tmem_wait_ld();
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int c = 16 * ch + k, node = node0 + c / 3, r = c % 3;
@@ -877,12 +899,13 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
 }
 
 // ---------------------------------------------------------------- CTA pairs
-// The split-BF16 backward and forward hidden GEMMs on CTA pairs
+// The backward and forward hidden GEMMs (split BF16 and F8) on CTA pairs
 // (cta_group::2): one pair tile is M = 256 neurons (128 per CTA, its own
 // weight rows) x N (backward 240 = 80 nodes x 3 adjoints, forward 256 nodes;
-// each CTA loads N / 2 rows of B, which the MMA reads across the pair) x K.
-// Each CTA's tensor memory holds its 128 rows x N columns, so the epilogues
-// are the single-CTA ones (activation ring and staged TMA stores).  Every B
+// each CTA loads N / 2 rows of every B piece, which the MMA reads across the
+// pair) x K.  Each CTA's tensor memory holds its 128 rows x N columns, so the
+// epilogues are the single-CTA ones (split BF16: activation ring and staged
+// TMA stores; F8: direct loads and piece stores).  Every B
 // row of a node group is read by two pair tiles instead of four M tiles:
 // per SM 23-24 KB instead of 38-40 KB per K block, the traffic through L2
 // that bounds the single-CTA kernels.  Rank 0 issues the MMAs; both CTAs'
@@ -892,22 +915,25 @@ __global__ void __launch_bounds__(Ly<MODE, F8>::THREADS, 1)
 // measured slower, 0.602 vs 0.592 ms per launch: its epilogue bounds it.)
 constexpr int LB2_STAGES = 6;
 constexpr int LB2_RING = 3;  // backward: activation ring buffers
-template <int MODE>
+template <int MODE, bool F8 = false>
 struct Lb2 {
-  using T = Ly<MODE>;
+  using T = Ly<MODE, F8>;
   static_assert(T::NA == 1, "one weight tile per stage");
-  static constexpr bool RING = MODE == LY_BWD;                        // activation loader warp + ring
+  static constexpr bool RING = MODE == LY_BWD && !F8;                 // activation loader warp + ring
   static constexpr int N_RING = RING ? LB2_RING : 0;
-  static constexpr uint32_t B_BYTES = (uint32_t)(T::N / 2) * 64u;     // one CTA's half of a B tile
+  static constexpr uint32_t B_BYTES = (uint32_t)(T::N / 2) * 64u;     // one CTA's half of a B piece
   static constexpr uint32_t B0 = LY_A_BYTES;                          // B's offset in a stage
-  static constexpr uint32_t LOAD = B0 + 2u * B_BYTES;                  // bytes one CTA loads per stage
+  static constexpr uint32_t LOAD = B0 + (uint32_t)T::NB * B_BYTES;    // bytes one CTA loads per stage
   static constexpr uint32_t STAGE = (LOAD + 1023u) / 1024u * 1024u;   // 1 KB aligned stages
   static constexpr uint32_t RING_BYTES = (uint32_t)N_RING * LY_ACT_BYTES;
   static constexpr int THREADS = 64 + 32 * T::EPI + (RING ? 32 : 0);  // TMA, MMA, epilogue, [loader]
   static constexpr size_t SMEM = LB2_STAGES * STAGE + RING_BYTES + T::OUT_BYTES + 1024 + 512;
 };
-static_assert(Lb2<LY_BWD>::SMEM <= 232448 && Lb2<LY_FWD>::SMEM <= 232448, "shared memory");
-static_assert(Lb2<LY_BWD>::B_BYTES % 512 == 0 && Lb2<LY_FWD>::B_BYTES % 512 == 0, "swizzle atoms");
+static_assert(Lb2<LY_BWD>::SMEM <= 232448 && Lb2<LY_FWD>::SMEM <= 232448 && Lb2<LY_BWD, true>::SMEM <= 232448 &&
+                  Lb2<LY_FWD, true>::SMEM <= 232448,
+              "shared memory");
+static_assert(Lb2<LY_BWD>::B_BYTES % 512 == 0 && Lb2<LY_FWD>::B_BYTES % 512 == 0 && Lb2<LY_BWD, true>::STAGE % 1024 == 0,
+              "swizzle atoms");
 
 // bounded wait with cluster-scope acquire (barriers with arrivals from the
 // peer CTA), every lane of a warp, warp-uniform result
@@ -932,11 +958,11 @@ __device__ __forceinline__ bool wait_cl_warp(uint32_t bar, uint32_t parity, vola
   return __all_sync(0xffffffffu, ok);
 }
 
-template <int MODE>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 1)
+template <int MODE, bool F8 = false>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE, F8>::THREADS, 1)
     lay2_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ LyMaps bm, LyArgs a) {
-  using T = Ly<MODE>;
-  using P = Lb2<MODE>;
+  using T = Ly<MODE, F8>;
+  using P = Lb2<MODE, F8>;
   constexpr int NS = LB2_STAGES, NR = P::N_RING;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t sraw = smem_u32(smem_raw);
@@ -1038,9 +1064,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
         if (elect_one()) {
           const uint32_t sa = st0 + s * P::STAGE, fb = full0 + 8u * s;
           if (rank == 0) mbar_expect_tx(full_bar(s), 2u * P::LOAD);
-          tma_load_2d_pair(sa, &amap, kb * LY_KB, arow, fb);
-          tma_load_2d_pair(sa + P::B0, &bm.bh, kb * LY_KB, brow, fb);
-          tma_load_2d_pair(sa + P::B0 + P::B_BYTES, &bm.bl, kb * LY_KB, brow, fb);
+          tma_load_2d_pair(sa, &amap, kb * T::KB, arow, fb);
+          tma_load_2d_pair(sa + P::B0, &bm.bh, kb * T::KB, brow, fb);
+          tma_load_2d_pair(sa + P::B0 + P::B_BYTES, &bm.bl, kb * T::KB, brow, fb);
+          if (F8) tma_load_2d_pair(sa + P::B0 + 2 * P::B_BYTES, &bm.b3, kb * T::KB, brow, fb);
         }
         __syncwarp();
         if (++s == NS) { s = 0; ph ^= 1u; }
@@ -1052,9 +1079,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
       if (++s == NS) { s = 0; ph ^= 1u; }
     }
   } else if (run && warp == 1 && rank == 0) {
-    // ---------------- MMA issuer of the pair: two K steps per 64 B row, B's
-    // hi and lo halves, M = 256
-    constexpr uint32_t idesc = idesc_bf16(256, T::N);
+    // ---------------- MMA issuer of the pair: two K steps per 64 B row
+    // against B's pieces (hi, lo; F8 hi, mid, lo), M = 256
+    constexpr uint32_t idesc = F8 ? idesc_e4m3(256, T::N) : idesc_bf16(256, T::N);
     int s = 0, acc = 0;
     uint32_t ph = 0, aph = 0;
     bool ok = true;
@@ -1066,16 +1093,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
         if (!(ok = mbar_wait_warp(full_bar(s), ph, abort_flag, a.err, budget))) break;
         tc_fence_after();
         const uint32_t sa = st0 + s * P::STAGE;
-        uint64_t ad[4], bd[4];
+        if constexpr (F8) {
+          uint64_t ad[2], bd[6];
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          const uint64_t aw = kmajor_desc(sa + ks * 32u, LY_SBO, LY_SWZ);
-          ad[2 * ks] = aw;
-          ad[2 * ks + 1] = aw;
-          bd[2 * ks] = kmajor_desc(sa + P::B0 + ks * 32u, LY_SBO, LY_SWZ);
-          bd[2 * ks + 1] = kmajor_desc(sa + P::B0 + P::B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+          for (int ks = 0; ks < 2; ++ks) {
+            ad[ks] = kmajor_desc(sa + ks * 32u, LY_SBO, LY_SWZ);
+#pragma unroll
+            for (int pc = 0; pc < 3; ++pc)
+              bd[3 * ks + pc] = kmajor_desc(sa + P::B0 + pc * P::B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+          }
+          mma2_f8_x6(d, ad, bd, idesc, kb != 0);
+        } else {
+          uint64_t ad[4], bd[4];
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t aw = kmajor_desc(sa + ks * 32u, LY_SBO, LY_SWZ);
+            ad[2 * ks] = aw;
+            ad[2 * ks + 1] = aw;
+            bd[2 * ks] = kmajor_desc(sa + P::B0 + ks * 32u, LY_SBO, LY_SWZ);
+            bd[2 * ks + 1] = kmajor_desc(sa + P::B0 + P::B_BYTES + ks * 32u, LY_SBO, LY_SWZ);
+          }
+          mma2_bf16_x4(d, ad, bd, idesc, kb != 0);
         }
-        mma2_bf16_x4(d, ad, bd, idesc, kb != 0);
         commit2(empty_bar(s), 3);
         if (++s == NS) { s = 0; ph ^= 1u; }
       }
@@ -1134,11 +1173,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Lb2<MODE>::THREADS, 
       const int i = mc * 128 + q * 32 + lane;
       const bool active = i < a.m_rows;
       const float bi = MODE == LY_FWD ? __ldg(a.bias + (active ? i : 0)) : 0.0f;
+      uint32_t p8[6];
+      const int tq = lane & 3;
+      if constexpr (MODE == LY_BWD && F8) bwd8_first(a, half, grp * T::NODES, active ? i : 0, tq, p8);
       if (!wait_cl_warp(acc_full(acc), aph, abort_flag, a.err, budget)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 256u;
-      bool ok;
-      if constexpr (MODE == LY_BWD)
+      bool ok = true;
+      if constexpr (MODE == LY_BWD && F8)
+        bwd8_tile_epilogue<T::NODES>(taddr, p8, grp * T::NODES, i, active ? i : 0, tq, active, half, a);
+      else if constexpr (MODE == LY_FWD && F8)
+        for (int ch = half; ch < T::N / 16; ch += T::EPI / 4)
+          act_chunk_epilogue<true>(taddr, ch, grp * T::NODES, i, active, bi, lane, a);
+      else if constexpr (MODE == LY_BWD)
         ok = bwd_tile_epilogue<LB2_RING>(taddr, j, grp * T::NODES, mc, active, a.n_nodes, half, q, lane,
                                          sm + (ring_s - st0), sm + (out_s - st0), out_s, act_full(0), act_empty(0),
                                          out_full0, out_empty0, &bm.oh, &bm.ol, abort_flag, a.err, budget);
@@ -1549,8 +1596,11 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
     };
     bool ok = enc8(s->q8map, s->q8, (long long)nh * HP, 128) && enc8(s->q8tmap, s->q8t, (long long)nh * HP, 128);
     for (int p = 0; p < 3 && ok; ++p) {
-      ok = enc8(s->a8map[p], s->act8[p], (long long)(L - 1) * npad, LY_NF);
-      for (int b = 0; b < 2 && ok; ++b) ok = enc8(s->b8map[b][p], s->xb8[b][p], 3 * npad, 3 * LY_NBN);
+      ok = enc8(s->a8map[p], s->act8[p], (long long)(L - 1) * npad, LY_NF) &&
+           enc8(s->a8map2[p], s->act8[p], (long long)(L - 1) * npad, LY_NF / 2);
+      for (int b = 0; b < 2 && ok; ++b)
+        ok = enc8(s->b8map[b][p], s->xb8[b][p], 3 * npad, 3 * LY_NBN) &&
+             enc8(s->b8map2[b][p], s->xb8[b][p], 3 * npad, 3 * LY_NBN / 2);
     }
     if (!ok) {
       err = "cuTensorMapEncodeTiled failed (FP8 operands)";
@@ -1561,6 +1611,12 @@ cudaError_t mlp_lay_prepare(rtn_ctx* ctx, std::string& err) {
       return e;
     if ((e = cudaFuncSetAttribute(lay_kernel<LY_BWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)ly_smem<LY_BWD, true>())) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(lay2_kernel<LY_FWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Lb2<LY_FWD, true>::SMEM)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(lay2_kernel<LY_BWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Lb2<LY_BWD, true>::SMEM)) != cudaSuccess)
       return e;
   }
   if ((e = cudaFuncSetAttribute(lay_kernel<LY_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1712,8 +1768,17 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
       a.y8m = s->act8[1] + (size_t)(g + 1) * dstride8;
       a.y8l = s->act8[2] + (size_t)(g + 1) * dstride8;
       if (g < nh - 2) a.yh = a.yl = nullptr;
-      lay_kernel<LY_FWD, true><<<grid_of((long long)gf * a.mts), Ly<LY_FWD, true>::THREADS, ly_smem<LY_FWD, true>(), st>>>(
-          *reinterpret_cast<const CUtensorMap*>(s->q8map), maps8(s->a8map), a);
+      if (s->pair_bwd && a.mts % 2 == 0) {
+        // pair tiles of 256 neurons: each CTA loads half of the pieces' node rows
+        const long long pt = (long long)gf * (a.mts / 2);
+        const int pairs = (int)std::min<long long>(pt, std::max(1, tc.n_sm / 2));
+        lay2_kernel<LY_FWD, true><<<2 * pairs, Lb2<LY_FWD, true>::THREADS, Lb2<LY_FWD, true>::SMEM, st>>>(
+            *reinterpret_cast<const CUtensorMap*>(s->q8map), maps8(s->a8map2), a);
+      } else {
+        lay_kernel<LY_FWD, true><<<grid_of((long long)gf * a.mts), Ly<LY_FWD, true>::THREADS,
+                                   ly_smem<LY_FWD, true>(), st>>>(*reinterpret_cast<const CUtensorMap*>(s->q8map),
+                                                                  maps8(s->a8map), a);
+      }
     } else {
       LyMaps m = maps(s->ma[0], s->ma[1]);
       memcpy(&m.oh, s->mact[0], sizeof(CUtensorMap));  // a_{g+2}: box 128 neurons x 16 nodes
@@ -1840,8 +1905,16 @@ cudaError_t mlp_lay_launch(rtn_ctx* ctx, const float* x, const float* u, float* 
         a.s8 = s->adj_scale[l];
       }
       a.a_row0 = (l - 1) * HP;
-      lay_kernel<LY_BWD, true><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD, true>(), st>>>(
-          *reinterpret_cast<const CUtensorMap*>(s->q8tmap), maps8(s->b8map[src]), a);
+      if (s->pair_bwd && a.mts % 2 == 0) {
+        // pair tiles of 256 neurons: each CTA loads half of the pieces' adjoint rows
+        const long long pt = (long long)gb * (a.mts / 2);
+        const int pairs = (int)std::min<long long>(pt, std::max(1, tc.n_sm / 2));
+        lay2_kernel<LY_BWD, true><<<2 * pairs, Lb2<LY_BWD, true>::THREADS, Lb2<LY_BWD, true>::SMEM, st>>>(
+            *reinterpret_cast<const CUtensorMap*>(s->q8tmap), maps8(s->b8map2[src]), a);
+      } else {
+        lay_kernel<LY_BWD, true><<<grid_of((long long)gb * a.mts), LY_THREADS, ly_smem<LY_BWD, true>(), st>>>(
+            *reinterpret_cast<const CUtensorMap*>(s->q8tmap), maps8(s->b8map[src]), a);
+      }
     } else {
       LyMaps m = maps(s->mb[src][0], s->mb[src][1]);
       memcpy(&m.sh, s->mact[0], sizeof(CUtensorMap));

@@ -455,7 +455,12 @@ int default_variant(int HP, bool split) {
   return best;
 }
 
-// the layered reverse-mode shape (tile mode 6), the only one of RTN_FP8
+// the layered reverse-mode shapes are the only ones of RTN_FP8; the default
+// runs its hidden GEMMs on single CTAs (tile mode 6).  On CTA pairs (mode 7,
+// selectable) the FP8 GEMMs measured slower at the precision workload
+// (backward 0.594 vs 0.535 ms, forward 0.186 vs 0.163 ms per launch): their
+// epilogues, not the operand traffic the pairs halve, bound them, and a pair
+// frees an accumulator only when both CTAs' epilogues are done.
 int layered_variant(int HP) {
   const auto& vs = all_variants();
   for (int i = 0; i < (int)vs.size(); ++i)
@@ -676,7 +681,7 @@ int mlp_tc_variant_info(rtn_ctx* ctx, int idx, int* npc, int* split, int* stages
   if (split) *split = vs[idx].mode;
   if (stages) *stages = vs[idx].stages;
   const bool want = ctx->opt.precision != RTN_BF16;
-  if (ctx->opt.precision == RTN_FP8 && vs[idx].mode != 6) return 1;  // FP8: single-CTA layered only
+  if (ctx->opt.precision == RTN_FP8 && !vs[idx].layered()) return 1;  // FP8: layered tiles only
   return (vs[idx].split() == want && fits(vs[idx], ctx->net.tc.h_pad)) ? 0 : 1;
 }
 

@@ -109,6 +109,8 @@ struct LayState {
   alignas(64) unsigned char q8map[128], q8tmap[128];  // box 64 x 128
   alignas(64) unsigned char a8map[3][128];           // box 64 x 256
   alignas(64) unsigned char b8map[2][3][128];        // box 64 x 240
+  alignas(64) unsigned char a8map2[3][128];          // CTA-pair halves: box 64 x 128
+  alignas(64) unsigned char b8map2[2][3][128];       // box 64 x 120
 };
 
 // Packed network for the tensor-core path -- see mlp_tc.cu.

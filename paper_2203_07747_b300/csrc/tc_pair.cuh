@@ -141,6 +141,25 @@ __device__ __forceinline__ void mma2_bf16_x4(uint32_t d_tmem, const uint64_t (&a
       : "memory");
 }
 
+// the six kind::f8f6f4 MMAs of one 64-byte K block (two K steps of 32 e4m3
+// elements, each against three B pieces) under one election: accumulate into
+// D unless accum0 == 0 for the first
+__device__ __forceinline__ void mma2_f8_x6(uint32_t d_tmem, const uint64_t (&a)[2], const uint64_t (&b)[6],
+                                           uint32_t idesc, uint32_t accum0) {
+  asm volatile(
+      "{\n\t.reg .pred p, t, e;\n\tsetp.ne.b32 p, %10, 0;\n\tsetp.eq.b32 t, %10, %10;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %3, %9, p;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %4, %9, t;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %5, %9, t;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %2, %6, %9, t;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %2, %7, %9, t;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %2, %8, %9, t;\n\t}" ::"r"(d_tmem),
+      "l"(a[0]), "l"(a[1]), "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]), "l"(b[5]), "r"(idesc),
+      "r"(accum0)
+      : "memory");
+}
+
 // arrive on the barrier at this offset in the CTAs of `mask` (bit r = rank r);
 // one elected lane of a converged warp
 __device__ __forceinline__ void commit2(uint32_t bar, uint16_t mask) {

@@ -68,21 +68,36 @@ def test_library_quantisation_matches_workload(rtn):
     ([17, 384, 384, 384, 3], [20] * 70 + [13]),        # several tiles per CTA
 ])
 def test_fp8_network_matches_oracle(rtn, orc, widths, N):
+    # every layered shape the network admits: single CTAs (tile mode 6, the
+    # default) and, where the padded width is a multiple of 256, the hidden
+    # GEMMs on CTA pairs (mode 7; layers with an odd number of 128-neuron
+    # tiles stay on single CTAs)
     layers = fp8_layers(widths, 3)
     N = np.asarray(N, np.int32)
     dt = np.full(len(N), 0.05)
     ctl = rtn.Controller(N, dt, W.Q_DIAG, W.R_DIAG, quad=QUAD, layers=layers, precision="fp8")
-    assert [v[2] for v in ctl.tc_variants()] == [6]
+    hp = (max(widths[1:-1]) + 127) // 128 * 128
+    modes = sorted(v[2] for v in ctl.tc_variants())
+    assert modes == ([6, 7] if hp % 256 == 0 else [6]), modes
     X, U = W.random_nodes(ctl.n_states, 6)
     X, U = f32(X), f32(U[:ctl.n_nodes])
-    fD, JD = ctl.mlp_eval(dev(X), dev(U))
-    assert ctl.device_error() == 0
     fr, Jr, *_ = orc.linearize(QUAD, layers, N, dt, X, U)
-    F, J = fD.double().cpu().numpy(), JD.double().cpu().numpy()
-    assert np.isfinite(F).all() and np.isfinite(J).all()
-    ej = rel_rows(J, Jr)
-    assert ej.max() < 1e-3, (ej.max(), np.median(ej))
-    assert np.abs(F - fr).max() / np.abs(fr).max() < 1e-3
+    got = {}
+    for vi, _, mode, *_ in ctl.tc_variants():
+        ctl.tc_select(vi)
+        fD, JD = ctl.mlp_eval(dev(X), dev(U))
+        assert ctl.device_error() == 0
+        F, J = fD.double().cpu().numpy(), JD.double().cpu().numpy()
+        assert np.isfinite(F).all() and np.isfinite(J).all()
+        ej = rel_rows(J, Jr)
+        assert ej.max() < 1e-3, (mode, ej.max(), np.median(ej))
+        assert np.abs(F - fr).max() / np.abs(fr).max() < 1e-3, mode
+        got[mode] = (F, J)
+    if 7 in got:
+        # the two shapes run the same products: they agree far inside the gate
+        assert rel_rows(got[7][1], got[6][1]).max() < 1e-4
+        assert np.abs(got[7][0] - got[6][0]).max() / np.abs(got[6][0]).max() < 1e-5
+    ctl.close()
 
 
 def test_fp8_rti_step_matches_oracle(rtn, orc):
@@ -101,3 +116,35 @@ def test_fp8_rti_step_matches_oracle(rtn, orc):
     u0r, _, _, str_ = orc.rti_step(QUAD, layers, N, dt, prob["Q"], prob["R"], prob["QN"], X, U, xref, uref, x0)
     assert (st.cpu().numpy() == 0).all() and (str_ == 0).all()
     assert np.abs(u0.double().cpu().numpy() - u0r).max() / np.abs(u0r).max() < 1e-3
+
+
+def test_fp8_full_size_pairs(rtn, orc):
+    # the precision workload at full size (163,840 nodes) with the FP8 hidden
+    # GEMMs on CTA pairs (tile mode 7): f_D and J_D of sampled nodes
+    # (the first, the last, 40 spread over the batch) against the oracle on
+    # the same dequantised weights
+    prob = W.make_problem("cfg3_bf16_precision", seed=0)
+    layers = W.quantize_e4m3(prob["layers"])
+    N = prob["N"]
+    B, nn = len(N), int(N.sum())
+    X, U = W.random_nodes(nn + B, 5)
+    X, U = f32(X), f32(U[:nn])
+    ctl = rtn.Controller(N, f32(prob["dt"]), prob["Q"], prob["R"], QN=prob["QN"], quad=QUAD, layers=layers,
+                         precision="fp8")
+    vi = [v[0] for v in ctl.tc_variants() if v[2] == 7]
+    assert vi
+    ctl.tc_select(vi[0])
+    fD, JD = (t.double().cpu().numpy() for t in ctl.mlp_eval(dev(X), dev(U)))
+    assert ctl.device_error() == 0
+    assert np.isfinite(fD).all() and np.isfinite(JD).all()
+    xo = np.concatenate([[0], np.cumsum(N + 1)])[:-1]
+    uo = np.concatenate([[0], np.cumsum(N)])[:-1]
+    inst = np.repeat(np.arange(B), N)
+    rng = np.random.default_rng(12)
+    for n in sorted(set(rng.choice(nn, 40, replace=False).tolist()) | {0, nn - 1}):
+        b = inst[n]
+        z = np.concatenate([X[xo[b] + (n - uo[b])], U[n]])
+        rf, rJ = orc.mlp_fwd_jac(layers, z)
+        assert np.linalg.norm(JD[n] - rJ) / np.linalg.norm(rJ) < 1e-3, ("J_D", n)
+        assert np.abs(fD[n] - rf).max() / max(np.abs(rf).max(), 1e-3) < 1e-3, ("f_D", n)
+    ctl.close()
