@@ -66,6 +66,8 @@ def test_library_quantisation_matches_workload(rtn):
     ([17, 256, 256, 256, 256, 3], [17, 50, 10, 33]),   # the ragged workload's network
     ([17, 300, 200, 3], [7, 9]),                       # widths off the tile sizes, one hidden->hidden layer
     ([17, 384, 384, 384, 3], [20] * 70 + [13]),        # several tiles per CTA
+    ([17, 512, 300, 512, 3], [20] * 40 + [7]),         # padded to 512: in tile mode 7 the layers with
+                                                       # three 128-neuron tiles run on single CTAs
 ])
 def test_fp8_network_matches_oracle(rtn, orc, widths, N):
     # every layered shape the network admits: single CTAs (tile mode 6, the
