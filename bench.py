@@ -859,6 +859,10 @@ def layered_roofline(ctl, x, u, out, widths, nn, pass_roof, hbm, bf16_burst, pea
             "kernel": f"{lay_kernel_name(dom, mode)}: {dom} of the layered reverse mode ({c} per pass, "
                       f"{100 * t / sum(v[1] for v in tot.values()):.0f}% of the pass)",
             "split_operands": "BF16 hi + lo activations/adjoints: 2 MMAs per product, frac <= 0.5",
+            "tensor_pipe_active_pct": profiled_tensor_pipe(dom, mode),
+            "tensor_pipe_note": "sm__pipe_tensor_cycles_active of this kernel (ncu --set full, 2,048 "
+                                "instances): the pipe counts both MMAs of every split product, frac only "
+                                "the method's reverse-mode FLOPs",
             "hbm_view": {"design_bytes_per_launch": by, "achieved_gbs": by / (ms * 1e-3) / 1e9,
                          "frac_of_hbm": by / (ms * 1e-3) / 1e9 / hbm, "hbm_peak": hbm,
                          "method_bytes_per_launch": A1_METHOD_BYTES_PER_NODE * nn,
@@ -891,6 +895,21 @@ def profiled_layer_traffic(kind, mode=6):
         key = {"backward GEMM": "bwd", "first backward GEMM": "bw0", "forward GEMM": "fwd"}.get(kind)
         r = re.search(r"dram_bytes_per_launch_%s: (\d+)" % key, text) if key else None
         return int(r.group(1)) if r else None
+    except (OSError, AttributeError):
+        return None
+
+
+def profiled_tensor_pipe(kind, mode=6):
+    """sm__pipe_tensor_cycles_active (% of peak) of one kind of layered
+    launch from the committed summary's full-set capture, or None when the
+    kernel sources or the tile mode differ from the capture's."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", LAYERED_PROFILE)).read()
+        if not _profile_current(text, mode):
+            return None
+        key = {"backward GEMM": "bwd", "first backward GEMM": "bw0", "forward GEMM": "fwd"}.get(kind)
+        r = re.search(r"tensor_pipe_active_pct_%s: ([0-9.]+)" % key, text) if key else None
+        return float(r.group(1)) if r else None
     except (OSError, AttributeError):
         return None
 

@@ -61,3 +61,17 @@ def test_clock_summary_keeps_the_timed_window():
     ck.mark(3.0, 3.01)  # no sample inside: the two nearest
     s = ck.summary()
     assert s["samples"] == 2 and s["sm_min_mhz"] == 1800.0
+
+
+def test_profiled_figures_follow_the_committed_summary():
+    # the layered summary under profiles/ was captured on the current kernel
+    # sources in tile mode 7: its DRAM bytes and tensor-pipe activity are read
+    # back per launch kind, and nothing is read for another tile mode or a
+    # launch kind the summary does not cover
+    import bench
+    assert bench.profiled_layer_traffic("backward GEMM", 7) > 0
+    pipe = bench.profiled_tensor_pipe("backward GEMM", 7)
+    assert pipe is not None and 0.0 < pipe <= 100.0
+    assert bench.profiled_tensor_pipe("first backward GEMM", 7) is not None
+    assert bench.profiled_tensor_pipe("backward GEMM", 6) is None
+    assert bench.profiled_tensor_pipe("Jacobian GEMM", 7) is None
