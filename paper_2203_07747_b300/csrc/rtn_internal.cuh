@@ -395,16 +395,17 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
 cudaError_t train_grad(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
                        int start, float* loss);
 // the same for a step captured once and replayed: minibatch (k mod
-// per_epoch) and loss entry losses[k] for k = *k_dev, which
-// train_next_step advances at the end of the step
+// per_epoch) and loss entry losses[k] for k = *k_dev, which train_adam
+// advances at the end of the step; its gather launch advances the Adam
+// step counter ts.t_dev
 cudaError_t train_grad_dev(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
                            const int* k_dev, int per_epoch, float* losses);
-cudaError_t train_next_step(rtn_ctx* ctx, int* k_dev);
 // the partials summed into ts.grad (weights part)
 cudaError_t train_reduce(rtn_ctx* ctx, TrainState& ts);
 // one Adam step of every parameter from the partials and db, with the
-// weight splits refreshed
-cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr);
+// weight splits refreshed, in the replayed step after train_grad_dev (step
+// counter ts.t_dev already advanced); then *k_dev += 1
+cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr, int* k_dev);
 // the split weight copies of the training GEMMs from the current W32
 cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts);
 void train_release(rtn_ctx* ctx);

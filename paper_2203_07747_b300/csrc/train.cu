@@ -190,8 +190,7 @@ rtn_status rtn_train(rtn_ctx* ctx, const float* X, const float* U, const float* 
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
         e = train_grad_dev(ctx, ts, X, U, Y, k_dev, per_epoch, dloss);
-        if (e == cudaSuccess) e = train_adam(ctx, ts, lr);
-        if (e == cudaSuccess) e = train_next_step(ctx, k_dev);
+        if (e == cudaSuccess) e = train_adam(ctx, ts, lr, k_dev);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
       }

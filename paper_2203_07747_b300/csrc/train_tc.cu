@@ -14,8 +14,14 @@
 // contracts over the batch, so it reads them feature-major ([feature][node]).
 // The epilogues write every activation and gradient in both layouts.
 // Tiles: M = 128 rows x N = 128 columns, K in blocks of 32 (64 B swizzle),
-// six TMA stages, two TMEM accumulators; persistent CTAs; one warp issues
-// the TMA copies, one the MMAs, eight run the epilogue.
+// six TMA stages, two TMEM accumulators (256 columns); persistent CTAs; one
+// warp issues the TMA copies, one the MMAs, eight run the epilogue.  Each
+// GEMM of a training step is one tile per CTA and ~2 GFLOP, so much of its
+// time is launch and drain: in the BF16 mode the stages hold hi tiles only
+// (96 KB), and the next GEMM's CTAs (programmatic dependent launch) fit
+// beside the running ones (half the tensor memory each) and run their
+// prologue during its drain; with split operands the stages hold hi + lo
+// tiles (192 KB, one CTA per SM: three stages of 32 KB measured slower).
 #include <algorithm>
 #include <vector>
 
@@ -36,13 +42,15 @@ constexpr uint32_t TG_A_BYTES = 128u * TG_KB * 2u;
 // deep, so the Adam launch summed twice the partial products)
 template <int NT>
 struct Tg {
-  static constexpr int STAGES = NT == 128 ? 6 : 4;
   static constexpr uint32_t B_BYTES = (uint32_t)NT * TG_KB * 2u;
-  static constexpr uint32_t STAGE = 2u * TG_A_BYTES + 2u * B_BYTES;
-  static constexpr size_t SMEM = STAGES * STAGE + 1024 + 256;
+  static constexpr uint32_t STAGE = 2u * TG_A_BYTES + 2u * B_BYTES;  // hi + lo tiles
+  static constexpr uint32_t STAGE1 = TG_A_BYTES + B_BYTES;             // hi tiles
+  static constexpr int STAGES = 6;
+  static constexpr size_t SMEM = STAGES * STAGE + 1024 + 512;     // split operands
+  static constexpr size_t SMEM1 = STAGES * STAGE1 + 1024 + 512;   // BF16 mode
   static constexpr uint32_t TMEM_COLS = 2 * NT;
 };
-static_assert(Tg<128>::SMEM <= 232448, "shared memory");
+static_assert(Tg<128>::SMEM <= 232448 && 2 * (Tg<128>::SMEM1 + 1024) <= 233472, "shared memory");
 
 enum { TG_FWD = 0, TG_OUT = 1, TG_BWD = 2, TG_WG = 3 };
 // N tile of the weight gradient
@@ -74,8 +82,11 @@ struct TgArgs {
 
 template <int MODE, int NT>
 __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant__ TgMaps mp, TgArgs a) {
-  constexpr int TG_STAGES = Tg<NT>::STAGES, TG_N = NT;
-  constexpr uint32_t TG_B_BYTES = Tg<NT>::B_BYTES, TG_STAGE = Tg<NT>::STAGE;
+  constexpr int TG_N = NT, TG_STAGES = Tg<NT>::STAGES;
+  constexpr uint32_t TG_B_BYTES = Tg<NT>::B_BYTES;
+  // a stage holds hi + lo tiles with split operands, hi tiles otherwise
+  const uint32_t TG_STAGE = a.split ? Tg<NT>::STAGE : Tg<NT>::STAGE1;
+  const uint32_t b_off = a.split ? 2u * TG_A_BYTES : TG_A_BYTES;  // B hi within a stage
   extern __shared__ uint8_t smem_raw[];
   const uint32_t sraw = smem_u32(smem_raw);
   const uint32_t pad = (1024u - (sraw & 1023u)) & 1023u;
@@ -136,7 +147,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
           const int kx = (ks * a.nkb + kb) * TG_KB;
           mbar_expect_tx(full_bar(s), a.split ? TG_STAGE : TG_A_BYTES + TG_B_BYTES);
           tma_load_2d(sa, &mp.ah, kx, mt * 128, full_bar(s));
-          tma_load_2d(sa + 2 * TG_A_BYTES, &mp.bh, kx, nt * TG_N, full_bar(s));
+          tma_load_2d(sa + b_off, &mp.bh, kx, nt * TG_N, full_bar(s));
           if (a.split) {
             tma_load_2d(sa + TG_A_BYTES, &mp.al, kx, mt * 128, full_bar(s));
             tma_load_2d(sa + 2 * TG_A_BYTES + TG_B_BYTES, &mp.bl, kx, nt * TG_N, full_bar(s));
@@ -173,7 +184,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tg_kernel(const __grid_constant
         for (int k = 0; k < TG_KB / 16; ++k) {
           const uint64_t ah = kmajor_desc(sa + k * 32u, TG_SBO, TG_SWZ);
           const uint64_t al = kmajor_desc(sa + TG_A_BYTES + k * 32u, TG_SBO, TG_SWZ);
-          const uint64_t bh = kmajor_desc(sa + 2 * TG_A_BYTES + k * 32u, TG_SBO, TG_SWZ);
+          const uint64_t bh = kmajor_desc(sa + b_off + k * 32u, TG_SBO, TG_SWZ);
           const uint64_t bl = kmajor_desc(sa + 2 * TG_A_BYTES + TG_B_BYTES + k * 32u, TG_SBO, TG_SWZ);
           mma_bf16_elect(d, ah, bh, idesc, (kb | k) != 0);
           if (a.split) {
@@ -381,19 +392,23 @@ bool tg_plan(TgGemm& g, int mode, const __nv_bfloat16* ah, const __nv_bfloat16* 
   return true;
 }
 
+// dynamic shared memory of the four GEMM kernels, and the whole carveout as
+// shared memory so that two CTAs (the running GEMM's and the next one's)
+// fit on an SM
+template <typename K>
+cudaError_t tg_attrs(K* k, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
 cudaError_t tg_setup() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(tg_kernel<TG_FWD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Tg<128>::SMEM)))
-    return e;
-  if ((e = cudaFuncSetAttribute(tg_kernel<TG_OUT, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Tg<128>::SMEM)))
-    return e;
-  if ((e = cudaFuncSetAttribute(tg_kernel<TG_BWD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Tg<128>::SMEM)))
-    return e;
-  return cudaFuncSetAttribute(tg_kernel<TG_WG, TG_WG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Tg<TG_WG_NT>::SMEM);
+  if ((e = tg_attrs(tg_kernel<TG_FWD, 128>, Tg<128>::SMEM))) return e;
+  if ((e = tg_attrs(tg_kernel<TG_OUT, 128>, Tg<128>::SMEM))) return e;
+  if ((e = tg_attrs(tg_kernel<TG_BWD, 128>, Tg<128>::SMEM))) return e;
+  return tg_attrs(tg_kernel<TG_WG, TG_WG_NT>, Tg<TG_WG_NT>::SMEM);
 }
 
 // err: the context's device status word (re-read at every launch: the
@@ -401,12 +416,13 @@ cudaError_t tg_setup() {
 cudaError_t tg_launch(const TgGemm& g, int* err, cudaStream_t s) {
   TgArgs a = g.args;
   a.err = err;
+  const size_t sm = a.split ? Tg<128>::SMEM : Tg<128>::SMEM1;
+  static_assert(TG_WG_NT == 128, "one shared-memory size for the four kernels");
   switch (g.mode) {
-    case TG_FWD: return launch_pdl(tg_kernel<TG_FWD, 128>, dim3(g.grid), dim3(TG_THREADS), Tg<128>::SMEM, s, g.maps, a);
-    case TG_OUT: return launch_pdl(tg_kernel<TG_OUT, 128>, dim3(g.grid), dim3(TG_THREADS), Tg<128>::SMEM, s, g.maps, a);
-    case TG_BWD: return launch_pdl(tg_kernel<TG_BWD, 128>, dim3(g.grid), dim3(TG_THREADS), Tg<128>::SMEM, s, g.maps, a);
-    default:
-      return launch_pdl(tg_kernel<TG_WG, TG_WG_NT>, dim3(g.grid), dim3(TG_THREADS), Tg<TG_WG_NT>::SMEM, s, g.maps, a);
+    case TG_FWD: return launch_pdl(tg_kernel<TG_FWD, 128>, dim3(g.grid), dim3(TG_THREADS), sm, s, g.maps, a);
+    case TG_OUT: return launch_pdl(tg_kernel<TG_OUT, 128>, dim3(g.grid), dim3(TG_THREADS), sm, s, g.maps, a);
+    case TG_BWD: return launch_pdl(tg_kernel<TG_BWD, 128>, dim3(g.grid), dim3(TG_THREADS), sm, s, g.maps, a);
+    default: return launch_pdl(tg_kernel<TG_WG, TG_WG_NT>, dim3(g.grid), dim3(TG_THREADS), sm, s, g.maps, a);
   }
 }
 
@@ -436,13 +452,17 @@ __device__ __forceinline__ void split2(float v, __nv_bfloat16& h, __nv_bfloat16&
 }
 
 // z = [x; u] of samples start .. start + bs - 1 as A_0: node-major [rows][32]
-// (features 17..31 zero) and feature-major [17][ldf]; samples j >= bs are 0
+// (features 17..31 zero) and feature-major [17][ldf]; samples j >= bs are 0.
+// In a replayed training step it also advances the Adam step counter t_inc,
+// which only the step's Adam launch, several launches later, reads.
 __global__ void tg_gather_kernel(const float* __restrict__ X, const float* __restrict__ U, int start, int bs,
                                  int ldf, __nv_bfloat16* __restrict__ nh, __nv_bfloat16* __restrict__ nl,
                                  __nv_bfloat16* __restrict__ fh, __nv_bfloat16* __restrict__ fl,
-                                 const int* __restrict__ k_dev, int per_epoch, float* __restrict__ db, int nb) {
+                                 const int* __restrict__ k_dev, int per_epoch, float* __restrict__ db, int nb,
+                                 int* __restrict__ t_inc) {
   pdl_wait();
   pdl_trigger();
+  if (t_inc && blockIdx.x == 0 && threadIdx.x == 0) *t_inc += 1;
   // the bias gradients, which the loss and backward launches accumulate
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nb; e += (long long)gridDim.x * blockDim.x)
     db[e] = 0.0f;
@@ -642,17 +662,42 @@ __global__ void __launch_bounds__(256) tg_split_kernel(WJob J) {
   weights_tile(J, blockIdx.x, blockIdx.y, 0, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f);
 }
 
-// the Adam step (bias-corrected, step t) of every layer's weights in one
-// launch: block -> (layer, 32 x 32 tile) by the jobs' first blocks
-__global__ void __launch_bounds__(256) tg_weights_kernel(const WJob* __restrict__ jobs, int n_jobs, float lr, float b1,
-                                                         float b2, float eps, const int* __restrict__ t_dev) {
+// Adam of the biases: element i of n
+__device__ __forceinline__ void bias_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
+                                          float* __restrict__ v, size_t i, float lr, float b1, float b2, float eps,
+                                          float c1, float c2) {
+  const float g = G[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * g;
+  const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// The Adam step (bias-corrected, step t) of every layer's weights and of the
+// biases in one launch: blocks below wblocks -> (layer, 32 x 32 tile) by the
+// jobs' first blocks, the rest -> 256 biases each.  In a replayed step the
+// first bias block advances the minibatch counter k_inc for the next replay
+// (its readers, the gather and loss launches, ran before this one).
+__global__ void __launch_bounds__(256) tg_weights_kernel(const WJob* __restrict__ jobs, int n_jobs, int wblocks,
+                                                         float lr, float b1, float b2, float eps,
+                                                         const int* __restrict__ t_dev, float* __restrict__ bP,
+                                                         const float* __restrict__ bG, float* __restrict__ bm,
+                                                         float* __restrict__ bv, int nb, int* __restrict__ k_inc) {
   pdl_wait();
   pdl_trigger();
+  const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
+  if ((int)blockIdx.x >= wblocks) {
+    const int bb = (int)blockIdx.x - wblocks;
+    if (bb == 0 && threadIdx.x == 0 && k_inc) *k_inc += 1;
+    const size_t i = (size_t)bb * blockDim.x + threadIdx.x;
+    if (i < (size_t)nb) bias_adam(bP, bG, bm, bv, i, lr, b1, b2, eps, c1, c2);
+    return;
+  }
   int li = 0;
   while (li + 1 < n_jobs && (int)blockIdx.x >= jobs[li + 1].blk0) ++li;
   const WJob J = jobs[li];
   const int b = (int)blockIdx.x - J.blk0;
-  const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
   weights_tile(J, b % J.bx, b / J.bx, 1, lr, b1, b2, eps, c1, c2);
 }
 
@@ -679,23 +724,6 @@ WJob weight_job(const Net& net, const TrainState& ts, int l) {
   J.bx = (w[l] + 31) / 32;
   J.blk0 = 0;
   return J;
-}
-
-// fused Adam of the biases
-__global__ void tg_adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
-                               float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
-                               const int* __restrict__ t_dev) {
-  pdl_wait();
-  pdl_trigger();
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float c1 = 1.0f - powf(b1, (float)*t_dev), c2 = 1.0f - powf(b2, (float)*t_dev);
-  const float g = G[i];
-  const float mi = b1 * m[i] + (1.0f - b1) * g;
-  const float vi = b2 * v[i] + (1.0f - b2) * g * g;
-  m[i] = mi;
-  v[i] = vi;
-  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
 struct TgPlan {
@@ -858,13 +886,6 @@ cudaError_t train_prepare(rtn_ctx* ctx, TrainState& ts, int cap, int bs, std::st
   return cudaSuccess;
 }
 
-// the step counter of a replayed training step, advanced at the step's end
-__global__ void tg_next_step_kernel(int* k_dev) {
-  pdl_wait();
-  pdl_trigger();
-  *k_dev += 1;
-}
-
 static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
                              int start, float* loss, const int* k_dev, int per_epoch);
 
@@ -878,10 +899,6 @@ cudaError_t train_grad_dev(rtn_ctx* ctx, TrainState& ts, const float* X, const f
   return grad_impl(ctx, ts, X, U, Y, 0, losses, k_dev, per_epoch);
 }
 
-cudaError_t train_next_step(rtn_ctx* ctx, int* k_dev) {
-  return launch_pdl(tg_next_step_kernel, dim3(1), dim3(1), 0, ctx->stream, k_dev);
-}
-
 static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const float* U, const float* Y,
                              int start, float* loss, const int* k_dev, int per_epoch) {
   Net& net = ctx->net;
@@ -893,7 +910,8 @@ static cudaError_t grad_impl(rtn_ctx* ctx, TrainState& ts, const float* X, const
   // the gather also zeroes the bias gradients, which the loss and backward
   // launches accumulate atomically
   if ((e = launch_pdl(tg_gather_kernel, dim3(nblk((size_t)ts.ldf * 32)), dim3(256), 0, s, X, U, start, bs, ts.ldf,
-                      ts.an[0], ts.an[1], ts.af[0], ts.af[1], k_dev, per_epoch, ts.grad + ts.b_base, (int)ts.nb)))
+                      ts.an[0], ts.an[1], ts.af[0], ts.af[1], k_dev, per_epoch, ts.grad + ts.b_base, (int)ts.nb,
+                      k_dev ? ts.t_dev : nullptr)))
     return e;
   for (int l = 0; l < L; ++l)
     if ((e = tg_launch(P->fwd[l], net.tc.err, s))) return e;
@@ -925,26 +943,18 @@ cudaError_t train_reduce(rtn_ctx* ctx, TrainState& ts) {
   return cudaGetLastError();
 }
 
-// the Adam step counter (on the device, so that a captured step can be
-// replayed) advanced by one
-__global__ void tg_step_kernel(int* t_dev) {
-  pdl_wait();
-  pdl_trigger();
-  *t_dev += 1;
-}
-
-cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr) {
+// The Adam step of a replayed training step: the step counter on the device
+// (so that a captured step can be replayed) was advanced by the step's
+// gather launch; one launch updates every weight matrix and the biases and
+// advances the minibatch counter k_dev for the next replay.
+cudaError_t train_adam(rtn_ctx* ctx, TrainState& ts, float lr, int* k_dev) {
   Net& net = ctx->net;
   ts.t += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  cudaError_t e;
-  if ((e = launch_pdl(tg_step_kernel, dim3(1), dim3(1), 0, ctx->stream, ts.t_dev))) return e;
-  if ((e = launch_pdl(tg_weights_kernel, dim3(ts.wjob_blocks), WBLOCK, 0, ctx->stream,
-                      static_cast<const WJob*>(ts.wjobs), net.n_layers, lr, b1, b2, eps, (const int*)ts.t_dev)))
-    return e;
-  return launch_pdl(tg_adam_kernel, dim3(nblk(ts.nb)), dim3(256), 0, ctx->stream, net.b32,
-                    (const float*)(ts.grad + ts.b_base), ts.m + ts.nw, ts.v + ts.nw, ts.nb, lr, b1, b2, eps,
-                    (const int*)ts.t_dev);
+  return launch_pdl(tg_weights_kernel, dim3(ts.wjob_blocks + nblk(ts.nb)), WBLOCK, 0, ctx->stream,
+                    static_cast<const WJob*>(ts.wjobs), net.n_layers, ts.wjob_blocks, lr, b1, b2, eps,
+                    (const int*)ts.t_dev, net.b32, (const float*)(ts.grad + ts.b_base), ts.m + ts.nw,
+                    ts.v + ts.nw, (int)ts.nb, k_dev);
 }
 
 cudaError_t train_resplit(rtn_ctx* ctx, TrainState& ts) {
