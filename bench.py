@@ -512,7 +512,7 @@ def bench_fp8(prob, bf16_burst, steps=20):
 
 def bench_riccati(prob, precision, tile, steps=20):
     """The headline closed loop with the other Riccati arithmetics: the FP32
-    sweep with the factorisation of R + B'PB and the gain solves in FP64
+    sweep with the factorisation of R + B'PB in FP64
     (riccati_f64 = 2) and the FP64 sweep (riccati_f64 = 1); RTI steps/s, the
     QP kernel's time per call and tracking RMSE of each."""
     out = {}

@@ -114,8 +114,9 @@ typedef struct {
   int precision;    /* RTN_FP32 / RTN_BF16 / RTN_BF16X2 / RTN_FP8 */
   int riccati_f64;  /* Riccati sweep arithmetic: 0 FP32 (the Cholesky of
                        R + B'PB in FP32); 1 FP64 throughout; 2 FP32 with the
-                       Cholesky of R + B'PB and the solves for the gains
-                       [K | k] in FP64 */
+                       Cholesky of R + B'PB in FP64 (R + B'PB formed in FP32,
+                       its factor rounded to FP32 for the solves of the gains
+                       [K | k]) */
   int shift;        /* 1: shift the iterate by one stage after every RTI step */
   int box_qp;       /* 1: the QP carries the thrust bounds 0 <= u_k + du_k <= u_max
                        (Sec. V) and is solved by a primal-dual active-set method

@@ -186,7 +186,7 @@ class Controller:
             mlp = _MLP(len(layers), w, Wp, bp)
             mlp_p = C.byref(mlp)
         # riccati_f64: False/0 FP32 sweep, True/1 FP64 sweep, "chol64"/2 FP32 sweep
-        # with the factorisation of R + B'PB and the gain solves in FP64
+        # with the factorisation of R + B'PB in FP64
         ric = 2 if riccati_f64 == "chol64" else int(riccati_f64)
         opt = _Opt(PRECISION[precision], ric, int(bool(shift)), int(bool(box_qp)),
                    int(box_max_iter), int(bool(second_order)), int(bool(fused_qp)), int(bool(train_bf16)),

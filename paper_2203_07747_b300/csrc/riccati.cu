@@ -37,7 +37,8 @@
 namespace rtn {
 namespace {
 
-// TC: the type of the factorisation of Huu and of the solves for [K | k]
+// TC: the type of the factorisation of Huu (its factor is kept rounded to T,
+// the type of the solves for [K | k] and of the rest of the sweep)
 template <typename T, typename TC>
 struct __align__(16) Slot {
   T A[NX][16];    // A_k
@@ -48,7 +49,7 @@ struct __align__(16) Slot {
   T Bm[NX][NU], PB[NX][NU];
   T c[16], g[16];  // c_k, p + P c
   T Huu[NU * NU], hu[NU], k[NU];
-  TC Lt[NU * NU], Linvt[NU];  // Cholesky factor of Huu (strict lower part) and 1/diag
+  T Lt[NU * NU], Linvt[NU];  // Cholesky factor of Huu (strict lower part) and 1/diag
   T dx[16], du[NU];
   int notpd;
 };
@@ -258,7 +259,7 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
           if constexpr (sizeof(TC) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
           else inv = rsqrt(fmax(s, 1e-300));
           L[j][j] = s * inv;
-          S.Linvt[j] = inv;
+          S.Linvt[j] = (T)inv;
   #pragma unroll
           for (int i = j + 1; i < NU; ++i) {
             TC v = Hm(i, j);
@@ -270,24 +271,24 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
   #pragma unroll
         for (int i = 0; i < NU; ++i)
   #pragma unroll
-          for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (TC)0;
+          for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? (T)L[i][j] : (T)0;
         if (!pd) S.notpd = 1;
       }
       __syncwarp(gm);
       // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `lane` (13 = hu)
       if (lane < NX + 1) {
-        TC y[NU];
+        T y[NU];
   #pragma unroll
         for (int i = 0; i < NU; ++i) {
-          TC v;
+          T v;
           if (fx[i]) {
-            v = (lane < NX) ? (TC)0 : -(TC)av[i];
+            v = (lane < NX) ? (T)0 : -av[i];
           } else {
-            v = (lane < NX) ? (TC)S.Hux[i][lane] : (TC)S.hu[i];
+            v = (lane < NX) ? S.Hux[i][lane] : S.hu[i];
             if (lane == NX) {
   #pragma unroll
               for (int n = 0; n < NU; ++n)
-                if (fx[n]) v += (TC)S.Huu[i * NU + n] * (TC)av[n];
+                if (fx[n]) v += S.Huu[i * NU + n] * av[n];
             }
           }
   #pragma unroll
@@ -296,15 +297,15 @@ __device__ __forceinline__ void qp_instance(const KArgs& ka, int b, SlotOf<T, CH
         }
   #pragma unroll
         for (int i = NU - 1; i >= 0; --i) {
-          TC v = y[i];
+          T v = y[i];
   #pragma unroll
           for (int q = i + 1; q < NU; ++q) v -= S.Lt[q * NU + i] * y[q];
           y[i] = v * S.Linvt[i];
         }
   #pragma unroll
         for (int i = 0; i < NU; ++i) {
-          if (lane < NX) S.K[i][lane] = (T)(-y[i]);
-          else S.k[i] = (T)(-y[i]);
+          if (lane < NX) S.K[i][lane] = -y[i];
+          else S.k[i] = -y[i];
         }
       }
       __syncwarp(gm);
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(QB) qp_block_kernel(KArgs ka) {
         if constexpr (sizeof(TC) == 4) inv = rsqrtf(fmaxf(s, 1e-30f));
         else inv = rsqrt(fmax(s, 1e-300));
         L[j][j] = s * inv;
-        S.Linvt[j] = inv;
+        S.Linvt[j] = (T)inv;
 #pragma unroll
         for (int i = j + 1; i < NU; ++i) {
           TC v = (TC)S.Huu[i * NU + j];
@@ -751,31 +752,31 @@ __global__ void __launch_bounds__(QB) qp_block_kernel(KArgs ka) {
 #pragma unroll
       for (int i = 0; i < NU; ++i)
 #pragma unroll
-        for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? L[i][j] : (TC)0;
+        for (int j = 0; j < NU; ++j) S.Lt[i * NU + j] = (j < i) ? (T)L[i][j] : (T)0;
       if (!pd) S.notpd = 1;
     }
     __syncthreads();
     // [K | k] = -Huu^{-1} [Hux | hu]: right-hand side `tid` (13 = hu); the
     // gains to global memory and to the shared copies of the roll-out
     if (tid < NX + 1) {
-      TC y[NU];
+      T y[NU];
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
-        TC v = (tid < NX) ? (TC)S.Hux[i][tid] : (TC)S.hu[i];
+        T v = (tid < NX) ? S.Hux[i][tid] : S.hu[i];
 #pragma unroll
         for (int q = 0; q < i; ++q) v -= S.Lt[i * NU + q] * y[q];
         y[i] = v * S.Linvt[i];
       }
 #pragma unroll
       for (int i = NU - 1; i >= 0; --i) {
-        TC v = y[i];
+        T v = y[i];
 #pragma unroll
         for (int q = i + 1; q < NU; ++q) v -= S.Lt[q * NU + i] * y[q];
         y[i] = v * S.Linvt[i];
       }
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
-        const T g = (T)(-y[i]);
+        const T g = -y[i];
         if (tid < NX) {
           S.K[i][tid] = g;
           sK[((size_t)k * NU + i) * NX + tid] = g;
