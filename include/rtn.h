@@ -309,9 +309,9 @@ rtn_status rtn_mse_grad(rtn_ctx* ctx, const float* X, const float* U, const floa
  * backward and weight-gradient GEMMs run on the tcgen05 tensor cores with
  * BF16 hi + lo split operands (three MMAs per product; with
  * rtn_options.train_bf16 BF16 operands, one MMA) and FP32 accumulation,
- * their bias / tanh / tanh' epilogues fused; one fused Adam
- * launch per weight matrix (which also refreshes the split weights) and one
- * for the biases.  Adam state persists across calls.  loss_out (host, may be
+ * their bias / tanh / tanh' epilogues fused; one fused Adam launch per step
+ * for every weight matrix (which also refreshes the split weights) and the
+ * biases.  Adam state persists across calls.  loss_out (host, may be
  * NULL) receives the loss of every step [epochs * (n / batch)].  Afterwards
  * the network copies of the inference kernels and of the plant are
  * refreshed.  Synchronous. */
